@@ -1,0 +1,291 @@
+"""FP64 CPU oracle for the entropic (KBC) D3Q27 step with Grad moving-wall
+boundaries and momentum-exchange coupling (arXiv 1608.04658, Secs. 2-4.1).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` are the only callers.  The library under
+``paper_1608_04658_gb300`` never imports this package and shares no code with
+it; the two meet only through the seeded generators in ``synth``.
+
+The arithmetic lives in ``kbc_oracle.c`` (plain C99, IEEE double, compiled
+without fast-math or FMA contraction); this module is ctypes marshalling.
+Layout of a population array: numpy ``(27, nz, ny, nx)`` float64, direction
+index i = 9(cx+1) + 3(cy+1) + (cz+1).
+
+Parity status per function (pins live in tests/test_oracle_*.py):
+  feq, kbc_split, collide (all modes), gamma_exact, grad, stream/box faces,
+  refill moments, momentum exchange, Couette with Grad walls, shear-wave and
+  Taylor-Green viscosity: pinned.
+  Sphere refill density average and the sphere's Euler update beyond one step:
+  pinned only by invariants (moments of the refilled node, mass accounting).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kbc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
+BODY_NONE, BODY_SPHERE, BODY_PLANES = 0, 1, 2
+MODE_ANALYTIC, MODE_EXACT, MODE_LBGK = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile kbc_oracle.c into oracle/_build/liboracle.so (gcc, -O2, no
+    fast-math, no FMA contraction so x86 and Arm hosts agree)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("face", C.c_int * 6), ("gamma_mode", C.c_int), ("pad_", C.c_int),
+                ("beta", C.c_double), ("rho0", C.c_double), ("u_face", C.c_double * 3)]
+
+
+class Body(C.Structure):
+    _fields_ = [("kind", C.c_int), ("free_motion", C.c_int),
+                ("X", C.c_double * 3), ("U", C.c_double * 3), ("R", C.c_double),
+                ("y_lo", C.c_double), ("y_hi", C.c_double),
+                ("U_lo", C.c_double * 3), ("U_hi", C.c_double * 3),
+                ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3),
+                ("F", C.c_double * 3), ("M", C.c_double * 3)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = build()
+            L = C.CDLL(so)
+            L.orc_lattice.argtypes = [_I, _D]
+            L.orc_feq.argtypes = [C.c_double, _D, _D]
+            L.orc_kbc_split.argtypes = [_D, _D, _D, _D]
+            L.orc_entropy.argtypes = [_D]
+            L.orc_entropy.restype = C.c_double
+            L.orc_gamma_residual.argtypes = [_D, _D, _D, C.c_double, C.c_double]
+            L.orc_gamma_residual.restype = C.c_double
+            L.orc_gamma_exact.argtypes = [_D, _D, _D, C.c_double]
+            L.orc_gamma_exact.restype = C.c_double
+            L.orc_collide.argtypes = [_D, C.c_double, C.c_int, _D]
+            L.orc_collide.restype = C.c_double
+            L.orc_grad.argtypes = [C.c_double, _D, _D, _D]
+            L.orc_create.argtypes = [C.POINTER(Params), C.POINTER(Body)]
+            L.orc_create.restype = C.c_void_p
+            L.orc_destroy.argtypes = [C.c_void_p]
+            L.orc_set_f.argtypes = [C.c_void_p, _D]
+            L.orc_get_f.argtypes = [C.c_void_p, _D]
+            L.orc_get_solid.argtypes = [C.c_void_p, C.c_void_p]
+            L.orc_get_body.argtypes = [C.c_void_p, C.POINTER(Body)]
+            L.orc_set_body.argtypes = [C.c_void_p, C.POINTER(Body)]
+            L.orc_counter.argtypes = [C.c_void_p, C.c_int]
+            L.orc_counter.restype = C.c_long
+            L.orc_init_state.argtypes = [C.c_void_p, _D, _D, C.c_void_p, C.c_double]
+            L.orc_step.argtypes = [C.c_void_p, C.c_int]
+            L.orc_step.restype = C.c_int
+            L.orc_step_sampled.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_long), _D]
+            L.orc_step_sampled.restype = C.c_int
+            L.orc_totals.argtypes = [C.c_void_p, _D]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def lattice():
+    """(c[27,3] int, W[27]) of the D3Q27 lattice."""
+    c = np.zeros((27, 3), dtype=np.int32)
+    w = np.zeros(27)
+    lib().orc_lattice(c.ctypes.data_as(_I), _dp(w))
+    return c.astype(np.int64), w
+
+
+def feq(rho: float, u) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(27)
+    lib().orc_feq(float(rho), _dp(u), _dp(out))
+    return out
+
+
+def kbc_split(f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    fe, ds, dh = np.zeros(27), np.zeros(27), np.zeros(27)
+    lib().orc_kbc_split(_dp(f), _dp(fe), _dp(ds), _dp(dh))
+    return fe, ds, dh
+
+
+def entropy(f) -> float:
+    return lib().orc_entropy(_dp(np.ascontiguousarray(f, dtype=np.float64)))
+
+
+def gamma_residual(ds, dh, fe, beta, g) -> float:
+    return lib().orc_gamma_residual(_dp(np.ascontiguousarray(ds)), _dp(np.ascontiguousarray(dh)),
+                                    _dp(np.ascontiguousarray(fe)), float(beta), float(g))
+
+
+def gamma_exact(ds, dh, fe, beta) -> float:
+    return lib().orc_gamma_exact(_dp(np.ascontiguousarray(ds)), _dp(np.ascontiguousarray(dh)),
+                                 _dp(np.ascontiguousarray(fe)), float(beta))
+
+
+def collide(f, beta: float, mode: int = MODE_ANALYTIC):
+    """Post-collision populations and the stabilizer used."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(27)
+    g = lib().orc_collide(_dp(f), float(beta), int(mode), _dp(out))
+    return out, g
+
+
+def grad(rho: float, u, Pi) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    Pi = np.ascontiguousarray(np.asarray(Pi, dtype=np.float64).reshape(9))
+    out = np.zeros(27)
+    lib().orc_grad(float(rho), _dp(u), _dp(Pi), _dp(out))
+    return out
+
+
+def beta_from_nu(nu: float) -> float:
+    """nu = c_s^2 (1/(2b) - 1/2) with c_s^2 = 1/3 (Sec. 2)."""
+    return 1.0 / (6.0 * nu + 1.0)
+
+
+class Oracle:
+    """Whole-lattice oracle state.  ``faces`` = (x-, x+, y-, y+, z-, z+)."""
+
+    def __init__(self, shape, nu=None, beta=None, faces=(0,) * 6, rho0=1.0,
+                 u_face=(0.0, 0.0, 0.0), gamma_mode=MODE_ANALYTIC, body=None):
+        nx, ny, nz = shape
+        self.shape = (nx, ny, nz)
+        if beta is None:
+            beta = beta_from_nu(nu)
+        p = Params()
+        p.nx, p.ny, p.nz = nx, ny, nz
+        for k in range(6):
+            p.face[k] = int(faces[k])
+        p.gamma_mode = int(gamma_mode)
+        p.beta = float(beta)
+        p.rho0 = float(rho0)
+        for a in range(3):
+            p.u_face[a] = float(u_face[a])
+        self.params = p
+        b = Body() if body is None else body
+        self._ctx = lib().orc_create(C.byref(p), C.byref(b))
+        if not self._ctx:
+            raise MemoryError("oracle allocation failed")
+        self.N = nx * ny * nz
+
+    def __del__(self):
+        if getattr(self, "_ctx", None):
+            lib().orc_destroy(self._ctx)
+            self._ctx = None
+
+    # state ------------------------------------------------------------
+    def set_f(self, f: np.ndarray):
+        nx, ny, nz = self.shape
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(27, nz, ny, nx)
+        lib().orc_set_f(self._ctx, _dp(f))
+
+    def get_f(self) -> np.ndarray:
+        nx, ny, nz = self.shape
+        out = np.empty((27, nz, ny, nx))
+        lib().orc_get_f(self._ctx, _dp(out))
+        return out
+
+    def init_state(self, rho: np.ndarray, u: np.ndarray, xi: np.ndarray | None = None,
+                   amp: float = 0.0):
+        """f = f^eq(rho, u) + amp * W_i * xi_i.  rho: (nz,ny,nx); u: (nz,ny,nx,3);
+        xi: (27,nz,ny,nx) or None."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        if xi is None:
+            lib().orc_init_state(self._ctx, _dp(rho), _dp(u), None, 0.0)
+        else:
+            xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1)
+            lib().orc_init_state(self._ctx, _dp(rho), _dp(u), xi.ctypes.data_as(C.c_void_p),
+                                 float(amp))
+
+    def solid(self) -> np.ndarray:
+        nx, ny, nz = self.shape
+        out = np.empty((nz, ny, nx), dtype=np.uint8)
+        lib().orc_get_solid(self._ctx, out.ctypes.data_as(C.c_void_p))
+        return out
+
+    @property
+    def body(self) -> Body:
+        b = Body()
+        lib().orc_get_body(self._ctx, C.byref(b))
+        return b
+
+    @body.setter
+    def body(self, b: Body):
+        lib().orc_set_body(self._ctx, C.byref(b))
+
+    def counters(self):
+        L = lib()
+        return dict(step=L.orc_counter(self._ctx, 0), boundary=L.orc_counter(self._ctx, 1),
+                    links=L.orc_counter(self._ctx, 2), refill=L.orc_counter(self._ctx, 3))
+
+    # dynamics ---------------------------------------------------------
+    def step(self, n: int = 1):
+        if lib().orc_step(self._ctx, int(n)) != 0:
+            raise MemoryError("oracle step allocation failed")
+
+    def step_sampled(self, nodes) -> np.ndarray:
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        out = np.empty((len(nodes), 27))
+        lib().orc_step_sampled(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_long)),
+                               _dp(out))
+        return out
+
+    def totals(self) -> np.ndarray:
+        """[mass, jx, jy, jz, kinetic energy] over fluid nodes."""
+        out = np.zeros(5)
+        lib().orc_totals(self._ctx, _dp(out))
+        return out
+
+
+def sphere_body(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0, 0.0),
+                mass=None) -> Body:
+    b = Body()
+    b.kind = BODY_SPHERE
+    b.free_motion = 1 if free else 0
+    for a in range(3):
+        b.X[a], b.U[a], b.g[a] = float(X[a]), float(U[a]), float(g[a])
+    b.R = float(R)
+    b.rho_ratio = float(rho_ratio)
+    # m_s = rho_s * pi D^3 / 6 with rho_f = 1 (analytic volume)
+    b.mass = float(mass) if mass is not None else float(rho_ratio) * np.pi * (2 * R) ** 3 / 6.0
+    return b
+
+
+def planes_body(y_lo, y_hi, U_lo=(0.0, 0.0, 0.0), U_hi=(0.0, 0.0, 0.0)) -> Body:
+    b = Body()
+    b.kind = BODY_PLANES
+    b.y_lo, b.y_hi = float(y_lo), float(y_hi)
+    for a in range(3):
+        b.U_lo[a], b.U_hi[a] = float(U_lo[a]), float(U_hi[a])
+    return b

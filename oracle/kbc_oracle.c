@@ -1,0 +1,670 @@
+/*
+ * FP64 CPU oracle for the entropic (KBC) lattice Boltzmann step with Grad
+ * wall boundaries for moving bodies and momentum-exchange force coupling.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * statement of what the GPU path computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * Paper: Dorschner, Chikatamarla, Karlin, "Entropic lattice Boltzmann method
+ * for moving and deforming geometries in three dimensions" (arXiv 1608.04658).
+ *   Sec. 2  Eq. (kineticEq)   stream + convex combination with the mirror state
+ *           Eq. (kbc_relax)   KBC mirror state  k + (2 s^eq - s) + ((1-g) h + g h^eq)
+ *           Eq. (feq_min)     entropic equilibrium (exact D3Q27 product solution)
+ *           Eq. (gamma_min)   exact stabilizer (post-collision entropy minimum)
+ *           analytic stabilizer  g = 1/b - (2 - 1/b) <ds|dh>/<dh|dh>
+ *   Sec. 3  Eq. (grad)        Grad distribution f*(rho, u, Pi)
+ *           Eqs. (pressure, pressure2)  Pi = Pi^eq + Pi^neq
+ *           target velocity / target density (static + dynamic parts), refill
+ *   Sec. 4.1  Newton's equations for the sphere, Euler integration,
+ *             Galilean-invariant momentum exchange (Wen et al.)
+ *
+ * Readings of points the paper leaves open are listed at the top of each
+ * routine that takes them.  All arithmetic is IEEE double.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 27
+
+/* ---------------------------------------------------------------- lattice */
+/* D3Q27: c_i in {-1,0,1}^3 with index i = 9(cx+1) + 3(cy+1) + (cz+1), so the
+ * opposite direction of i is 26 - i.  Weights are products of the 1-D weights
+ * (2/3 for 0, 1/6 for +-1), c_s^2 = 1/3 (Sec. 2, standard D3Q27). */
+static int C[Q][3];
+static double W[Q];
+static int tables_done = 0;
+
+static double w1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+static void tables(void)
+{
+    if (tables_done) return;
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+                int i = 9 * (a + 1) + 3 * (b + 1) + (c + 1);
+                C[i][0] = a; C[i][1] = b; C[i][2] = c;
+                W[i] = w1(a) * w1(b) * w1(c);
+            }
+    tables_done = 1;
+}
+
+static int opp(int i) { return 26 - i; }
+
+void orc_lattice(int *c_out, double *w_out)
+{
+    tables();
+    for (int i = 0; i < Q; ++i) {
+        for (int a = 0; a < 3; ++a) c_out[3 * i + a] = C[i][a];
+        w_out[i] = W[i];
+    }
+}
+
+/* ------------------------------------------------------------ equilibrium */
+/* Eq. (feq_min): minimiser of H = sum f ln(f/W) under fixed rho, j.  The
+ * exact D3Q27 solution (Ansumali, Karlin, Oettinger 2003, cited in Sec. 2) is
+ * a product over the three axes:
+ *   f_i^eq = rho * prod_a  w(c_ia) (2 - S_a) B_a^{c_ia},
+ *   S_a = sqrt(1 + 3 u_a^2),  B_a = (2 u_a + S_a) / (1 - u_a). */
+void orc_feq(double rho, const double *u, double *feq)
+{
+    tables();
+    double fac[3][3]; /* fac[a][c+1] */
+    for (int a = 0; a < 3; ++a) {
+        double S = sqrt(1.0 + 3.0 * u[a] * u[a]);
+        double B = (2.0 * u[a] + S) / (1.0 - u[a]);
+        fac[a][0] = w1(-1) * (2.0 - S) / B;
+        fac[a][1] = w1(0) * (2.0 - S);
+        fac[a][2] = w1(1) * (2.0 - S) * B;
+    }
+    for (int i = 0; i < Q; ++i)
+        feq[i] = rho * fac[0][C[i][0] + 1] * fac[1][C[i][1] + 1] * fac[2][C[i][2] + 1];
+}
+
+/* ---------------------------------------------------------------- moments */
+static void moments(const double *f, double *rho, double *u)
+{
+    double r = 0, j[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        for (int a = 0; a < 3; ++a) j[a] += C[i][a] * f[i];
+    }
+    *rho = r;
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
+}
+
+/* 1-D dual basis of the monomials {1, c, c^2} on {-1,0,1}:
+ * sum_c A_p(c) c^q = delta_pq.  A_0 = 1 - c^2, A_1 = c/2, A_2 = (3c^2 - 2)/2. */
+static double A0(int c) { return 1.0 - (double)(c * c); }
+static double A1(int c) { return 0.5 * c; }
+static double A2(int c) { return 0.5 * (3.0 * c * c - 2.0); }
+
+/* KBC split of the deviation df = f - f^eq (Sec. 2, Eq. kbc_relax).  The
+ * kinematic part k carries the conserved moments, which f and f^eq share, so
+ * dk = 0.  The shear part s carries the deviatoric (traceless) part of the
+ * natural second moments P_ab = sum c_a c_b f; the trace is left in h because
+ * the bulk viscosity relaxes with g*b (Sec. 2, xi = c_s^2 (1/(g b) - 1/2)).
+ * s is rebuilt from its moments with the tensor-product dual basis, so that
+ * its only non-zero natural moments are the deviatoric second moments.
+ * dh = df - ds collects everything else. */
+void orc_kbc_split(const double *f, double *feq, double *ds, double *dh)
+{
+    tables();
+    double rho, u[3];
+    moments(f, &rho, u);
+    orc_feq(rho, u, feq);
+    double df[Q], P[3][3] = {{0}};
+    for (int i = 0; i < Q; ++i) {
+        df[i] = f[i] - feq[i];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) P[a][b] += C[i][a] * C[i][b] * df[i];
+    }
+    double tr = P[0][0] + P[1][1] + P[2][2];
+    double dev[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) dev[a][b] = P[a][b] - (a == b ? tr / 3.0 : 0.0);
+    for (int i = 0; i < Q; ++i) {
+        const int *c = C[i];
+        double s = 0;
+        /* diagonal moments M200, M020, M002 */
+        s += dev[0][0] * A2(c[0]) * A0(c[1]) * A0(c[2]);
+        s += dev[1][1] * A0(c[0]) * A2(c[1]) * A0(c[2]);
+        s += dev[2][2] * A0(c[0]) * A0(c[1]) * A2(c[2]);
+        /* off-diagonal moments M110, M101, M011 */
+        s += dev[0][1] * A1(c[0]) * A1(c[1]) * A0(c[2]);
+        s += dev[0][2] * A1(c[0]) * A0(c[1]) * A1(c[2]);
+        s += dev[1][2] * A0(c[0]) * A1(c[1]) * A1(c[2]);
+        ds[i] = s;
+        dh[i] = df[i] - s;
+    }
+}
+
+/* Entropic scalar product <X|Y> = sum X_i Y_i / f_i^eq (Sec. 2). */
+static double esp(const double *X, const double *Y, const double *feq)
+{
+    double s = 0;
+    for (int i = 0; i < Q; ++i) s += X[i] * Y[i] / feq[i];
+    return s;
+}
+
+/* Discrete entropy H(f) = sum f ln(f/W) (Eq. feq_min). */
+double orc_entropy(const double *f)
+{
+    tables();
+    double H = 0;
+    for (int i = 0; i < Q; ++i) H += f[i] * log(f[i] / W[i]);
+    return H;
+}
+
+/* Left side of Eq. (gamma_min) as a function of the stabilizer g. */
+double orc_gamma_residual(const double *ds, const double *dh, const double *feq,
+                          double beta, double g)
+{
+    double s = 0;
+    for (int i = 0; i < Q; ++i)
+        s += dh[i] * log(1.0 + ((1.0 - beta * g) * dh[i] - (2.0 * beta - 1.0) * ds[i]) / feq[i]);
+    return s;
+}
+
+/* Exact stabilizer: the root of Eq. (gamma_min).  Reading: the root is taken
+ * on the interval of g where every post-collision population stays positive;
+ * there the left side falls monotonically from +inf to -inf (its derivative is
+ * -b sum dh_i^2 / f'_i), so plain bisection to machine precision finds the
+ * unique root.  Returns 2 (the LBGK value) when dh vanishes. */
+double orc_gamma_exact(const double *ds, const double *dh, const double *feq, double beta)
+{
+    double lo = -INFINITY, hi = INFINITY;
+    int any = 0;
+    for (int i = 0; i < Q; ++i) {
+        /* positivity of f'_i:  a_i - g b_i > 0 */
+        double a = feq[i] + dh[i] - (2.0 * beta - 1.0) * ds[i];
+        double b = beta * dh[i];
+        if (b > 0) { any = 1; if (a / b < hi) hi = a / b; }
+        else if (b < 0) { any = 1; if (a / b > lo) lo = a / b; }
+    }
+    if (!any) return 2.0;
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double r = orc_gamma_residual(ds, dh, feq, beta, mid);
+        if (r > 0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* KBC collision (Eqs. kineticEq, kbc_relax):
+ *   f' = (1-b) f + b f^mirr = f - b (2 ds + g dh).
+ * mode 0: analytic stabilizer  g = 1/b - (2 - 1/b) <ds|dh>/<dh|dh>;
+ *         reading: when <dh|dh> underflows (<= 1e-300) g = 2 (dh is then
+ *         zero, so the value does not matter); no clamping of g.
+ * mode 1: exact stabilizer, the root of Eq. (gamma_min).
+ * mode 2: g forced to 2, which is LBGK with relaxation 2b. */
+double orc_collide(const double *f, double beta, int mode, double *out)
+{
+    double feq[Q], ds[Q], dh[Q], g;
+    orc_kbc_split(f, feq, ds, dh);
+    if (mode == 1) {
+        g = orc_gamma_exact(ds, dh, feq, beta);
+    } else if (mode == 2) {
+        g = 2.0;
+    } else {
+        double hh = esp(dh, dh, feq);
+        double sh = esp(ds, dh, feq);
+        g = hh > 1e-300 ? 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh : 2.0;
+    }
+    for (int i = 0; i < Q; ++i) out[i] = f[i] - beta * (2.0 * ds[i] + g * dh[i]);
+    return g;
+}
+
+/* Grad distribution, Eq. (grad), with c_s^2 = 1/3:
+ *   f*_i = W_i [ rho + 3 rho c_i.u + (9/2) (Pi - rho/3 I) : (c_i c_i - 1/3 I) ]. */
+void orc_grad(double rho, const double *u, const double *Pi, double *out)
+{
+    tables();
+    for (int i = 0; i < Q; ++i) {
+        const int *c = C[i];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        double contr = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double P = Pi[3 * a + b] - (a == b ? rho / 3.0 : 0.0);
+                double H = c[a] * c[b] - (a == b ? 1.0 / 3.0 : 0.0);
+                contr += P * H;
+            }
+        out[i] = W[i] * (rho + 3.0 * rho * cu + 4.5 * contr);
+    }
+}
+
+/* Pressure tensor, Eqs. (pressure, pressure2):
+ *   Pi = rho c_s^2 I + rho u u - (rho c_s^2 / (2 b)) (grad u + grad u^T),
+ * with dudx[a][b] = d u_a / d x_b. */
+static void pressure_tensor(double rho, const double *u, double dudx[3][3], double beta, double *Pi)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            Pi[3 * a + b] = (a == b ? rho / 3.0 : 0.0) + rho * u[a] * u[b]
+                            - rho / 3.0 / (2.0 * beta) * (dudx[a][b] + dudx[b][a]);
+}
+
+/* ----------------------------------------------------------------- lattice state */
+enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_EQ = 2, FACE_OUTFLOW = 3 };
+enum { BODY_NONE = 0, BODY_SPHERE = 1, BODY_PLANES = 2 };
+
+typedef struct {
+    int nx, ny, nz;
+    int face[6];       /* x-, x+, y-, y+, z-, z+ */
+    int gamma_mode;    /* 0 analytic, 1 exact root, 2 LBGK */
+    int pad_;
+    double beta;       /* 1/(6 nu + 1) from nu = c_s^2 (1/(2b) - 1/2) */
+    double rho0;
+    double u_face[3];  /* velocity of the equilibrium faces */
+} orc_params;
+
+typedef struct {
+    int kind;
+    int free_motion;   /* 1: integrate translation (Newton + Euler) */
+    double X[3];       /* sphere centre */
+    double U[3];       /* translational velocity */
+    double R;          /* sphere radius */
+    double y_lo, y_hi; /* planes: solid where y < y_lo or y > y_hi */
+    double U_lo[3], U_hi[3];
+    double mass;       /* m_s */
+    double rho_ratio;  /* rho_s / rho_f */
+    double g[3];       /* gravity */
+    double F[3], M[3]; /* hydrodynamic force and torque of the last step */
+} orc_body;
+
+typedef struct {
+    orc_params p;
+    orc_body b;
+    long N;
+    double *fa, *fb;      /* f[i*N + n], post-collision state */
+    uint8_t *solid0;      /* solid at t */
+    uint8_t *solid1;      /* solid at t+1 */
+    double feq_face[Q];
+    long step;
+    long n_links, n_boundary, n_refill;
+} orc_ctx;
+
+static long nid(const orc_ctx *c, int x, int y, int z)
+{
+    return x + (long)c->p.nx * (y + (long)c->p.ny * z);
+}
+
+static int inside_body(const orc_body *b, double x, double y, double z)
+{
+    if (b->kind == BODY_SPHERE) {
+        double dx = x - b->X[0], dy = y - b->X[1], dz = z - b->X[2];
+        return dx * dx + dy * dy + dz * dz < b->R * b->R;
+    }
+    if (b->kind == BODY_PLANES) return y < b->y_lo || y > b->y_hi;
+    return 0;
+}
+
+/* Fraction q of the link from fluid x_b towards the solid node x_b - c where the
+ * wall is crossed: the wall point is x_w = x_b - q c, q in (0, 1]. */
+static double link_q(const orc_body *b, double x, double y, double z, const int *c)
+{
+    if (b->kind == BODY_SPHERE) {
+        double d[3] = {x - b->X[0], y - b->X[1], z - b->X[2]};
+        double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        double cd = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
+        double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        /* |d - s c|^2 = R^2, smaller root */
+        double disc = cd * cd - cc * (dd - b->R * b->R);
+        return (cd - sqrt(disc)) / cc;
+    }
+    if (b->kind == BODY_PLANES) {
+        if (y - c[1] < b->y_lo) return (y - b->y_lo) / c[1];
+        return (b->y_hi - y) / (-c[1]);
+    }
+    return 0.5;
+}
+
+/* Velocity of the body surface at the wall point (translation only: the
+ * sphere and the channel walls do not rotate). */
+static void wall_velocity(const orc_body *b, double y_solid, double *uw)
+{
+    if (b->kind == BODY_PLANES) {
+        const double *v = y_solid < b->y_lo ? b->U_lo : b->U_hi;
+        for (int a = 0; a < 3; ++a) uw[a] = v[a];
+        return;
+    }
+    for (int a = 0; a < 3; ++a) uw[a] = b->U[a];
+}
+
+/* Source of the pull F_i(x) = f'_i(x - c_i).  Box faces (the paper gives none):
+ * per axis, a source outside [0,n) wraps on a periodic face, is clamped to the
+ * face (zero-gradient) on an outflow face, and is marked wall / equilibrium on
+ * those faces.  Precedence when several axes leave the box: wall, then
+ * equilibrium, then the clamped/wrapped interior source.
+ * Returns 0 (interior source in s[]), 1 (wall), 2 (equilibrium). */
+static int pull_source(const orc_ctx *c, int x, int y, int z, int i, int *s)
+{
+    int pos[3] = {x - C[i][0], y - C[i][1], z - C[i][2]};
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    int wall = 0, eq = 0;
+    for (int a = 0; a < 3; ++a) {
+        int face = -1;
+        if (pos[a] < 0) face = c->p.face[2 * a];
+        else if (pos[a] >= n[a]) face = c->p.face[2 * a + 1];
+        if (face < 0) continue;
+        if (face == FACE_PERIODIC) pos[a] = (pos[a] + n[a]) % n[a];
+        else if (face == FACE_OUTFLOW) pos[a] = pos[a] < 0 ? 0 : n[a] - 1;
+        else if (face == FACE_WALL) wall = 1;
+        else eq = 1;
+    }
+    if (wall) return 1;
+    if (eq) return 2;
+    for (int a = 0; a < 3; ++a) s[a] = pos[a];
+    return 0;
+}
+
+/* Neighbour position x + d for finite differences and interpolation: wraps on
+ * periodic faces, otherwise outside the box is unavailable (returns -1). */
+static long neighbour(const orc_ctx *c, int x, int y, int z, int dx, int dy, int dz)
+{
+    int pos[3] = {x + dx, y + dy, z + dz};
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (pos[a] >= 0 && pos[a] < n[a]) continue;
+        int face = pos[a] < 0 ? c->p.face[2 * a] : c->p.face[2 * a + 1];
+        if (face != FACE_PERIODIC) return -1;
+        pos[a] = (pos[a] + n[a]) % n[a];
+    }
+    return nid(c, pos[0], pos[1], pos[2]);
+}
+
+static void node_moments(const orc_ctx *c, const double *f, long n, double *rho, double *u)
+{
+    double g[Q];
+    for (int i = 0; i < Q; ++i) g[i] = f[i * c->N + n];
+    moments(g, rho, u);
+}
+
+/* Velocity gradient by finite differences of the previous-step velocities
+ * (Sec. 3: "computing grad u using a finite difference scheme and the velocity
+ * values from the previous time step").  Reading: central difference where
+ * both face neighbours are available, first-order one-sided where one is,
+ * zero where neither is.  u_centre is the velocity used at the node itself. */
+static void velocity_gradient(const orc_ctx *c, int x, int y, int z, const double *u_centre,
+                              const uint8_t *solid, double dudx[3][3])
+{
+    for (int b = 0; b < 3; ++b) {
+        int e[3] = {0, 0, 0};
+        e[b] = 1;
+        long np = neighbour(c, x, y, z, e[0], e[1], e[2]);
+        long nm = neighbour(c, x, y, z, -e[0], -e[1], -e[2]);
+        int okp = np >= 0 && !solid[np];
+        int okm = nm >= 0 && !solid[nm];
+        double up[3] = {0, 0, 0}, um[3] = {0, 0, 0}, r;
+        if (okp) node_moments(c, c->fa, np, &r, up);
+        if (okm) node_moments(c, c->fa, nm, &r, um);
+        for (int a = 0; a < 3; ++a) {
+            if (okp && okm) dudx[a][b] = 0.5 * (up[a] - um[a]);
+            else if (okp) dudx[a][b] = up[a] - u_centre[a];
+            else if (okm) dudx[a][b] = u_centre[a] - um[a];
+            else dudx[a][b] = 0.0;
+        }
+    }
+}
+
+/* Refill of a node uncovered by the moving body (Sec. 3): the Grad
+ * distribution with the wall velocity, a local density average and the pressure
+ * tensor evaluated as for the wall boundary.  Readings: the density average is
+ * the mean density of the neighbours among the 26 that were fluid at t (rho0 if
+ * none); the velocity is the body velocity at the node; the gradient uses the
+ * node's own wall velocity at its centre and the neighbours fluid at t. */
+static void refill(orc_ctx *c, int x, int y, int z)
+{
+    long n = nid(c, x, y, z);
+    double rsum = 0;
+    int cnt = 0;
+    for (int i = 0; i < Q; ++i) {
+        if (i == 13) continue;
+        long m = neighbour(c, x, y, z, C[i][0], C[i][1], C[i][2]);
+        if (m < 0 || c->solid0[m]) continue;
+        double r, u[3];
+        node_moments(c, c->fa, m, &r, u);
+        rsum += r;
+        cnt++;
+    }
+    double rho = cnt ? rsum / cnt : c->p.rho0;
+    double uw[3];
+    wall_velocity(&c->b, (double)y, uw);
+    double dudx[3][3], Pi[9], f[Q];
+    velocity_gradient(c, x, y, z, uw, c->solid0, dudx);
+    pressure_tensor(rho, uw, dudx, c->p.beta, Pi);
+    orc_grad(rho, uw, Pi, f);
+    for (int i = 0; i < Q; ++i) c->fa[i * c->N + n] = f[i];
+    c->n_refill++;
+}
+
+/* Post-collision state of fluid node (x,y,z) at t+1, written to out[27].
+ * Adds the node's momentum-exchange force and torque to F, M. */
+static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F, double *M)
+{
+    const long N = c->N;
+    const long n = nid(c, x, y, z);
+    double Fi[Q];
+    int missing[Q], nmiss = 0;
+    for (int i = 0; i < Q; ++i) {
+        int s[3];
+        int kind = pull_source(c, x, y, z, i, s);
+        missing[i] = 0;
+        if (kind == 1) Fi[i] = c->fa[opp(i) * N + n];         /* halfway bounce-back */
+        else if (kind == 2) Fi[i] = c->feq_face[i];           /* equilibrium face */
+        else {
+            long m = nid(c, s[0], s[1], s[2]);
+            if (c->solid1[m]) { missing[i] = 1; nmiss++; Fi[i] = 0.0; }
+            else Fi[i] = c->fa[i * N + m];
+        }
+    }
+    if (nmiss) {
+        /* Sec. 3 Grad boundary at x_b.  D = {i : x_b - c_i solid at t+1}. */
+        double q[Q], uw[Q][3];
+        double rho_stat = 0, rho_dyn = 0, utgt[3] = {0, 0, 0};
+        double rb, ub[3];
+        node_moments(c, c->fa, n, &rb, ub);
+        for (int i = 0; i < Q; ++i) {
+            if (!missing[i]) { rho_stat += Fi[i]; continue; }
+            const int *ci = C[i];
+            q[i] = link_q(&c->b, x, y, z, ci);
+            wall_velocity(&c->b, (double)(y - ci[1]), uw[i]);
+            /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
+             * the wall and returns reflected (halfway bounce-back). */
+            rho_stat += c->fa[opp(i) * N + n];
+            rho_dyn += 6.0 * W[i] * c->p.rho0 * (ci[0] * uw[i][0] + ci[1] * uw[i][1] + ci[2] * uw[i][2]);
+            /* target velocity: linear interpolation between the wall point at
+             * -q and the fluid node x_f = x_b + c_i at +1, read at x_b.
+             * Reading: if x_f is not fluid the term is the wall velocity. */
+            long mf = neighbour(c, x, y, z, ci[0], ci[1], ci[2]);
+            if (mf >= 0 && !c->solid1[mf]) {
+                double rf, uf[3];
+                node_moments(c, c->fa, mf, &rf, uf);
+                for (int a = 0; a < 3; ++a) utgt[a] += (q[i] * uf[a] + uw[i][a]) / (1.0 + q[i]);
+            } else {
+                for (int a = 0; a < 3; ++a) utgt[a] += uw[i][a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) utgt[a] /= nmiss;
+        /* Reading: rho_dyn uses the reference density rho0. */
+        double rho = rho_stat + rho_dyn;
+        double dudx[3][3], Pi[9], fs[Q];
+        velocity_gradient(c, x, y, z, ub, c->solid1, dudx);
+        pressure_tensor(rho, utgt, dudx, c->p.beta, Pi);
+        orc_grad(rho, utgt, Pi, fs);
+        for (int i = 0; i < Q; ++i)
+            if (missing[i]) Fi[i] = fs[i];
+        /* Galilean-invariant momentum exchange on each link (Sec. 4.1, Wen et
+         * al.): the fluid hands the body (c_opp - u_w) f'_opp(x_b, t) and gets
+         * back (c_i - u_w) F_i(x_b, t+1).  Torque arm: x_w - X_c. */
+        for (int i = 0; i < Q; ++i) {
+            if (!missing[i]) continue;
+            const int *ci = C[i];
+            double fout = c->fa[opp(i) * N + n];
+            double dF[3];
+            for (int a = 0; a < 3; ++a)
+                dF[a] = (-ci[a] - uw[i][a]) * fout - (ci[a] - uw[i][a]) * Fi[i];
+            double r[3] = {x - q[i] * ci[0] - c->b.X[0], y - q[i] * ci[1] - c->b.X[1],
+                           z - q[i] * ci[2] - c->b.X[2]};
+            F[0] += dF[0]; F[1] += dF[1]; F[2] += dF[2];
+            M[0] += r[1] * dF[2] - r[2] * dF[1];
+            M[1] += r[2] * dF[0] - r[0] * dF[2];
+            M[2] += r[0] * dF[1] - r[1] * dF[0];
+            c->n_links++;
+        }
+        c->n_boundary++;
+    }
+    orc_collide(Fi, c->p.beta, c->p.gamma_mode, out);
+}
+
+/* ------------------------------------------------------------------ public */
+orc_ctx *orc_create(const orc_params *p, const orc_body *b)
+{
+    tables();
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    if (!c) return NULL;
+    c->p = *p;
+    c->b = *b;
+    c->N = (long)p->nx * p->ny * p->nz;
+    c->fa = (double *)calloc((size_t)Q * c->N, sizeof(double));
+    c->solid0 = (uint8_t *)calloc((size_t)c->N, 1);
+    c->solid1 = (uint8_t *)calloc((size_t)c->N, 1);
+    if (!c->fa || !c->solid0 || !c->solid1) return NULL;
+    orc_feq(p->rho0, p->u_face, c->feq_face);
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                c->solid0[nid(c, x, y, z)] = (uint8_t)inside_body(&c->b, x, y, z);
+    return c;
+}
+
+void orc_destroy(orc_ctx *c)
+{
+    if (!c) return;
+    free(c->fa); free(c->fb); free(c->solid0); free(c->solid1); free(c);
+}
+
+void orc_set_f(orc_ctx *c, const double *f) { memcpy(c->fa, f, sizeof(double) * Q * c->N); }
+void orc_get_f(const orc_ctx *c, double *f) { memcpy(f, c->fa, sizeof(double) * Q * c->N); }
+void orc_get_solid(const orc_ctx *c, uint8_t *s) { memcpy(s, c->solid0, (size_t)c->N); }
+void orc_get_body(const orc_ctx *c, orc_body *b) { *b = c->b; }
+void orc_set_body(orc_ctx *c, const orc_body *b) { c->b = *b; }
+long orc_counter(const orc_ctx *c, int which)
+{
+    return which == 0 ? c->step : which == 1 ? c->n_boundary : which == 2 ? c->n_links : c->n_refill;
+}
+
+/* Initial state f = f^eq(rho(x), u(x)) + amp * W_i * xi_i(x) from host fields
+ * rho[N], u[3N] (node-major), xi[27N] (direction-major; NULL for none). */
+void orc_init_state(orc_ctx *c, const double *rho, const double *u, const double *xi, double amp)
+{
+    double feq[Q];
+    for (long n = 0; n < c->N; ++n) {
+        double un[3] = {u[3 * n], u[3 * n + 1], u[3 * n + 2]};
+        orc_feq(rho[n], un, feq);
+        for (int i = 0; i < Q; ++i)
+            c->fa[i * c->N + n] = feq[i] + (xi ? amp * W[i] * xi[i * c->N + n] : 0.0);
+    }
+}
+
+/* Newton's equations of the sphere (Sec. 4.1) by explicit Euler:
+ * X^{t+1} = X^t + U^t,  U^{t+1} = U^t + F^t/m_s + (1 - rho_f/rho_s) g. */
+static void body_update(orc_body *b)
+{
+    if (!b->free_motion) return;
+    for (int a = 0; a < 3; ++a) {
+        double acc = b->F[a] / b->mass + (1.0 - 1.0 / b->rho_ratio) * b->g[a];
+        b->X[a] += b->U[a];
+        b->U[a] += acc;
+    }
+}
+
+/* Geometry and refill for the step t -> t+1: moves the body, marks solid
+ * nodes at t+1 and refills uncovered nodes in the current state. */
+static void step_prepare(orc_ctx *c)
+{
+    body_update(&c->b);
+    const orc_params *p = &c->p;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                c->solid1[nid(c, x, y, z)] = (uint8_t)inside_body(&c->b, x, y, z);
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nid(c, x, y, z);
+                if (c->solid0[n] && !c->solid1[n]) refill(c, x, y, z);
+            }
+}
+
+/* One or more full steps t -> t+1 (stream + collide with Grad boundaries and
+ * momentum exchange).  Solid nodes carry their state unchanged. */
+int orc_step(orc_ctx *c, int nsteps)
+{
+    const orc_params *p = &c->p;
+    if (!c->fb) {
+        c->fb = (double *)calloc((size_t)Q * c->N, sizeof(double));
+        if (!c->fb) return 1;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        step_prepare(c);
+        double F[3] = {0, 0, 0}, M[3] = {0, 0, 0}, out[Q];
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long n = nid(c, x, y, z);
+                    if (c->solid1[n]) {
+                        for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = c->fa[i * c->N + n];
+                        continue;
+                    }
+                    node_update(c, x, y, z, out, F, M);
+                    for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = out[i];
+                }
+        double *t = c->fa; c->fa = c->fb; c->fb = t;
+        uint8_t *u = c->solid0; c->solid0 = c->solid1; c->solid1 = u;
+        for (int a = 0; a < 3; ++a) { c->b.F[a] = F[a]; c->b.M[a] = M[a]; }
+        c->step++;
+    }
+    return 0;
+}
+
+/* One step evaluated only at the listed nodes: moves the body, updates the
+ * solid marks, refills, and writes the new post-collision populations of the
+ * listed nodes to out[k*27 + i] (NaN for nodes solid at t+1).  The state is
+ * left as after the refill, not advanced. */
+int orc_step_sampled(orc_ctx *c, long nsample, const long *nodes, double *out)
+{
+    step_prepare(c);
+    const orc_params *p = &c->p;
+    double F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
+    for (long k = 0; k < nsample; ++k) {
+        long n = nodes[k];
+        int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx * p->ny));
+        if (c->solid1[n]) {
+            for (int i = 0; i < Q; ++i) out[k * Q + i] = NAN;
+            continue;
+        }
+        node_update(c, x, y, z, out + k * Q, F, M);
+    }
+    return 0;
+}
+
+/* Global sums over fluid nodes: mass, momentum (3), kinetic energy. */
+void orc_totals(const orc_ctx *c, double *out)
+{
+    for (int k = 0; k < 5; ++k) out[k] = 0;
+    for (long n = 0; n < c->N; ++n) {
+        if (c->solid0[n]) continue;
+        double r, u[3];
+        node_moments(c, c->fa, n, &r, u);
+        out[0] += r;
+        for (int a = 0; a < 3; ++a) out[1 + a] += r * u[a];
+        out[4] += 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    }
+}

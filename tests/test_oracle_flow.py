@@ -1,0 +1,232 @@
+"""Pins of the oracle's whole step: streaming (Eq. kineticEq, left side), box
+faces, the Grad wall boundary (Sec. 3), refill, momentum exchange and the
+sphere's Euler update (Sec. 4.1), and the viscosity relation (Sec. 2) through
+shear-wave, Taylor-Green and Couette closed forms."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def _u(orc, f):
+    c, _ = orc.lattice()
+    rho = f.sum(0)
+    return np.einsum("ia,izyx->zyxa", c, f) / rho[..., None], rho
+
+
+def test_pure_streaming_is_exact_shift(orc):
+    """beta = 0 in the LBGK form turns the collision off (f' = f), leaving the
+    streaming step f_i(x + c_i, t+1) = f_i(x, t) on a periodic box."""
+    c, _ = orc.lattice()
+    shape = (5, 4, 3)
+    rho, u, xi = synth.parity_fields(shape, 3)
+    o = orc.Oracle(shape, beta=0.0, gamma_mode=orc.MODE_LBGK)
+    o.init_state(rho, u, xi, 0.01)
+    f0 = o.get_f()
+    o.step(1)
+    f1 = o.get_f()
+    for i in range(27):
+        # axes of the array are (z, y, x)
+        ref = np.roll(f0[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2))
+        assert np.array_equal(f1[i], ref)
+
+
+def test_box_faces_with_streaming_only(orc):
+    """Wall faces reflect (F_i = f'_opp at the node itself), equilibrium faces
+    inject f^eq(rho0, u_face), outflow faces copy from the face node."""
+    c, _ = orc.lattice()
+    shape = (4, 3, 3)
+    rho, u, xi = synth.parity_fields(shape, 4)
+    uf = (0.04, 0.01, 0.0)
+    o = orc.Oracle(shape, beta=0.0, faces=(1, 2, 0, 0, 3, 3), u_face=uf,
+                   gamma_mode=orc.MODE_LBGK)
+    o.init_state(rho, u, xi, 0.01)
+    f0 = o.get_f()
+    o.step(1)
+    f1 = o.get_f()
+    fe = orc.feq(1.0, uf)
+    nx, ny, nz = shape
+    for i in range(27):
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    sx, sy, sz = x - c[i, 0], (y - c[i, 1]) % ny, min(max(z - c[i, 2], 0), nz - 1)
+                    if sx < 0:
+                        ref = f0[26 - i, z, y, x]
+                    elif sx >= nx:
+                        ref = fe[i]
+                    else:
+                        ref = f0[i, sz, sy, sx]
+                    assert f1[i, z, y, x] == ref
+
+
+def test_grad_distribution_moments(orc):
+    """Eq. (grad): f* reproduces rho, rho u and Pi exactly (D3Q27 isotropy)."""
+    c, _ = orc.lattice()
+    rng = np.random.default_rng(31)
+    for _ in range(30):
+        rho = 1 + 0.1 * rng.random()
+        u = 0.1 * rng.standard_normal(3)
+        P = 0.01 * rng.standard_normal((3, 3))
+        Pi = rho / 3 * np.eye(3) + rho * np.outer(u, u) + P + P.T
+        f = orc.grad(rho, u, Pi)
+        assert abs(f.sum() - rho) < 1e-15
+        assert np.allclose(c.T @ f, rho * u, atol=1e-16)
+        assert np.allclose(np.einsum("ia,ib,i->ab", c, c, f), Pi, atol=1e-15)
+
+
+def test_shear_wave_decays_at_nominal_viscosity(orc):
+    """nu = c_s^2 (1/(2 beta) - 1/2): a shear wave u_x = u0 sin(k y) decays as
+    exp(-nu k^2 t); on 64 nodes per wavelength the lattice error is below 2e-3."""
+    nu = 0.02
+    shape = (1, 64, 1)
+    o = orc.Oracle(shape, nu=nu)
+    o.init_state(*synth.shear_wave_fields(shape, 1e-3))
+    o.step(100)  # past the initial layer of an equilibrium start
+    amps = []
+    for _ in range(10):
+        ux = _u(orc, o.get_f())[0][0, :, 0, 0]
+        amps.append(np.abs(np.fft.rfft(ux))[1])
+        o.step(100)
+    k = 2 * np.pi / 64
+    rate = -np.diff(np.log(amps)) / 100
+    assert np.allclose(rate, nu * k * k, rtol=2e-3)
+
+
+def test_taylor_green_early_energy_decay(orc):
+    """Taylor-Green vortex: dE/dt = -6 nu k^2 E at early time (k = 2 pi/n)."""
+    n, nu = 32, 0.02
+    shape = (n, n, n)
+    o = orc.Oracle(shape, nu=nu)
+    o.init_state(*synth.taylor_green_fields(shape, 0.01))
+    o.step(10)
+    E = []
+    for _ in range(3):
+        E.append(o.totals()[4])
+        o.step(10)
+    k = 2 * np.pi / n
+    rate = -np.diff(np.log(E)) / 10
+    assert np.allclose(rate, 6 * nu * k * k, rtol=2e-2)
+
+
+def test_tgv_re1600_conserves_mass_and_momentum(orc):
+    """Plain method, periodic 32^3 Taylor-Green at Re = 1600, u0 = 0.05, 100
+    steps: the collision conserves mass and momentum and streaming permutes, so
+    the totals are constant up to round-off."""
+    wl = synth.tgv_periodic(32)
+    o = orc.Oracle(wl["shape"], nu=wl["nu"])
+    o.init_state(*synth.taylor_green_fields(wl["shape"], wl["u0"]))
+    T0 = o.totals()
+    o.step(100)
+    T1 = o.totals()
+    assert abs(T1[0] - T0[0]) < 1e-13 * T0[0]
+    assert np.abs(T1[1:4] - T0[1:4]).max() < 1e-13 * T0[0]
+    assert T1[4] < T0[4]
+
+
+@pytest.mark.parametrize("U", [1e-3, 5e-3])
+def test_couette_with_grad_walls_is_exact(orc, U):
+    """Plane Couette flow between walls at fractional link distance q = 0.3
+    (bottom at rest, top moving with U): the steady profile is linear in y and
+    the Grad boundary with linear interpolation and finite differences
+    reproduces it to round-off."""
+    ny = 20
+    y_lo, y_hi = 1.7, ny - 2 + 0.3
+    body = orc.planes_body(y_lo, y_hi, U_hi=(U, 0, 0))
+    o = orc.Oracle((1, ny, 1), beta=0.5, body=body)
+    o.init_state(*synth.uniform_fields((1, ny, 1)))
+    o.step(20000)
+    u, _ = _u(orc, o.get_f())
+    fluid = o.solid()[0, :, 0] == 0
+    y = np.arange(ny)
+    exact = U * (y - y_lo) / (y_hi - y_lo)
+    assert np.abs(u[0, :, 0, 0] - exact)[fluid].max() < 1e-10 * U
+    assert np.abs(u[0, :, 0, 1:])[fluid].max() < 1e-13
+
+
+def test_momentum_exchange_balances_fluid_momentum(orc):
+    """Stationary sphere in a periodic box: streaming moves momentum between
+    fluid nodes, collision conserves it, so the fluid's momentum change in one
+    step is exactly minus the momentum-exchange force on the body."""
+    shape = (16, 14, 12)
+    body = orc.sphere_body((7.3, 6.6, 5.8), 3.1)
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    rho, u, xi = synth.parity_fields(shape, 5)
+    o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
+    for _ in range(3):
+        T0 = o.totals()
+        o.step(1)
+        T1 = o.totals()
+        F = np.array(o.body.F)
+        assert np.linalg.norm(F) > 0.05
+        assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
+
+
+def test_stationary_wall_force_is_zero_at_rest(orc):
+    """Fluid at rest at uniform density around a fixed sphere: no force."""
+    shape = (12, 12, 12)
+    o = orc.Oracle(shape, nu=0.05, body=orc.sphere_body((5.6, 6.1, 5.9), 2.7))
+    o.init_state(*synth.uniform_fields(shape))
+    o.step(2)
+    assert np.abs(np.array(o.body.F)).max() < 1e-13
+    f = o.get_f()
+    u, rho = _u(orc, f)
+    fluid = o.solid() == 0
+    assert np.abs(u[fluid]).max() < 1e-14
+    assert np.abs(rho[fluid] - 1).max() < 1e-14
+
+
+def test_refill_sets_density_average_and_wall_velocity(orc):
+    """Sec. 3 refill: a node uncovered by the moving sphere gets the Grad
+    distribution of the wall velocity and the mean density of its 26
+    neighbours that were fluid; its moments are exactly those."""
+    c, _ = orc.lattice()
+    shape = (14, 12, 12)
+    U = (0.6, 0.2, -0.1)  # large step so a step uncovers several nodes
+    body = orc.sphere_body((6.3, 5.8, 6.1), 3.2, U=U, free=True, g=(0, 0, 0), mass=1e30)
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    rho, u, xi = synth.parity_fields(shape, 6)
+    o.init_state(rho, u, xi, 1e-3)
+    f0 = o.get_f()
+    s0 = o.solid()
+    o.step_sampled([0])  # moves the body and refills, leaves the state at t
+    f1 = o.get_f()
+    # solid marks at t+1 from the new centre
+    X = np.array(o.body.X)
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape[::-1]], indexing="ij")
+    s1 = ((x - X[0]) ** 2 + (y - X[1]) ** 2 + (z - X[2]) ** 2) < 3.2 ** 2
+    unc = np.argwhere((s0 == 1) & ~s1)
+    assert len(unc) >= 5
+    u0, r0 = _u(orc, f0)
+    u1, r1 = _u(orc, f1)
+    nz, ny, nx = s0.shape
+    for zz, yy, xx in unc:
+        nb = [((zz + d[2]) % nz, (yy + d[1]) % ny, (xx + d[0]) % nx) for d in c if d.any()]
+        dens = [r0[p] for p in nb if s0[p] == 0]
+        assert r1[zz, yy, xx] == pytest.approx(np.mean(dens) if dens else 1.0, rel=1e-14)
+        assert np.allclose(u1[zz, yy, xx], U, atol=1e-14)
+    # nodes that were fluid keep their state
+    fl = s0 == 0
+    assert np.array_equal(f1[:, fl], f0[:, fl])
+
+
+def test_sphere_euler_update(orc):
+    """Sec. 4.1: X^{t+1} = X^t + U^t, U^{t+1} = U^t + F^t/m + (1 - rho_f/rho_s) g,
+    with F^t the momentum-exchange force of the previous step."""
+    shape = (16, 16, 16)
+    X0, U0, g = np.array([7.4, 7.7, 8.2]), np.array([0.01, -0.02, 0.03]), np.array([0, 0, -2e-4])
+    body = orc.sphere_body(X0, 3.0, U=U0, free=True, g=g, rho_ratio=1.5)
+    m = body.mass
+    assert m == pytest.approx(1.5 * np.pi * 6.0 ** 3 / 6)
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    o.init_state(*synth.uniform_fields(shape, (0.0, 0.0, 0.01)))
+    o.step(1)
+    b1 = o.body
+    assert np.allclose(b1.X, X0 + U0, rtol=0, atol=1e-15)
+    U1 = U0 + (1 - 1 / 1.5) * g
+    assert np.allclose(b1.U, U1, rtol=0, atol=1e-16)
+    F1 = np.array(b1.F)
+    o.step(1)
+    b2 = o.body
+    assert np.allclose(b2.X, X0 + U0 + U1, rtol=0, atol=1e-14)
+    assert np.allclose(b2.U, U1 + F1 / m + (1 - 1 / 1.5) * g, rtol=0, atol=1e-16)
