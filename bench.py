@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of the entropic (KBC) D3Q27 step on the two-way coupled
+sedimenting-sphere workload: 128x128x256 box, sphere D = 16, no-slip x/y
+walls, periodic z, solid/fluid density ratio 1.5, gravity set from the
+terminal-velocity force balance for u_t = 0.04 (arXiv 1608.04658, Sec. 4.1).
+
+One step = the whole hot path: body update, node marks and boundary list,
+refill, bulk stream+collide, Grad boundary + collide, momentum-exchange
+reduction.  The value is GLUPS over box nodes, FP32 storage; FP16 and BF16
+storage forms are reported under "variants".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the path has
+no data-parallel split without a halo exchange); the value is all ranks'
+node updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % of HBM roofline, D3Q27 entropic step (FP32 vs 16-bit); adjoint/fwd time"
+BYTES_PER_NODE = {"fp64": 432, "fp32": 216, "fp16": 108, "bf16": 108}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32", "bf16": "f32"}
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "bulk_kernel_sedimenting_sphere.md")
+KERNEL_SOURCES = ["bulk.cu", "kbc.cuh", "lbm_internal.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=list(BYTES_PER_NODE))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(value: float, world: int) -> float:
+    """Maximum of a float over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.proc = None
+        self.windows = []
+        self.dev = device_index
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            bus = _pci_bus_id(self.dev)
+            if bus:
+                cmd += ["-i", bus]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def mark(self, t0: float, t1: float):
+        self.windows.append((t0, t1))
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if any(a - 0.15 <= r[0] <= b + 0.15 for a, b in self.windows)]
+        sel = inside or rows
+        mhz = sorted(r[1] for r in sel)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in sel for k in range(4) if r[3][k].lower() == "active"})
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in sel), "reasons": reasons,
+                "samples": len(sel), "in_timed_region": bool(inside)}
+
+
+def _pci_bus_id(dev: int) -> str | None:
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------- roofline inputs
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs_sustained", "hbm_gbs", "hbm_GBps", "hbm_copy_gbs"):
+                if key in d and d[key]:
+                    return float(d[key]), f"measured ({key})"
+        except (ValueError, OSError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1608_04658_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage: str):
+    """DRAM bytes per bulk launch from the committed ncu summary, or None when
+    the kernel sources changed since the capture."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    sha, val = None, None
+    for line in open(PROFILE_SUMMARY):
+        line = line.strip().strip("`")
+        if line.startswith("source_sha:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_launch[{storage}]:"):
+            try:
+                val = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                val = None
+    return val if sha == kernel_sha() else None
+
+
+# ----------------------------------------------------------------- workload
+def workload(shape=None):
+    import synth
+    if shape:
+        return synth.sedimenting_sphere(shape=tuple(int(v) for v in shape.split(",")))
+    return synth.sedimenting_sphere()
+
+
+def make_lattice(storage, wl, device):
+    import numpy as np
+
+    import paper_1608_04658_gb300 as lbm
+    import synth
+    shape = wl["shape"]
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device)
+    lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
+    rho, u = synth.uniform_fields(shape)
+    lat.init_state(rho, u)
+    return lat, np
+
+
+def time_storage(storage, wl, args, world, device, clocks):
+    import torch
+    lat, np = make_lattice(storage, wl, device)
+    K, W = args.steps, args.warmup
+    lat.step(W)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    lat.profile_begin(K)
+    t0 = time.time()
+    start.record(lat.stream)
+    lat.step(K)
+    end.record(lat.stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    dist_barrier(world)
+    clocks.mark(t0, t1)
+    launches = lat.launches()
+    bulk_ms, nbulk = lat.profile_end()
+    ms = dist_max(start.elapsed_time(end), world)
+    flags = lat.flags
+    bulk_nodes = int(((flags & 5) == 0).sum().item())
+    body = lat.body()
+    F, _ = lat.forces()  # raises on an unstable run
+    N = lat.N
+    res = dict(ms=ms, glups=N * K * world / (ms * 1e-3) / 1e9, launches=launches,
+               bulk_ms=bulk_ms / max(nbulk, 1), bulk_nodes=bulk_nodes, body=body, F=F)
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return res
+
+
+def e2e_storage(storage, wl, args, device):
+    """Same workload through the public API with host buffers: the pinned FP64
+    state goes in, K steps run with the body force read back every step, and
+    the state comes out, all inside the timed region."""
+    import numpy as np
+    import torch
+    lat, _ = make_lattice(storage, wl, device)
+    nx, ny, nz = wl["shape"]
+    host_in = torch.empty((27, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((27, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    lat.populations(out=host_in)
+    K = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.set_populations(host_in)
+    for _ in range(K):
+        lat.step(1)
+        lat.forces()
+    lat.populations(out=host_out)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    N = lat.N
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    state = 27 * N * 8
+    return {"value": round(N * K / t / 1e9, 4), "unit": "GLUPS",
+            "h2d_bytes_per_step": int(round(state / K)), "d2h_bytes_per_step": int(round(state / K + 48)),
+            "note": "pinned FP64 state in and out once per run (amortised), 48-byte force/torque read every step"}
+
+
+def cpu_baseline(wl, nsteps=2):
+    """The FP64 oracle, single-threaded, on the full sedimenting-sphere box."""
+    import oracle
+    import synth
+    shape = wl["shape"]
+    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
+                        body=oracle.sphere_body(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"],
+                                                g=wl["g"]))
+    orc.init_state(*synth.uniform_fields(shape))
+    t0 = time.perf_counter()
+    orc.step(nsteps)
+    t = time.perf_counter() - t0
+    n = shape[0] * shape[1] * shape[2]
+    return {"value": n * nsteps / t / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} steps of the full {shape[0]}x{shape[1]}x{shape[2]} box, FP64, one thread",
+            "seconds": round(t, 2)}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the compute path is liblbm.so)")
+    import paper_1608_04658_gb300 as lbm
+    lbm.build()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    wl = workload(args.shape)
+    clocks = ClockSampler(local)
+    clocks.start()
+    main = time_storage(args.storage, wl, args, world, device, clocks)
+    variants = {}
+    if not args.no_variants:
+        for st in ("fp16", "bf16", "fp32"):
+            if st == args.storage:
+                continue
+            r = time_storage(st, wl, args, world, device, clocks)
+            variants[st] = r
+    clk = clocks.stop()
+    e2e = None if args.no_e2e else e2e_storage(args.storage, wl, args, device)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_hbm_peak()
+
+    def roofline(st, r):
+        bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
+        achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
+        tr = ncu_traffic(st)
+        return {"bound": "hbm", "kernel": "bulk_kernel", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch,
+                "bulk_ms_per_launch": round(r["bulk_ms"], 5)}
+
+    nx, ny, nz = wl["shape"]
+    N = nx * ny * nz
+    line = {
+        "metric": METRIC, "value": round(main["glups"], 4), "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(main["ms"] / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.storage],
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "storage": args.storage, "nodes": N,
+                   "bytes_per_node_update": BYTES_PER_NODE[args.storage],
+                   "hbm_roofline_glups": round(peak / BYTES_PER_NODE[args.storage], 3),
+                   "percent_of_hbm_roofline_step": round(100 * main["glups"] * BYTES_PER_NODE[args.storage]
+                                                         / world / peak, 2),
+                   "l2": "inputs larger than L2 (population buffers %d MB each)"
+                         % (27 * N * (BYTES_PER_NODE[args.storage] // 54) // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "boundary_nodes": main["body"]["n_boundary"], "links": main["body"]["n_links"]},
+        "roofline": roofline(args.storage, main),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": main["launches"],
+        "clocks": clk,
+        "variants": {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],
+                          "ms_per_step": round(r["ms"] / args.steps, 5),
+                          "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st] / world / peak, 2),
+                          "roofline": roofline(st, r), "gpu_launches": r["launches"]}
+                     for st, r in variants.items()},
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm: each step is one oracle step of a
+    bounded sub-box of the workload (same physics, sphere D = 16), sized so the
+    whole run stays within a few minutes on one host core."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    wl = workload()
+    total = args.steps + args.warmup
+    budget_nodes = 1.0e8  # node updates for the whole run
+    side = int(max(24, min(128, round((budget_nodes / max(total, 1)) ** (1 / 3)))))
+    shape = (side, side, side)
+    X = (side / 2 - 0.5 + 0.123, side / 2 - 0.5 + 0.0567, side / 2 + 0.311)
+    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
+                        body=oracle.sphere_body(X, wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
+    orc.init_state(*synth.uniform_fields(shape))
+    orc.step(args.warmup)
+    t0 = time.perf_counter()
+    orc.step(args.steps)
+    t = time.perf_counter() - t0
+    n = side ** 3
+    v = n * args.steps / t / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "sample_box": list(shape)},
+        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{side}^3 sub-box of the workload (walls x/y, periodic z, sphere D=16) per step"},
+        "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

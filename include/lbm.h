@@ -1,0 +1,199 @@
+/*
+ * C ABI of the GB300 entropic lattice Boltzmann library (liblbm.so).
+ *
+ * Method: Dorschner, Chikatamarla, Karlin, "Entropic lattice Boltzmann method
+ * for moving and deforming geometries in three dimensions", arXiv 1608.04658.
+ *   - Sec. 2, Eqs. (kineticEq), (kbc_relax), (feq_min) and the analytic
+ *     stabilizer: the D3Q27 KBC stream + collide step (lbm_step).
+ *   - Sec. 3, Eqs. (grad), (pressure), (pressure2), target density and
+ *     velocity, refill: the moving-wall boundary (lbm_step, geometry set by
+ *     lbm_set_geometry).
+ *   - Sec. 4.1: Galilean-invariant momentum exchange and Newton's equations
+ *     of the sphere with Euler integration (lbm_step, lbm_body_forces).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an lbm_status; LBM_OK is 0.  On failure the message
+ *     is kept in the context and returned by lbm_last_error.  No C++
+ *     exception crosses the ABI.
+ *   - Lattice layout: populations are structure-of-arrays, element
+ *     f[i * N + x + nx * (y + ny * z)] with N = nx * ny * nz and direction
+ *     index i = 9 (cx + 1) + 3 (cy + 1) + (cz + 1) (opposite direction 26 - i).
+ *   - Stored value: the shifted population g_i = f_i - W_i * rho0 in the
+ *     storage type (FP64, FP32, FP16 or BF16, round-to-nearest-even); the
+ *     collision computes in FP64 for FP64 storage and in FP32 otherwise.
+ *   - The stored state is the post-collision population f'_i(x, t), the
+ *     right side of Eq. (kineticEq).
+ *   - Calls are asynchronous on the context's CUDA stream unless documented
+ *     as synchronising.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument: sizes, null pointers, mixed faces */
+    LBM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    LBM_ERR_OOM = 3,         /* device allocation failed */
+    LBM_ERR_UNSTABLE = 4,    /* a node had non-finite or non-positive density */
+    LBM_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    LBM_ERR_STATE = 6,       /* call out of order (e.g. step before init) */
+    LBM_ERR_UNSUPPORTED = 7  /* option not built */
+} lbm_status;
+
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Box faces.  The paper specifies none; these are the conditions the
+ * workloads need.  For a pull F_i(x) = f'_i(x - c_i) whose source leaves the
+ * box through a face:
+ *   PERIODIC  the source wraps around (both faces of an axis must be periodic),
+ *   WALL      halfway bounce-back at rest: F_i(x) = f'_{26-i}(x),
+ *   EQ        F_i(x) = f_i^eq(rho0, u_face),
+ *   OUTFLOW   the source is clamped onto the face (zero-gradient).
+ * When a source leaves through several faces, WALL wins over EQ, and EQ over
+ * the clamped or wrapped source. */
+typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_EQ = 2, LBM_FACE_OUTFLOW = 3 } lbm_face;
+
+/* Stabilizer: ANALYTIC is gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>
+ * (Sec. 2; gamma = 2 when <dh|dh> underflows).  LBGK forces gamma = 2, which
+ * is BGK with relaxation 2 beta. */
+typedef enum { LBM_GAMMA_ANALYTIC = 0, LBM_GAMMA_LBGK = 2 } lbm_gamma_mode;
+
+typedef struct {
+    int32_t nx, ny, nz;   /* lattice size, each >= 1 */
+    int32_t storage;      /* lbm_storage */
+    int32_t face[6];      /* lbm_face for x-, x+, y-, y+, z-, z+ */
+    int32_t gamma_mode;   /* lbm_gamma_mode */
+    int32_t reserved;
+    double nu;            /* kinematic viscosity: beta = 1/(6 nu + 1) (Sec. 2, c_s^2 = 1/3) */
+    double rho0;          /* reference density of the shifted storage and of rho_dyn */
+    double u_face[3];     /* velocity of EQ faces */
+} lbm_params;
+
+typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2 } lbm_body_kind;
+
+/* Immersed body.  A node is solid when its centre lies inside the body
+ * (strictly).  On periodic axes the sphere is taken at its nearest image.
+ *   SPHERE: centre X, radius R, translational velocity U.  With free_motion
+ *     the centre follows Newton's equations (Sec. 4.1) by explicit Euler:
+ *     X += U, then U += F/mass + (1 - 1/rho_ratio) g, with F the momentum-
+ *     exchange force of the previous step.
+ *   PLANES: solid where y < y_lo or y > y_hi; walls move with U_lo / U_hi. */
+typedef struct {
+    int32_t kind;         /* lbm_body_kind */
+    int32_t free_motion;  /* 1: integrate the sphere's translation */
+    double X[3];
+    double U[3];
+    double R;
+    double y_lo, y_hi;
+    double U_lo[3], U_hi[3];
+    double mass;          /* m_s (rho_s * pi D^3 / 6 for the analytic volume) */
+    double rho_ratio;     /* rho_s / rho_f */
+    double g[3];          /* gravity */
+} lbm_geometry;
+
+/* Body state on the device, read back by lbm_get_body. */
+typedef struct {
+    double X[3], U[3];    /* pose at the current step */
+    double F[3], M[3];    /* force and torque of the fluid on the body, last step */
+    double F_sum[3], M_sum[3]; /* sums since the last lbm_reset_average */
+    int64_t n_sum;        /* number of steps in the sums */
+    int32_t n_boundary;   /* boundary nodes of the last step */
+    int32_t n_uncovered;  /* nodes refilled in the last step */
+    int32_t n_links;      /* missing populations of the last step */
+    int32_t status;       /* device status bits (1: unstable node, 2: band overflow) */
+} lbm_body_state;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Creates a context over caller-owned device buffers.
+ *   f_a, f_b  device buffers of 27 * N elements of the storage type
+ *             (8, 4, 2 or 2 bytes each), 16-byte aligned; f_a holds the state.
+ *   flags     device buffer of N bytes (node marks, written by the library).
+ *   stream    cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * The library never frees the caller's buffers.  Returns LBM_ERR_ARG for
+ * bad sizes or null pointers.  *out is NULL on failure. */
+LBM_API lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
+                              void *stream, lbm_ctx **out);
+
+/* Releases the context and the library's own device scratch. */
+LBM_API void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Sets the state to f_i = f_i^eq(rho, u) + amp * W_i * xi_i (Eq. feq_min, exact
+ * D3Q27 equilibrium), computed on the device.
+ *   rho  device, N doubles; u device, 3N doubles node-major (u[3n + a]);
+ *   xi   device, 27N doubles direction-major, or NULL for none. */
+LBM_API lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u,
+                                  const double *xi, double amp);
+
+/* Sets the immersed body (copied; may be called again to replace it) and
+ * marks the nodes inside it as solid at the current step.  Allocates the
+ * library's boundary scratch (sized from the body) with cudaMalloc. */
+LBM_API lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g);
+
+/* Advances nsteps time steps (Eq. kineticEq with the KBC collision, Grad
+ * boundaries, refill, momentum exchange and body update), asynchronously.
+ * After an odd number of total steps the state lives in f_b: see
+ * lbm_current_buffer. */
+LBM_API lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* 0 if the current state is in f_a, 1 if in f_b. */
+LBM_API int lbm_current_buffer(const lbm_ctx *ctx);
+
+/* Copies the current state to host memory as full populations
+ * f_i = g_i + W_i rho0 in double, layout as above (27 * N doubles).
+ * Synchronises the context stream. */
+LBM_API lbm_status lbm_get_populations(lbm_ctx *ctx, double *host_f);
+
+/* Sets the current state from full host populations (27 * N doubles),
+ * rounding to the storage type.  Synchronises. */
+LBM_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *host_f);
+
+/* Force and torque of the fluid on the body (Sec. 4.1, Galilean-invariant
+ * momentum exchange); averaged != 0 returns the mean since the last
+ * lbm_reset_average.  Synchronises.  Returns LBM_ERR_UNSTABLE if a node went
+ * unstable since creation. */
+LBM_API lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged);
+
+/* Full body state (pose, forces, counters, status).  Synchronises. */
+LBM_API lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out);
+
+/* Clears the force/torque sums used for averages (asynchronous). */
+LBM_API lbm_status lbm_reset_average(lbm_ctx *ctx);
+
+/* Mass, momentum (3) and kinetic energy summed over fluid nodes in double,
+ * written to host out[5].  Synchronises. */
+LBM_API lbm_status lbm_totals(lbm_ctx *ctx, double out[5]);
+
+/* Number of device kernels the last lbm_step call enqueued. */
+LBM_API int64_t lbm_kernel_launches(const lbm_ctx *ctx);
+
+/* Kernel timing with CUDA events on the context stream.  After
+ * lbm_profile_begin(ctx, max_launches), each bulk stream-collide launch of the
+ * following lbm_step calls (up to max_launches) is bracketed by two events.
+ * lbm_profile_end synchronises, returns the summed device time of the
+ * bracketed launches in *total_ms and their number in *launches, and releases
+ * the events.  Returns LBM_ERR_STATE if no profile is open. */
+LBM_API lbm_status lbm_profile_begin(lbm_ctx *ctx, int max_launches);
+LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -295,11 +295,27 @@ static long nid(const orc_ctx *c, int x, int y, int z)
     return x + (long)c->p.nx * (y + (long)c->p.ny * z);
 }
 
-static int inside_body(const orc_body *b, double x, double y, double z)
+/* Displacement of a node from the sphere centre.  Reading (the paper's
+ * sedimenting sphere falls through a periodic box): on a periodic axis the
+ * sphere is taken at its nearest image, d - n floor(d/n + 1/2). */
+static void sphere_offset(const orc_ctx *c, double x, double y, double z, double *d)
 {
+    const orc_body *b = &c->b;
+    double p[3] = {x, y, z};
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a) {
+        d[a] = p[a] - b->X[a];
+        if (c->p.face[2 * a] == FACE_PERIODIC) d[a] = d[a] - n[a] * floor(d[a] / n[a] + 0.5);
+    }
+}
+
+static int inside_body(const orc_ctx *c, double x, double y, double z)
+{
+    const orc_body *b = &c->b;
     if (b->kind == BODY_SPHERE) {
-        double dx = x - b->X[0], dy = y - b->X[1], dz = z - b->X[2];
-        return dx * dx + dy * dy + dz * dz < b->R * b->R;
+        double d[3];
+        sphere_offset(c, x, y, z, d);
+        return d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < b->R * b->R;
     }
     if (b->kind == BODY_PLANES) return y < b->y_lo || y > b->y_hi;
     return 0;
@@ -307,20 +323,22 @@ static int inside_body(const orc_body *b, double x, double y, double z)
 
 /* Fraction q of the link from fluid x_b towards the solid node x_b - c where the
  * wall is crossed: the wall point is x_w = x_b - q c, q in (0, 1]. */
-static double link_q(const orc_body *b, double x, double y, double z, const int *c)
+static double link_q(const orc_ctx *c, double x, double y, double z, const int *ci)
 {
+    const orc_body *b = &c->b;
     if (b->kind == BODY_SPHERE) {
-        double d[3] = {x - b->X[0], y - b->X[1], z - b->X[2]};
-        double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-        double cd = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
+        double d[3];
+        sphere_offset(c, x, y, z, d);
+        double cc = ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2];
+        double cd = ci[0] * d[0] + ci[1] * d[1] + ci[2] * d[2];
         double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         /* |d - s c|^2 = R^2, smaller root */
         double disc = cd * cd - cc * (dd - b->R * b->R);
         return (cd - sqrt(disc)) / cc;
     }
     if (b->kind == BODY_PLANES) {
-        if (y - c[1] < b->y_lo) return (y - b->y_lo) / c[1];
-        return (b->y_hi - y) / (-c[1]);
+        if (y - ci[1] < b->y_lo) return (y - b->y_lo) / ci[1];
+        return (b->y_hi - y) / (-ci[1]);
     }
     return 0.5;
 }
@@ -473,7 +491,7 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
         for (int i = 0; i < Q; ++i) {
             if (!missing[i]) { rho_stat += Fi[i]; continue; }
             const int *ci = C[i];
-            q[i] = link_q(&c->b, x, y, z, ci);
+            q[i] = link_q(c, x, y, z, ci);
             wall_velocity(&c->b, (double)(y - ci[1]), uw[i]);
             /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
              * the wall and returns reflected (halfway bounce-back). */
@@ -510,8 +528,10 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
             double dF[3];
             for (int a = 0; a < 3; ++a)
                 dF[a] = (-ci[a] - uw[i][a]) * fout - (ci[a] - uw[i][a]) * Fi[i];
-            double r[3] = {x - q[i] * ci[0] - c->b.X[0], y - q[i] * ci[1] - c->b.X[1],
-                           z - q[i] * ci[2] - c->b.X[2]};
+            double r[3];
+            if (c->b.kind == BODY_SPHERE) sphere_offset(c, x, y, z, r);
+            else { r[0] = x; r[1] = y; r[2] = z; }
+            for (int a = 0; a < 3; ++a) r[a] -= q[i] * ci[a];
             F[0] += dF[0]; F[1] += dF[1]; F[2] += dF[2];
             M[0] += r[1] * dF[2] - r[2] * dF[1];
             M[1] += r[2] * dF[0] - r[0] * dF[2];
@@ -540,7 +560,7 @@ orc_ctx *orc_create(const orc_params *p, const orc_body *b)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x)
-                c->solid0[nid(c, x, y, z)] = (uint8_t)inside_body(&c->b, x, y, z);
+                c->solid0[nid(c, x, y, z)] = (uint8_t)inside_body(c, x, y, z);
     return c;
 }
 
@@ -594,7 +614,7 @@ static void step_prepare(orc_ctx *c)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x)
-                c->solid1[nid(c, x, y, z)] = (uint8_t)inside_body(&c->b, x, y, z);
+                c->solid1[nid(c, x, y, z)] = (uint8_t)inside_body(c, x, y, z);
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {

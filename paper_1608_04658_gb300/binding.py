@@ -1,0 +1,283 @@
+"""ctypes binding of liblbm.so (C ABI in include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device buffers and the stream.  The
+library is loaded from ``paper_1608_04658_gb300/_build/liblbm.so``; if it is
+missing the import of this module fails with an error that says how to build
+it.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import builder as _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE = 0, 1, 2, 3, 4
+LBM_ERR_TIMEOUT, LBM_ERR_STATE, LBM_ERR_UNSUPPORTED = 5, 6, 7
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
+                4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE",
+                7: "LBM_ERR_UNSUPPORTED"}
+STORAGES = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
+BODY_NONE, BODY_SPHERE, BODY_PLANES = 0, 1, 2
+GAMMA_ANALYTIC, GAMMA_LBGK = 0, 2
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("storage", C.c_int32),
+                ("face", C.c_int32 * 6), ("gamma_mode", C.c_int32), ("reserved", C.c_int32),
+                ("nu", C.c_double), ("rho0", C.c_double), ("u_face", C.c_double * 3)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("free_motion", C.c_int32),
+                ("X", C.c_double * 3), ("U", C.c_double * 3), ("R", C.c_double),
+                ("y_lo", C.c_double), ("y_hi", C.c_double),
+                ("U_lo", C.c_double * 3), ("U_hi", C.c_double * 3),
+                ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3)]
+
+
+class BodyState(C.Structure):
+    _fields_ = [("X", C.c_double * 3), ("U", C.c_double * 3), ("F", C.c_double * 3),
+                ("M", C.c_double * 3), ("F_sum", C.c_double * 3), ("M_sum", C.c_double * 3),
+                ("n_sum", C.c_int64), ("n_boundary", C.c_int32), ("n_uncovered", C.c_int32),
+                ("n_links", C.c_int32), ("status", C.c_int32)]
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/lbm.h."""
+    text = open(HEADER).read()
+    return re.findall(r"LBM_API\s+[\w\s\*]+?\b(lbm_\w+)\s*\(", text)
+
+
+def lib():
+    """Load liblbm.so (built by paper_1608_04658_gb300.builder)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.SO):
+            raise ImportError(f"liblbm.so not built ({_build.SO}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(_build.SO)
+        vp = C.c_void_p
+        L.lbm_create.argtypes = [C.POINTER(Params), vp, vp, vp, vp, C.POINTER(vp)]
+        L.lbm_create.restype = C.c_int
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = C.c_char_p
+        L.lbm_init_state.argtypes = [vp, vp, vp, vp, C.c_double]
+        L.lbm_init_state.restype = C.c_int
+        L.lbm_set_geometry.argtypes = [vp, C.POINTER(Geometry)]
+        L.lbm_set_geometry.restype = C.c_int
+        L.lbm_step.argtypes = [vp, C.c_int]
+        L.lbm_step.restype = C.c_int
+        L.lbm_current_buffer.argtypes = [vp]
+        L.lbm_current_buffer.restype = C.c_int
+        L.lbm_get_populations.argtypes = [vp, _D]
+        L.lbm_get_populations.restype = C.c_int
+        L.lbm_set_populations.argtypes = [vp, _D]
+        L.lbm_set_populations.restype = C.c_int
+        L.lbm_body_forces.argtypes = [vp, _D, _D, C.c_int]
+        L.lbm_body_forces.restype = C.c_int
+        L.lbm_get_body.argtypes = [vp, C.POINTER(BodyState)]
+        L.lbm_get_body.restype = C.c_int
+        L.lbm_reset_average.argtypes = [vp]
+        L.lbm_reset_average.restype = C.c_int
+        L.lbm_totals.argtypes = [vp, _D]
+        L.lbm_totals.restype = C.c_int
+        L.lbm_kernel_launches.argtypes = [vp]
+        L.lbm_kernel_launches.restype = C.c_int64
+        L.lbm_profile_begin.argtypes = [vp, C.c_int]
+        L.lbm_profile_begin.restype = C.c_int
+        L.lbm_profile_end.argtypes = [vp, _D, C.POINTER(C.c_int64)]
+        L.lbm_profile_end.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+_TORCH_DTYPES = {"fp64": "float64", "fp32": "float32", "fp16": "float16", "bf16": "bfloat16"}
+
+
+def make_params(shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0, u_face=(0.0, 0.0, 0.0),
+                gamma_mode=GAMMA_ANALYTIC) -> Params:
+    p = Params()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    p.storage = STORAGES[storage]
+    for k in range(6):
+        p.face[k] = int(faces[k])
+    p.gamma_mode = int(gamma_mode)
+    p.nu = float(nu)
+    p.rho0 = float(rho0)
+    for a in range(3):
+        p.u_face[a] = float(u_face[a])
+    return p
+
+
+def sphere(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0, 0.0), mass=None) -> Geometry:
+    """Sphere of radius R at X; mass defaults to rho_s pi D^3 / 6 with rho_f = 1."""
+    G = Geometry()
+    G.kind = BODY_SPHERE
+    G.free_motion = 1 if free else 0
+    for a in range(3):
+        G.X[a], G.U[a], G.g[a] = float(X[a]), float(U[a]), float(g[a])
+    G.R = float(R)
+    G.rho_ratio = float(rho_ratio)
+    G.mass = float(mass) if mass is not None else float(rho_ratio) * np.pi * (2 * R) ** 3 / 6.0
+    return G
+
+
+def planes(y_lo, y_hi, U_lo=(0.0, 0.0, 0.0), U_hi=(0.0, 0.0, 0.0)) -> Geometry:
+    G = Geometry()
+    G.kind = BODY_PLANES
+    G.y_lo, G.y_hi = float(y_lo), float(y_hi)
+    for a in range(3):
+        G.U_lo[a], G.U_hi[a] = float(U_lo[a]), float(U_hi[a])
+    return G
+
+
+class Lattice:
+    """A D3Q27 lattice on the current CUDA device.
+
+    shape = (nx, ny, nz); populations are torch tensors of shape (27, nz, ny, nx)
+    in the storage dtype, holding g_i = f_i - W_i rho0.  Calls enqueue on the
+    torch stream current at construction.
+    """
+
+    def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0,
+                 u_face=(0.0, 0.0, 0.0), gamma_mode=GAMMA_ANALYTIC, device=None):
+        torch = _torch()
+        self.shape = tuple(int(v) for v in shape)
+        nx, ny, nz = self.shape
+        self.N = nx * ny * nz
+        self.storage = storage
+        self.rho0 = float(rho0)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dt = getattr(torch, _TORCH_DTYPES[storage])
+        self.f_a = torch.empty((27, nz, ny, nx), dtype=dt, device=self.device)
+        self.f_b = torch.empty((27, nz, ny, nx), dtype=dt, device=self.device)
+        self.flags = torch.zeros((nz, ny, nx), dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.params = make_params(shape, nu, storage, faces, rho0, u_face, gamma_mode)
+        ctx = C.c_void_p()
+        st = lib().lbm_create(C.byref(self.params), self.f_a.data_ptr(), self.f_b.data_ptr(),
+                              self.flags.data_ptr(), C.c_void_p(self.stream.cuda_stream), C.byref(ctx))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_create failed")
+        self._ctx = ctx
+        self._keep = []
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st: int):
+        if st != LBM_OK:
+            raise LbmError(st, lib().lbm_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().lbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def f(self):
+        """Tensor holding the current state."""
+        return self.f_b if lib().lbm_current_buffer(self._ctx) else self.f_a
+
+    # -------------------------------------------------------------- state
+    def init_state(self, rho, u, xi=None, amp: float = 0.0):
+        """f = f^eq(rho, u) + amp W xi on the device.  rho (nz,ny,nx), u (nz,ny,nx,3),
+        xi (27,nz,ny,nx) or None; numpy or torch."""
+        torch = _torch()
+        dev = self.device
+        t_rho = torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64)).to(dev).contiguous()
+        t_u = torch.as_tensor(np.ascontiguousarray(u, dtype=np.float64)).to(dev).contiguous()
+        t_xi = None
+        if xi is not None:
+            t_xi = torch.as_tensor(np.ascontiguousarray(xi, dtype=np.float64)).to(dev).contiguous()
+        self.stream.synchronize()
+        self._check(lib().lbm_init_state(self._ctx, t_rho.data_ptr(), t_u.data_ptr(),
+                                         t_xi.data_ptr() if t_xi is not None else None, float(amp)))
+        self.stream.synchronize()
+
+    def set_geometry(self, g: Geometry):
+        self._check(lib().lbm_set_geometry(self._ctx, C.byref(g)))
+
+    def step(self, n: int = 1):
+        self._check(lib().lbm_step(self._ctx, int(n)))
+
+    def launches(self) -> int:
+        """Kernels enqueued by the last step() call."""
+        return int(lib().lbm_kernel_launches(self._ctx))
+
+    def profile_begin(self, max_launches: int):
+        """Bracket the next bulk stream-collide launches with CUDA events."""
+        self._check(lib().lbm_profile_begin(self._ctx, int(max_launches)))
+
+    def profile_end(self):
+        """(summed bulk-kernel milliseconds, number of bracketed launches)."""
+        ms = C.c_double()
+        n = C.c_int64()
+        self._check(lib().lbm_profile_end(self._ctx, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def populations(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Current state as full FP64 populations (27, nz, ny, nx); ``out`` may be
+        a preallocated (e.g. pinned) C-contiguous float64 array."""
+        nx, ny, nz = self.shape
+        if out is None:
+            out = np.empty((27, nz, ny, nx), dtype=np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 27 * self.N
+        self._check(lib().lbm_get_populations(self._ctx, out.ctypes.data_as(_D)))
+        return out
+
+    def set_populations(self, f: np.ndarray):
+        nx, ny, nz = self.shape
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(27, nz, ny, nx)
+        self._check(lib().lbm_set_populations(self._ctx, f.ctypes.data_as(_D)))
+
+    def body(self) -> dict:
+        b = BodyState()
+        self._check(lib().lbm_get_body(self._ctx, C.byref(b)))
+        return dict(X=np.array(b.X), U=np.array(b.U), F=np.array(b.F), M=np.array(b.M),
+                    F_sum=np.array(b.F_sum), M_sum=np.array(b.M_sum), n_sum=b.n_sum,
+                    n_boundary=b.n_boundary, n_uncovered=b.n_uncovered, n_links=b.n_links,
+                    status=b.status)
+
+    def forces(self, averaged: bool = False):
+        F = np.zeros(3)
+        M = np.zeros(3)
+        self._check(lib().lbm_body_forces(self._ctx, F.ctypes.data_as(_D), M.ctypes.data_as(_D),
+                                          1 if averaged else 0))
+        return F, M
+
+    def reset_average(self):
+        self._check(lib().lbm_reset_average(self._ctx))
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(5)
+        self._check(lib().lbm_totals(self._ctx, out.ctypes.data_as(_D)))
+        return out

@@ -1,0 +1,450 @@
+// C ABI of liblbm.so (declared in include/lbm.h): argument checks, scratch
+// management and the per-step launch sequence.  Host code only enqueues
+// kernels; the state, the body and its force never leave the device during
+// lbm_step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    Lattice L;
+    int storage = 0;
+    size_t elem = 0;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *flags = nullptr;
+    cudaStream_t stream = nullptr;
+    GeomParams G{};
+    bool has_body = false;
+    bool initialised = false;
+    Scratch S{};
+    double *plane = nullptr;      // N doubles for the host codec
+    double *tot_partials = nullptr;
+    int tot_blocks = 608;
+    int64_t launches = 0;
+    std::vector<cudaEvent_t> prof;  // start/stop pairs around bulk launches
+    int prof_used = 0;
+    bool prof_open = false;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, where)                                        \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);     \
+    } while (0)
+
+size_t elem_size(int storage)
+{
+    switch (storage) {
+    case LBM_FP64: return 8;
+    case LBM_FP32: return 4;
+    case LBM_FP16: return 2;
+    case LBM_BF16: return 2;
+    default: return 0;
+    }
+}
+
+double host_weight(int i)
+{
+    const int nz = (i / 9 != 1) + ((i / 3) % 3 != 1) + (i % 3 != 1);
+    return nz == 0 ? 8.0 / 27.0 : nz == 1 ? 2.0 / 27.0 : nz == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+}
+
+// shifted equilibrium for the EQ faces, exact product form (host, double)
+void face_equilibrium(double rho0, const double u[3], double out[27])
+{
+    double fac[3][3];
+    for (int a = 0; a < 3; ++a) {
+        const double S = std::sqrt(1.0 + 3.0 * u[a] * u[a]);
+        const double B = (2.0 * u[a] + S) / (1.0 - u[a]);
+        fac[a][0] = (2.0 - S) / B;
+        fac[a][1] = 2.0 - S;
+        fac[a][2] = (2.0 - S) * B;
+    }
+    for (int i = 0; i < 27; ++i) {
+        const int cx = i / 9, cy = (i / 3) % 3, cz = i % 3;
+        out[i] = host_weight(i) * (rho0 * fac[0][cx] * fac[1][cy] * fac[2][cz] - rho0);
+    }
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+void free_scratch(Scratch &S, bool keep_body)
+{
+    cudaFree(S.bnode); cudaFree(S.bmask); cudaFree(S.bq); cudaFree(S.buw); cudaFree(S.bforce);
+    cudaFree(S.unode); cudaFree(S.blk_count); cudaFree(S.blk_ucount); cudaFree(S.blk_off);
+    cudaFree(S.blk_uoff); cudaFree(S.partials);
+    DevBody *b = S.body;
+    S = Scratch{};
+    if (keep_body) S.body = b;
+    else cudaFree(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags, void *stream,
+                      lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!p || !f_a || !f_b || !flags) return LBM_ERR_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (N >= (1LL << 31)) return LBM_ERR_ARG;
+    const size_t es = elem_size(p->storage);
+    if (es == 0) return LBM_ERR_ARG;
+    if (((uintptr_t)f_a % 16) || ((uintptr_t)f_b % 16)) return LBM_ERR_ARG;
+    for (int k = 0; k < 6; ++k)
+        if (p->face[k] < LBM_FACE_PERIODIC || p->face[k] > LBM_FACE_OUTFLOW) return LBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if ((p->face[2 * a] == LBM_FACE_PERIODIC) != (p->face[2 * a + 1] == LBM_FACE_PERIODIC))
+            return LBM_ERR_ARG;
+    if (!(p->nu >= 0.0) || !std::isfinite(p->nu) || !(p->rho0 > 0.0)) return LBM_ERR_ARG;
+    if (p->gamma_mode != LBM_GAMMA_ANALYTIC && p->gamma_mode != LBM_GAMMA_LBGK) return LBM_ERR_ARG;
+
+    lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
+    if (!ctx) return LBM_ERR_OOM;
+    Lattice &L = ctx->L;
+    L.nx = p->nx; L.ny = p->ny; L.nz = p->nz; L.N = N;
+    for (int k = 0; k < 6; ++k) L.face[k] = p->face[k];
+    L.gamma_mode = p->gamma_mode;
+    L.beta = 1.0 / (6.0 * p->nu + 1.0);
+    L.rho0 = p->rho0;
+    for (int a = 0; a < 3; ++a) L.u_face[a] = p->u_face[a];
+    face_equilibrium(p->rho0, p->u_face, L.g_face);
+    ctx->storage = p->storage;
+    ctx->elem = es;
+    ctx->f[0] = f_a;
+    ctx->f[1] = f_b;
+    ctx->flags = flags;
+    ctx->stream = (cudaStream_t)stream;
+    if (dalloc(&ctx->S.body, 1) != cudaSuccess || dalloc(&ctx->tot_partials, (size_t)ctx->tot_blocks * 5) != cudaSuccess) {
+        free_scratch(ctx->S, false);
+        cudaFree(ctx->tot_partials);
+        delete ctx;
+        return LBM_ERR_OOM;
+    }
+    DevBody zero{};
+    if (cudaMemcpyAsync(ctx->S.body, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(flags, 0, (size_t)N, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        free_scratch(ctx->S, false);
+        cudaFree(ctx->tot_partials);
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
+    free_scratch(ctx->S, false);
+    cudaFree(ctx->plane);
+    cudaFree(ctx->tot_partials);
+    delete ctx;
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, const double *xi, double amp)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!rho || !u) return fail(ctx, LBM_ERR_ARG, "lbm_init_state: rho and u are required");
+    LBM_CUDA(launch_init(ctx->storage, ctx->L, ctx->f[ctx->cur], rho, u, xi, amp, ctx->stream), "init");
+    ctx->initialised = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!g) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: null geometry");
+    if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_PLANES)
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: unknown body kind");
+    const Lattice &L = ctx->L;
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    free_scratch(ctx->S, true);
+    ctx->has_body = g->kind != LBM_BODY_NONE;
+    GeomParams &G = ctx->G;
+    G = GeomParams{};
+    G.kind = g->kind;
+    G.free_motion = g->free_motion;
+    G.R = g->R;
+    G.y_lo = g->y_lo;
+    G.y_hi = g->y_hi;
+    for (int a = 0; a < 3; ++a) {
+        G.U_lo[a] = g->U_lo[a];
+        G.U_hi[a] = g->U_hi[a];
+        G.g[a] = g->g[a];
+        G.periodic[a] = L.face[2 * a] == LBM_FACE_PERIODIC;
+    }
+    G.mass = g->mass;
+    G.rho_ratio = g->rho_ratio;
+    const int n[3] = {L.nx, L.ny, L.nz};
+    if (g->kind == LBM_BODY_SPHERE) {
+        if (!(g->R > 0.0) || (g->free_motion && (!(g->mass > 0.0) || !(g->rho_ratio > 0.0))))
+            return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: sphere needs R > 0 (and mass, rho_ratio > 0 when free)");
+        for (int a = 0; a < 3; ++a) {
+            const int c = (int)std::ceil(2.0 * g->R) + 9;
+            G.cap[a] = c < n[a] ? c : n[a];
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) G.cap[a] = n[a];
+    }
+    const long long vol = (long long)G.cap[0] * G.cap[1] * G.cap[2];
+    G.cap_boundary = (int)vol;
+    G.cap_uncovered = (int)vol;
+    Scratch &S = ctx->S;
+    S.n_count_blocks = (int)((vol + 255) / 256);
+    S.n_partials = 64;
+    bool ok = true;
+    if (ctx->has_body) {
+        ok = dalloc(&S.bnode, vol) == cudaSuccess && dalloc(&S.bmask, vol) == cudaSuccess &&
+             dalloc(&S.bq, vol * Q) == cudaSuccess && dalloc(&S.buw, vol * Q * 3) == cudaSuccess &&
+             dalloc(&S.bforce, vol * 6) == cudaSuccess && dalloc(&S.unode, vol) == cudaSuccess &&
+             dalloc(&S.blk_count, S.n_count_blocks) == cudaSuccess &&
+             dalloc(&S.blk_ucount, S.n_count_blocks) == cudaSuccess &&
+             dalloc(&S.blk_off, S.n_count_blocks) == cudaSuccess &&
+             dalloc(&S.blk_uoff, S.n_count_blocks) == cudaSuccess &&
+             dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess;
+    }
+    if (!ok) {
+        free_scratch(ctx->S, true);
+        ctx->has_body = false;
+        return fail(ctx, LBM_ERR_OOM, "lbm_set_geometry: device allocation failed");
+    }
+    DevBody hb{};
+    for (int a = 0; a < 3; ++a) { hb.X[a] = g->X[a]; hb.U[a] = g->U[a]; }
+    LBM_CUDA(cudaMemcpyAsync(S.body, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
+    LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
+    if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, g->X, ctx->flags, ctx->stream), "initial marks");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
+    return LBM_OK;
+}
+
+// records the start (which = 0) or stop (1) event of a profiled bulk launch
+static cudaError_t prof_mark(lbm_ctx *ctx, int which)
+{
+    if (!ctx->prof_open) return cudaSuccess;
+    const int k = 2 * ctx->prof_used + which;
+    if (k >= (int)ctx->prof.size()) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ctx->prof[k], ctx->stream);
+    if (which == 1) ctx->prof_used++;
+    return e;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "lbm_step: nsteps < 0");
+    if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step: state not initialised");
+    int launches = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
+        if (ctx->has_body) {
+            LBM_CUDA(launch_body_update(ctx->L, ctx->G, ctx->S, ctx->stream), "body update");
+            LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, ctx->flags, ctx->stream, &launches), "geometry");
+            LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, fa, ctx->flags, ctx->stream), "refill");
+            LBM_CUDA(prof_mark(ctx, 0), "profile event");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, &ctx->S.body->status, ctx->stream), "bulk");
+            LBM_CUDA(prof_mark(ctx, 1), "profile event");
+            LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, fa, fb, ctx->flags, ctx->stream), "boundary");
+            LBM_CUDA(launch_forces(ctx->L, ctx->S, ctx->stream, &launches), "forces");
+            launches += 4;
+        } else {
+            LBM_CUDA(prof_mark(ctx, 0), "profile event");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, &ctx->S.body->status, ctx->stream), "bulk");
+            LBM_CUDA(prof_mark(ctx, 1), "profile event");
+            launches += 1;
+        }
+        ctx->cur ^= 1;
+    }
+    ctx->launches = launches;
+    return LBM_OK;
+}
+
+int lbm_current_buffer(const lbm_ctx *ctx) { return ctx ? ctx->cur : -1; }
+
+int64_t lbm_kernel_launches(const lbm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+static lbm_status ensure_plane(lbm_ctx *ctx)
+{
+    if (ctx->plane) return LBM_OK;
+    if (dalloc(&ctx->plane, (size_t)ctx->L.N) != cudaSuccess)
+        return fail(ctx, LBM_ERR_OOM, "plane buffer allocation failed");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *host_f)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!host_f) return fail(ctx, LBM_ERR_ARG, "lbm_get_populations: null output");
+    lbm_status st = ensure_plane(ctx);
+    if (st != LBM_OK) return st;
+    const size_t N = (size_t)ctx->L.N;
+    for (int i = 0; i < Q; ++i) {
+        LBM_CUDA(launch_decode_plane(ctx->storage, ctx->L, ctx->f[ctx->cur], i, ctx->plane, ctx->stream), "decode");
+        LBM_CUDA(cudaMemcpyAsync(host_f + (size_t)i * N, ctx->plane, N * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream), "copy out");
+        LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *host_f)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!host_f) return fail(ctx, LBM_ERR_ARG, "lbm_set_populations: null input");
+    lbm_status st = ensure_plane(ctx);
+    if (st != LBM_OK) return st;
+    const size_t N = (size_t)ctx->L.N;
+    for (int i = 0; i < Q; ++i) {
+        LBM_CUDA(cudaMemcpyAsync(ctx->plane, host_f + (size_t)i * N, N * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream), "copy in");
+        LBM_CUDA(launch_encode_plane(ctx->storage, ctx->L, ctx->f[ctx->cur], i, ctx->plane, ctx->stream), "encode");
+        LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+    ctx->initialised = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!out) return fail(ctx, LBM_ERR_ARG, "lbm_get_body: null output");
+    DevBody hb;
+    LBM_CUDA(cudaMemcpyAsync(&hb, ctx->S.body, sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream), "body read");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    for (int a = 0; a < 3; ++a) {
+        out->X[a] = hb.X[a]; out->U[a] = hb.U[a];
+        out->F[a] = hb.F[a]; out->M[a] = hb.M[a];
+        out->F_sum[a] = hb.F_sum[a]; out->M_sum[a] = hb.M_sum[a];
+    }
+    out->n_sum = hb.n_sum;
+    out->n_boundary = hb.n_boundary;
+    out->n_uncovered = hb.n_uncovered;
+    out->n_links = hb.n_links;
+    out->status = hb.status;
+    return LBM_OK;
+}
+
+lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!F || !M) return fail(ctx, LBM_ERR_ARG, "lbm_body_forces: null output");
+    lbm_body_state b;
+    lbm_status st = lbm_get_body(ctx, &b);
+    if (st != LBM_OK) return st;
+    for (int a = 0; a < 3; ++a) {
+        if (averaged) {
+            const double n = b.n_sum > 0 ? (double)b.n_sum : 1.0;
+            F[a] = b.F_sum[a] / n;
+            M[a] = b.M_sum[a] / n;
+        } else {
+            F[a] = b.F[a];
+            M[a] = b.M[a];
+        }
+    }
+    if (b.status & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
+    if (b.status & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
+    return LBM_OK;
+}
+
+lbm_status lbm_reset_average(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    DevBody *b = ctx->S.body;
+    LBM_CUDA(cudaMemsetAsync(&b->F_sum, 0, sizeof(b->F_sum) + sizeof(b->M_sum) + sizeof(b->n_sum), ctx->stream), "reset");
+    return LBM_OK;
+}
+
+lbm_status lbm_totals(lbm_ctx *ctx, double out[5])
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!out) return fail(ctx, LBM_ERR_ARG, "lbm_totals: null output");
+    const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;
+    LBM_CUDA(launch_totals(ctx->storage, ctx->L, ctx->f[ctx->cur], fl, ctx->tot_partials, ctx->tot_blocks,
+                           nullptr, ctx->stream), "totals");
+    std::vector<double> h((size_t)ctx->tot_blocks * 5);
+    LBM_CUDA(cudaMemcpyAsync(h.data(), ctx->tot_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             ctx->stream), "totals read");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    for (int k = 0; k < 5; ++k) out[k] = 0;
+    for (int b = 0; b < ctx->tot_blocks; ++b)
+        for (int k = 0; k < 5; ++k) out[k] += h[(size_t)b * 5 + k];
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_begin(lbm_ctx *ctx, int max_launches)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (max_launches < 1) return fail(ctx, LBM_ERR_ARG, "lbm_profile_begin: max_launches < 1");
+    if (ctx->prof_open) return fail(ctx, LBM_ERR_STATE, "lbm_profile_begin: a profile is already open");
+    ctx->prof.assign((size_t)2 * max_launches, nullptr);
+    for (auto &e : ctx->prof) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto &f : ctx->prof) if (f) cudaEventDestroy(f);
+            ctx->prof.clear();
+            return fail(ctx, LBM_ERR_CUDA, "lbm_profile_begin: event creation failed");
+        }
+    }
+    ctx->prof_used = 0;
+    ctx->prof_open = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *launches)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!ctx->prof_open) return fail(ctx, LBM_ERR_STATE, "lbm_profile_end: no profile open");
+    if (!total_ms || !launches) return fail(ctx, LBM_ERR_ARG, "lbm_profile_end: null output");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    double sum = 0;
+    for (int k = 0; k < ctx->prof_used; ++k) {
+        float ms = 0;
+        LBM_CUDA(cudaEventElapsedTime(&ms, ctx->prof[2 * k], ctx->prof[2 * k + 1]), "elapsed");
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = ctx->prof_used;
+    for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
+    ctx->prof.clear();
+    ctx->prof_open = false;
+    ctx->prof_used = 0;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,396 @@
+// Moving-wall Grad boundary with KBC collision and momentum exchange, and the
+// refill of uncovered nodes (arXiv 1608.04658, Sec. 3, Eqs. grad, pressure,
+// pressure2, target velocity/density; Sec. 4.1 Galilean-invariant momentum
+// exchange).
+//
+// One warp per listed node; lane i < 27 owns direction i.  The populations of
+// the 3x3x3 neighbourhood that a node needs (itself, its six face neighbours
+// for the finite-difference velocity gradient, and x_b + c_i for each missing
+// i) are staged in shared memory as [node k][direction i]; lane k then forms
+// the density and velocity of neighbourhood node k.  Sums over directions are
+// shuffle trees whose lane-0 result is broadcast, so every lane sees the same
+// density, velocity and stabilizer.
+//
+// Readings of points the paper leaves open (the oracle takes the same ones):
+//   missing set D = {i : x_b - c_i solid at t+1}; wall point x_w = x_b - q_i c_i;
+//   u_f,i from the previous-step state at x_b + c_i, or the wall velocity alone
+//   when that node is not fluid; rho_dyn with rho0; f^bb_i = f'_{opp i}(x_b, t);
+//   grad u: central difference where both face neighbours are fluid,
+//   one-sided where one is, zero otherwise; Pi with rho_tgt and u_tgt; only
+//   the missing populations are replaced; the node then collides with KBC.
+//   Refill: mean density of the neighbours fluid at t (rho0 if none), the body
+//   velocity, gradient with the wall velocity at the centre.
+#include "kbc.cuh"
+
+namespace lbm {
+
+constexpr int BWARPS = 4;
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename R>
+__device__ __forceinline__ R wsum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return __shfl_sync(FULL, v, 0);
+}
+
+template <typename R>
+__device__ __forceinline__ R pick(const R e[3], int c)
+{
+    return c < 0 ? e[0] : (c > 0 ? e[2] : e[1]);
+}
+
+// x + d with periodic wrap; -1 when it leaves the box through a non-periodic face
+__device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int z, int dx, int dy, int dz)
+{
+    int p[3] = {x + dx, y + dy, z + dz};
+    const int n[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (p[a] >= 0 && p[a] < n[a]) continue;
+        const int face = p[a] < 0 ? L.face[2 * a] : L.face[2 * a + 1];
+        if (face != LBM_FACE_PERIODIC) return -1;
+        p[a] = (p[a] + n[a]) % n[a];
+    }
+    return p[0] + L.nx * (p[1] + L.ny * p[2]);
+}
+
+// Lane-parallel KBC collision: lane i < 27 holds the shifted population g_i.
+template <typename R>
+__device__ R kbc_collide_lanes(R g, int i, R beta, R rho0, int gamma_mode, bool &ok)
+{
+    const bool act = i < Q;
+    const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
+    const R gv = act ? g : R(0);
+    const R drho = wsum(gv);
+    const R jx = wsum(R(cx) * gv), jy = wsum(R(cy) * gv), jz = wsum(R(cz) * gv);
+    const R rho = rho0 + drho;
+    ok = rho > R(0) && rho < R(1e30);
+    const R inv_rho = R(1) / rho;
+    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
+    axis_eq(jx * inv_rho, ex, rx);
+    axis_eq(jy * inv_rho, ey, ry);
+    axis_eq(jz * inv_rho, ez, rz);
+    const R exy = pick(ex, cx) + pick(ey, cy) + pick(ex, cx) * pick(ey, cy);
+    const R E = exy + pick(ez, cz) + exy * pick(ez, cz);
+    const R geq = act ? weight<R>(i) * (drho + rho * E) : R(0);
+    const R d = gv - geq;
+    const R pxx = wsum(R(cx * cx) * d), pyy = wsum(R(cy * cy) * d), pzz = wsum(R(cz * cz) * d);
+    const R pxy = wsum(R(cx * cy) * d), pxz = wsum(R(cx * cz) * d), pyz = wsum(R(cy * cz) * d);
+    const R nxz = pxx - pzz, nyz = pyy - pzz;
+    const R ds = act ? shear_part<R>(i, nxz, nyz, pxy, pxz, pyz) : R(0);
+    const R dh = d - ds;
+    const R ifeq = act ? inv_rho * inv_weight<R>(i) * pick(rx, cx) * pick(ry, cy) * pick(rz, cz) : R(0);
+    const R sh = wsum(ds * dh * ifeq), hh = wsum(dh * dh * ifeq);
+    R gam = R(2);
+    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>()) {
+        const R ib = R(1) / beta;
+        gam = ib - (R(2) - ib) * sh / hh;
+    }
+    return geq + (R(1) - beta * gam) * d + beta * (gam - R(2)) * ds;
+}
+
+// Shifted Grad distribution g*_i = f*_i - W_i rho0 (Eq. grad, c_s^2 = 1/3):
+//   f*_i = W_i [rho + 3 rho c.u + (9/2) Qt : (c c - I/3)],  Qt = Pi - rho/3 I.
+template <typename R>
+__device__ __forceinline__ R grad_shifted(int i, R rho, R rho0, const R u[3], const R Qt[6])
+{
+    const R cx = R(cx_of(i)), cy = R(cy_of(i)), cz = R(cz_of(i));
+    const R cu = cx * u[0] + cy * u[1] + cz * u[2];
+    // Qt = (xx, yy, zz, xy, xz, yz)
+    const R qcc = Qt[0] * cx * cx + Qt[1] * cy * cy + Qt[2] * cz * cz
+                + R(2) * (Qt[3] * cx * cy + Qt[4] * cx * cz + Qt[5] * cy * cz);
+    const R tr = (Qt[0] + Qt[1] + Qt[2]) * R(1.0 / 3.0);
+    return weight<R>(i) * ((rho - rho0) + R(3) * rho * cu + R(4.5) * (qcc - tr));
+}
+
+// Qt = rho u u - (rho c_s^2 / (2 beta)) (grad u + grad u^T)  (Eqs. pressure, pressure2)
+template <typename R>
+__device__ __forceinline__ void pressure_excess(R rho, const R u[3], const R du[3][3], R beta, R Qt[6])
+{
+    const R k = rho / (R(6) * beta);
+    Qt[0] = rho * u[0] * u[0] - k * R(2) * du[0][0];
+    Qt[1] = rho * u[1] * u[1] - k * R(2) * du[1][1];
+    Qt[2] = rho * u[2] * u[2] - k * R(2) * du[2][2];
+    Qt[3] = rho * u[0] * u[1] - k * (du[0][1] + du[1][0]);
+    Qt[4] = rho * u[0] * u[2] - k * (du[0][2] + du[2][0]);
+    Qt[5] = rho * u[1] * u[2] - k * (du[1][2] + du[2][1]);
+}
+
+// velocity gradient du[a][b] = d u_a / d x_b from the staged neighbourhood
+template <typename R>
+__device__ __forceinline__ void fd_gradient(const R (*su)[4], const int *sok, const R uc[3], R du[3][3])
+{
+    const int step[3] = {9, 3, 1};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const int kp = 13 + step[b], km = 13 - step[b];
+        const bool op = sok[kp], om = sok[km];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R v = R(0);
+            if (op && om) v = R(0.5) * (su[kp][1 + a] - su[km][1 + a]);
+            else if (op) v = su[kp][1 + a] - uc[a];
+            else if (om) v = uc[a] - su[km][1 + a];
+            du[a][b] = v;
+        }
+    }
+}
+
+// Stage populations of neighbourhood nodes selected by 'need' into sf[k][i]
+// and their density/velocity into su[k] (lane k).  sok[k] must be set.
+template <typename S, typename R>
+__device__ __forceinline__ void stage(const Lattice &L, const S *__restrict__ fa, int lane, int nk,
+                                      uint32_t need, R (*sf)[28], R (*su)[4], const int *sok)
+{
+    const size_t N = (size_t)L.N;
+    for (int k = 0; k < Q; ++k) {
+        const int nodek = __shfl_sync(FULL, nk, k);
+        if (!((need >> k) & 1u) || nodek < 0) continue;
+        if (lane < Q) sf[k][lane] = Codec<S>::load(fa + (size_t)lane * N + nodek);
+    }
+    __syncwarp();
+    if (lane < Q && ((need >> lane) & 1u) && nk >= 0) {
+        R r = 0, j[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+            const R v = sf[lane][i];
+            r += v;
+            j[0] += R(cx_of(i)) * v;
+            j[1] += R(cy_of(i)) * v;
+            j[2] += R(cz_of(i)) * v;
+        }
+        const R rho = R(L.rho0) + r;
+        su[lane][0] = rho;
+        su[lane][1] = j[0] / rho;
+        su[lane][2] = j[1] / rho;
+        su[lane][3] = j[2] / rho;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void node_xyz(const Lattice &L, int n, int &x, int &y, int &z)
+{
+    x = n % L.nx;
+    y = (n / L.nx) % L.ny;
+    z = n / (L.nx * L.ny);
+}
+
+__device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams &G, const DevBody *b,
+                                              int a, int p)
+{
+    if (G.kind != LBM_BODY_SPHERE) return (double)p;
+    const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
+    double d = __dsub_rn((double)p, b->X[a]);
+    if (G.periodic[a]) d = __dsub_rn(d, __dmul_rn((double)n, floor(__dadd_rn(__ddiv_rn(d, (double)n), 0.5))));
+    return d;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
+    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ bnode,
+    const uint32_t *__restrict__ bmask, const double *__restrict__ bq, const double *__restrict__ buw,
+    double *__restrict__ bforce, const S *__restrict__ fa, S *__restrict__ fb,
+    const uint8_t *__restrict__ flags, int *__restrict__ status)
+{
+    using R = typename Codec<S>::R;
+    __shared__ R s_f[BWARPS][Q][28];
+    __shared__ R s_u[BWARPS][Q][4];
+    __shared__ int s_ok[BWARPS][Q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    R (*sf)[28] = s_f[w];
+    R (*su)[4] = s_u[w];
+    int *sok = s_ok[w];
+    const int count = b->n_boundary;
+    const size_t N = (size_t)L.N;
+    const R rho0 = (R)L.rho0;
+
+    for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
+        const int n = bnode[slot];
+        const uint32_t mask = bmask[slot];
+        int x, y, z;
+        node_xyz(L, n, x, y, z);
+        const int i = lane;
+        const bool act = i < Q;
+        const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
+
+        // neighbourhood node k = lane: x_b + c_k
+        int nk = -1;
+        if (act) nk = neighbour(L, x, y, z, cx, cy, cz);
+        if (act) sok[lane] = nk >= 0 && !(flags[nk] & FL_SOLID);
+        __syncwarp();
+        const uint32_t need = (1u << 13) | (1u << 22) | (1u << 4) | (1u << 16) | (1u << 10) |
+                              (1u << 14) | (1u << 12) | mask;
+        stage<S, R>(L, fa, lane, nk, need, sf, su, sok);
+
+        const bool miss = act && ((mask >> i) & 1u);
+        // known pulled populations (face rules as in the bulk kernel)
+        R Fi = R(0);
+        if (act && !miss) {
+            int p[3] = {x - cx, y - cy, z - cz};
+            const int nn[3] = {L.nx, L.ny, L.nz};
+            int kind = 0;
+            for (int a = 0; a < 3; ++a) {
+                int face = -1;
+                if (p[a] < 0) face = L.face[2 * a];
+                else if (p[a] >= nn[a]) face = L.face[2 * a + 1];
+                if (face < 0) continue;
+                if (face == LBM_FACE_PERIODIC) p[a] = (p[a] + nn[a]) % nn[a];
+                else if (face == LBM_FACE_OUTFLOW) p[a] = p[a] < 0 ? 0 : nn[a] - 1;
+                else if (face == LBM_FACE_WALL) kind = 2;
+                else kind = kind > 1 ? kind : 1;
+            }
+            if (kind == 2) Fi = sf[13][26 - i];
+            else if (kind == 1) Fi = (R)L.g_face[i];
+            else Fi = Codec<S>::load(fa + (size_t)i * N + (p[0] + L.nx * (p[1] + L.ny * p[2])));
+        }
+        // target density and velocity over the missing set
+        const R fbb = act ? sf[13][26 - (act ? i : 0)] : R(0);  // shifted f'_{opp i}(x_b, t)
+        double q = 0, uw[3] = {0, 0, 0};
+        if (miss) {
+            q = bq[(size_t)slot * Q + i];
+            uw[0] = buw[((size_t)slot * Q + i) * 3 + 0];
+            uw[1] = buw[((size_t)slot * Q + i) * 3 + 1];
+            uw[2] = buw[((size_t)slot * Q + i) * 3 + 2];
+        }
+        const R gstat = miss ? fbb : Fi;
+        const R dyn = miss ? R(6) * weight<R>(i) * rho0 * (R(cx) * (R)uw[0] + R(cy) * (R)uw[1] + R(cz) * (R)uw[2])
+                           : R(0);
+        R ut[3] = {0, 0, 0};
+        if (miss) {
+            const R qq = (R)q;
+            if (sok[i]) {
+                for (int a = 0; a < 3; ++a) ut[a] = (qq * su[i][1 + a] + (R)uw[a]) / (R(1) + qq);
+            } else {
+                for (int a = 0; a < 3; ++a) ut[a] = (R)uw[a];
+            }
+        }
+        const R nmiss = R(__popc(mask));
+        const R rho_t = rho0 + wsum(act ? gstat : R(0)) + wsum(dyn);
+        R u_t[3];
+        for (int a = 0; a < 3; ++a) u_t[a] = wsum(ut[a]) / nmiss;
+        R du[3][3];
+        const R uc[3] = {su[13][1], su[13][2], su[13][3]};
+        fd_gradient<R>(su, sok, uc, du);
+        R Qt[6];
+        pressure_excess<R>(rho_t, u_t, du, (R)L.beta, Qt);
+        R gi = Fi;
+        if (miss) gi = grad_shifted<R>(i, rho_t, rho0, u_t, Qt);
+
+        // momentum exchange on missing links (FP64): the fluid hands the body
+        // (c_opp - u_w) f'_opp(x_b, t) and gets back (c_i - u_w) F_i(x_b, t+1)
+        double dF[6] = {0, 0, 0, 0, 0, 0};
+        if (miss) {
+            const double W = weight<double>(i) * L.rho0;
+            const double fout = (double)fbb + W, fin = (double)gi + W;
+            const double c[3] = {(double)cx, (double)cy, (double)cz};
+            for (int a = 0; a < 3; ++a) dF[a] = (-c[a] - uw[a]) * fout - (c[a] - uw[a]) * fin;
+            double r[3];
+            r[0] = body_offset(L, G, b, 0, x) - q * c[0];
+            r[1] = body_offset(L, G, b, 1, y) - q * c[1];
+            r[2] = body_offset(L, G, b, 2, z) - q * c[2];
+            dF[3] = r[1] * dF[2] - r[2] * dF[1];
+            dF[4] = r[2] * dF[0] - r[0] * dF[2];
+            dF[5] = r[0] * dF[1] - r[1] * dF[0];
+        }
+        for (int k = 0; k < 6; ++k) {
+            double v = dF[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0) bforce[(size_t)slot * 6 + k] = v;
+        }
+
+        bool ok;
+        const R out = kbc_collide_lanes<R>(gi, i, (R)L.beta, rho0, L.gamma_mode, ok);
+        if (lane == 0 && !ok) atomicOr(status, ST_UNSTABLE);
+        if (act) Codec<S>::store(fb + (size_t)i * N + n, out);
+        __syncwarp();
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
+    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ unode,
+    S *__restrict__ fa, const uint8_t *__restrict__ flags)
+{
+    using R = typename Codec<S>::R;
+    __shared__ R s_f[BWARPS][Q][28];
+    __shared__ R s_u[BWARPS][Q][4];
+    __shared__ int s_ok[BWARPS][Q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    R (*sf)[28] = s_f[w];
+    R (*su)[4] = s_u[w];
+    int *sok = s_ok[w];
+    const int count = b->n_uncovered;
+    const size_t N = (size_t)L.N;
+    const R rho0 = (R)L.rho0;
+    for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
+        const int n = unode[slot];
+        int x, y, z;
+        node_xyz(L, n, x, y, z);
+        const bool act = lane < Q;
+        int nk = -1;
+        if (act && lane != 13) nk = neighbour(L, x, y, z, cx_of(lane), cy_of(lane), cz_of(lane));
+        // neighbours that were fluid at t carry valid populations
+        if (act) sok[lane] = nk >= 0 && !(flags[nk] & FL_SOLID_PREV);
+        __syncwarp();
+        uint32_t need = __ballot_sync(FULL, act && sok[lane]);
+        stage<S, R>(L, fa, lane, nk, need, sf, su, sok);
+        const R cnt = R(__popc(need));
+        const R rsum = wsum((act && sok[lane]) ? su[lane][0] : R(0));
+        const R rho = cnt > R(0) ? rsum / cnt : rho0;
+        R u[3] = {(R)b->U[0], (R)b->U[1], (R)b->U[2]};
+        if (G.kind == LBM_BODY_PLANES) {
+            const double *v = (double)y < 0.5 * (G.y_lo + G.y_hi) ? G.U_lo : G.U_hi;
+            u[0] = (R)v[0]; u[1] = (R)v[1]; u[2] = (R)v[2];
+        }
+        R du[3][3], Qt[6];
+        fd_gradient<R>(su, sok, u, du);
+        pressure_excess<R>(rho, u, du, (R)L.beta, Qt);
+        if (act) Codec<S>::store(fa + (size_t)lane * N + n, grad_shifted<R>(lane, rho, rho0, u, Qt));
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------- launchers
+template <typename F>
+static cudaError_t dispatch(int storage, F &&fn)
+{
+    switch (storage) {
+    case LBM_FP64: return fn((double *)nullptr);
+    case LBM_FP32: return fn((float *)nullptr);
+    case LBM_FP16: return fn((__half *)nullptr);
+    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static int list_blocks(int cap)
+{
+    int nb = (cap + BWARPS - 1) / BWARPS;
+    return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
+}
+
+cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S,
+                            const void *fa, void *fb, const uint8_t *flags, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        boundary_kernel<T><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, s>>>(
+            L, G, S.body, S.bnode, S.bmask, S.bq, S.buw, S.bforce, (const T *)fa, (T *)fb, flags,
+            &S.body->status);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, void *fa,
+                          const uint8_t *flags, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        refill_kernel<T><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(L, G, S.body, S.unode,
+                                                                               (T *)fa, flags);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace lbm

@@ -1,0 +1,219 @@
+// Bulk fused pull-stream + KBC collide (arXiv 1608.04658, Sec. 2, Eq. kineticEq
+// with Eq. kbc_relax), plus state initialisation, plane codec and totals.
+//
+// One thread per node, threads along x (the fastest axis of every population
+// plane) so each of the 27 plane loads and stores of a warp is one contiguous
+// run; the +-1 x-shift of a pull touches one extra 32-byte sector per warp,
+// which the neighbouring warp reads anyway, so DRAM traffic stays at one read
+// and one write per population.  Nodes marked SOLID or BOUNDARY are left to
+// the boundary kernel.
+#include "kbc.cuh"
+
+namespace lbm {
+
+// Source coordinate per velocity component c = -1, 0, +1 for a pull from a - c,
+// and its kind: 0 interior (wrapped/clamped), 1 equilibrium face, 2 wall.
+__device__ __forceinline__ void axis_src(int a, int n, int face_lo, int face_hi, int s[3], int k[3])
+{
+    s[1] = a; k[1] = 0;
+    // c = +1 pulls from a - 1
+    int lo = a - 1, klo = 0;
+    if (lo < 0) {
+        if (face_lo == LBM_FACE_PERIODIC) lo = n - 1;
+        else if (face_lo == LBM_FACE_OUTFLOW) lo = 0;
+        else { klo = face_lo == LBM_FACE_WALL ? 2 : 1; lo = a; }
+    }
+    // c = -1 pulls from a + 1
+    int hi = a + 1, khi = 0;
+    if (hi >= n) {
+        if (face_hi == LBM_FACE_PERIODIC) hi = 0;
+        else if (face_hi == LBM_FACE_OUTFLOW) hi = n - 1;
+        else { khi = face_hi == LBM_FACE_WALL ? 2 : 1; hi = a; }
+    }
+    s[2] = lo; k[2] = klo;
+    s[0] = hi; k[0] = khi;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) bulk_kernel(const Lattice L, const S *__restrict__ fa,
+                                                   S *__restrict__ fb,
+                                                   const uint8_t *__restrict__ flags,
+                                                   int *__restrict__ status)
+{
+    using R = typename Codec<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= L.nx) return;
+    const int nx = L.nx, ny = L.ny;
+    const int n = x + nx * (y + ny * z);
+    if (flags != nullptr && (flags[n] & (FL_SOLID | FL_BOUNDARY))) return;
+    const size_t N = (size_t)L.N;
+
+    int sx[3], sy[3], sz[3], kx[3], ky[3], kz[3];
+    axis_src(x, nx, L.face[0], L.face[1], sx, kx);
+    axis_src(y, ny, L.face[2], L.face[3], sy, ky);
+    axis_src(z, L.nz, L.face[4], L.face[5], sz, kz);
+
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i) + 1, cy = cy_of(i) + 1, cz = cz_of(i) + 1;
+        const int k = max(kx[cx], max(ky[cy], kz[cz]));
+        const int src = sx[cx] + nx * (sy[cy] + ny * sz[cz]);
+        if (k == 0) g[i] = Codec<S>::load(fa + (size_t)i * N + src);
+        else if (k == 2) g[i] = Codec<S>::load(fa + (size_t)(26 - i) * N + n);
+        else g[i] = (R)L.g_face[i];
+    }
+    const bool ok = kbc_collide<R>(g, (R)L.beta, (R)L.rho0, L.gamma_mode);
+    if (!ok) atomicOr(status, ST_UNSTABLE);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Codec<S>::store(fb + (size_t)i * N + n, g[i]);
+}
+
+template <typename S>
+__global__ void init_kernel(const Lattice L, S *__restrict__ f, const double *__restrict__ rho,
+                            const double *__restrict__ u, const double *__restrict__ xi, double amp)
+{
+    using R = typename Codec<S>::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    // equilibrium evaluated in double, then rounded once to storage
+    double ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
+    axis_eq<double>(u[3 * n + 0], ex, rx);
+    axis_eq<double>(u[3 * n + 1], ey, ry);
+    axis_eq<double>(u[3 * n + 2], ez, rz);
+    const double r = rho[n], drho = r - L.rho0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        double g = shifted_feq<double>(i, drho, r, ex, ey, ez);
+        if (xi) g += amp * weight<double>(i) * xi[(size_t)i * L.N + n];
+        Codec<S>::store(f + (size_t)i * L.N + n, (R)g);
+    }
+}
+
+template <typename S>
+__global__ void decode_kernel(const Lattice L, const S *__restrict__ f, int i, double *__restrict__ out)
+{
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    out[n] = (double)Codec<S>::load(f + (size_t)i * L.N + n) + weight<double>(i) * L.rho0;
+}
+
+template <typename S>
+__global__ void encode_kernel(const Lattice L, S *__restrict__ f, int i, const double *__restrict__ in)
+{
+    using R = typename Codec<S>::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    Codec<S>::store(f + (size_t)i * L.N + n, (R)(in[n] - weight<double>(i) * L.rho0));
+}
+
+// Per-block FP64 partial sums of mass, momentum and kinetic energy over
+// non-solid nodes; the host adds the block partials in block order.
+template <typename S>
+__global__ void __launch_bounds__(256) totals_kernel(const Lattice L, const S *__restrict__ f,
+                                                     const uint8_t *__restrict__ flags,
+                                                     double *__restrict__ partials)
+{
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < L.N;
+         n += (long long)gridDim.x * blockDim.x) {
+        if (flags && (flags[n] & FL_SOLID)) continue;
+        double r = 0, j[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+            const double v = (double)Codec<S>::load(f + (size_t)i * L.N + n) + weight<double>(i) * L.rho0;
+            r += v;
+            j[0] += cx_of(i) * v;
+            j[1] += cy_of(i) * v;
+            j[2] += cz_of(i) * v;
+        }
+        acc[0] += r;
+        acc[1] += j[0];
+        acc[2] += j[1];
+        acc[3] += j[2];
+        acc[4] += 0.5 * (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) / r;
+    }
+    __shared__ double sm[8][5];
+    for (int k = 0; k < 5; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sm[w][threadIdx.x];
+        partials[blockIdx.x * 5 + threadIdx.x] = v;
+    }
+}
+
+// ----------------------------------------------------------------- launchers
+template <typename F>
+static cudaError_t dispatch(int storage, F &&fn)
+{
+    switch (storage) {
+    case LBM_FP64: return fn((double *)nullptr);
+    case LBM_FP32: return fn((float *)nullptr);
+    case LBM_FP16: return fn((__half *)nullptr);
+    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
+                        const uint8_t *flags, int *status, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
+        dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
+        bulk_kernel<S><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
+                        const double *u, const double *xi, double amp, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        const int nb = (int)((L.N + 255) / 256);
+        init_kernel<S><<<nb, 256, 0, s>>>(L, (S *)fa, rho, u, xi, amp);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,
+                                double *out, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        const int nb = (int)((L.N + 255) / 256);
+        decode_kernel<S><<<nb, 256, 0, s>>>(L, (const S *)f, i, out);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_encode_plane(int storage, const Lattice &L, void *f, int i,
+                                const double *in, cudaStream_t s)
+{
+    return dispatch(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        const int nb = (int)((L.N + 255) / 256);
+        encode_kernel<S><<<nb, 256, 0, s>>>(L, (S *)f, i, in);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_totals(int storage, const Lattice &L, const void *f, const uint8_t *flags,
+                          double *partials, int nblocks, double *out, cudaStream_t s)
+{
+    (void)out;
+    return dispatch(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        totals_kernel<S><<<nblocks, 256, 0, s>>>(L, (const S *)f, flags, partials);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace lbm

@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every entry point include/lbm.h declares, its structs have the layout the
+binding assumes, and argument errors are reported before any CUDA call."""
+import ctypes as C
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_1608_04658_gb300 as lbm
+from paper_1608_04658_gb300 import binding
+
+
+@pytest.fixture(scope="module")
+def L():
+    lbm.build()
+    return lbm.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = lbm.declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def _c_layout(struct, fields):
+    src = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{binding.HEADER}"', "int main(void){",
+           f'printf("%zu\\n", sizeof({struct}));']
+    src += [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src += ["return 0;}"]
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write("\n".join(src))
+        subprocess.check_call(["gcc", "-std=c99", "-o", exe, c])
+        return [int(v) for v in subprocess.check_output([exe]).split()]
+
+
+@pytest.mark.parametrize("cls,cname", [(binding.Params, "lbm_params"), (binding.Geometry, "lbm_geometry"),
+                                       (binding.BodyState, "lbm_body_state")])
+def test_struct_layout_matches_header(cls, cname):
+    fields = [f for f, _ in cls._fields_]
+    got = _c_layout(cname, fields)
+    assert got[0] == C.sizeof(cls)
+    for f, off in zip(fields, got[1:]):
+        assert getattr(cls, f).offset == off, f
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(L):
+    ctx = C.c_void_p()
+    dummy = C.c_void_p(16)
+    p = lbm.make_params((0, 4, 4), 0.1)
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((4, 4, 4), 0.1)
+    assert L.lbm_create(C.byref(p), None, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((4, 4, 4), 0.1, faces=(0, 1, 0, 0, 0, 0))  # periodic on one side only
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((4, 4, 4), -1.0)
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((4, 4, 4), 0.1)
+    p.storage = 9
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((4, 4, 4), 0.1)
+    assert L.lbm_create(C.byref(p), C.c_void_p(24), dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    assert not ctx.value
+    p = lbm.make_params((2048, 2048, 1024), 0.1)  # N >= 2^31
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    assert L.lbm_step(None, 1) == binding.LBM_ERR_ARG
+    assert L.lbm_last_error(None) == b"null context"
+
+
+def test_product_package_does_not_import_the_oracle():
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys, paper_1608_04658_gb300 as p; p.lib(); "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    out = subprocess.check_output([sys.executable, "-c", code], cwd=root).decode().strip()
+    assert out == "False"
+    for dirpath, _, files in os.walk(os.path.join(root, "paper_1608_04658_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "kbc_oracle" not in text, f

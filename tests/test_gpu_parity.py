@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element (arXiv 1608.04658, Secs. 2-4.1).
+
+Bars (max relative error of full populations over fluid nodes): 1e-12 for
+FP64 storage, 2e-6 for FP32, 2e-3 for FP16/BF16 after 10 steps."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import TOL, fluid_mask, random_fields, rel_err, run_pair
+
+pytestmark = pytest.mark.gpu
+STORAGES = ["fp64", "fp32", "fp16", "bf16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1608_04658_gb300 as lbm
+    lbm.build()
+    lbm.lib()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("shape", [(150, 6, 5), (24, 20, 18)])
+def test_periodic_random_state(storage, shape):
+    """Rough random fields on periodic boxes: two x-blocks with a ragged tail
+    (150 = 128 + 22) and a non-power-of-two box."""
+    fields = random_fields(shape, 1)
+    for steps in (1, 10):
+        lat, orc = run_pair(shape, 0.01, storage, fields, steps)
+        err = rel_err(lat.populations(), orc.get_f())
+        assert err <= TOL[storage], (storage, steps, err)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_lbgk_mode(storage):
+    shape = (40, 9, 7)
+    lat, orc = run_pair(shape, 0.02, storage, random_fields(shape, 2), 10, gamma_mode=2)
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage]
+
+
+def test_taylor_green_32_re1600_fp64_100_steps():
+    """Plain method, periodic 32^3 Taylor-Green vortex, u0 = 0.05, Re = 1600,
+    100 steps: FP64 parity, mass and momentum conservation, energy decay."""
+    wl = synth.tgv_periodic(32)
+    rho, u = synth.taylor_green_fields(wl["shape"], wl["u0"])
+    lat, orc = run_pair(wl["shape"], wl["nu"], "fp64", (rho, u, None, 0.0), 100)
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL["fp64"]
+    T = lat.totals()
+    To = orc.totals()
+    assert abs(T[0] - To[0]) < 1e-12 * To[0]
+    assert np.abs(T[1:4]).max() < 1e-11
+    assert T[4] == pytest.approx(To[4], rel=1e-11)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_taylor_green_storage_forms(storage):
+    wl = synth.tgv_periodic(32)
+    rho, u = synth.taylor_green_fields(wl["shape"], wl["u0"])
+    lat, orc = run_pair(wl["shape"], wl["nu"], storage, (rho, u, None, 0.0), 10)
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_box_faces(storage):
+    """Equilibrium inflow at x-, outflow at x+, walls at y+-, periodic z."""
+    shape = (20, 12, 10)
+    faces = (2, 3, 1, 1, 0, 0)
+    lat, orc = run_pair(shape, 0.02, storage, random_fields(shape, 3), 10, faces=faces,
+                        u_face=(0.04, 0.0, 0.01))
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage]
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_stationary_sphere(storage):
+    """Fixed sphere in a periodic box with a mean flow: Grad boundary, momentum
+    exchange."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (24, 20, 22)
+    rho, u, xi = synth.parity_fields(shape, 4)
+    fields = (rho, 0.3 * u + np.array([0.03, 0.01, -0.02]), xi, 1e-3)
+    geom = lbm.sphere((11.37, 9.61, 10.83), 4.3)
+    lat, orc = run_pair(shape, 0.02, storage, fields, 10, geom=geom)
+    mask = fluid_mask(lat, orc)
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+    F, M = lat.forces()
+    Fo, Mo = np.array(orc.body.F), np.array(orc.body.M)
+    ftol = 1e-10 if storage == "fp64" else (1e-5 if storage == "fp32" else 2e-2)
+    assert np.abs(F - Fo).max() <= ftol * np.abs(Fo).max()
+    assert np.abs(M - Mo).max() <= ftol * np.abs(Mo).max() + 1e-12
+    b = lat.body()
+    assert b["n_boundary"] == orc.counters()["boundary"] // 10
+    assert b["n_links"] == orc.counters()["links"] // 10
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_moving_free_sphere_with_refill(storage):
+    """Free sphere between no-slip x/y walls, periodic z, under gravity: body
+    update, moving-wall Grad boundary and refill of uncovered nodes."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (28, 24, 40)
+    faces = (1, 1, 1, 1, 0, 0)
+    rho, u, xi = synth.parity_fields(shape, 5)
+    fields = (rho, 0.2 * u, xi, 1e-3)
+    geom = lbm.sphere((13.71, 11.42, 19.13), 4.6, U=(0.05, -0.03, -0.12), free=True,
+                      rho_ratio=1.5, g=(0.0, 0.0, -2e-4))
+    lat, orc = run_pair(shape, 0.03, storage, fields, 10, faces=faces, geom=geom)
+    mask = fluid_mask(lat, orc)
+    assert orc.counters()["refill"] > 10
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+    b = lat.body()
+    ob = orc.body
+    # the trajectory integrates the force, whose error follows the storage rounding
+    xtol = {"fp64": 1e-13, "fp32": 1e-8, "fp16": 1e-5, "bf16": 1e-4}[storage]
+    assert np.abs(b["X"] - np.array(ob.X)).max() < xtol
+    assert np.abs(b["U"] - np.array(ob.U)).max() < xtol
+    assert b["status"] == 0
+
+
+def test_couette_planes_fp64():
+    """Channel walls at q = 0.3 with the top wall moving: Grad boundary on a
+    flat moving wall."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (3, 20, 4)
+    geom = lbm.planes(1.7, 18.3, U_hi=(0.01, 0.0, 0.0))
+    lat, orc = run_pair(shape, 1.0 / 6.0, "fp64", (*synth.uniform_fields(shape), None, 0.0), 200, geom=geom)
+    mask = fluid_mask(lat, orc)
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL["fp64"]
+
+
+def test_unstable_state_is_reported():
+    """A NaN in the initial density (made on the host) sets the device status
+    word; lbm_body_forces returns LBM_ERR_UNSTABLE.  No GPU fault is involved."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (16, 8, 8)
+    rho, u = synth.uniform_fields(shape)
+    rho[3, 4, 5] = np.nan
+    lat = lbm.Lattice(shape, 0.02, storage="fp32")
+    lat.init_state(rho, u)
+    lat.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.forces()
+    assert e.value.status == 4
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "fp64"])
+def test_sedimenting_sphere_full_size_sampled(storage):
+    """Full-size sedimenting-sphere box (128x128x256, D = 16, x/y walls,
+    periodic z) in the launch configuration the benchmark times: one step from
+    a seeded random state, compared at every boundary node and at 4000 random
+    nodes, which the oracle computes one by one."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.sedimenting_sphere()
+    shape = wl["shape"]
+    rho, u, xi = synth.parity_fields(shape, 7)
+    geom = lbm.sphere(wl["X"], wl["D"] / 2, U=(0.0, 0.0, -0.04), free=True, rho_ratio=wl["rho_ratio"],
+                      g=wl["g"])
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"])
+    lat.set_geometry(geom)
+    lat.init_state(rho, u, xi, 1e-3)
+    f0 = lat.populations()
+    lat.step(1)
+    f1 = lat.populations()
+    flags = lat.flags.cpu().numpy().reshape(-1)
+    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
+                        body=oracle.sphere_body(wl["X"], wl["D"] / 2, U=(0.0, 0.0, -0.04), free=True,
+                                                rho_ratio=wl["rho_ratio"], g=wl["g"]))
+    orc.set_f(f0)  # the decoded stored state is the common input
+    rng = np.random.default_rng(7)
+    bnodes = np.nonzero(flags & 4)[0]
+    assert len(bnodes) > 500
+    nodes = np.unique(np.concatenate([bnodes, rng.integers(0, lat.N, 4000),
+                                      [0, lat.N - 1, shape[0] - 1]]))
+    ref = orc.step_sampled(nodes)
+    got = f1.reshape(27, -1)[:, nodes].T
+    ok = ~np.isnan(ref[:, 0])
+    assert np.array_equal(ok, (flags[nodes] & 1) == 0)
+    # one step from the same stored input: FP32 arithmetic and one rounding to storage
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
+    assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
