@@ -297,7 +297,8 @@ static long nid(const orc_ctx *c, int x, int y, int z)
 
 /* Displacement of a node from the sphere centre.  Reading (the paper's
  * sedimenting sphere falls through a periodic box): on a periodic axis the
- * sphere is taken at its nearest image, d - n floor(d/n + 1/2). */
+ * centre is kept in [0, n) and the sphere is taken at its nearest image, by
+ * adding or subtracting n once when |d| exceeds n/2. */
 static void sphere_offset(const orc_ctx *c, double x, double y, double z, double *d)
 {
     const orc_body *b = &c->b;
@@ -305,7 +306,11 @@ static void sphere_offset(const orc_ctx *c, double x, double y, double z, double
     int n[3] = {c->p.nx, c->p.ny, c->p.nz};
     for (int a = 0; a < 3; ++a) {
         d[a] = p[a] - b->X[a];
-        if (c->p.face[2 * a] == FACE_PERIODIC) d[a] = d[a] - n[a] * floor(d[a] / n[a] + 0.5);
+        if (c->p.face[2 * a] == FACE_PERIODIC) {
+            double h = 0.5 * n[a];
+            if (d[a] > h) d[a] = d[a] - n[a];
+            else if (d[a] < -h) d[a] = d[a] + n[a];
+        }
     }
 }
 
@@ -594,14 +599,24 @@ void orc_init_state(orc_ctx *c, const double *rho, const double *u, const double
 }
 
 /* Newton's equations of the sphere (Sec. 4.1) by explicit Euler:
- * X^{t+1} = X^t + U^t,  U^{t+1} = U^t + F^t/m_s + (1 - rho_f/rho_s) g. */
-static void body_update(orc_body *b)
+ * X^{t+1} = X^t + U^t,  U^{t+1} = U^t + F^t (1/m_s) + (1 - rho_f/rho_s) g,
+ * with 1/m_s and (1 - rho_f/rho_s) g formed once.  On periodic axes the
+ * centre is wrapped back into [0, n). */
+static void body_update(orc_ctx *c)
 {
+    orc_body *b = &c->b;
     if (!b->free_motion) return;
+    const double inv_m = 1.0 / b->mass;
+    const double buoy = 1.0 - 1.0 / b->rho_ratio;
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
     for (int a = 0; a < 3; ++a) {
-        double acc = b->F[a] / b->mass + (1.0 - 1.0 / b->rho_ratio) * b->g[a];
-        b->X[a] += b->U[a];
-        b->U[a] += acc;
+        double acc = b->F[a] * inv_m + buoy * b->g[a];
+        b->X[a] = b->X[a] + b->U[a];
+        b->U[a] = b->U[a] + acc;
+        if (c->p.face[2 * a] == FACE_PERIODIC) {
+            if (b->X[a] >= n[a]) b->X[a] = b->X[a] - n[a];
+            else if (b->X[a] < 0.0) b->X[a] = b->X[a] + n[a];
+        }
     }
 }
 
@@ -609,7 +624,7 @@ static void body_update(orc_body *b)
  * nodes at t+1 and refills uncovered nodes in the current state. */
 static void step_prepare(orc_ctx *c)
 {
-    body_update(&c->b);
+    body_update(c);
     const orc_params *p = &c->p;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
