@@ -48,7 +48,7 @@ typedef enum {
     LBM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     LBM_ERR_OOM = 3,         /* device allocation failed */
     LBM_ERR_UNSTABLE = 4,    /* a node had non-finite or non-positive density */
-    LBM_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (status bit 4) */
     LBM_ERR_STATE = 6,       /* call out of order (e.g. step before init) */
     LBM_ERR_UNSUPPORTED = 7  /* option not built */
 } lbm_status;
@@ -71,12 +71,16 @@ typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_EQ = 2, LBM_FA
  * is BGK with relaxation 2 beta. */
 typedef enum { LBM_GAMMA_ANALYTIC = 0, LBM_GAMMA_LBGK = 2 } lbm_gamma_mode;
 
+#define LBM_OPT_PLAIN_BULK 1
+
 typedef struct {
-    int32_t nx, ny, nz;   /* lattice size, each >= 1 */
+    int32_t nx, ny, nz;   /* lattice size, each >= 1, 27 * nx * ny * nz < 2^31 */
     int32_t storage;      /* lbm_storage */
     int32_t face[6];      /* lbm_face for x-, x+, y-, y+, z-, z+ */
     int32_t gamma_mode;   /* lbm_gamma_mode */
-    int32_t reserved;
+    int32_t options;      /* bit 0 (LBM_OPT_PLAIN_BULK): bulk kernel with per-thread global
+                             loads instead of the pipelined one (which needs rows of a
+                             multiple of 16 bytes) */
     double nu;            /* kinematic viscosity: beta = 1/(6 nu + 1) (Sec. 2, c_s^2 = 1/3) */
     double rho0;          /* reference density of the shifted storage and of rho_dyn */
     double u_face[3];     /* velocity of EQ faces */
@@ -113,7 +117,7 @@ typedef struct {
     int32_t n_boundary;   /* boundary nodes of the last step */
     int32_t n_uncovered;  /* nodes refilled in the last step */
     int32_t n_links;      /* missing populations of the last step */
-    int32_t status;       /* device status bits (1: unstable node, 2: band overflow) */
+    int32_t status;       /* device status bits (1: unstable node, 2: band overflow, 4: timeout) */
 } lbm_body_state;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -36,7 +36,7 @@ class LbmError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("storage", C.c_int32),
-                ("face", C.c_int32 * 6), ("gamma_mode", C.c_int32), ("reserved", C.c_int32),
+                ("face", C.c_int32 * 6), ("gamma_mode", C.c_int32), ("options", C.c_int32),
                 ("nu", C.c_double), ("rho0", C.c_double), ("u_face", C.c_double * 3)]
 
 
@@ -118,14 +118,18 @@ def _torch():
 _TORCH_DTYPES = {"fp64": "float64", "fp32": "float32", "fp16": "float16", "bf16": "bfloat16"}
 
 
+OPT_PLAIN_BULK = 1
+
+
 def make_params(shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0, u_face=(0.0, 0.0, 0.0),
-                gamma_mode=GAMMA_ANALYTIC) -> Params:
+                gamma_mode=GAMMA_ANALYTIC, options=0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
     p.storage = STORAGES[storage]
     for k in range(6):
         p.face[k] = int(faces[k])
     p.gamma_mode = int(gamma_mode)
+    p.options = int(options)
     p.nu = float(nu)
     p.rho0 = float(rho0)
     for a in range(3):
@@ -164,7 +168,7 @@ class Lattice:
     """
 
     def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0,
-                 u_face=(0.0, 0.0, 0.0), gamma_mode=GAMMA_ANALYTIC, device=None):
+                 u_face=(0.0, 0.0, 0.0), gamma_mode=GAMMA_ANALYTIC, device=None, options=0):
         torch = _torch()
         self.shape = tuple(int(v) for v in shape)
         nx, ny, nz = self.shape
@@ -177,7 +181,7 @@ class Lattice:
         self.f_b = torch.empty((27, nz, ny, nx), dtype=dt, device=self.device)
         self.flags = torch.zeros((nz, ny, nx), dtype=torch.uint8, device=self.device)
         self.stream = torch.cuda.current_stream(self.device)
-        self.params = make_params(shape, nu, storage, faces, rho0, u_face, gamma_mode)
+        self.params = make_params(shape, nu, storage, faces, rho0, u_face, gamma_mode, options)
         ctx = C.c_void_p()
         st = lib().lbm_create(C.byref(self.params), self.f_a.data_ptr(), self.f_b.data_ptr(),
                               self.flags.data_ptr(), C.c_void_p(self.stream.cuda_stream), C.byref(ctx))

@@ -1,5 +1,8 @@
 """Compile liblbm.so in-tree with nvcc for sm_103a.
 
+Extra nvcc flags for build-time variants can be passed in LBM_NVCC_FLAGS
+(for example -DLBM_PAIR_MIN_BLOCKS=8); they force a rebuild.
+
 Each .cu translation unit under csrc/ is compiled in parallel to an object
 file, then nvcc links the shared library paper_1608_04658_gb300/_build/liblbm.so.
 The CUDA runtime is linked statically, so the library loads on a machine
@@ -44,6 +47,10 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Build (if stale) and return the path of liblbm.so."""
+    env_extra = os.environ.get("LBM_NVCC_FLAGS", "").split()
+    if env_extra:
+        extra = list(extra or []) + env_extra
+        force = True
     if not force and up_to_date():
         return SO
     os.makedirs(BUILD, exist_ok=True)

@@ -25,6 +25,9 @@ struct lbm_ctx {
     bool has_body = false;
     bool initialised = false;
     Scratch S{};
+    int bcur = 0;                 // body copy holding the latest state
+    cudaStream_t side = nullptr;  // boundary + force kernels, overlapping the bulk kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *plane = nullptr;      // N doubles for the host codec
     double *tot_partials = nullptr;
     int tot_blocks = 608;
@@ -98,9 +101,8 @@ cudaError_t dalloc(T **p, size_t count)
 
 void free_scratch(Scratch &S, bool keep_body)
 {
-    cudaFree(S.bnode); cudaFree(S.bmask); cudaFree(S.bq); cudaFree(S.buw); cudaFree(S.bforce);
-    cudaFree(S.unode); cudaFree(S.blk_count); cudaFree(S.blk_ucount); cudaFree(S.blk_off);
-    cudaFree(S.blk_uoff); cudaFree(S.partials);
+    cudaFree(S.blist); cudaFree(S.bpos); cudaFree(S.ulist); cudaFree(S.bforce);
+    cudaFree(S.partials); cudaFree(S.ticket);
     DevBody *b = S.body;
     S = Scratch{};
     if (keep_body) S.body = b;
@@ -119,7 +121,7 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     if (!p || !f_a || !f_b || !flags) return LBM_ERR_ARG;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
     const long long N = (long long)p->nx * p->ny * p->nz;
-    if (N >= (1LL << 31)) return LBM_ERR_ARG;
+    if (27 * N >= (1LL << 31)) return LBM_ERR_ARG;  // 32-bit element offsets
     const size_t es = elem_size(p->storage);
     if (es == 0) return LBM_ERR_ARG;
     if (((uintptr_t)f_a % 16) || ((uintptr_t)f_b % 16)) return LBM_ERR_ARG;
@@ -130,31 +132,46 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
             return LBM_ERR_ARG;
     if (!(p->nu >= 0.0) || !std::isfinite(p->nu) || !(p->rho0 > 0.0)) return LBM_ERR_ARG;
     if (p->gamma_mode != LBM_GAMMA_ANALYTIC && p->gamma_mode != LBM_GAMMA_LBGK) return LBM_ERR_ARG;
+    if (p->options & ~LBM_OPT_PLAIN_BULK) return LBM_ERR_ARG;
 
     lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
     if (!ctx) return LBM_ERR_OOM;
     Lattice &L = ctx->L;
     L.nx = p->nx; L.ny = p->ny; L.nz = p->nz; L.N = N;
+    for (int i = 0; i < Q; ++i) L.plane[i] = (int)(i * N);
     for (int k = 0; k < 6; ++k) L.face[k] = p->face[k];
     L.gamma_mode = p->gamma_mode;
     L.beta = 1.0 / (6.0 * p->nu + 1.0);
+    L.inv_beta = 6.0 * p->nu + 1.0;
     L.rho0 = p->rho0;
     for (int a = 0; a < 3; ++a) L.u_face[a] = p->u_face[a];
     face_equilibrium(p->rho0, p->u_face, L.g_face);
+    L.pipelined = !(p->options & LBM_OPT_PLAIN_BULK) && pipelined_eligible(p->storage, L);
     ctx->storage = p->storage;
     ctx->elem = es;
     ctx->f[0] = f_a;
     ctx->f[1] = f_b;
     ctx->flags = flags;
     ctx->stream = (cudaStream_t)stream;
-    if (dalloc(&ctx->S.body, 1) != cudaSuccess || dalloc(&ctx->tot_partials, (size_t)ctx->tot_blocks * 5) != cudaSuccess) {
+    if (dalloc(&ctx->S.body, 2) != cudaSuccess || dalloc(&ctx->tot_partials, (size_t)ctx->tot_blocks * 5) != cudaSuccess) {
         free_scratch(ctx->S, false);
         cudaFree(ctx->tot_partials);
         delete ctx;
         return LBM_ERR_OOM;
     }
-    DevBody zero{};
-    if (cudaMemcpyAsync(ctx->S.body, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        free_scratch(ctx->S, false);
+        cudaFree(ctx->tot_partials);
+        if (ctx->side) cudaStreamDestroy(ctx->side);
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    DevBody zero[2] = {};
+    if (cudaMemcpyAsync(ctx->S.body, zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(flags, 0, (size_t)N, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         free_scratch(ctx->S, false);
@@ -170,7 +187,11 @@ void lbm_destroy(lbm_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->side);
     for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
+    cudaStreamDestroy(ctx->side);
     free_scratch(ctx->S, false);
     cudaFree(ctx->plane);
     cudaFree(ctx->tot_partials);
@@ -211,8 +232,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.g[a] = g->g[a];
         G.periodic[a] = L.face[2 * a] == LBM_FACE_PERIODIC;
     }
-    G.mass = g->mass;
-    G.rho_ratio = g->rho_ratio;
+    G.inv_mass = g->mass > 0.0 ? 1.0 / g->mass : 0.0;
+    G.buoy = g->rho_ratio > 0.0 ? 1.0 - 1.0 / g->rho_ratio : 0.0;
     const int n[3] = {L.nx, L.ny, L.nz};
     if (g->kind == LBM_BODY_SPHERE) {
         if (!(g->R > 0.0) || (g->free_motion && (!(g->mass > 0.0) || !(g->rho_ratio > 0.0))))
@@ -220,35 +241,34 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         for (int a = 0; a < 3; ++a) {
             const int c = (int)std::ceil(2.0 * g->R) + 9;
             G.cap[a] = c < n[a] ? c : n[a];
+            if (G.periodic[a] && !(g->X[a] >= 0.0 && g->X[a] < (double)n[a]))
+                return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: centre outside [0, n) on a periodic axis");
         }
     } else {
         for (int a = 0; a < 3; ++a) G.cap[a] = n[a];
     }
     const long long vol = (long long)G.cap[0] * G.cap[1] * G.cap[2];
+    if (vol >= (1LL << 31) / 6) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: body band too large");
     G.cap_boundary = (int)vol;
     G.cap_uncovered = (int)vol;
     Scratch &S = ctx->S;
-    S.n_count_blocks = (int)((vol + 255) / 256);
     S.n_partials = 64;
     bool ok = true;
     if (ctx->has_body) {
-        ok = dalloc(&S.bnode, vol) == cudaSuccess && dalloc(&S.bmask, vol) == cudaSuccess &&
-             dalloc(&S.bq, vol * Q) == cudaSuccess && dalloc(&S.buw, vol * Q * 3) == cudaSuccess &&
-             dalloc(&S.bforce, vol * 6) == cudaSuccess && dalloc(&S.unode, vol) == cudaSuccess &&
-             dalloc(&S.blk_count, S.n_count_blocks) == cudaSuccess &&
-             dalloc(&S.blk_ucount, S.n_count_blocks) == cudaSuccess &&
-             dalloc(&S.blk_off, S.n_count_blocks) == cudaSuccess &&
-             dalloc(&S.blk_uoff, S.n_count_blocks) == cudaSuccess &&
-             dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess;
+        ok = dalloc(&S.blist, vol) == cudaSuccess && dalloc(&S.bpos, vol) == cudaSuccess &&
+             dalloc(&S.ulist, vol) == cudaSuccess && dalloc(&S.bforce, vol * 6) == cudaSuccess &&
+             dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess && dalloc(&S.ticket, 1) == cudaSuccess;
+        if (ok) ok = cudaMemsetAsync(S.ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
     }
     if (!ok) {
         free_scratch(ctx->S, true);
         ctx->has_body = false;
         return fail(ctx, LBM_ERR_OOM, "lbm_set_geometry: device allocation failed");
     }
-    DevBody hb{};
-    for (int a = 0; a < 3; ++a) { hb.X[a] = g->X[a]; hb.U[a] = g->U[a]; }
-    LBM_CUDA(cudaMemcpyAsync(S.body, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
+    DevBody hb[2] = {};
+    for (int a = 0; a < 3; ++a) { hb[0].X[a] = g->X[a]; hb[0].U[a] = g->U[a]; }
+    ctx->bcur = 0;
+    LBM_CUDA(cudaMemcpyAsync(S.body, hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
     LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
     if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, g->X, ctx->flags, ctx->stream), "initial marks");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
@@ -274,19 +294,27 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     int launches = 0;
     for (int s = 0; s < nsteps; ++s) {
         void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
+        int *status = &ctx->S.body[ctx->bcur].status;
         if (ctx->has_body) {
-            LBM_CUDA(launch_body_update(ctx->L, ctx->G, ctx->S, ctx->stream), "body update");
-            LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, ctx->flags, ctx->stream, &launches), "geometry");
-            LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, fa, ctx->flags, ctx->stream), "refill");
+            const int prev = ctx->bcur, cur = prev ^ 1;
+            status = &ctx->S.body[cur].status;
+            LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->stream, &launches), "geometry");
+            LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->stream), "refill");
+            // boundary nodes and the force reduction run beside the bulk kernel
+            LBM_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork");
+            LBM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
+            LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side), "boundary");
+            LBM_CUDA(launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches), "forces");
+            LBM_CUDA(cudaEventRecord(ctx->ev_join, ctx->side), "join");
             LBM_CUDA(prof_mark(ctx, 0), "profile event");
-            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, &ctx->S.body->status, ctx->stream), "bulk");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, status, ctx->stream), "bulk");
             LBM_CUDA(prof_mark(ctx, 1), "profile event");
-            LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, fa, fb, ctx->flags, ctx->stream), "boundary");
-            LBM_CUDA(launch_forces(ctx->L, ctx->S, ctx->stream, &launches), "forces");
-            launches += 4;
+            LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
+            launches += 3;
+            ctx->bcur = cur;
         } else {
             LBM_CUDA(prof_mark(ctx, 0), "profile event");
-            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, &ctx->S.body->status, ctx->stream), "bulk");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream), "bulk");
             LBM_CUDA(prof_mark(ctx, 1), "profile event");
             launches += 1;
         }
@@ -346,7 +374,8 @@ lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
     if (!ctx) return LBM_ERR_ARG;
     if (!out) return fail(ctx, LBM_ERR_ARG, "lbm_get_body: null output");
     DevBody hb;
-    LBM_CUDA(cudaMemcpyAsync(&hb, ctx->S.body, sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream), "body read");
+    LBM_CUDA(cudaMemcpyAsync(&hb, ctx->S.body + ctx->bcur, sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream),
+             "body read");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
     for (int a = 0; a < 3; ++a) {
         out->X[a] = hb.X[a]; out->U[a] = hb.U[a];
@@ -379,6 +408,7 @@ lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged)
         }
     }
     if (b.status & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
+    if (b.status & ST_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (b.status & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
     return LBM_OK;
 }
@@ -386,7 +416,7 @@ lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged)
 lbm_status lbm_reset_average(lbm_ctx *ctx)
 {
     if (!ctx) return LBM_ERR_ARG;
-    DevBody *b = ctx->S.body;
+    DevBody *b = ctx->S.body + ctx->bcur;
     LBM_CUDA(cudaMemsetAsync(&b->F_sum, 0, sizeof(b->F_sum) + sizeof(b->M_sum) + sizeof(b->n_sum), ctx->stream), "reset");
     return LBM_OK;
 }

@@ -20,6 +20,7 @@
 //   the missing populations are replaced; the node then collides with KBC.
 //   Refill: mean density of the neighbours fluid at t (rho0 if none), the body
 //   velocity, gradient with the wall velocity at the centre.
+#include "geom.cuh"
 #include "kbc.cuh"
 
 namespace lbm {
@@ -41,24 +42,9 @@ __device__ __forceinline__ R pick(const R e[3], int c)
     return c < 0 ? e[0] : (c > 0 ? e[2] : e[1]);
 }
 
-// x + d with periodic wrap; -1 when it leaves the box through a non-periodic face
-__device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int z, int dx, int dy, int dz)
-{
-    int p[3] = {x + dx, y + dy, z + dz};
-    const int n[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (p[a] >= 0 && p[a] < n[a]) continue;
-        const int face = p[a] < 0 ? L.face[2 * a] : L.face[2 * a + 1];
-        if (face != LBM_FACE_PERIODIC) return -1;
-        p[a] = (p[a] + n[a]) % n[a];
-    }
-    return p[0] + L.nx * (p[1] + L.ny * p[2]);
-}
-
 // Lane-parallel KBC collision: lane i < 27 holds the shifted population g_i.
 template <typename R>
-__device__ R kbc_collide_lanes(R g, int i, R beta, R rho0, int gamma_mode, bool &ok)
+__device__ R kbc_collide_lanes(R g, int i, R beta, R inv_beta, R rho0, int gamma_mode, bool &ok)
 {
     const bool act = i < Q;
     const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
@@ -67,7 +53,7 @@ __device__ R kbc_collide_lanes(R g, int i, R beta, R rho0, int gamma_mode, bool 
     const R jx = wsum(R(cx) * gv), jy = wsum(R(cy) * gv), jz = wsum(R(cz) * gv);
     const R rho = rho0 + drho;
     ok = rho > R(0) && rho < R(1e30);
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = rcp(rho);
     R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
     axis_eq(jx * inv_rho, ex, rx);
     axis_eq(jy * inv_rho, ey, ry);
@@ -79,15 +65,13 @@ __device__ R kbc_collide_lanes(R g, int i, R beta, R rho0, int gamma_mode, bool 
     const R pxx = wsum(R(cx * cx) * d), pyy = wsum(R(cy * cy) * d), pzz = wsum(R(cz * cz) * d);
     const R pxy = wsum(R(cx * cy) * d), pxz = wsum(R(cx * cz) * d), pyz = wsum(R(cy * cz) * d);
     const R nxz = pxx - pzz, nyz = pyy - pzz;
-    const R ds = act ? shear_part<R>(i, nxz, nyz, pxy, pxz, pyz) : R(0);
+    const R ds = act ? shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz) : R(0);
     const R dh = d - ds;
     const R ifeq = act ? inv_rho * inv_weight<R>(i) * pick(rx, cx) * pick(ry, cy) * pick(rz, cz) : R(0);
     const R sh = wsum(ds * dh * ifeq), hh = wsum(dh * dh * ifeq);
     R gam = R(2);
-    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>()) {
-        const R ib = R(1) / beta;
-        gam = ib - (R(2) - ib) * sh / hh;
-    }
+    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>())
+        gam = inv_beta - (R(2) - inv_beta) * sh * rcp(hh);
     return geq + (R(1) - beta * gam) * d + beta * (gam - R(2)) * ds;
 }
 
@@ -176,22 +160,11 @@ __device__ __forceinline__ void node_xyz(const Lattice &L, int n, int &x, int &y
     z = n / (L.nx * L.ny);
 }
 
-__device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams &G, const DevBody *b,
-                                              int a, int p)
-{
-    if (G.kind != LBM_BODY_SPHERE) return (double)p;
-    const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
-    double d = __dsub_rn((double)p, b->X[a]);
-    if (G.periodic[a]) d = __dsub_rn(d, __dmul_rn((double)n, floor(__dadd_rn(__ddiv_rn(d, (double)n), 0.5))));
-    return d;
-}
-
 template <typename S>
 __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
-    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ bnode,
-    const uint32_t *__restrict__ bmask, const double *__restrict__ bq, const double *__restrict__ buw,
-    double *__restrict__ bforce, const S *__restrict__ fa, S *__restrict__ fb,
-    const uint8_t *__restrict__ flags, int *__restrict__ status)
+    const Lattice L, const GeomParams G, DevBody *__restrict__ b, const int *__restrict__ blist,
+    const int *__restrict__ bpos, double *__restrict__ bforce, const S *__restrict__ fa,
+    S *__restrict__ fb, const uint8_t *__restrict__ flags)
 {
     using R = typename Codec<S>::R;
     __shared__ R s_f[BWARPS][Q][28];
@@ -201,18 +174,24 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
     R (*sf)[28] = s_f[w];
     R (*su)[4] = s_u[w];
     int *sok = s_ok[w];
-    const int count = b->n_boundary;
+    const int count = min(b->n_boundary, G.cap_boundary);
     const size_t N = (size_t)L.N;
     const R rho0 = (R)L.rho0;
 
     for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
-        const int n = bnode[slot];
-        const uint32_t mask = bmask[slot];
+        const int n = blist[slot];
         int x, y, z;
         node_xyz(L, n, x, y, z);
         const int i = lane;
         const bool act = i < Q;
         const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
+        // missing set: directions whose pull source is solid at t+1
+        bool solid_src = false;
+        if (act && i != 13) {
+            const int src = pull_source(L, x, y, z, cx, cy, cz);
+            solid_src = src >= 0 && (flags[src] & FL_SOLID);
+        }
+        const uint32_t mask = __ballot_sync(FULL, solid_src);
 
         // neighbourhood node k = lane: x_b + c_k
         int nk = -1;
@@ -247,12 +226,7 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
         // target density and velocity over the missing set
         const R fbb = act ? sf[13][26 - (act ? i : 0)] : R(0);  // shifted f'_{opp i}(x_b, t)
         double q = 0, uw[3] = {0, 0, 0};
-        if (miss) {
-            q = bq[(size_t)slot * Q + i];
-            uw[0] = buw[((size_t)slot * Q + i) * 3 + 0];
-            uw[1] = buw[((size_t)slot * Q + i) * 3 + 1];
-            uw[2] = buw[((size_t)slot * Q + i) * 3 + 2];
-        }
+        if (miss) link_data(L, G, b, x, y, z, cx, cy, cz, q, uw);
         const R gstat = miss ? fbb : Fi;
         const R dyn = miss ? R(6) * weight<R>(i) * rho0 * (R(cx) * (R)uw[0] + R(cy) * (R)uw[1] + R(cz) * (R)uw[2])
                            : R(0);
@@ -293,15 +267,16 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
             dF[4] = r[2] * dF[0] - r[0] * dF[2];
             dF[5] = r[0] * dF[1] - r[1] * dF[0];
         }
+        const int pos = bpos[slot];
         for (int k = 0; k < 6; ++k) {
             double v = dF[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) bforce[(size_t)slot * 6 + k] = v;
+            if (lane == 0) bforce[(size_t)pos * 6 + k] = v;
         }
 
         bool ok;
-        const R out = kbc_collide_lanes<R>(gi, i, (R)L.beta, rho0, L.gamma_mode, ok);
-        if (lane == 0 && !ok) atomicOr(status, ST_UNSTABLE);
+        const R out = kbc_collide_lanes<R>(gi, i, (R)L.beta, (R)L.inv_beta, rho0, L.gamma_mode, ok);
+        if (lane == 0 && !ok) atomicOr(&b->status, ST_UNSTABLE);
         if (act) Codec<S>::store(fb + (size_t)i * N + n, out);
         __syncwarp();
     }
@@ -309,7 +284,7 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
 
 template <typename S>
 __global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
-    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ unode,
+    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
     S *__restrict__ fa, const uint8_t *__restrict__ flags)
 {
     using R = typename Codec<S>::R;
@@ -320,11 +295,11 @@ __global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
     R (*sf)[28] = s_f[w];
     R (*su)[4] = s_u[w];
     int *sok = s_ok[w];
-    const int count = b->n_uncovered;
+    const int count = min(b->n_uncovered, G.cap_uncovered);
     const size_t N = (size_t)L.N;
     const R rho0 = (R)L.rho0;
     for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
-        const int n = unode[slot];
+        const int n = ulist[slot];
         int x, y, z;
         node_xyz(L, n, x, y, z);
         const bool act = lane < Q;
@@ -370,24 +345,23 @@ static int list_blocks(int cap)
     return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
 }
 
-cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S,
+cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s)
 {
     return dispatch(storage, [&](auto tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         boundary_kernel<T><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, s>>>(
-            L, G, S.body, S.bnode, S.bmask, S.bq, S.buw, S.bforce, (const T *)fa, (T *)fb, flags,
-            &S.body->status);
+            L, G, S.body + cur, S.blist, S.bpos, S.bforce, (const T *)fa, (T *)fb, flags);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, void *fa,
+cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur, void *fa,
                           const uint8_t *flags, cudaStream_t s)
 {
     return dispatch(storage, [&](auto tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
-        refill_kernel<T><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(L, G, S.body, S.unode,
+        refill_kernel<T><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(L, G, S.body + cur, S.ulist,
                                                                                (T *)fa, flags);
         return cudaGetLastError();
     });

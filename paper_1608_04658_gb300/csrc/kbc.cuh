@@ -14,7 +14,7 @@
 // deviations: populations are carried as g_i = f_i - W_i rho0, and each 1-D
 // equilibrium factor is written as w(c) (1 + e(c)) with e small:
 //   sigma = S - 1 = 3u^2 / (S + 1),  2 - S = 1 - sigma,
-//   B - 1 = (3u + sigma)/(1 - u),    1/B - 1 = -(3u + sigma)/(2u + S),
+//   B - 1 = (3u + sigma)/(1 - u),    1/B - 1 = -(B - 1)/B,
 //   e(0) = -sigma,  e(+1) = (B-1)(1-sigma) - sigma,  e(-1) = (1/B-1)(1-sigma) - sigma,
 // so g_i^eq = W_i (rho - rho0 + rho E_i) with E_i = prod_a (1 + e_a) - 1 formed
 // without cancellation.  The KBC shear part ds (deviatoric natural second
@@ -33,110 +33,204 @@ template <typename R> __device__ __forceinline__ R gamma_floor();
 template <> __device__ __forceinline__ float gamma_floor<float>() { return 1e-30f; }
 template <> __device__ __forceinline__ double gamma_floor<double>() { return 1e-300; }
 
-// e(-1), e(0), e(+1) and 1/(1 + e) for one axis.
+// correctly rounded reciprocal and square root of the arithmetic type
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ double sqrt_rn(double x) { return sqrt(x); }
+
+// e(-1), e(0), e(+1) and r(c) = 1/(1 + e(c)) for one axis.  With
+// bp = B - 1 = (3u + sigma)/(1 - u) the other factors follow without a
+// division each: 1/B - 1 = -bp/(1 + bp), 1 + e(+-1) = (1 - sigma) B^{+-1}.
 template <typename R>
 __device__ __forceinline__ void axis_eq(R u, R e[3], R r[3])
 {
     const R u2 = u * u;
-    const R S = sqrt(R(1) + R(3) * u2);
-    const R sig = R(3) * u2 / (S + R(1));
+    const R S = sqrt_rn(R(1) + R(3) * u2);
+    const R sig = R(3) * u2 * rcp(S + R(1));
     const R a = R(3) * u + sig;
     const R oms = R(1) - sig;
-    const R bp = a / (R(1) - u);
-    const R bm = -a / (R(2) * u + S);
+    const R bp = a * rcp(R(1) - u);
+    const R bm = -bp * rcp(R(1) + bp);
     e[0] = bm * oms - sig;
     e[1] = -sig;
     e[2] = bp * oms - sig;
-    r[0] = R(1) / (R(1) + e[0]);
-    r[1] = R(1) / oms;
-    r[2] = R(1) / (R(1) + e[2]);
+    const R r1 = rcp(oms);
+    r[0] = r1 * (R(1) + bp);
+    r[1] = r1;
+    r[2] = r1 * (R(1) + bm);
 }
 
-// Shear part ds_i for direction i from N_xz, N_yz and the off-diagonal P.
+// Shear part ds_i for direction i from the face values (sx, sy, sz) and the
+// quarter off-diagonal moments (qxy, qxz, qyz).
 template <typename R>
-__device__ __forceinline__ R shear_part(int i, R nxz, R nyz, R pxy, R pxz, R pyz)
+__device__ __forceinline__ R shear_part(int i, R sx, R sy, R sz, R qxy, R qxz, R qyz)
 {
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     const int nz = nonzero_of(i);
-    if (nz == 1) {
-        if (cx) return (R(2) * nxz - nyz) * R(1.0 / 6.0);
-        if (cy) return (R(2) * nyz - nxz) * R(1.0 / 6.0);
-        return -(nxz + nyz) * R(1.0 / 6.0);
-    }
+    if (nz == 1) return cx ? sx : (cy ? sy : sz);
     if (nz == 2) {
-        if (cz == 0) return R(cx * cy) * pxy * R(0.25);
-        if (cy == 0) return R(cx * cz) * pxz * R(0.25);
-        return R(cy * cz) * pyz * R(0.25);
+        if (cz == 0) return cx * cy > 0 ? qxy : -qxy;
+        if (cy == 0) return cx * cz > 0 ? qxz : -qxz;
+        return cy * cz > 0 ? qyz : -qyz;
     }
     return R(0);
 }
 
+// Shear part from N_xz, N_yz and the off-diagonal second moments (used by the
+// lane-parallel boundary collision).
+template <typename R>
+__device__ __forceinline__ R shear_part_raw(int i, R nxz, R nyz, R pxy, R pxz, R pyz)
+{
+    return shear_part<R>(i, (R(2) * nxz - nyz) * R(1.0 / 6.0), (R(2) * nyz - nxz) * R(1.0 / 6.0),
+                         -(nxz + nyz) * R(1.0 / 6.0), R(0.25) * pxy, R(0.25) * pxz, R(0.25) * pyz);
+}
+
+// reciprocal / square root for the bulk collision: the hardware approximations
+// (relative error about 1 ulp) in FP32, correctly rounded in FP64
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
+
+// e(c), Phi(c) = 1 + e(c) and r(c) = 1/Phi(c) for one axis (see axis_eq)
+template <typename R>
+__device__ __forceinline__ void axis_eq_phi(R u, R e[3], R phi[3], R r[3])
+{
+    const R u2 = u * u;
+    const R S = sqrt_fast(R(1) + R(3) * u2);
+    const R sig = R(3) * u2 * rcp_fast(S + R(1));
+    const R a = R(3) * u + sig;
+    const R oms = R(1) - sig;
+    const R bp = a * rcp_fast(R(1) - u);
+    const R bm = -bp * rcp_fast(R(1) + bp);
+    e[0] = bm * oms - sig;
+    e[1] = -sig;
+    e[2] = bp * oms - sig;
+    phi[0] = bm * oms + oms;
+    phi[1] = oms;
+    phi[2] = bp * oms + oms;
+    const R r1 = rcp_fast(oms);
+    r[0] = r1 * bp + r1;
+    r[1] = r1;
+    r[2] = r1 * bm + r1;
+}
+
 // In-place collision of the 27 shifted populations g[] of one node.
 // Returns false when the density is not finite and positive.
+//
+// Operation count is kept low by regrouping (same mathematics):
+//   - moments from the nine x-lines l = 3(cy+1) + (cz+1) of the velocity cube
+//     (directions l, 9 + l, 18 + l have c_x = -1, 0, +1);
+//   - E_i = Phi_x Phi_y Phi_z - 1 as exy = e_y Phi_x + e_x, E = exy Phi_z + e_z,
+//     and g^eq_i = (rho W_i) E_i + W_i (rho - rho0);
+//   - 1/f^eq_i = Rx Ry Rz with R_a(c) = r_a(c)/w(c) (1/rho folded into Rx).
 template <typename R>
-__device__ __forceinline__ bool kbc_collide(R g[Q], R beta, R rho0, int gamma_mode)
+__device__ __forceinline__ bool kbc_collide(R g[Q], R beta, R inv_beta, R rho0, int gamma_mode)
 {
-    R drho = 0, jx = 0, jy = 0, jz = 0;
+    R Ls[9], Ld[9];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += g[i];
-        if (cx_of(i) > 0) jx += g[i]; else if (cx_of(i) < 0) jx -= g[i];
-        if (cy_of(i) > 0) jy += g[i]; else if (cy_of(i) < 0) jy -= g[i];
-        if (cz_of(i) > 0) jz += g[i]; else if (cz_of(i) < 0) jz -= g[i];
+    for (int l = 0; l < 9; ++l) {
+        Ld[l] = g[18 + l] - g[l];
+        Ls[l] = (g[18 + l] + g[l]) + g[9 + l];
     }
+    const R drho = ((Ls[0] + Ls[1]) + (Ls[2] + Ls[3])) + ((Ls[4] + Ls[5]) + ((Ls[6] + Ls[7]) + Ls[8]));
+    const R jx = ((Ld[0] + Ld[1]) + (Ld[2] + Ld[3])) + ((Ld[4] + Ld[5]) + ((Ld[6] + Ld[7]) + Ld[8]));
+    const R jy = ((Ls[6] + Ls[7]) + Ls[8]) - ((Ls[0] + Ls[1]) + Ls[2]);
+    const R jz = ((Ls[2] + Ls[5]) + Ls[8]) - ((Ls[0] + Ls[3]) + Ls[6]);
     const R rho = rho0 + drho;
     const bool ok = rho > R(0) && rho < R(1e30);
-    const R inv_rho = R(1) / rho;
-    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
-    axis_eq(jx * inv_rho, ex, rx);
-    axis_eq(jy * inv_rho, ey, ry);
-    axis_eq(jz * inv_rho, ez, rz);
+    const R inv_rho = rcp_fast(rho);
+    R ex[3], ey[3], ez[3], px[3], py[3], pz[3], rx[3], ry[3], rz[3];
+    axis_eq_phi(jx * inv_rho, ex, px, rx);
+    axis_eq_phi(jy * inv_rho, ey, py, ry);
+    axis_eq_phi(jz * inv_rho, ez, pz, rz);
+    R rw[4], dw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R w = k == 0 ? R(8) / R(27) : k == 1 ? R(2) / R(27) : k == 2 ? R(1) / R(54) : R(1) / R(216);
+        rw[k] = rho * w;
+        dw[k] = drho * w;
+    }
+    R exy[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) exy[a][b] = ey[b] * px[a] + ex[a];
 
-    // df_i = g_i - g_i^eq (stored in g), and the second moments of df
-    R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    // d = g - g^eq in place
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R exy = ex[cx + 1] + ey[cy + 1] + ex[cx + 1] * ey[cy + 1];
-        const R E = exy + ez[cz + 1] + exy * ez[cz + 1];
-        const R geq = weight<R>(i) * (drho + rho * E);
-        const R d = g[i] - geq;
-        g[i] = d;
-        if (cx) pxx += d;
-        if (cy) pyy += d;
-        if (cz) pzz += d;
-        if (cx && cy) pxy += R(cx * cy) * d;
-        if (cx && cz) pxz += R(cx * cz) * d;
-        if (cy && cz) pyz += R(cy * cz) * d;
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R E = exy[cx + 1][cy + 1] * pz[cz + 1] + ez[cz + 1];
+        g[i] = g[i] - (rw[nz] * E + dw[nz]);
     }
+    // second moments of d from line sums
+    R A[9], B[9], T[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        A[l] = g[18 + l] + g[l];
+        B[l] = g[18 + l] - g[l];
+        T[l] = A[l] + g[9 + l];
+    }
+    const R pxx = ((A[0] + A[1]) + (A[2] + A[3])) + ((A[4] + A[5]) + ((A[6] + A[7]) + A[8]));
+    const R pxy = ((B[6] + B[7]) + B[8]) - ((B[0] + B[1]) + B[2]);
+    const R pxz = ((B[2] + B[5]) + B[8]) - ((B[0] + B[3]) + B[6]);
+    const R pyy = ((T[0] + T[1]) + T[2]) + ((T[6] + T[7]) + T[8]);
+    const R pzz = ((T[0] + T[3]) + T[6]) + ((T[2] + T[5]) + T[8]);
+    const R pyz = (T[0] + T[8]) - (T[2] + T[6]);
     const R nxz = pxx - pzz, nyz = pyy - pzz;
+    const R sx = (R(2) * nxz - nyz) * R(1.0 / 6.0);
+    const R sy = (R(2) * nyz - nxz) * R(1.0 / 6.0);
+    const R sz = -(nxz + nyz) * R(1.0 / 6.0);
+    const R qxy = R(0.25) * pxy, qxz = R(0.25) * pxz, qyz = R(0.25) * pyz;
 
-    // entropic scalar products <ds|dh>, <dh|dh> with 1/f^eq = 1/(rho W) prod r
+    // entropic scalar products <ds|dh>, <dh|dh>
+    R Rx[3], Ry[3], Rz[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R iw = c == 1 ? R(1.5) : R(6);
+        Rx[c] = rx[c] * inv_rho * iw;
+        Ry[c] = ry[c] * iw;
+        Rz[c] = rz[c] * iw;
+    }
     R sh = 0, hh = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R ifeq = inv_rho * inv_weight<R>(i) * rx[cx + 1] * ry[cy + 1] * rz[cz + 1];
-        const R ds = shear_part<R>(i, nxz, nyz, pxy, pxz, pyz);
-        const R dh = g[i] - ds;
-        sh += ds * dh * ifeq;
-        hh += dh * dh * ifeq;
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R ifeq = (Rx[cx + 1] * Ry[cy + 1]) * Rz[cz + 1];
+        if (nz == 1 || nz == 2) {
+            const R ds = shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz);
+            const R dh = g[i] - ds;
+            const R t = dh * ifeq;
+            sh += ds * t;
+            hh += dh * t;
+        } else {
+            hh += g[i] * (g[i] * ifeq);
+        }
     }
     R gam = R(2);
-    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>()) {
-        const R ib = R(1) / beta;
-        gam = ib - (R(2) - ib) * sh / hh;
-    }
+    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>())
+        gam = inv_beta - (R(2) - inv_beta) * sh * rcp_fast(hh);
     const R c1 = R(1) - beta * gam;
     const R c2 = beta * (gam - R(2));
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R exy = ex[cx + 1] + ey[cy + 1] + ex[cx + 1] * ey[cy + 1];
-        const R E = exy + ez[cz + 1] + exy * ez[cz + 1];
-        const R geq = weight<R>(i) * (drho + rho * E);
-        const R ds = shear_part<R>(i, nxz, nyz, pxy, pxz, pyz);
-        g[i] = geq + c1 * g[i] + c2 * ds;
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R E = exy[cx + 1][cy + 1] * pz[cz + 1] + ez[cz + 1];
+        R v = c1 * g[i] + (rw[nz] * E + dw[nz]);
+        if (nz == 1 || nz == 2) v += c2 * shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz);
+        g[i] = v;
     }
     return ok;
 }

@@ -23,6 +23,7 @@ constexpr uint8_t FL_UNCOVERED = 8;  // solid at the previous step, fluid now
 // device status bits
 constexpr int ST_UNSTABLE = 1;
 constexpr int ST_BAND_OVERFLOW = 2;
+constexpr int ST_TIMEOUT = 4;        // a bounded wait on an mbarrier gave up
 
 __host__ __device__ constexpr int cx_of(int i) { return i / 9 - 1; }
 __host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
@@ -76,9 +77,12 @@ template <> struct Codec<__nv_bfloat16> {
 struct Lattice {
     int nx, ny, nz;
     long long N;
+    int plane[27];      // i * N: offset of population plane i (27 N < 2^31)
     int face[6];
     int gamma_mode;
+    int pipelined;      // 1: warp-specialised bulk kernel with bulk-copied rows
     double beta;
+    double inv_beta;
     double rho0;
     double u_face[3];
     double g_face[27];  // f^eq(rho0, u_face) - W rho0 for EQ faces
@@ -90,13 +94,17 @@ struct GeomParams {
     double R;
     double y_lo, y_hi;
     double U_lo[3], U_hi[3];
-    double mass, rho_ratio, g[3];
+    double inv_mass;     // 1 / m_s
+    double buoy;         // 1 - rho_f / rho_s
+    double g[3];
     int periodic[3];
     int cap[3];          // band capacity per axis
     int cap_boundary;    // slots in the boundary list
     int cap_uncovered;   // slots in the uncovered list
 };
 
+// Body state; two copies alternate between steps (the mark kernel reads the
+// previous one and writes the next).
 struct DevBody {
     double X[3], U[3];
     double F[3], M[3];
@@ -109,25 +117,20 @@ struct DevBody {
 
 // scratch owned by the library for the boundary path
 struct Scratch {
-    DevBody *body;
-    int *bnode;          // [cap_boundary] node index of each boundary node
-    uint32_t *bmask;     // [cap_boundary] missing-direction mask
-    double *bq;          // [cap_boundary * 27] link fraction q_i
-    double *buw;         // [cap_boundary * 27 * 3] wall velocity u_w,i
-    double *bforce;      // [cap_boundary * 6] force and torque of each node
-    int *unode;          // [cap_uncovered]
-    int *blk_count;      // [n_count_blocks] boundary count per block
-    int *blk_ucount;     // [n_count_blocks] uncovered count per block
-    int *blk_off;        // [n_count_blocks] boundary offset per block
-    int *blk_uoff;       // [n_count_blocks] uncovered offset per block
+    DevBody *body;       // [2]
+    int *blist;          // [cap_boundary] node index of each boundary node
+    int *bpos;           // [cap_boundary] band position of each boundary node
+    int *ulist;          // [cap_uncovered] node index of each uncovered node
+    double *bforce;      // [band capacity * 6] force and torque per band position
     double *partials;    // [n_partials * 6]
-    int n_count_blocks;
+    unsigned *ticket;    // last-block counter of the force reduction
     int n_partials;
 };
 
 // launchers ------------------------------------------------------------------
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s);
+bool pipelined_eligible(int storage, const Lattice &L);
 cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
                         const double *u, const double *xi, double amp, cudaStream_t s);
 cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,
@@ -137,15 +140,14 @@ cudaError_t launch_encode_plane(int storage, const Lattice &L, void *f, int i,
 cudaError_t launch_totals(int storage, const Lattice &L, const void *f, const uint8_t *flags,
                           double *partials, int nblocks, double *out, cudaStream_t s);
 
-cudaError_t launch_body_update(const Lattice &L, const GeomParams &G, Scratch &S, cudaStream_t s);
-cudaError_t launch_geometry(const Lattice &L, const GeomParams &G, Scratch &S, uint8_t *flags,
+cudaError_t launch_geometry(const Lattice &L, const GeomParams &G, Scratch &S, int prev, uint8_t *flags,
                             cudaStream_t s, int *nlaunch);
 cudaError_t launch_mark_initial(const Lattice &L, const GeomParams &G, const double *X,
                                 uint8_t *flags, cudaStream_t s);
-cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S,
+cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                           void *fa, const uint8_t *flags, cudaStream_t s);
-cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S,
+cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s);
-cudaError_t launch_forces(const Lattice &L, Scratch &S, cudaStream_t s, int *nlaunch);
+cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
 
 }  // namespace lbm
