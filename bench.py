@@ -48,8 +48,6 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--plain-bulk", action="store_true",
-                    help="one node per thread in the bulk kernel (comparison runs)")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
     return ap.parse_args()
@@ -201,13 +199,13 @@ def workload(shape=None):
     return synth.sedimenting_sphere()
 
 
-def make_lattice(storage, wl, device, options=0):
+def make_lattice(storage, wl, device):
     import numpy as np
 
     import paper_1608_04658_gb300 as lbm
     import synth
     shape = wl["shape"]
-    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device, options=options)
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device)
     lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
     rho, u = synth.uniform_fields(shape)
     lat.init_state(rho, u)
@@ -216,7 +214,7 @@ def make_lattice(storage, wl, device, options=0):
 
 def time_storage(storage, wl, args, world, device, clocks):
     import torch
-    lat, np = make_lattice(storage, wl, device, options=1 if args.plain_bulk else 0)
+    lat, np = make_lattice(storage, wl, device)
     K, W = args.steps, args.warmup
     lat.step(W)
     torch.cuda.synchronize()

@@ -71,16 +71,13 @@ typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_EQ = 2, LBM_FA
  * is BGK with relaxation 2 beta. */
 typedef enum { LBM_GAMMA_ANALYTIC = 0, LBM_GAMMA_LBGK = 2 } lbm_gamma_mode;
 
-#define LBM_OPT_PLAIN_BULK 1
 
 typedef struct {
     int32_t nx, ny, nz;   /* lattice size, each >= 1, 27 * nx * ny * nz < 2^31 */
     int32_t storage;      /* lbm_storage */
     int32_t face[6];      /* lbm_face for x-, x+, y-, y+, z-, z+ */
     int32_t gamma_mode;   /* lbm_gamma_mode */
-    int32_t options;      /* bit 0 (LBM_OPT_PLAIN_BULK): bulk kernel with per-thread global
-                             loads instead of the pipelined one (which needs rows of a
-                             multiple of 16 bytes) */
+    int32_t options;      /* reserved, must be 0 */
     double nu;            /* kinematic viscosity: beta = 1/(6 nu + 1) (Sec. 2, c_s^2 = 1/3) */
     double rho0;          /* reference density of the shifted storage and of rho_dyn */
     double u_face[3];     /* velocity of EQ faces */

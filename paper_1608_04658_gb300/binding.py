@@ -118,9 +118,6 @@ def _torch():
 _TORCH_DTYPES = {"fp64": "float64", "fp32": "float32", "fp16": "float16", "bf16": "bfloat16"}
 
 
-OPT_PLAIN_BULK = 1
-
-
 def make_params(shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0, u_face=(0.0, 0.0, 0.0),
                 gamma_mode=GAMMA_ANALYTIC, options=0) -> Params:
     p = Params()

@@ -1,7 +1,7 @@
 """Compile liblbm.so in-tree with nvcc for sm_103a.
 
 Extra nvcc flags for build-time variants can be passed in LBM_NVCC_FLAGS
-(for example -DLBM_PAIR_MIN_BLOCKS=8); they force a rebuild.
+(for example -DLBM_BULK_MIN_BLOCKS=7); they force a rebuild.
 
 Each .cu translation unit under csrc/ is compiled in parallel to an object
 file, then nvcc links the shared library paper_1608_04658_gb300/_build/liblbm.so.

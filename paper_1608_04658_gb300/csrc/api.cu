@@ -132,7 +132,7 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
             return LBM_ERR_ARG;
     if (!(p->nu >= 0.0) || !std::isfinite(p->nu) || !(p->rho0 > 0.0)) return LBM_ERR_ARG;
     if (p->gamma_mode != LBM_GAMMA_ANALYTIC && p->gamma_mode != LBM_GAMMA_LBGK) return LBM_ERR_ARG;
-    if (p->options & ~LBM_OPT_PLAIN_BULK) return LBM_ERR_ARG;
+    if (p->options != 0) return LBM_ERR_ARG;
 
     lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
     if (!ctx) return LBM_ERR_OOM;
@@ -146,7 +146,6 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     L.rho0 = p->rho0;
     for (int a = 0; a < 3; ++a) L.u_face[a] = p->u_face[a];
     face_equilibrium(p->rho0, p->u_face, L.g_face);
-    L.pipelined = !(p->options & LBM_OPT_PLAIN_BULK) && pipelined_eligible(p->storage, L);
     ctx->storage = p->storage;
     ctx->elem = es;
     ctx->f[0] = f_a;
@@ -295,29 +294,32 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
         int *status = &ctx->S.body[ctx->bcur].status;
+        const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;
+        int cur = ctx->bcur;
         if (ctx->has_body) {
-            const int prev = ctx->bcur, cur = prev ^ 1;
+            const int prev = ctx->bcur;
+            cur = prev ^ 1;
             status = &ctx->S.body[cur].status;
             LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->stream, &launches), "geometry");
             LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->stream), "refill");
-            // boundary nodes and the force reduction run beside the bulk kernel
+            launches += 1;
+        }
+        // the boundary nodes and the force reduction run on a side stream beside
+        // the bulk kernel (they write disjoint nodes)
+        if (ctx->has_body) {
             LBM_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork");
             LBM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
             LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side), "boundary");
             LBM_CUDA(launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches), "forces");
             LBM_CUDA(cudaEventRecord(ctx->ev_join, ctx->side), "join");
-            LBM_CUDA(prof_mark(ctx, 0), "profile event");
-            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, status, ctx->stream), "bulk");
-            LBM_CUDA(prof_mark(ctx, 1), "profile event");
-            LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
-            launches += 3;
-            ctx->bcur = cur;
-        } else {
-            LBM_CUDA(prof_mark(ctx, 0), "profile event");
-            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream), "bulk");
-            LBM_CUDA(prof_mark(ctx, 1), "profile event");
             launches += 1;
         }
+        LBM_CUDA(prof_mark(ctx, 0), "profile event");
+        LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream), "bulk");
+        LBM_CUDA(prof_mark(ctx, 1), "profile event");
+        if (ctx->has_body) LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
+        launches += 1;
+        ctx->bcur = cur;
         ctx->cur ^= 1;
     }
     ctx->launches = launches;

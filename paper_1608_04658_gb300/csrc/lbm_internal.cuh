@@ -80,7 +80,6 @@ struct Lattice {
     int plane[27];      // i * N: offset of population plane i (27 N < 2^31)
     int face[6];
     int gamma_mode;
-    int pipelined;      // 1: warp-specialised bulk kernel with bulk-copied rows
     double beta;
     double inv_beta;
     double rho0;
@@ -130,7 +129,6 @@ struct Scratch {
 // launchers ------------------------------------------------------------------
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s);
-bool pipelined_eligible(int storage, const Lattice &L);
 cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
                         const double *u, const double *xi, double amp, cudaStream_t s);
 cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,

@@ -29,12 +29,11 @@ def oracle_body(geom):
 
 
 def run_pair(shape, nu, storage, fields, steps, faces=(0,) * 6, geom=None, u_face=(0.0, 0.0, 0.0),
-             gamma_mode=0, options=0):
+             gamma_mode=0):
     """fields = (rho, u, xi, amp).  Returns (gpu Lattice, oracle.Oracle)."""
     import paper_1608_04658_gb300 as lbm
     rho, u, xi, amp = fields
-    lat = lbm.Lattice(shape, nu, storage=storage, faces=faces, u_face=u_face, gamma_mode=gamma_mode,
-                      options=options)
+    lat = lbm.Lattice(shape, nu, storage=storage, faces=faces, u_face=u_face, gamma_mode=gamma_mode)
     if geom is not None:
         lat.set_geometry(geom)
     lat.init_state(rho, u, xi, amp)

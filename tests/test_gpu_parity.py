@@ -25,16 +25,14 @@ def _built():
 
 
 @pytest.mark.parametrize("storage", STORAGES)
-@pytest.mark.parametrize("shape,options", [((150, 6, 5), 0), ((152, 6, 5), 0), ((24, 20, 18), 0),
-                                           ((152, 6, 5), 1), ((24, 20, 18), 1)])
-def test_periodic_random_state(storage, shape, options):
-    """Rough random fields on periodic boxes.  nx = 150 FP32 rows are not 16-byte
-    multiples and take the per-thread-load bulk kernel; nx = 152 (a 128-node
-    segment plus a ragged 24-node one) and the non-power-of-two 24x20x18 box
-    take the pipelined kernel; options = 1 forces the per-thread-load kernel."""
+@pytest.mark.parametrize("shape", [(150, 6, 5), (24, 20, 17), (1, 64, 1), (3, 3, 3)])
+def test_periodic_random_state(storage, shape):
+    """Rough random fields on periodic boxes: 150 = 128 + 22 nodes per row (two
+    x-blocks with a ragged tail), a non-power-of-two box, a one-node-wide
+    column (every pull wraps) and the smallest cube."""
     fields = random_fields(shape, 1)
     for steps in (1, 10):
-        lat, orc = run_pair(shape, 0.01, storage, fields, steps, options=options)
+        lat, orc = run_pair(shape, 0.01, storage, fields, steps)
         err = rel_err(lat.populations(), orc.get_f())
         assert err <= TOL[storage], (storage, steps, err)
 
@@ -69,14 +67,13 @@ def test_taylor_green_storage_forms(storage):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
-@pytest.mark.parametrize("options", [0, 1])
-def test_box_faces(storage, options):
+def test_box_faces(storage):
     """Equilibrium inflow at x-, outflow at x+, walls at y+-, periodic z; and
     walls on x with equilibrium y faces and outflow z faces."""
     shape = (24, 12, 10)
     for faces in [(2, 3, 1, 1, 0, 0), (1, 1, 2, 2, 3, 3)]:
         lat, orc = run_pair(shape, 0.02, storage, random_fields(shape, 3), 10, faces=faces,
-                            u_face=(0.04, 0.0, 0.01), options=options)
+                            u_face=(0.04, 0.0, 0.01))
         assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage], faces
 
 
