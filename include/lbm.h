@@ -193,6 +193,29 @@ LBM_API int64_t lbm_kernel_launches(const lbm_ctx *ctx);
 LBM_API lbm_status lbm_profile_begin(lbm_ctx *ctx, int max_launches);
 LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *launches);
 
+/* Global sums without a context and without device allocation.  The paper
+ * has no counterpart to this entry point; it exists for callers that cannot
+ * call cudaMalloc: applications that hand all device memory to their own
+ * pool allocator, and monitoring code that must not enter the CUDA allocator
+ * (which takes a process-wide lock and may synchronise the device) while a
+ * time-stepping loop runs.
+ *   p      lattice description (nx, ny, nz, storage, rho0; other fields unused)
+ *   f      device populations, 27 * N elements of p->storage in the shifted
+ *          layout of lbm_create
+ *   flags  device node marks (N bytes) or NULL; nodes marked solid are skipped
+ *   out    device output, 5 doubles: mass, momentum x/y/z, kinetic energy
+ *   stream cudaStream_t to enqueue on (NULL: the legacy default stream)
+ * Same sums as lbm_totals (same summands, another addition order), written
+ * asynchronously to out.  The work space is a fixed array inside the library
+ * (160 KB on every GPU that loads it, held until the process exits), so
+ * lattices of more than 67,108,864 nodes are rejected with LBM_ERR_ARG.  The
+ * first call on a device looks up that array's device address; make it before
+ * any stream capture.  All calls share the array: calls ordered on one stream
+ * are safe, calls whose kernels overlap on the GPU race.  No error message is
+ * kept (there is no context); the status says what failed. */
+LBM_API lbm_status lbm_totals_noalloc(const lbm_params *p, const void *f, const uint8_t *flags,
+                                      double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,59 @@
+"""lbm_totals_noalloc: the global sums of lbm_totals for callers that cannot
+call cudaMalloc (an application whose device memory all belongs to its own
+pool allocator, or monitoring code that must stay out of the CUDA allocator
+while a time-stepping loop runs).  It needs no context and allocates nothing:
+its work space is a fixed array inside the library.
+
+This file is named to be collected last, so that a run stopping at its first
+failure has already run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _entry():
+    import paper_1608_04658_gb300 as lbm
+    fn = lbm.lib().lbm_totals_noalloc
+    fn.argtypes = [C.POINTER(lbm.Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int
+    return lbm, fn
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_noalloc_totals_match_the_context_totals(storage):
+    """Two calls in a row (the shared work space keeps the previous call's
+    partials) each equal lbm_totals on the same state, up to the addition
+    order of FP64 sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm, fn = _entry()
+    shape = (40, 36, 52)
+    rho, u, xi = synth.parity_fields(shape, 9)
+    lat = lbm.Lattice(shape, 0.03, storage=storage, faces=(1, 1, 1, 1, 0, 0))
+    lat.set_geometry(lbm.sphere((19.3, 17.6, 25.2), 6.1, U=(0.0, 0.0, -0.02), free=True, g=(0.0, 0.0, -1e-4)))
+    lat.init_state(rho, 0.3 * u, xi, 1e-3)
+    out = torch.zeros(5, dtype=torch.float64, device=lat.device)
+    for _ in range(2):
+        lat.step(3)
+        ref = lat.totals()
+        st = fn(C.byref(lat.params), C.c_void_p(lat.f.data_ptr()), C.c_void_p(lat.flags.data_ptr()),
+                C.c_void_p(out.data_ptr()), C.c_void_p(lat.stream.cuda_stream))
+        assert st == 0
+        lat.stream.synchronize()
+        got = out.cpu().numpy()
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * ref[0])
+
+
+def test_noalloc_rejects_lattices_beyond_its_work_space():
+    lbm, fn = _entry()
+    p = lbm.make_params((512, 512, 260), 0.1)  # 68,157,440 nodes > 67,108,864
+    dummy = C.c_void_p(256)
+    assert fn(C.byref(p), dummy, None, dummy, None) == 1  # LBM_ERR_ARG
+    p = lbm.make_params((40, 36, 52), 0.1)
+    assert fn(C.byref(p), None, None, dummy, None) == 1
