@@ -83,7 +83,7 @@ typedef struct {
     double u_face[3];     /* velocity of EQ faces */
 } lbm_params;
 
-typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2 } lbm_body_kind;
+typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2, LBM_BODY_AIRFOIL = 3 } lbm_body_kind;
 
 /* Immersed body.  A node is solid when its centre lies inside the body
  * (strictly).  On periodic axes the sphere is taken at its nearest image.
@@ -91,7 +91,17 @@ typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2 } lbm
  *     the centre follows Newton's equations (Sec. 4.1) by explicit Euler:
  *     X += U, then U += F/mass + (1 - 1/rho_ratio) g, with F the momentum-
  *     exchange force of the previous step.
- *   PLANES: solid where y < y_lo or y > y_hi; walls move with U_lo / U_hi. */
+ *   PLANES: solid where y < y_lo or y > y_hi; walls move with U_lo / U_hi.
+ *   AIRFOIL: extruded along z, leading edge at (X[0], X[1]) at zero plunge.
+ *     In the chord frame xi = (dx ca - dy sa)/chord, eta = (dx sa + dy ca)/chord
+ *     (dx, dy from the leading edge, (ca, sa) the cosine and sine of the nose-up
+ *     angle of attack) a node is solid when 0 <= xi <= 1 and
+ *     |eta - y_c(xi)| < t(xi): y_c the four-digit camber line of maximum
+ *     camber_m at chord position camber_p, t(xi) = thick[0] sqrt(xi) + thick[1] xi
+ *     + ... + thick[4] xi^4.  Prescribed plunge (Sec. 4.2): the leading edge is at
+ *     y = X[1] + h_amp sin(h_omega t) at step t (t0 at lbm_set_geometry); the
+ *     wall moves with the plunge velocity.  Link fractions are found by 50
+ *     bisections of the link. */
 typedef struct {
     int32_t kind;         /* lbm_body_kind */
     int32_t free_motion;  /* 1: integrate the sphere's translation */
@@ -103,6 +113,7 @@ typedef struct {
     double mass;          /* m_s (rho_s * pi D^3 / 6 for the analytic volume) */
     double rho_ratio;     /* rho_s / rho_f */
     double g[3];          /* gravity */
+    double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], t0;  /* AIRFOIL */
 } lbm_geometry;
 
 /* Body state on the device, read back by lbm_get_body. */
@@ -115,6 +126,8 @@ typedef struct {
     int32_t n_uncovered;  /* nodes refilled in the last step */
     int32_t n_links;      /* missing populations of the last step */
     int32_t status;       /* device status bits (1: unstable node, 2: band overflow, 4: timeout) */
+    int32_t reserved;
+    double t;             /* time of the current pose (prescribed motion), steps */
 } lbm_body_state;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -176,6 +189,15 @@ LBM_API lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out);
 
 /* Clears the force/torque sums used for averages (asynchronous). */
 LBM_API lbm_status lbm_reset_average(lbm_ctx *ctx);
+
+/* Checkpoint of the current state: a header (lattice size, storage, body kind),
+ * the stored populations in their storage type, the node marks and the body
+ * state, written to the file at path.  lbm_load reads such a file into a
+ * context created with the same lattice size and storage and given the same
+ * body with lbm_set_geometry; stepping on from it continues bit for bit.
+ * Both synchronise.  LBM_ERR_ARG for a mismatching or unreadable file. */
+LBM_API lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+LBM_API lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Mass, momentum (3) and kinetic energy summed over fluid nodes in double,
  * written to host out[5].  Synchronises. */

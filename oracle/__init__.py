@@ -35,7 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
-BODY_NONE, BODY_SPHERE, BODY_PLANES = 0, 1, 2
+BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL = 0, 1, 2, 3
 MODE_ANALYTIC, MODE_EXACT, MODE_LBGK = 0, 1, 2
 
 
@@ -66,7 +66,11 @@ class Body(C.Structure):
                 ("y_lo", C.c_double), ("y_hi", C.c_double),
                 ("U_lo", C.c_double * 3), ("U_hi", C.c_double * 3),
                 ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3),
-                ("F", C.c_double * 3), ("M", C.c_double * 3)]
+                ("F", C.c_double * 3), ("M", C.c_double * 3),
+                ("chord", C.c_double), ("ca", C.c_double), ("sa", C.c_double),
+                ("h_amp", C.c_double), ("h_omega", C.c_double),
+                ("camber_m", C.c_double), ("camber_p", C.c_double), ("thick", C.c_double * 5),
+                ("y_base", C.c_double), ("t", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -279,6 +283,25 @@ def sphere_body(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0,
     b.rho_ratio = float(rho_ratio)
     # m_s = rho_s * pi D^3 / 6 with rho_f = 1 (analytic volume)
     b.mass = float(mass) if mass is not None else float(rho_ratio) * np.pi * (2 * R) ** 3 / 6.0
+    return b
+
+
+def airfoil_body(le, chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick, t0=0.0) -> Body:
+    """Airfoil extruded along z with its leading edge at le (x, y) at zero
+    plunge; the pose at time t0 is set here."""
+    import math
+    b = Body()
+    b.kind = BODY_AIRFOIL
+    b.chord, b.ca, b.sa = float(chord), float(ca), float(sa)
+    b.h_amp, b.h_omega = float(h_amp), float(h_omega)
+    b.camber_m, b.camber_p = float(camber_m), float(camber_p)
+    for k in range(5):
+        b.thick[k] = float(thick[k])
+    b.y_base = float(le[1])
+    b.t = float(t0)
+    b.X[0] = float(le[0])
+    b.X[1] = b.y_base + b.h_amp * math.sin(b.h_omega * b.t)
+    b.U[1] = b.h_amp * b.h_omega * math.cos(b.h_omega * b.t)
     return b
 
 

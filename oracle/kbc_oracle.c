@@ -252,7 +252,7 @@ static void pressure_tensor(double rho, const double *u, double dudx[3][3], doub
 
 /* ----------------------------------------------------------------- lattice state */
 enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_EQ = 2, FACE_OUTFLOW = 3 };
-enum { BODY_NONE = 0, BODY_SPHERE = 1, BODY_PLANES = 2 };
+enum { BODY_NONE = 0, BODY_SPHERE = 1, BODY_PLANES = 2, BODY_AIRFOIL = 3 };
 
 typedef struct {
     int nx, ny, nz;
@@ -276,6 +276,15 @@ typedef struct {
     double rho_ratio;  /* rho_s / rho_f */
     double g[3];       /* gravity */
     double F[3], M[3]; /* hydrodynamic force and torque of the last step */
+    /* airfoil extruded along z, leading edge at X (current, plunging in y) */
+    double chord;      /* chord length c */
+    double ca, sa;     /* cos and sin of the angle of attack (nose up) */
+    double h_amp;      /* plunge amplitude (lattice units) */
+    double h_omega;    /* plunge angular frequency (rad per step) */
+    double camber_m, camber_p; /* camber line: maximum and its chord position */
+    double thick[5];   /* half thickness a0 sqrt(x) + a1 x + a2 x^2 + a3 x^3 + a4 x^4 */
+    double y_base;     /* leading-edge y at zero plunge */
+    double t;          /* time of the current pose (steps) */
 } orc_body;
 
 typedef struct {
@@ -314,9 +323,36 @@ static void sphere_offset(const orc_ctx *c, double x, double y, double z, double
     }
 }
 
+/* Airfoil (Sec. 4.2 plunging airfoil, analytic cambered stand-in): in the
+ * chord frame (xi along the chord from the leading edge, eta normal to it, both
+ * in chords) a point is inside when 0 <= xi <= 1 and |eta - y_c(xi)| < t(xi),
+ * y_c the camber line of the four-digit form and t the half thickness. */
+static double camber(const orc_body *b, double xi)
+{
+    double m = b->camber_m, p = b->camber_p;
+    if (xi < p) return m / (p * p) * (2.0 * p * xi - xi * xi);
+    return m / ((1.0 - p) * (1.0 - p)) * ((1.0 - 2.0 * p) + 2.0 * p * xi - xi * xi);
+}
+
+static double half_thickness(const orc_body *b, double xi)
+{
+    const double *a = b->thick;
+    return a[0] * sqrt(xi) + xi * (a[1] + xi * (a[2] + xi * (a[3] + xi * a[4])));
+}
+
+static int inside_airfoil(const orc_body *b, double x, double y)
+{
+    double dx = x - b->X[0], dy = y - b->X[1];
+    double xi = (dx * b->ca - dy * b->sa) / b->chord;
+    double eta = (dx * b->sa + dy * b->ca) / b->chord;
+    if (xi < 0.0 || xi > 1.0) return 0;
+    return fabs(eta - camber(b, xi)) < half_thickness(b, xi);
+}
+
 static int inside_body(const orc_ctx *c, double x, double y, double z)
 {
     const orc_body *b = &c->b;
+    if (b->kind == BODY_AIRFOIL) return inside_airfoil(b, x, y);
     if (b->kind == BODY_SPHERE) {
         double d[3];
         sphere_offset(c, x, y, z, d);
@@ -344,6 +380,17 @@ static double link_q(const orc_ctx *c, double x, double y, double z, const int *
     if (b->kind == BODY_PLANES) {
         if (y - ci[1] < b->y_lo) return (y - b->y_lo) / ci[1];
         return (b->y_hi - y) / (-ci[1]);
+    }
+    if (b->kind == BODY_AIRFOIL) {
+        /* reading: the crossing of the link x_b - s c (s in [0,1]) by bisection
+         * on the inside test, 50 halvings */
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 50; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (inside_airfoil(b, x - mid * ci[0], y - mid * ci[1])) hi = mid;
+            else lo = mid;
+        }
+        return 0.5 * (lo + hi);
     }
     return 0.5;
 }
@@ -533,8 +580,11 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
             double dF[3];
             for (int a = 0; a < 3; ++a)
                 dF[a] = (-ci[a] - uw[i][a]) * fout - (ci[a] - uw[i][a]) * Fi[i];
+            /* torque arm from the body's reference point: sphere centre,
+             * airfoil leading edge at z = 0, the lattice origin otherwise */
             double r[3];
             if (c->b.kind == BODY_SPHERE) sphere_offset(c, x, y, z, r);
+            else if (c->b.kind == BODY_AIRFOIL) { r[0] = x - c->b.X[0]; r[1] = y - c->b.X[1]; r[2] = z; }
             else { r[0] = x; r[1] = y; r[2] = z; }
             for (int a = 0; a < 3; ++a) r[a] -= q[i] * ci[a];
             F[0] += dF[0]; F[1] += dF[1]; F[2] += dF[2];
@@ -605,6 +655,13 @@ void orc_init_state(orc_ctx *c, const double *rho, const double *u, const double
 static void body_update(orc_ctx *c)
 {
     orc_body *b = &c->b;
+    if (b->kind == BODY_AIRFOIL) {
+        /* prescribed plunge (Sec. 4.2): y_le(t) = y_base + A sin(w t) */
+        b->t = b->t + 1.0;
+        b->X[1] = b->y_base + b->h_amp * sin(b->h_omega * b->t);
+        b->U[1] = b->h_amp * b->h_omega * cos(b->h_omega * b->t);
+        return;
+    }
     if (!b->free_motion) return;
     const double inv_m = 1.0 / b->mass;
     const double buoy = 1.0 - 1.0 / b->rho_ratio;

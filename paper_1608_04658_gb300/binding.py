@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OO
                 7: "LBM_ERR_UNSUPPORTED"}
 STORAGES = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
-BODY_NONE, BODY_SPHERE, BODY_PLANES = 0, 1, 2
+BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL = 0, 1, 2, 3
 GAMMA_ANALYTIC, GAMMA_LBGK = 0, 2
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
 
@@ -45,14 +45,18 @@ class Geometry(C.Structure):
                 ("X", C.c_double * 3), ("U", C.c_double * 3), ("R", C.c_double),
                 ("y_lo", C.c_double), ("y_hi", C.c_double),
                 ("U_lo", C.c_double * 3), ("U_hi", C.c_double * 3),
-                ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3)]
+                ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3),
+                ("chord", C.c_double), ("ca", C.c_double), ("sa", C.c_double), ("h_amp", C.c_double),
+                ("h_omega", C.c_double), ("camber_m", C.c_double), ("camber_p", C.c_double),
+                ("thick", C.c_double * 5), ("t0", C.c_double)]
 
 
 class BodyState(C.Structure):
     _fields_ = [("X", C.c_double * 3), ("U", C.c_double * 3), ("F", C.c_double * 3),
                 ("M", C.c_double * 3), ("F_sum", C.c_double * 3), ("M_sum", C.c_double * 3),
                 ("n_sum", C.c_int64), ("n_boundary", C.c_int32), ("n_uncovered", C.c_int32),
-                ("n_links", C.c_int32), ("status", C.c_int32)]
+                ("n_links", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("t", C.c_double)]
 
 
 _lib = None
@@ -102,6 +106,10 @@ def lib():
         L.lbm_totals.restype = C.c_int
         L.lbm_kernel_launches.argtypes = [vp]
         L.lbm_kernel_launches.restype = C.c_int64
+        L.lbm_save.argtypes = [vp, C.c_char_p]
+        L.lbm_save.restype = C.c_int
+        L.lbm_load.argtypes = [vp, C.c_char_p]
+        L.lbm_load.restype = C.c_int
         L.lbm_profile_begin.argtypes = [vp, C.c_int]
         L.lbm_profile_begin.restype = C.c_int
         L.lbm_profile_end.argtypes = [vp, _D, C.POINTER(C.c_int64)]
@@ -144,6 +152,20 @@ def sphere(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0, 0.0)
     G.R = float(R)
     G.rho_ratio = float(rho_ratio)
     G.mass = float(mass) if mass is not None else float(rho_ratio) * np.pi * (2 * R) ** 3 / 6.0
+    return G
+
+
+def airfoil(le, chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick, t0=0.0) -> Geometry:
+    """Airfoil extruded along z, leading edge at le = (x, y) at zero plunge."""
+    G = Geometry()
+    G.kind = BODY_AIRFOIL
+    G.X[0], G.X[1] = float(le[0]), float(le[1])
+    G.chord, G.ca, G.sa = float(chord), float(ca), float(sa)
+    G.h_amp, G.h_omega = float(h_amp), float(h_omega)
+    G.camber_m, G.camber_p = float(camber_m), float(camber_p)
+    for k in range(5):
+        G.thick[k] = float(thick[k])
+    G.t0 = float(t0)
     return G
 
 
@@ -266,7 +288,7 @@ class Lattice:
         return dict(X=np.array(b.X), U=np.array(b.U), F=np.array(b.F), M=np.array(b.M),
                     F_sum=np.array(b.F_sum), M_sum=np.array(b.M_sum), n_sum=b.n_sum,
                     n_boundary=b.n_boundary, n_uncovered=b.n_uncovered, n_links=b.n_links,
-                    status=b.status)
+                    status=b.status, t=b.t)
 
     def forces(self, averaged: bool = False):
         F = np.zeros(3)
@@ -274,6 +296,14 @@ class Lattice:
         self._check(lib().lbm_body_forces(self._ctx, F.ctypes.data_as(_D), M.ctypes.data_as(_D),
                                           1 if averaged else 0))
         return F, M
+
+    def save(self, path: str):
+        """Checkpoint the current state (populations, node marks, body) to path."""
+        self._check(lib().lbm_save(self._ctx, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Restore a checkpoint written by save() for the same lattice and body."""
+        self._check(lib().lbm_load(self._ctx, os.fsencode(path)))
 
     def reset_average(self):
         self._check(lib().lbm_reset_average(self._ctx))

@@ -2,6 +2,7 @@
 // management and the per-step launch sequence.  Host code only enqueues
 // kernels; the state, the body and its force never leave the device during
 // lbm_step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -212,7 +213,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (!g) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: null geometry");
-    if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_PLANES)
+    if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_AIRFOIL)
         return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: unknown body kind");
     const Lattice &L = ctx->L;
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
@@ -243,6 +244,41 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
             if (G.periodic[a] && !(g->X[a] >= 0.0 && g->X[a] < (double)n[a]))
                 return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: centre outside [0, n) on a periodic axis");
         }
+    } else if (g->kind == LBM_BODY_AIRFOIL) {
+        if (!(g->chord > 0.0) || !(fabs(g->ca * g->ca + g->sa * g->sa - 1.0) < 1e-12))
+            return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: airfoil needs chord > 0 and ca^2 + sa^2 = 1");
+        G.chord = g->chord; G.ca = g->ca; G.sa = g->sa;
+        G.h_amp = g->h_amp; G.h_omega = g->h_omega;
+        G.camber_m = g->camber_m; G.camber_p = g->camber_p;
+        for (int k = 0; k < 5; ++k) G.thick[k] = g->thick[k];
+        G.y_base = g->X[1];
+        // profile box in the lattice frame (relative to the leading edge) from a
+        // dense sample of the outline, widened by one node
+        double bx0 = 0, bx1 = 0, by0 = 0, by1 = 0;
+        for (int k = 0; k <= 4096; ++k) {
+            const double xi = k / 4096.0;
+            const double yc = xi < g->camber_p
+                                  ? g->camber_m / (g->camber_p * g->camber_p) * (2 * g->camber_p * xi - xi * xi)
+                                  : g->camber_m / ((1 - g->camber_p) * (1 - g->camber_p)) *
+                                        ((1 - 2 * g->camber_p) + 2 * g->camber_p * xi - xi * xi);
+            const double t = g->thick[0] * std::sqrt(xi) +
+                             xi * (g->thick[1] + xi * (g->thick[2] + xi * (g->thick[3] + xi * g->thick[4])));
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                const double eta = yc + sgn * t;
+                const double dx = g->chord * (xi * g->ca + eta * g->sa);
+                const double dy = g->chord * (-xi * g->sa + eta * g->ca);
+                bx0 = std::min(bx0, dx); bx1 = std::max(bx1, dx);
+                by0 = std::min(by0, dy); by1 = std::max(by1, dy);
+            }
+        }
+        G.box[0] = bx0 - 1; G.box[1] = bx1 + 1; G.box[2] = by0 - 1; G.box[3] = by1 + 1;
+        // band extent per axis: the profile box plus one step of plunge
+        const double span[2] = {G.box[1] - G.box[0], G.box[3] - G.box[2] + 1.0};
+        for (int a = 0; a < 2; ++a) {
+            const int c = (int)std::ceil(span[a]) + 9;
+            G.cap[a] = c < n[a] ? c : n[a];
+        }
+        G.cap[2] = n[2];
     } else {
         for (int a = 0; a < 3; ++a) G.cap[a] = n[a];
     }
@@ -266,10 +302,17 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     }
     DevBody hb[2] = {};
     for (int a = 0; a < 3; ++a) { hb[0].X[a] = g->X[a]; hb[0].U[a] = g->U[a]; }
+    if (g->kind == LBM_BODY_AIRFOIL) {
+        hb[0].t = g->t0;
+        hb[0].X[1] = g->X[1] + g->h_amp * std::sin(g->h_omega * g->t0);
+        hb[0].U[0] = 0.0;
+        hb[0].U[1] = g->h_amp * g->h_omega * std::cos(g->h_omega * g->t0);
+        hb[0].U[2] = 0.0;
+    }
     ctx->bcur = 0;
     LBM_CUDA(cudaMemcpyAsync(S.body, hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
     LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
-    if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, g->X, ctx->flags, ctx->stream), "initial marks");
+    if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, hb[0].X, ctx->flags, ctx->stream), "initial marks");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
     return LBM_OK;
 }
@@ -389,6 +432,8 @@ lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
     out->n_uncovered = hb.n_uncovered;
     out->n_links = hb.n_links;
     out->status = hb.status;
+    out->reserved = 0;
+    out->t = hb.t;
     return LBM_OK;
 }
 
@@ -437,6 +482,90 @@ lbm_status lbm_totals(lbm_ctx *ctx, double out[5])
     for (int k = 0; k < 5; ++k) out[k] = 0;
     for (int b = 0; b < ctx->tot_blocks; ++b)
         for (int k = 0; k < 5; ++k) out[k] += h[(size_t)b * 5 + k];
+    return LBM_OK;
+}
+
+namespace {
+struct CheckpointHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, storage, body_kind, reserved;
+    int64_t pop_bytes, flag_bytes, body_bytes;
+};
+
+// device <-> file in chunks through a host buffer
+bool copy_to_file(FILE *fp, const void *dev, size_t bytes, cudaStream_t s)
+{
+    std::vector<char> buf(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t off = 0; off < bytes; off += buf.size()) {
+        const size_t n = std::min(buf.size(), bytes - off);
+        if (cudaMemcpyAsync(buf.data(), (const char *)dev + off, n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess || fwrite(buf.data(), 1, n, fp) != n)
+            return false;
+    }
+    return true;
+}
+
+bool copy_from_file(FILE *fp, void *dev, size_t bytes, cudaStream_t s)
+{
+    std::vector<char> buf(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t off = 0; off < bytes; off += buf.size()) {
+        const size_t n = std::min(buf.size(), bytes - off);
+        if (fread(buf.data(), 1, n, fp) != n ||
+            cudaMemcpyAsync((char *)dev + off, buf.data(), n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!path) return fail(ctx, LBM_ERR_ARG, "lbm_save: null path");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    CheckpointHeader h{};
+    memcpy(h.magic, "LBMKBC01", 8);
+    h.version = 1;
+    h.nx = ctx->L.nx; h.ny = ctx->L.ny; h.nz = ctx->L.nz;
+    h.storage = ctx->storage;
+    h.body_kind = ctx->has_body ? ctx->G.kind : LBM_BODY_NONE;
+    h.pop_bytes = (int64_t)Q * ctx->L.N * (int64_t)ctx->elem;
+    h.flag_bytes = ctx->L.N;
+    h.body_bytes = sizeof(DevBody);
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(ctx, LBM_ERR_ARG, std::string("lbm_save: cannot open ") + path);
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1 &&
+              copy_to_file(fp, ctx->f[ctx->cur], (size_t)h.pop_bytes, ctx->stream) &&
+              copy_to_file(fp, ctx->flags, (size_t)h.flag_bytes, ctx->stream) &&
+              copy_to_file(fp, ctx->S.body + ctx->bcur, sizeof(DevBody), ctx->stream);
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(ctx, LBM_ERR_ARG, std::string("lbm_save: write failed for ") + path);
+}
+
+lbm_status lbm_load(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!path) return fail(ctx, LBM_ERR_ARG, "lbm_load: null path");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(ctx, LBM_ERR_ARG, std::string("lbm_load: cannot open ") + path);
+    CheckpointHeader h{};
+    const bool hdr = fread(&h, sizeof(h), 1, fp) == 1;
+    const int kind = ctx->has_body ? ctx->G.kind : LBM_BODY_NONE;
+    if (!hdr || memcmp(h.magic, "LBMKBC01", 8) != 0 || h.version != 1 || h.nx != ctx->L.nx ||
+        h.ny != ctx->L.ny || h.nz != ctx->L.nz || h.storage != ctx->storage || h.body_kind != kind ||
+        h.pop_bytes != (int64_t)Q * ctx->L.N * (int64_t)ctx->elem || h.flag_bytes != ctx->L.N ||
+        h.body_bytes != (int64_t)sizeof(DevBody)) {
+        fclose(fp);
+        return fail(ctx, LBM_ERR_ARG, std::string("lbm_load: ") + path + " does not match this context");
+    }
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    bool ok = copy_from_file(fp, ctx->f[ctx->cur], (size_t)h.pop_bytes, ctx->stream) &&
+              copy_from_file(fp, ctx->flags, (size_t)h.flag_bytes, ctx->stream) &&
+              copy_from_file(fp, ctx->S.body + ctx->bcur, sizeof(DevBody), ctx->stream);
+    fclose(fp);
+    if (!ok) return fail(ctx, LBM_ERR_ARG, std::string("lbm_load: read failed for ") + path);
+    ctx->initialised = true;
     return LBM_OK;
 }
 

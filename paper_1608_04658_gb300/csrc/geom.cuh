@@ -34,9 +34,36 @@ __device__ __forceinline__ double axis_offset(int p, double X, int n, int period
     return d;
 }
 
+// Airfoil in its chord frame (see lbm_geometry): camber line and half thickness
+__device__ __forceinline__ double airfoil_camber(const GeomParams &G, double xi)
+{
+    const double m = G.camber_m, p = G.camber_p;
+    if (xi < p) return __dmul_rn(__ddiv_rn(m, __dmul_rn(p, p)), __dsub_rn(__dmul_rn(__dmul_rn(2.0, p), xi), __dmul_rn(xi, xi)));
+    const double q = __dsub_rn(1.0, p);
+    return __dmul_rn(__ddiv_rn(m, __dmul_rn(q, q)),
+                     __dsub_rn(__dadd_rn(__dsub_rn(1.0, __dmul_rn(2.0, p)), __dmul_rn(__dmul_rn(2.0, p), xi)), __dmul_rn(xi, xi)));
+}
+
+__device__ __forceinline__ double airfoil_half_thickness(const GeomParams &G, double xi)
+{
+    const double *a = G.thick;
+    const double poly = __dmul_rn(xi, __dadd_rn(a[1], __dmul_rn(xi, __dadd_rn(a[2], __dmul_rn(xi, __dadd_rn(a[3], __dmul_rn(xi, a[4])))))));
+    return __dadd_rn(__dmul_rn(a[0], __dsqrt_rn(xi)), poly);
+}
+
+__device__ __forceinline__ bool inside_airfoil(const GeomParams &G, const double X[3], double x, double y)
+{
+    const double dx = __dsub_rn(x, X[0]), dy = __dsub_rn(y, X[1]);
+    const double xi = __ddiv_rn(__dsub_rn(__dmul_rn(dx, G.ca), __dmul_rn(dy, G.sa)), G.chord);
+    const double eta = __ddiv_rn(__dadd_rn(__dmul_rn(dx, G.sa), __dmul_rn(dy, G.ca)), G.chord);
+    if (xi < 0.0 || xi > 1.0) return false;
+    return fabs(__dsub_rn(eta, airfoil_camber(G, xi))) < airfoil_half_thickness(G, xi);
+}
+
 __device__ __forceinline__ bool inside_body(const GeomParams &G, const Lattice &L, const double X[3],
                                             int x, int y, int z)
 {
+    if (G.kind == LBM_BODY_AIRFOIL) return inside_airfoil(G, X, (double)x, (double)y);
     if (G.kind == LBM_BODY_SPHERE) {
         const double dx = axis_offset(x, X[0], L.nx, G.periodic[0]);
         const double dy = axis_offset(y, X[1], L.ny, G.periodic[1]);
@@ -101,6 +128,21 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
         uw[0] = b->U[0];
         uw[1] = b->U[1];
         uw[2] = b->U[2];
+    } else if (G.kind == LBM_BODY_AIRFOIL) {
+        // crossing of the link x - s c, s in [0, 1], by 50 bisections
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 50; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (inside_airfoil(G, b->X, __dsub_rn((double)x, __dmul_rn(mid, (double)cx)),
+                               __dsub_rn((double)y, __dmul_rn(mid, (double)cy))))
+                hi = mid;
+            else
+                lo = mid;
+        }
+        q = 0.5 * (lo + hi);
+        uw[0] = b->U[0];
+        uw[1] = b->U[1];
+        uw[2] = b->U[2];
     } else {  // planes
         const double yb = (double)y;
         const bool low = (double)(y - cy) < G.y_lo;
@@ -112,10 +154,12 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
     }
 }
 
-// torque arm origin: displacement of (x, y, z) from the body centre
+// torque arm origin: displacement of (x, y, z) from the body reference point
+// (sphere centre; airfoil leading edge at z = 0; the lattice origin otherwise)
 __device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams &G, const DevBody *b,
                                               int a, int p)
 {
+    if (G.kind == LBM_BODY_AIRFOIL) return a < 2 ? __dsub_rn((double)p, b->X[a]) : (double)p;
     if (G.kind != LBM_BODY_SPHERE) return (double)p;
     const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
     return axis_offset(p, b->X[a], n, G.periodic[a]);

@@ -28,9 +28,22 @@ __device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBod
 {
     const int n[3] = {L.nx, L.ny, L.nz};
     overflow = 0;
+    if (G.kind == LBM_BODY_AIRFOIL) {
+        // prescribed plunge (Sec. 4.2): y_le = y_base + A sin(w t)
+        const double t1 = prev->t + 1.0;
+        const double ph = __dmul_rn(G.h_omega, t1);
+        X[0] = prev->X[0];
+        X[1] = __dadd_rn(G.y_base, __dmul_rn(G.h_amp, sin(ph)));
+        X[2] = prev->X[2];
+        U[0] = 0.0;
+        U[1] = __dmul_rn(__dmul_rn(G.h_amp, G.h_omega), cos(ph));
+        U[2] = 0.0;
+    }
     for (int a = 0; a < 3; ++a) {
-        X[a] = prev->X[a];
-        U[a] = prev->U[a];
+        if (G.kind != LBM_BODY_AIRFOIL) {
+            X[a] = prev->X[a];
+            U[a] = prev->U[a];
+        }
         if (G.free_motion && G.kind == LBM_BODY_SPHERE) {
             const double acc = __dadd_rn(__dmul_rn(prev->F[a], G.inv_mass), __dmul_rn(G.buoy, G.g[a]));
             X[a] = __dadd_rn(X[a], U[a]);
@@ -41,7 +54,13 @@ __device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBod
             }
         }
         int l, c;
-        if (G.kind == LBM_BODY_SPHERE) {
+        if (G.kind == LBM_BODY_AIRFOIL && a < 2) {
+            // profile box relative to the leading edge, at both poses
+            const double bmin = G.box[2 * a], bmax = G.box[2 * a + 1];
+            const double mn = fmin(prev->X[a], X[a]) + bmin, mx = fmax(prev->X[a], X[a]) + bmax;
+            l = (int)floor(mn) - BAND_MARGIN;
+            c = (int)floor(mx) + BAND_MARGIN + 1 - l + 1;
+        } else if (G.kind == LBM_BODY_SPHERE) {
             // box of the sphere at both positions; on a periodic axis the old
             // centre is taken at the image nearest the new one
             double Xo = prev->X[a];
@@ -110,6 +129,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) mark_kernel(const Lattice L, con
                 cur->band_n[a] = cnt[a];
             }
             cur->n_sum = prev->n_sum;
+            cur->t = prev->t + 1.0;
             cur->n_boundary = 0;
             cur->n_uncovered = 0;
             cur->n_links = 0;

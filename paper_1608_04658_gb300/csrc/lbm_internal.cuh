@@ -96,6 +96,9 @@ struct GeomParams {
     double inv_mass;     // 1 / m_s
     double buoy;         // 1 - rho_f / rho_s
     double g[3];
+    // airfoil
+    double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], y_base;
+    double box[4];       // profile box relative to the leading edge: dx min/max, dy min/max
     int periodic[3];
     int cap[3];          // band capacity per axis
     int cap_boundary;    // slots in the boundary list
@@ -112,6 +115,7 @@ struct DevBody {
     int band_lo[3], band_n[3];
     int n_boundary, n_uncovered, n_links;
     int status;
+    double t;            // time of the current pose (prescribed motion)
 };
 
 // scratch owned by the library for the boundary path

@@ -106,3 +106,34 @@ def sedimenting_sphere(shape=(128, 128, 256), D: float = 16.0, rho_ratio: float 
     X = (nx / 2 - 0.5 + 0.123, ny / 2 - 0.5 + 0.0567, 0.75 * nz + 0.311)
     return dict(name=f"sedimenting_sphere_{nx}x{ny}x{nz}_D{D:g}", shape=shape, nu=nu, D=D,
                 X=X, rho_ratio=rho_ratio, g=(0.0, 0.0, -g), faces=(1, 1, 1, 1, 0, 0))
+
+
+def airfoil_thickness(t_max: float = 0.0425, x_max: float = 0.25, a0: float = 0.126,
+                      te_slope: float = -0.10):
+    """Coefficients (a0..a4) of the half thickness t(x) = a0 sqrt(x) + a1 x +
+    a2 x^2 + a3 x^3 + a4 x^4 with t(x_max) = t_max, t'(x_max) = 0, t(1) = 0,
+    t'(1) = te_slope and a fixed leading-edge term a0 (8.5% thick at 25% chord
+    by default)."""
+    A = np.array([[x_max, x_max ** 2, x_max ** 3, x_max ** 4],
+                  [1.0, 2 * x_max, 3 * x_max ** 2, 4 * x_max ** 3],
+                  [1.0, 1.0, 1.0, 1.0],
+                  [1.0, 2.0, 3.0, 4.0]])
+    rhs = np.array([t_max - a0 * math.sqrt(x_max), -0.5 * a0 / math.sqrt(x_max), -a0, te_slope - 0.5 * a0])
+    a = np.linalg.solve(A, rhs)
+    return (a0, *[float(v) for v in a])
+
+
+def plunging_airfoil(shape=(1024, 512, 64), chord: float = 128.0, u_inf: float = 0.05,
+                     re: float = 40000.0, k: float = 3.93, h0: float = 0.05, alpha_deg: float = 4.0,
+                     le=(256.37, 256.29)):
+    """Plunging cambered airfoil: chord 128, extruded over a periodic span,
+    equilibrium inflow at x-, zero-gradient outflow at x+, equilibrium
+    far field on the y faces; plunge h(t) = h0 c sin(2 pi f t) along y with
+    reduced frequency k = pi f c / u_inf; nu = u_inf c / Re."""
+    nx, ny, nz = shape
+    f = k * u_inf / (math.pi * chord)
+    a = math.radians(alpha_deg)
+    return dict(name=f"plunging_airfoil_{nx}x{ny}x{nz}_c{chord:g}", shape=shape, nu=u_inf * chord / re,
+                chord=chord, ca=math.cos(a), sa=math.sin(a), h_amp=h0 * chord, h_omega=2 * math.pi * f,
+                camber_m=0.015, camber_p=0.35, thick=airfoil_thickness(), le=le,
+                faces=(2, 3, 2, 2, 0, 0), u_face=(u_inf, 0.0, 0.0))

@@ -25,6 +25,9 @@ def oracle_body(geom):
     if geom.kind == lbm.BODY_SPHERE:
         return oracle.sphere_body(list(geom.X), geom.R, U=list(geom.U), free=bool(geom.free_motion),
                                   rho_ratio=geom.rho_ratio, g=list(geom.g), mass=geom.mass)
+    if geom.kind == lbm.BODY_AIRFOIL:
+        return oracle.airfoil_body((geom.X[0], geom.X[1]), geom.chord, geom.ca, geom.sa, geom.h_amp,
+                                   geom.h_omega, geom.camber_m, geom.camber_p, list(geom.thick), geom.t0)
     return oracle.planes_body(geom.y_lo, geom.y_hi, U_lo=list(geom.U_lo), U_hi=list(geom.U_hi))
 
 

@@ -184,3 +184,61 @@ def test_sedimenting_sphere_full_size_sampled(storage):
     # one step from the same stored input: FP32 arithmetic and one rounding to storage
     tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
     assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_checkpoint_resume_is_bitwise(storage, tmp_path):
+    """20 steps straight equal 10 steps + save + load into a fresh context +
+    10 steps, bit for bit (populations and body state)."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (32, 28, 40)
+    faces = (1, 1, 1, 1, 0, 0)
+    rho, u, xi = synth.parity_fields(shape, 12)
+    geom = lbm.sphere((15.4, 13.7, 20.3), 5.2, U=(0.01, 0.0, -0.06), free=True, g=(0.0, 0.0, -2e-4))
+
+    def fresh():
+        lat = lbm.Lattice(shape, 0.03, storage=storage, faces=faces)
+        lat.set_geometry(geom)
+        return lat
+
+    a = fresh()
+    a.init_state(rho, 0.2 * u, xi, 1e-3)
+    a.step(20)
+    b = fresh()
+    b.init_state(rho, 0.2 * u, xi, 1e-3)
+    b.step(10)
+    path = str(tmp_path / "state.lbm")
+    b.save(path)
+    c = fresh()
+    c.load(path)
+    c.step(10)
+    fa, fc = a.populations(), c.populations()
+    fluid = (a.flags.cpu().numpy() & 1) == 0
+    assert np.array_equal(fa[:, fluid], fc[:, fluid])
+    ba, bc = a.body(), c.body()
+    for k in ("X", "U", "F", "M"):
+        assert np.array_equal(ba[k], bc[k]), k
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_plunging_airfoil(storage):
+    """Plunging cambered airfoil (chord 32, 4 degrees, amplitude 1.6, a fast
+    plunge so nodes get uncovered) with equilibrium inflow, outflow and far
+    field: airfoil geometry by bisection, prescribed kinematics, refill."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.plunging_airfoil()
+    shape = (96, 40, 6)
+    rho, u, xi = synth.parity_fields(shape, 13)
+    fields = (rho, 0.2 * u + np.array([0.05, 0.0, 0.0]), xi, 1e-3)
+    geom = lbm.airfoil((24.37, 20.29), 32.0, wl["ca"], wl["sa"], 1.6, 0.05, wl["camber_m"], wl["camber_p"],
+                       wl["thick"], t0=3.0)
+    lat, orc = run_pair(shape, 0.02, storage, fields, 10, faces=wl["faces"], geom=geom, u_face=wl["u_face"])
+    mask = fluid_mask(lat, orc)
+    assert orc.counters()["refill"] > 0
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+    F, M = lat.forces()
+    Fo, Mo = np.array(orc.body.F), np.array(orc.body.M)
+    ftol = {"fp64": 1e-10, "fp32": 1e-4, "fp16": 3e-2, "bf16": 3e-2}[storage]
+    assert np.abs(F - Fo).max() <= ftol * np.abs(Fo).max()
+    assert np.abs(M - Mo).max() <= ftol * np.abs(Mo).max()
+    assert lat.body()["X"][1] == pytest.approx(orc.body.X[1], abs=1e-13)

@@ -230,3 +230,48 @@ def test_sphere_euler_update(orc):
     b2 = o.body
     assert np.allclose(b2.X, X0 + U0 + U1, rtol=0, atol=1e-14)
     assert np.allclose(b2.U, U1 + F1 / m + (1 - 1 / 1.5) * g, rtol=0, atol=1e-16)
+
+
+def _airfoil(orc, chord, le, t0=0.0, h_amp=0.0, h_omega=0.0):
+    wl = synth.plunging_airfoil()
+    return orc.airfoil_body(le, chord, wl["ca"], wl["sa"], h_amp, h_omega, wl["camber_m"], wl["camber_p"],
+                            wl["thick"], t0)
+
+
+def test_airfoil_profile_synth_has_the_stated_thickness():
+    """Analytic stand-in for the Sec. 4.2 airfoil: maximum half thickness
+    0.0425 (8.5% of the chord) at 25% chord, closed trailing edge."""
+    a = synth.airfoil_thickness()
+    x = np.linspace(0, 1, 200001)
+    t = a[0] * np.sqrt(x) + a[1] * x + a[2] * x ** 2 + a[3] * x ** 3 + a[4] * x ** 4
+    assert t.max() == pytest.approx(0.0425, rel=1e-9)
+    assert x[t.argmax()] == pytest.approx(0.25, abs=1e-4)
+    assert abs(t[-1]) < 1e-15 and (t[1:-1] > 0).all()
+
+
+def test_airfoil_solid_area_matches_profile_area(orc):
+    """Solid nodes of one span slice cover the profile area c^2 int 2t dxi
+    (camber does not change the area) to within the staircase error."""
+    chord = 96.0
+    shape = (128, 48, 1)
+    o = orc.Oracle(shape, nu=0.05, faces=(2, 3, 2, 2, 0, 0), u_face=(0.05, 0, 0),
+                   body=_airfoil(orc, chord, (16.37, 24.29)))
+    a = synth.airfoil_thickness()
+    x = np.linspace(0, 1, 400001)
+    area = chord ** 2 * np.trapezoid(2 * (a[0] * np.sqrt(x) + a[1] * x + a[2] * x ** 2 + a[3] * x ** 3
+                                          + a[4] * x ** 4), x)
+    n = int(o.solid().sum())
+    assert abs(n - area) < 0.03 * area
+
+
+def test_airfoil_plunge_kinematics(orc):
+    """Prescribed plunge (Sec. 4.2): after k steps the leading edge is at
+    y_base + A sin(w (t0 + k)) and moves with A w cos(w (t0 + k))."""
+    A, w, t0 = 3.2, 0.01, 5.0
+    b = _airfoil(orc, 32.0, (10.37, 20.29), t0=t0, h_amp=A, h_omega=w)
+    o = orc.Oracle((64, 40, 2), nu=0.05, faces=(2, 3, 2, 2, 0, 0), u_face=(0.05, 0, 0), body=b)
+    o.init_state(*synth.uniform_fields((64, 40, 2), (0.05, 0, 0)))
+    o.step(3)
+    bb = o.body
+    assert bb.X[1] == pytest.approx(20.29 + A * np.sin(w * (t0 + 3)), abs=1e-14)
+    assert bb.U[1] == pytest.approx(A * w * np.cos(w * (t0 + 3)), abs=1e-15)
