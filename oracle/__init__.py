@@ -35,7 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
-BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL = 0, 1, 2, 3
+BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL, BODY_MESH = 0, 1, 2, 3, 4
 MODE_ANALYTIC, MODE_EXACT, MODE_LBGK = 0, 1, 2
 
 
@@ -70,7 +70,11 @@ class Body(C.Structure):
                 ("chord", C.c_double), ("ca", C.c_double), ("sa", C.c_double),
                 ("h_amp", C.c_double), ("h_omega", C.c_double),
                 ("camber_m", C.c_double), ("camber_p", C.c_double), ("thick", C.c_double * 5),
-                ("y_base", C.c_double), ("t", C.c_double)]
+                ("y_base", C.c_double), ("t", C.c_double),
+                ("mesh_rest", C.POINTER(C.c_double)), ("mesh_tris", C.POINTER(C.c_int)),
+                ("n_vertices", C.c_int), ("n_triangles", C.c_int),
+                ("length", C.c_double), ("wave_amp", C.c_double), ("wave_length", C.c_double),
+                ("wave_period", C.c_double), ("wave_ramp", C.c_int), ("pad2_", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -111,6 +115,9 @@ def lib():
             L.orc_step_sampled.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_long), _D]
             L.orc_step_sampled.restype = C.c_int
             L.orc_totals.argtypes = [C.c_void_p, _D]
+            L.orc_mesh_pose.argtypes = [C.c_void_p, _D, _D]
+            L.orc_mesh_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
+            L.orc_mesh_link.restype = C.c_double
             _lib = L
     return _lib
 
@@ -197,6 +204,8 @@ class Oracle:
             p.u_face[a] = float(u_face[a])
         self.params = p
         b = Body() if body is None else body
+        # the mesh arrays a body points to must outlive the context
+        self._keep = getattr(b, "_arrays", None)
         self._ctx = lib().orc_create(C.byref(p), C.byref(b))
         if not self._ctx:
             raise MemoryError("oracle allocation failed")
@@ -251,7 +260,8 @@ class Oracle:
     def counters(self):
         L = lib()
         return dict(step=L.orc_counter(self._ctx, 0), boundary=L.orc_counter(self._ctx, 1),
-                    links=L.orc_counter(self._ctx, 2), refill=L.orc_counter(self._ctx, 3))
+                    links=L.orc_counter(self._ctx, 2), refill=L.orc_counter(self._ctx, 3),
+                    error=L.orc_counter(self._ctx, 4))
 
     # dynamics ---------------------------------------------------------
     def step(self, n: int = 1):
@@ -264,6 +274,19 @@ class Oracle:
         lib().orc_step_sampled(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_long)),
                                _dp(out))
         return out
+
+    def mesh_pose(self):
+        """(positions, velocities) of the mesh vertices, each (n_vertices, 3)."""
+        n = self.body.n_vertices
+        pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+        lib().orc_mesh_pose(self._ctx, _dp(pos), _dp(vel))
+        return pos, vel
+
+    def mesh_link(self, x: int, y: int, z: int, i: int):
+        """(q, u_w) of the link from node (x, y, z) along -c_i."""
+        uw = np.zeros(3)
+        q = lib().orc_mesh_link(self._ctx, int(x), int(y), int(z), int(i), _dp(uw))
+        return q, uw
 
     def totals(self) -> np.ndarray:
         """[mass, jx, jy, jz, kinetic energy] over fluid nodes."""
@@ -311,4 +334,28 @@ def planes_body(y_lo, y_hi, U_lo=(0.0, 0.0, 0.0), U_hi=(0.0, 0.0, 0.0)) -> Body:
     b.y_lo, b.y_hi = float(y_lo), float(y_hi)
     for a in range(3):
         b.U_lo[a], b.U_hi[a] = float(U_lo[a]), float(U_hi[a])
+    return b
+
+
+def mesh_body(X, rest, tris, length, wave_amp, wave_length, wave_period, ramp=False,
+              U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0) -> Body:
+    """Triangulated swimmer (Sec. 4.3): rest[v] = (s, dy, dz) per vertex, tris
+    (n, 3) vertex indices, head at X, centre line along +x.  The arrays are
+    kept alive by the returned Body."""
+    b = Body()
+    b.kind = BODY_MESH
+    b.free_motion = 1 if free else 0
+    rest = np.ascontiguousarray(rest, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    b._arrays = (rest, tris)
+    b.mesh_rest = rest.ctypes.data_as(C.POINTER(C.c_double))
+    b.mesh_tris = tris.ctypes.data_as(C.POINTER(C.c_int))
+    b.n_vertices, b.n_triangles = len(rest), len(tris)
+    for a in range(3):
+        b.X[a], b.U[a] = float(X[a]), float(U[a])
+    b.length, b.wave_amp = float(length), float(wave_amp)
+    b.wave_length, b.wave_period = float(wave_length), float(wave_period)
+    b.wave_ramp = 1 if ramp else 0
+    b.mass = float(mass)
+    b.t = float(t0)
     return b

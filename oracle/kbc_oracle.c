@@ -19,6 +19,9 @@
  *           target velocity / target density (static + dynamic parts), refill
  *   Sec. 4.1  Newton's equations for the sphere, Euler integration,
  *             Galilean-invariant momentum exchange (Wen et al.)
+ *   Sec. 4.2  plunging airfoil (analytic cambered stand-in, prescribed plunge)
+ *   Sec. 4.3  anguilliform swimmer: triangulated body of elliptic cross
+ *             sections, prescribed midline deformation, free translation
  *
  * Readings of points the paper leaves open are listed at the top of each
  * routine that takes them.  All arithmetic is IEEE double.
@@ -29,6 +32,7 @@
 #include <string.h>
 
 #define Q 27
+#define ORC_PI 3.14159265358979323846
 
 /* ---------------------------------------------------------------- lattice */
 /* D3Q27: c_i in {-1,0,1}^3 with index i = 9(cx+1) + 3(cy+1) + (cz+1), so the
@@ -252,7 +256,7 @@ static void pressure_tensor(double rho, const double *u, double dudx[3][3], doub
 
 /* ----------------------------------------------------------------- lattice state */
 enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_EQ = 2, FACE_OUTFLOW = 3 };
-enum { BODY_NONE = 0, BODY_SPHERE = 1, BODY_PLANES = 2, BODY_AIRFOIL = 3 };
+enum { BODY_NONE = 0, BODY_SPHERE = 1, BODY_PLANES = 2, BODY_AIRFOIL = 3, BODY_MESH = 4 };
 
 typedef struct {
     int nx, ny, nz;
@@ -285,6 +289,17 @@ typedef struct {
     double thick[5];   /* half thickness a0 sqrt(x) + a1 x + a2 x^2 + a3 x^3 + a4 x^4 */
     double y_base;     /* leading-edge y at zero plunge */
     double t;          /* time of the current pose (steps) */
+    /* triangulated swimmer: head at X (X[0] moves with U[0] when free), the
+     * centre line along +x at (X[1], X[2]) displaced by the midline in y */
+    const double *mesh_rest; /* (s, dy, dz) per vertex */
+    const int *mesh_tris;    /* three vertex indices per triangle */
+    int n_vertices, n_triangles;
+    double length;     /* body length L */
+    double wave_amp;   /* midline amplitude factor (0.125 in Sec. 4.3) */
+    double wave_length;/* lambda */
+    double wave_period;/* T (steps) */
+    int wave_ramp;     /* 1: amplitude ramp over the first period */
+    int pad2_;
 } orc_body;
 
 typedef struct {
@@ -297,6 +312,9 @@ typedef struct {
     double feq_face[Q];
     long step;
     long n_links, n_boundary, n_refill;
+    double *vpos, *vvel;  /* mesh vertex positions and velocities at the current pose */
+    double box_lo[3], box_hi[3]; /* bounding box of the mesh vertices */
+    int error;            /* 1: the mesh left the box */
 } orc_ctx;
 
 static long nid(const orc_ctx *c, int x, int y, int z)
@@ -349,9 +367,156 @@ static int inside_airfoil(const orc_body *b, double x, double y)
     return fabs(eta - camber(b, xi)) < half_thickness(b, xi);
 }
 
+
+/* Anguilliform swimmer (Sec. 4.3).  Lateral midline displacement at arc
+ * position s and time t:
+ *   y(s,t) = r(t) a L (s/L + 0.03125)/1.03125 sin(2 pi (s/lambda - t/T)),
+ * with the ramp r(t) = (1 - cos(pi t/T))/2 for 0 <= t <= T, 1 after it, 0
+ * before t = 0 (when enabled; 1 otherwise).  Readings: the cross sections stay
+ * normal to x and s is measured along x from the head (no arc-length
+ * correction); the body translates only along x. */
+static double midline(const orc_body *b, double s, double t)
+{
+    double r = 1.0;
+    if (b->wave_ramp) {
+        if (t < 0.0) r = 0.0;
+        else if (t < b->wave_period) r = 0.5 * (1.0 - cos(ORC_PI * t / b->wave_period));
+    }
+    double A = b->wave_amp * b->length * (s / b->length + 0.03125) / 1.03125;
+    return r * (A * sin(2.0 * ORC_PI * (s / b->wave_length - t / b->wave_period)));
+}
+
+/* Velocity of the body material at arc position s at the current pose:
+ * translation U plus the midline velocity by the central difference
+ * (y(s, t+1) - y(s, t-1)) / 2 (Sec. 4.3: finite differences of the given
+ * deformation). */
+static void body_field_velocity(const orc_body *b, double s, double *v)
+{
+    v[0] = b->U[0];
+    v[1] = b->U[1] + (midline(b, s, b->t + 1.0) - midline(b, s, b->t - 1.0)) / 2.0;
+    v[2] = b->U[2];
+}
+
+/* Vertex positions and velocities of the mesh at the current pose:
+ * x = X0 + s, y = (X1 + y(s,t)) + dy, z = X2 + dz. */
+static void mesh_pose(orc_ctx *c)
+{
+    const orc_body *b = &c->b;
+    for (int a = 0; a < 3; ++a) { c->box_lo[a] = INFINITY; c->box_hi[a] = -INFINITY; }
+    for (int v = 0; v < b->n_vertices; ++v) {
+        const double *r = b->mesh_rest + 3 * v;
+        double *p = c->vpos + 3 * v;
+        p[0] = b->X[0] + r[0];
+        p[1] = (b->X[1] + midline(b, r[0], b->t)) + r[1];
+        p[2] = b->X[2] + r[2];
+        body_field_velocity(b, r[0], c->vvel + 3 * v);
+        for (int a = 0; a < 3; ++a) {
+            if (p[a] < c->box_lo[a]) c->box_lo[a] = p[a];
+            if (p[a] > c->box_hi[a]) c->box_hi[a] = p[a];
+        }
+    }
+    const int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a)
+        if (c->box_lo[a] < 2.0 || c->box_hi[a] > n[a] - 3.0) c->error = 1;
+}
+
+/* Edge value of the (y, z) projection of the directed edge u -> v at (y, z):
+ * the 2-D cross product (P_b - P_a) x (p - P_a), taken with the lower vertex
+ * index as a, so the two triangles sharing an edge get exactly opposite
+ * values; its sign, with zero counted as positive in that lower-index
+ * direction, is returned. */
+static int edge_value(const double *P, int u, int v, double y, double z, double *e)
+{
+    int a = u < v ? u : v, bb = u < v ? v : u;
+    const double *A = P + 3 * a, *B = P + 3 * bb;
+    double val = (B[1] - A[1]) * (z - A[2]) - (B[2] - A[2]) * (y - A[1]);
+    int sg = val >= 0.0 ? 1 : -1;
+    if (u > v) { val = -val; sg = -sg; }
+    *e = val;
+    return sg;
+}
+
+/* A node is inside the closed mesh when the ray from it along +x crosses the
+ * surface an odd number of times.  The ray meets triangle (A, B, C) when the
+ * three edge values of its (y, z) projection share one sign; the crossing is
+ * at x = (e_BC x_A + e_CA x_B + e_AB x_C) / (e_BC + e_CA + e_AB) (barycentric
+ * weights of the projection) and counts when it lies strictly beyond x. */
+static int inside_mesh(const orc_ctx *c, double x, double y, double z)
+{
+    if (x < c->box_lo[0] || x > c->box_hi[0] || y < c->box_lo[1] || y > c->box_hi[1] ||
+        z < c->box_lo[2] || z > c->box_hi[2])
+        return 0;
+    const orc_body *b = &c->b;
+    const double *P = c->vpos;
+    int crossings = 0;
+    for (int k = 0; k < b->n_triangles; ++k) {
+        const int *t = b->mesh_tris + 3 * k;
+        double e0, e1, e2;
+        int s0 = edge_value(P, t[1], t[2], y, z, &e0);
+        int s1 = edge_value(P, t[2], t[0], y, z, &e1);
+        int s2 = edge_value(P, t[0], t[1], y, z, &e2);
+        if (s0 != s1 || s1 != s2) continue;
+        double den = (e0 + e1) + e2;
+        if (den == 0.0) continue;
+        double xc = ((e0 * P[3 * t[0]] + e1 * P[3 * t[1]]) + e2 * P[3 * t[2]]) / den;
+        if (xc > x) crossings++;
+    }
+    return crossings & 1;
+}
+
+static double det3(const double *a, const double *b, const double *d)
+{
+    return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0])
+         + a[2] * (b[0] * d[1] - b[1] * d[0]);
+}
+
+/* Link of boundary node x_b towards the solid node x_b - c: the first point
+ * x_b - s c, s in [0, 1], on any triangle.  Each triangle A + u (B - A) +
+ * v (C - A) is solved for (u, v, s) by Cramer's rule and hit when u, v >= 0,
+ * u + v <= 1.  The wall velocity is the barycentric interpolation of the
+ * vertex velocities at the hit (Sec. 4.3).  Reading: a link that meets no
+ * triangle (only possible through round-off at an edge) takes q = 1/2 and the
+ * body velocity at the link's midpoint. */
+static double mesh_link(const orc_ctx *c, double x, double y, double z, const int *ci, double *uw)
+{
+    const orc_body *b = &c->b;
+    const double *P = c->vpos;
+    const double cv[3] = {ci[0], ci[1], ci[2]};
+    double best = INFINITY;
+    for (int k = 0; k < b->n_triangles; ++k) {
+        const int *t = b->mesh_tris + 3 * k;
+        const double *A = P + 3 * t[0], *B = P + 3 * t[1], *C3 = P + 3 * t[2];
+        double e1[3], e2[3], r[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = B[a] - A[a];
+            e2[a] = C3[a] - A[a];
+        }
+        r[0] = x - A[0]; r[1] = y - A[1]; r[2] = z - A[2];
+        double D = det3(e1, e2, cv);
+        if (D == 0.0) continue;
+        double u = det3(r, e2, cv) / D;
+        double v = det3(e1, r, cv) / D;
+        double s = det3(e1, e2, r) / D;
+        if (u < 0.0 || v < 0.0 || u + v > 1.0 || s < 0.0 || s > 1.0) continue;
+        if (s < best) {
+            best = s;
+            for (int a = 0; a < 3; ++a)
+                uw[a] = (1.0 - u - v) * c->vvel[3 * t[0] + a] + u * c->vvel[3 * t[1] + a]
+                      + v * c->vvel[3 * t[2] + a];
+        }
+    }
+    if (best == INFINITY) {
+        best = 0.5;
+        double sm = x - 0.5 * ci[0] - b->X[0];
+        body_field_velocity(b, sm < 0.0 ? 0.0 : sm > b->length ? b->length : sm, uw);
+    }
+    return best;
+}
+
 static int inside_body(const orc_ctx *c, double x, double y, double z)
 {
     const orc_body *b = &c->b;
+    if (b->kind == BODY_MESH) return inside_mesh(c, x, y, z);
     if (b->kind == BODY_AIRFOIL) return inside_airfoil(b, x, y);
     if (b->kind == BODY_SPHERE) {
         double d[3];
@@ -396,9 +561,15 @@ static double link_q(const orc_ctx *c, double x, double y, double z, const int *
 }
 
 /* Velocity of the body surface at the wall point (translation only: the
- * sphere and the channel walls do not rotate). */
-static void wall_velocity(const orc_body *b, double y_solid, double *uw)
+ * sphere and the channel walls do not rotate; the swimmer's material velocity
+ * at the point's arc position). */
+static void wall_velocity(const orc_body *b, double x_solid, double y_solid, double *uw)
 {
+    if (b->kind == BODY_MESH) {
+        double s = x_solid - b->X[0];
+        body_field_velocity(b, s < 0.0 ? 0.0 : s > b->length ? b->length : s, uw);
+        return;
+    }
     if (b->kind == BODY_PLANES) {
         const double *v = y_solid < b->y_lo ? b->U_lo : b->U_hi;
         for (int a = 0; a < 3; ++a) uw[a] = v[a];
@@ -505,7 +676,7 @@ static void refill(orc_ctx *c, int x, int y, int z)
     }
     double rho = cnt ? rsum / cnt : c->p.rho0;
     double uw[3];
-    wall_velocity(&c->b, (double)y, uw);
+    wall_velocity(&c->b, (double)x, (double)y, uw);
     double dudx[3][3], Pi[9], f[Q];
     velocity_gradient(c, x, y, z, uw, c->solid0, dudx);
     pressure_tensor(rho, uw, dudx, c->p.beta, Pi);
@@ -543,8 +714,12 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
         for (int i = 0; i < Q; ++i) {
             if (!missing[i]) { rho_stat += Fi[i]; continue; }
             const int *ci = C[i];
-            q[i] = link_q(c, x, y, z, ci);
-            wall_velocity(&c->b, (double)(y - ci[1]), uw[i]);
+            if (c->b.kind == BODY_MESH) {
+                q[i] = mesh_link(c, x, y, z, ci, uw[i]);
+            } else {
+                q[i] = link_q(c, x, y, z, ci);
+                wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), uw[i]);
+            }
             /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
              * the wall and returns reflected (halfway bounce-back). */
             rho_stat += c->fa[opp(i) * N + n];
@@ -581,10 +756,12 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
             for (int a = 0; a < 3; ++a)
                 dF[a] = (-ci[a] - uw[i][a]) * fout - (ci[a] - uw[i][a]) * Fi[i];
             /* torque arm from the body's reference point: sphere centre,
-             * airfoil leading edge at z = 0, the lattice origin otherwise */
+             * airfoil leading edge at z = 0, swimmer head on the centre line,
+             * the lattice origin otherwise */
             double r[3];
             if (c->b.kind == BODY_SPHERE) sphere_offset(c, x, y, z, r);
             else if (c->b.kind == BODY_AIRFOIL) { r[0] = x - c->b.X[0]; r[1] = y - c->b.X[1]; r[2] = z; }
+            else if (c->b.kind == BODY_MESH) { r[0] = x - c->b.X[0]; r[1] = y - c->b.X[1]; r[2] = z - c->b.X[2]; }
             else { r[0] = x; r[1] = y; r[2] = z; }
             for (int a = 0; a < 3; ++a) r[a] -= q[i] * ci[a];
             F[0] += dF[0]; F[1] += dF[1]; F[2] += dF[2];
@@ -611,6 +788,12 @@ orc_ctx *orc_create(const orc_params *p, const orc_body *b)
     c->solid0 = (uint8_t *)calloc((size_t)c->N, 1);
     c->solid1 = (uint8_t *)calloc((size_t)c->N, 1);
     if (!c->fa || !c->solid0 || !c->solid1) return NULL;
+    if (b->kind == BODY_MESH) {
+        c->vpos = (double *)calloc((size_t)3 * b->n_vertices, sizeof(double));
+        c->vvel = (double *)calloc((size_t)3 * b->n_vertices, sizeof(double));
+        if (!c->vpos || !c->vvel) return NULL;
+        mesh_pose(c);
+    }
     orc_feq(p->rho0, p->u_face, c->feq_face);
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -622,17 +805,36 @@ orc_ctx *orc_create(const orc_params *p, const orc_body *b)
 void orc_destroy(orc_ctx *c)
 {
     if (!c) return;
-    free(c->fa); free(c->fb); free(c->solid0); free(c->solid1); free(c);
+    free(c->fa); free(c->fb); free(c->solid0); free(c->solid1); free(c->vpos); free(c->vvel); free(c);
 }
 
 void orc_set_f(orc_ctx *c, const double *f) { memcpy(c->fa, f, sizeof(double) * Q * c->N); }
 void orc_get_f(const orc_ctx *c, double *f) { memcpy(f, c->fa, sizeof(double) * Q * c->N); }
 void orc_get_solid(const orc_ctx *c, uint8_t *s) { memcpy(s, c->solid0, (size_t)c->N); }
 void orc_get_body(const orc_ctx *c, orc_body *b) { *b = c->b; }
-void orc_set_body(orc_ctx *c, const orc_body *b) { c->b = *b; }
+void orc_set_body(orc_ctx *c, const orc_body *b)
+{
+    c->b = *b;
+    if (b->kind == BODY_MESH && c->vpos) mesh_pose(c);
+}
+/* Vertex positions and velocities of the mesh at the current pose (3 n_vertices each). */
+void orc_mesh_pose(const orc_ctx *c, double *pos, double *vel)
+{
+    memcpy(pos, c->vpos, sizeof(double) * 3 * c->b.n_vertices);
+    memcpy(vel, c->vvel, sizeof(double) * 3 * c->b.n_vertices);
+}
+
+/* Link fraction q and wall velocity of the link from (x, y, z) along -c_i at
+ * the current pose of the mesh. */
+double orc_mesh_link(const orc_ctx *c, int x, int y, int z, int i, double *uw)
+{
+    return mesh_link(c, x, y, z, C[i], uw);
+}
+
 long orc_counter(const orc_ctx *c, int which)
 {
-    return which == 0 ? c->step : which == 1 ? c->n_boundary : which == 2 ? c->n_links : c->n_refill;
+    return which == 0 ? c->step : which == 1 ? c->n_boundary : which == 2 ? c->n_links
+         : which == 3 ? c->n_refill : c->error;
 }
 
 /* Initial state f = f^eq(rho(x), u(x)) + amp * W_i * xi_i(x) from host fields
@@ -660,6 +862,18 @@ static void body_update(orc_ctx *c)
         b->t = b->t + 1.0;
         b->X[1] = b->y_base + b->h_amp * sin(b->h_omega * b->t);
         b->U[1] = b->h_amp * b->h_omega * cos(b->h_omega * b->t);
+        return;
+    }
+    if (b->kind == BODY_MESH) {
+        /* Sec. 4.3: Newton's equation along the swimming axis by explicit
+         * Euler, X0 += U0, U0 += F0 / m; then the new pose of the mesh */
+        b->t = b->t + 1.0;
+        if (b->free_motion) {
+            const double inv_m = 1.0 / b->mass;
+            b->X[0] = b->X[0] + b->U[0];
+            b->U[0] = b->U[0] + b->F[0] * inv_m;
+        }
+        mesh_pose(c);
         return;
     }
     if (!b->free_motion) return;

@@ -137,3 +137,86 @@ def plunging_airfoil(shape=(1024, 512, 64), chord: float = 128.0, u_inf: float =
                 chord=chord, ca=math.cos(a), sa=math.sin(a), h_amp=h0 * chord, h_omega=2 * math.pi * f,
                 camber_m=0.015, camber_p=0.35, thick=airfoil_thickness(), le=le,
                 faces=(2, 3, 2, 2, 0, 0), u_face=(u_inf, 0.0, 0.0))
+
+
+# ------------------------------------------------------------------ swimmer
+def swimmer_half_width(s, L: float):
+    """Half width w(s) of the anguilliform body (Sec. 4.3): sqrt(2 w_h s - s^2)
+    up to s_b, a quadratic decrease to w_t at s_t, then linear to zero at the
+    tail; w_h = s_b = 0.04 L, s_t = 0.95 L, w_t = 0.01 L."""
+    s = np.asarray(s, dtype=np.float64)
+    wh = sb = 0.04 * L
+    st, wt = 0.95 * L, 0.01 * L
+    a = np.sqrt(np.clip(2.0 * wh * s - s * s, 0.0, None))
+    b = wh - (wh - wt) * ((s - sb) / (st - sb)) ** 2
+    c = wt * (L - s) / (L - st)
+    return np.where(s < sb, a, np.where(s < st, b, np.clip(c, 0.0, None)))
+
+
+def swimmer_half_height(s, L: float):
+    """Half height h(s) = b sqrt(1 - ((s - a)/a)^2), a = 0.51 L, b = 0.08 L (Sec. 4.3)."""
+    s = np.asarray(s, dtype=np.float64)
+    a, b = 0.51 * L, 0.08 * L
+    return b * np.sqrt(np.clip(1.0 - ((s - a) / a) ** 2, 0.0, None))
+
+
+def swimmer_mesh(L: float, segments: int = 150, ring: int = 64):
+    """Closed triangulated surface of elliptic cross sections along the centre
+    line (Sec. 4.3: 150 segments).  Returns (rest, tris): rest[v] = (s, dy, dz),
+    the arc position and the offsets of vertex v from the centre line, and
+    tris[k] = three vertex indices, counter-clockwise seen from outside.
+    Vertex 0 is the head (s = 0), then `segments` rings of `ring` vertices at
+    s = k L / segments, k = 1..segments, then the tail-cap centre (s = L).  The
+    tail ring has zero width, so the cap triangles have zero area."""
+    rest = [(0.0, 0.0, 0.0)]
+    phi = 2.0 * np.pi * (np.arange(ring) + 0.5) / ring
+    for k in range(1, segments + 1):
+        s = L * k / segments
+        w = float(swimmer_half_width(s, L))
+        h = float(swimmer_half_height(s, L))
+        for j in range(ring):
+            rest.append((s, w * math.cos(phi[j]), h * math.sin(phi[j])))
+    tail = len(rest)
+    rest.append((float(L), 0.0, 0.0))
+
+    def rv(k, j):  # vertex of ring k (1-based), position j
+        return 1 + (k - 1) * ring + (j % ring)
+
+    tris = []
+    # (ds, dy, dz) axes: outward normal of the head fan points to -s
+    for j in range(ring):
+        tris.append((0, rv(1, j + 1), rv(1, j)))
+    for k in range(1, segments):
+        for j in range(ring):
+            a, b = rv(k, j), rv(k, j + 1)
+            c, d = rv(k + 1, j), rv(k + 1, j + 1)
+            tris.append((a, b, d))
+            tris.append((a, d, c))
+    for j in range(ring):
+        tris.append((tail, rv(segments, j), rv(segments, j + 1)))
+    return np.asarray(rest, dtype=np.float64), np.asarray(tris, dtype=np.int32)
+
+
+def swimmer_volume(L: float, n: int = 200001) -> float:
+    """Volume of the analytic body, integral of pi w(s) h(s) ds (trapezoidal rule)."""
+    s = np.linspace(0.0, L, n)
+    return float(np.trapezoid(np.pi * swimmer_half_width(s, L) * swimmer_half_height(s, L), s))
+
+
+def anguilliform_swimmer(shape=(768, 256, 256), L: float = 128.0, period: float = 4000.0,
+                         amp: float = 0.125, wavelength=None, re: float = 7142.0,
+                         segments: int = 150, ring: int = 64, ramp: bool = False,
+                         head=None):
+    """Self-propelled anguilliform swimmer (Sec. 4.3): body of length L, midline
+    y(s,t) = amp L (s/L + 0.03125)/1.03125 sin(2 pi (s/lambda - t/T)), free in x,
+    neutrally buoyant (m = rho0 V), all faces periodic; nu from Re = (L^2/T)/nu.
+    The head starts at 2/3 of the box length, heading -x; the centre line sits
+    off the lattice planes."""
+    nx, ny, nz = shape
+    if head is None:
+        head = (round(2 * nx / 3) + 0.137, ny / 2 + 0.371, nz / 2 + 0.293)
+    rest, tris = swimmer_mesh(L, segments, ring)
+    return dict(name=f"anguilliform_swimmer_{nx}x{ny}x{nz}_L{L:g}", shape=shape,
+                nu=(L * L / period) / re, L=L, period=period, amp=amp,
+                wavelength=L if wavelength is None else wavelength, ramp=int(ramp),
+                X=tuple(head), mass=swimmer_volume(L), rest=rest, tris=tris, faces=(0,) * 6)

@@ -1,0 +1,206 @@
+"""Pins of the oracle's triangulated swimmer (Sec. 4.3): the closed mesh of
+elliptic cross sections, the prescribed midline deformation, the ray-parity
+solid test, the link fraction and barycentric wall velocity, the momentum
+balance and the Euler update along the swimming axis.  Each is checked against
+the analytic body, the paper's printed amplitudes or an exact invariant."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+
+def _body(orc, L, segments, ring, X, amp=0.0, period=64.0, **kw):
+    rest, tris = synth.swimmer_mesh(L, segments, ring)
+    return orc.mesh_body(X, rest, tris, L, amp, L, period, mass=synth.swimmer_volume(L), **kw)
+
+
+def test_synth_mesh_is_closed_and_encloses_the_analytic_volume():
+    """Every directed edge appears once and its reverse once (a closed,
+    consistently oriented surface); the divergence-theorem volume approaches
+    the integral of pi w h (Sec. 4.3 cross sections) from below."""
+    L = 128.0
+    rest, tris = synth.swimmer_mesh(L)
+    assert len(tris) == 19200  # 150 segments x 64 x 2, head fan and tail cap
+    edges = {}
+    for a, b, c in tris:
+        for u, v in ((a, b), (b, c), (c, a)):
+            edges[(u, v)] = edges.get((u, v), 0) + 1
+    assert max(edges.values()) == 1
+    assert all((v, u) in edges for (u, v) in edges)
+    P = rest
+    vol = np.einsum("ij,ij->i", P[tris[:, 0]], np.cross(P[tris[:, 1]], P[tris[:, 2]])).sum() / 6.0
+    ref = synth.swimmer_volume(L)
+    assert 0.98 * ref < vol < ref
+    # printed half axes: w_h = 0.04 L at s_b = 0.04 L, tail width 0.01 L at 0.95 L,
+    # height b = 0.08 L at s = a = 0.51 L
+    assert synth.swimmer_half_width(0.04 * L, L) == pytest.approx(0.04 * L)
+    assert synth.swimmer_half_width(0.95 * L, L) == pytest.approx(0.01 * L)
+    assert synth.swimmer_half_width(L, L) == 0.0
+    assert synth.swimmer_half_height(0.51 * L, L) == pytest.approx(0.08 * L)
+
+
+def test_midline_amplitudes_and_travelling_wave(orc):
+    """Sec. 4.3 midline: lateral amplitude 0.125 L at the tail and
+    0.125 L * 0.03125/1.03125 at the head; the wave moves one wavelength per
+    period towards the tail; the pose repeats after one period."""
+    L, T = 40.0, 64.0
+    shape = (72, 40, 24)
+    X = (16.137, 20.371, 12.293)
+    o = orc.Oracle(shape, nu=0.02, body=_body(orc, L, 20, 8, X, amp=0.125, period=T))
+    rest = o.body
+    n = rest.n_vertices
+    head, tail = 0, n - 1
+    ys_head, ys_tail, poses = [], [], []
+    for k in range(int(T)):
+        pos, _ = o.mesh_pose()
+        ys_head.append(pos[head, 1] - X[1])
+        ys_tail.append(pos[tail, 1] - X[1])
+        poses.append(pos.copy())
+        o.step_sampled([0])  # advances the pose, state untouched except refill
+    assert max(np.abs(ys_tail)) == pytest.approx(0.125 * L, rel=2e-3)
+    assert max(np.abs(ys_head)) == pytest.approx(0.125 * L * 0.03125 / 1.03125, rel=2e-3)
+    pos, _ = o.mesh_pose()
+    assert np.abs(pos - poses[0]).max() < 1e-12
+    # travelling wave: y(s, t + T/4) / A(s) = y(s - lambda/4, t) / A(s - lambda/4)
+    r, _ = synth.swimmer_mesh(L, 20, 8)
+    s = r[:, 0]
+    env = 0.125 * L * (s / L + 0.03125) / 1.03125
+    ring0 = 1 + 8 * np.arange(20)  # position 0 of each of the 20 rings of 8 vertices
+    ss = s[ring0]
+    y0 = (poses[0][ring0, 1] - X[1] - r[ring0, 1]) / env[ring0]
+    y1 = (poses[int(T // 4)][ring0, 1] - X[1] - r[ring0, 1]) / env[ring0]
+    shifted = ss + L / 4
+    ok = shifted <= L
+    assert np.abs(np.interp(shifted[ok], ss, y1) - y0[ok]).max() < 0.02
+
+
+@pytest.mark.parametrize("amp,t0", [(0.0, 0.0), (0.125, 9.0)])
+def test_ray_parity_solid_test_matches_analytic_body(orc, amp, t0):
+    """A node is solid when it lies inside the elliptic cross section of the
+    (displaced) centre line at s = x - X0; nodes clearly inside or outside the
+    analytic surface (10% margin) are classified by ray parity accordingly,
+    and the solid count approaches the analytic volume."""
+    L, T = 48.0, 64.0
+    shape = (72, 48, 24)
+    X = (12.137, 24.371, 12.293)
+    body = _body(orc, L, 150, 96, X, amp=amp, period=T, t0=t0)
+    o = orc.Oracle(shape, nu=0.02, body=body)
+    solid = o.solid().astype(bool)
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape[::-1]], indexing="ij")
+    s = x - X[0]
+    w = synth.swimmer_half_width(np.clip(s, 0, L), L)
+    h = synth.swimmer_half_height(np.clip(s, 0, L), L)
+    ymid = amp * L * (s / L + 0.03125) / 1.03125 * np.sin(2 * np.pi * (s / L - t0 / T))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        phi = ((y - X[1] - ymid) / w) ** 2 + ((z - X[2]) / h) ** 2
+    core = (s > 2.0) & (s < L - 2.0)
+    inside = core & (phi < 0.9)
+    outside = (s < -0.5) | (s > L + 0.5) | (core & (phi > 1.1))
+    assert inside.sum() > 300
+    assert solid[inside].all()
+    assert not solid[outside].any()
+    vol = synth.swimmer_volume(L)
+    assert abs(solid.sum() - vol) < 0.05 * vol
+
+
+def test_link_fraction_and_wall_velocity_on_the_analytic_surface(orc):
+    """Straight body translating with U (prescribed): for lateral links
+    (c = +-e_y) the wall point lies on the elliptic cross section,
+    y_w = Y + w(s) sqrt(1 - (dz/h(s))^2), and the barycentric wall velocity
+    of equal vertex velocities is U."""
+    L = 48.0
+    shape = (64, 32, 24)
+    X = (8.137, 16.371, 12.293)
+    U = (0.013, -0.004, 0.002)
+    o = orc.Oracle(shape, nu=0.02, body=_body(orc, L, 150, 256, X, U=U))
+    solid = o.solid().astype(bool)
+    c, _ = orc.lattice()
+    iy = {+1: int(np.where((c == [0, 1, 0]).all(1))[0][0]), -1: int(np.where((c == [0, -1, 0]).all(1))[0][0])}
+    checked = 0
+    for xx in range(int(X[0]) + 6, int(X[0] + L) - 6, 3):
+        s = xx - X[0]
+        w = float(synth.swimmer_half_width(s, L))
+        h = float(synth.swimmer_half_height(s, L))
+        for zz in range(24):
+            dz = zz - X[2]
+            if abs(dz) > 0.8 * h:
+                continue
+            yw = w * math.sqrt(1 - (dz / h) ** 2)
+            for sign in (+1, -1):
+                # fluid node just outside the wall on this side, solid node inside
+                yb = int(math.floor(X[1] + sign * yw)) + (1 if sign > 0 else 0)
+                ys = yb - sign
+                if solid[zz, yb, xx] or not solid[zz, ys, xx]:
+                    continue
+                # link from x_b towards x_b - c_i = the solid node
+                q, uw = o.mesh_link(xx, yb, zz, iy[sign])
+                q_ref = abs(yb - (X[1] + sign * yw))
+                assert q == pytest.approx(q_ref, abs=5e-3)
+                assert np.abs(uw - U).max() < 1e-15
+                checked += 1
+    assert checked > 40
+
+
+def test_vertex_velocity_is_central_difference_of_the_pose(orc):
+    """Sec. 4.3 wall velocity by finite differences of the prescribed
+    deformation: the vertex velocity at t equals (x(t+1) - x(t-1))/2 of the
+    poses the oracle actually takes (prescribed body, no translation)."""
+    L, T = 40.0, 32.0
+    o = orc.Oracle((72, 40, 24), nu=0.02,
+                   body=_body(orc, L, 20, 8, (16.137, 20.371, 12.293), amp=0.125, period=T, ramp=True))
+    pos = []
+    vel = []
+    for _ in range(4):
+        p, v = o.mesh_pose()
+        pos.append(p)
+        vel.append(v)
+        o.step_sampled([0])
+    for k in (1, 2):
+        assert np.abs(vel[k] - 0.5 * (pos[k + 1] - pos[k - 1])).max() < 1e-13
+    # ramp: the body starts straight
+    rest = synth.swimmer_mesh(L, 20, 8)[0]
+    assert np.abs(pos[0][:, 1] - 20.371 - rest[:, 1]).max() < 1e-13
+
+
+def test_swimmer_momentum_exchange_balances_fluid_momentum(orc):
+    """Fixed straight mesh in a periodic box: the fluid's momentum change in
+    one step is exactly minus the momentum-exchange force (as for the sphere)."""
+    shape = (40, 16, 16)
+    o = orc.Oracle(shape, nu=0.05, body=_body(orc, 24.0, 24, 12, (8.137, 8.371, 8.293)))
+    rho, u, xi = synth.parity_fields(shape, 9)
+    o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
+    for _ in range(2):
+        T0 = o.totals()
+        o.step(1)
+        T1 = o.totals()
+        F = np.array(o.body.F)
+        assert np.linalg.norm(F) > 0.01
+        assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
+        assert o.counters()["error"] == 0
+
+
+def test_swimmer_euler_update_along_the_swimming_axis(orc):
+    """Newton's equation along x by explicit Euler (Sec. 4.3 with Sec. 4.1's
+    scheme): X0 += U0, U0 += F0/m; the lateral and vertical position of the
+    centre line stay fixed."""
+    shape = (48, 20, 20)
+    X0 = np.array([10.137, 10.371, 10.293])
+    U0 = 0.01
+    m = 7.5
+    body = _body(orc, 24.0, 24, 12, X0, amp=0.125, period=32.0, U=(U0, 0, 0), free=True)
+    body.mass = m
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    o.init_state(*synth.uniform_fields(shape, (0.01, 0.0, 0.0)))
+    o.step(1)
+    b1 = o.body
+    assert b1.X[0] == pytest.approx(X0[0] + U0, abs=1e-15)
+    assert list(b1.X[1:]) == list(X0[1:])
+    assert b1.U[0] == U0
+    F1 = b1.F[0]
+    o.step(1)
+    b2 = o.body
+    assert b2.X[0] == pytest.approx(X0[0] + 2 * U0, abs=1e-14)
+    assert b2.U[0] == pytest.approx(U0 + F1 / m, abs=1e-16)
+    assert b2.t == 2.0
