@@ -10,6 +10,11 @@ reduction.  The value is GLUPS over box nodes, FP32 storage; FP16 and BF16
 storage forms are reported under "variants".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sphere|airfoil|swimmer]
+
+--workload selects another of the paper's configurations for the same
+measurement: the plunging airfoil (1024x512x64, chord 128, Sec. 4.2) or the
+self-propelled anguilliform swimmer (768x256x256, L = 128, Sec. 4.3).
 
 With N > 1 (torchrun) every rank runs an independent replica (the path has
 no data-parallel split without a halo exchange); the value is all ranks'
@@ -50,6 +55,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer"])
     return ap.parse_args()
 
 
@@ -192,22 +198,42 @@ def ncu_traffic(storage: str):
 
 
 # ----------------------------------------------------------------- workload
-def workload(shape=None):
+def workload(shape=None, kind="sphere"):
     import synth
-    if shape:
-        return synth.sedimenting_sphere(shape=tuple(int(v) for v in shape.split(",")))
-    return synth.sedimenting_sphere()
+    if kind == "airfoil":
+        wl = synth.plunging_airfoil()
+    elif kind == "swimmer":
+        wl = synth.anguilliform_swimmer()
+    elif shape:
+        wl = synth.sedimenting_sphere(shape=tuple(int(v) for v in shape.split(",")))
+    else:
+        wl = synth.sedimenting_sphere()
+    wl["kind"] = kind
+    return wl
+
+
+def initial_flow(wl):
+    """Quiescent fluid, or the inflow velocity everywhere for the airfoil."""
+    import synth
+    return synth.uniform_fields(wl["shape"], wl.get("u_face", (0.0, 0.0, 0.0)))
 
 
 def make_lattice(storage, wl, device):
     import numpy as np
 
     import paper_1608_04658_gb300 as lbm
-    import synth
     shape = wl["shape"]
-    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device)
-    lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
-    rho, u = synth.uniform_fields(shape)
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device,
+                      u_face=wl.get("u_face", (0.0, 0.0, 0.0)))
+    if wl["kind"] == "airfoil":
+        lat.set_geometry(lbm.airfoil(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
+                                     wl["camber_m"], wl["camber_p"], wl["thick"]))
+    elif wl["kind"] == "swimmer":
+        lat.set_geometry(lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
+                                     wl["period"], ramp=bool(wl["ramp"]), free=True, mass=wl["mass"]))
+    else:
+        lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
+    rho, u = initial_flow(wl)
     lat.init_state(rho, u)
     return lat, np
 
@@ -278,15 +304,27 @@ def e2e_storage(storage, wl, args, device):
             "note": "pinned FP64 state in and out once per run (amortised), 48-byte force/torque read every step"}
 
 
-def cpu_baseline(wl, nsteps=2):
-    """The FP64 oracle, single-threaded, on the full sedimenting-sphere box."""
+def oracle_body(wl):
     import oracle
-    import synth
+    if wl["kind"] == "airfoil":
+        return oracle.airfoil_body(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
+                                   wl["camber_m"], wl["camber_p"], wl["thick"])
+    if wl["kind"] == "swimmer":
+        return oracle.mesh_body(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
+                                wl["period"], ramp=bool(wl["ramp"]), free=True, mass=wl["mass"])
+    return oracle.sphere_body(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"])
+
+
+def cpu_baseline(wl, nsteps=None):
+    """The FP64 oracle, single-threaded, on the full box of the workload
+    (2 steps of the sphere box, 1 step of the larger boxes)."""
+    import oracle
     shape = wl["shape"]
-    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
-                        body=oracle.sphere_body(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"],
-                                                g=wl["g"]))
-    orc.init_state(*synth.uniform_fields(shape))
+    if nsteps is None:
+        nsteps = 2 if wl["kind"] == "sphere" else 1
+    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"], u_face=wl.get("u_face", (0.0, 0.0, 0.0)),
+                        body=oracle_body(wl))
+    orc.init_state(*initial_flow(wl))
     t0 = time.perf_counter()
     orc.step(nsteps)
     t = time.perf_counter() - t0
@@ -305,7 +343,7 @@ def run_ours(args):
     lbm.build()
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
-    wl = workload(args.shape)
+    wl = workload(args.shape, args.workload)
     clocks = ClockSampler(local)
     clocks.start()
     main = time_storage(args.storage, wl, args, world, device, clocks)

@@ -10,6 +10,9 @@
  *     lbm_set_geometry).
  *   - Sec. 4.1: Galilean-invariant momentum exchange and Newton's equations
  *     of the sphere with Euler integration (lbm_step, lbm_body_forces).
+ *   - Sec. 4.2: plunging airfoil (prescribed plunge); Sec. 4.3: triangulated
+ *     anguilliform swimmer with a prescribed midline deformation, free along
+ *     the swimming axis (lbm_set_geometry).
  *
  * Conventions shared by every entry point:
  *   - Every call returns an lbm_status; LBM_OK is 0.  On failure the message
@@ -83,7 +86,9 @@ typedef struct {
     double u_face[3];     /* velocity of EQ faces */
 } lbm_params;
 
-typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2, LBM_BODY_AIRFOIL = 3 } lbm_body_kind;
+typedef enum {
+    LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2, LBM_BODY_AIRFOIL = 3, LBM_BODY_MESH = 4
+} lbm_body_kind;
 
 /* Immersed body.  A node is solid when its centre lies inside the body
  * (strictly).  On periodic axes the sphere is taken at its nearest image.
@@ -101,7 +106,27 @@ typedef enum { LBM_BODY_NONE = 0, LBM_BODY_SPHERE = 1, LBM_BODY_PLANES = 2, LBM_
  *     + ... + thick[4] xi^4.  Prescribed plunge (Sec. 4.2): the leading edge is at
  *     y = X[1] + h_amp sin(h_omega t) at step t (t0 at lbm_set_geometry); the
  *     wall moves with the plunge velocity.  Link fractions are found by 50
- *     bisections of the link. */
+ *     bisections of the link.
+ *   MESH: closed triangulated swimmer (Sec. 4.3).  mesh_rest holds, per
+ *     vertex, its arc position s >= 0 along the centre line and its offsets
+ *     (dy, dz) from it; mesh_tris three vertex indices per triangle (a closed,
+ *     consistently oriented surface).  Both are host arrays, copied.  At step t
+ *     vertex v sits at (X[0] + s, (X[1] + y(s,t)) + dy, X[2] + dz) with the
+ *     midline y(s,t) = r(t) wave_amp length (s/length + 0.03125)/1.03125
+ *     sin(2 pi (s/wave_length - t/wave_period)); r(t) = (1 - cos(pi t/T))/2 for
+ *     0 <= t < T with wave_ramp, 1 otherwise.  Its velocity is U plus the
+ *     central difference (y(s,t+1) - y(s,t-1))/2 along y.  A node is solid when
+ *     the ray from it along +x crosses the surface an odd number of times
+ *     (edge functions of the (y, z) projection, each edge evaluated from its
+ *     lower-index vertex, zero counted positive).  A link's wall point is its
+ *     first crossing with a triangle; the wall velocity there is the
+ *     barycentric interpolation of the vertex velocities.  With free_motion
+ *     the head follows Newton's equation along x by explicit Euler:
+ *     X[0] += U[0], then U[0] += F[0]/mass.  t0 is the time of the initial
+ *     pose.  The body must stay two nodes clear of every box face; a pose
+ *     outside that sets status bit 2 (band overflow), as does a column crossed
+ *     more than 32 times or a 2x2x2 cell overlapped by more than 384
+ *     triangles. */
 typedef struct {
     int32_t kind;         /* lbm_body_kind */
     int32_t free_motion;  /* 1: integrate the sphere's translation */
@@ -113,7 +138,16 @@ typedef struct {
     double mass;          /* m_s (rho_s * pi D^3 / 6 for the analytic volume) */
     double rho_ratio;     /* rho_s / rho_f */
     double g[3];          /* gravity */
-    double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], t0;  /* AIRFOIL */
+    double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], t0;  /* AIRFOIL; t0 also MESH */
+    const double *mesh_rest;   /* MESH: host, 3 doubles (s, dy, dz) per vertex */
+    const int32_t *mesh_tris;  /* MESH: host, 3 vertex indices per triangle */
+    int32_t n_vertices, n_triangles;
+    double length;             /* MESH: body length L */
+    double wave_amp;           /* MESH: midline amplitude factor (0.125 in Sec. 4.3) */
+    double wave_length;        /* MESH: lambda */
+    double wave_period;        /* MESH: T, steps */
+    int32_t wave_ramp;         /* MESH: 1 to ramp the amplitude up over the first period */
+    int32_t reserved_mesh;     /* must be 0 */
 } lbm_geometry;
 
 /* Body state on the device, read back by lbm_get_body. */

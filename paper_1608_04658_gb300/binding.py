@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OO
                 7: "LBM_ERR_UNSUPPORTED"}
 STORAGES = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
-BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL = 0, 1, 2, 3
+BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL, BODY_MESH = 0, 1, 2, 3, 4
 GAMMA_ANALYTIC, GAMMA_LBGK = 0, 2
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
 
@@ -48,7 +48,11 @@ class Geometry(C.Structure):
                 ("mass", C.c_double), ("rho_ratio", C.c_double), ("g", C.c_double * 3),
                 ("chord", C.c_double), ("ca", C.c_double), ("sa", C.c_double), ("h_amp", C.c_double),
                 ("h_omega", C.c_double), ("camber_m", C.c_double), ("camber_p", C.c_double),
-                ("thick", C.c_double * 5), ("t0", C.c_double)]
+                ("thick", C.c_double * 5), ("t0", C.c_double),
+                ("mesh_rest", C.POINTER(C.c_double)), ("mesh_tris", C.POINTER(C.c_int32)),
+                ("n_vertices", C.c_int32), ("n_triangles", C.c_int32),
+                ("length", C.c_double), ("wave_amp", C.c_double), ("wave_length", C.c_double),
+                ("wave_period", C.c_double), ("wave_ramp", C.c_int32), ("reserved_mesh", C.c_int32)]
 
 
 class BodyState(C.Structure):
@@ -165,6 +169,31 @@ def airfoil(le, chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick, t0=0.0
     G.camber_m, G.camber_p = float(camber_m), float(camber_p)
     for k in range(5):
         G.thick[k] = float(thick[k])
+    G.t0 = float(t0)
+    return G
+
+
+def swimmer(X, rest, tris, length, wave_amp, wave_length, wave_period, ramp=False,
+            U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0) -> Geometry:
+    """Triangulated swimmer (Sec. 4.3): rest (n, 3) = (s, dy, dz) per vertex,
+    tris (m, 3) vertex indices, head at X, centre line along +x.  The arrays
+    are kept alive by the returned Geometry (the library copies them)."""
+    import numpy as np
+    G = Geometry()
+    G.kind = BODY_MESH
+    G.free_motion = 1 if free else 0
+    rest = np.ascontiguousarray(rest, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    G._arrays = (rest, tris)
+    G.mesh_rest = rest.ctypes.data_as(C.POINTER(C.c_double))
+    G.mesh_tris = tris.ctypes.data_as(C.POINTER(C.c_int32))
+    G.n_vertices, G.n_triangles = len(rest), len(tris)
+    for a in range(3):
+        G.X[a], G.U[a] = float(X[a]), float(U[a])
+    G.length, G.wave_amp = float(length), float(wave_amp)
+    G.wave_length, G.wave_period = float(wave_length), float(wave_period)
+    G.wave_ramp = 1 if ramp else 0
+    G.mass = float(mass)
     G.t0 = float(t0)
     return G
 

@@ -104,6 +104,9 @@ void free_scratch(Scratch &S, bool keep_body)
 {
     cudaFree(S.blist); cudaFree(S.bpos); cudaFree(S.ulist); cudaFree(S.bforce);
     cudaFree(S.partials); cudaFree(S.ticket);
+    cudaFree(S.mesh_rest); cudaFree(S.mesh_pos); cudaFree(S.mesh_vel); cudaFree(S.col_x);
+    cudaFree(S.mesh_tris); cudaFree(S.col_count); cudaFree(S.cell_count); cudaFree(S.cell_tri);
+    cudaFree(S.mesh_status); cudaFree(S.tri_box);
     DevBody *b = S.body;
     S = Scratch{};
     if (keep_body) S.body = b;
@@ -213,7 +216,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (!g) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: null geometry");
-    if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_AIRFOIL)
+    if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_MESH)
         return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: unknown body kind");
     const Lattice &L = ctx->L;
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
@@ -279,6 +282,43 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
             G.cap[a] = c < n[a] ? c : n[a];
         }
         G.cap[2] = n[2];
+    } else if (g->kind == LBM_BODY_MESH) {
+        const int nv = g->n_vertices, nt = g->n_triangles;
+        if (!g->mesh_rest || !g->mesh_tris || nv < 4 || nt < 4 || nv > (1 << 24) || nt > (1 << 24) ||
+            !(g->length > 0.0) || g->wave_length == 0.0 || g->wave_period == 0.0 || g->reserved_mesh != 0 ||
+            (g->free_motion && !(g->mass > 0.0)))
+            return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh needs vertices, triangles, length > 0, "
+                                          "non-zero wavelength and period (and mass > 0 when free)");
+        for (long long k = 0; k < 3LL * nt; ++k)
+            if (g->mesh_tris[k] < 0 || g->mesh_tris[k] >= nv)
+                return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh triangle index out of range");
+        double ext[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
+        for (int v = 0; v < nv; ++v)
+            for (int a = 0; a < 3; ++a) {
+                const double r = g->mesh_rest[3 * v + a];
+                if (!std::isfinite(r) || (a == 0 && r < 0.0))
+                    return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh rest data not finite (or s < 0)");
+                ext[2 * a] = std::min(ext[2 * a], r);
+                ext[2 * a + 1] = std::max(ext[2 * a + 1], r);
+            }
+        // lateral reach of the midline: its envelope at the largest arc position
+        const double env = std::fabs(g->wave_amp) * g->length * (ext[1] / g->length + 0.03125) / 1.03125;
+        ext[2] -= env;
+        ext[3] += env;
+        G.n_vertices = nv;
+        G.n_triangles = nt;
+        G.length = g->length;
+        G.wave_amp = g->wave_amp;
+        G.wave_length = g->wave_length;
+        G.wave_period = g->wave_period;
+        G.wave_ramp = g->wave_ramp ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+            G.mesh_ext[2 * a] = ext[2 * a];
+            G.mesh_ext[2 * a + 1] = ext[2 * a + 1];
+            const int c = (int)std::ceil(ext[2 * a + 1] - ext[2 * a]) + 9;
+            G.cap[a] = c < n[a] ? c : n[a];
+            G.cells[a] = (G.cap[a] + MESH_CELL - 1) / MESH_CELL + 1;
+        }
     } else {
         for (int a = 0; a < 3; ++a) G.cap[a] = n[a];
     }
@@ -295,6 +335,29 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
              dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess && dalloc(&S.ticket, 1) == cudaSuccess;
         if (ok) ok = cudaMemsetAsync(S.ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
     }
+    if (ok && g->kind == LBM_BODY_MESH) {
+        const size_t nv = (size_t)G.n_vertices, nt = (size_t)G.n_triangles;
+        const size_t ncols = (size_t)G.cap[1] * G.cap[2];
+        const size_t ncells = (size_t)G.cells[0] * G.cells[1] * G.cells[2];
+        ok = dalloc(&S.mesh_rest, 3 * nv) == cudaSuccess && dalloc(&S.mesh_pos, 3 * nv) == cudaSuccess &&
+             dalloc(&S.mesh_vel, 3 * nv) == cudaSuccess && dalloc(&S.mesh_tris, 3 * nt) == cudaSuccess &&
+             dalloc(&S.tri_box, 6 * nt) == cudaSuccess && dalloc(&S.col_count, ncols) == cudaSuccess &&
+             dalloc(&S.col_x, ncols * MESH_COL_CAP) == cudaSuccess && dalloc(&S.cell_count, ncells) == cudaSuccess &&
+             dalloc(&S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && dalloc(&S.mesh_status, 1) == cudaSuccess;
+        if (ok)
+            ok = cudaMemcpy(S.mesh_rest, g->mesh_rest, 3 * nv * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                 cudaMemcpy(S.mesh_tris, g->mesh_tris, 3 * nt * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        G.mesh_rest = S.mesh_rest;
+        G.mesh_tris = S.mesh_tris;
+        G.mesh_pos = S.mesh_pos;
+        G.mesh_vel = S.mesh_vel;
+        G.tri_box = S.tri_box;
+        G.col_count = S.col_count;
+        G.col_x = S.col_x;
+        G.cell_count = S.cell_count;
+        G.cell_tri = S.cell_tri;
+        G.mesh_status = S.mesh_status;
+    }
     if (!ok) {
         free_scratch(ctx->S, true);
         ctx->has_body = false;
@@ -309,9 +372,23 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         hb[0].U[1] = g->h_amp * g->h_omega * std::cos(g->h_omega * g->t0);
         hb[0].U[2] = 0.0;
     }
+    if (g->kind == LBM_BODY_MESH) hb[0].t = g->t0;
     ctx->bcur = 0;
     LBM_CUDA(cudaMemcpyAsync(S.body, hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
     LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
+    if (g->kind == LBM_BODY_MESH) {
+        LBM_CUDA(launch_mesh_mark_initial(L, G, S, 0, ctx->flags, ctx->stream), "initial marks");
+        int mst = 0;
+        LBM_CUDA(cudaMemcpyAsync(&mst, S.mesh_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "mesh status");
+        LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
+        if (mst) {
+            free_scratch(ctx->S, true);
+            ctx->has_body = false;
+            return fail(ctx, LBM_ERR_ARG, (mst & 2) ? "lbm_set_geometry: mesh closer than two nodes to a box face"
+                                                    : "lbm_set_geometry: mesh column or cell list overflow");
+        }
+        return LBM_OK;
+    }
     if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, hb[0].X, ctx->flags, ctx->stream), "initial marks");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
     return LBM_OK;

@@ -19,7 +19,8 @@
 //   one-sided where one is, zero otherwise; Pi with rho_tgt and u_tgt; only
 //   the missing populations are replaced; the node then collides with KBC.
 //   Refill: mean density of the neighbours fluid at t (rho0 if none), the body
-//   velocity, gradient with the wall velocity at the centre.
+//   velocity (the swimmer's material velocity at the node's arc position),
+//   gradient with the wall velocity at the centre.
 #include "geom.cuh"
 #include "kbc.cuh"
 
@@ -316,6 +317,11 @@ __global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
         R u[3] = {(R)b->U[0], (R)b->U[1], (R)b->U[2]};
         if (G.kind == LBM_BODY_PLANES) {
             const double *v = (double)y < 0.5 * (G.y_lo + G.y_hi) ? G.U_lo : G.U_hi;
+            u[0] = (R)v[0]; u[1] = (R)v[1]; u[2] = (R)v[2];
+        } else if (G.kind == LBM_BODY_MESH) {
+            // material velocity of the swimmer at the node's arc position
+            double v[3];
+            swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - b->X[0]), v);
             u[0] = (R)v[0]; u[1] = (R)v[1]; u[2] = (R)v[2];
         }
         R du[3][3], Qt[6];

@@ -75,6 +75,151 @@ __device__ __forceinline__ bool inside_body(const GeomParams &G, const Lattice &
     return false;
 }
 
+// ---------------------------------------------------------------- swimmer mesh
+// Anguilliform swimmer (Sec. 4.3): midline, material velocity, ray-parity
+// solid test on per-column crossing lists and the link search on triangle
+// cells.  The solid decision (edge values, crossing abscissa) uses the same
+// explicitly rounded double expressions as a plain evaluation.
+constexpr double MESH_PI = 3.14159265358979323846;
+
+// y(s,t) = r(t) a L (s/L + 0.03125)/1.03125 sin(2 pi (s/lambda - t/T))
+__device__ __forceinline__ double swimmer_midline(const GeomParams &G, double s, double t)
+{
+    double r = 1.0;
+    if (G.wave_ramp) {
+        if (t < 0.0) r = 0.0;
+        else if (t < G.wave_period)
+            r = __dmul_rn(0.5, __dsub_rn(1.0, cos(__ddiv_rn(__dmul_rn(MESH_PI, t), G.wave_period))));
+    }
+    const double A = __ddiv_rn(__dmul_rn(__dmul_rn(G.wave_amp, G.length), __dadd_rn(__ddiv_rn(s, G.length), 0.03125)),
+                               1.03125);
+    const double arg = __dmul_rn(2.0 * MESH_PI, __dsub_rn(__ddiv_rn(s, G.wave_length), __ddiv_rn(t, G.wave_period)));
+    return __dmul_rn(r, __dmul_rn(A, sin(arg)));
+}
+
+// material velocity at arc position s (already clamped to [0, L]) at the pose
+// of body time t: U plus the central difference of the midline along y
+__device__ __forceinline__ void swimmer_velocity(const GeomParams &G, const double U[3], double t, double s,
+                                                 double v[3])
+{
+    const double m1 = swimmer_midline(G, s, __dadd_rn(t, 1.0));
+    const double m0 = swimmer_midline(G, s, __dsub_rn(t, 1.0));
+    v[0] = U[0];
+    v[1] = __dadd_rn(U[1], __ddiv_rn(__dsub_rn(m1, m0), 2.0));
+    v[2] = U[2];
+}
+
+__device__ __forceinline__ double clamp_arc(const GeomParams &G, double s)
+{
+    return s < 0.0 ? 0.0 : (s > G.length ? G.length : s);
+}
+
+// edge value of the (y, z) projection of directed edge u -> v at (y, z),
+// evaluated from the lower-index vertex; sign with zero counted positive in
+// that direction
+__device__ __forceinline__ double mesh_edge(const double *__restrict__ P, int u, int v, double y, double z, int &sg)
+{
+    const int a = u < v ? u : v, b = u < v ? v : u;
+    const double Ay = P[3 * a + 1], Az = P[3 * a + 2], By = P[3 * b + 1], Bz = P[3 * b + 2];
+    double val = __dsub_rn(__dmul_rn(__dsub_rn(By, Ay), __dsub_rn(z, Az)), __dmul_rn(__dsub_rn(Bz, Az), __dsub_rn(y, Ay)));
+    sg = val >= 0.0 ? 1 : -1;
+    if (u > v) { val = -val; sg = -sg; }
+    return val;
+}
+
+// does the line {(., y, z)} cross triangle t?  xc = crossing abscissa
+__device__ __forceinline__ bool mesh_column_crossing(const double *__restrict__ P, int t0, int t1, int t2,
+                                                     double y, double z, double &xc)
+{
+    int s0, s1, s2;
+    const double e0 = mesh_edge(P, t1, t2, y, z, s0);
+    const double e1 = mesh_edge(P, t2, t0, y, z, s1);
+    const double e2 = mesh_edge(P, t0, t1, y, z, s2);
+    if (s0 != s1 || s1 != s2) return false;
+    const double den = __dadd_rn(__dadd_rn(e0, e1), e2);
+    if (den == 0.0) return false;
+    const double num = __dadd_rn(__dadd_rn(__dmul_rn(e0, P[3 * t0]), __dmul_rn(e1, P[3 * t1])), __dmul_rn(e2, P[3 * t2]));
+    xc = __ddiv_rn(num, den);
+    return true;
+}
+
+// parity of the crossings of band column col beyond x
+__device__ __forceinline__ bool mesh_inside_column(const GeomParams &G, int col, double x)
+{
+    const int n = min(G.col_count[col], MESH_COL_CAP);
+    const double *xs = G.col_x + (size_t)col * MESH_COL_CAP;
+    int k = 0;
+    for (int j = 0; j < n; ++j) k += xs[j] > x;
+    return k & 1;
+}
+
+__device__ __forceinline__ double det3(const double a[3], const double b[3], const double d[3])
+{
+    return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) + a[2] * (b[0] * d[1] - b[1] * d[0]);
+}
+
+// first crossing x_b - s c (s in [0,1]) of the mesh, over the triangles of the
+// cells that the link's box overlaps; Cramer's rule for (u, v, s) per
+// triangle; wall velocity by barycentric interpolation of vertex velocities.
+// No hit (round-off at an edge): q = 1/2 and the material velocity at the
+// link's midpoint.
+__device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
+                          double &q, double uw[3])
+{
+    const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
+    int c0[3], c1[3];
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int e0 = min(p[a], p[a] - c[a]), e1 = max(p[a], p[a] - c[a]);
+        lo[a] = (float)e0;
+        hi[a] = (float)e1;
+        c0[a] = max(0, (e0 - b->band_lo[a]) / MESH_CELL);
+        c1[a] = min(G.cells[a] - 1, (e1 - b->band_lo[a]) / MESH_CELL);
+    }
+    const double *P = G.mesh_pos;
+    const double dc[3] = {(double)cx, (double)cy, (double)cz};
+    double best = 2.0;
+    for (int kz = c0[2]; kz <= c1[2]; ++kz)
+        for (int ky = c0[1]; ky <= c1[1]; ++ky)
+            for (int kx = c0[0]; kx <= c1[0]; ++kx) {
+                const int cell = kx + G.cells[0] * (ky + G.cells[1] * kz);
+                const int n = min(G.cell_count[cell], MESH_CELL_CAP);
+                const int *list = G.cell_tri + (size_t)cell * MESH_CELL_CAP;
+                for (int j = 0; j < n; ++j) {
+                    const int k = list[j];
+                    const float *bx = G.tri_box + 6 * (size_t)k;
+                    if (bx[3] < lo[0] || bx[0] > hi[0] || bx[4] < lo[1] || bx[1] > hi[1] || bx[5] < lo[2] ||
+                        bx[2] > hi[2])
+                        continue;
+                    const int t0 = G.mesh_tris[3 * k], t1 = G.mesh_tris[3 * k + 1], t2 = G.mesh_tris[3 * k + 2];
+                    double e1[3], e2[3], r[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        e1[a] = P[3 * t1 + a] - P[3 * t0 + a];
+                        e2[a] = P[3 * t2 + a] - P[3 * t0 + a];
+                        r[a] = (double)p[a] - P[3 * t0 + a];
+                    }
+                    const double D = det3(e1, e2, dc);
+                    if (D == 0.0) continue;
+                    const double u = det3(r, e2, dc) / D;
+                    const double v = det3(e1, r, dc) / D;
+                    const double s = det3(e1, e2, r) / D;
+                    if (u < 0.0 || v < 0.0 || u + v > 1.0 || s < 0.0 || s > 1.0 || !(s < best)) continue;
+                    best = s;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        uw[a] = (1.0 - u - v) * G.mesh_vel[3 * t0 + a] + u * G.mesh_vel[3 * t1 + a] +
+                                v * G.mesh_vel[3 * t2 + a];
+                }
+            }
+    if (best > 1.0) {
+        best = 0.5;
+        swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
+    }
+    q = best;
+}
+
 // Pull source x - c under the box rules; node index, or -1 when a wall or
 // equilibrium face serves the pull (such a source is never solid).
 __device__ __forceinline__ int pull_source(const Lattice &L, int x, int y, int z, int cx, int cy, int cz)
@@ -116,7 +261,9 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
                                           int x, int y, int z, int cx, int cy, int cz, double &q,
                                           double uw[3])
 {
-    if (G.kind == LBM_BODY_SPHERE) {
+    if (G.kind == LBM_BODY_MESH) {
+        mesh_link(G, b, x, y, z, cx, cy, cz, q, uw);
+    } else if (G.kind == LBM_BODY_SPHERE) {
         const double d0 = axis_offset(x, b->X[0], L.nx, G.periodic[0]);
         const double d1 = axis_offset(y, b->X[1], L.ny, G.periodic[1]);
         const double d2 = axis_offset(z, b->X[2], L.nz, G.periodic[2]);
@@ -155,10 +302,12 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
 }
 
 // torque arm origin: displacement of (x, y, z) from the body reference point
-// (sphere centre; airfoil leading edge at z = 0; the lattice origin otherwise)
+// (sphere centre; airfoil leading edge at z = 0; swimmer head on the centre
+// line; the lattice origin otherwise)
 __device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams &G, const DevBody *b,
                                               int a, int p)
 {
+    if (G.kind == LBM_BODY_MESH) return __dsub_rn((double)p, b->X[a]);
     if (G.kind == LBM_BODY_AIRFOIL) return a < 2 ? __dsub_rn((double)p, b->X[a]) : (double)p;
     if (G.kind != LBM_BODY_SPHERE) return (double)p;
     const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);

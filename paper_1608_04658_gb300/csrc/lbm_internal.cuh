@@ -20,6 +20,11 @@ constexpr uint8_t FL_SOLID_PREV = 2; // inside the body at the previous step
 constexpr uint8_t FL_BOUNDARY = 4;   // fluid node with at least one solid pull source
 constexpr uint8_t FL_UNCOVERED = 8;  // solid at the previous step, fluid now
 
+// swimmer mesh lists (Sec. 4.3 body)
+constexpr int MESH_COL_CAP = 32;    // crossings kept per band column
+constexpr int MESH_CELL = 2;        // edge of a triangle cell (lattice units)
+constexpr int MESH_CELL_CAP = 384;  // triangles kept per cell
+
 // device status bits
 constexpr int ST_UNSTABLE = 1;
 constexpr int ST_BAND_OVERFLOW = 2;
@@ -99,6 +104,22 @@ struct GeomParams {
     // airfoil
     double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], y_base;
     double box[4];       // profile box relative to the leading edge: dx min/max, dy min/max
+    // swimmer mesh (device arrays owned by Scratch)
+    const double *mesh_rest;  // (s, dy, dz) per vertex
+    const int *mesh_tris;     // three vertex indices per triangle
+    double *mesh_pos;         // vertex positions at the current pose
+    double *mesh_vel;         // vertex velocities at the current pose
+    float *tri_box;           // per triangle: min x, y, z, max x, y, z (rounded outwards)
+    int *col_count;           // crossings per band column (y, z)
+    double *col_x;            // [column][MESH_COL_CAP] crossing abscissae
+    int *cell_count;          // triangles per band cell
+    int *cell_tri;            // [cell][MESH_CELL_CAP] triangle indices
+    int *mesh_status;         // overflow of the column or cell lists in this step
+    int n_vertices, n_triangles;
+    int cells[3];             // cell grid of the band capacity box
+    double length, wave_amp, wave_length, wave_period;
+    int wave_ramp;
+    double mesh_ext[6];       // pose extent relative to the head: x, y, z min/max
     int periodic[3];
     int cap[3];          // band capacity per axis
     int cap_boundary;    // slots in the boundary list
@@ -128,6 +149,10 @@ struct Scratch {
     double *partials;    // [n_partials * 6]
     unsigned *ticket;    // last-block counter of the force reduction
     int n_partials;
+    // swimmer mesh
+    double *mesh_rest, *mesh_pos, *mesh_vel, *col_x;
+    int *mesh_tris, *col_count, *cell_count, *cell_tri, *mesh_status;
+    float *tri_box;
 };
 
 // launchers ------------------------------------------------------------------
@@ -151,5 +176,9 @@ cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Sc
 cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s);
 cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
+cudaError_t launch_mesh_prepare(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
+                                cudaStream_t s, int *nlaunch);
+cudaError_t launch_mesh_mark_initial(const Lattice &L, const GeomParams &G, Scratch &S, int cur,
+                                     uint8_t *flags, cudaStream_t s);
 
 }  // namespace lbm

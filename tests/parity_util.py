@@ -32,6 +32,11 @@ def oracle_body(geom):
     if geom.kind == lbm.BODY_AIRFOIL:
         return oracle.airfoil_body((geom.X[0], geom.X[1]), geom.chord, geom.ca, geom.sa, geom.h_amp,
                                    geom.h_omega, geom.camber_m, geom.camber_p, list(geom.thick), geom.t0)
+    if geom.kind == lbm.BODY_MESH:
+        rest, tris = geom._arrays
+        return oracle.mesh_body(list(geom.X), rest, tris, geom.length, geom.wave_amp, geom.wave_length,
+                                geom.wave_period, ramp=bool(geom.wave_ramp), U=list(geom.U),
+                                free=bool(geom.free_motion), mass=geom.mass, t0=geom.t0)
     return oracle.planes_body(geom.y_lo, geom.y_hi, U_lo=list(geom.U_lo), U_hi=list(geom.U_hi))
 
 

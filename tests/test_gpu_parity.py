@@ -242,3 +242,53 @@ def test_plunging_airfoil(storage):
     assert np.abs(F - Fo).max() <= ftol * np.abs(Fo).max()
     assert np.abs(M - Mo).max() <= ftol * np.abs(Mo).max()
     assert lat.body()["X"][1] == pytest.approx(orc.body.X[1], abs=1e-13)
+
+
+def _swimmer_geom(lat_mod, L=32.0, segments=40, ring=24, X=(20.137, 16.371, 10.293), period=160.0, **kw):
+    rest, tris = synth.swimmer_mesh(L, segments, ring)
+    return lat_mod.swimmer(X, rest, tris, L, 0.125, L, period, mass=synth.swimmer_volume(L), **kw)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_anguilliform_swimmer(storage):
+    """Deforming triangulated swimmer (L = 32, 40 segments x 24 around, a fast
+    undulation so nodes get uncovered every step, free along x) in a periodic
+    box: ray-parity solid marks, link search over the triangle cells,
+    barycentric wall velocity, refill with the material velocity, Euler step
+    of the head along x."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (64, 32, 20)
+    rho, u, xi = synth.parity_fields(shape, 17)
+    fields = (rho, 0.2 * u + np.array([0.01, 0.0, 0.0]), xi, 1e-3)
+    geom = _swimmer_geom(lbm, U=(-0.004, 0.0, 0.0), free=True, t0=5.0)
+    lat, orc = run_pair(shape, 0.02, storage, fields, 10, geom=geom)
+    mask = fluid_mask(lat, orc)
+    cnt = orc.counters()
+    assert cnt["refill"] > 0 and cnt["error"] == 0
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+    F, M = lat.forces()
+    Fo, Mo = np.array(orc.body.F), np.array(orc.body.M)
+    ftol = {"fp64": 1e-10, "fp32": 1e-4, "fp16": 3e-2, "bf16": 3e-2}[storage]
+    assert np.abs(F - Fo).max() <= ftol * np.abs(Fo).max()
+    assert np.abs(M - Mo).max() <= ftol * np.abs(Mo).max()
+    b = lat.body()
+    xtol = {"fp64": 1e-13, "fp32": 1e-9, "fp16": 1e-6, "bf16": 1e-5}[storage]
+    assert b["X"][0] == pytest.approx(orc.body.X[0], abs=xtol)
+    assert b["t"] == orc.body.t == 15.0
+    assert b["status"] == 0
+
+
+def test_swimmer_rejects_bad_meshes():
+    """Host-side checks of lbm_set_geometry for a mesh: triangle indices out
+    of range and a pose too close to a box face are rejected, nothing runs."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (64, 32, 20)
+    lat = lbm.Lattice(shape, 0.02, storage="fp32")
+    rest, tris = synth.swimmer_mesh(32.0, 40, 24)
+    bad = tris.copy()
+    bad[5, 1] = len(rest)
+    with pytest.raises(lbm.LbmError):
+        lat.set_geometry(lbm.swimmer((20.137, 16.371, 10.293), rest, bad, 32.0, 0.125, 32.0, 160.0))
+    with pytest.raises(lbm.LbmError):
+        lat.set_geometry(lbm.swimmer((40.137, 16.371, 10.293), rest, tris, 32.0, 0.125, 32.0, 160.0))
+    lat.set_geometry(lbm.swimmer((20.137, 16.371, 10.293), rest, tris, 32.0, 0.125, 32.0, 160.0))
