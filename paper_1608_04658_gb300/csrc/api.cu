@@ -253,6 +253,9 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.chord = g->chord; G.ca = g->ca; G.sa = g->sa;
         G.h_amp = g->h_amp; G.h_omega = g->h_omega;
         G.camber_m = g->camber_m; G.camber_p = g->camber_p;
+        G.inv_chord = 1.0 / g->chord;
+        G.camber_k1 = g->camber_p > 0.0 ? g->camber_m / (g->camber_p * g->camber_p) : 0.0;
+        G.camber_k2 = g->camber_p < 1.0 ? g->camber_m / ((1.0 - g->camber_p) * (1.0 - g->camber_p)) : 0.0;
         for (int k = 0; k < 5; ++k) G.thick[k] = g->thick[k];
         G.y_base = g->X[1];
         // profile box in the lattice frame (relative to the leading edge) from a

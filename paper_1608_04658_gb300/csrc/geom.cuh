@@ -220,6 +220,113 @@ __device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody
     q = best;
 }
 
+// Single-precision forms of the link search, used when the populations are
+// stored in FP32 or 16 bits (their collision runs in FP32): coordinates are
+// taken relative to the node in double and then rounded, so the link
+// fraction keeps about 1e-7 absolute accuracy.  The solid marks themselves
+// stay the double decisions above.
+__device__ __forceinline__ float det3f(const float a[3], const float b[3], const float d[3])
+{
+    return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) + a[2] * (b[0] * d[1] - b[1] * d[0]);
+}
+
+__device__ __noinline__ static void mesh_link_f(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx,
+                                                int cy, int cz, double &q, double uw[3])
+{
+    constexpr float EPS = 1e-6f;  // barycentric slack: a link through a shared edge hits one of its triangles
+    const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
+    int c0[3], c1[3];
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int e0 = min(p[a], p[a] - c[a]), e1 = max(p[a], p[a] - c[a]);
+        lo[a] = (float)e0;
+        hi[a] = (float)e1;
+        c0[a] = max(0, (e0 - b->band_lo[a]) / MESH_CELL);
+        c1[a] = min(G.cells[a] - 1, (e1 - b->band_lo[a]) / MESH_CELL);
+    }
+    const double *P = G.mesh_pos;
+    const float dc[3] = {(float)cx, (float)cy, (float)cz};
+    float best = 2.0f;
+    float bu = 0.f, bv = 0.f;
+    int bt = -1;
+    for (int kz = c0[2]; kz <= c1[2]; ++kz)
+        for (int ky = c0[1]; ky <= c1[1]; ++ky)
+            for (int kx = c0[0]; kx <= c1[0]; ++kx) {
+                const int cell = kx + G.cells[0] * (ky + G.cells[1] * kz);
+                const int n = min(G.cell_count[cell], MESH_CELL_CAP);
+                const int *list = G.cell_tri + (size_t)cell * MESH_CELL_CAP;
+                for (int j = 0; j < n; ++j) {
+                    const int k = list[j];
+                    const float *bx = G.tri_box + 6 * (size_t)k;
+                    if (bx[3] < lo[0] || bx[0] > hi[0] || bx[4] < lo[1] || bx[1] > hi[1] || bx[5] < lo[2] ||
+                        bx[2] > hi[2])
+                        continue;
+                    const int t0 = G.mesh_tris[3 * k], t1 = G.mesh_tris[3 * k + 1], t2 = G.mesh_tris[3 * k + 2];
+                    float A[3], e1[3], e2[3], r[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        A[a] = (float)(P[3 * t0 + a] - (double)p[a]);
+                        e1[a] = (float)(P[3 * t1 + a] - (double)p[a]) - A[a];
+                        e2[a] = (float)(P[3 * t2 + a] - (double)p[a]) - A[a];
+                        r[a] = -A[a];
+                    }
+                    const float D = det3f(e1, e2, dc);
+                    if (D == 0.0f) continue;
+                    const float iD = 1.0f / D;
+                    const float u = det3f(r, e2, dc) * iD;
+                    const float v = det3f(e1, r, dc) * iD;
+                    const float sv = det3f(e1, e2, r) * iD;
+                    if (u < -EPS || v < -EPS || u + v > 1.0f + EPS || sv < -EPS || sv > 1.0f + EPS || !(sv < best))
+                        continue;
+                    best = sv;
+                    bu = u;
+                    bv = v;
+                    bt = k;
+                }
+            }
+    if (bt < 0) {
+        q = 0.5;
+        swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
+        return;
+    }
+    q = fmin(fmax((double)best, 0.0), 1.0);
+    const int t0 = G.mesh_tris[3 * bt], t1 = G.mesh_tris[3 * bt + 1], t2 = G.mesh_tris[3 * bt + 2];
+    const double u = bu, v = bv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        uw[a] = (1.0 - u - v) * G.mesh_vel[3 * t0 + a] + u * G.mesh_vel[3 * t1 + a] + v * G.mesh_vel[3 * t2 + a];
+}
+
+// airfoil link in the chord frame: node position and link direction in
+// double, the 24 halvings in float with reciprocal constants
+__device__ __forceinline__ bool inside_airfoil_f(const GeomParams &G, float xi, float eta)
+{
+    if (xi < 0.0f || xi > 1.0f) return false;
+    const float p = (float)G.camber_p;
+    const float yc = xi < p ? (float)G.camber_k1 * (2.0f * p * xi - xi * xi)
+                            : (float)G.camber_k2 * ((1.0f - 2.0f * p) + 2.0f * p * xi - xi * xi);
+    const float t = (float)G.thick[0] * sqrtf(xi) +
+                    xi * ((float)G.thick[1] + xi * ((float)G.thick[2] + xi * ((float)G.thick[3] + xi * (float)G.thick[4])));
+    return fabsf(eta - yc) < t;
+}
+
+__device__ __forceinline__ double link_airfoil_f(const GeomParams &G, const DevBody *b, int x, int y, int cx, int cy)
+{
+    const double dx = (double)x - b->X[0], dy = (double)y - b->X[1];
+    const float xi0 = (float)((dx * G.ca - dy * G.sa) * G.inv_chord);
+    const float eta0 = (float)((dx * G.sa + dy * G.ca) * G.inv_chord);
+    const float dxi = (float)(-(cx * G.ca - cy * G.sa) * G.inv_chord);
+    const float deta = (float)(-(cx * G.sa + cy * G.ca) * G.inv_chord);
+    float lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 24; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (inside_airfoil_f(G, xi0 + mid * dxi, eta0 + mid * deta)) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * ((double)lo + (double)hi);
+}
+
 // Pull source x - c under the box rules; node index, or -1 when a wall or
 // equilibrium face serves the pull (such a source is never solid).
 __device__ __forceinline__ int pull_source(const Lattice &L, int x, int y, int z, int cx, int cy, int cz)
@@ -256,13 +363,23 @@ __device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int z, 
 
 // Link of boundary node (x, y, z) towards the solid node x - c: fraction q of
 // the link at which the wall is crossed (wall point x_w = x - q c, q in (0,1])
-// and the wall velocity there.
+// and the wall velocity there.  R is the collision arithmetic: double keeps
+// the plain double evaluation; float uses the single-precision link search
+// for the airfoil and the mesh.
+template <typename R>
 __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G, const DevBody *b,
                                           int x, int y, int z, int cx, int cy, int cz, double &q,
                                           double uw[3])
 {
+    constexpr bool single = sizeof(R) == 4;
     if (G.kind == LBM_BODY_MESH) {
-        mesh_link(G, b, x, y, z, cx, cy, cz, q, uw);
+        if (single) mesh_link_f(G, b, x, y, z, cx, cy, cz, q, uw);
+        else mesh_link(G, b, x, y, z, cx, cy, cz, q, uw);
+    } else if (G.kind == LBM_BODY_AIRFOIL && single) {
+        q = link_airfoil_f(G, b, x, y, cx, cy);
+        uw[0] = b->U[0];
+        uw[1] = b->U[1];
+        uw[2] = b->U[2];
     } else if (G.kind == LBM_BODY_SPHERE) {
         const double d0 = axis_offset(x, b->X[0], L.nx, G.periodic[0]);
         const double d1 = axis_offset(y, b->X[1], L.ny, G.periodic[1]);

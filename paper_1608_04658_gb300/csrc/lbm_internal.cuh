@@ -103,6 +103,7 @@ struct GeomParams {
     double g[3];
     // airfoil
     double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], y_base;
+    double inv_chord, camber_k1, camber_k2;  // 1/c, m/p^2, m/(1-p)^2 (single-precision link search)
     double box[4];       // profile box relative to the leading edge: dx min/max, dy min/max
     // swimmer mesh (device arrays owned by Scratch)
     const double *mesh_rest;  // (s, dy, dz) per vertex
