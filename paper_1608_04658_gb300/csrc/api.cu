@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "lbm_internal.cuh"
+#include "body.cuh"
 
 using namespace lbm;
 

@@ -1,0 +1,94 @@
+// Immersed-body state shared by the geometry, boundary and API translation
+// units of liblbm.so (arXiv 1608.04658, Secs. 3 and 4): body parameters,
+// the device body state, the library's boundary scratch and their launchers.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// swimmer mesh lists (Sec. 4.3 body)
+constexpr int MESH_COL_CAP = 32;    // crossings kept per band column
+constexpr int MESH_CELL = 2;        // edge of a triangle cell (lattice units)
+constexpr int MESH_CELL_CAP = 384;  // triangles kept per cell
+
+struct GeomParams {
+    int kind;
+    int free_motion;
+    double R;
+    double y_lo, y_hi;
+    double U_lo[3], U_hi[3];
+    double inv_mass;     // 1 / m_s
+    double buoy;         // 1 - rho_f / rho_s
+    double g[3];
+    // airfoil
+    double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], y_base;
+    double inv_chord, camber_k1, camber_k2;  // 1/c, m/p^2, m/(1-p)^2 (single-precision link search)
+    double box[4];       // profile box relative to the leading edge: dx min/max, dy min/max
+    // swimmer mesh (device arrays owned by Scratch)
+    const double *mesh_rest;  // (s, dy, dz) per vertex
+    const int *mesh_tris;     // three vertex indices per triangle
+    double *mesh_pos;         // vertex positions at the current pose
+    double *mesh_vel;         // vertex velocities at the current pose
+    float *tri_box;           // per triangle: min x, y, z, max x, y, z (rounded outwards)
+    int *col_count;           // crossings per band column (y, z)
+    double *col_x;            // [column][MESH_COL_CAP] crossing abscissae
+    int *cell_count;          // triangles per band cell
+    int *cell_tri;            // [cell][MESH_CELL_CAP] triangle indices
+    int *mesh_status;         // overflow of the column or cell lists in this step
+    int n_vertices, n_triangles;
+    int cells[3];             // cell grid of the band capacity box
+    double length, wave_amp, wave_length, wave_period;
+    int wave_ramp;
+    double mesh_ext[6];       // pose extent relative to the head: x, y, z min/max
+    int periodic[3];
+    int cap[3];          // band capacity per axis
+    int cap_boundary;    // slots in the boundary list
+    int cap_uncovered;   // slots in the uncovered list
+};
+
+// Body state; two copies alternate between steps (the mark kernel reads the
+// previous one and writes the next).
+struct DevBody {
+    double X[3], U[3];
+    double F[3], M[3];
+    double F_sum[3], M_sum[3];
+    long long n_sum;
+    int band_lo[3], band_n[3];
+    int n_boundary, n_uncovered, n_links;
+    int status;
+    double t;            // time of the current pose (prescribed motion)
+};
+
+// scratch owned by the library for the boundary path
+struct Scratch {
+    DevBody *body;       // [2]
+    int *blist;          // [cap_boundary] node index of each boundary node
+    int *bpos;           // [cap_boundary] band position of each boundary node
+    int *ulist;          // [cap_uncovered] node index of each uncovered node
+    double *bforce;      // [band capacity * 6] force and torque per band position
+    double *partials;    // [n_partials * 6]
+    unsigned *ticket;    // last-block counter of the force reduction
+    int n_partials;
+    // swimmer mesh
+    double *mesh_rest, *mesh_pos, *mesh_vel, *col_x;
+    int *mesh_tris, *col_count, *cell_count, *cell_tri, *mesh_status;
+    float *tri_box;
+};
+
+// launchers ------------------------------------------------------------------
+cudaError_t launch_geometry(const Lattice &L, const GeomParams &G, Scratch &S, int prev, uint8_t *flags,
+                            cudaStream_t s, int *nlaunch);
+cudaError_t launch_mark_initial(const Lattice &L, const GeomParams &G, const double *X,
+                                uint8_t *flags, cudaStream_t s);
+cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
+                          void *fa, const uint8_t *flags, cudaStream_t s);
+cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
+                            const void *fa, void *fb, const uint8_t *flags, cudaStream_t s);
+cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
+cudaError_t launch_mesh_prepare(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
+                                cudaStream_t s, int *nlaunch);
+cudaError_t launch_mesh_mark_initial(const Lattice &L, const GeomParams &G, Scratch &S, int cur,
+                                     uint8_t *flags, cudaStream_t s);
+
+}  // namespace lbm

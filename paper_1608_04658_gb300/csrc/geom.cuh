@@ -7,7 +7,7 @@
 // same decisions as a plain double evaluation of the same expressions.
 #pragma once
 
-#include "lbm_internal.cuh"
+#include "body.cuh"
 
 namespace lbm {
 
