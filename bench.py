@@ -40,7 +40,7 @@ BYTES_PER_NODE = {"fp64": 432, "fp32": 216, "fp16": 108, "bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32", "bf16": "f32"}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "bulk_kernel_sedimenting_sphere.md")
-KERNEL_SOURCES = ["bulk.cu", "kbc.cuh", "lbm_internal.cuh"]
+KERNEL_SOURCES = ["bulk.cu", "pull.cuh", "kbc.cuh", "lbm_internal.cuh"]
 
 
 def parse_args():

@@ -249,6 +249,48 @@ LBM_API int64_t lbm_kernel_launches(const lbm_ctx *ctx);
 LBM_API lbm_status lbm_profile_begin(lbm_ctx *ctx, int max_launches);
 LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *launches);
 
+/* Adjoint (reverse-mode) gradient of a time-averaged force objective over a
+ * horizon of steps, by a hand-written adjoint of every part of lbm_step: the
+ * KBC collision with its exact Jacobian (the stabilizer's dependence on f
+ * included), the pull streaming with the box faces, the Grad boundary
+ * (target density and velocity, finite-difference velocity gradient, link
+ * fraction and wall velocity), the refill and the momentum exchange.  The
+ * node marks, boundary links and refilled nodes of each step are taken as
+ * fixed (piecewise-constant in the parameters).
+ *
+ * Objective: J = (1/horizon) sum_{t=0}^{horizon-1} w_force . F^t
+ *              + sum over nodes fluid at the end of lambda_T . f(horizon),
+ * F^t the force of the fluid on the body in step t (Sec. 4.1 momentum
+ * exchange), f(horizon) the full populations after the last step.
+ * Parameters theta (dJ_dtheta[3]):
+ *   MESH: (wave_amp, wave_length, wave_period) of the midline (Sec. 4.3);
+ *   other bodies: none (zeros).
+ * The body must be held (free_motion = 0); AIRFOIL bodies are not supported.
+ * Storage FP64 (arithmetic in double) or FP32 (arithmetic in float);
+ * 16-bit storage returns LBM_ERR_UNSUPPORTED.
+ *
+ * Memory: the forward states are kept by checkpoint-and-recompute: every
+ * checkpoint_every steps (0: ceil(sqrt(horizon))) a state is kept, and each
+ * segment is recomputed once during the reverse sweep; the call allocates
+ * (ceil(horizon/K) + K + 3) state buffers of 27 N elements and frees them
+ * before returning (LBM_ERR_OOM if they do not fit).
+ *
+ * On return the context has advanced by horizon steps, exactly as
+ * lbm_step(horizon) would have (the forces of those steps are in the body
+ * sums).  Synchronises. */
+typedef struct {
+    int32_t horizon;          /* steps, >= 1 */
+    int32_t checkpoint_every; /* K, 0 for ceil(sqrt(horizon)) */
+    double w_force[3];        /* weights of the mean force in J */
+    const void *lambda_T;     /* device, 27 N values (double for FP64 storage, float for FP32) in
+                                 the population layout, or NULL */
+    void *lambda_0;           /* device out, same layout: dJ/df at the start (0 at solid and
+                                 refilled nodes), or NULL */
+    int32_t reserved[4];      /* must be 0 */
+} lbm_adjoint;
+
+LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double dJ_dtheta[3]);
+
 /* Global sums without a context and without device allocation.  The paper
  * has no counterpart to this entry point; it exists for callers that cannot
  * call cudaMalloc: applications that hand all device memory to their own

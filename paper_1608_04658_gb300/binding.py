@@ -55,6 +55,11 @@ class Geometry(C.Structure):
                 ("wave_period", C.c_double), ("wave_ramp", C.c_int32), ("reserved_mesh", C.c_int32)]
 
 
+class AdjointSpec(C.Structure):
+    _fields_ = [("horizon", C.c_int32), ("checkpoint_every", C.c_int32), ("w_force", C.c_double * 3),
+                ("lambda_T", C.c_void_p), ("lambda_0", C.c_void_p), ("reserved", C.c_int32 * 4)]
+
+
 class BodyState(C.Structure):
     _fields_ = [("X", C.c_double * 3), ("U", C.c_double * 3), ("F", C.c_double * 3),
                 ("M", C.c_double * 3), ("F_sum", C.c_double * 3), ("M_sum", C.c_double * 3),
@@ -118,6 +123,8 @@ def lib():
         L.lbm_profile_begin.restype = C.c_int
         L.lbm_profile_end.argtypes = [vp, _D, C.POINTER(C.c_int64)]
         L.lbm_profile_end.restype = C.c_int
+        L.lbm_adjoint_step.argtypes = [vp, C.POINTER(AdjointSpec), _D, _D]
+        L.lbm_adjoint_step.restype = C.c_int
         _lib = L
     return _lib
 
@@ -336,6 +343,32 @@ class Lattice:
 
     def reset_average(self):
         self._check(lib().lbm_reset_average(self._ctx))
+
+    def adjoint(self, horizon: int, w_force=(0.0, 0.0, 0.0), lambda_T=None, want_lambda0: bool = False,
+                checkpoint_every: int = 0):
+        """Runs horizon steps and the adjoint sweep (lbm_adjoint_step).  J is
+        the mean of w_force . F over the steps plus lambda_T . f at the end
+        (lambda_T: device tensor (27, nz, ny, nx) of float64 for FP64 storage,
+        float32 for FP32).  Returns dict(J, dJ_dtheta, lambda_0)."""
+        torch = _torch()
+        spec = AdjointSpec()
+        spec.horizon = int(horizon)
+        spec.checkpoint_every = int(checkpoint_every)
+        for a in range(3):
+            spec.w_force[a] = float(w_force[a])
+        rdt = torch.float64 if self.storage == "fp64" else torch.float32
+        nx, ny, nz = self.shape
+        if lambda_T is not None:
+            lambda_T = lambda_T.to(device=self.device, dtype=rdt).contiguous()
+            spec.lambda_T = lambda_T.data_ptr()
+        lam0 = None
+        if want_lambda0:
+            lam0 = torch.zeros((27, nz, ny, nx), dtype=rdt, device=self.device)
+            spec.lambda_0 = lam0.data_ptr()
+        J = np.zeros(1)
+        dJ = np.zeros(3)
+        self._check(lib().lbm_adjoint_step(self._ctx, C.byref(spec), J.ctypes.data_as(_D), dJ.ctypes.data_as(_D)))
+        return dict(J=float(J[0]), dJ_dtheta=dJ, lambda_0=lam0)
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

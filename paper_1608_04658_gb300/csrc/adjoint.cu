@@ -1,0 +1,994 @@
+// Reverse-mode adjoint of the time step and the checkpointed driver behind
+// lbm_adjoint_step (arXiv 1608.04658: Sec. 2 collision and pull streaming,
+// Sec. 3 Grad boundary and refill, Sec. 4.1 momentum exchange, Sec. 4.3
+// swimmer kinematics).
+//
+// Forward step t -> t+1: S^t is the stored post-collision state, the refill
+// R_t overwrites the nodes uncovered at t+1 (St^t = R_t(S^t)), every node x
+// fluid at t+1 pulls F_i(x) from St^t (boundary nodes complete the missing
+// F_i with Grad's distribution) and stores S^{t+1}(x) = C(F(x)); the
+// momentum exchange gives the force F^t of the step.
+//
+// The adjoint of S^{t+1} is never stored as a full array.  Each node x fluid
+// at t+1 stores
+//     Lam^t(x)_i = dJ/dF_i(x)      (0 for missing directions, 0 at solid nodes)
+// and the adjoint of St^t at node y is the transpose of the pull plus what the
+// boundary and refill adjoints add at nearby nodes (band buffer ext^t):
+//     lambda(St^t)(y)_i = sum over the nodes x that pulled St^t(y)_i of
+//                         Lam^t(x)_i  +  ext^t(y)_i,
+// the pull transpose covering the periodic wrap, wall bounce-back and the
+// outflow clamp.  lambda(S^t)(y) = 0 where y is refilled in step t, else
+// lambda(St^t)(y).  The marks, boundary links and refilled nodes of each step
+// are those of the forward run (held fixed).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+#include "lanes.cuh"
+#include "pull.cuh"
+
+namespace lbm {
+
+// ----------------------------------------------------------------- collision VJP
+// 1-D equilibrium factors of one axis for the adjoint: phi(c) = 1 + e(c), its
+// reciprocal r(c), e(c) (shifted form, see axis_eq) and the logarithmic
+// derivatives dl(c) = d ln phi(c) / du = D0 + c dlnB with
+//   D0 = -(3u/S)/(2 - S),   dlnB = (2 + 3u/S)/(2u + S) + 1/(1 - u).
+template <typename R>
+__device__ __forceinline__ void axis_eq_adj(R u, R e[3], R phi[3], R r[3], R dl[3])
+{
+    const R u2 = u * u;
+    const R S = sqrt(R(1) + R(3) * u2);
+    const R sig = R(3) * u2 / (S + R(1));
+    const R oms = R(1) - sig;
+    const R bp = (R(3) * u + sig) / (R(1) - u);
+    const R bm = -bp / (R(1) + bp);
+    e[0] = bm * oms - sig;
+    e[1] = -sig;
+    e[2] = bp * oms - sig;
+    phi[0] = oms * (R(1) + bm);
+    phi[1] = oms;
+    phi[2] = oms * (R(1) + bp);
+    r[0] = R(1) / phi[0];
+    r[1] = R(1) / phi[1];
+    r[2] = R(1) / phi[2];
+    const R sp = R(3) * u / S;
+    const R D0 = -sp / oms;
+    const R dlnB = (R(2) + sp) / ((R(1) - u) * (R(1) + bp)) + R(1) / (R(1) - u);
+    dl[0] = D0 - dlnB;
+    dl[1] = D0;
+    dl[2] = D0 + dlnB;
+}
+
+// Transpose of the KBC collision f' = f - b (2 ds + g dh) (Eq. kbc_relax with
+// the analytic stabilizer), per node: lam holds dJ/df' on entry and dJ/df on
+// exit; g are the shifted pre-collision populations.  Backward sweep:
+//   ds_bar = -2b lam + a_bar dh/feq,  dh_bar = -b g lam + a_bar ds/feq + 2 b_bar dh/feq,
+//   g_bar = -b <lam, dh>,  a = <ds|dh>, b = <dh|dh>, g = 1/b - (2 - 1/b) a/b,
+//   df_bar = dh_bar + S^T (ds_bar - dh_bar),   feq_bar = -df_bar - (a_bar ds dh + b_bar dh^2)/feq^2,
+//   then f^eq(rho, u) and u = j/rho back to f.
+template <typename R>
+__device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int gamma_mode)
+{
+    R drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += g[i];
+        j[0] += R(cx_of(i)) * g[i];
+        j[1] += R(cy_of(i)) * g[i];
+        j[2] += R(cz_of(i)) * g[i];
+    }
+    const R rho = rho0 + drho, irho = R(1) / rho;
+    const R u[3] = {j[0] * irho, j[1] * irho, j[2] * irho};
+    R e[3][3], phi[3][3], rr[3][3], dl[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) axis_eq_adj(u[a], e[a], phi[a], rr[a], dl[a]);
+    R d[Q];
+    R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const R exy = e[0][cx + 1] + e[1][cy + 1] + e[0][cx + 1] * e[1][cy + 1];
+        const R E = exy + e[2][cz + 1] + exy * e[2][cz + 1];
+        d[i] = g[i] - weight<R>(i) * (drho + rho * E);
+        pxx += R(cx * cx) * d[i];
+        pyy += R(cy * cy) * d[i];
+        pzz += R(cz * cz) * d[i];
+        pxy += R(cx * cy) * d[i];
+        pxz += R(cx * cz) * d[i];
+        pyz += R(cy * cz) * d[i];
+    }
+    const R nxz = pxx - pzz, nyz = pyy - pzz;
+    R sh = 0, hh = 0, lh = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
+        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const R dh = d[i] - ds;
+        sh += ds * dh * ifeq;
+        hh += dh * dh * ifeq;
+        lh += lam[i] * dh;
+    }
+    const bool analytic = gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>();
+    const R gam = analytic ? inv_beta - (R(2) - inv_beta) * sh / hh : R(2);
+    const R gb = -beta * lh;
+    const R kk = R(2) - inv_beta;
+    const R ab = analytic ? -kk * gb / hh : R(0);
+    const R bb = analytic ? kk * gb * sh / (hh * hh) : R(0);
+    // shear sums of ds_bar - dh_bar
+    R Sx = 0, Sy = 0, Sz = 0, Qxy = 0, Qxz = 0, Qyz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        if (nz != 1 && nz != 2) continue;
+        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
+        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const R dh = d[i] - ds;
+        const R dsb = -R(2) * beta * lam[i] + ab * dh * ifeq;
+        const R dhb = -beta * gam * lam[i] + ab * ds * ifeq + R(2) * bb * dh * ifeq;
+        const R t = dsb - dhb;
+        if (nz == 1) {
+            if (cx) Sx += t;
+            else if (cy) Sy += t;
+            else Sz += t;
+        } else {
+            if (cz == 0) Qxy += R(cx * cy) * t;
+            else if (cy == 0) Qxz += R(cx * cz) * t;
+            else Qyz += R(cy * cz) * t;
+        }
+    }
+    const R nxzb = (R(2) * Sx - Sy - Sz) * R(1.0 / 6.0);
+    const R nyzb = (R(2) * Sy - Sx - Sz) * R(1.0 / 6.0);
+    const R pxxb = nxzb, pyyb = nyzb, pzzb = -(nxzb + nyzb);
+    const R pxyb = R(0.25) * Qxy, pxzb = R(0.25) * Qxz, pyzb = R(0.25) * Qyz;
+    R rhob = 0, ub[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
+        const R feq = rho * weight<R>(i) * phi[0][cx + 1] * phi[1][cy + 1] * phi[2][cz + 1];
+        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const R dh = d[i] - ds;
+        const R dhb = -beta * gam * lam[i] + ab * ds * ifeq + R(2) * bb * dh * ifeq;
+        const R dfb = dhb + pxxb * R(cx * cx) + pyyb * R(cy * cy) + pzzb * R(cz * cz) + pxyb * R(cx * cy) +
+                      pxzb * R(cx * cz) + pyzb * R(cy * cz);
+        // feq_bar * feq
+        const R t = -(ab * ds * dh + bb * dh * dh) * ifeq - dfb * feq;
+        rhob += t;
+        ub[0] += t * dl[0][cx + 1];
+        ub[1] += t * dl[1][cy + 1];
+        ub[2] += t * dl[2][cz + 1];
+        lam[i] += dfb;
+    }
+    rhob *= irho;
+    const R jb[3] = {ub[0] * irho, ub[1] * irho, ub[2] * irho};
+    rhob -= (ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * irho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        lam[i] += rhob + R(cx_of(i)) * jb[0] + R(cy_of(i)) * jb[1] + R(cz_of(i)) * jb[2];
+}
+
+// The same transpose with lane i < 27 holding g_i and lam_i (boundary nodes);
+// returns dJ/dg_i.
+template <typename R>
+__device__ R kbc_vjp_lanes(R g, R lam, int i, R beta, R inv_beta, R rho0, int gamma_mode)
+{
+    const bool act = i < Q;
+    const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
+    const int nz = act ? nonzero_of(i) : 0;
+    const R gv = act ? g : R(0), lv = act ? lam : R(0);
+    const R drho = wsum(gv);
+    const R jx = wsum(R(cx) * gv), jy = wsum(R(cy) * gv), jz = wsum(R(cz) * gv);
+    const R rho = rho0 + drho, irho = R(1) / rho;
+    const R u[3] = {jx * irho, jy * irho, jz * irho};
+    R e[3][3], phi[3][3], rr[3][3], dl[3][3];
+    for (int a = 0; a < 3; ++a) axis_eq_adj(u[a], e[a], phi[a], rr[a], dl[a]);
+    const R exy = pick(e[0], cx) + pick(e[1], cy) + pick(e[0], cx) * pick(e[1], cy);
+    const R E = exy + pick(e[2], cz) + exy * pick(e[2], cz);
+    const R d = act ? gv - weight<R>(i) * (drho + rho * E) : R(0);
+    const R pxx = wsum(R(cx * cx) * d), pyy = wsum(R(cy * cy) * d), pzz = wsum(R(cz * cz) * d);
+    const R pxy = wsum(R(cx * cy) * d), pxz = wsum(R(cx * cz) * d), pyz = wsum(R(cy * cz) * d);
+    const R nxz = pxx - pzz, nyz = pyy - pzz;
+    const R ds = act ? shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz) : R(0);
+    const R dh = d - ds;
+    const R ifeq = act ? irho * inv_weight<R>(i) * pick(rr[0], cx) * pick(rr[1], cy) * pick(rr[2], cz) : R(0);
+    const R feq = act ? rho * weight<R>(i) * pick(phi[0], cx) * pick(phi[1], cy) * pick(phi[2], cz) : R(0);
+    const R sh = wsum(ds * dh * ifeq), hh = wsum(dh * dh * ifeq), lh = wsum(lv * dh);
+    const bool analytic = gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>();
+    const R gam = analytic ? inv_beta - (R(2) - inv_beta) * sh / hh : R(2);
+    const R gb = -beta * lh;
+    const R kk = R(2) - inv_beta;
+    const R ab = analytic ? -kk * gb / hh : R(0);
+    const R bb = analytic ? kk * gb * sh / (hh * hh) : R(0);
+    const R dsb = -R(2) * beta * lv + ab * dh * ifeq;
+    const R dhb = -beta * gam * lv + ab * ds * ifeq + R(2) * bb * dh * ifeq;
+    const R t = (nz == 1 || nz == 2) ? dsb - dhb : R(0);
+    const R Sx = wsum((nz == 1 && cx) ? t : R(0));
+    const R Sy = wsum((nz == 1 && cy) ? t : R(0));
+    const R Sz = wsum((nz == 1 && cz) ? t : R(0));
+    const R Qxy = wsum((nz == 2 && cz == 0) ? R(cx * cy) * t : R(0));
+    const R Qxz = wsum((nz == 2 && cy == 0) ? R(cx * cz) * t : R(0));
+    const R Qyz = wsum((nz == 2 && cx == 0) ? R(cy * cz) * t : R(0));
+    const R nxzb = (R(2) * Sx - Sy - Sz) * R(1.0 / 6.0);
+    const R nyzb = (R(2) * Sy - Sx - Sz) * R(1.0 / 6.0);
+    const R dfb = dhb + nxzb * R(cx * cx) + nyzb * R(cy * cy) - (nxzb + nyzb) * R(cz * cz) +
+                  R(0.25) * (Qxy * R(cx * cy) + Qxz * R(cx * cz) + Qyz * R(cy * cz));
+    const R tf = act ? -(ab * ds * dh + bb * dh * dh) * ifeq - dfb * feq : R(0);
+    R rhob = wsum(tf) * irho;
+    const R ub[3] = {wsum(tf * pick(dl[0], cx)), wsum(tf * pick(dl[1], cy)), wsum(tf * pick(dl[2], cz))};
+    rhob -= (ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * irho;
+    if (!act) return R(0);
+    return lv + dfb + rhob + (R(cx) * ub[0] + R(cy) * ub[1] + R(cz) * ub[2]) * irho;
+}
+
+// ----------------------------------------------------------------- pull transpose
+// Sum of Lam(x)_i over the nodes x whose pull of direction i read node y:
+// per axis the reader coordinate y_a + c_a (wrapped on a periodic face, none
+// through another face) and, on an outflow face layer, y_a itself (its source
+// was clamped onto y); a wall face adds the bounce-back reader y itself for
+// direction 26 - i.
+template <typename R>
+__device__ __forceinline__ R pull_transpose(const Lattice &L, const R *__restrict__ lam, int x, int y, int z, int i)
+{
+    const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+    const int p[3] = {x, y, z}, n[3] = {L.nx, L.ny, L.nz};
+    int r0[3], r1[3];
+    bool h0[3], h1[3], wall = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int t = p[a] + c[a];
+        h0[a] = true;
+        r0[a] = t;
+        if (t < 0 || t >= n[a]) {
+            const int face = t < 0 ? L.face[2 * a] : L.face[2 * a + 1];
+            if (face == LBM_FACE_PERIODIC) r0[a] = (t + n[a]) % n[a];
+            else {
+                h0[a] = false;
+                if (face == LBM_FACE_WALL) wall = true;
+            }
+        }
+        h1[a] = (c[a] == 1 && p[a] == 0 && L.face[2 * a] == LBM_FACE_OUTFLOW) ||
+                (c[a] == -1 && p[a] == n[a] - 1 && L.face[2 * a + 1] == LBM_FACE_OUTFLOW);
+        r1[a] = p[a];
+    }
+    const size_t N = (size_t)L.N;
+    R s = 0;
+    for (int m = 0; m < 8; ++m) {
+        int q[3];
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            const bool alt = (m >> a) & 1;
+            if (alt ? !h1[a] : !h0[a]) { ok = false; break; }
+            q[a] = alt ? r1[a] : r0[a];
+        }
+        if (ok) s += lam[(size_t)i * N + q[0] + (size_t)L.nx * (q[1] + (size_t)L.ny * q[2])];
+    }
+    if (wall) s += lam[(size_t)(26 - i) * N + x + (size_t)L.nx * (y + (size_t)L.ny * z)];
+    return s;
+}
+
+// band position of node (x, y, z) in the band of body state b, or -1
+__device__ __forceinline__ int band_index(const Lattice &L, const GeomParams &G, const DevBody *b, int x, int y,
+                                          int z)
+{
+    const int p[3] = {x, y, z}, n[3] = {L.nx, L.ny, L.nz};
+    int l[3];
+    for (int a = 0; a < 3; ++a) {
+        int d = p[a] - b->band_lo[a];
+        if (G.periodic[a]) d = ((d % n[a]) + n[a]) % n[a];
+        if (d < 0 || d >= b->band_n[a]) return -1;
+        l[a] = d;
+    }
+    return l[0] + G.cap[0] * (l[1] + G.cap[1] * l[2]);
+}
+
+// Where the adjoint of S^{t+1} comes from when step t is reversed.
+template <typename R>
+struct NextAdj {
+    const R *lam;          // Lam^{t+1}, or lambda_T (direct), or NULL (zero)
+    const double *ext;     // ext^{t+1} (band of step t+1)
+    const DevBody *band;   // body state of step t+1 (band)
+    const uint8_t *flags;  // marks after step t+1 (UNCOVERED: refilled in step t+1)
+    int direct;            // 1: lam is the full adjoint of S^{t+1}
+};
+
+// lambda(S^{t+1})(x)_i
+template <typename R>
+__device__ __forceinline__ R next_adjoint(const Lattice &L, const GeomParams &G, const NextAdj<R> &A, int x, int y,
+                                          int z, int n, int i)
+{
+    if (A.direct) return A.lam ? A.lam[(size_t)i * (size_t)L.N + n] : R(0);
+    if (A.flags && (A.flags[n] & FL_UNCOVERED)) return R(0);
+    R v = pull_transpose<R>(L, A.lam, x, y, z, i);
+    if (A.ext) {
+        const int k = band_index(L, G, A.band, x, y, z);
+        if (k >= 0) v += (R)A.ext[(size_t)k * Q + i];
+    }
+    return v;
+}
+
+// ----------------------------------------------------------------- kernels
+// Nodes fluid at t+1 without missing links: Lam^t(x) = C'(F(x))^T lambda(S^{t+1})(x);
+// solid nodes get Lam^t = 0; boundary nodes are left to the boundary adjoint.
+template <typename S>
+__global__ void __launch_bounds__(128) adjoint_bulk_kernel(const Lattice L, const GeomParams G,
+                                                           const S *__restrict__ st,
+                                                           const NextAdj<typename Codec<S>::R> A,
+                                                           const uint8_t *__restrict__ flags1,
+                                                           typename Codec<S>::R *__restrict__ lam_out)
+{
+    using R = typename Codec<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= L.nx) return;
+    const int n = x + L.nx * (y + L.ny * z);
+    const size_t N = (size_t)L.N;
+    const uint8_t f1 = flags1 ? flags1[n] : 0;
+    if (f1 & FL_SOLID) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lam_out[(size_t)i * N + n] = R(0);
+        return;
+    }
+    if (f1 & FL_BOUNDARY) return;
+    R lam[Q];
+    const bool interior = x > 0 && x < L.nx - 1 && y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1;
+    if (A.direct || !interior || (A.flags && (A.flags[n] & FL_UNCOVERED))) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lam[i] = next_adjoint<R>(L, G, A, x, y, z, n, i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            lam[i] = A.lam[(long long)i * (long long)N + n + (cx_of(i) + L.nx * (cy_of(i) + L.ny * cz_of(i)))];
+        if (A.ext) {
+            const int k = band_index(L, G, A.band, x, y, z);
+            if (k >= 0) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) lam[i] += (R)A.ext[(size_t)k * Q + i];
+            }
+        }
+    }
+    R g[Q];
+    gather_global<S>(L, st, x, y, z, n, g);
+    kbc_vjp<R>(g, lam, (R)L.beta, (R)L.inv_beta, (R)L.rho0, L.gamma_mode);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lam_out[(size_t)i * N + n] = lam[i];
+}
+
+// adds (ub . (c_m - u_k)) / rho_k + rb to ext[node k][m] for every lane k with a
+// non-zero velocity or density adjoint; all lanes m < 27 write one entry each
+template <typename R>
+__device__ __forceinline__ void scatter_moment_adjoints(const Lattice &L, const GeomParams &G, const DevBody *b,
+                                                        int lane, int nk, bool has, const R ubk[3], R rbk,
+                                                        const R (*su)[4], double *__restrict__ ext)
+{
+    unsigned m = __ballot_sync(FULL, has);
+    while (m) {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        const int node = __shfl_sync(FULL, nk, k);
+        const R u0 = __shfl_sync(FULL, ubk[0], k), u1 = __shfl_sync(FULL, ubk[1], k);
+        const R u2 = __shfl_sync(FULL, ubk[2], k), r = __shfl_sync(FULL, rbk, k);
+        int x, y, z;
+        node_xyz(L, node, x, y, z);
+        const int kb = band_index(L, G, b, x, y, z);
+        if (kb >= 0 && lane < Q) {
+            const R rho = su[k][0];
+            const R v = (u0 * (R(cx_of(lane)) - su[k][1]) + u1 * (R(cy_of(lane)) - su[k][2]) +
+                         u2 * (R(cz_of(lane)) - su[k][3])) / rho + r;
+            atomicAdd(ext + (size_t)kb * Q + lane, (double)v);
+        }
+    }
+}
+
+// fd_gradient transposed: velocity adjoints of the staged neighbourhood (lane
+// k) and of the centre velocity from du_bar
+template <typename R>
+__device__ __forceinline__ void fd_gradient_adj(const int *sok, const R dub[3][3], int lane, R unb[3], R ucb[3])
+{
+    const int step[3] = {9, 3, 1};
+    for (int b = 0; b < 3; ++b) {
+        const int kp = 13 + step[b], km = 13 - step[b];
+        const bool op = sok[kp], om = sok[km];
+        for (int a = 0; a < 3; ++a) {
+            const R v = dub[a][b];
+            if (op && om) {
+                if (lane == kp) unb[a] += R(0.5) * v;
+                if (lane == km) unb[a] -= R(0.5) * v;
+            } else if (op) {
+                if (lane == kp) unb[a] += v;
+                ucb[a] -= v;
+            } else if (om) {
+                ucb[a] += v;
+                if (lane == km) unb[a] -= v;
+            }
+        }
+    }
+}
+
+// transposes of grad_shifted and pressure_excess for lane-held gb = dJ/dg*_i:
+// accumulates rho_bar, u_bar (3) and du_bar (3x3)
+template <typename R>
+__device__ __forceinline__ void grad_pressure_adj(R gb, int i, bool act, R rho, const R u[3], const R du[3][3],
+                                                  R beta, R &rhob, R ub[3], R dub[3][3])
+{
+    const R cx = act ? R(cx_of(i)) : R(0), cy = act ? R(cy_of(i)) : R(0), cz = act ? R(cz_of(i)) : R(0);
+    const R w = act ? weight<R>(i) * gb : R(0);
+    const R cu = cx * u[0] + cy * u[1] + cz * u[2];
+    rhob += wsum(w * (R(1) + R(3) * cu));
+    ub[0] += wsum(w * R(3) * rho * cx);
+    ub[1] += wsum(w * R(3) * rho * cy);
+    ub[2] += wsum(w * R(3) * rho * cz);
+    const R third = R(1.0 / 3.0);
+    R Qb[6];
+    Qb[0] = wsum(w * R(4.5) * (cx * cx - third));
+    Qb[1] = wsum(w * R(4.5) * (cy * cy - third));
+    Qb[2] = wsum(w * R(4.5) * (cz * cz - third));
+    Qb[3] = wsum(w * R(9) * cx * cy);
+    Qb[4] = wsum(w * R(9) * cx * cz);
+    Qb[5] = wsum(w * R(9) * cy * cz);
+    // Qt_ab = rho u_a u_b - (rho / (6 beta)) (du_ab + du_ba)
+    const R k6 = R(1) / (R(6) * beta);
+    const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
+    for (int m = 0; m < 6; ++m) {
+        const int a = A[m], b = B[m];
+        rhob += Qb[m] * (u[a] * u[b] - k6 * (du[a][b] + du[b][a]));
+        ub[a] += Qb[m] * rho * u[b];
+        ub[b] += Qb[m] * rho * u[a];
+        dub[a][b] -= Qb[m] * rho * k6;
+        dub[b][a] -= Qb[m] * rho * k6;
+    }
+}
+
+struct ForceWeights {
+    double w[3];  // weights of the force of this step in J (already divided by the horizon)
+};
+
+// Boundary nodes of step t: forward recomputation of the Grad completion
+// (same operations as the boundary kernel), then its transpose.
+template <typename S>
+__global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
+    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ blist,
+    const int *__restrict__ bpos, const S *__restrict__ st, const NextAdj<typename Codec<S>::R> A,
+    const uint8_t *__restrict__ flags1, typename Codec<S>::R *__restrict__ lam_out, double *__restrict__ ext,
+    double *__restrict__ tslots, const ForceWeights fw)
+{
+    using R = typename Codec<S>::R;
+    __shared__ R s_f[BWARPS][Q][28];
+    __shared__ R s_u[BWARPS][Q][4];
+    __shared__ int s_ok[BWARPS][Q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    R (*sf)[28] = s_f[w];
+    R (*su)[4] = s_u[w];
+    int *sok = s_ok[w];
+    const int count = min(b->n_boundary, G.cap_boundary);
+    const size_t N = (size_t)L.N;
+    const R rho0 = (R)L.rho0, beta = (R)L.beta;
+
+    for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
+        const int n = blist[slot];
+        int x, y, z;
+        node_xyz(L, n, x, y, z);
+        const int i = lane;
+        const bool act = i < Q;
+        const int cx = act ? cx_of(i) : 0, cy = act ? cy_of(i) : 0, cz = act ? cz_of(i) : 0;
+        bool solid_src = false;
+        if (act && i != 13) {
+            const int src = pull_source(L, x, y, z, cx, cy, cz);
+            solid_src = src >= 0 && (flags1[src] & FL_SOLID);
+        }
+        const uint32_t mask = __ballot_sync(FULL, solid_src);
+        int nk = -1;
+        if (act) nk = neighbour(L, x, y, z, cx, cy, cz);
+        if (act) sok[lane] = nk >= 0 && !(flags1[nk] & FL_SOLID);
+        __syncwarp();
+        const uint32_t need = (1u << 13) | (1u << 22) | (1u << 4) | (1u << 16) | (1u << 10) |
+                              (1u << 14) | (1u << 12) | mask;
+        stage<S, R>(L, st, lane, nk, need, sf, su, sok);
+        const bool miss = act && ((mask >> i) & 1u);
+        // known pulls (face rules as in the bulk kernel)
+        R Fi = R(0);
+        if (act && !miss) {
+            int p[3] = {x - cx, y - cy, z - cz};
+            const int nn[3] = {L.nx, L.ny, L.nz};
+            int kind = 0;
+            for (int a = 0; a < 3; ++a) {
+                int face = -1;
+                if (p[a] < 0) face = L.face[2 * a];
+                else if (p[a] >= nn[a]) face = L.face[2 * a + 1];
+                if (face < 0) continue;
+                if (face == LBM_FACE_PERIODIC) p[a] = (p[a] + nn[a]) % nn[a];
+                else if (face == LBM_FACE_OUTFLOW) p[a] = p[a] < 0 ? 0 : nn[a] - 1;
+                else if (face == LBM_FACE_WALL) kind = 2;
+                else kind = kind > 1 ? kind : 1;
+            }
+            if (kind == 2) Fi = sf[13][26 - i];
+            else if (kind == 1) Fi = (R)L.g_face[i];
+            else Fi = Codec<S>::load(st + (size_t)i * N + (p[0] + L.nx * (p[1] + L.ny * p[2])));
+        }
+        const R fbb = act ? sf[13][26 - (act ? i : 0)] : R(0);
+        double q = 0, uw[3] = {0, 0, 0};
+        MeshHit hit{-1, 0.0, 0.0};
+        if (miss) link_data<R>(L, G, b, x, y, z, cx, cy, cz, q, uw, &hit);
+        const R gstat = miss ? fbb : Fi;
+        const R dyn = miss ? R(6) * weight<R>(i) * rho0 * (R(cx) * (R)uw[0] + R(cy) * (R)uw[1] + R(cz) * (R)uw[2])
+                           : R(0);
+        const R qq = (R)q;
+        R ut[3] = {0, 0, 0};
+        if (miss) {
+            if (sok[i]) {
+                for (int a = 0; a < 3; ++a) ut[a] = (qq * su[i][1 + a] + (R)uw[a]) / (R(1) + qq);
+            } else {
+                for (int a = 0; a < 3; ++a) ut[a] = (R)uw[a];
+            }
+        }
+        const R nmiss = R(__popc(mask));
+        const R rho_t = rho0 + wsum(act ? gstat : R(0)) + wsum(dyn);
+        R u_t[3];
+        for (int a = 0; a < 3; ++a) u_t[a] = wsum(ut[a]) / nmiss;
+        R du[3][3];
+        const R uc[3] = {su[13][1], su[13][2], su[13][3]};
+        fd_gradient<R>(su, sok, uc, du);
+        R Qt[6];
+        pressure_excess<R>(rho_t, u_t, du, beta, Qt);
+        R gi = Fi;
+        if (miss) gi = grad_shifted<R>(i, rho_t, rho0, u_t, Qt);
+
+        // ---- adjoint
+        const R lam = act ? next_adjoint<R>(L, G, A, x, y, z, n, i) : R(0);
+        R Fb = kbc_vjp_lanes<R>(gi, lam, i, beta, (R)L.inv_beta, rho0, L.gamma_mode);
+        // momentum exchange in J: dF_a = (-c_a - uw_a) fout - (c_a - uw_a) fin
+        double uwb[3] = {0, 0, 0};
+        R fbbb = 0;
+        if (miss) {
+            const double Wr = weight<double>(i) * L.rho0;
+            const double fout = (double)fbb + Wr, fin = (double)gi + Wr;
+            const double c[3] = {(double)cx, (double)cy, (double)cz};
+            double sin_ = 0, sout = 0;
+            for (int a = 0; a < 3; ++a) {
+                sin_ -= (c[a] - uw[a]) * fw.w[a];
+                sout += (-c[a] - uw[a]) * fw.w[a];
+                uwb[a] += fw.w[a] * (fin - fout);
+            }
+            Fb += (R)sin_;
+            fbbb += (R)sout;
+        }
+        // Grad completion (missing lanes) and pressure excess
+        R rhob = 0, utb[3] = {0, 0, 0}, dub[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        grad_pressure_adj<R>(miss ? Fb : R(0), i, act, rho_t, u_t, du, beta, rhob, utb, dub);
+        // u_t = mean over missing links of (q u_f + u_w)/(1 + q), or u_w
+        R unb[3] = {0, 0, 0}, ucb[3] = {0, 0, 0};
+        double qb = 0;
+        if (miss) {
+            const R inv1q = R(1) / (R(1) + qq);
+            for (int a = 0; a < 3; ++a) {
+                const R v = utb[a] / nmiss;
+                if (sok[i]) {
+                    unb[a] += v * qq * inv1q;
+                    uwb[a] += (double)(v * inv1q);
+                    qb += (double)(v * (su[i][1 + a] - (R)uw[a]) * inv1q * inv1q);
+                } else {
+                    uwb[a] += (double)v;
+                }
+            }
+        }
+        // rho_t = rho0 + sum gstat + sum dyn
+        R lam_row = 0;
+        if (act && !miss) lam_row = Fb + rhob;
+        if (miss) {
+            fbbb += rhob;
+            for (int a = 0; a < 3; ++a)
+                uwb[a] += (double)(rhob * R(6) * weight<R>(i) * rho0 * R(a == 0 ? cx : a == 1 ? cy : cz));
+        }
+        fd_gradient_adj<R>(sok, dub, lane, unb, ucb);
+        if (lane == 13)
+            for (int a = 0; a < 3; ++a) unb[a] += ucb[a];
+        // outputs: Lam row of this node, ext at this node and at the neighbours
+        if (act) lam_out[(size_t)i * N + n] = lam_row;
+        const int kb = band_index(L, G, b, x, y, z);
+        if (miss && kb >= 0) atomicAdd(ext + (size_t)kb * Q + (26 - i), (double)fbbb);
+        const bool has = act && nk >= 0 && (unb[0] != R(0) || unb[1] != R(0) || unb[2] != R(0));
+        scatter_moment_adjoints<R>(L, G, b, lane, nk, has, unb, R(0), su, ext);
+        // parameters: dJ/dtheta through q and u_w of each missing link
+        double tb[3] = {0, 0, 0};
+        if (miss && G.kind == LBM_BODY_MESH) {
+            double dq[3], duw[3][3];
+            mesh_link_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
+            for (int k = 0; k < 3; ++k) tb[k] = qb * dq[k] + uwb[0] * duw[k][0] + uwb[1] * duw[k][1] + uwb[2] * duw[k][2];
+        }
+        for (int k = 0; k < 3; ++k) {
+            double v = tb[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] = v;
+        }
+        __syncwarp();
+    }
+}
+
+// Refilled nodes of step t: transpose of the refill (Grad distribution of the
+// neighbour-mean density, the body velocity and the finite-difference
+// gradient), fed by lambda(St^t) at the node.
+template <typename S>
+__global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
+    const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
+    const int *__restrict__ upos, const S *__restrict__ st, const typename Codec<S>::R *__restrict__ lam_t,
+    const uint8_t *__restrict__ flags1, double *__restrict__ ext, double *__restrict__ tslots)
+{
+    using R = typename Codec<S>::R;
+    __shared__ R s_f[BWARPS][Q][28];
+    __shared__ R s_u[BWARPS][Q][4];
+    __shared__ int s_ok[BWARPS][Q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    R (*sf)[28] = s_f[w];
+    R (*su)[4] = s_u[w];
+    int *sok = s_ok[w];
+    const int count = min(b->n_uncovered, G.cap_uncovered);
+    const R rho0 = (R)L.rho0, beta = (R)L.beta;
+    for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
+        const int n = ulist[slot];
+        int x, y, z;
+        node_xyz(L, n, x, y, z);
+        const bool act = lane < Q;
+        int nk = -1;
+        if (act && lane != 13) nk = neighbour(L, x, y, z, cx_of(lane), cy_of(lane), cz_of(lane));
+        if (act) sok[lane] = nk >= 0 && !(flags1[nk] & FL_SOLID_PREV);
+        __syncwarp();
+        const uint32_t need = __ballot_sync(FULL, act && sok[lane]);
+        stage<S, R>(L, st, lane, nk, need, sf, su, sok);
+        const R cnt = R(__popc(need));
+        const R rsum = wsum((act && sok[lane]) ? su[lane][0] : R(0));
+        const R rho = cnt > R(0) ? rsum / cnt : rho0;
+        double ud[3] = {b->U[0], b->U[1], b->U[2]};
+        if (G.kind == LBM_BODY_PLANES) {
+            const double *v = (double)y < 0.5 * (G.y_lo + G.y_hi) ? G.U_lo : G.U_hi;
+            ud[0] = v[0]; ud[1] = v[1]; ud[2] = v[2];
+        } else if (G.kind == LBM_BODY_MESH) {
+            swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - b->X[0]), ud);
+        }
+        const R u[3] = {(R)ud[0], (R)ud[1], (R)ud[2]};
+        R du[3][3];
+        fd_gradient<R>(su, sok, u, du);
+        // adjoint of the refilled populations: lambda(St^t) at the node
+        R lam = 0;
+        if (act) {
+            lam = pull_transpose<R>(L, lam_t, x, y, z, lane);
+            const int kb = band_index(L, G, b, x, y, z);
+            if (kb >= 0) lam += (R)ext[(size_t)kb * Q + lane];
+        }
+        R rhob = 0, ub[3] = {0, 0, 0}, dub[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        grad_pressure_adj<R>(lam, lane, act, rho, u, du, beta, rhob, ub, dub);
+        R unb[3] = {0, 0, 0}, ucb[3] = {0, 0, 0};
+        fd_gradient_adj<R>(sok, dub, lane, unb, ucb);
+        for (int a = 0; a < 3; ++a) ub[a] += ucb[a];
+        // rho = mean of the neighbours' densities
+        const R rkb = (act && sok[lane] && cnt > R(0)) ? rhob / cnt : R(0);
+        const bool has = act && sok[lane] && (rkb != R(0) || unb[0] != R(0) || unb[1] != R(0) || unb[2] != R(0));
+        scatter_moment_adjoints<R>(L, G, b, lane, nk, has, unb, rkb, su, ext);
+        // parameters through the body velocity
+        double tb[3] = {0, 0, 0};
+        if (lane == 0 && G.kind == LBM_BODY_MESH) {
+            double dv[3];
+            swimmer_velocity_tangent(G, b->t, clamp_arc(G, (double)x - b->X[0]), dv);
+            for (int k = 0; k < 3; ++k) tb[k] = (double)ub[1] * dv[k];
+        }
+        if (lane == 0)
+            for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] = tb[k];
+        __syncwarp();
+    }
+}
+
+// acc[k] += sum over band slots of slot[6 s + k] + slot[6 s + 3 + k], fixed order
+__global__ void __launch_bounds__(256) theta_reduce_kernel(const double *__restrict__ slots, int nslots,
+                                                            double *__restrict__ acc)
+{
+    __shared__ double sm[256][3];
+    double v[3] = {0, 0, 0};
+    for (int s = threadIdx.x; s < nslots; s += 256)
+        for (int k = 0; k < 3; ++k) v[k] += slots[(size_t)s * 6 + k] + slots[(size_t)s * 6 + 3 + k];
+    for (int k = 0; k < 3; ++k) sm[threadIdx.x][k] = v[k];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int k = 0; k < 3; ++k) sm[threadIdx.x][k] += sm[threadIdx.x + h][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) acc[threadIdx.x] += sm[0][threadIdx.x];
+}
+
+// lambda(S^0): the transpose of step 0's pull and band contributions, zero at
+// nodes refilled in step 0
+template <typename R>
+__global__ void lambda0_kernel(const Lattice L, const GeomParams G, const NextAdj<R> A, R *__restrict__ out)
+{
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((long long)L.nx * L.ny));
+    for (int i = 0; i < Q; ++i) out[(size_t)i * (size_t)L.N + n] = next_adjoint<R>(L, G, A, x, y, z, (int)n, i);
+}
+
+// per-block partial sums of lambda_T . f over nodes fluid at the end
+template <typename S>
+__global__ void __launch_bounds__(256) terminal_kernel(const Lattice L, const S *__restrict__ f,
+                                                        const typename Codec<S>::R *__restrict__ lamT,
+                                                        const uint8_t *__restrict__ flags, double *__restrict__ part)
+{
+    __shared__ double sm[256];
+    double acc = 0;
+    for (long long n = blockIdx.x * 256LL + threadIdx.x; n < L.N; n += (long long)gridDim.x * 256) {
+        if (flags && (flags[n] & FL_SOLID)) continue;
+        for (int i = 0; i < Q; ++i) {
+            const size_t k = (size_t)i * (size_t)L.N + n;
+            acc += (double)lamT[k] * ((double)Codec<S>::load(f + k) + weight<double>(i) * L.rho0);
+        }
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+}  // namespace lbm
+
+// ----------------------------------------------------------------- driver
+using namespace lbm;
+
+namespace {
+
+lbm_status afail(lbm_ctx *c, lbm_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+#define ADJ_CUDA(call, where)                                                                           \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            st = afail(ctx, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_));          \
+            goto done;                                                                                  \
+        }                                                                                               \
+    } while (0)
+
+// device buffers of one adjoint call, released together
+struct AdjBuffers {
+    std::vector<void *> ptrs;
+    template <typename T>
+    bool get(T **p, size_t count)
+    {
+        void *v = nullptr;
+        if (cudaMalloc(&v, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+            *p = nullptr;
+            return false;
+        }
+        ptrs.push_back(v);
+        *p = static_cast<T *>(v);
+        return true;
+    }
+    ~AdjBuffers()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+};
+
+// one forward step from fa into fb with the context's body scratch and the
+// given marks (the same launch sequence as lbm_step)
+cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
+{
+    int nl = 0;
+    cudaError_t e;
+    const uint8_t *fl = ctx->has_body ? flags : nullptr;
+    int cur = ctx->bcur;
+    int *status = &ctx->S.body[cur].status;
+    if (ctx->has_body) {
+        const int prev = ctx->bcur;
+        cur = prev ^ 1;
+        status = &ctx->S.body[cur].status;
+        if ((e = launch_geometry(ctx->L, ctx->G, ctx->S, prev, flags, ctx->stream, &nl)) != cudaSuccess) return e;
+        if ((e = launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, flags, ctx->stream)) != cudaSuccess)
+            return e;
+        if ((e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->stream)) != cudaSuccess)
+            return e;
+        if ((e = launch_forces(ctx->G, ctx->S, cur, ctx->stream, &nl)) != cudaSuccess) return e;
+    }
+    if ((e = launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream)) != cudaSuccess) return e;
+    ctx->bcur = cur;
+    return cudaSuccess;
+}
+
+int list_blocks(int cap)
+{
+    int nb = (cap + BWARPS - 1) / BWARPS;
+    return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
+}
+
+// the reverse of step t (body state of step t in S.body[bcur], marks of step t
+// in flags1 after the geometry re-run) for storage type S
+template <typename S>
+cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
+                         typename Codec<S>::R *lam_out, double *ext, double *tslots, const ForceWeights &fw,
+                         double *acc)
+{
+    using R = typename Codec<S>::R;
+    const Lattice &L = ctx->L;
+    const GeomParams &G = ctx->G;
+    Scratch &Sc = ctx->S;
+    const DevBody *b = Sc.body + ctx->bcur;
+    cudaStream_t s = ctx->stream;
+    const int cap = ctx->has_body ? G.cap[0] * G.cap[1] * G.cap[2] : 0;
+    if (ctx->has_body) {
+        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, s>>>(
+            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, fw);
+    }
+    const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
+    dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
+    adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, ctx->has_body ? flags1 : nullptr, lam_out);
+    if (ctx->has_body) {
+        adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
+            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots);
+        theta_reduce_kernel<<<1, 256, 0, s>>>(tslots, cap, acc);
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double dJ[3])
+{
+    using R = typename Codec<S>::R;
+    const Lattice &L = ctx->L;
+    const size_t N = (size_t)L.N;
+    const size_t state = 27 * N;
+    const int T = spec->horizon;
+    int K = spec->checkpoint_every > 0 ? spec->checkpoint_every : (int)std::ceil(std::sqrt((double)T));
+    if (K > T) K = T;
+    const int nseg = (T + K - 1) / K;
+    const bool body = ctx->has_body;
+    const int cap = body ? ctx->G.cap[0] * ctx->G.cap[1] * ctx->G.cap[2] : 1;
+    cudaStream_t s = ctx->stream;
+    lbm_status st = LBM_OK;
+    AdjBuffers B;
+    S *ck = nullptr, *seg = nullptr;
+    uint8_t *ckflags = nullptr, *segflags = nullptr, *wf[2] = {nullptr, nullptr}, *wrec = nullptr;
+    DevBody *ckbody = nullptr, *segbody = nullptr, *adjbody = nullptr, *savebody = nullptr;
+    R *lam[2] = {nullptr, nullptr};
+    double *ext[2] = {nullptr, nullptr}, *tslots = nullptr, *acc = nullptr, *part = nullptr;
+    double F0[3] = {0, 0, 0}, F1[3] = {0, 0, 0}, accv[3] = {0, 0, 0};
+    ForceWeights fw{{spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}};
+    DevBody hb{};
+    int p = 0;
+    const int save_bcur = ctx->bcur;
+    const int nparts = 1024;
+    double Jt = 0.0;
+
+    if (!B.get(&ck, (size_t)nseg * state) || !B.get(&seg, (size_t)(K + 1) * state) ||
+        !B.get(&ckflags, (size_t)nseg * N) || !B.get(&segflags, (size_t)K * N) || !B.get(&wf[0], N) ||
+        !B.get(&wf[1], N) || !B.get(&wrec, N) || !B.get(&ckbody, nseg) || !B.get(&segbody, K) || !B.get(&adjbody, 2) ||
+        !B.get(&savebody, 2) || !B.get(&lam[0], state) || !B.get(&lam[1], state) ||
+        !B.get(&ext[0], (size_t)cap * Q) || !B.get(&ext[1], (size_t)cap * Q) || !B.get(&tslots, (size_t)cap * 6) ||
+        !B.get(&acc, 3) || !B.get(&part, nparts))
+        return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the checkpoints failed");
+
+    // ---- forward over the horizon with checkpoints
+    ADJ_CUDA(cudaMemcpyAsync(&hb, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToHost, s), "body read");
+    ADJ_CUDA(cudaStreamSynchronize(s), "sync");
+    for (int a = 0; a < 3; ++a) F0[a] = hb.F_sum[a];
+    for (int t = 0; t < T; ++t) {
+        if (t % K == 0) {
+            const int k = t / K;
+            ADJ_CUDA(cudaMemcpyAsync(ck + (size_t)k * state, ctx->f[ctx->cur], state * sizeof(S),
+                                     cudaMemcpyDeviceToDevice, s), "checkpoint");
+            ADJ_CUDA(cudaMemcpyAsync(ckflags + (size_t)k * N, ctx->flags, N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+            ADJ_CUDA(cudaMemcpyAsync(ckbody + k, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToDevice, s),
+                     "checkpoint");
+        }
+        st = lbm_step(ctx, 1);
+        if (st != LBM_OK) goto done;
+    }
+    ADJ_CUDA(cudaMemcpyAsync(&hb, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToHost, s), "body read");
+    ADJ_CUDA(cudaMemcpyAsync(savebody, ctx->S.body, 2 * sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "body save");
+    if (spec->lambda_T) {
+        terminal_kernel<S><<<nparts, 256, 0, s>>>(L, (const S *)ctx->f[ctx->cur], (const R *)spec->lambda_T,
+                                                  body ? ctx->flags : nullptr, part);
+        std::vector<double> hp(nparts);
+        ADJ_CUDA(cudaMemcpyAsync(hp.data(), part, nparts * sizeof(double), cudaMemcpyDeviceToHost, s), "terminal");
+        ADJ_CUDA(cudaStreamSynchronize(s), "sync");
+        for (int k = 0; k < nparts; ++k) Jt += hp[k];
+    }
+    ADJ_CUDA(cudaStreamSynchronize(s), "sync");
+    if (hb.status & ST_UNSTABLE) {
+        st = afail(ctx, LBM_ERR_UNSTABLE, "lbm_adjoint_step: a node went unstable in the forward run");
+        goto done;
+    }
+    for (int a = 0; a < 3; ++a) F1[a] = hb.F_sum[a];
+    *J = Jt;
+    for (int a = 0; a < 3; ++a) *J += spec->w_force[a] * (F1[a] - F0[a]) / T;
+
+    // ---- reverse sweep, one recomputed segment at a time
+    ADJ_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s), "clear");
+    {
+        bool first = true;
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            const int t0 = sg * K, t1 = std::min(T, t0 + K);
+            // recompute the segment: seg[j] holds St^{t0+j} once step t0+j has run
+            ADJ_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sg * state, state * sizeof(S), cudaMemcpyDeviceToDevice, s),
+                     "restore");
+            ADJ_CUDA(cudaMemcpyAsync(wrec, ckflags + (size_t)sg * N, N, cudaMemcpyDeviceToDevice, s), "restore");
+            ctx->bcur = 0;
+            ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, ckbody + sg, sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "restore");
+            for (int t = t0; t < t1; ++t) {
+                const int j = t - t0;
+                ADJ_CUDA(cudaMemcpyAsync(segflags + (size_t)j * N, wrec, N, cudaMemcpyDeviceToDevice, s), "seg flags");
+                ADJ_CUDA(cudaMemcpyAsync(segbody + j, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToDevice,
+                                         s), "seg body");
+                ADJ_CUDA(forward_step(ctx, seg + (size_t)j * state, seg + (size_t)(j + 1) * state, wrec), "recompute");
+            }
+            // reverse the segment's steps
+            for (int t = t1 - 1; t >= t0; --t) {
+                const int j = t - t0;
+                ADJ_CUDA(cudaMemcpyAsync(wf[p], segflags + (size_t)j * N, N, cudaMemcpyDeviceToDevice, s), "flags");
+                ctx->bcur = 0;
+                ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, segbody + j, sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "body");
+                if (body) {
+                    int nl = 0;
+                    ADJ_CUDA(launch_geometry(L, ctx->G, ctx->S, 0, wf[p], s, &nl), "geometry");
+                    ctx->bcur = 1;
+                    ADJ_CUDA(cudaMemsetAsync(ext[p], 0, (size_t)cap * Q * sizeof(double), s), "clear");
+                    ADJ_CUDA(cudaMemsetAsync(tslots, 0, (size_t)cap * 6 * sizeof(double), s), "clear");
+                }
+                NextAdj<R> A;
+                if (first) {
+                    A = NextAdj<R>{(const R *)spec->lambda_T, nullptr, nullptr, nullptr, 1};
+                } else {
+                    A = NextAdj<R>{lam[p ^ 1], body ? ext[p ^ 1] : nullptr, adjbody + (p ^ 1),
+                                   body ? wf[p ^ 1] : nullptr, 0};
+                }
+                ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, fw, acc),
+                         "reverse step");
+                if (body)
+                    ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),
+                                             cudaMemcpyDeviceToDevice, s), "band");
+                first = false;
+                p ^= 1;
+            }
+        }
+        // lambda(S^0) from the last reversed step (step 0)
+        if (spec->lambda_0) {
+            NextAdj<R> A{lam[p ^ 1], body ? ext[p ^ 1] : nullptr, adjbody + (p ^ 1), body ? wf[p ^ 1] : nullptr, 0};
+            lambda0_kernel<R><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, ctx->G, A, (R *)spec->lambda_0);
+            ADJ_CUDA(cudaGetLastError(), "lambda0");
+        }
+    }
+    ADJ_CUDA(cudaMemcpyAsync(accv, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "theta");
+    ADJ_CUDA(cudaStreamSynchronize(s), "sync");
+    for (int k = 0; k < 3; ++k) dJ[k] = accv[k];
+
+done:
+    // the context keeps the state after the horizon; restore its body copies
+    cudaMemcpyAsync(ctx->S.body, savebody, 2 * sizeof(DevBody), cudaMemcpyDeviceToDevice, s);
+    ctx->bcur = save_bcur;
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double dJ_dtheta[3])
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!spec || !J || !dJ_dtheta) return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: null argument");
+    if (spec->horizon < 1 || spec->checkpoint_every < 0)
+        return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: horizon >= 1 and checkpoint_every >= 0 required");
+    for (int k = 0; k < 4; ++k)
+        if (spec->reserved[k] != 0) return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: reserved fields must be 0");
+    if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
+    if (ctx->has_body && (ctx->G.free_motion || ctx->G.kind == LBM_BODY_AIRFOIL))
+        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held body (no free motion, no airfoil)");
+    for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
+    *J = 0.0;
+    if (ctx->storage == LBM_FP64) return adjoint_run<double>(ctx, spec, J, dJ_dtheta);
+    if (ctx->storage == LBM_FP32) return adjoint_run<float>(ctx, spec, J, dJ_dtheta);
+    return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: FP64 or FP32 storage only");
+}

@@ -10,34 +10,9 @@
 #include <string>
 #include <vector>
 
-#include "body.cuh"
+#include "ctx.cuh"
 
 using namespace lbm;
-
-struct lbm_ctx {
-    Lattice L;
-    int storage = 0;
-    size_t elem = 0;
-    void *f[2] = {nullptr, nullptr};
-    int cur = 0;
-    uint8_t *flags = nullptr;
-    cudaStream_t stream = nullptr;
-    GeomParams G{};
-    bool has_body = false;
-    bool initialised = false;
-    Scratch S{};
-    int bcur = 0;                 // body copy holding the latest state
-    cudaStream_t side = nullptr;  // boundary + force kernels, overlapping the bulk kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    double *plane = nullptr;      // N doubles for the host codec
-    double *tot_partials = nullptr;
-    int tot_blocks = 608;
-    int64_t launches = 0;
-    std::vector<cudaEvent_t> prof;  // start/stop pairs around bulk launches
-    int prof_used = 0;
-    bool prof_open = false;
-    std::string err;
-};
 
 namespace {
 
@@ -102,7 +77,7 @@ cudaError_t dalloc(T **p, size_t count)
 
 void free_scratch(Scratch &S, bool keep_body)
 {
-    cudaFree(S.blist); cudaFree(S.bpos); cudaFree(S.ulist); cudaFree(S.bforce);
+    cudaFree(S.blist); cudaFree(S.bpos); cudaFree(S.ulist); cudaFree(S.upos); cudaFree(S.bforce);
     cudaFree(S.partials); cudaFree(S.ticket);
     cudaFree(S.mesh_rest); cudaFree(S.mesh_pos); cudaFree(S.mesh_vel); cudaFree(S.col_x);
     cudaFree(S.mesh_tris); cudaFree(S.col_count); cudaFree(S.cell_count); cudaFree(S.cell_tri);
@@ -334,7 +309,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     bool ok = true;
     if (ctx->has_body) {
         ok = dalloc(&S.blist, vol) == cudaSuccess && dalloc(&S.bpos, vol) == cudaSuccess &&
-             dalloc(&S.ulist, vol) == cudaSuccess && dalloc(&S.bforce, vol * 6) == cudaSuccess &&
+             dalloc(&S.ulist, vol) == cudaSuccess && dalloc(&S.upos, vol) == cudaSuccess &&
+             dalloc(&S.bforce, vol * 6) == cudaSuccess &&
              dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess && dalloc(&S.ticket, 1) == cudaSuccess;
         if (ok) ok = cudaMemsetAsync(S.ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
     }

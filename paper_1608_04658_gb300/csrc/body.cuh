@@ -66,6 +66,7 @@ struct Scratch {
     int *blist;          // [cap_boundary] node index of each boundary node
     int *bpos;           // [cap_boundary] band position of each boundary node
     int *ulist;          // [cap_uncovered] node index of each uncovered node
+    int *upos;           // [cap_uncovered] band position of each uncovered node
     double *bforce;      // [band capacity * 6] force and torque per band position
     double *partials;    // [n_partials * 6]
     unsigned *ticket;    // last-block counter of the force reduction

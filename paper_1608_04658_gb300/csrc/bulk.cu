@@ -9,62 +9,9 @@
 // the boundary kernel.
 #include <type_traits>
 
-#include "kbc.cuh"
+#include "pull.cuh"
 
 namespace lbm {
-
-// Relative source offsets for velocity component c = -1, 0, +1 of a pull from
-// a - c along one axis (stride = element distance of one step on that axis),
-// and the kind of the source: 0 node in the box (wrapped on periodic faces,
-// clamped on outflow faces), 1 equilibrium face, 2 wall face.
-__device__ __forceinline__ void axis_off(int a, int n, int stride, int face_lo, int face_hi,
-                                         int o[3], int k[3])
-{
-    o[1] = 0;
-    k[1] = 0;
-    // c = +1 pulls from a - 1
-    o[2] = -stride;
-    k[2] = 0;
-    if (a == 0) {
-        o[2] = 0;
-        if (face_lo == LBM_FACE_PERIODIC) o[2] = (n - 1) * stride;
-        else if (face_lo == LBM_FACE_WALL) k[2] = 2;
-        else if (face_lo == LBM_FACE_EQ) k[2] = 1;
-    }
-    // c = -1 pulls from a + 1
-    o[0] = stride;
-    k[0] = 0;
-    if (a == n - 1) {
-        o[0] = 0;
-        if (face_hi == LBM_FACE_PERIODIC) o[0] = -(n - 1) * stride;
-        else if (face_hi == LBM_FACE_WALL) k[0] = 2;
-        else if (face_hi == LBM_FACE_EQ) k[0] = 1;
-    }
-}
-
-// pulls of node (x, y, z) from global memory under the box rules
-template <typename S>
-__device__ __forceinline__ void gather_global(const Lattice &L, const S *__restrict__ fa, int x, int y, int z,
-                                              int n, typename Codec<S>::R g[Q])
-{
-    using R = typename Codec<S>::R;
-    int ox[3], oy[3], oz[3], kx[3], ky[3], kz[3];
-    axis_off(x, L.nx, 1, L.face[0], L.face[1], ox, kx);
-    axis_off(y, L.ny, L.nx, L.face[2], L.face[3], oy, ky);
-    axis_off(z, L.nz, L.nx * L.ny, L.face[4], L.face[5], oz, kz);
-    const S *p = fa + n;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        g[i] = Codec<S>::load(p + (L.plane[i] + ox[cx_of(i) + 1] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1]));
-    if (kx[0] | kx[2] | ky[0] | ky[2] | kz[0] | kz[2]) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int k = max(kx[cx_of(i) + 1], max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]));
-            if (k == 2) g[i] = Codec<S>::load(p + L.plane[26 - i]);
-            else if (k == 1) g[i] = (R)L.g_face[i];
-        }
-    }
-}
 
 // Minimum resident blocks per SM requested from the register allocator: 7
 // blocks of 128 threads cap the kernel at 72 registers (a 32-byte spill) and

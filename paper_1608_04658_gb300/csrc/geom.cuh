@@ -153,6 +153,13 @@ __device__ __forceinline__ bool mesh_inside_column(const GeomParams &G, int col,
     return k & 1;
 }
 
+// triangle hit by a link and the barycentric coordinates of the wall point
+// (tri = -1 for the no-hit fallback)
+struct MeshHit {
+    int tri;
+    double u, v;
+};
+
 __device__ __forceinline__ double det3(const double a[3], const double b[3], const double d[3])
 {
     return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) + a[2] * (b[0] * d[1] - b[1] * d[0]);
@@ -164,8 +171,10 @@ __device__ __forceinline__ double det3(const double a[3], const double b[3], con
 // No hit (round-off at an edge): q = 1/2 and the material velocity at the
 // link's midpoint.
 __device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
-                          double &q, double uw[3])
+                          double &q, double uw[3], MeshHit *hit)
 {
+    int bt = -1;
+    double bu = 0.0, bv = 0.0;
     const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
     int c0[3], c1[3];
     float lo[3], hi[3];
@@ -207,6 +216,9 @@ __device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody
                     const double s = det3(e1, e2, r) / D;
                     if (u < 0.0 || v < 0.0 || u + v > 1.0 || s < 0.0 || s > 1.0 || !(s < best)) continue;
                     best = s;
+                    bt = k;
+                    bu = u;
+                    bv = v;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         uw[a] = (1.0 - u - v) * G.mesh_vel[3 * t0 + a] + u * G.mesh_vel[3 * t1 + a] +
@@ -215,9 +227,15 @@ __device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody
             }
     if (best > 1.0) {
         best = 0.5;
+        bt = -1;
         swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
     }
     q = best;
+    if (hit) {
+        hit->tri = bt;
+        hit->u = bu;
+        hit->v = bv;
+    }
 }
 
 // Single-precision forms of the link search, used when the populations are
@@ -231,7 +249,7 @@ __device__ __forceinline__ float det3f(const float a[3], const float b[3], const
 }
 
 __device__ __noinline__ static void mesh_link_f(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx,
-                                                int cy, int cz, double &q, double uw[3])
+                                                int cy, int cz, double &q, double uw[3], MeshHit *hit)
 {
     constexpr float EPS = 1e-6f;  // barycentric slack: a link through a shared edge hits one of its triangles
     const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
@@ -285,6 +303,11 @@ __device__ __noinline__ static void mesh_link_f(const GeomParams &G, const DevBo
                     bt = k;
                 }
             }
+    if (hit) {
+        hit->tri = bt;
+        hit->u = bu;
+        hit->v = bv;
+    }
     if (bt < 0) {
         q = 0.5;
         swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
@@ -369,12 +392,12 @@ __device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int z, 
 template <typename R>
 __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G, const DevBody *b,
                                           int x, int y, int z, int cx, int cy, int cz, double &q,
-                                          double uw[3])
+                                          double uw[3], MeshHit *hit = nullptr)
 {
     constexpr bool single = sizeof(R) == 4;
     if (G.kind == LBM_BODY_MESH) {
-        if (single) mesh_link_f(G, b, x, y, z, cx, cy, cz, q, uw);
-        else mesh_link(G, b, x, y, z, cx, cy, cz, q, uw);
+        if (single) mesh_link_f(G, b, x, y, z, cx, cy, cz, q, uw, hit);
+        else mesh_link(G, b, x, y, z, cx, cy, cz, q, uw, hit);
     } else if (G.kind == LBM_BODY_AIRFOIL && single) {
         q = link_airfoil_f(G, b, x, y, cx, cy);
         uw[0] = b->U[0];
@@ -415,6 +438,114 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
         uw[0] = v[0];
         uw[1] = v[1];
         uw[2] = v[2];
+    }
+}
+
+// ---------------------------------------------------------------- swimmer tangents
+// Derivatives with respect to theta = (wave_amp, wave_length, wave_period) of
+// the midline y(s,t) = r(t) a env(s) sin(phi), env = L (s/L + 0.03125)/1.03125,
+// phi = 2 pi (s/lambda - t/T), r the optional ramp (1 - cos(pi t/T))/2 on
+// [0, T):
+//   dy/da = r env sin(phi),  dy/dlambda = -r a env cos(phi) 2 pi s/lambda^2,
+//   dy/dT = r a env cos(phi) 2 pi t/T^2 + (dr/dT) a env sin(phi),
+//   dr/dT = -(1/2) sin(pi t/T) pi t/T^2.
+__device__ __forceinline__ void swimmer_midline_tangent(const GeomParams &G, double s, double t, double d[3])
+{
+    const double T = G.wave_period, lam = G.wave_length, a = G.wave_amp;
+    double r = 1.0, drT = 0.0;
+    if (G.wave_ramp) {
+        if (t < 0.0) r = 0.0;
+        else if (t < T) {
+            r = 0.5 * (1.0 - cos(MESH_PI * t / T));
+            drT = -0.5 * sin(MESH_PI * t / T) * MESH_PI * t / (T * T);
+        }
+    }
+    const double env = G.length * (s / G.length + 0.03125) / 1.03125;
+    const double ph = 2.0 * MESH_PI * (s / lam - t / T);
+    const double sn = sin(ph), cs = cos(ph);
+    d[0] = r * env * sn;
+    d[1] = -r * a * env * cs * 2.0 * MESH_PI * s / (lam * lam);
+    d[2] = r * a * env * cs * 2.0 * MESH_PI * t / (T * T) + drT * a * env * sn;
+}
+
+// theta-tangent of the material velocity (only its y component moves):
+// the central difference (dy(s,t+1) - dy(s,t-1))/2
+__device__ __forceinline__ void swimmer_velocity_tangent(const GeomParams &G, double t, double s, double dv[3])
+{
+    double d1[3], d0[3];
+    swimmer_midline_tangent(G, s, t + 1.0, d1);
+    swimmer_midline_tangent(G, s, t - 1.0, d0);
+    for (int k = 0; k < 3; ++k) dv[k] = 0.5 * (d1[k] - d0[k]);
+}
+
+// theta-tangents of a mesh link's fraction q and wall velocity u_w.  The wall
+// point H = x_b - q c lies on the plane n.(H - A) = 0 of the hit triangle
+// (A, B, C), n = (B - A) x (C - A), so dq = (dn.(H - A) - n.dA)/(n.c); the
+// barycentric coordinates follow from dH - dA = du e1 + dv e2 + u de1 + v de2
+// (normal equations with e1, e2); u_w = (1-u-v) V_A + u V_B + v V_C.  Vertex
+// positions move only in y, by the midline tangent at the pose's time.
+__device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
+                                  double q, const MeshHit &h, double dq[3], double duw[3][3])
+{
+    if (h.tri < 0) {
+        double dv[3];
+        swimmer_velocity_tangent(G, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), dv);
+        for (int k = 0; k < 3; ++k) {
+            dq[k] = 0.0;
+            duw[k][0] = 0.0;
+            duw[k][1] = dv[k];
+            duw[k][2] = 0.0;
+        }
+        return;
+    }
+    const int tv[3] = {G.mesh_tris[3 * h.tri], G.mesh_tris[3 * h.tri + 1], G.mesh_tris[3 * h.tri + 2]};
+    double P[3][3], V[3][3], dy[3][3], dvy[3][3];
+    for (int m = 0; m < 3; ++m) {
+        for (int a = 0; a < 3; ++a) {
+            P[m][a] = G.mesh_pos[3 * tv[m] + a];
+            V[m][a] = G.mesh_vel[3 * tv[m] + a];
+        }
+        const double s = G.mesh_rest[3 * tv[m]];
+        swimmer_midline_tangent(G, s, b->t, dy[m]);
+        swimmer_velocity_tangent(G, b->t, s, dvy[m]);
+    }
+    const double c[3] = {(double)cx, (double)cy, (double)cz};
+    double e1[3], e2[3], H[3], n[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = P[1][a] - P[0][a];
+        e2[a] = P[2][a] - P[0][a];
+    }
+    H[0] = (double)x - q * c[0] - P[0][0];
+    H[1] = (double)y - q * c[1] - P[0][1];
+    H[2] = (double)z - q * c[2] - P[0][2];
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double nc = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+    const double g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const double gdet = g11 * g22 - g12 * g12;
+    for (int k = 0; k < 3; ++k) {
+        // vertex displacements along y only
+        const double dA = dy[0][k], dB = dy[1][k], dC = dy[2][k];
+        const double de1[3] = {0.0, dB - dA, 0.0}, de2[3] = {0.0, dC - dA, 0.0};
+        double dn[3];
+        dn[0] = de1[1] * e2[2] - de1[2] * e2[1] + e1[1] * de2[2] - e1[2] * de2[1];
+        dn[1] = de1[2] * e2[0] - de1[0] * e2[2] + e1[2] * de2[0] - e1[0] * de2[2];
+        dn[2] = de1[0] * e2[1] - de1[1] * e2[0] + e1[0] * de2[1] - e1[1] * de2[0];
+        const double ds = nc != 0.0 ? ((dn[0] * H[0] + dn[1] * H[1] + dn[2] * H[2]) - n[1] * dA) / nc : 0.0;
+        double rhs[3];
+        for (int a = 0; a < 3; ++a) rhs[a] = -ds * c[a] - h.u * de1[a] - h.v * de2[a];
+        rhs[1] -= dA;
+        const double b1 = e1[0] * rhs[0] + e1[1] * rhs[1] + e1[2] * rhs[2];
+        const double b2 = e2[0] * rhs[0] + e2[1] * rhs[1] + e2[2] * rhs[2];
+        const double du = gdet != 0.0 ? (b1 * g22 - b2 * g12) / gdet : 0.0;
+        const double dv = gdet != 0.0 ? (g11 * b2 - g12 * b1) / gdet : 0.0;
+        dq[k] = ds;
+        for (int a = 0; a < 3; ++a)
+            duw[k][a] = du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]);
+        duw[k][1] += (1.0 - h.u - h.v) * dvy[0][k] + h.u * dvy[1][k] + h.v * dvy[2][k];
     }
 }
 

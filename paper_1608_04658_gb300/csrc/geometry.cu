@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(GEOM_THREADS) classify_kernel(const Lattice L,
                                                                 uint8_t *__restrict__ flags,
                                                                 int *__restrict__ blist,
                                                                 int *__restrict__ bpos,
-                                                                int *__restrict__ ulist)
+                                                                int *__restrict__ ulist,
+                                                                int *__restrict__ upos)
 {
     const int cap = G.cap[0] * G.cap[1] * G.cap[2];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) classify_kernel(const Lattice L,
             }
             if (f & FL_UNCOVERED) {
                 const int slot = atomicAdd(&cur->n_uncovered, 1);
-                if (slot < G.cap_uncovered) ulist[slot] = n;
+                if (slot < G.cap_uncovered) { ulist[slot] = n; upos[slot] = k; }
                 else atomicOr(&cur->status, ST_BAND_OVERFLOW);
             }
         }
@@ -435,7 +436,7 @@ cudaError_t launch_geometry(const Lattice &L, const GeomParams &G, Scratch &S, i
         if (e != cudaSuccess) return e;
     }
     mark_kernel<<<nb, GEOM_THREADS, 0, s>>>(L, G, bp, bc, flags, S.bforce);
-    classify_kernel<<<nb, GEOM_THREADS, 0, s>>>(L, G, bc, flags, S.blist, S.bpos, S.ulist);
+    classify_kernel<<<nb, GEOM_THREADS, 0, s>>>(L, G, bc, flags, S.blist, S.bpos, S.ulist, S.upos);
     *nlaunch += 2;
     return cudaGetLastError();
 }

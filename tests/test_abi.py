@@ -39,7 +39,8 @@ def _c_layout(struct, fields):
 
 
 @pytest.mark.parametrize("cls,cname", [(binding.Params, "lbm_params"), (binding.Geometry, "lbm_geometry"),
-                                       (binding.BodyState, "lbm_body_state")])
+                                       (binding.BodyState, "lbm_body_state"),
+                                       (binding.AdjointSpec, "lbm_adjoint")])
 def test_struct_layout_matches_header(cls, cname):
     fields = [f for f, _ in cls._fields_]
     got = _c_layout(cname, fields)
