@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer"])
+    ap.add_argument("--adjoint-horizon", type=int, default=8000,
+                    help="steps of the adjoint/forward measurement (0 to skip it)")
     return ap.parse_args()
 
 
@@ -315,6 +317,49 @@ def oracle_body(wl):
     return oracle.sphere_body(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"])
 
 
+def adjoint_bench(args, world, device):
+    """Adjoint/forward time on the differentiated swimmer (256x128x128,
+    L = 64, FP32, held): lbm_step over the horizon vs lbm_adjoint_step over
+    the same horizon (forward with checkpoints, recompute, reverse sweep),
+    objective = mean thrust, gradient w.r.t. (amplitude, wavelength, period)."""
+    import torch
+
+    import paper_1608_04658_gb300 as lbm
+    import synth
+    wl = synth.differentiated_swimmer()
+    H = args.adjoint_horizon
+    lat = lbm.Lattice(wl["shape"], wl["nu"], storage="fp32", faces=wl["faces"], device=device)
+    lat.set_geometry(lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
+                                 wl["period"], mass=wl["mass"]))
+    lat.init_state(*synth.uniform_fields(wl["shape"]))
+    lat.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(H)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    fwd_ms = dist_max(e0.elapsed_time(e1), world)
+    dist_barrier(world)
+    t0 = time.perf_counter()
+    out = lat.adjoint(H, (-1.0, 0.0, 0.0))
+    torch.cuda.synchronize()
+    adj_ms = dist_max(1e3 * (time.perf_counter() - t0), world)
+    K = int(math.ceil(math.sqrt(H)))
+    nx, ny, nz = wl["shape"]
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return {"workload": wl["name"], "storage": "fp32", "horizon": H, "checkpoint_every": K,
+            "objective": "mean thrust -F_x over the horizon",
+            "theta": "(wave amplitude, wavelength, period)",
+            "fwd_ms_per_step": round(fwd_ms / H, 5), "adjoint_ms_per_step": round(adj_ms / H, 5),
+            "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+            "J": out["J"], "dJ_dtheta": [float(v) for v in out["dJ_dtheta"]],
+            "checkpoint_bytes": int((math.ceil(H / K) + K + 3) * 27 * nx * ny * nz * 4)}
+
+
 def cpu_baseline(wl, nsteps=None):
     """The FP64 oracle, single-threaded, on the full box of the workload
     (2 steps of the sphere box, 1 step of the larger boxes)."""
@@ -354,6 +399,7 @@ def run_ours(args):
                 continue
             r = time_storage(st, wl, args, world, device, clocks)
             variants[st] = r
+    adj = adjoint_bench(args, world, device) if args.adjoint_horizon > 0 else None
     clk = clocks.stop()
     e2e = None if args.no_e2e else e2e_storage(args.storage, wl, args, device)
     cpu = None
@@ -393,6 +439,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": main["launches"],
         "clocks": clk,
+        "adjoint": adj,
         "variants": {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],
                           "ms_per_step": round(r["ms"] / args.steps, 5),
                           "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st] / world / peak, 2),

@@ -35,27 +35,33 @@ namespace lbm {
 // reciprocal r(c), e(c) (shifted form, see axis_eq) and the logarithmic
 // derivatives dl(c) = d ln phi(c) / du = D0 + c dlnB with
 //   D0 = -(3u/S)/(2 - S),   dlnB = (2 + 3u/S)/(2u + S) + 1/(1 - u).
+// (reciprocals and square roots by rcp_fast / sqrt_fast: the hardware
+// approximations in FP32, exact in FP64)
 template <typename R>
 __device__ __forceinline__ void axis_eq_adj(R u, R e[3], R phi[3], R r[3], R dl[3])
 {
     const R u2 = u * u;
-    const R S = sqrt(R(1) + R(3) * u2);
-    const R sig = R(3) * u2 / (S + R(1));
+    const R S = sqrt_fast(R(1) + R(3) * u2);
+    const R iS = rcp_fast(S);
+    const R sig = R(3) * u2 * rcp_fast(S + R(1));
     const R oms = R(1) - sig;
-    const R bp = (R(3) * u + sig) / (R(1) - u);
-    const R bm = -bp / (R(1) + bp);
+    const R i1u = rcp_fast(R(1) - u);
+    const R bp = (R(3) * u + sig) * i1u;
+    const R i1bp = rcp_fast(R(1) + bp);
+    const R bm = -bp * i1bp;
     e[0] = bm * oms - sig;
     e[1] = -sig;
     e[2] = bp * oms - sig;
     phi[0] = oms * (R(1) + bm);
     phi[1] = oms;
     phi[2] = oms * (R(1) + bp);
-    r[0] = R(1) / phi[0];
-    r[1] = R(1) / phi[1];
-    r[2] = R(1) / phi[2];
-    const R sp = R(3) * u / S;
-    const R D0 = -sp / oms;
-    const R dlnB = (R(2) + sp) / ((R(1) - u) * (R(1) + bp)) + R(1) / (R(1) - u);
+    const R ioms = rcp_fast(oms);
+    r[0] = ioms * (R(1) + bp);
+    r[1] = ioms;
+    r[2] = ioms * i1bp;
+    const R sp = R(3) * u * iS;
+    const R D0 = -sp * ioms;
+    const R dlnB = (R(2) + sp) * i1u * i1bp + i1u;
     dl[0] = D0 - dlnB;
     dl[1] = D0;
     dl[2] = D0 + dlnB;
@@ -68,67 +74,108 @@ __device__ __forceinline__ void axis_eq_adj(R u, R e[3], R phi[3], R r[3], R dl[
 //   g_bar = -b <lam, dh>,  a = <ds|dh>, b = <dh|dh>, g = 1/b - (2 - 1/b) a/b,
 //   df_bar = dh_bar + S^T (ds_bar - dh_bar),   feq_bar = -df_bar - (a_bar ds dh + b_bar dh^2)/feq^2,
 //   then f^eq(rho, u) and u = j/rho back to f.
+// Operation count as in the forward collision: moments from the x-lines of
+// the velocity cube, f^eq and 1/f^eq as products of per-axis factors with the
+// x-y pairs formed once, the shear values formed once.
 template <typename R>
 __device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int gamma_mode)
 {
-    R drho = 0, j[3] = {0, 0, 0};
+    R Ls[9], Ld[9];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += g[i];
-        j[0] += R(cx_of(i)) * g[i];
-        j[1] += R(cy_of(i)) * g[i];
-        j[2] += R(cz_of(i)) * g[i];
+    for (int l = 0; l < 9; ++l) {
+        Ld[l] = g[18 + l] - g[l];
+        Ls[l] = (g[18 + l] + g[l]) + g[9 + l];
     }
-    const R rho = rho0 + drho, irho = R(1) / rho;
-    const R u[3] = {j[0] * irho, j[1] * irho, j[2] * irho};
-    R e[3][3], phi[3][3], rr[3][3], dl[3][3];
+    const R drho = ((Ls[0] + Ls[1]) + (Ls[2] + Ls[3])) + ((Ls[4] + Ls[5]) + ((Ls[6] + Ls[7]) + Ls[8]));
+    const R jx = ((Ld[0] + Ld[1]) + (Ld[2] + Ld[3])) + ((Ld[4] + Ld[5]) + ((Ld[6] + Ld[7]) + Ld[8]));
+    const R jy = ((Ls[6] + Ls[7]) + Ls[8]) - ((Ls[0] + Ls[1]) + Ls[2]);
+    const R jz = ((Ls[2] + Ls[5]) + Ls[8]) - ((Ls[0] + Ls[3]) + Ls[6]);
+    const R rho = rho0 + drho, irho = rcp_fast(rho);
+    const R u[3] = {jx * irho, jy * irho, jz * irho};
+    R ex[3], ey[3], ez[3], px[3], py[3], pz[3], rx[3], ry[3], rz[3], dl[3][3];
+    axis_eq_adj(u[0], ex, px, rx, dl[0]);
+    axis_eq_adj(u[1], ey, py, ry, dl[1]);
+    axis_eq_adj(u[2], ez, pz, rz, dl[2]);
+    // f^eq_i = Fxy[cx][cy] Fz[cz], 1/f^eq_i = Rxy[cx][cy] Rz[cz] (1-D weights
+    // w(0) = 2/3, w(+-1) = 1/6 and rho folded in)
+    R Fxy[3][3], Rxy[3][3], Fz[3], Rz[3], exy[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) axis_eq_adj(u[a], e[a], phi[a], rr[a], dl[a]);
+    for (int a = 0; a < 3; ++a) {
+        const R w = a == 1 ? R(2.0 / 3.0) : R(1.0 / 6.0), iw = a == 1 ? R(1.5) : R(6);
+        Fz[a] = w * pz[a];
+        Rz[a] = iw * rz[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R wb = b == 1 ? R(2.0 / 3.0) : R(1.0 / 6.0), iwb = b == 1 ? R(1.5) : R(6);
+            Fxy[a][b] = rho * (w * px[a]) * (wb * py[b]);
+            Rxy[a][b] = irho * (iw * rx[a]) * (iwb * ry[b]);
+            exy[a][b] = ey[b] * px[a] + ex[a];
+        }
+    }
+    R rw[4], dw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R w = k == 0 ? R(8) / R(27) : k == 1 ? R(2) / R(27) : k == 2 ? R(1) / R(54) : R(1) / R(216);
+        rw[k] = rho * w;
+        dw[k] = drho * w;
+    }
     R d[Q];
-    R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R exy = e[0][cx + 1] + e[1][cy + 1] + e[0][cx + 1] * e[1][cy + 1];
-        const R E = exy + e[2][cz + 1] + exy * e[2][cz + 1];
-        d[i] = g[i] - weight<R>(i) * (drho + rho * E);
-        pxx += R(cx * cx) * d[i];
-        pyy += R(cy * cy) * d[i];
-        pzz += R(cz * cz) * d[i];
-        pxy += R(cx * cy) * d[i];
-        pxz += R(cx * cz) * d[i];
-        pyz += R(cy * cz) * d[i];
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R E = exy[cx + 1][cy + 1] * pz[cz + 1] + ez[cz + 1];
+        d[i] = g[i] - (rw[nz] * E + dw[nz]);
     }
+    R A[9], B[9], T[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        A[l] = d[18 + l] + d[l];
+        B[l] = d[18 + l] - d[l];
+        T[l] = A[l] + d[9 + l];
+    }
+    const R pxx = ((A[0] + A[1]) + (A[2] + A[3])) + ((A[4] + A[5]) + ((A[6] + A[7]) + A[8]));
+    const R pxy = ((B[6] + B[7]) + B[8]) - ((B[0] + B[1]) + B[2]);
+    const R pxz = ((B[2] + B[5]) + B[8]) - ((B[0] + B[3]) + B[6]);
+    const R pyy = ((T[0] + T[1]) + T[2]) + ((T[6] + T[7]) + T[8]);
+    const R pzz = ((T[0] + T[3]) + T[6]) + ((T[2] + T[5]) + T[8]);
+    const R pyz = (T[0] + T[8]) - (T[2] + T[6]);
     const R nxz = pxx - pzz, nyz = pyy - pzz;
+    const R sx = (R(2) * nxz - nyz) * R(1.0 / 6.0);
+    const R sy = (R(2) * nyz - nxz) * R(1.0 / 6.0);
+    const R sz = -(nxz + nyz) * R(1.0 / 6.0);
+    const R qxy = R(0.25) * pxy, qxz = R(0.25) * pxz, qyz = R(0.25) * pyz;
     R sh = 0, hh = 0, lh = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
-        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R ifeq = Rxy[cx + 1][cy + 1] * Rz[cz + 1];
+        const R ds = (nz == 1 || nz == 2) ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
         const R dh = d[i] - ds;
-        sh += ds * dh * ifeq;
-        hh += dh * dh * ifeq;
+        const R t = dh * ifeq;
+        sh += ds * t;
+        hh += dh * t;
         lh += lam[i] * dh;
     }
     const bool analytic = gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>();
-    const R gam = analytic ? inv_beta - (R(2) - inv_beta) * sh / hh : R(2);
+    const R ihh = analytic ? rcp_fast(hh) : R(0);
+    const R gam = analytic ? inv_beta - (R(2) - inv_beta) * sh * ihh : R(2);
     const R gb = -beta * lh;
     const R kk = R(2) - inv_beta;
-    const R ab = analytic ? -kk * gb / hh : R(0);
-    const R bb = analytic ? kk * gb * sh / (hh * hh) : R(0);
-    // shear sums of ds_bar - dh_bar
+    const R ab = -kk * gb * ihh;
+    // (kk gb)(sh/hh)/hh: the square hh^2 would underflow in FP32 near rest
+    const R bb = kk * gb * (sh * ihh) * ihh;
+    const R cl_s = -R(2) * beta, cl_h = -beta * gam, bb2 = R(2) * bb;
+    // shear sums of ds_bar - dh_bar (faces and edges carry ds)
     R Sx = 0, Sy = 0, Sz = 0, Qxy = 0, Qxz = 0, Qyz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
         if (nz != 1 && nz != 2) continue;
-        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
-        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const R ifeq = Rxy[cx + 1][cy + 1] * Rz[cz + 1];
+        const R ds = shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz);
         const R dh = d[i] - ds;
-        const R dsb = -R(2) * beta * lam[i] + ab * dh * ifeq;
-        const R dhb = -beta * gam * lam[i] + ab * ds * ifeq + R(2) * bb * dh * ifeq;
-        const R t = dsb - dhb;
+        // (ds_bar - dh_bar) = (cl_s - cl_h) lam + (ab (dh - ds) - 2 bb dh) / feq
+        const R t = (cl_s - cl_h) * lam[i] + (ab * (dh - ds) - bb2 * dh) * ifeq;
         if (nz == 1) {
             if (cx) Sx += t;
             else if (cy) Sy += t;
@@ -141,30 +188,30 @@ __device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int 
     }
     const R nxzb = (R(2) * Sx - Sy - Sz) * R(1.0 / 6.0);
     const R nyzb = (R(2) * Sy - Sx - Sz) * R(1.0 / 6.0);
-    const R pxxb = nxzb, pyyb = nyzb, pzzb = -(nxzb + nyzb);
+    const R pzzb = -(nxzb + nyzb);
     const R pxyb = R(0.25) * Qxy, pxzb = R(0.25) * Qxz, pyzb = R(0.25) * Qyz;
-    R rhob = 0, ub[3] = {0, 0, 0};
+    R rhob = 0, ub0 = 0, ub1 = 0, ub2 = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const R ifeq = irho * inv_weight<R>(i) * rr[0][cx + 1] * rr[1][cy + 1] * rr[2][cz + 1];
-        const R feq = rho * weight<R>(i) * phi[0][cx + 1] * phi[1][cy + 1] * phi[2][cz + 1];
-        const R ds = shear_part_raw<R>(i, nxz, nyz, pxy, pxz, pyz);
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+        const R ifeq = Rxy[cx + 1][cy + 1] * Rz[cz + 1];
+        const R feq = Fxy[cx + 1][cy + 1] * Fz[cz + 1];
+        const R ds = (nz == 1 || nz == 2) ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
         const R dh = d[i] - ds;
-        const R dhb = -beta * gam * lam[i] + ab * ds * ifeq + R(2) * bb * dh * ifeq;
-        const R dfb = dhb + pxxb * R(cx * cx) + pyyb * R(cy * cy) + pzzb * R(cz * cz) + pxyb * R(cx * cy) +
+        const R dhb = cl_h * lam[i] + (ab * ds + bb2 * dh) * ifeq;
+        const R dfb = dhb + nxzb * R(cx * cx) + nyzb * R(cy * cy) + pzzb * R(cz * cz) + pxyb * R(cx * cy) +
                       pxzb * R(cx * cz) + pyzb * R(cy * cz);
         // feq_bar * feq
-        const R t = -(ab * ds * dh + bb * dh * dh) * ifeq - dfb * feq;
+        const R t = -(ab * ds + bb * dh) * dh * ifeq - dfb * feq;
         rhob += t;
-        ub[0] += t * dl[0][cx + 1];
-        ub[1] += t * dl[1][cy + 1];
-        ub[2] += t * dl[2][cz + 1];
+        ub0 += t * dl[0][cx + 1];
+        ub1 += t * dl[1][cy + 1];
+        ub2 += t * dl[2][cz + 1];
         lam[i] += dfb;
     }
     rhob *= irho;
-    const R jb[3] = {ub[0] * irho, ub[1] * irho, ub[2] * irho};
-    rhob -= (ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * irho;
+    const R jb[3] = {ub0 * irho, ub1 * irho, ub2 * irho};
+    rhob -= (ub0 * u[0] + ub1 * u[1] + ub2 * u[2]) * irho;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         lam[i] += rhob + R(cx_of(i)) * jb[0] + R(cy_of(i)) * jb[1] + R(cz_of(i)) * jb[2];
@@ -201,7 +248,8 @@ __device__ R kbc_vjp_lanes(R g, R lam, int i, R beta, R inv_beta, R rho0, int ga
     const R gb = -beta * lh;
     const R kk = R(2) - inv_beta;
     const R ab = analytic ? -kk * gb / hh : R(0);
-    const R bb = analytic ? kk * gb * sh / (hh * hh) : R(0);
+    // (kk gb)(sh/hh)/hh: the square hh^2 would underflow in FP32 near rest
+    const R bb = analytic ? kk * gb * (sh / hh) / hh : R(0);
     const R dsb = -R(2) * beta * lv + ab * dh * ifeq;
     const R dhb = -beta * gam * lv + ab * ds * ifeq + R(2) * bb * dh * ifeq;
     const R t = (nz == 1 || nz == 2) ? dsb - dhb : R(0);
@@ -269,6 +317,28 @@ __device__ __forceinline__ R pull_transpose(const Lattice &L, const R *__restric
     return s;
 }
 
+// Reader offsets for one axis: o[c+1] is the offset of the node at a + c (the
+// node that pulled direction component c from a), wrapped on periodic faces.
+// Returns true when the plain offsets do not describe every reader: a + c
+// leaves the box through a non-periodic face, or a lies on an outflow face
+// layer (clamped readers).
+__device__ __forceinline__ bool axis_readers(int a, int n, int stride, int face_lo, int face_hi, int o[3])
+{
+    o[0] = -stride;
+    o[1] = 0;
+    o[2] = stride;
+    bool special = false;
+    if (a == 0) {
+        if (face_lo == LBM_FACE_PERIODIC) o[0] = (n - 1) * stride;
+        else special = true;
+    }
+    if (a == n - 1) {
+        if (face_hi == LBM_FACE_PERIODIC) o[2] = -(n - 1) * stride;
+        else special = true;
+    }
+    return special;
+}
+
 // band position of node (x, y, z) in the band of body state b, or -1
 __device__ __forceinline__ int band_index(const Lattice &L, const GeomParams &G, const DevBody *b, int x, int y,
                                           int z)
@@ -309,11 +379,26 @@ __device__ __forceinline__ R next_adjoint(const Lattice &L, const GeomParams &G,
     return v;
 }
 
+// lambda(S^{t+1})(x)_i on the rare path, out of line to keep the bulk
+// kernel's code small
+template <typename R>
+__device__ __noinline__ R next_adjoint_rare(const Lattice &L, const GeomParams &G, const NextAdj<R> &A, int x, int y,
+                                            int z, int n, int i)
+{
+    return next_adjoint<R>(L, G, A, x, y, z, n, i);
+}
+
 // ----------------------------------------------------------------- kernels
 // Nodes fluid at t+1 without missing links: Lam^t(x) = C'(F(x))^T lambda(S^{t+1})(x);
 // solid nodes get Lam^t = 0; boundary nodes are left to the boundary adjoint.
+// Minimum resident blocks per SM requested for the bulk adjoint (a register
+// cap; LBM_ADJ_MIN_BLOCKS overrides it at build time).
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 4
+#endif
+
 template <typename S>
-__global__ void __launch_bounds__(128) adjoint_bulk_kernel(const Lattice L, const GeomParams G,
+__global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) adjoint_bulk_kernel(const Lattice L, const GeomParams G,
                                                            const S *__restrict__ st,
                                                            const NextAdj<typename Codec<S>::R> A,
                                                            const uint8_t *__restrict__ flags1,
@@ -333,14 +418,18 @@ __global__ void __launch_bounds__(128) adjoint_bulk_kernel(const Lattice L, cons
     }
     if (f1 & FL_BOUNDARY) return;
     R lam[Q];
-    const bool interior = x > 0 && x < L.nx - 1 && y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1;
-    if (A.direct || !interior || (A.flags && (A.flags[n] & FL_UNCOVERED))) {
+    int ox[3], oy[3], oz[3];
+    bool special = axis_readers(x, L.nx, 1, L.face[0], L.face[1], ox);
+    special |= axis_readers(y, L.ny, L.nx, L.face[2], L.face[3], oy);
+    special |= axis_readers(z, L.nz, L.nx * L.ny, L.face[4], L.face[5], oz);
+    if (A.direct || special || (A.flags && (A.flags[n] & FL_UNCOVERED))) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) lam[i] = next_adjoint<R>(L, G, A, x, y, z, n, i);
+        for (int i = 0; i < Q; ++i) lam[i] = next_adjoint_rare<R>(L, G, A, x, y, z, n, i);
     } else {
+        const R *p = A.lam + n;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            lam[i] = A.lam[(long long)i * (long long)N + n + (cx_of(i) + L.nx * (cy_of(i) + L.ny * cz_of(i)))];
+            lam[i] = p[(long long)i * (long long)N + (ox[cx_of(i) + 1] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1])];
         if (A.ext) {
             const int k = band_index(L, G, A.band, x, y, z);
             if (k >= 0) {
@@ -510,7 +599,8 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
         const R fbb = act ? sf[13][26 - (act ? i : 0)] : R(0);
         double q = 0, uw[3] = {0, 0, 0};
         MeshHit hit{-1, 0.0, 0.0};
-        if (miss) link_data<R>(L, G, b, x, y, z, cx, cy, cz, q, uw, &hit);
+        if (G.kind == LBM_BODY_MESH) mesh_links_warp<R>(G, b, x, y, z, mask, lane, q, uw, hit);
+        else if (miss) link_data<R>(L, G, b, x, y, z, cx, cy, cz, q, uw);
         const R gstat = miss ? fbb : Fi;
         const R dyn = miss ? R(6) * weight<R>(i) * rho0 * (R(cx) * (R)uw[0] + R(cy) * (R)uw[1] + R(cz) * (R)uw[2])
                            : R(0);
@@ -600,7 +690,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
         for (int k = 0; k < 3; ++k) {
             double v = tb[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] = v;
+            if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] += v;
         }
         __syncwarp();
     }
@@ -673,12 +763,25 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
             for (int k = 0; k < 3; ++k) tb[k] = (double)ub[1] * dv[k];
         }
         if (lane == 0)
-            for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] = tb[k];
+            for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] += tb[k];
         __syncwarp();
     }
 }
 
-// acc[k] += sum over band slots of slot[6 s + k] + slot[6 s + 3 + k], fixed order
+// theta-tangents of every mesh vertex at the pose of body state b: dy/dtheta
+// (position) and the central difference of it (velocity), 3 + 3 per vertex
+__global__ void __launch_bounds__(256) vertex_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G.n_vertices) return;
+    const double s = G.mesh_rest[3 * v];
+    swimmer_midline_tangent(G, s, b->t, G.mesh_dy + 3 * (size_t)v);
+    swimmer_velocity_tangent(G, b->t, s, G.mesh_dvy + 3 * (size_t)v);
+}
+
+// acc[k] = sum over band slots of slot[6 s + k] + slot[6 s + 3 + k], fixed
+// order (the slots hold each band position's sums over all reversed steps:
+// one writer per slot and step, so the totals do not depend on timing)
 __global__ void __launch_bounds__(256) theta_reduce_kernel(const double *__restrict__ slots, int nslots,
                                                             double *__restrict__ acc)
 {
@@ -693,7 +796,7 @@ __global__ void __launch_bounds__(256) theta_reduce_kernel(const double *__restr
             for (int k = 0; k < 3; ++k) sm[threadIdx.x][k] += sm[threadIdx.x + h][k];
         __syncthreads();
     }
-    if (threadIdx.x < 3) acc[threadIdx.x] += sm[0][threadIdx.x];
+    if (threadIdx.x < 3) acc[threadIdx.x] = sm[0][threadIdx.x];
 }
 
 // lambda(S^0): the transpose of step 0's pull and band contributions, zero at
@@ -775,7 +878,8 @@ struct AdjBuffers {
 };
 
 // one forward step from fa into fb with the context's body scratch and the
-// given marks (the same launch sequence as lbm_step)
+// given marks (the launch sequence of lbm_step without the force reduction,
+// which the recomputation does not need)
 cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
 {
     int nl = 0;
@@ -790,11 +894,15 @@ cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
         if ((e = launch_geometry(ctx->L, ctx->G, ctx->S, prev, flags, ctx->stream, &nl)) != cudaSuccess) return e;
         if ((e = launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, flags, ctx->stream)) != cudaSuccess)
             return e;
-        if ((e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->stream)) != cudaSuccess)
+        // boundary nodes beside the bulk kernel, as in lbm_step
+        if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->side)) != cudaSuccess)
             return e;
-        if ((e = launch_forces(ctx->G, ctx->S, cur, ctx->stream, &nl)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
     }
     if ((e = launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream)) != cudaSuccess) return e;
+    if (ctx->has_body && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess) return e;
     ctx->bcur = cur;
     return cudaSuccess;
 }
@@ -809,8 +917,7 @@ int list_blocks(int cap)
 // in flags1 after the geometry re-run) for storage type S
 template <typename S>
 cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
-                         typename Codec<S>::R *lam_out, double *ext, double *tslots, const ForceWeights &fw,
-                         double *acc)
+                         typename Codec<S>::R *lam_out, double *ext, double *tslots, const ForceWeights &fw)
 {
     using R = typename Codec<S>::R;
     const Lattice &L = ctx->L;
@@ -818,18 +925,24 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     Scratch &Sc = ctx->S;
     const DevBody *b = Sc.body + ctx->bcur;
     cudaStream_t s = ctx->stream;
-    const int cap = ctx->has_body ? G.cap[0] * G.cap[1] * G.cap[2] : 0;
+    cudaError_t e;
+    // the boundary adjoint runs beside the bulk adjoint (disjoint rows of Lam^t)
     if (ctx->has_body) {
-        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, s>>>(
+        if (G.kind == LBM_BODY_MESH)
+            vertex_tangent_kernel<<<(G.n_vertices + 255) / 256, 256, 0, s>>>(G, b);
+        if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, ctx->side>>>(
             L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, fw);
+        if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
     }
     const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
     dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
     adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, ctx->has_body ? flags1 : nullptr, lam_out);
     if (ctx->has_body) {
+        if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
             L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots);
-        theta_reduce_kernel<<<1, 256, 0, s>>>(tslots, cap, acc);
     }
     return cudaGetLastError();
 }
@@ -855,6 +968,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     DevBody *ckbody = nullptr, *segbody = nullptr, *adjbody = nullptr, *savebody = nullptr;
     R *lam[2] = {nullptr, nullptr};
     double *ext[2] = {nullptr, nullptr}, *tslots = nullptr, *acc = nullptr, *part = nullptr;
+    double *tan_dy = nullptr, *tan_dvy = nullptr;
     double F0[3] = {0, 0, 0}, F1[3] = {0, 0, 0}, accv[3] = {0, 0, 0};
     ForceWeights fw{{spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}};
     DevBody hb{};
@@ -868,8 +982,12 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
         !B.get(&wf[1], N) || !B.get(&wrec, N) || !B.get(&ckbody, nseg) || !B.get(&segbody, K) || !B.get(&adjbody, 2) ||
         !B.get(&savebody, 2) || !B.get(&lam[0], state) || !B.get(&lam[1], state) ||
         !B.get(&ext[0], (size_t)cap * Q) || !B.get(&ext[1], (size_t)cap * Q) || !B.get(&tslots, (size_t)cap * 6) ||
-        !B.get(&acc, 3) || !B.get(&part, nparts))
+        !B.get(&acc, 3) || !B.get(&part, nparts) ||
+        (body && ctx->G.kind == LBM_BODY_MESH &&
+         (!B.get(&tan_dy, 3 * (size_t)ctx->G.n_vertices) || !B.get(&tan_dvy, 3 * (size_t)ctx->G.n_vertices))))
         return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the checkpoints failed");
+    ctx->G.mesh_dy = tan_dy;
+    ctx->G.mesh_dvy = tan_dvy;
 
     // ---- forward over the horizon with checkpoints
     ADJ_CUDA(cudaMemcpyAsync(&hb, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToHost, s), "body read");
@@ -908,6 +1026,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
 
     // ---- reverse sweep, one recomputed segment at a time
     ADJ_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s), "clear");
+    ADJ_CUDA(cudaMemsetAsync(tslots, 0, (size_t)cap * 6 * sizeof(double), s), "clear");
     {
         bool first = true;
         for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -936,7 +1055,6 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                     ADJ_CUDA(launch_geometry(L, ctx->G, ctx->S, 0, wf[p], s, &nl), "geometry");
                     ctx->bcur = 1;
                     ADJ_CUDA(cudaMemsetAsync(ext[p], 0, (size_t)cap * Q * sizeof(double), s), "clear");
-                    ADJ_CUDA(cudaMemsetAsync(tslots, 0, (size_t)cap * 6 * sizeof(double), s), "clear");
                 }
                 NextAdj<R> A;
                 if (first) {
@@ -945,7 +1063,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                     A = NextAdj<R>{lam[p ^ 1], body ? ext[p ^ 1] : nullptr, adjbody + (p ^ 1),
                                    body ? wf[p ^ 1] : nullptr, 0};
                 }
-                ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, fw, acc),
+                ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, fw),
                          "reverse step");
                 if (body)
                     ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),
@@ -961,11 +1079,14 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
             ADJ_CUDA(cudaGetLastError(), "lambda0");
         }
     }
+    if (body) theta_reduce_kernel<<<1, 256, 0, s>>>(tslots, cap, acc);
     ADJ_CUDA(cudaMemcpyAsync(accv, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "theta");
     ADJ_CUDA(cudaStreamSynchronize(s), "sync");
     for (int k = 0; k < 3; ++k) dJ[k] = accv[k];
 
 done:
+    ctx->G.mesh_dy = nullptr;
+    ctx->G.mesh_dvy = nullptr;
     // the context keeps the state after the horizon; restore its body copies
     cudaMemcpyAsync(ctx->S.body, savebody, 2 * sizeof(DevBody), cudaMemcpyDeviceToDevice, s);
     ctx->bcur = save_bcur;

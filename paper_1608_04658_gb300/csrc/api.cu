@@ -81,7 +81,7 @@ void free_scratch(Scratch &S, bool keep_body)
     cudaFree(S.partials); cudaFree(S.ticket);
     cudaFree(S.mesh_rest); cudaFree(S.mesh_pos); cudaFree(S.mesh_vel); cudaFree(S.col_x);
     cudaFree(S.mesh_tris); cudaFree(S.col_count); cudaFree(S.cell_count); cudaFree(S.cell_tri);
-    cudaFree(S.mesh_status); cudaFree(S.tri_box);
+    cudaFree(S.mesh_status); cudaFree(S.tri_box); cudaFree(S.mesh_ipos); cudaFree(S.mesh_frac);
     DevBody *b = S.body;
     S = Scratch{};
     if (keep_body) S.body = b;
@@ -322,7 +322,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
              dalloc(&S.mesh_vel, 3 * nv) == cudaSuccess && dalloc(&S.mesh_tris, 3 * nt) == cudaSuccess &&
              dalloc(&S.tri_box, 6 * nt) == cudaSuccess && dalloc(&S.col_count, ncols) == cudaSuccess &&
              dalloc(&S.col_x, ncols * MESH_COL_CAP) == cudaSuccess && dalloc(&S.cell_count, ncells) == cudaSuccess &&
-             dalloc(&S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && dalloc(&S.mesh_status, 1) == cudaSuccess;
+             dalloc(&S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && dalloc(&S.mesh_status, 1) == cudaSuccess &&
+             dalloc(&S.mesh_ipos, 3 * nv) == cudaSuccess && dalloc(&S.mesh_frac, 3 * nv) == cudaSuccess;
         if (ok)
             ok = cudaMemcpy(S.mesh_rest, g->mesh_rest, 3 * nv * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemcpy(S.mesh_tris, g->mesh_tris, 3 * nt * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -336,6 +337,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.cell_count = S.cell_count;
         G.cell_tri = S.cell_tri;
         G.mesh_status = S.mesh_status;
+        G.mesh_ipos = S.mesh_ipos;
+        G.mesh_frac = S.mesh_frac;
     }
     if (!ok) {
         free_scratch(ctx->S, true);

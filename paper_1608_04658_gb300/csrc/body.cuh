@@ -30,12 +30,15 @@ struct GeomParams {
     const int *mesh_tris;     // three vertex indices per triangle
     double *mesh_pos;         // vertex positions at the current pose
     double *mesh_vel;         // vertex velocities at the current pose
+    int *mesh_ipos;           // vertex positions split as nearest lattice point ...
+    float *mesh_frac;         // ... plus the remainder in [-1/2, 1/2] (FP32 link search)
     float *tri_box;           // per triangle: min x, y, z, max x, y, z (rounded outwards)
     int *col_count;           // crossings per band column (y, z)
     double *col_x;            // [column][MESH_COL_CAP] crossing abscissae
     int *cell_count;          // triangles per band cell
     int *cell_tri;            // [cell][MESH_CELL_CAP] triangle indices
     int *mesh_status;         // overflow of the column or cell lists in this step
+    double *mesh_dy, *mesh_dvy; // adjoint only: theta-tangents of vertex position / velocity (y)
     int n_vertices, n_triangles;
     int cells[3];             // cell grid of the band capacity box
     double length, wave_amp, wave_length, wave_period;
@@ -73,8 +76,8 @@ struct Scratch {
     int n_partials;
     // swimmer mesh
     double *mesh_rest, *mesh_pos, *mesh_vel, *col_x;
-    int *mesh_tris, *col_count, *cell_count, *cell_tri, *mesh_status;
-    float *tri_box;
+    int *mesh_tris, *col_count, *cell_count, *cell_tri, *mesh_status, *mesh_ipos;
+    float *tri_box, *mesh_frac;
 };
 
 // launchers ------------------------------------------------------------------

@@ -91,7 +91,12 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
         // target density and velocity over the missing set
         const R fbb = act ? sf[13][26 - (act ? i : 0)] : R(0);  // shifted f'_{opp i}(x_b, t)
         double q = 0, uw[3] = {0, 0, 0};
-        if (miss) link_data<R>(L, G, b, x, y, z, cx, cy, cz, q, uw);
+        if (G.kind == LBM_BODY_MESH) {
+            MeshHit hit{-1, 0.0, 0.0};
+            mesh_links_warp<R>(G, b, x, y, z, mask, lane, q, uw, hit);
+        } else if (miss) {
+            link_data<R>(L, G, b, x, y, z, cx, cy, cz, q, uw);
+        }
         const R gstat = miss ? fbb : Fi;
         const R dyn = miss ? R(6) * weight<R>(i) * rho0 * (R(cx) * (R)uw[0] + R(cy) * (R)uw[1] + R(cz) * (R)uw[2])
                            : R(0);

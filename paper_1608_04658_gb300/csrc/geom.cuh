@@ -165,79 +165,6 @@ __device__ __forceinline__ double det3(const double a[3], const double b[3], con
     return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) + a[2] * (b[0] * d[1] - b[1] * d[0]);
 }
 
-// first crossing x_b - s c (s in [0,1]) of the mesh, over the triangles of the
-// cells that the link's box overlaps; Cramer's rule for (u, v, s) per
-// triangle; wall velocity by barycentric interpolation of vertex velocities.
-// No hit (round-off at an edge): q = 1/2 and the material velocity at the
-// link's midpoint.
-__device__ __noinline__ static void mesh_link(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
-                          double &q, double uw[3], MeshHit *hit)
-{
-    int bt = -1;
-    double bu = 0.0, bv = 0.0;
-    const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
-    int c0[3], c1[3];
-    float lo[3], hi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int e0 = min(p[a], p[a] - c[a]), e1 = max(p[a], p[a] - c[a]);
-        lo[a] = (float)e0;
-        hi[a] = (float)e1;
-        c0[a] = max(0, (e0 - b->band_lo[a]) / MESH_CELL);
-        c1[a] = min(G.cells[a] - 1, (e1 - b->band_lo[a]) / MESH_CELL);
-    }
-    const double *P = G.mesh_pos;
-    const double dc[3] = {(double)cx, (double)cy, (double)cz};
-    double best = 2.0;
-    for (int kz = c0[2]; kz <= c1[2]; ++kz)
-        for (int ky = c0[1]; ky <= c1[1]; ++ky)
-            for (int kx = c0[0]; kx <= c1[0]; ++kx) {
-                const int cell = kx + G.cells[0] * (ky + G.cells[1] * kz);
-                const int n = min(G.cell_count[cell], MESH_CELL_CAP);
-                const int *list = G.cell_tri + (size_t)cell * MESH_CELL_CAP;
-                for (int j = 0; j < n; ++j) {
-                    const int k = list[j];
-                    const float *bx = G.tri_box + 6 * (size_t)k;
-                    if (bx[3] < lo[0] || bx[0] > hi[0] || bx[4] < lo[1] || bx[1] > hi[1] || bx[5] < lo[2] ||
-                        bx[2] > hi[2])
-                        continue;
-                    const int t0 = G.mesh_tris[3 * k], t1 = G.mesh_tris[3 * k + 1], t2 = G.mesh_tris[3 * k + 2];
-                    double e1[3], e2[3], r[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        e1[a] = P[3 * t1 + a] - P[3 * t0 + a];
-                        e2[a] = P[3 * t2 + a] - P[3 * t0 + a];
-                        r[a] = (double)p[a] - P[3 * t0 + a];
-                    }
-                    const double D = det3(e1, e2, dc);
-                    if (D == 0.0) continue;
-                    const double u = det3(r, e2, dc) / D;
-                    const double v = det3(e1, r, dc) / D;
-                    const double s = det3(e1, e2, r) / D;
-                    if (u < 0.0 || v < 0.0 || u + v > 1.0 || s < 0.0 || s > 1.0 || !(s < best)) continue;
-                    best = s;
-                    bt = k;
-                    bu = u;
-                    bv = v;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        uw[a] = (1.0 - u - v) * G.mesh_vel[3 * t0 + a] + u * G.mesh_vel[3 * t1 + a] +
-                                v * G.mesh_vel[3 * t2 + a];
-                }
-            }
-    if (best > 1.0) {
-        best = 0.5;
-        bt = -1;
-        swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
-    }
-    q = best;
-    if (hit) {
-        hit->tri = bt;
-        hit->u = bu;
-        hit->v = bv;
-    }
-}
-
 // Single-precision forms of the link search, used when the populations are
 // stored in FP32 or 16 bits (their collision runs in FP32): coordinates are
 // taken relative to the node in double and then rounded, so the link
@@ -248,77 +175,128 @@ __device__ __forceinline__ float det3f(const float a[3], const float b[3], const
     return a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) + a[2] * (b[0] * d[1] - b[1] * d[0]);
 }
 
-__device__ __noinline__ static void mesh_link_f(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx,
-                                                int cy, int cz, double &q, double uw[3], MeshHit *hit)
+// Warp-cooperative form of the mesh link search for a boundary node: the
+// missing links (bits of mask) are taken one at a time by the whole warp;
+// each lane tests a strided share of the candidate triangles (same tests as
+// mesh_link for double, mesh_link_f for float), and a warp arg-min over
+// (s, triangle index) picks the first crossing.  Lane i receives q, u_w and
+// the hit of link i.  Every lane of the warp must call it.
+template <typename R>
+__device__ void mesh_links_warp(const GeomParams &G, const DevBody *b, int x, int y, int z, uint32_t mask, int lane,
+                                double &q, double uw[3], MeshHit &hitout)
 {
-    constexpr float EPS = 1e-6f;  // barycentric slack: a link through a shared edge hits one of its triangles
-    const int p[3] = {x, y, z}, c[3] = {cx, cy, cz};
-    int c0[3], c1[3];
-    float lo[3], hi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int e0 = min(p[a], p[a] - c[a]), e1 = max(p[a], p[a] - c[a]);
-        lo[a] = (float)e0;
-        hi[a] = (float)e1;
-        c0[a] = max(0, (e0 - b->band_lo[a]) / MESH_CELL);
-        c1[a] = min(G.cells[a] - 1, (e1 - b->band_lo[a]) / MESH_CELL);
-    }
+    constexpr bool single = sizeof(R) == 4;
+    const int p[3] = {x, y, z};
     const double *P = G.mesh_pos;
-    const float dc[3] = {(float)cx, (float)cy, (float)cz};
-    float best = 2.0f;
-    float bu = 0.f, bv = 0.f;
-    int bt = -1;
-    for (int kz = c0[2]; kz <= c1[2]; ++kz)
-        for (int ky = c0[1]; ky <= c1[1]; ++ky)
-            for (int kx = c0[0]; kx <= c1[0]; ++kx) {
-                const int cell = kx + G.cells[0] * (ky + G.cells[1] * kz);
-                const int n = min(G.cell_count[cell], MESH_CELL_CAP);
-                const int *list = G.cell_tri + (size_t)cell * MESH_CELL_CAP;
-                for (int j = 0; j < n; ++j) {
-                    const int k = list[j];
-                    const float *bx = G.tri_box + 6 * (size_t)k;
-                    if (bx[3] < lo[0] || bx[0] > hi[0] || bx[4] < lo[1] || bx[1] > hi[1] || bx[5] < lo[2] ||
-                        bx[2] > hi[2])
-                        continue;
-                    const int t0 = G.mesh_tris[3 * k], t1 = G.mesh_tris[3 * k + 1], t2 = G.mesh_tris[3 * k + 2];
-                    float A[3], e1[3], e2[3], r[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        A[a] = (float)(P[3 * t0 + a] - (double)p[a]);
-                        e1[a] = (float)(P[3 * t1 + a] - (double)p[a]) - A[a];
-                        e2[a] = (float)(P[3 * t2 + a] - (double)p[a]) - A[a];
-                        r[a] = -A[a];
+    uint32_t m = mask;
+    while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+        int c0[3], c1[3];
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            const int e0 = min(p[a], p[a] - c[a]), e1 = max(p[a], p[a] - c[a]);
+            lo[a] = (float)e0;
+            hi[a] = (float)e1;
+            c0[a] = max(0, (e0 - b->band_lo[a]) / MESH_CELL);
+            c1[a] = min(G.cells[a] - 1, (e1 - b->band_lo[a]) / MESH_CELL);
+        }
+        // candidate values in the search precision (float coordinates relative
+        // to the node from the split vertex positions; double as in the oracle)
+        R best = R(2), bu = R(0), bv = R(0);
+        int bt = -1;
+        for (int kz = c0[2]; kz <= c1[2]; ++kz)
+            for (int ky = c0[1]; ky <= c1[1]; ++ky)
+                for (int kx = c0[0]; kx <= c1[0]; ++kx) {
+                    const int cell = kx + G.cells[0] * (ky + G.cells[1] * kz);
+                    const int n = min(G.cell_count[cell], MESH_CELL_CAP);
+                    const int *list = G.cell_tri + (size_t)cell * MESH_CELL_CAP;
+                    for (int j = lane; j < n; j += 32) {
+                        const int k = list[j];
+                        const float *bx = G.tri_box + 6 * (size_t)k;
+                        if (bx[3] < lo[0] || bx[0] > hi[0] || bx[4] < lo[1] || bx[1] > hi[1] || bx[5] < lo[2] ||
+                            bx[2] > hi[2])
+                            continue;
+                        const int t0 = G.mesh_tris[3 * k], t1 = G.mesh_tris[3 * k + 1], t2 = G.mesh_tris[3 * k + 2];
+                        R sv, u, v;
+                        if (single) {
+                            constexpr float EPS = 1e-6f;
+                            float A[3], e1[3], e2[3], r[3];
+                            for (int a = 0; a < 3; ++a) {
+                                const float pa = (float)(G.mesh_ipos[3 * t0 + a] - p[a]) + G.mesh_frac[3 * t0 + a];
+                                const float pb = (float)(G.mesh_ipos[3 * t1 + a] - p[a]) + G.mesh_frac[3 * t1 + a];
+                                const float pc = (float)(G.mesh_ipos[3 * t2 + a] - p[a]) + G.mesh_frac[3 * t2 + a];
+                                A[a] = pa;
+                                e1[a] = pb - pa;
+                                e2[a] = pc - pa;
+                                r[a] = -pa;
+                            }
+                            const float dc[3] = {(float)c[0], (float)c[1], (float)c[2]};
+                            const float D = det3f(e1, e2, dc);
+                            if (D == 0.0f) continue;
+                            const float iD = 1.0f / D;
+                            const float uf = det3f(r, e2, dc) * iD, vf = det3f(e1, r, dc) * iD;
+                            const float sf = det3f(e1, e2, r) * iD;
+                            if (uf < -EPS || vf < -EPS || uf + vf > 1.0f + EPS || sf < -EPS || sf > 1.0f + EPS) continue;
+                            sv = (R)fminf(fmaxf(sf, 0.0f), 1.0f);
+                            u = (R)uf;
+                            v = (R)vf;
+                        } else {
+                            double e1[3], e2[3], r[3];
+                            for (int a = 0; a < 3; ++a) {
+                                e1[a] = P[3 * t1 + a] - P[3 * t0 + a];
+                                e2[a] = P[3 * t2 + a] - P[3 * t0 + a];
+                                r[a] = (double)p[a] - P[3 * t0 + a];
+                            }
+                            const double dc[3] = {(double)c[0], (double)c[1], (double)c[2]};
+                            const double D = det3(e1, e2, dc);
+                            if (D == 0.0) continue;
+                            const double ud = det3(r, e2, dc) / D;
+                            const double vd = det3(e1, r, dc) / D;
+                            const double sd = det3(e1, e2, r) / D;
+                            if (ud < 0.0 || vd < 0.0 || ud + vd > 1.0 || sd < 0.0 || sd > 1.0) continue;
+                            sv = (R)sd;
+                            u = (R)ud;
+                            v = (R)vd;
+                        }
+                        if (sv < best || (sv == best && k < bt)) {
+                            best = sv;
+                            bt = k;
+                            bu = u;
+                            bv = v;
+                        }
                     }
-                    const float D = det3f(e1, e2, dc);
-                    if (D == 0.0f) continue;
-                    const float iD = 1.0f / D;
-                    const float u = det3f(r, e2, dc) * iD;
-                    const float v = det3f(e1, r, dc) * iD;
-                    const float sv = det3f(e1, e2, r) * iD;
-                    if (u < -EPS || v < -EPS || u + v > 1.0f + EPS || sv < -EPS || sv > 1.0f + EPS || !(sv < best))
-                        continue;
-                    best = sv;
-                    bu = u;
-                    bv = v;
-                    bt = k;
                 }
+        // arg-min over the warp, ties to the lower triangle index
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+            const R ou = __shfl_xor_sync(0xffffffffu, bu, o);
+            const R ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            if (ot >= 0 && (bt < 0 || ob < best || (ob == best && ot < bt))) {
+                best = ob;
+                bt = ot;
+                bu = ou;
+                bv = ov;
             }
-    if (hit) {
-        hit->tri = bt;
-        hit->u = bu;
-        hit->v = bv;
+        }
+        if (lane == i) {
+            hitout.tri = bt;
+            hitout.u = bu;
+            hitout.v = bv;
+            if (bt < 0) {
+                q = 0.5;
+                swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * c[0] - b->X[0]), uw);
+            } else {
+                q = best;
+                const int t0 = G.mesh_tris[3 * bt], t1 = G.mesh_tris[3 * bt + 1], t2 = G.mesh_tris[3 * bt + 2];
+                for (int a = 0; a < 3; ++a)
+                    uw[a] = (1.0 - bu - bv) * G.mesh_vel[3 * t0 + a] + bu * G.mesh_vel[3 * t1 + a] +
+                            bv * G.mesh_vel[3 * t2 + a];
+            }
+        }
     }
-    if (bt < 0) {
-        q = 0.5;
-        swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * cx - b->X[0]), uw);
-        return;
-    }
-    q = fmin(fmax((double)best, 0.0), 1.0);
-    const int t0 = G.mesh_tris[3 * bt], t1 = G.mesh_tris[3 * bt + 1], t2 = G.mesh_tris[3 * bt + 2];
-    const double u = bu, v = bv;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        uw[a] = (1.0 - u - v) * G.mesh_vel[3 * t0 + a] + u * G.mesh_vel[3 * t1 + a] + v * G.mesh_vel[3 * t2 + a];
 }
 
 // airfoil link in the chord frame: node position and link direction in
@@ -387,18 +365,16 @@ __device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int z, 
 // Link of boundary node (x, y, z) towards the solid node x - c: fraction q of
 // the link at which the wall is crossed (wall point x_w = x - q c, q in (0,1])
 // and the wall velocity there.  R is the collision arithmetic: double keeps
-// the plain double evaluation; float uses the single-precision link search
-// for the airfoil and the mesh.
+// the plain double evaluation; float uses the single-precision bisection for
+// the airfoil.  Mesh links are found for a whole node at once by
+// mesh_links_warp.
 template <typename R>
 __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G, const DevBody *b,
                                           int x, int y, int z, int cx, int cy, int cz, double &q,
-                                          double uw[3], MeshHit *hit = nullptr)
+                                          double uw[3])
 {
     constexpr bool single = sizeof(R) == 4;
-    if (G.kind == LBM_BODY_MESH) {
-        if (single) mesh_link_f(G, b, x, y, z, cx, cy, cz, q, uw, hit);
-        else mesh_link(G, b, x, y, z, cx, cy, cz, q, uw, hit);
-    } else if (G.kind == LBM_BODY_AIRFOIL && single) {
+    if (G.kind == LBM_BODY_AIRFOIL && single) {
         q = link_airfoil_f(G, b, x, y, cx, cy);
         uw[0] = b->U[0];
         uw[1] = b->U[1];
@@ -483,7 +459,8 @@ __device__ __forceinline__ void swimmer_velocity_tangent(const GeomParams &G, do
 // (A, B, C), n = (B - A) x (C - A), so dq = (dn.(H - A) - n.dA)/(n.c); the
 // barycentric coordinates follow from dH - dA = du e1 + dv e2 + u de1 + v de2
 // (normal equations with e1, e2); u_w = (1-u-v) V_A + u V_B + v V_C.  Vertex
-// positions move only in y, by the midline tangent at the pose's time.
+// positions move only in y, by the midline tangent at the pose's time
+// (per-vertex tangents in G.mesh_dy / G.mesh_dvy).
 __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
                                   double q, const MeshHit &h, double dq[3], double duw[3][3])
 {
@@ -504,10 +481,9 @@ __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const
         for (int a = 0; a < 3; ++a) {
             P[m][a] = G.mesh_pos[3 * tv[m] + a];
             V[m][a] = G.mesh_vel[3 * tv[m] + a];
+            dy[m][a] = G.mesh_dy[3 * tv[m] + a];
+            dvy[m][a] = G.mesh_dvy[3 * tv[m] + a];
         }
-        const double s = G.mesh_rest[3 * tv[m]];
-        swimmer_midline_tangent(G, s, b->t, dy[m]);
-        swimmer_velocity_tangent(G, b->t, s, dvy[m]);
     }
     const double c[3] = {(double)cx, (double)cy, (double)cz};
     double e1[3], e2[3], H[3], n[3];

@@ -329,6 +329,11 @@ __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L
     p[0] = __dadd_rn(sX[0], s);
     p[1] = __dadd_rn(__dadd_rn(sX[1], swimmer_midline(G, s, t)), dy);
     p[2] = __dadd_rn(sX[2], dz);
+    for (int a = 0; a < 3; ++a) {
+        const double r = rint(p[a]);
+        G.mesh_ipos[3 * (size_t)gid + a] = (int)r;
+        G.mesh_frac[3 * (size_t)gid + a] = (float)(p[a] - r);
+    }
     const double U[3] = {sU[0], sU[1], sU[2]};
     double v[3];
     swimmer_velocity(G, U, t, s, v);

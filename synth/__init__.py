@@ -220,3 +220,16 @@ def anguilliform_swimmer(shape=(768, 256, 256), L: float = 128.0, period: float 
                 nu=(L * L / period) / re, L=L, period=period, amp=amp,
                 wavelength=L if wavelength is None else wavelength, ramp=int(ramp),
                 X=tuple(head), mass=swimmer_volume(L), rest=rest, tris=tris, faces=(0,) * 6)
+
+
+def differentiated_swimmer(shape=(256, 128, 128), L: float = 64.0, period: float = 4000.0,
+                           amp: float = 0.125, re: float = 7142.0, segments: int = 150, ring: int = 64):
+    """The swimmer of Sec. 4.3 held in place (no free motion) in a 4L x 2L x 2L
+    periodic box, for gradients of its mean thrust with respect to the
+    kinematic parameters; same midline law, nu = (L^2/T)/Re."""
+    nx, ny, nz = shape
+    rest, tris = swimmer_mesh(L, segments, ring)
+    head = (nx / 2 - L / 2 + 0.137, ny / 2 + 0.371, nz / 2 + 0.293)
+    return dict(name=f"differentiated_swimmer_{nx}x{ny}x{nz}_L{L:g}", shape=shape, nu=(L * L / period) / re,
+                L=L, period=period, amp=amp, wavelength=L, ramp=0, X=head, mass=swimmer_volume(L),
+                rest=rest, tris=tris, faces=(0,) * 6)

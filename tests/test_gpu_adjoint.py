@@ -193,6 +193,20 @@ def test_autograd_function_returns_the_adjoint_gradient():
     assert np.allclose(theta.grad.numpy(), ref["dJ_dtheta"], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_adjoint_near_rest_is_finite(storage):
+    """A swimmer starting in fluid at rest: <dh|dh> is tiny at most nodes,
+    where the stabilizer's derivative must not underflow to inf/NaN."""
+    shape, H = (48, 24, 24), 6
+    lat = _lat(shape, 0.02, storage=storage)
+    lat.set_geometry(_swimmer_geom())
+    lat.init_state(*synth.uniform_fields(shape))
+    out = lat.adjoint(H, (-1.0, 0.0, 0.0), want_lambda0=True)
+    assert np.isfinite(out["J"]) and np.all(np.isfinite(out["dJ_dtheta"]))
+    assert torch.isfinite(out["lambda_0"]).all()
+    assert np.abs(out["dJ_dtheta"]).max() > 0
+
+
 def test_adjoint_rejects_free_bodies_and_16_bit_storage():
     import paper_1608_04658_gb300 as lbm
     lat = _lat((12, 12, 12), 0.05)
