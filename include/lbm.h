@@ -264,8 +264,9 @@ LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *laun
  * exchange), f(horizon) the full populations after the last step.
  * Parameters theta (dJ_dtheta[3]):
  *   MESH: (wave_amp, wave_length, wave_period) of the midline (Sec. 4.3);
+ *   AIRFOIL: (h_amp, h_omega) of the plunge (Sec. 4.2), third entry 0;
  *   other bodies: none (zeros).
- * The body must be held (free_motion = 0); AIRFOIL bodies are not supported.
+ * The body must not move freely (free_motion = 0).
  * Storage FP64 (arithmetic in double) or FP32 (arithmetic in float);
  * 16-bit storage returns LBM_ERR_UNSUPPORTED.
  *

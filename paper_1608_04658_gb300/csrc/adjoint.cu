@@ -686,6 +686,11 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             double dq[3], duw[3][3];
             mesh_link_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
             for (int k = 0; k < 3; ++k) tb[k] = qb * dq[k] + uwb[0] * duw[k][0] + uwb[1] * duw[k][1] + uwb[2] * duw[k][2];
+        } else if (miss && G.kind == LBM_BODY_AIRFOIL) {
+            double dq[2], dX1[2], dU1[2];
+            airfoil_link_tangent(G, b, x, y, cx, cy, q, dq);
+            airfoil_plunge_tangent(G, b->t, dX1, dU1);
+            for (int k = 0; k < 2; ++k) tb[k] = qb * dq[k] + uwb[1] * dU1[k];
         }
         for (int k = 0; k < 3; ++k) {
             double v = tb[k];
@@ -761,6 +766,10 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
             double dv[3];
             swimmer_velocity_tangent(G, b->t, clamp_arc(G, (double)x - b->X[0]), dv);
             for (int k = 0; k < 3; ++k) tb[k] = (double)ub[1] * dv[k];
+        } else if (lane == 0 && G.kind == LBM_BODY_AIRFOIL) {
+            double dX1[2], dU1[2];
+            airfoil_plunge_tangent(G, b->t, dX1, dU1);
+            for (int k = 0; k < 2; ++k) tb[k] = (double)ub[1] * dU1[k];
         }
         if (lane == 0)
             for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] += tb[k];
@@ -1105,8 +1114,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     for (int k = 0; k < 4; ++k)
         if (spec->reserved[k] != 0) return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: reserved fields must be 0");
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
-    if (ctx->has_body && (ctx->G.free_motion || ctx->G.kind == LBM_BODY_AIRFOIL))
-        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held body (no free motion, no airfoil)");
+    if (ctx->has_body && ctx->G.free_motion)
+        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held or prescribed body (no free motion)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
     if (ctx->storage == LBM_FP64) return adjoint_run<double>(ctx, spec, J, dJ_dtheta);

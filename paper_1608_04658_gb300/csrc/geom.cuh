@@ -525,6 +525,41 @@ __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const
     }
 }
 
+// ---------------------------------------------------------------- airfoil tangents
+// Derivatives with respect to theta = (h_amp, h_omega) of the plunge at body
+// time t (Sec. 4.2): X1 = y_base + A sin(w t), U1 = A w cos(w t).
+__device__ __forceinline__ void airfoil_plunge_tangent(const GeomParams &G, double t, double dX1[2], double dU1[2])
+{
+    const double A = G.h_amp, w = G.h_omega, sn = sin(w * t), cs = cos(w * t);
+    dX1[0] = sn;
+    dX1[1] = A * t * cs;
+    dU1[0] = w * cs;
+    dU1[1] = A * cs - A * w * t * sn;
+}
+
+// dq/dtheta of an airfoil link.  The wall point H = x_b - q c stays on the
+// plunging surface phi(H - X) = 0, phi = |eta - y_c(xi)| - t(xi) in the chord
+// frame, so dq = -(grad phi . dX)/(grad phi . c) with dX = (0, dX1, 0).
+__device__ __forceinline__ void airfoil_link_tangent(const GeomParams &G, const DevBody *b, int x, int y, int cx,
+                                                     int cy, double q, double dq[2])
+{
+    const double dx = (double)x - q * cx - b->X[0], dy = (double)y - q * cy - b->X[1];
+    const double xi = (dx * G.ca - dy * G.sa) * G.inv_chord, eta = (dx * G.sa + dy * G.ca) * G.inv_chord;
+    const double p = G.camber_p, xc = fmin(fmax(xi, 1e-12), 1.0);
+    const double yc = xc < p ? G.camber_k1 * (2.0 * p * xc - xc * xc)
+                             : G.camber_k2 * ((1.0 - 2.0 * p) + 2.0 * p * xc - xc * xc);
+    const double ycp = (xc < p ? G.camber_k1 : G.camber_k2) * (2.0 * p - 2.0 * xc);
+    const double *a = G.thick;
+    const double tp = 0.5 * a[0] / sqrt(xc) + a[1] + xc * (2.0 * a[2] + xc * (3.0 * a[3] + xc * 4.0 * a[4]));
+    const double sg = eta - yc >= 0.0 ? 1.0 : -1.0;
+    const double dxi = -sg * ycp - tp, deta = sg;
+    const double gx = (dxi * G.ca + deta * G.sa) * G.inv_chord, gy = (-dxi * G.sa + deta * G.ca) * G.inv_chord;
+    const double gc = gx * cx + gy * cy;
+    double dX1[2], dU1[2];
+    airfoil_plunge_tangent(G, b->t, dX1, dU1);
+    for (int k = 0; k < 2; ++k) dq[k] = gc != 0.0 ? -gy * dX1[k] / gc : 0.0;
+}
+
 // torque arm origin: displacement of (x, y, z) from the body reference point
 // (sphere centre; airfoil leading edge at z = 0; swimmer head on the centre
 // line; the lattice origin otherwise)
