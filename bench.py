@@ -13,8 +13,9 @@ storage forms are reported under "variants".
                     [--workload sphere|airfoil|swimmer]
 
 --workload selects another of the paper's configurations for the same
-measurement: the plunging airfoil (1024x512x64, chord 128, Sec. 4.2) or the
-self-propelled anguilliform swimmer (768x256x256, L = 128, Sec. 4.3).
+measurement: the plunging airfoil (1024x512x64, chord 128, Sec. 4.2), the
+self-propelled anguilliform swimmer (768x256x256, L = 128, Sec. 4.3) or the
+bodiless periodic Taylor-Green box (256^3) that isolates the bulk kernel.
 
 With N > 1 (torchrun) every rank runs an independent replica (the path has
 no data-parallel split without a halo exchange); the value is all ranks'
@@ -55,7 +56,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv"])
+    ap.add_argument("--accuracy-steps", type=int, default=2000,
+                    help="steps of the FP64/FP32/FP16/BF16 sphere comparison (0 to skip it)")
     ap.add_argument("--adjoint-horizon", type=int, default=8000,
                     help="steps of the adjoint/forward measurement (0 to skip it)")
     return ap.parse_args()
@@ -202,7 +205,9 @@ def ncu_traffic(storage: str):
 # ----------------------------------------------------------------- workload
 def workload(shape=None, kind="sphere"):
     import synth
-    if kind == "airfoil":
+    if kind == "tgv":
+        wl = synth.tgv_periodic(256)
+    elif kind == "airfoil":
         wl = synth.plunging_airfoil()
     elif kind == "swimmer":
         wl = synth.anguilliform_swimmer()
@@ -215,8 +220,11 @@ def workload(shape=None, kind="sphere"):
 
 
 def initial_flow(wl):
-    """Quiescent fluid, or the inflow velocity everywhere for the airfoil."""
+    """Quiescent fluid, the inflow velocity everywhere for the airfoil, the
+    Taylor-Green field for the bodiless box."""
     import synth
+    if wl["kind"] == "tgv":
+        return synth.taylor_green_fields(wl["shape"], wl["u0"])
     return synth.uniform_fields(wl["shape"], wl.get("u_face", (0.0, 0.0, 0.0)))
 
 
@@ -233,6 +241,8 @@ def make_lattice(storage, wl, device):
     elif wl["kind"] == "swimmer":
         lat.set_geometry(lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
                                      wl["period"], ramp=bool(wl["ramp"]), free=True, mass=wl["mass"]))
+    elif wl["kind"] == "tgv":
+        pass
     else:
         lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
     rho, u = initial_flow(wl)
@@ -308,6 +318,8 @@ def e2e_storage(storage, wl, args, device):
 
 def oracle_body(wl):
     import oracle
+    if wl["kind"] == "tgv":
+        return None
     if wl["kind"] == "airfoil":
         return oracle.airfoil_body(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
                                    wl["camber_m"], wl["camber_p"], wl["thick"])
@@ -360,6 +372,41 @@ def adjoint_bench(args, world, device):
             "checkpoint_bytes": int((math.ceil(H / K) + K + 3) * 27 * nx * ny * nz * 4)}
 
 
+def accuracy_bench(args, device):
+    """The sedimenting sphere run for N steps with FP64, FP32, FP16 and BF16
+    storage on the GPU: mean hydrodynamic force over the second half and the
+    final settling velocity of each form against the FP64 run (the FP64 GPU
+    path is itself within 1e-12 of the FP64 oracle over 10 steps)."""
+    import numpy as np
+    import torch
+    N = args.accuracy_steps
+    wl = workload(None, "sphere")
+    res, t_ms = {}, {}
+    for st in ("fp64", "fp32", "fp16", "bf16"):
+        lat, _ = make_lattice(st, wl, device)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(N // 2)
+        lat.reset_average()
+        lat.step(N - N // 2)
+        F, _ = lat.forces(averaged=True)
+        t_ms[st] = 1e3 * (time.perf_counter() - t0) / N
+        b = lat.body()
+        res[st] = (np.array(F), np.array(b["U"]))
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    F64, U64 = res["fp64"]
+    out = {"workload": wl["name"], "steps": N, "force_window": "mean over the second half",
+           "reference": "fp64 storage on the GPU", "fp64": {"F_mean_z": F64[2], "U_z": U64[2],
+                                                           "ms_per_step": round(t_ms["fp64"], 4)}}
+    for st in ("fp32", "fp16", "bf16"):
+        F, U = res[st]
+        out[st] = {"F_mean_z": F[2], "U_z": U[2], "drag_rel_err": abs(F[2] - F64[2]) / abs(F64[2]),
+                   "U_rel_err": abs(U[2] - U64[2]) / abs(U64[2]), "ms_per_step": round(t_ms[st], 4)}
+    return out
+
+
 def cpu_baseline(wl, nsteps=None):
     """The FP64 oracle, single-threaded, on the full box of the workload
     (2 steps of the sphere box, 1 step of the larger boxes)."""
@@ -400,6 +447,7 @@ def run_ours(args):
             r = time_storage(st, wl, args, world, device, clocks)
             variants[st] = r
     adj = adjoint_bench(args, world, device) if args.adjoint_horizon > 0 else None
+    acc = accuracy_bench(args, device) if args.accuracy_steps > 0 and rank == 0 else None
     clk = clocks.stop()
     e2e = None if args.no_e2e else e2e_storage(args.storage, wl, args, device)
     cpu = None
@@ -440,6 +488,7 @@ def run_ours(args):
         "gpu_launches": main["launches"],
         "clocks": clk,
         "adjoint": adj,
+        "accuracy": acc,
         "variants": {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],
                           "ms_per_step": round(r["ms"] / args.steps, 5),
                           "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st] / world / peak, 2),

@@ -50,13 +50,37 @@ __device__ __forceinline__ void gather_global(const Lattice &L, const S *__restr
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         g[i] = Codec<S>::load(p + (L.plane[i] + ox[cx_of(i) + 1] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1]));
-    if (kx[0] | kx[2] | ky[0] | ky[2] | kz[0] | kz[2]) {
+    if (!(kx[0] | kx[2] | ky[0] | ky[2] | kz[0] | kz[2])) return;
+    if (sizeof(S) > 2) {
+        // precedence per direction: the largest kind over its three axes
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int k = max(kx[cx_of(i) + 1], max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]));
             if (k == 2) g[i] = Codec<S>::load(p + L.plane[26 - i]);
             else if (k == 1) g[i] = (R)L.g_face[i];
         }
+    } else {
+        // (the shorter form for 16-bit storage, measured faster there) a face
+        // touches the nine directions whose component along its axis points
+        // away from it: equilibrium faces first, then walls, so a wall wins
+        // where a pull leaves through both
+        const int k[3][3] = {{kx[0], kx[1], kx[2]}, {ky[0], ky[1], ky[2]}, {kz[0], kz[1], kz[2]}};
+#pragma unroll
+        for (int pass = 1; pass <= 2; ++pass)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int side = 0; side < 3; side += 2) {
+                    if (k[a][side] != pass) continue;
+                    const int c = side - 1;  // component of the directions concerned
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int ci = a == 0 ? cx_of(i) : a == 1 ? cy_of(i) : cz_of(i);
+                        if (ci != c) continue;
+                        if (pass == 2) g[i] = Codec<S>::load(p + L.plane[26 - i]);
+                        else g[i] = (R)L.g_face[i];
+                    }
+                }
     }
 }
 
