@@ -5,6 +5,7 @@ Bars (max relative error of full populations over fluid nodes): 1e-12 for
 FP64 storage, 2e-6 for FP32, 2e-3 for FP16/BF16 after 10 steps."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synth
@@ -184,6 +185,93 @@ def test_sedimenting_sphere_full_size_sampled(storage):
     # one step from the same stored input: FP32 arithmetic and one rounding to storage
     tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
     assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
+
+
+def _sampled_after_one_step(lat, nodes):
+    """Full populations of the listed nodes after the step, read from the
+    device state without decoding the whole lattice."""
+    _, W = oracle.lattice()
+    g = lat.f.reshape(27, -1)[:, torch.as_tensor(nodes, device=lat.device)].double().cpu().numpy()
+    return (g + W[:, None] * lat.rho0).T
+
+
+def _rough_fields(shape, seed, u_mean=(0.0, 0.0, 0.0)):
+    """Seeded random density and velocity (the parity-field ranges) without
+    the 27-plane noise array, which would not fit comfortably at full size;
+    the steps before the compared one develop the non-equilibrium part."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    rho = (1.0 + 0.01 * (2.0 * synth.uniform(seed, 0, N) - 1.0)).reshape(nz, ny, nx)
+    u = (0.01 * (2.0 * synth.uniform(seed, 1, 3 * N) - 1.0)).reshape(nz, ny, nx, 3) + np.array(u_mean)
+    return rho, u
+
+
+def _full_size_sampled(lat, orc_body, wl, f_fields, storage, seed):
+    lat.step(2)
+    f0 = lat.populations()
+    lat.step(1)
+    flags = lat.flags.cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(seed)
+    bnodes = np.nonzero(flags & 4)[0]
+    unodes = np.nonzero(flags & 8)[0]
+    nodes = np.unique(np.concatenate([bnodes, unodes, rng.integers(0, lat.N, 4000), [0, lat.N - 1]]))
+    got = _sampled_after_one_step(lat, nodes)
+    del lat
+    orc = oracle.Oracle(wl["shape"], nu=wl["nu"], faces=wl["faces"], u_face=wl.get("u_face", (0.0, 0.0, 0.0)),
+                        body=orc_body)
+    orc.set_f(f0)
+    del f0
+    ref = orc.step_sampled(nodes)
+    ok = ~np.isnan(ref[:, 0])
+    assert np.array_equal(ok, (flags[nodes] & 1) == 0)
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
+    assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
+    return len(bnodes), len(unodes)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_plunging_airfoil_full_size_sampled(storage):
+    """Full-size plunging airfoil (1024x512x64, chord 128, equilibrium inflow,
+    outflow, far field) in the benchmark's configuration: after two steps from
+    a seeded random state around the inflow, one step compared at every
+    boundary and refilled node and at 4000 random nodes computed one by one by
+    the oracle."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.plunging_airfoil()
+    shape = wl["shape"]
+    rho, u = _rough_fields(shape, 11, wl["u_face"])
+    geom = (wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"], wl["camber_m"],
+            wl["camber_p"], wl["thick"], 500.0)
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], u_face=wl["u_face"])
+    lat.set_geometry(lbm.airfoil(*geom))
+    lat.init_state(rho, u)
+    del rho, u
+    # the oracle's body starts at the pose after the two warm-up steps
+    geom2 = geom[:-1] + (502.0,)
+    nb, nu_ = _full_size_sampled(lat, oracle.airfoil_body(*geom2), wl, None, storage, 11)
+    assert nb > 10000
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_anguilliform_swimmer_full_size_sampled(storage):
+    """Full-size swimmer (768x256x256, L = 128, 19,200 triangles) in the
+    benchmark's launch configuration, held so that its pose after the warm-up
+    steps is known to the oracle: one step from a seeded random state,
+    compared at every boundary and refilled node and 4000 random nodes."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.anguilliform_swimmer()
+    shape = wl["shape"]
+    rho, u = _rough_fields(shape, 13)
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"])
+    lat.set_geometry(lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
+                                 wl["period"], U=(-0.003, 0.0, 0.0), mass=wl["mass"], t0=700.0))
+    lat.init_state(rho, u)
+    del rho, u
+    # held swimmer (its pose after the warm-up steps is then known exactly)
+    body = oracle.mesh_body(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"], wl["period"],
+                            U=(-0.003, 0.0, 0.0), mass=wl["mass"], t0=702.0)
+    nb, nu_ = _full_size_sampled(lat, body, wl, None, storage, 13)
+    assert nb > 5000
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
