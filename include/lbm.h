@@ -70,9 +70,12 @@ typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 } lbm_stor
 typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_EQ = 2, LBM_FACE_OUTFLOW = 3 } lbm_face;
 
 /* Stabilizer: ANALYTIC is gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>
- * (Sec. 2; gamma = 2 when <dh|dh> underflows).  LBGK forces gamma = 2, which
- * is BGK with relaxation 2 beta. */
-typedef enum { LBM_GAMMA_ANALYTIC = 0, LBM_GAMMA_LBGK = 2 } lbm_gamma_mode;
+ * (Sec. 2; gamma = 2 when <dh|dh> underflows).  EXACT is the root of Eq.
+ * (gamma_min), sum_i dh_i log(f'_i(gamma)/f^eq_i) = 0, on the interval where
+ * every post-collision population stays positive (safeguarded Newton from the
+ * analytic value, at most 40 iterations; not supported by lbm_adjoint_step).
+ * LBGK forces gamma = 2, which is BGK with relaxation 2 beta. */
+typedef enum { LBM_GAMMA_ANALYTIC = 0, LBM_GAMMA_EXACT = 1, LBM_GAMMA_LBGK = 2 } lbm_gamma_mode;
 
 
 typedef struct {

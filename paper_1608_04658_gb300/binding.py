@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OO
 STORAGES = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FACE_PERIODIC, FACE_WALL, FACE_EQ, FACE_OUTFLOW = 0, 1, 2, 3
 BODY_NONE, BODY_SPHERE, BODY_PLANES, BODY_AIRFOIL, BODY_MESH = 0, 1, 2, 3, 4
-GAMMA_ANALYTIC, GAMMA_LBGK = 0, 2
+GAMMA_ANALYTIC, GAMMA_EXACT, GAMMA_LBGK = 0, 1, 2
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
 
 

@@ -1114,6 +1114,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     for (int k = 0; k < 4; ++k)
         if (spec->reserved[k] != 0) return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: reserved fields must be 0");
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
+    if (ctx->L.gamma_mode == LBM_GAMMA_EXACT)
+        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: the exact stabilizer has no adjoint here");
     if (ctx->has_body && ctx->G.free_motion)
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held or prescribed body (no free motion)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;

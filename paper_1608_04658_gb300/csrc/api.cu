@@ -110,7 +110,8 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
         if ((p->face[2 * a] == LBM_FACE_PERIODIC) != (p->face[2 * a + 1] == LBM_FACE_PERIODIC))
             return LBM_ERR_ARG;
     if (!(p->nu >= 0.0) || !std::isfinite(p->nu) || !(p->rho0 > 0.0)) return LBM_ERR_ARG;
-    if (p->gamma_mode != LBM_GAMMA_ANALYTIC && p->gamma_mode != LBM_GAMMA_LBGK) return LBM_ERR_ARG;
+    if (p->gamma_mode != LBM_GAMMA_ANALYTIC && p->gamma_mode != LBM_GAMMA_EXACT && p->gamma_mode != LBM_GAMMA_LBGK)
+        return LBM_ERR_ARG;
     if (p->options != 0) return LBM_ERR_ARG;
 
     lbm_ctx *ctx = new (std::nothrow) lbm_ctx();

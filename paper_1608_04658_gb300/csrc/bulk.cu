@@ -21,7 +21,7 @@ namespace lbm {
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
 
-template <typename S>
+template <typename S, bool EXACT>
 __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const Lattice L, const S *__restrict__ fa,
                                                    S *__restrict__ fb,
                                                    const uint8_t *__restrict__ flags,
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const La
     // the node itself and are replaced afterwards)
     R g[Q];
     gather_global<S>(L, fa, x, y, z, n, g);
-    const bool ok = kbc_collide<R>(g, (R)L.beta, (R)L.inv_beta, (R)L.rho0, L.gamma_mode);
+    const bool ok = kbc_collide<R, EXACT>(g, (R)L.beta, (R)L.inv_beta, (R)L.rho0, L.gamma_mode);
     if (!ok) atomicOr(status, ST_UNSTABLE);
     S *q = fb + n;
 #pragma unroll
@@ -143,7 +143,10 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
         using S = std::remove_pointer_t<decltype(tag)>;
         const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
         dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
-        bulk_kernel<S><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
+        // the exact stabilizer is a separate instance, so the analytic kernel
+        // keeps its registers and code size
+        if (L.gamma_mode == LBM_GAMMA_EXACT) bulk_kernel<S, true><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
+        else bulk_kernel<S, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
         return cudaGetLastError();
     });
 }

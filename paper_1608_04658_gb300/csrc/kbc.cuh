@@ -126,6 +126,59 @@ __device__ __forceinline__ void axis_eq_phi(R u, R e[3], R phi[3], R r[3])
     r[2] = r1 * bm + r1;
 }
 
+// log(1 + x) in the arithmetic type
+__device__ __forceinline__ float log1p_r(float x) { return log1pf(x); }
+__device__ __forceinline__ double log1p_r(double x) { return log1p(x); }
+
+// Exact stabilizer (Eq. gamma_min): the root of
+//   r(g) = sum_i dh_i log(f'_i(g)/f^eq_i) = sum_i dh_i log(1 + e_i - g B_i),
+//   e_i = (dh_i - (2b - 1) ds_i)/f^eq_i,  B_i = b dh_i/f^eq_i,
+// on the interval where every f'_i(g) is positive; r falls monotonically
+// there (r' = -sum dh_i B_i/(1 + e_i - g B_i) <= 0).  Safeguarded Newton from
+// the analytic value g0 with the interval as bracket (bisection when a step
+// leaves it) until the step is below tol, at most 40 iterations.  e and B come from the caller through
+// the per-direction values (dh, ds, 1/f^eq) the function below recomputes.
+template <typename R, typename Terms>
+__device__ R exact_gamma(const Terms &terms, R beta, R g0, R tol)
+{
+    R lo = -R(1e30), hi = R(1e30);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        R dh, ds, ifeq;
+        terms(i, dh, ds, ifeq);
+        const R e = (dh - (R(2) * beta - R(1)) * ds) * ifeq, B = beta * dh * ifeq;
+        if (B > R(0)) hi = fmin(hi, (R(1) + e) / B);
+        else if (B < R(0)) lo = fmax(lo, (R(1) + e) / B);
+    }
+    R g = g0;
+    if (!(g > lo && g < hi)) g = (lo > -R(1e29) && hi < R(1e29)) ? R(0.5) * (lo + hi) : (g <= lo ? lo + R(1) : hi - R(1));
+    for (int it = 0; it < 40; ++it) {
+        R r = 0, dr = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            R dh, ds, ifeq;
+            terms(i, dh, ds, ifeq);
+            const R e = (dh - (R(2) * beta - R(1)) * ds) * ifeq, B = beta * dh * ifeq;
+            const R x = e - g * B;
+            r += dh * log1p_r(x);
+            dr -= dh * B / (R(1) + x);
+        }
+        if (r > R(0)) lo = g;
+        else hi = g;
+        const R step = dr < R(0) ? r / dr : R(0);
+        // converged: the Newton step is below the tolerance (tested before the
+        // bracket, which the last iterate itself now bounds)
+        if (fabs(step) <= tol * fmax(R(1), fabs(g))) {
+            g -= step;
+            break;
+        }
+        R gn = g - step;
+        if (!(gn > lo && gn < hi)) gn = R(0.5) * (lo + hi);
+        g = gn;
+    }
+    return g;
+}
+
 // In-place collision of the 27 shifted populations g[] of one node.
 // Returns false when the density is not finite and positive.
 //
@@ -135,7 +188,7 @@ __device__ __forceinline__ void axis_eq_phi(R u, R e[3], R phi[3], R r[3])
 //   - E_i = Phi_x Phi_y Phi_z - 1 as exy = e_y Phi_x + e_x, E = exy Phi_z + e_z,
 //     and g^eq_i = (rho W_i) E_i + W_i (rho - rho0);
 //   - 1/f^eq_i = Rx Ry Rz with R_a(c) = r_a(c)/w(c) (1/rho folded into Rx).
-template <typename R>
+template <typename R, bool EXACT = false>
 __device__ __forceinline__ bool kbc_collide(R g[Q], R beta, R inv_beta, R rho0, int gamma_mode)
 {
     R Ls[9], Ld[9];
@@ -220,8 +273,17 @@ __device__ __forceinline__ bool kbc_collide(R g[Q], R beta, R inv_beta, R rho0, 
         }
     }
     R gam = R(2);
-    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>())
+    if (gamma_mode != LBM_GAMMA_LBGK && hh > gamma_floor<R>())
         gam = inv_beta - (R(2) - inv_beta) * sh * rcp_fast(hh);
+    if (EXACT && gamma_mode == LBM_GAMMA_EXACT && hh > gamma_floor<R>()) {
+        const auto terms = [&](int i, R &dh, R &ds, R &ifeq) {
+            const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
+            ifeq = (Rx[cx + 1] * Ry[cy + 1]) * Rz[cz + 1];
+            ds = (nz == 1 || nz == 2) ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
+            dh = g[i] - ds;
+        };
+        gam = exact_gamma<R>(terms, beta, gam, sizeof(R) == 8 ? R(1e-14) : R(1e-6));
+    }
     const R c1 = R(1) - beta * gam;
     const R c2 = beta * (gam - R(2));
 #pragma unroll

@@ -54,8 +54,38 @@ __device__ R kbc_collide_lanes(R g, int i, R beta, R inv_beta, R rho0, int gamma
     const R ifeq = act ? inv_rho * inv_weight<R>(i) * pick(rx, cx) * pick(ry, cy) * pick(rz, cz) : R(0);
     const R sh = wsum(ds * dh * ifeq), hh = wsum(dh * dh * ifeq);
     R gam = R(2);
-    if (gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>())
+    if (gamma_mode != LBM_GAMMA_LBGK && hh > gamma_floor<R>())
         gam = inv_beta - (R(2) - inv_beta) * sh * rcp(hh);
+    if (gamma_mode == LBM_GAMMA_EXACT && hh > gamma_floor<R>()) {
+        // exact stabilizer (see exact_gamma) with the directions on the lanes
+        const R e = act ? (dh - (R(2) * beta - R(1)) * ds) * ifeq : R(0);
+        const R B = act ? beta * dh * ifeq : R(0);
+        R lo = B < R(0) ? (R(1) + e) / B : -R(1e30), hi = B > R(0) ? (R(1) + e) / B : R(1e30);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmax(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmin(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        R g = gam;
+        if (!(g > lo && g < hi))
+            g = (lo > -R(1e29) && hi < R(1e29)) ? R(0.5) * (lo + hi) : (g <= lo ? lo + R(1) : hi - R(1));
+        const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+        for (int it = 0; it < 40; ++it) {
+            const R x = e - g * B;
+            const R r = wsum(act ? dh * log1p_r(x) : R(0));
+            const R dr = wsum(act ? -dh * B / (R(1) + x) : R(0));
+            if (r > R(0)) lo = g;
+            else hi = g;
+            const R step = dr < R(0) ? r / dr : R(0);
+            if (fabs(step) <= tol * fmax(R(1), fabs(g))) {
+                g -= step;
+                break;
+            }
+            R gn = g - step;
+            if (!(gn > lo && gn < hi)) gn = R(0.5) * (lo + hi);
+            g = gn;
+        }
+        gam = g;
+    }
     return geq + (R(1) - beta * gam) * d + beta * (gam - R(2)) * ds;
 }
 

@@ -45,6 +45,24 @@ def test_lbgk_mode(storage):
     assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage]
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_exact_stabilizer(storage):
+    """Exact stabilizer (root of Eq. gamma_min by safeguarded Newton on the
+    GPU) vs the oracle's bisection root: rough random state on a periodic box
+    and a moving sphere with refill, 10 steps."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (12, 10, 9)
+    lat, orc = run_pair(shape, 0.01, storage, random_fields(shape, 17), 10, gamma_mode=lbm.GAMMA_EXACT)
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage]
+    shape = (16, 14, 12)
+    geom = lbm.sphere((7.3, 6.6, 5.8), 3.1, U=(0.05, -0.03, 0.02))
+    rho, u, xi = synth.parity_fields(shape, 19)
+    lat, orc = run_pair(shape, 0.02, storage, (rho, 0.3 * u, xi, 1e-3), 10, geom=geom,
+                        gamma_mode=lbm.GAMMA_EXACT)
+    mask = fluid_mask(lat, orc)
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+
+
 def test_taylor_green_32_re1600_fp64_100_steps():
     """Plain method, periodic 32^3 Taylor-Green vortex, u0 = 0.05, Re = 1600,
     100 steps: FP64 parity, mass and momentum conservation, energy decay."""
