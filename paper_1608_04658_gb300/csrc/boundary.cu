@@ -214,10 +214,17 @@ static cudaError_t dispatch(int storage, F &&fn)
     }
 }
 
+// Grid of the list kernels (grid-stride over the list).  The boundary kernel
+// runs beside the bulk kernel, and every resident block of it holds shared
+// memory and registers the bulk kernel could use; LBM_LIST_BLOCKS caps the
+// grid (build-time knob).
+#ifndef LBM_LIST_BLOCKS
+#define LBM_LIST_BLOCKS 152
+#endif
 static int list_blocks(int cap)
 {
     int nb = (cap + BWARPS - 1) / BWARPS;
-    return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
+    return nb < 1 ? 1 : (nb > LBM_LIST_BLOCKS ? LBM_LIST_BLOCKS : nb);
 }
 
 cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
