@@ -74,7 +74,9 @@ class Body(C.Structure):
                 ("mesh_rest", C.POINTER(C.c_double)), ("mesh_tris", C.POINTER(C.c_int)),
                 ("n_vertices", C.c_int), ("n_triangles", C.c_int),
                 ("length", C.c_double), ("wave_amp", C.c_double), ("wave_length", C.c_double),
-                ("wave_period", C.c_double), ("wave_ramp", C.c_int), ("pad2_", C.c_int)]
+                ("wave_period", C.c_double), ("wave_ramp", C.c_int), ("pad2_", C.c_int),
+                ("psi", C.c_double), ("omega", C.c_double), ("Iw", C.c_double), ("Izz", C.c_double),
+                ("com", C.c_double * 2), ("com_dot", C.c_double * 2)]
 
 
 _D = C.POINTER(C.c_double)
@@ -118,6 +120,7 @@ def lib():
             L.orc_mesh_pose.argtypes = [C.c_void_p, _D, _D]
             L.orc_mesh_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
             L.orc_mesh_link.restype = C.c_double
+            L.orc_mesh_mass.argtypes = [C.c_void_p, C.c_double, _D]
             _lib = L
     return _lib
 
@@ -282,6 +285,12 @@ class Oracle:
         lib().orc_mesh_pose(self._ctx, _dp(pos), _dp(vel))
         return pos, vel
 
+    def mesh_mass(self, t: float):
+        """(V, cx, cy, Izz) of the mesh at time t in the body frame, unit density."""
+        out = np.zeros(4)
+        lib().orc_mesh_mass(self._ctx, float(t), _dp(out))
+        return out
+
     def mesh_link(self, x: int, y: int, z: int, i: int):
         """(q, u_w) of the link from node (x, y, z) along -c_i."""
         uw = np.zeros(3)
@@ -338,13 +347,16 @@ def planes_body(y_lo, y_hi, U_lo=(0.0, 0.0, 0.0), U_hi=(0.0, 0.0, 0.0)) -> Body:
 
 
 def mesh_body(X, rest, tris, length, wave_amp, wave_length, wave_period, ramp=False,
-              U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0) -> Body:
+              U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0, psi=0.0, omega=0.0) -> Body:
     """Triangulated swimmer (Sec. 4.3): rest[v] = (s, dy, dz) per vertex, tris
-    (n, 3) vertex indices, head at X, centre line along +x.  The arrays are
-    kept alive by the returned Body."""
+    (n, 3) vertex indices, centre line along +x.  free: False (held), True (x
+    only) or a bit mask (1 x, 2 y, 4 yaw).  Held or free in x only, X is the
+    head; free in y or yaw, X is the centre of mass and psi, omega the yaw
+    angle and rate.  The arrays are kept alive by the returned Body."""
     b = Body()
     b.kind = BODY_MESH
-    b.free_motion = 1 if free else 0
+    b.free_motion = (1 if free else 0) if isinstance(free, bool) else int(free)
+    b.psi, b.omega = float(psi), float(omega)
     rest = np.ascontiguousarray(rest, dtype=np.float64)
     tris = np.ascontiguousarray(tris, dtype=np.int32)
     b._arrays = (rest, tris)

@@ -300,6 +300,13 @@ typedef struct {
     double wave_period;/* T (steps) */
     int wave_ramp;     /* 1: amplitude ramp over the first period */
     int pad2_;
+    /* swimmer free in y or in yaw (free_motion bits 2, 4): X is the centre of
+     * mass and the body frame turns by psi about z */
+    double psi, omega; /* yaw angle and rate */
+    double Iw;         /* angular momentum about the centre of mass, I_zz omega */
+    double Izz;        /* moment of inertia of the current pose */
+    double com[2];     /* centre of mass in the body frame (x, y) at the current pose */
+    double com_dot[2]; /* its central-difference rate */
 } orc_body;
 
 typedef struct {
@@ -397,19 +404,127 @@ static void body_field_velocity(const orc_body *b, double s, double *v)
     v[2] = b->U[2];
 }
 
-/* Vertex positions and velocities of the mesh at the current pose:
- * x = X0 + s, y = (X1 + y(s,t)) + dy, z = X2 + dz. */
+/* Free in y or in yaw: the centre-of-mass frame. */
+static int com_frame(const orc_body *b) { return (b->free_motion & 6) != 0; }
+
+/* Body-frame position of vertex v at time t: (s, y(s,t) + dy, dz). */
+static void body_point(const orc_body *b, int v, double t, double *q)
+{
+    const double *r = b->mesh_rest + 3 * v;
+    q[0] = r[0];
+    q[1] = midline(b, r[0], t) + r[1];
+    q[2] = r[2];
+}
+
+/* Volume, centre of mass (x, y) and moment of inertia about the vertical axis
+ * through it of the closed mesh at time t, in the body frame, for density
+ * rho.  Divergence theorem: for a polynomial p with F . e_a = P, dP/da = p,
+ * the volume integral of p is the sum over triangles of the integral of P n_a;
+ * over a flat triangle the mean of x^k is h_k(x0, x1, x2) / C(k+2, 2) (h_k the
+ * complete homogeneous symmetric polynomial of the vertex coordinates), and
+ * n_a dA integrates to d_a / 2 with d = (v1 - v0) x (v2 - v0).  Hence
+ *   V = sum d_x h1(x)/6,  int x = sum d_x h2(x)/24,  int x^2 = sum d_x h3(x)/60,
+ * and likewise for y. */
+static void mesh_mass(const orc_body *b, double t, double rho, double *V, double *cx, double *cy, double *Izz)
+{
+    double v0 = 0, sx = 0, sy = 0, sxx = 0, syy = 0;
+    for (int k = 0; k < b->n_triangles; ++k) {
+        const int *tr = b->mesh_tris + 3 * k;
+        double P[3][3];
+        for (int m = 0; m < 3; ++m) body_point(b, tr[m], t, P[m]);
+        double e1[3], e2[3], d[3];
+        for (int a = 0; a < 3; ++a) { e1[a] = P[1][a] - P[0][a]; e2[a] = P[2][a] - P[0][a]; }
+        d[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        d[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        d[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double h[2][4];
+        for (int a = 0; a < 2; ++a) {
+            const double x0 = P[0][a], x1 = P[1][a], x2 = P[2][a];
+            h[a][1] = x0 + x1 + x2;
+            h[a][2] = x0 * x0 + x1 * x1 + x2 * x2 + x0 * x1 + x0 * x2 + x1 * x2;
+            h[a][3] = x0 * x0 * x0 + x1 * x1 * x1 + x2 * x2 * x2 + x0 * x0 * (x1 + x2) + x1 * x1 * (x0 + x2) +
+                      x2 * x2 * (x0 + x1) + x0 * x1 * x2;
+        }
+        v0 += d[0] * h[0][1] / 6.0;
+        sx += d[0] * h[0][2] / 24.0;
+        sy += d[1] * h[1][2] / 24.0;
+        sxx += d[0] * h[0][3] / 60.0;
+        syy += d[1] * h[1][3] / 60.0;
+    }
+    *V = v0;
+    *cx = sx / v0;
+    *cy = sy / v0;
+    *Izz = rho * ((sxx + syy) - v0 * (*cx * *cx + *cy * *cy));
+}
+
+/* Body-frame velocity of a material point at arc position s: the midline's
+ * central difference (Sec. 4.3, finite differences of the given deformation). */
+static double midline_rate(const orc_body *b, double s)
+{
+    return (midline(b, s, b->t + 1.0) - midline(b, s, b->t - 1.0)) / 2.0;
+}
+
+/* Velocity of the body material at world point p (current pose).  Head frame:
+ * U + (0, y_rate(s), 0) at s = p_x - X0 (clamped to [0, L]).  Centre-of-mass
+ * frame: U + omega e_z x (p - X) + R(psi) ((0, y_rate(s), 0) - c_dot), with s
+ * the body-frame abscissa of p. */
+static void material_velocity(const orc_body *b, const double *p, double *v)
+{
+    if (!com_frame(b)) {
+        double s = p[0] - b->X[0];
+        body_field_velocity(b, s < 0.0 ? 0.0 : s > b->length ? b->length : s, v);
+        return;
+    }
+    const double cs = cos(b->psi), sn = sin(b->psi);
+    const double rx = p[0] - b->X[0], ry = p[1] - b->X[1];
+    double s = cs * rx + sn * ry + b->com[0];
+    s = s < 0.0 ? 0.0 : s > b->length ? b->length : s;
+    const double wx = -b->com_dot[0], wy = midline_rate(b, s) - b->com_dot[1];
+    v[0] = b->U[0] - b->omega * ry + (cs * wx - sn * wy);
+    v[1] = b->U[1] + b->omega * rx + (sn * wx + cs * wy);
+    v[2] = b->U[2];
+}
+
+/* Vertex positions and velocities of the mesh at the current pose.  Head
+ * frame: x = X0 + s, y = (X1 + y(s,t)) + dy, z = X2 + dz.  Centre-of-mass
+ * frame: X + R(psi) (b - c(t)) with b the body-frame point and c(t) the centre
+ * of mass of the mesh at t, and the velocity of material_velocity. */
 static void mesh_pose(orc_ctx *c)
 {
-    const orc_body *b = &c->b;
+    orc_body *b = &c->b;
     for (int a = 0; a < 3; ++a) { c->box_lo[a] = INFINITY; c->box_hi[a] = -INFINITY; }
+    const int cf = com_frame(b);
+    if (cf) {
+        double V, cx, cy, I, Vp, cxp, cyp, Ip, Vm, cxm, cym, Im;
+        double rho = 1.0;
+        mesh_mass(b, b->t, 1.0, &V, &cx, &cy, &I);
+        rho = b->mass / V;
+        mesh_mass(b, b->t + 1.0, rho, &Vp, &cxp, &cyp, &Ip);
+        mesh_mass(b, b->t - 1.0, rho, &Vm, &cxm, &cym, &Im);
+        b->com[0] = cx;
+        b->com[1] = cy;
+        b->com_dot[0] = (cxp - cxm) / 2.0;
+        b->com_dot[1] = (cyp - cym) / 2.0;
+        b->Izz = rho * I;
+    }
+    const double cs = cos(b->psi), sn = sin(b->psi);
     for (int v = 0; v < b->n_vertices; ++v) {
         const double *r = b->mesh_rest + 3 * v;
         double *p = c->vpos + 3 * v;
-        p[0] = b->X[0] + r[0];
-        p[1] = (b->X[1] + midline(b, r[0], b->t)) + r[1];
-        p[2] = b->X[2] + r[2];
-        body_field_velocity(b, r[0], c->vvel + 3 * v);
+        if (cf) {
+            double q[3];
+            body_point(b, v, b->t, q);
+            const double qx = q[0] - b->com[0], qy = q[1] - b->com[1];
+            p[0] = b->X[0] + (cs * qx - sn * qy);
+            p[1] = b->X[1] + (sn * qx + cs * qy);
+            p[2] = b->X[2] + q[2];
+            material_velocity(b, p, c->vvel + 3 * v);
+        } else {
+            p[0] = b->X[0] + r[0];
+            p[1] = (b->X[1] + midline(b, r[0], b->t)) + r[1];
+            p[2] = b->X[2] + r[2];
+            body_field_velocity(b, r[0], c->vvel + 3 * v);
+        }
         for (int a = 0; a < 3; ++a) {
             if (p[a] < c->box_lo[a]) c->box_lo[a] = p[a];
             if (p[a] > c->box_hi[a]) c->box_hi[a] = p[a];
@@ -507,8 +622,8 @@ static double mesh_link(const orc_ctx *c, double x, double y, double z, const in
     }
     if (best == INFINITY) {
         best = 0.5;
-        double sm = x - 0.5 * ci[0] - b->X[0];
-        body_field_velocity(b, sm < 0.0 ? 0.0 : sm > b->length ? b->length : sm, uw);
+        const double mid[3] = {x - 0.5 * ci[0], y - 0.5 * ci[1], z - 0.5 * ci[2]};
+        material_velocity(b, mid, uw);
     }
     return best;
 }
@@ -563,11 +678,11 @@ static double link_q(const orc_ctx *c, double x, double y, double z, const int *
 /* Velocity of the body surface at the wall point (translation only: the
  * sphere and the channel walls do not rotate; the swimmer's material velocity
  * at the point's arc position). */
-static void wall_velocity(const orc_body *b, double x_solid, double y_solid, double *uw)
+static void wall_velocity(const orc_body *b, double x_solid, double y_solid, double z_solid, double *uw)
 {
     if (b->kind == BODY_MESH) {
-        double s = x_solid - b->X[0];
-        body_field_velocity(b, s < 0.0 ? 0.0 : s > b->length ? b->length : s, uw);
+        const double p[3] = {x_solid, y_solid, z_solid};
+        material_velocity(b, p, uw);
         return;
     }
     if (b->kind == BODY_PLANES) {
@@ -676,7 +791,7 @@ static void refill(orc_ctx *c, int x, int y, int z)
     }
     double rho = cnt ? rsum / cnt : c->p.rho0;
     double uw[3];
-    wall_velocity(&c->b, (double)x, (double)y, uw);
+    wall_velocity(&c->b, (double)x, (double)y, (double)z, uw);
     double dudx[3][3], Pi[9], f[Q];
     velocity_gradient(c, x, y, z, uw, c->solid0, dudx);
     pressure_tensor(rho, uw, dudx, c->p.beta, Pi);
@@ -718,7 +833,7 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
                 q[i] = mesh_link(c, x, y, z, ci, uw[i]);
             } else {
                 q[i] = link_q(c, x, y, z, ci);
-                wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), uw[i]);
+                wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), (double)(z - ci[2]), uw[i]);
             }
             /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
              * the wall and returns reflected (halfway bounce-back). */
@@ -793,6 +908,7 @@ orc_ctx *orc_create(const orc_params *p, const orc_body *b)
         c->vvel = (double *)calloc((size_t)3 * b->n_vertices, sizeof(double));
         if (!c->vpos || !c->vvel) return NULL;
         mesh_pose(c);
+        if (com_frame(&c->b)) c->b.Iw = c->b.Izz * c->b.omega;
     }
     orc_feq(p->rho0, p->u_face, c->feq_face);
     for (int z = 0; z < p->nz; ++z)
@@ -822,6 +938,13 @@ void orc_mesh_pose(const orc_ctx *c, double *pos, double *vel)
 {
     memcpy(pos, c->vpos, sizeof(double) * 3 * c->b.n_vertices);
     memcpy(vel, c->vvel, sizeof(double) * 3 * c->b.n_vertices);
+}
+
+/* Mass properties of the mesh at time t in the body frame for unit density:
+ * out = (V, cx, cy, Izz). */
+void orc_mesh_mass(const orc_ctx *c, double t, double *out)
+{
+    mesh_mass(&c->b, t, 1.0, out, out + 1, out + 2, out + 3);
 }
 
 /* Link fraction q and wall velocity of the link from (x, y, z) along -c_i at
@@ -865,13 +988,23 @@ static void body_update(orc_ctx *c)
         return;
     }
     if (b->kind == BODY_MESH) {
-        /* Sec. 4.3: Newton's equation along the swimming axis by explicit
-         * Euler, X0 += U0, U0 += F0 / m; then the new pose of the mesh */
+        /* Sec. 4.3: Newton's equations by explicit Euler on the free degrees
+         * of freedom (bit 1 x, bit 2 y, bit 4 yaw): X += U, U += F / m;
+         * psi += omega, (I omega) += M_z with I of the new pose (the yaw
+         * equation d(I omega)/dt = M as printed); then the new pose */
         b->t = b->t + 1.0;
-        if (b->free_motion) {
-            const double inv_m = 1.0 / b->mass;
-            b->X[0] = b->X[0] + b->U[0];
-            b->U[0] = b->U[0] + b->F[0] * inv_m;
+        const double inv_m = 1.0 / b->mass;
+        for (int a = 0; a < 2; ++a)
+            if (b->free_motion & (1 << a)) {
+                b->X[a] = b->X[a] + b->U[a];
+                b->U[a] = b->U[a] + b->F[a] * inv_m;
+            }
+        if (b->free_motion & 4) {
+            double V, cx, cy, I;
+            mesh_mass(b, b->t, 1.0, &V, &cx, &cy, &I);
+            b->psi = b->psi + b->omega;
+            b->Iw = b->Iw + b->M[2];
+            b->omega = b->Iw / (b->mass / V * I);
         }
         mesh_pose(c);
         return;

@@ -204,3 +204,131 @@ def test_swimmer_euler_update_along_the_swimming_axis(orc):
     assert b2.X[0] == pytest.approx(X0[0] + 2 * U0, abs=1e-14)
     assert b2.U[0] == pytest.approx(U0 + F1 / m, abs=1e-16)
     assert b2.t == 2.0
+
+
+# ---------------------------------------------------------------- three degrees of freedom
+def _box_mesh(a, b, c):
+    """Closed, outward-oriented triangulation of the box [0,a]x[0,b]x[0,c] in the
+    (s, dy, dz) rest format (12 triangles)."""
+    V = np.array([[x, y, z] for x in (0, a) for y in (0, b) for z in (0, c)], dtype=float)
+    faces = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    T = []
+    for q in faces:
+        T += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+    T = np.array(T, dtype=np.int32)
+    # orient every triangle outwards (normal away from the centre)
+    ctr = V.mean(0)
+    for k, (i, j, l) in enumerate(T):
+        n = np.cross(V[j] - V[i], V[l] - V[i])
+        if np.dot(n, V[i] - ctr) < 0:
+            T[k] = (i, l, j)
+    return V, T
+
+
+def test_mesh_mass_properties_of_a_box(orc):
+    """Divergence-theorem mass properties (volume, centre of mass, moment of
+    inertia about the vertical axis through it) are exact for a polyhedron:
+    box a x b x c -> V = abc, c = (a/2, b/2), Izz = V (a^2 + b^2)/12."""
+    a, b, c = 3.0, 2.0, 1.5
+    V, T = _box_mesh(a, b, c)
+    o = orc.Oracle((24, 24, 24), nu=0.05, body=orc.mesh_body((10.1, 10.2, 10.3), V, T, 3.0, 0.0, 3.0, 50.0))
+    vol, cx, cy, Izz = o.mesh_mass(0.0)
+    assert vol == pytest.approx(a * b * c, rel=1e-14)
+    assert cx == pytest.approx(a / 2, rel=1e-14) and cy == pytest.approx(b / 2, rel=1e-14)
+    assert Izz == pytest.approx(a * b * c * (a * a + b * b) / 12, rel=1e-13)
+
+
+def test_swimmer_mass_properties_track_the_deformation(orc):
+    """The sheared mesh keeps its volume (the midline only moves rings
+    sideways); its centre of mass moves sideways with the mean midline
+    displacement weighted by the cross-section areas."""
+    L = 48.0
+    body = _body(orc, L, 150, 64, (40.0, 24.371, 12.293), amp=0.125, period=64.0)
+    o = orc.Oracle((96, 48, 24), nu=0.02, body=body)
+    m0 = o.mesh_mass(0.0)
+    m1 = o.mesh_mass(17.0)
+    assert m1[0] == pytest.approx(m0[0], rel=1e-12)
+    assert m0[0] == pytest.approx(synth.swimmer_volume(L), rel=0.02)
+    s = np.linspace(0, L, 20001)
+    A = np.pi * synth.swimmer_half_width(s, L) * synth.swimmer_half_height(s, L)
+    for t, m in ((0.0, m0), (17.0, m1)):
+        ym = 0.125 * L * (s / L + 0.03125) / 1.03125 * np.sin(2 * np.pi * (s / L - t / 64.0))
+        assert m[2] == pytest.approx(np.trapezoid(A * ym, s) / np.trapezoid(A, s), abs=2e-3 * L)
+        assert m[1] == pytest.approx(np.trapezoid(A * s, s) / np.trapezoid(A, s), abs=2e-3 * L)
+
+
+def test_rotated_pose_matches_the_analytic_body(orc):
+    """Centre-of-mass frame with a yaw angle: nodes clearly inside / outside
+    the analytic elliptic body rotated by psi about the centre of mass are
+    classified accordingly by ray parity."""
+    L, psi = 40.0, 0.5
+    X = (36.137, 30.371, 12.293)
+    body = _body(orc, L, 150, 96, X, free=4, psi=psi)
+    o = orc.Oracle((72, 60, 24), nu=0.02, body=body)
+    solid = o.solid().astype(bool)
+    vol, cx, cy, _ = o.mesh_mass(0.0)
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in (24, 60, 72)], indexing="ij")
+    rx, ry = x - X[0], y - X[1]
+    s = np.cos(psi) * rx + np.sin(psi) * ry + cx
+    q = -np.sin(psi) * rx + np.cos(psi) * ry + cy
+    w = synth.swimmer_half_width(np.clip(s, 0, L), L)
+    h = synth.swimmer_half_height(np.clip(s, 0, L), L)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        phi = (q / w) ** 2 + ((z - X[2]) / h) ** 2
+    core = (s > 2.0) & (s < L - 2.0)
+    inside = core & (phi < 0.9)
+    outside = (s < -0.7) | (s > L + 0.7) | (core & (phi > 1.1))
+    assert inside.sum() > 200
+    assert solid[inside].all() and not solid[outside].any()
+
+
+def test_three_dof_euler_update(orc):
+    """Free in x, y and yaw (Sec. 4.3, Euler): X += U, U += F/m on x and y,
+    psi += omega, I omega += M_z with I of the new pose; the pose's vertex
+    velocities are the central differences of the poses."""
+    shape = (64, 48, 24)
+    X0 = np.array([30.137, 24.371, 12.293])
+    U0 = np.array([0.004, -0.002, 0.0])
+    body = _body(orc, 24.0, 48, 16, X0, amp=0.125, period=64.0, U=tuple(U0), free=7, omega=2e-3)
+    body.mass = 40.0
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    rho, u, xi = synth.parity_fields(shape, 23)
+    o.init_state(rho, 0.2 * u, xi, 1e-3)
+    b0 = o.body
+    I0 = b0.Izz
+    assert b0.Iw == pytest.approx(I0 * 2e-3, rel=1e-14)
+    vol0 = o.mesh_mass(0.0)[0]
+    assert I0 == pytest.approx(40.0 / vol0 * o.mesh_mass(0.0)[3], rel=1e-14)
+    o.step(1)
+    b1 = o.body
+    assert np.allclose(b1.X[:2], X0[:2] + U0[:2], atol=1e-14, rtol=0) and b1.X[2] == X0[2]
+    assert np.allclose(b1.U[:2], U0[:2], atol=1e-15, rtol=0)   # F of the step before the first is 0
+    assert b1.psi == pytest.approx(2e-3, abs=1e-15)
+    I1 = 40.0 / vol0 * o.mesh_mass(1.0)[3]
+    assert b1.omega == pytest.approx(I0 * 2e-3 / I1, rel=1e-12)
+    F1, M1 = np.array(b1.F), np.array(b1.M)
+    assert np.abs(F1[:2]).max() > 0 and abs(M1[2]) > 0
+    o.step(1)
+    b2 = o.body
+    assert np.allclose(b2.U[:2], U0[:2] + F1[:2] / 40.0, atol=1e-15, rtol=0)
+    assert b2.psi == pytest.approx(2e-3 + b1.omega, abs=1e-15)
+    I2 = 40.0 / vol0 * o.mesh_mass(2.0)[3]
+    assert b2.omega == pytest.approx((I0 * 2e-3 + M1[2]) / I2, rel=1e-12)
+
+
+def test_com_frame_vertex_velocity_is_central_difference(orc):
+    """Held yaw rate and translation in the centre-of-mass frame: the vertex
+    velocity U + omega x r + R (b_dot - c_dot) agrees with the central
+    difference of the actual poses to O(omega^2)."""
+    body = _body(orc, 24.0, 48, 16, (30.137, 24.371, 12.293), amp=0.125, period=64.0,
+                 U=(0.003, 0.001, 0.0), free=7, omega=1e-4)
+    body.mass = 1e30   # forces do not change U, omega changes only with I
+    o = orc.Oracle((64, 48, 24), nu=0.05, body=body)
+    pos, vel = [], []
+    for _ in range(3):
+        p, v = o.mesh_pose()
+        pos.append(p)
+        vel.append(v)
+        o.step_sampled([0])
+    fd = 0.5 * (pos[2] - pos[0])
+    assert np.abs(vel[1] - fd).max() < 1e-5
