@@ -123,10 +123,19 @@ typedef enum {
  *     (edge functions of the (y, z) projection, each edge evaluated from its
  *     lower-index vertex, zero counted positive).  A link's wall point is its
  *     first crossing with a triangle; the wall velocity there is the
- *     barycentric interpolation of the vertex velocities.  With free_motion
- *     the head follows Newton's equation along x by explicit Euler:
- *     X[0] += U[0], then U[0] += F[0]/mass.  t0 is the time of the initial
- *     pose.  The body must stay two nodes clear of every box face; a pose
+ *     barycentric interpolation of the vertex velocities.  free_motion is a
+ *     bit mask of the free degrees of freedom: 1 x, 2 y, 4 yaw.  Held (0) or
+ *     free in x only (1), X is the head and Newton's equation along x is
+ *     advanced by explicit Euler: X[0] += U[0], then U[0] += F[0]/mass.  With
+ *     y or yaw free, X is the centre of mass and the body frame turns by psi
+ *     about z: vertex v sits at X + R(psi) (b_v - c(t)), b_v = (s, y(s,t) + dy,
+ *     dz), c(t) the centre of mass of the mesh (divergence theorem, density
+ *     mass / volume); its velocity is U + omega e_z x (p - X) +
+ *     R(psi) (b_v_dot - c_dot) (central differences); Euler on the free
+ *     degrees: X += U, U += F/mass, psi += omega, I omega += M_z with I the
+ *     moment of inertia about the vertical axis through the centre of mass of
+ *     the new pose (d(I omega)/dt = M of Sec. 4.3).  t0 is the time of the
+ *     initial pose.  The body must stay two nodes clear of every box face; a pose
  *     outside that sets status bit 2 (band overflow), as does a column crossed
  *     more than 32 times or a 2x2x2 cell overlapped by more than 384
  *     triangles. */
@@ -151,6 +160,7 @@ typedef struct {
     double wave_period;        /* MESH: T, steps */
     int32_t wave_ramp;         /* MESH: 1 to ramp the amplitude up over the first period */
     int32_t reserved_mesh;     /* must be 0 */
+    double psi, omega;         /* MESH free in y or yaw: initial yaw angle and rate (rad, rad/step) */
 } lbm_geometry;
 
 /* Body state on the device, read back by lbm_get_body. */
@@ -165,6 +175,8 @@ typedef struct {
     int32_t status;       /* device status bits (1: unstable node, 2: band overflow, 4: timeout) */
     int32_t reserved;
     double t;             /* time of the current pose (prescribed motion), steps */
+    double psi, omega;    /* MESH in the centre-of-mass frame: yaw angle and rate */
+    double Izz;           /* MESH in the centre-of-mass frame: moment of inertia of the pose */
 } lbm_body_state;
 
 typedef struct lbm_ctx lbm_ctx;

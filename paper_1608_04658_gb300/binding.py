@@ -52,7 +52,8 @@ class Geometry(C.Structure):
                 ("mesh_rest", C.POINTER(C.c_double)), ("mesh_tris", C.POINTER(C.c_int32)),
                 ("n_vertices", C.c_int32), ("n_triangles", C.c_int32),
                 ("length", C.c_double), ("wave_amp", C.c_double), ("wave_length", C.c_double),
-                ("wave_period", C.c_double), ("wave_ramp", C.c_int32), ("reserved_mesh", C.c_int32)]
+                ("wave_period", C.c_double), ("wave_ramp", C.c_int32), ("reserved_mesh", C.c_int32),
+                ("psi", C.c_double), ("omega", C.c_double)]
 
 
 class AdjointSpec(C.Structure):
@@ -65,7 +66,7 @@ class BodyState(C.Structure):
                 ("M", C.c_double * 3), ("F_sum", C.c_double * 3), ("M_sum", C.c_double * 3),
                 ("n_sum", C.c_int64), ("n_boundary", C.c_int32), ("n_uncovered", C.c_int32),
                 ("n_links", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
-                ("t", C.c_double)]
+                ("t", C.c_double), ("psi", C.c_double), ("omega", C.c_double), ("Izz", C.c_double)]
 
 
 _lib = None
@@ -181,14 +182,18 @@ def airfoil(le, chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick, t0=0.0
 
 
 def swimmer(X, rest, tris, length, wave_amp, wave_length, wave_period, ramp=False,
-            U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0) -> Geometry:
+            U=(0.0, 0.0, 0.0), free=False, mass=1.0, t0=0.0, psi=0.0, omega=0.0) -> Geometry:
     """Triangulated swimmer (Sec. 4.3): rest (n, 3) = (s, dy, dz) per vertex,
-    tris (m, 3) vertex indices, head at X, centre line along +x.  The arrays
-    are kept alive by the returned Geometry (the library copies them)."""
+    tris (m, 3) vertex indices, centre line along +x.  free: False (held),
+    True (x only) or a bit mask (1 x, 2 y, 4 yaw); held or free in x only, X
+    is the head, otherwise the centre of mass, psi/omega the initial yaw angle
+    and rate.  The arrays are kept alive by the returned Geometry (the
+    library copies them)."""
     import numpy as np
     G = Geometry()
     G.kind = BODY_MESH
-    G.free_motion = 1 if free else 0
+    G.free_motion = (1 if free else 0) if isinstance(free, bool) else int(free)
+    G.psi, G.omega = float(psi), float(omega)
     rest = np.ascontiguousarray(rest, dtype=np.float64)
     tris = np.ascontiguousarray(tris, dtype=np.int32)
     G._arrays = (rest, tris)
@@ -324,7 +329,7 @@ class Lattice:
         return dict(X=np.array(b.X), U=np.array(b.U), F=np.array(b.F), M=np.array(b.M),
                     F_sum=np.array(b.F_sum), M_sum=np.array(b.M_sum), n_sum=b.n_sum,
                     n_boundary=b.n_boundary, n_uncovered=b.n_uncovered, n_links=b.n_links,
-                    status=b.status, t=b.t)
+                    status=b.status, t=b.t, psi=b.psi, omega=b.omega, Izz=b.Izz)
 
     def forces(self, averaged: bool = False):
         F = np.zeros(3)

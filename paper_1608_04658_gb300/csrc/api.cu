@@ -82,6 +82,7 @@ void free_scratch(Scratch &S, bool keep_body)
     cudaFree(S.mesh_rest); cudaFree(S.mesh_pos); cudaFree(S.mesh_vel); cudaFree(S.col_x);
     cudaFree(S.mesh_tris); cudaFree(S.col_count); cudaFree(S.cell_count); cudaFree(S.cell_tri);
     cudaFree(S.mesh_status); cudaFree(S.tri_box); cudaFree(S.mesh_ipos); cudaFree(S.mesh_frac);
+    cudaFree(S.mesh_partials); cudaFree(S.mesh_ticket);
     DevBody *b = S.body;
     S = Scratch{};
     if (keep_body) S.body = b;
@@ -265,9 +266,11 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         const int nv = g->n_vertices, nt = g->n_triangles;
         if (!g->mesh_rest || !g->mesh_tris || nv < 4 || nt < 4 || nv > (1 << 24) || nt > (1 << 24) ||
             !(g->length > 0.0) || g->wave_length == 0.0 || g->wave_period == 0.0 || g->reserved_mesh != 0 ||
-            (g->free_motion && !(g->mass > 0.0)))
+            (g->free_motion && !(g->mass > 0.0)) || g->free_motion < 0 || g->free_motion > 7 ||
+            !std::isfinite(g->psi) || !std::isfinite(g->omega))
             return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh needs vertices, triangles, length > 0, "
-                                          "non-zero wavelength and period (and mass > 0 when free)");
+                                          "non-zero wavelength and period, free_motion in 0..7 (and mass > 0 "
+                                          "when free), finite psi and omega");
         for (long long k = 0; k < 3LL * nt; ++k)
             if (g->mesh_tris[k] < 0 || g->mesh_tris[k] >= nv)
                 return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh triangle index out of range");
@@ -291,10 +294,40 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.wave_length = g->wave_length;
         G.wave_period = g->wave_period;
         G.wave_ramp = g->wave_ramp ? 1 : 0;
+        G.com_frame = (g->free_motion & 6) != 0;
+        G.mass = g->mass;
+        double span[3];
+        for (int a = 0; a < 3; ++a) span[a] = ext[2 * a + 1] - ext[2 * a];
+        if (G.com_frame) {
+            // the body turns about its centre of mass: x and y reach at most
+            // r_max from it.  The midline only shears along y, so the body
+            // frame x of the centre of mass is that of the rest mesh; its y
+            // lies within the envelope.
+            double V = 0.0, Sx = 0.0;
+            for (int k = 0; k < nt; ++k) {
+                const int *tr = g->mesh_tris + 3 * k;
+                const double *p0 = g->mesh_rest + 3 * tr[0], *p1 = g->mesh_rest + 3 * tr[1],
+                             *p2 = g->mesh_rest + 3 * tr[2];
+                const double d = (p1[1] - p0[1]) * (p2[2] - p0[2]) - (p1[2] - p0[2]) * (p2[1] - p0[1]);
+                V += d * (p0[0] + p1[0] + p2[0]) / 6.0;
+                Sx += d * (p0[0] * p0[0] + p1[0] * p1[0] + p2[0] * p2[0] + p0[0] * p1[0] + p0[0] * p2[0] +
+                           p1[0] * p2[0]) / 24.0;
+            }
+            if (!(V > 0.0))
+                return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: mesh volume not positive (triangles must be "
+                                              "oriented outwards)");
+            const double sc = Sx / V;
+            double rmax = 0.0;
+            for (int v = 0; v < nv; ++v) {
+                const double *r = g->mesh_rest + 3 * v;
+                rmax = std::max(rmax, std::hypot(r[0] - sc, std::fabs(r[1]) + 2.0 * env));
+            }
+            span[0] = span[1] = 2.0 * rmax + 3.0;
+        }
         for (int a = 0; a < 3; ++a) {
             G.mesh_ext[2 * a] = ext[2 * a];
             G.mesh_ext[2 * a + 1] = ext[2 * a + 1];
-            const int c = (int)std::ceil(ext[2 * a + 1] - ext[2 * a]) + 9;
+            const int c = (int)std::ceil(span[a]) + 9;
             G.cap[a] = c < n[a] ? c : n[a];
             G.cells[a] = (G.cap[a] + MESH_CELL - 1) / MESH_CELL + 1;
         }
@@ -324,7 +357,10 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
              dalloc(&S.tri_box, 6 * nt) == cudaSuccess && dalloc(&S.col_count, ncols) == cudaSuccess &&
              dalloc(&S.col_x, ncols * MESH_COL_CAP) == cudaSuccess && dalloc(&S.cell_count, ncells) == cudaSuccess &&
              dalloc(&S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && dalloc(&S.mesh_status, 1) == cudaSuccess &&
-             dalloc(&S.mesh_ipos, 3 * nv) == cudaSuccess && dalloc(&S.mesh_frac, 3 * nv) == cudaSuccess;
+             dalloc(&S.mesh_ipos, 3 * nv) == cudaSuccess && dalloc(&S.mesh_frac, 3 * nv) == cudaSuccess &&
+             dalloc(&S.mesh_partials, (nt + MESH_THREADS - 1) / MESH_THREADS * 11) == cudaSuccess &&
+             dalloc(&S.mesh_ticket, 1) == cudaSuccess;
+        if (ok) ok = cudaMemsetAsync(S.mesh_ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
         if (ok)
             ok = cudaMemcpy(S.mesh_rest, g->mesh_rest, 3 * nv * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemcpy(S.mesh_tris, g->mesh_tris, 3 * nt * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -340,6 +376,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.mesh_status = S.mesh_status;
         G.mesh_ipos = S.mesh_ipos;
         G.mesh_frac = S.mesh_frac;
+        G.mesh_partials = S.mesh_partials;
+        G.mesh_ticket = S.mesh_ticket;
     }
     if (!ok) {
         free_scratch(ctx->S, true);
@@ -355,7 +393,11 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         hb[0].U[1] = g->h_amp * g->h_omega * std::cos(g->h_omega * g->t0);
         hb[0].U[2] = 0.0;
     }
-    if (g->kind == LBM_BODY_MESH) hb[0].t = g->t0;
+    if (g->kind == LBM_BODY_MESH) {
+        hb[0].t = g->t0;
+        hb[0].psi = g->psi;
+        hb[0].omega = g->omega;
+    }
     ctx->bcur = 0;
     LBM_CUDA(cudaMemcpyAsync(S.body, hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
     LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
@@ -494,6 +536,9 @@ lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
     out->status = hb.status;
     out->reserved = 0;
     out->t = hb.t;
+    out->psi = hb.psi;
+    out->omega = hb.omega;
+    out->Izz = hb.Izz;
     return LBM_OK;
 }
 

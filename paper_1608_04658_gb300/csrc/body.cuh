@@ -11,6 +11,7 @@ namespace lbm {
 constexpr int MESH_COL_CAP = 32;    // crossings kept per band column
 constexpr int MESH_CELL = 2;        // edge of a triangle cell (lattice units)
 constexpr int MESH_CELL_CAP = 384;  // triangles kept per cell
+constexpr int MESH_THREADS = 256;   // block size of the per-vertex and per-triangle mesh kernels
 
 struct GeomParams {
     int kind;
@@ -38,11 +39,15 @@ struct GeomParams {
     int *cell_count;          // triangles per band cell
     int *cell_tri;            // [cell][MESH_CELL_CAP] triangle indices
     int *mesh_status;         // overflow of the column or cell lists in this step
+    double *mesh_partials;    // centre-of-mass frame: per-block volume sums (9 per block)
+    unsigned *mesh_ticket;    // last-block counter of their reduction
     double *mesh_dy, *mesh_dvy; // adjoint only: theta-tangents of vertex position / velocity (y)
     int n_vertices, n_triangles;
     int cells[3];             // cell grid of the band capacity box
     double length, wave_amp, wave_length, wave_period;
     int wave_ramp;
+    int com_frame;            // free in y or yaw: X is the centre of mass, yaw psi
+    double mass;              // body mass (density mass / mesh volume in the centre-of-mass frame)
     double mesh_ext[6];       // pose extent relative to the head: x, y, z min/max
     int periodic[3];
     int cap[3];          // band capacity per axis
@@ -61,6 +66,12 @@ struct DevBody {
     int n_boundary, n_uncovered, n_links;
     int status;
     double t;            // time of the current pose (prescribed motion)
+    // swimmer in the centre-of-mass frame
+    double psi, omega;   // yaw angle and rate
+    double Iw, Izz;      // angular momentum and moment of inertia about the centre of mass
+    double com[2];       // centre of mass in the body frame at the pose
+    double com_dot[2];   // its central-difference rate
+    int ibox[4];         // lattice x/y box of the pose: x min, x max, y min, y max
 };
 
 // scratch owned by the library for the boundary path
@@ -78,6 +89,8 @@ struct Scratch {
     double *mesh_rest, *mesh_pos, *mesh_vel, *col_x;
     int *mesh_tris, *col_count, *cell_count, *cell_tri, *mesh_status, *mesh_ipos;
     float *tri_box, *mesh_frac;
+    double *mesh_partials;
+    unsigned *mesh_ticket;
 };
 
 // launchers ------------------------------------------------------------------
@@ -92,6 +105,8 @@ cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, 
 cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
 cudaError_t launch_mesh_prepare(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
                                 cudaStream_t s, int *nlaunch);
+cudaError_t launch_mesh_body(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
+                             cudaStream_t s, int *nlaunch);
 cudaError_t launch_mesh_mark_initial(const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                                      uint8_t *flags, cudaStream_t s);
 

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
         } else if (G.kind == LBM_BODY_MESH) {
             // material velocity of the swimmer at the node's arc position
             double v[3];
-            swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - b->X[0]), v);
+            mesh_material_velocity(G, b, (double)x, (double)y, v);
             u[0] = (R)v[0]; u[1] = (R)v[1]; u[2] = (R)v[2];
         }
         R du[3][3], Qt[6];

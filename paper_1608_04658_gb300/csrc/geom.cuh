@@ -114,6 +114,27 @@ __device__ __forceinline__ double clamp_arc(const GeomParams &G, double s)
     return s < 0.0 ? 0.0 : (s > G.length ? G.length : s);
 }
 
+// material velocity of the swimmer at world point (px, py) of the current
+// pose.  Head frame: that of the arc position px - X0.  Centre-of-mass frame:
+// U + omega e_z x (p - X) + R(psi) ((0, y_rate(s), 0) - c_dot) at the
+// body-frame abscissa s of p (Sec. 4.3, rigid motion plus deformation)
+__device__ __forceinline__ void mesh_material_velocity(const GeomParams &G, const DevBody *b, double px, double py,
+                                                       double v[3])
+{
+    if (!G.com_frame) {
+        swimmer_velocity(G, b->U, b->t, clamp_arc(G, px - b->X[0]), v);
+        return;
+    }
+    const double cs = cos(b->psi), sn = sin(b->psi);
+    const double rx = px - b->X[0], ry = py - b->X[1];
+    const double s = clamp_arc(G, cs * rx + sn * ry + b->com[0]);
+    const double rate = (swimmer_midline(G, s, b->t + 1.0) - swimmer_midline(G, s, b->t - 1.0)) / 2.0;
+    const double wx = -b->com_dot[0], wy = rate - b->com_dot[1];
+    v[0] = b->U[0] - b->omega * ry + (cs * wx - sn * wy);
+    v[1] = b->U[1] + b->omega * rx + (sn * wx + cs * wy);
+    v[2] = b->U[2];
+}
+
 // edge value of the (y, z) projection of directed edge u -> v at (y, z),
 // evaluated from the lower-index vertex; sign with zero counted positive in
 // that direction
@@ -287,7 +308,7 @@ __device__ void mesh_links_warp(const GeomParams &G, const DevBody *b, int x, in
             hitout.v = bv;
             if (bt < 0) {
                 q = 0.5;
-                swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - 0.5 * c[0] - b->X[0]), uw);
+                mesh_material_velocity(G, b, (double)x - 0.5 * c[0], (double)y - 0.5 * c[1], uw);
             } else {
                 q = best;
                 const int t0 = G.mesh_tris[3 * bt], t1 = G.mesh_tris[3 * bt + 1], t2 = G.mesh_tris[3 * bt + 2];

@@ -24,11 +24,35 @@ constexpr int FORCE_THREADS = 256;
 
 // Swimmer (Sec. 4.3): Euler step along x when free; band = the pose extent
 // at t and t+1 plus the margin, which must stay inside the box.
-__device__ void advance_mesh(const Lattice &L, const GeomParams &G, const DevBody *prev, bool advance,
-                             double X[3], double U[3], int lo[3], int cnt[3], int &overflow)
+__device__ void advance_mesh(const Lattice &L, const GeomParams &G, const DevBody *prev, const DevBody *next,
+                             bool advance, double X[3], double U[3], int lo[3], int cnt[3], int &overflow)
 {
     const int n[3] = {L.nx, L.ny, L.nz};
     overflow = 0;
+    if (G.com_frame) {
+        // centre-of-mass frame: the pose was advanced by mesh_mass_kernel into
+        // next; band = lattice boxes of both poses (x, y), the z extent, margin
+        for (int a = 0; a < 3; ++a) {
+            X[a] = next->X[a];
+            U[a] = next->U[a];
+        }
+        int l[3], h[3];
+        l[0] = min(prev->ibox[0], next->ibox[0]) - BAND_MARGIN;
+        h[0] = max(prev->ibox[1], next->ibox[1]) + BAND_MARGIN;
+        l[1] = min(prev->ibox[2], next->ibox[2]) - BAND_MARGIN;
+        h[1] = max(prev->ibox[3], next->ibox[3]) + BAND_MARGIN;
+        l[2] = (int)floor(X[2] + G.mesh_ext[4]) - BAND_MARGIN;
+        h[2] = (int)floor(X[2] + G.mesh_ext[5]) + BAND_MARGIN + 1;
+        for (int a = 0; a < 3; ++a) {
+            if (l[a] < 0) { l[a] = 0; overflow = 1; }
+            if (h[a] > n[a] - 1) { h[a] = n[a] - 1; overflow = 1; }
+            int c = h[a] >= l[a] ? h[a] - l[a] + 1 : 0;
+            if (c > G.cap[a]) { c = G.cap[a]; overflow = 1; }
+            lo[a] = l[a];
+            cnt[a] = c;
+        }
+        return;
+    }
     for (int a = 0; a < 3; ++a) {
         X[a] = prev->X[a];
         U[a] = prev->U[a];
@@ -52,11 +76,11 @@ __device__ void advance_mesh(const Lattice &L, const GeomParams &G, const DevBod
 }
 
 // Explicit Euler update of the body (Sec. 4.1) and the band it sweeps.
-__device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBody *prev, double X[3],
-                             double U[3], int lo[3], int cnt[3], int &overflow)
+__device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBody *prev, const DevBody *next,
+                             double X[3], double U[3], int lo[3], int cnt[3], int &overflow)
 {
     if (G.kind == LBM_BODY_MESH) {
-        advance_mesh(L, G, prev, true, X, U, lo, cnt, overflow);
+        advance_mesh(L, G, prev, next, true, X, U, lo, cnt, overflow);
         return;
     }
     const int n[3] = {L.nx, L.ny, L.nz};
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) mark_kernel(const Lattice L, con
     if (threadIdx.x == 0) {
         double X[3], U[3];
         int lo[3], cnt[3], ovf;
-        advance_body(L, G, prev, X, U, lo, cnt, ovf);
+        advance_body(L, G, prev, cur, X, U, lo, cnt, ovf);
         for (int a = 0; a < 3; ++a) { sX[a] = X[a]; slo[a] = lo[a]; scnt[a] = cnt[a]; }
         if (blockIdx.x == 0) {
             for (int a = 0; a < 3; ++a) {
@@ -301,20 +325,25 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const GeomParams G
 }
 
 // ----------------------------------------------------------------- swimmer mesh
-constexpr int MESH_THREADS = 256;
 
 // Pose of the mesh at the new step (or at the current one when !advance):
-// vertex positions x = X0 + s, y = (X1 + y(s,t)) + dy, z = X2 + dz and
-// velocities; clears the column and cell lists of the step.
+// vertex positions x = X0 + s, y = (X1 + y(s,t)) + dy, z = X2 + dz (head
+// frame) or X + R(psi) (b - c(t)) (centre-of-mass frame, with the lattice box
+// of the pose) and velocities; clears the column and cell lists of the step.
 __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L, const GeomParams G,
-                                                                 const DevBody *__restrict__ prev, int advance,
+                                                                 const DevBody *__restrict__ prev,
+                                                                 DevBody *__restrict__ next, int advance,
                                                                  int ncols, int ncells)
 {
     __shared__ double sX[3], sU[3];
     if (threadIdx.x == 0) {
         double X[3], U[3];
         int lo[3], cnt[3], ovf;
-        advance_mesh(L, G, prev, advance != 0, X, U, lo, cnt, ovf);
+        if (G.com_frame) {
+            for (int a = 0; a < 3; ++a) { X[a] = next->X[a]; U[a] = next->U[a]; }
+        } else {
+            advance_mesh(L, G, prev, next, advance != 0, X, U, lo, cnt, ovf);
+        }
         for (int a = 0; a < 3; ++a) { sX[a] = X[a]; sU[a] = U[a]; }
     }
     __syncthreads();
@@ -326,6 +355,31 @@ __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L
     const double t = advance ? __dadd_rn(prev->t, 1.0) : prev->t;
     const double s = G.mesh_rest[3 * gid], dy = G.mesh_rest[3 * gid + 1], dz = G.mesh_rest[3 * gid + 2];
     double *p = G.mesh_pos + 3 * (size_t)gid;
+    if (G.com_frame) {
+        // X + R(psi) (b - c(t)), b = (s, y(s,t) + dy, dz); velocity
+        // U + omega e_z x (p - X) + R(psi) (b_dot - c_dot)
+        const double cs = cos(next->psi), sn = sin(next->psi);
+        const double qx = s - next->com[0], qy = (swimmer_midline(G, s, t) + dy) - next->com[1];
+        p[0] = sX[0] + (cs * qx - sn * qy);
+        p[1] = sX[1] + (sn * qx + cs * qy);
+        p[2] = sX[2] + dz;
+        const double rate = 0.5 * (swimmer_midline(G, s, t + 1.0) - swimmer_midline(G, s, t - 1.0));
+        const double wx = -next->com_dot[0], wy = rate - next->com_dot[1];
+        double *q = G.mesh_vel + 3 * (size_t)gid;
+        q[0] = sU[0] - next->omega * (p[1] - sX[1]) + (cs * wx - sn * wy);
+        q[1] = sU[1] + next->omega * (p[0] - sX[0]) + (sn * wx + cs * wy);
+        q[2] = sU[2];
+        for (int a = 0; a < 3; ++a) {
+            const double r = rint(p[a]);
+            G.mesh_ipos[3 * (size_t)gid + a] = (int)r;
+            G.mesh_frac[3 * (size_t)gid + a] = (float)(p[a] - r);
+        }
+        atomicMin(&next->ibox[0], (int)floor(p[0]));
+        atomicMax(&next->ibox[1], (int)ceil(p[0]));
+        atomicMin(&next->ibox[2], (int)floor(p[1]));
+        atomicMax(&next->ibox[3], (int)ceil(p[1]));
+        return;
+    }
     p[0] = __dadd_rn(sX[0], s);
     p[1] = __dadd_rn(__dadd_rn(sX[1], swimmer_midline(G, s, t)), dy);
     p[2] = __dadd_rn(sX[2], dz);
@@ -346,13 +400,14 @@ __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L
 // Per triangle: its box, the band columns whose line crosses it (with the
 // crossing abscissa) and the band cells its box overlaps.
 __global__ void __launch_bounds__(MESH_THREADS) mesh_bin_kernel(const Lattice L, const GeomParams G,
-                                                                const DevBody *__restrict__ prev, int advance)
+                                                                const DevBody *__restrict__ prev,
+                                                                const DevBody *__restrict__ next, int advance)
 {
     __shared__ int slo[3], scnt[3];
     if (threadIdx.x == 0) {
         double X[3], U[3];
         int lo[3], cnt[3], ovf;
-        advance_mesh(L, G, prev, advance != 0, X, U, lo, cnt, ovf);
+        advance_mesh(L, G, prev, next, advance != 0, X, U, lo, cnt, ovf);
         for (int a = 0; a < 3; ++a) { slo[a] = lo[a]; scnt[a] = cnt[a]; }
     }
     __syncthreads();
@@ -412,7 +467,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) mesh_mark_initial_kernel(const L
     if (threadIdx.x == 0) {
         double X[3], U[3];
         int lo[3], cnt[3], ovf;
-        advance_mesh(L, G, b, false, X, U, lo, cnt, ovf);
+        advance_mesh(L, G, b, b, false, X, U, lo, cnt, ovf);
         for (int a = 0; a < 3; ++a) { slo[a] = lo[a]; scnt[a] = cnt[a]; }
         if (ovf && blockIdx.x == 0) atomicOr(G.mesh_status, 2);
     }
@@ -422,6 +477,132 @@ __global__ void __launch_bounds__(GEOM_THREADS) mesh_mark_initial_kernel(const L
     if (k >= G.cap[0] * G.cap[1] * G.cap[2] || !band_node(L, G, slo, scnt, k, x, y, z)) return;
     const int ly = (k / G.cap[0]) % G.cap[1], lz = k / (G.cap[0] * G.cap[1]);
     if (mesh_inside_column(G, ly + G.cap[1] * lz, (double)x)) flags[x + L.nx * (y + L.ny * z)] = FL_SOLID;
+}
+
+// Centre-of-mass frame: volume sums of the mesh in the body frame at t (V,
+// int x, int y, int x^2, int y^2) and t -+ 1 (V, int x, int y) by the divergence
+// theorem (per triangle d = (v1 - v0) x (v2 - v0), h_k the complete
+// homogeneous symmetric polynomials of its vertex coordinates:
+// V += d_x h1(x)/6, int x += d_x h2(x)/24, int x^2 += d_x h3(x)/60, likewise
+// for y), block partials and a last-block fixed-order sum; that block then
+// advances the body (Sec. 4.3, explicit Euler on the free degrees: X += U,
+// U += F/m, psi += omega, I omega += M_z with I of the new pose) and resets
+// the lattice box the pose kernel fills.
+constexpr int MASS_SUMS = 11;
+
+__device__ __forceinline__ void mesh_triangle_sums(const GeomParams &G, int k, double t, bool second,
+                                                   double &v, double &sx, double &sy, double &sxx, double &syy)
+{
+    double P[3][2];
+    double Z[3];
+    for (int m = 0; m < 3; ++m) {
+        const int iv = G.mesh_tris[3 * k + m];
+        const double s = G.mesh_rest[3 * iv];
+        P[m][0] = s;
+        P[m][1] = swimmer_midline(G, s, t) + G.mesh_rest[3 * iv + 1];
+        Z[m] = G.mesh_rest[3 * iv + 2];
+    }
+    const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], Z[1] - Z[0]};
+    const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], Z[2] - Z[0]};
+    const double dx = e1[1] * e2[2] - e1[2] * e2[1], dy = e1[2] * e2[0] - e1[0] * e2[2];
+    double h1[2], h2[2], h3[2];
+    for (int a = 0; a < 2; ++a) {
+        const double x0 = P[0][a], x1 = P[1][a], x2 = P[2][a];
+        h1[a] = x0 + x1 + x2;
+        h2[a] = x0 * x0 + x1 * x1 + x2 * x2 + x0 * x1 + x0 * x2 + x1 * x2;
+        h3[a] = second ? x0 * x0 * x0 + x1 * x1 * x1 + x2 * x2 * x2 + x0 * x0 * (x1 + x2) + x1 * x1 * (x0 + x2) +
+                             x2 * x2 * (x0 + x1) + x0 * x1 * x2
+                       : 0.0;
+    }
+    v = dx * h1[0] / 6.0;
+    sx = dx * h2[0] / 24.0;
+    sy = dy * h2[1] / 24.0;
+    sxx = dx * h3[0] / 60.0;
+    syy = dy * h3[1] / 60.0;
+}
+
+__global__ void __launch_bounds__(MESH_THREADS) mesh_mass_kernel(const Lattice L, const GeomParams G,
+                                                                 const DevBody *__restrict__ prev,
+                                                                 DevBody *__restrict__ next, int advance)
+{
+    const double t = advance ? prev->t + 1.0 : prev->t;
+    double acc[MASS_SUMS] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < G.n_triangles) {
+        double v, sx, sy, sxx, syy;
+        mesh_triangle_sums(G, k, t, true, v, sx, sy, sxx, syy);
+        acc[0] = v; acc[1] = sx; acc[2] = sy; acc[3] = sxx; acc[4] = syy;
+        mesh_triangle_sums(G, k, t + 1.0, false, v, sx, sy, sxx, syy);
+        acc[5] = v; acc[6] = sx; acc[7] = sy;
+        mesh_triangle_sums(G, k, t - 1.0, false, v, sx, sy, sxx, syy);
+        acc[8] = v; acc[9] = sx; acc[10] = sy;
+    }
+    __shared__ double sm[MESH_THREADS / 32][MASS_SUMS];
+    __shared__ bool last;
+    for (int c = 0; c < MASS_SUMS; ++c) {
+        double x = acc[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < MASS_SUMS) {
+        double x = 0;
+        for (int w = 0; w < MESH_THREADS / 32; ++w) x += sm[w][threadIdx.x];
+        G.mesh_partials[blockIdx.x * MASS_SUMS + threadIdx.x] = x;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(G.mesh_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double S[MASS_SUMS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = w; c < MASS_SUMS; c += MESH_THREADS / 32) {
+        double x = 0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) x += ((volatile double *)G.mesh_partials)[b * MASS_SUMS + c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) S[c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double V = S[0], rho = G.mass / V;
+    const double cx = S[1] / V, cy = S[2] / V;
+    const double Izz = rho * ((S[3] + S[4]) - V * (cx * cx + cy * cy));
+    double X[3], U[3];
+    for (int a = 0; a < 3; ++a) { X[a] = prev->X[a]; U[a] = prev->U[a]; }
+    double psi = prev->psi, omega = prev->omega, Iw;
+    if (advance) {
+        for (int a = 0; a < 2; ++a)
+            if (G.free_motion & (1 << a)) {
+                X[a] = X[a] + U[a];
+                U[a] = U[a] + prev->F[a] * G.inv_mass;
+            }
+        if (G.free_motion & 4) {
+            psi = psi + omega;
+            Iw = prev->Iw + prev->M[2];
+            omega = Iw / Izz;
+        } else {
+            Iw = Izz * omega;
+        }
+    } else {
+        Iw = Izz * omega;
+    }
+    for (int a = 0; a < 3; ++a) { next->X[a] = X[a]; next->U[a] = U[a]; }
+    next->t = t;
+    next->psi = psi;
+    next->omega = omega;
+    next->Iw = Iw;
+    next->Izz = Izz;
+    next->com[0] = cx;
+    next->com[1] = cy;
+    next->com_dot[0] = (S[6] / S[5] - S[9] / S[8]) / 2.0;
+    next->com_dot[1] = (S[7] / S[5] - S[10] / S[8]) / 2.0;
+    next->ibox[0] = 0x7fffffff;
+    next->ibox[1] = -0x7fffffff;
+    next->ibox[2] = 0x7fffffff;
+    next->ibox[3] = -0x7fffffff;
+    *G.mesh_ticket = 0u;
 }
 
 // ----------------------------------------------------------------- launchers
@@ -437,8 +618,9 @@ cudaError_t launch_geometry(const Lattice &L, const GeomParams &G, Scratch &S, i
     const int nb = band_blocks(G);
     DevBody *bp = S.body + prev, *bc = S.body + (prev ^ 1);
     if (G.kind == LBM_BODY_MESH) {
-        cudaError_t e = launch_mesh_prepare(L, G, S, prev, true, s, nlaunch);
-        if (e != cudaSuccess) return e;
+        cudaError_t e;
+        if (G.com_frame && (e = launch_mesh_body(L, G, S, prev, true, s, nlaunch)) != cudaSuccess) return e;
+        if ((e = launch_mesh_prepare(L, G, S, prev, true, s, nlaunch)) != cudaSuccess) return e;
     }
     mark_kernel<<<nb, GEOM_THREADS, 0, s>>>(L, G, bp, bc, flags, S.bforce);
     classify_kernel<<<nb, GEOM_THREADS, 0, s>>>(L, G, bc, flags, S.blist, S.bpos, S.ulist, S.upos);
@@ -472,8 +654,10 @@ cudaError_t launch_mesh_prepare(const Lattice &L, const GeomParams &G, Scratch &
     const int ncells = G.cells[0] * G.cells[1] * G.cells[2];
     const int nb_v = (G.n_vertices + MESH_THREADS - 1) / MESH_THREADS;
     const int nb_t = (G.n_triangles + MESH_THREADS - 1) / MESH_THREADS;
-    mesh_pose_kernel<<<nb_v > 0 ? nb_v : 1, MESH_THREADS, 0, s>>>(L, G, S.body + prev, advance ? 1 : 0, ncols, ncells);
-    mesh_bin_kernel<<<nb_t > 0 ? nb_t : 1, MESH_THREADS, 0, s>>>(L, G, S.body + prev, advance ? 1 : 0);
+    DevBody *next = S.body + (advance ? prev ^ 1 : prev);
+    mesh_pose_kernel<<<nb_v > 0 ? nb_v : 1, MESH_THREADS, 0, s>>>(L, G, S.body + prev, next, advance ? 1 : 0, ncols,
+                                                                    ncells);
+    mesh_bin_kernel<<<nb_t > 0 ? nb_t : 1, MESH_THREADS, 0, s>>>(L, G, S.body + prev, next, advance ? 1 : 0);
     *nlaunch += 2;
     return cudaGetLastError();
 }
@@ -482,9 +666,22 @@ cudaError_t launch_mesh_mark_initial(const Lattice &L, const GeomParams &G, Scra
                                      uint8_t *flags, cudaStream_t s)
 {
     int n = 0;
-    cudaError_t e = launch_mesh_prepare(L, G, S, cur, false, s, &n);
+    cudaError_t e;
+    if (G.com_frame && (e = launch_mesh_body(L, G, S, cur, false, s, &n)) != cudaSuccess) return e;
+    e = launch_mesh_prepare(L, G, S, cur, false, s, &n);
     if (e != cudaSuccess) return e;
     mesh_mark_initial_kernel<<<band_blocks(G), GEOM_THREADS, 0, s>>>(L, G, S.body + cur, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mesh_body(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
+                             cudaStream_t s, int *nlaunch)
+{
+    const int nb_t = (G.n_triangles + MESH_THREADS - 1) / MESH_THREADS;
+    mesh_mass_kernel<<<nb_t > 0 ? nb_t : 1, MESH_THREADS, 0, s>>>(L, G, S.body + prev,
+                                                                   S.body + (advance ? prev ^ 1 : prev),
+                                                                   advance ? 1 : 0);
+    *nlaunch += 1;
     return cudaGetLastError();
 }
 

@@ -36,7 +36,8 @@ def oracle_body(geom):
         rest, tris = geom._arrays
         return oracle.mesh_body(list(geom.X), rest, tris, geom.length, geom.wave_amp, geom.wave_length,
                                 geom.wave_period, ramp=bool(geom.wave_ramp), U=list(geom.U),
-                                free=bool(geom.free_motion), mass=geom.mass, t0=geom.t0)
+                                free=int(geom.free_motion), mass=geom.mass, t0=geom.t0, psi=geom.psi,
+                                omega=geom.omega)
     return oracle.planes_body(geom.y_lo, geom.y_hi, U_lo=list(geom.U_lo), U_hi=list(geom.U_hi))
 
 

@@ -384,6 +384,48 @@ def test_anguilliform_swimmer(storage):
     assert b["status"] == 0
 
 
+@pytest.mark.parametrize("storage", STORAGES)
+def test_three_dof_swimmer(storage):
+    """Swimmer free in x, y and yaw (Sec. 4.3) in a periodic box: the centre of
+    mass frame (pose X + R(psi)(b - c(t)) with the mesh's mass properties by
+    the divergence theorem), the rotating wall velocity in the links and the
+    refill, and the Euler update of X, U, psi and the angular momentum."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (64, 40, 20)
+    rho, u, xi = synth.parity_fields(shape, 23)
+    fields = (rho, 0.2 * u + np.array([0.01, -0.004, 0.0]), xi, 1e-3)
+    geom = _swimmer_geom(lbm, X=(33.137, 19.371, 10.293), U=(-0.004, 0.003, 0.0), free=7, t0=5.0, psi=0.21,
+                         omega=0.004)
+    lat, orc = run_pair(shape, 0.02, storage, fields, 10, geom=geom)
+    mask = fluid_mask(lat, orc)
+    cnt = orc.counters()
+    assert cnt["refill"] > 0 and cnt["error"] == 0
+    assert rel_err(lat.populations(), orc.get_f(), mask) <= TOL[storage]
+    F, M = lat.forces()
+    Fo, Mo = np.array(orc.body.F), np.array(orc.body.M)
+    ftol = {"fp64": 1e-10, "fp32": 1e-4, "fp16": 3e-2, "bf16": 3e-2}[storage]
+    assert np.abs(F - Fo).max() <= ftol * np.abs(Fo).max()
+    assert np.abs(M - Mo).max() <= ftol * np.abs(Mo).max()
+    b = lat.body()
+    if storage == "fp64":
+        xtol = wtol = 1e-13
+    else:
+        # explicit Euler over n steps sums the per-step force (torque) error
+        # at most n(n-1)/2 times into X (psi) and n times into U (omega)
+        n = 10
+        xtol = 0.5 * n * (n - 1) * ftol * np.abs(Fo).max() / geom.mass
+        wtol = 0.5 * n * (n - 1) * ftol * np.abs(Mo).max() / orc.body.Izz
+    for a in range(2):
+        assert b["X"][a] == pytest.approx(orc.body.X[a], abs=xtol)
+        assert b["U"][a] == pytest.approx(orc.body.U[a], abs=xtol)
+    assert b["psi"] == pytest.approx(orc.body.psi, abs=wtol)
+    assert b["omega"] == pytest.approx(orc.body.omega, abs=wtol)
+    assert b["Izz"] == pytest.approx(orc.body.Izz, rel=1e-12)
+    assert abs(b["psi"] - 0.21) > 1e-3 and abs(b["omega"] - 0.004) > 1e-3
+    assert b["t"] == orc.body.t == 15.0
+    assert b["status"] == 0
+
+
 def test_swimmer_rejects_bad_meshes():
     """Host-side checks of lbm_set_geometry for a mesh: triangle indices out
     of range and a pose too close to a box face are rejected, nothing runs."""
