@@ -273,8 +273,10 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     bulk_ms, nbulk = lat.profile_end()
     ms = dist_max(start.elapsed_time(end), world)
     flags = lat.flags
-    bulk_nodes = int(((flags & 5) == 0).sum().item())
     body = lat.body()
+    # the timed launch: all bulk nodes, or those outside the body's sweep box
+    # when the band's nodes have a launch of their own
+    bulk_nodes = lat.N - body["n_band"] if body["n_band"] > 0 else int(((flags & 5) == 0).sum().item())
     F, _ = lat.forces()  # raises on an unstable run
     N = lat.N
     res = dict(ms=ms, glups=N * K * world / (ms * 1e-3) / 1e9, launches=launches,

@@ -173,7 +173,8 @@ typedef struct {
     int32_t n_uncovered;  /* nodes refilled in the last step */
     int32_t n_links;      /* missing populations of the last step */
     int32_t status;       /* device status bits (1: unstable node, 2: band overflow, 4: timeout) */
-    int32_t reserved;
+    int32_t n_band;       /* nodes of the last step's sweep box, updated by a launch of their own after the
+                             body's marks (0 when the step used one flag-aware bulk launch) */
     double t;             /* time of the current pose (prescribed motion), steps */
     double psi, omega;    /* MESH in the centre-of-mass frame: yaw angle and rate */
     double Izz;           /* MESH in the centre-of-mass frame: moment of inertia of the pose */

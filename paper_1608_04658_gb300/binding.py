@@ -65,7 +65,7 @@ class BodyState(C.Structure):
     _fields_ = [("X", C.c_double * 3), ("U", C.c_double * 3), ("F", C.c_double * 3),
                 ("M", C.c_double * 3), ("F_sum", C.c_double * 3), ("M_sum", C.c_double * 3),
                 ("n_sum", C.c_int64), ("n_boundary", C.c_int32), ("n_uncovered", C.c_int32),
-                ("n_links", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("n_links", C.c_int32), ("status", C.c_int32), ("n_band", C.c_int32),
                 ("t", C.c_double), ("psi", C.c_double), ("omega", C.c_double), ("Izz", C.c_double)]
 
 
@@ -329,7 +329,7 @@ class Lattice:
         return dict(X=np.array(b.X), U=np.array(b.U), F=np.array(b.F), M=np.array(b.M),
                     F_sum=np.array(b.F_sum), M_sum=np.array(b.M_sum), n_sum=b.n_sum,
                     n_boundary=b.n_boundary, n_uncovered=b.n_uncovered, n_links=b.n_links,
-                    status=b.status, t=b.t, psi=b.psi, omega=b.omega, Izz=b.Izz)
+                    status=b.status, n_band=b.n_band, t=b.t, psi=b.psi, omega=b.omega, Izz=b.Izz)
 
     def forces(self, averaged: bool = False):
         F = np.zeros(3)

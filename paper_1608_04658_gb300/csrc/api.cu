@@ -139,7 +139,12 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
         delete ctx;
         return LBM_ERR_OOM;
     }
-    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side stream carries the body's geometry and boundary work beside the
+    // bulk launch on the caller's stream: the greatest priority, so its
+    // blocks take the SM slots that bulk blocks free first
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_greatest = 0;
+    if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         free_scratch(ctx->S, false);
@@ -403,6 +408,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
     if (g->kind == LBM_BODY_MESH) {
         LBM_CUDA(launch_mesh_mark_initial(L, G, S, 0, ctx->flags, ctx->stream), "initial marks");
+        LBM_CUDA(launch_sweep_init(L, G, S, 0, ctx->stream), "sweep box");
         int mst = 0;
         LBM_CUDA(cudaMemcpyAsync(&mst, S.mesh_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "mesh status");
         LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
@@ -414,7 +420,10 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         }
         return LBM_OK;
     }
-    if (ctx->has_body) LBM_CUDA(launch_mark_initial(L, G, hb[0].X, ctx->flags, ctx->stream), "initial marks");
+    if (ctx->has_body) {
+        LBM_CUDA(launch_mark_initial(L, G, hb[0].X, ctx->flags, ctx->stream), "initial marks");
+        LBM_CUDA(launch_sweep_init(L, G, S, 0, ctx->stream), "sweep box");
+    }
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
     return LBM_OK;
 }
@@ -441,6 +450,34 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
         int *status = &ctx->S.body[ctx->bcur].status;
         const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;
         int cur = ctx->bcur;
+        if (ctx->has_body && sweep_ahead(ctx->G)) {
+            // the band of this step is known from the previous state: the
+            // nodes outside it run on the caller's stream at once, the body's
+            // geometry, refill, boundary nodes, force and the band's bulk
+            // nodes on the side stream beside them
+            const int prev = ctx->bcur;
+            cur = prev ^ 1;
+            status = &ctx->S.body[cur].status;
+            const int *sweep = ctx->S.body[prev].sweep;
+            LBM_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork");
+            LBM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
+            LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->side, &launches), "geometry");
+            LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->side), "refill");
+            LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side), "boundary");
+            LBM_CUDA(launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches), "forces");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, status, ctx->side, BULK_BAND, sweep,
+                                 ctx->G.cap), "bulk band");
+            LBM_CUDA(cudaEventRecord(ctx->ev_join, ctx->side), "join");
+            LBM_CUDA(prof_mark(ctx, 0), "profile event");
+            LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream, BULK_OUTSIDE, sweep),
+                     "bulk outside");
+            LBM_CUDA(prof_mark(ctx, 1), "profile event");
+            LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
+            launches += 4;
+            ctx->bcur = cur;
+            ctx->cur ^= 1;
+            continue;
+        }
         if (ctx->has_body) {
             const int prev = ctx->bcur;
             cur = prev ^ 1;
@@ -534,7 +571,7 @@ lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
     out->n_uncovered = hb.n_uncovered;
     out->n_links = hb.n_links;
     out->status = hb.status;
-    out->reserved = 0;
+    out->n_band = ctx->has_body && sweep_ahead(ctx->G) ? hb.band_n[0] * hb.band_n[1] * hb.band_n[2] : 0;
     out->t = hb.t;
     out->psi = hb.psi;
     out->omega = hb.omega;

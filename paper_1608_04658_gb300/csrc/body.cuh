@@ -72,6 +72,9 @@ struct DevBody {
     double com[2];       // centre of mass in the body frame at the pose
     double com_dot[2];   // its central-difference rate
     int ibox[4];         // lattice x/y box of the pose: x min, x max, y min, y max
+    // band of the step that starts from this state {lo x, y, z, n x, y, z}
+    // (the box the mark kernel of that step sweeps)
+    int sweep[6];
 };
 
 // scratch owned by the library for the boundary path
@@ -103,6 +106,14 @@ cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Sc
 cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s);
 cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
+cudaError_t launch_sweep_init(const Lattice &L, const GeomParams &G, Scratch &S, int cur, cudaStream_t s);
+// true when the band is known before the step's geometry runs (all bodies but
+// the walls, whose band is the whole box, and the swimmer in the
+// centre-of-mass frame, whose band follows from the pose of the step)
+__host__ __device__ inline bool sweep_ahead(const GeomParams &G)
+{
+    return G.kind != LBM_BODY_NONE && G.kind != LBM_BODY_PLANES && !(G.kind == LBM_BODY_MESH && G.com_frame);
+}
 cudaError_t launch_mesh_prepare(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,
                                 cudaStream_t s, int *nlaunch);
 cudaError_t launch_mesh_body(const Lattice &L, const GeomParams &G, Scratch &S, int prev, bool advance,

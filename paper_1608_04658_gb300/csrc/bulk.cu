@@ -6,7 +6,9 @@
 // run; the +-1 x-shift of a pull touches one extra 32-byte sector per warp,
 // which the neighbouring warp reads anyway, so DRAM traffic stays at one read
 // and one write per population.  Nodes marked SOLID or BOUNDARY are left to
-// the boundary kernel.
+// the boundary kernel.  With a body, one launch takes the nodes outside the
+// body's sweep box (no flag read) while the body's geometry runs beside it,
+// and a second the nodes of the box once their marks are known.
 #include <type_traits>
 
 #include "pull.cuh"
@@ -21,16 +23,53 @@ namespace lbm {
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
 
+// coordinate c on axis a (n nodes) inside the sweep box sw (wrapping on a
+// periodic axis, where lo lies in (-n, n))
+__device__ __forceinline__ bool in_sweep(const int *__restrict__ sw, int a, int c, int n, bool periodic)
+{
+    int d = c - sw[a];
+    if (periodic) {
+        if (d < 0) d += n;
+        else if (d >= n) d -= n;
+    }
+    return (unsigned)d < (unsigned)sw[3 + a];
+}
+
+__device__ __forceinline__ int sweep_coord(int v, int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
 template <typename S, bool EXACT>
 __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const Lattice L, const S *__restrict__ fa,
                                                    S *__restrict__ fb,
                                                    const uint8_t *__restrict__ flags,
-                                                   int *__restrict__ status)
+                                                   int *__restrict__ status,
+                                                   const int *__restrict__ sweep, int mode, int capx,
+                                                   int capy)
 {
     using R = typename Codec<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= L.nx) return;
+    int x, y, z;
+    if (mode == BULK_BAND) {
+        // one thread per position of the capacity box, x fastest
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        const int lx = k % capx, ly = (k / capx) % capy, lz = k / (capx * capy);
+        if (lx >= sweep[3] || ly >= sweep[4] || lz >= sweep[5]) return;
+        x = sweep_coord(sweep[0] + lx, L.nx);
+        y = sweep_coord(sweep[1] + ly, L.ny);
+        z = sweep_coord(sweep[2] + lz, L.nz);
+    } else {
+        x = blockIdx.x * blockDim.x + threadIdx.x;
+        y = blockIdx.y;
+        z = blockIdx.z;
+        if (x >= L.nx) return;
+        // y and z are uniform over the block, so only rows crossing the box
+        // test x
+        if (mode == BULK_OUTSIDE && in_sweep(sweep, 1, y, L.ny, L.face[2] == LBM_FACE_PERIODIC) &&
+            in_sweep(sweep, 2, z, L.nz, L.face[4] == LBM_FACE_PERIODIC) &&
+            in_sweep(sweep, 0, x, L.nx, L.face[0] == LBM_FACE_PERIODIC))
+            return;
+    }
     const int nx = L.nx, ny = L.ny;
     const int n = x + nx * (y + ny * z);
     if (flags != nullptr && (flags[n] & (FL_SOLID | FL_BOUNDARY))) return;
@@ -137,16 +176,28 @@ static cudaError_t dispatch(int storage, F &&fn)
 }
 
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
-                        const uint8_t *flags, int *status, cudaStream_t s)
+                        const uint8_t *flags, int *status, cudaStream_t s, int mode, const int *sweep,
+                        const int *cap)
 {
+    if (mode != BULK_ALL && (!sweep || (mode == BULK_BAND && !cap))) return cudaErrorInvalidValue;
     return dispatch(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
+        int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
         dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
+        int capx = 1, capy = 1;
+        if (mode == BULK_BAND) {
+            bx = 128;
+            capx = cap[0];
+            capy = cap[1];
+            const long long vol = (long long)cap[0] * cap[1] * cap[2];
+            grid = dim3((unsigned)((vol + bx - 1) / bx), 1, 1);
+        }
         // the exact stabilizer is a separate instance, so the analytic kernel
         // keeps its registers and code size
-        if (L.gamma_mode == LBM_GAMMA_EXACT) bulk_kernel<S, true><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
-        else bulk_kernel<S, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status);
+        if (L.gamma_mode == LBM_GAMMA_EXACT)
+            bulk_kernel<S, true><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode, capx, capy);
+        else
+            bulk_kernel<S, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode, capx, capy);
         return cudaGetLastError();
     });
 }

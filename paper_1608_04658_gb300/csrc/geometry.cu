@@ -147,6 +147,26 @@ __device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBod
     }
 }
 
+// band of the step that starts from body state b: the same function of b as
+// the mark kernel of that step evaluates.  The band depends on b's pose,
+// velocity and time only, not on its force, so it is final once the mark
+// kernel has written b.
+__device__ void store_sweep(const Lattice &L, const GeomParams &G, DevBody *b)
+{
+    double X[3], U[3];
+    int lo[3], cnt[3], ovf;
+    advance_body(L, G, b, b, X, U, lo, cnt, ovf);
+    for (int a = 0; a < 3; ++a) {
+        b->sweep[a] = lo[a];
+        b->sweep[3 + a] = cnt[a];
+    }
+}
+
+__global__ void sweep_init_kernel(const Lattice L, const GeomParams G, DevBody *__restrict__ b)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) store_sweep(L, G, b);
+}
+
 // capacity-box index k -> box coordinates; false outside the band
 __device__ __forceinline__ bool band_node(const Lattice &L, const GeomParams &G, const int lo[3],
                                           const int cnt[3], int k, int &x, int &y, int &z)
@@ -191,7 +211,16 @@ __global__ void __launch_bounds__(GEOM_THREADS) mark_kernel(const Lattice L, con
             cur->n_uncovered = 0;
             cur->n_links = 0;
             const bool mesh_ovf = G.kind == LBM_BODY_MESH && *G.mesh_status;
-            cur->status = prev->status | ((ovf || mesh_ovf) ? ST_BAND_OVERFLOW : 0);
+            // the band must be the sweep box the outside bulk launch skipped
+            bool sweep_ok = true;
+            if (sweep_ahead(G))
+                for (int a = 0; a < 3; ++a)
+                    sweep_ok = sweep_ok && prev->sweep[a] == lo[a] && prev->sweep[3 + a] == cnt[a];
+            // atomic: a bulk launch of this step may already have raised a
+            // bit; the slot's older bits are a subset of prev's (they only
+            // accumulate)
+            atomicOr(&cur->status, prev->status | ((ovf || mesh_ovf || !sweep_ok) ? ST_BAND_OVERFLOW : 0));
+            if (sweep_ahead(G)) store_sweep(L, G, cur);
         }
     }
     __syncthreads();
@@ -640,6 +669,13 @@ cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t
 {
     force_kernel<<<S.n_partials, FORCE_THREADS, 0, s>>>(G, S.body + cur, S.bforce, S.partials, S.ticket);
     *nlaunch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_init(const Lattice &L, const GeomParams &G, Scratch &S, int cur, cudaStream_t s)
+{
+    if (!sweep_ahead(G)) return cudaSuccess;
+    sweep_init_kernel<<<1, 32, 0, s>>>(L, G, S.body + cur);
     return cudaGetLastError();
 }
 

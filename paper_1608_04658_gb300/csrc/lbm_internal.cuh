@@ -87,9 +87,18 @@ struct Lattice {
     double g_face[27];  // f^eq(rho0, u_face) - W rho0 for EQ faces
 };
 
+// Which nodes one bulk launch updates.  ALL: every node (those flagged SOLID
+// or BOUNDARY skipped when flags are given).  OUTSIDE: the nodes outside the
+// body's sweep box, which are fluid and no boundary node at t and t+1, so no
+// flag is read.  BAND: the nodes of the sweep box (flags read).  sweep =
+// {lo x, lo y, lo z, n x, n y, n z} of the box, in device memory (wrapping on
+// periodic axes); cap = capacity of the box per axis (the BAND grid).
+enum BulkMode { BULK_ALL = 0, BULK_OUTSIDE = 1, BULK_BAND = 2 };
+
 // launchers ------------------------------------------------------------------
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
-                        const uint8_t *flags, int *status, cudaStream_t s);
+                        const uint8_t *flags, int *status, cudaStream_t s, int mode = BULK_ALL,
+                        const int *sweep = nullptr, const int *cap = nullptr);
 cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
                         const double *u, const double *xi, double amp, cudaStream_t s);
 cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,
