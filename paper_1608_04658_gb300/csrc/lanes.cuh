@@ -143,11 +143,21 @@ __device__ __forceinline__ void stage(const Lattice &L, const S *__restrict__ fa
                                       uint32_t need, R (*sf)[28], R (*su)[4], const int *sok)
 {
     const size_t N = (size_t)L.N;
+    // all loads first, into registers, so they are in flight together (a
+    // store to shared memory right behind each load would wait out one
+    // memory latency per node)
+    R v[Q];
+    uint32_t got = 0;
+#pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int nodek = __shfl_sync(FULL, nk, k);
-        if (!((need >> k) & 1u) || nodek < 0) continue;
-        if (lane < Q) sf[k][lane] = Codec<S>::load(fa + (size_t)lane * N + nodek);
+        const bool use = ((need >> k) & 1u) && nodek >= 0 && lane < Q;
+        v[k] = use ? Codec<S>::load(fa + (size_t)lane * N + nodek) : R(0);
+        got |= (use ? 1u : 0u) << k;
     }
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if ((got >> k) & 1u) sf[k][lane] = v[k];
     __syncwarp();
     if (lane < Q && ((need >> lane) & 1u) && nk >= 0) {
         R r = 0, j[3] = {0, 0, 0};
