@@ -26,7 +26,7 @@
 namespace lbm {
 
 template <typename S>
-__global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
+__global__ void __launch_bounds__(BWARPS * 32, 7) boundary_kernel(
     const Lattice L, const GeomParams G, DevBody *__restrict__ b, const int *__restrict__ blist,
     const int *__restrict__ bpos, double *__restrict__ bforce, const S *__restrict__ fa,
     S *__restrict__ fb, const uint8_t *__restrict__ flags)
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(BWARPS * 32) boundary_kernel(
 }
 
 template <typename S>
-__global__ void __launch_bounds__(BWARPS * 32) refill_kernel(
+__global__ void __launch_bounds__(BWARPS * 32, 7) refill_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
     S *__restrict__ fa, const uint8_t *__restrict__ flags)
 {
