@@ -11,8 +11,8 @@
  *   - Sec. 4.1: Galilean-invariant momentum exchange and Newton's equations
  *     of the sphere with Euler integration (lbm_step, lbm_body_forces).
  *   - Sec. 4.2: plunging airfoil (prescribed plunge); Sec. 4.3: triangulated
- *     anguilliform swimmer with a prescribed midline deformation, free along
- *     the swimming axis (lbm_set_geometry).
+ *     anguilliform swimmer with a prescribed midline deformation, held or
+ *     free in any of x, y and yaw (lbm_set_geometry).
  *
  * Conventions shared by every entry point:
  *   - Every call returns an lbm_status; LBM_OK is 0.  On failure the message
@@ -234,6 +234,36 @@ LBM_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *host_f);
  * unstable since creation. */
 LBM_API lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged);
 
+/* Force record of one step, written by lbm_body_forces_async. */
+typedef struct {
+    double F[3], M[3];  /* force and torque of the fluid on the body, as lbm_body_forces (averaged = 0) */
+    double t;           /* time of the body pose after that step */
+    int32_t status;     /* device status bits after that step (as lbm_body_state.status) */
+    int32_t reserved;
+} lbm_force_record;
+
+/* Depth of the ring of outstanding asynchronous force records per context. */
+#define LBM_RECORD_DEPTH 8
+
+/* Asynchronous form of lbm_body_forces (Sec. 4.1, the same momentum exchange
+ * force): enqueues, behind the work already on the context's stream, a copy
+ * of the last step's force, torque, time and status into *out and returns at
+ * once, so the host can enqueue the next steps while the copy is in flight.
+ * out must be page-locked host memory (cudaHostAlloc / cudaHostRegister, a
+ * pinned torch tensor) owned by the caller and left untouched until
+ * lbm_body_forces_wait on the returned *ticket has returned; LBM_ERR_ARG
+ * otherwise.  The copy runs on a library stream of its own; the step that
+ * would overwrite the copied body state waits for it on the device.  At most
+ * LBM_RECORD_DEPTH records should be outstanding: a ticket older than that is
+ * waited for through a later copy. */
+LBM_API lbm_status lbm_body_forces_async(lbm_ctx *ctx, lbm_force_record *out, int64_t *ticket);
+
+/* Blocks until the record of ticket has landed in host memory, then returns
+ * the error lbm_body_forces would return for that step's status bits
+ * (LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE) or LBM_OK.  LBM_ERR_ARG
+ * for a ticket not yet issued. */
+LBM_API lbm_status lbm_body_forces_wait(lbm_ctx *ctx, int64_t ticket);
+
 /* Full body state (pose, forces, counters, status).  Synchronises. */
 LBM_API lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out);
 
@@ -252,6 +282,29 @@ LBM_API lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 /* Mass, momentum (3) and kinetic energy summed over fluid nodes in double,
  * written to host out[5].  Synchronises. */
 LBM_API lbm_status lbm_totals(lbm_ctx *ctx, double out[5]);
+
+/* Launch order of the steps of a body whose band is known before its
+ * geometry runs (sphere, airfoil, swimmer free at most along x).
+ * LBM_ORDER_SPLIT: the nodes outside the body's band are updated on the
+ * caller's stream while the body's geometry, boundary nodes, force and the
+ * band's nodes run beside them on a library stream.  LBM_ORDER_SEQUENTIAL:
+ * the geometry runs first, then one bulk launch over all nodes beside the
+ * boundary nodes.  Both give the same results bit for bit; which is faster
+ * depends on the size of the box against the body's work.  LBM_ORDER_AUTO
+ * (the default): the first six steps after lbm_set_geometry alternate the two,
+ * the last four of them timed with CUDA events, and the faster is kept. */
+#define LBM_ORDER_AUTO 0
+#define LBM_ORDER_SPLIT 1
+#define LBM_ORDER_SEQUENTIAL 2
+
+/* Requests a launch order (LBM_ORDER_*) for this and later geometries;
+ * LBM_ERR_ARG for another value. */
+LBM_API lbm_status lbm_set_launch_order(lbm_ctx *ctx, int order);
+
+/* The order in use: LBM_ORDER_SPLIT or LBM_ORDER_SEQUENTIAL once chosen,
+ * LBM_ORDER_AUTO while the trial is still open (split steps meanwhile), -1
+ * for a null context. */
+LBM_API int lbm_launch_order(const lbm_ctx *ctx);
 
 /* Number of device kernels the last lbm_step call enqueued. */
 LBM_API int64_t lbm_kernel_launches(const lbm_ctx *ctx);

@@ -69,6 +69,10 @@ class BodyState(C.Structure):
                 ("t", C.c_double), ("psi", C.c_double), ("omega", C.c_double), ("Izz", C.c_double)]
 
 
+# lbm_force_record: F[3], M[3], t (doubles), status, reserved (int32)
+RECORD_DOUBLES = 8
+RECORD_DEPTH = 8
+
 _lib = None
 _D = C.POINTER(C.c_double)
 
@@ -108,6 +112,14 @@ def lib():
         L.lbm_set_populations.restype = C.c_int
         L.lbm_body_forces.argtypes = [vp, _D, _D, C.c_int]
         L.lbm_body_forces.restype = C.c_int
+        L.lbm_body_forces_async.argtypes = [vp, vp, C.POINTER(C.c_int64)]
+        L.lbm_body_forces_async.restype = C.c_int
+        L.lbm_body_forces_wait.argtypes = [vp, C.c_int64]
+        L.lbm_body_forces_wait.restype = C.c_int
+        L.lbm_set_launch_order.argtypes = [vp, C.c_int]
+        L.lbm_set_launch_order.restype = C.c_int
+        L.lbm_launch_order.argtypes = [vp]
+        L.lbm_launch_order.restype = C.c_int
         L.lbm_get_body.argtypes = [vp, C.POINTER(BodyState)]
         L.lbm_get_body.restype = C.c_int
         L.lbm_reset_average.argtypes = [vp]
@@ -337,6 +349,37 @@ class Lattice:
         self._check(lib().lbm_body_forces(self._ctx, F.ctypes.data_as(_D), M.ctypes.data_as(_D),
                                           1 if averaged else 0))
         return F, M
+
+    def set_launch_order(self, order: str):
+        """'auto' (time both in the first steps), 'split' or 'sequential'
+        (lbm_set_launch_order); the results do not depend on it."""
+        self._check(lib().lbm_set_launch_order(self._ctx, {"auto": 0, "split": 1, "sequential": 2}[order]))
+
+    def launch_order(self) -> str:
+        return {0: "auto", 1: "split", 2: "sequential"}[lib().lbm_launch_order(self._ctx)]
+
+    def forces_async(self) -> int:
+        """Enqueue a copy of the last step's force and torque into a pinned
+        host record (lbm_body_forces_async) and return its ticket at once; up
+        to RECORD_DEPTH records may be outstanding."""
+        torch = _torch()
+        if getattr(self, "_rec", None) is None:
+            self._rec = torch.zeros((RECORD_DEPTH, RECORD_DOUBLES), dtype=torch.float64, pin_memory=True)
+            self._rec_next = 0
+        k = self._rec_next % RECORD_DEPTH
+        t = C.c_int64()
+        self._check(lib().lbm_body_forces_async(self._ctx, C.c_void_p(self._rec.data_ptr() + 8 * RECORD_DOUBLES * k),
+                                                C.byref(t)))
+        assert t.value == self._rec_next
+        self._rec_next += 1
+        return t.value
+
+    def forces_wait(self, ticket: int):
+        """Wait for the record of ticket (lbm_body_forces_wait; raises like
+        forces() on a failed step) and return its (F, M)."""
+        self._check(lib().lbm_body_forces_wait(self._ctx, int(ticket)))
+        r = self._rec[ticket % RECORD_DEPTH].numpy()
+        return r[0:3].copy(), r[3:6].copy()
 
     def save(self, path: str):
         """Checkpoint the current state (populations, node marks, body) to path."""

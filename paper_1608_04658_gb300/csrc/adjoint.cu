@@ -1120,6 +1120,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held or prescribed body (no free motion)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
+    if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");
     if (ctx->storage == LBM_FP64) return adjoint_run<double>(ctx, spec, J, dJ_dtheta);
     if (ctx->storage == LBM_FP32) return adjoint_run<float>(ctx, spec, J, dJ_dtheta);
     return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: FP64 or FP32 storage only");

@@ -144,7 +144,9 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     // blocks take the SM slots that bulk blocks free first
     int prio_least = 0, prio_greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_greatest = 0;
-    if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+    bool trial_ok = true;
+    for (cudaEvent_t &e : ctx->ev_trial) trial_ok = trial_ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!trial_ok || cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         free_scratch(ctx->S, false);
@@ -152,6 +154,8 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
         if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+        for (cudaEvent_t e : ctx->ev_trial)
+            if (e) cudaEventDestroy(e);
         delete ctx;
         return LBM_ERR_CUDA;
     }
@@ -176,7 +180,15 @@ void lbm_destroy(lbm_ctx *ctx)
     for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
+    for (cudaEvent_t e : ctx->ev_trial) cudaEventDestroy(e);
     cudaStreamDestroy(ctx->side);
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaEventDestroy(ctx->ev_step);
+        for (cudaEvent_t e : ctx->ev_copy) cudaEventDestroy(e);
+        for (cudaEvent_t e : ctx->ev_slot) cudaEventDestroy(e);
+        cudaStreamDestroy(ctx->copy);
+    }
     free_scratch(ctx->S, false);
     cudaFree(ctx->plane);
     cudaFree(ctx->tot_partials);
@@ -202,10 +214,13 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: unknown body kind");
     const Lattice &L = ctx->L;
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    LBM_CUDA(drain_records(ctx), "record copies");
     free_scratch(ctx->S, true);
     ctx->has_body = g->kind != LBM_BODY_NONE;
     GeomParams &G = ctx->G;
     G = GeomParams{};
+    ctx->order = ctx->order_request;
+    ctx->trial = 0;
     G.kind = g->kind;
     G.free_motion = g->free_motion;
     G.R = g->R;
@@ -439,22 +454,93 @@ static cudaError_t prof_mark(lbm_ctx *ctx, int which)
     return e;
 }
 
+// Geometry and refill first, then the boundary nodes and the force on the
+// side stream beside one bulk launch over all nodes (flags read when there is
+// a body).
+static cudaError_t sequential_step(lbm_ctx *ctx, void *fa, void *fb, int &cur, int *&status, int *launches_out)
+{
+    int &launches = *launches_out;
+    const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;
+    cudaError_t e;
+    if (ctx->has_body) {
+        const int prev = ctx->bcur;
+        cur = prev ^ 1;
+        status = &ctx->S.body[cur].status;
+        if ((e = launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->stream, &launches)) != cudaSuccess ||
+            (e = launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->stream)) != cudaSuccess)
+            return e;
+        launches += 1;
+        // the boundary nodes and the force reduction run on a side stream
+        // beside the bulk kernel (they write disjoint nodes)
+        if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess ||
+            (e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side)) !=
+                cudaSuccess ||
+            (e = launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess)
+            return e;
+        launches += 1;
+    }
+    if ((e = prof_mark(ctx, 0)) != cudaSuccess ||
+        (e = launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream)) != cudaSuccess ||
+        (e = prof_mark(ctx, 1)) != cudaSuccess)
+        return e;
+    if (ctx->has_body && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess) return e;
+    launches += 1;
+    return cudaSuccess;
+}
+
+// Chooses the launch order once the trial steps have run: the order whose
+// two timed steps took less (the first pair of trial steps only warms up).
+static void choose_order(lbm_ctx *ctx)
+{
+    if (ctx->order != ORDER_UNDECIDED || ctx->trial < TRIAL_STEPS) return;
+    if (cudaEventQuery(ctx->ev_trial[4]) != cudaSuccess) {
+        cudaGetLastError();  // not reached yet: keep the split order meanwhile
+        return;
+    }
+    float t[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventElapsedTime(&t[k], ctx->ev_trial[k], ctx->ev_trial[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->order = ORDER_SPLIT;
+            return;
+        }
+    ctx->order = (t[0] + t[2] <= t[1] + t[3]) ? ORDER_SPLIT : ORDER_SEQUENTIAL;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "lbm_step: nsteps < 0");
     if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step: state not initialised");
     int launches = 0;
+    choose_order(ctx);
     for (int s = 0; s < nsteps; ++s) {
         void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
         int *status = &ctx->S.body[ctx->bcur].status;
-        const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;
         int cur = ctx->bcur;
-        if (ctx->has_body && sweep_ahead(ctx->G)) {
-            // the band of this step is known from the previous state: the
-            // nodes outside it run on the caller's stream at once, the body's
-            // geometry, refill, boundary nodes, force and the band's bulk
-            // nodes on the side stream beside them
+        // a step writes the body slot other than the current one: it waits
+        // for a pending record copy out of that slot
+        if (ctx->has_body && ctx->slot_pending[ctx->bcur ^ 1]) {
+            LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_slot[ctx->bcur ^ 1], 0), "record wait");
+            ctx->slot_pending[ctx->bcur ^ 1] = false;
+        }
+        // the band of this step is known from the previous state: split, the
+        // nodes outside it run on the caller's stream at once and the body's
+        // geometry, refill, boundary nodes, force and the band's bulk nodes on
+        // the side stream beside them; sequential, the geometry and refill run
+        // first and the boundary nodes beside one flag-aware bulk launch.  The
+        // results are the same; the trial steps time both.
+        const bool ahead = ctx->has_body && sweep_ahead(ctx->G);
+        bool split = ahead && ctx->order != ORDER_SEQUENTIAL;
+        const bool trial = ahead && ctx->order == ORDER_UNDECIDED && ctx->trial < TRIAL_STEPS;
+        if (trial) {
+            split = ctx->trial % 2 == 0;
+            if (ctx->trial >= 2) LBM_CUDA(cudaEventRecord(ctx->ev_trial[ctx->trial - 2], ctx->stream), "trial");
+        }
+        ctx->last_split = split;
+        if (split) {
             const int prev = ctx->bcur;
             cur = prev ^ 1;
             status = &ctx->S.body[cur].status;
@@ -474,33 +560,10 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
             LBM_CUDA(prof_mark(ctx, 1), "profile event");
             LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
             launches += 4;
-            ctx->bcur = cur;
-            ctx->cur ^= 1;
-            continue;
+        } else {
+            LBM_CUDA(sequential_step(ctx, fa, fb, cur, status, &launches), "step");
         }
-        if (ctx->has_body) {
-            const int prev = ctx->bcur;
-            cur = prev ^ 1;
-            status = &ctx->S.body[cur].status;
-            LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->stream, &launches), "geometry");
-            LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->stream), "refill");
-            launches += 1;
-        }
-        // the boundary nodes and the force reduction run on a side stream beside
-        // the bulk kernel (they write disjoint nodes)
-        if (ctx->has_body) {
-            LBM_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork");
-            LBM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
-            LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side), "boundary");
-            LBM_CUDA(launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches), "forces");
-            LBM_CUDA(cudaEventRecord(ctx->ev_join, ctx->side), "join");
-            launches += 1;
-        }
-        LBM_CUDA(prof_mark(ctx, 0), "profile event");
-        LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream), "bulk");
-        LBM_CUDA(prof_mark(ctx, 1), "profile event");
-        if (ctx->has_body) LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
-        launches += 1;
+        if (trial && ++ctx->trial == TRIAL_STEPS) LBM_CUDA(cudaEventRecord(ctx->ev_trial[4], ctx->stream), "trial");
         ctx->bcur = cur;
         ctx->cur ^= 1;
     }
@@ -508,7 +571,21 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     return LBM_OK;
 }
 
+
 int lbm_current_buffer(const lbm_ctx *ctx) { return ctx ? ctx->cur : -1; }
+
+lbm_status lbm_set_launch_order(lbm_ctx *ctx, int order)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (order != LBM_ORDER_AUTO && order != LBM_ORDER_SPLIT && order != LBM_ORDER_SEQUENTIAL)
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_launch_order: unknown order");
+    ctx->order_request = order;
+    ctx->order = order;
+    ctx->trial = 0;
+    return LBM_OK;
+}
+
+int lbm_launch_order(const lbm_ctx *ctx) { return ctx ? ctx->order : -1; }
 
 int64_t lbm_kernel_launches(const lbm_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
@@ -571,7 +648,7 @@ lbm_status lbm_get_body(lbm_ctx *ctx, lbm_body_state *out)
     out->n_uncovered = hb.n_uncovered;
     out->n_links = hb.n_links;
     out->status = hb.status;
-    out->n_band = ctx->has_body && sweep_ahead(ctx->G) ? hb.band_n[0] * hb.band_n[1] * hb.band_n[2] : 0;
+    out->n_band = ctx->has_body && ctx->last_split ? hb.band_n[0] * hb.band_n[1] * hb.band_n[2] : 0;
     out->t = hb.t;
     out->psi = hb.psi;
     out->omega = hb.omega;
@@ -599,6 +676,59 @@ lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged)
     if (b.status & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
     if (b.status & ST_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (b.status & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
+    return LBM_OK;
+}
+
+lbm_status lbm_body_forces_async(lbm_ctx *ctx, lbm_force_record *out, int64_t *ticket)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!out || !ticket) return fail(ctx, LBM_ERR_ARG, "lbm_body_forces_async: null argument");
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, out) != cudaSuccess || attr.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return fail(ctx, LBM_ERR_ARG, "lbm_body_forces_async: the record must be page-locked host memory");
+    }
+    if (!ctx->copy) {
+        bool ok = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < LBM_RECORD_DEPTH; ++k)
+            ok = cudaEventCreateWithFlags(&ctx->ev_copy[k], cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < 2; ++k)
+            ok = cudaEventCreateWithFlags(&ctx->ev_slot[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return fail(ctx, LBM_ERR_CUDA, "lbm_body_forces_async: stream or event creation failed");
+    }
+    const int slot = ctx->bcur;
+    const DevBody *src = ctx->S.body + slot;
+    const int k = (int)(ctx->next_ticket % LBM_RECORD_DEPTH);
+    LBM_CUDA(cudaEventRecord(ctx->ev_step, ctx->stream), "record step");
+    LBM_CUDA(cudaStreamWaitEvent(ctx->copy, ctx->ev_step, 0), "record wait");
+    // F and M are adjacent in both structures
+    LBM_CUDA(cudaMemcpyAsync(out->F, src->F, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->copy), "record F, M");
+    LBM_CUDA(cudaMemcpyAsync(&out->t, &src->t, sizeof(double), cudaMemcpyDeviceToHost, ctx->copy), "record t");
+    LBM_CUDA(cudaMemcpyAsync(&out->status, &src->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->copy),
+             "record status");
+    LBM_CUDA(cudaEventRecord(ctx->ev_copy[k], ctx->copy), "record done");
+    LBM_CUDA(cudaEventRecord(ctx->ev_slot[slot], ctx->copy), "slot done");
+    ctx->slot_pending[slot] = true;
+    ctx->rec[k] = out;
+    *ticket = ctx->next_ticket++;
+    return LBM_OK;
+}
+
+lbm_status lbm_body_forces_wait(lbm_ctx *ctx, int64_t ticket)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (ticket < 0 || ticket >= ctx->next_ticket)
+        return fail(ctx, LBM_ERR_ARG, "lbm_body_forces_wait: ticket not issued");
+    // an older ticket's ring entry was recorded again by a later copy, which
+    // lands after it
+    const int k = (int)(ticket % LBM_RECORD_DEPTH);
+    LBM_CUDA(cudaEventSynchronize(ctx->ev_copy[k]), "record wait");
+    if (ticket < ctx->next_ticket - LBM_RECORD_DEPTH) return LBM_OK;
+    const int st = ctx->rec[k]->status;
+    if (st & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
+    if (st & ST_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
     return LBM_OK;
 }
 
@@ -702,6 +832,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path)
         return fail(ctx, LBM_ERR_ARG, std::string("lbm_load: ") + path + " does not match this context");
     }
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
+    LBM_CUDA(drain_records(ctx), "record copies");
     bool ok = copy_from_file(fp, ctx->f[ctx->cur], (size_t)h.pop_bytes, ctx->stream) &&
               copy_from_file(fp, ctx->flags, (size_t)h.flag_bytes, ctx->stream) &&
               copy_from_file(fp, ctx->S.body + ctx->bcur, sizeof(DevBody), ctx->stream);

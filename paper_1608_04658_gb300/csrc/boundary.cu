@@ -25,8 +25,16 @@
 
 namespace lbm {
 
+// Minimum resident blocks per SM for the boundary and refill kernels: 7
+// blocks of 128 threads cap them at 72 registers, so each of their blocks
+// takes the registers of one bulk block on the SM it shares with the bulk
+// launch beside it.
+#ifndef LBM_LIST_MIN_BLOCKS
+#define LBM_LIST_MIN_BLOCKS 7
+#endif
+
 template <typename S>
-__global__ void __launch_bounds__(BWARPS * 32, 7) boundary_kernel(
+__global__ void __launch_bounds__(BWARPS * 32, LBM_LIST_MIN_BLOCKS) boundary_kernel(
     const Lattice L, const GeomParams G, DevBody *__restrict__ b, const int *__restrict__ blist,
     const int *__restrict__ bpos, double *__restrict__ bforce, const S *__restrict__ fa,
     S *__restrict__ fb, const uint8_t *__restrict__ flags)
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(BWARPS * 32, 7) boundary_kernel(
 }
 
 template <typename S>
-__global__ void __launch_bounds__(BWARPS * 32, 7) refill_kernel(
+__global__ void __launch_bounds__(BWARPS * 32, LBM_LIST_MIN_BLOCKS) refill_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
     S *__restrict__ fa, const uint8_t *__restrict__ flags)
 {
@@ -217,14 +225,23 @@ static cudaError_t dispatch(int storage, F &&fn)
 // Grid of the list kernels (grid-stride over the list).  The boundary kernel
 // runs beside the bulk kernel, and every resident block of it holds shared
 // memory and registers the bulk kernel could use; LBM_LIST_BLOCKS caps the
-// grid (build-time knob).
+// grid (build-time knob; two blocks per SM measured best for the sphere and
+// the airfoil with the 72-register cap, FP16 sphere step 0.178 -> 0.167 ms
+// against one block per SM).
 #ifndef LBM_LIST_BLOCKS
-#define LBM_LIST_BLOCKS 152
+#define LBM_LIST_BLOCKS 304
 #endif
-static int list_blocks(int cap)
+// The swimmer's boundary nodes each carry a triangle search, so its
+// boundary kernel is the long part of the body's launch chain:
+// LBM_MESH_LIST_BLOCKS gives it more blocks (608 took the 256x128x128
+// swimmer's step from 0.359 to 0.256 ms).
+#ifndef LBM_MESH_LIST_BLOCKS
+#define LBM_MESH_LIST_BLOCKS 608
+#endif
+static int list_blocks(int cap, int max_blocks = LBM_LIST_BLOCKS)
 {
     int nb = (cap + BWARPS - 1) / BWARPS;
-    return nb < 1 ? 1 : (nb > LBM_LIST_BLOCKS ? LBM_LIST_BLOCKS : nb);
+    return nb < 1 ? 1 : (nb > max_blocks ? max_blocks : nb);
 }
 
 cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
@@ -232,8 +249,9 @@ cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, 
 {
     return dispatch(storage, [&](auto tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
-        boundary_kernel<T><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, s>>>(
-            L, G, S.body + cur, S.blist, S.bpos, S.bforce, (const T *)fa, (T *)fb, flags);
+        const int nb = list_blocks(G.cap_boundary, G.kind == LBM_BODY_MESH ? LBM_MESH_LIST_BLOCKS : LBM_LIST_BLOCKS);
+        boundary_kernel<T><<<nb, BWARPS * 32, 0, s>>>(L, G, S.body + cur, S.blist, S.bpos, S.bforce, (const T *)fa,
+                                                      (T *)fb, flags);
         return cudaGetLastError();
     });
 }

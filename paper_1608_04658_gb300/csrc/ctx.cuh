@@ -7,6 +7,12 @@
 
 #include "body.cuh"
 
+// launch orders of a step whose band is known ahead (see lbm_step); the
+// first TRIAL_STEPS steps after lbm_set_geometry alternate them, the first
+// pair warming up, the other two pairs timed
+enum { ORDER_UNDECIDED = LBM_ORDER_AUTO, ORDER_SPLIT = LBM_ORDER_SPLIT, ORDER_SEQUENTIAL = LBM_ORDER_SEQUENTIAL };
+constexpr int TRIAL_STEPS = 6;
+
 struct lbm_ctx {
     lbm::Lattice L;
     int storage = 0;
@@ -26,9 +32,35 @@ struct lbm_ctx {
     double *tot_partials = nullptr;
     int tot_blocks = 608;
     int64_t launches = 0;
+    // asynchronous force records: a copy stream, one event per ring entry,
+    // the record each ticket writes, and per body slot the last copy out of it
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_step = nullptr;
+    cudaEvent_t ev_copy[LBM_RECORD_DEPTH] = {};
+    lbm_force_record *rec[LBM_RECORD_DEPTH] = {};
+    cudaEvent_t ev_slot[2] = {nullptr, nullptr};
+    bool slot_pending[2] = {false, false};
+    int64_t next_ticket = 0;
+    // launch order of steps whose band is known ahead (lbm_step): 0 not yet
+    // chosen, 1 split, 2 sequential; the trial steps that time both and the
+    // events around them; whether the last step ran split
+    int order = 0;
+    int order_request = 0;  // LBM_ORDER_* asked for by the caller
+    int trial = 0;
+    cudaEvent_t ev_trial[5] = {};
+    bool last_split = false;
     std::vector<cudaEvent_t> prof;  // start/stop pairs around bulk launches
     int prof_used = 0;
     bool prof_open = false;
     std::string err;
 };
+
+// waits on the host for the asynchronous force-record copies that may still
+// read the body slots (before a call that rewrites the slots)
+inline cudaError_t drain_records(lbm_ctx *ctx)
+{
+    if (!ctx->copy) return cudaSuccess;
+    ctx->slot_pending[0] = ctx->slot_pending[1] = false;
+    return cudaStreamSynchronize(ctx->copy);
+}
 

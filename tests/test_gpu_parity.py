@@ -326,6 +326,83 @@ def test_checkpoint_resume_is_bitwise(storage, tmp_path):
         assert np.array_equal(ba[k], bc[k]), k
 
 
+@pytest.mark.parametrize("kind", ["sphere", "swimmer"])
+def test_launch_orders_agree_bitwise(kind):
+    """The split and the sequential launch order of a step (and the automatic
+    choice between them after its timed trial steps) give the same
+    populations and body state bit for bit."""
+    import paper_1608_04658_gb300 as lbm
+    if kind == "sphere":
+        shape, faces = (32, 28, 40), (1, 1, 1, 1, 0, 0)
+        geom = lbm.sphere((15.4, 13.7, 20.3), 5.2, U=(0.01, 0.0, -0.06), free=True, g=(0.0, 0.0, -2e-4))
+    else:
+        shape, faces = (64, 32, 20), (0,) * 6
+        geom = _swimmer_geom(lbm, U=(-0.004, 0.0, 0.0), free=True, t0=5.0)
+    rho, u, xi = synth.parity_fields(shape, 41)
+    runs = {}
+    for order in ("split", "sequential", "auto"):
+        lat = lbm.Lattice(shape, 0.03, storage="fp32", faces=faces)
+        lat.set_launch_order(order)
+        lat.set_geometry(geom)
+        lat.init_state(rho, 0.2 * u + np.array([0.01, 0.0, 0.0]), xi, 1e-3)
+        lat.step(9)
+        lat.body()  # synchronises: the trial steps have run
+        lat.step(3)
+        runs[order] = (lat.populations(), lat.body(), lat.launch_order())
+    assert runs["split"][2] == "split" and runs["sequential"][2] == "sequential"
+    assert runs["auto"][2] in ("split", "sequential")
+    for order in ("sequential", "auto"):
+        assert np.array_equal(runs[order][0], runs["split"][0]), order
+        for k in ("X", "U", "F", "M"):
+            assert np.array_equal(runs[order][1][k], runs["split"][1][k]), (order, k)
+    assert lbm.binding.lib().lbm_set_launch_order(lat._ctx, 7) != 0
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_async_force_records(storage):
+    """Force records copied while later steps run (lbm_body_forces_async /
+    lbm_body_forces_wait, two records outstanding) equal, bit for bit, the
+    synchronous force of the same step in an identical run; a pageable
+    record and an unissued ticket are rejected."""
+    import ctypes
+    import paper_1608_04658_gb300 as lbm
+    shape = (32, 28, 40)
+    faces = (1, 1, 1, 1, 0, 0)
+    rho, u, xi = synth.parity_fields(shape, 31)
+    geom = lbm.sphere((15.4, 13.7, 20.3), 5.2, U=(0.01, 0.0, -0.06), free=True, g=(0.0, 0.0, -2e-4))
+
+    def fresh():
+        lat = lbm.Lattice(shape, 0.03, storage=storage, faces=faces)
+        lat.set_geometry(geom)
+        lat.init_state(rho, 0.2 * u, xi, 1e-3)
+        return lat
+
+    a, b = fresh(), fresh()
+    steps = 20
+    sync = []
+    for _ in range(steps):
+        b.step(1)
+        sync.append(b.forces())
+    pending, got = [], []
+    for _ in range(steps):
+        a.step(1)
+        pending.append(a.forces_async())
+        if len(pending) > 2:
+            got.append(a.forces_wait(pending.pop(0)))
+    got += [a.forces_wait(t) for t in pending]
+    assert len(got) == steps
+    for k in range(steps):
+        assert np.array_equal(got[k][0], sync[k][0]) and np.array_equal(got[k][1], sync[k][1]), k
+    assert np.abs(got[-1][0]).max() > 0
+    assert a.body()["t"] == a._rec[(steps - 1) % lbm.binding.RECORD_DEPTH].numpy()[6] == steps
+    # a pageable record is refused; so is a ticket not yet issued
+    pageable = np.zeros(8)
+    t = ctypes.c_int64()
+    assert lbm.binding.lib().lbm_body_forces_async(a._ctx, ctypes.c_void_p(pageable.ctypes.data),
+                                                   ctypes.byref(t)) != 0
+    assert lbm.binding.lib().lbm_body_forces_wait(a._ctx, steps + 5) != 0
+
+
 @pytest.mark.parametrize("storage", STORAGES)
 def test_plunging_airfoil(storage):
     """Plunging cambered airfoil (chord 32, 4 degrees, amplitude 1.6, a fast
