@@ -887,7 +887,7 @@ struct AdjBuffers {
 };
 
 // one forward step from fa into fb with the context's body scratch and the
-// given marks (the launch sequence of lbm_step without the force reduction,
+// given marks (the launch sequences of lbm_step without the force reduction,
 // which the recomputation does not need)
 cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
 {
@@ -896,6 +896,29 @@ cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
     const uint8_t *fl = ctx->has_body ? flags : nullptr;
     int cur = ctx->bcur;
     int *status = &ctx->S.body[cur].status;
+    if (ctx->has_body && sweep_ahead(ctx->G) && ctx->order != ORDER_SEQUENTIAL) {
+        // split order, as in lbm_step: the nodes outside the sweep box beside
+        // the body's geometry, refill, boundary nodes and the box's nodes
+        const int prev = ctx->bcur;
+        cur = prev ^ 1;
+        status = &ctx->S.body[cur].status;
+        const int *sweep = ctx->S.body[prev].sweep;
+        if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess ||
+            (e = launch_geometry(ctx->L, ctx->G, ctx->S, prev, flags, ctx->side, &nl)) != cudaSuccess ||
+            (e = launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, flags, ctx->side)) != cudaSuccess ||
+            (e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->side)) !=
+                cudaSuccess ||
+            (e = launch_bulk(ctx->storage, ctx->L, fa, fb, flags, status, ctx->side, BULK_BAND, sweep, ctx->G.cap)) !=
+                cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess ||
+            (e = launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream, BULK_OUTSIDE, sweep)) !=
+                cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess)
+            return e;
+        ctx->bcur = cur;
+        return cudaSuccess;
+    }
     if (ctx->has_body) {
         const int prev = ctx->bcur;
         cur = prev ^ 1;
