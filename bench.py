@@ -61,6 +61,10 @@ def parse_args():
                     help="steps of the FP64/FP32/FP16/BF16 sphere comparison (0 to skip it)")
     ap.add_argument("--adjoint-horizon", type=int, default=8000,
                     help="steps of the adjoint/forward measurement (0 to skip it)")
+    ap.add_argument("--adjoint-checkpoint", type=int, default=0,
+                    help="checkpoint spacing of the adjoint measurement (0: ceil(sqrt(horizon)))")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint measurement and print it (profiling runs)")
     return ap.parse_args()
 
 
@@ -366,10 +370,10 @@ def adjoint_bench(args, world, device):
     fwd_ms = dist_max(e0.elapsed_time(e1), world)
     dist_barrier(world)
     t0 = time.perf_counter()
-    out = lat.adjoint(H, (-1.0, 0.0, 0.0))
+    K = args.adjoint_checkpoint if args.adjoint_checkpoint > 0 else int(math.ceil(math.sqrt(H)))
+    out = lat.adjoint(H, (-1.0, 0.0, 0.0), checkpoint_every=K)
     torch.cuda.synchronize()
     adj_ms = dist_max(1e3 * (time.perf_counter() - t0), world)
-    K = int(math.ceil(math.sqrt(H)))
     nx, ny, nz = wl["shape"]
     lat.close()
     del lat
@@ -448,6 +452,11 @@ def run_ours(args):
     lbm.build()
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
+    if args.adjoint_only:
+        adj = adjoint_bench(args, world, device)
+        if rank == 0:
+            print(json.dumps({"adjoint": adj}), flush=True)
+        return
     wl = workload(args.shape, args.workload)
     clocks = ClockSampler(local)
     clocks.start()
