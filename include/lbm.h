@@ -335,7 +335,13 @@ LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *laun
  *   MESH: (wave_amp, wave_length, wave_period) of the midline (Sec. 4.3);
  *   AIRFOIL: (h_amp, h_omega) of the plunge (Sec. 4.2), third entry 0;
  *   other bodies: none (zeros).
- * The body must not move freely (free_motion = 0).
+ * The body is held or prescribed, or it is the swimmer free along x alone
+ * (free_motion = 1): then the head's position X0 and velocity U0 are adjoint
+ * state too, carried back through the explicit Euler update X0 += U0,
+ * U0 += F_x/mass, the links' fraction and wall velocity (every vertex moves
+ * with X0, the wall velocity with U0) and the refill velocity.  Other free
+ * bodies (the sphere, the swimmer free in y or yaw) return
+ * LBM_ERR_UNSUPPORTED.
  * Storage FP64 (arithmetic in double) or FP32 (arithmetic in float);
  * 16-bit storage returns LBM_ERR_UNSUPPORTED.
  *

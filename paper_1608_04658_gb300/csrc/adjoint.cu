@@ -530,9 +530,19 @@ __device__ __forceinline__ void grad_pressure_adj(R gb, int i, bool act, R rho, 
     }
 }
 
-struct ForceWeights {
-    double w[3];  // weights of the force of this step in J (already divided by the horizon)
+// Adjoint state of a swimmer free along x (head frame), in device memory:
+// a_X, a_U = dJ/dX0, dJ/dU0 of the body state of the step last reversed, and
+// the weights of the force of the step reversed next in J: w/T plus, along x,
+// a_U/m (the force enters U0 of the state after it, U' = U + F/m).  For a held
+// or prescribed body only the weights are used (w/T, constant).
+struct BodyAdjoint {
+    double aX, aU;
+    double fw[3];
 };
+
+// one writer per band position and reversed step: d(terms)/dX0, d(terms)/dU0
+// from the boundary node there (0, 1) and from the refilled node there (2, 3)
+constexpr int BODY_SLOTS = 4;
 
 // Boundary nodes of step t: forward recomputation of the Grad completion
 // (same operations as the boundary kernel), then its transpose.
@@ -541,7 +551,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ blist,
     const int *__restrict__ bpos, const S *__restrict__ st, const NextAdj<typename Codec<S>::R> A,
     const uint8_t *__restrict__ flags1, typename Codec<S>::R *__restrict__ lam_out, double *__restrict__ ext,
-    double *__restrict__ tslots, const ForceWeights fw)
+    double *__restrict__ tslots, const BodyAdjoint *__restrict__ badj, double *__restrict__ bslot)
 {
     using R = typename Codec<S>::R;
     __shared__ R s_f[BWARPS][Q][28];
@@ -554,6 +564,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
     const int count = min(b->n_boundary, G.cap_boundary);
     const size_t N = (size_t)L.N;
     const R rho0 = (R)L.rho0, beta = (R)L.beta;
+    const double fw[3] = {badj->fw[0], badj->fw[1], badj->fw[2]};
 
     for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
         const int n = blist[slot];
@@ -637,9 +648,9 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             const double c[3] = {(double)cx, (double)cy, (double)cz};
             double sin_ = 0, sout = 0;
             for (int a = 0; a < 3; ++a) {
-                sin_ -= (c[a] - uw[a]) * fw.w[a];
-                sout += (-c[a] - uw[a]) * fw.w[a];
-                uwb[a] += fw.w[a] * (fin - fout);
+                sin_ -= (c[a] - uw[a]) * fw[a];
+                sout += (-c[a] - uw[a]) * fw[a];
+                uwb[a] += fw[a] * (fin - fout);
             }
             Fb += (R)sin_;
             fbbb += (R)sout;
@@ -697,6 +708,25 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
             if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] += v;
         }
+        // the free swimmer's state: through q and u_w of each missing link
+        // (every vertex moves with X0; u_w moves with U0 along x)
+        if (bslot) {
+            double gX = 0.0, gU = 0.0;
+            if (miss) {
+                double dq, duw[3];
+                mesh_link_body_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
+                gX = qb * dq + uwb[0] * duw[0] + uwb[1] * duw[1] + uwb[2] * duw[2];
+                gU = uwb[0];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                gX += __shfl_down_sync(FULL, gX, o);
+                gU += __shfl_down_sync(FULL, gU, o);
+            }
+            if (lane == 0) {
+                bslot[(size_t)bpos[slot] * BODY_SLOTS + 0] = gX;
+                bslot[(size_t)bpos[slot] * BODY_SLOTS + 1] = gU;
+            }
+        }
         __syncwarp();
     }
 }
@@ -708,7 +738,8 @@ template <typename S>
 __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
     const int *__restrict__ upos, const S *__restrict__ st, const typename Codec<S>::R *__restrict__ lam_t,
-    const uint8_t *__restrict__ flags1, double *__restrict__ ext, double *__restrict__ tslots)
+    const uint8_t *__restrict__ flags1, double *__restrict__ ext, double *__restrict__ tslots,
+    double *__restrict__ bslot)
 {
     using R = typename Codec<S>::R;
     __shared__ R s_f[BWARPS][Q][28];
@@ -773,6 +804,11 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
         }
         if (lane == 0)
             for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] += tb[k];
+        // the free swimmer's state through the refill velocity U0 e_x + rate(x - X0) e_y
+        if (lane == 0 && bslot) {
+            bslot[(size_t)upos[slot] * BODY_SLOTS + 2] = (double)ub[1] * swimmer_rate_dX(G, b->t, (double)x - b->X[0]);
+            bslot[(size_t)upos[slot] * BODY_SLOTS + 3] = (double)ub[0];
+        }
         __syncwarp();
     }
 }
@@ -786,6 +822,41 @@ __global__ void __launch_bounds__(256) vertex_tangent_kernel(const GeomParams G,
     const double s = G.mesh_rest[3 * v];
     swimmer_midline_tangent(G, s, b->t, G.mesh_dy + 3 * (size_t)v);
     swimmer_velocity_tangent(G, b->t, s, G.mesh_dvy + 3 * (size_t)v);
+}
+
+// One reversed step of the free swimmer's state (explicit Euler, Sec. 4.3:
+// X' = X + U, U' = U + F/m with F the force of the step before): the step's
+// geometry gives g_X, g_U (sum of the band slots, fixed order; the slots are
+// cleared for the next step), then a_X = g_X + a_X', a_U = g_U + a_X' + a_U',
+// and the force of the step reversed next weighs w/T + a_U/m along x.
+__global__ void __launch_bounds__(256) body_reduce_kernel(double *__restrict__ slots, int nslots,
+                                                          BodyAdjoint *__restrict__ badj, double wx, double inv_mass)
+{
+    __shared__ double sm[256][2];
+    double v[2] = {0, 0};
+    for (int s = threadIdx.x; s < nslots; s += 256) {
+        double *p = slots + (size_t)s * BODY_SLOTS;
+        v[0] += p[0] + p[2];
+        v[1] += p[1] + p[3];
+        p[0] = p[1] = p[2] = p[3] = 0.0;
+    }
+    sm[threadIdx.x][0] = v[0];
+    sm[threadIdx.x][1] = v[1];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sm[threadIdx.x][0] += sm[threadIdx.x + h][0];
+            sm[threadIdx.x][1] += sm[threadIdx.x + h][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double aX = sm[0][0] + badj->aX;
+        const double aU = sm[0][1] + badj->aX + badj->aU;
+        badj->aX = aX;
+        badj->aU = aU;
+        badj->fw[0] = wx + aU * inv_mass;
+    }
 }
 
 // acc[k] = sum over band slots of slot[6 s + k] + slot[6 s + 3 + k], fixed
@@ -887,8 +958,8 @@ struct AdjBuffers {
 };
 
 // one forward step from fa into fb with the context's body scratch and the
-// given marks (the launch sequences of lbm_step without the force reduction,
-// which the recomputation does not need)
+// given marks (the launch sequences of lbm_step; the force reduction only for
+// a free body, whose next pose needs it)
 cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
 {
     int nl = 0;
@@ -909,6 +980,7 @@ cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
             (e = launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, flags, ctx->side)) != cudaSuccess ||
             (e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->side)) !=
                 cudaSuccess ||
+            (ctx->G.free_motion && (e = launch_forces(ctx->G, ctx->S, cur, ctx->side, &nl)) != cudaSuccess) ||
             (e = launch_bulk(ctx->storage, ctx->L, fa, fb, flags, status, ctx->side, BULK_BAND, sweep, ctx->G.cap)) !=
                 cudaSuccess ||
             (e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess ||
@@ -931,6 +1003,7 @@ cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
         if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
         if ((e = launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, flags, ctx->side)) != cudaSuccess)
             return e;
+        if (ctx->G.free_motion && (e = launch_forces(ctx->G, ctx->S, cur, ctx->side, &nl)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
     }
     if ((e = launch_bulk(ctx->storage, ctx->L, fa, fb, fl, status, ctx->stream)) != cudaSuccess) return e;
@@ -949,7 +1022,8 @@ int list_blocks(int cap)
 // in flags1 after the geometry re-run) for storage type S
 template <typename S>
 cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
-                         typename Codec<S>::R *lam_out, double *ext, double *tslots, const ForceWeights &fw)
+                         typename Codec<S>::R *lam_out, double *ext, double *tslots, BodyAdjoint *badj,
+                         double *bslot, double wx)
 {
     using R = typename Codec<S>::R;
     const Lattice &L = ctx->L;
@@ -965,7 +1039,7 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
         adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, ctx->side>>>(
-            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, fw);
+            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot);
         if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
     }
     const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
@@ -974,7 +1048,9 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     if (ctx->has_body) {
         if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
-            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots);
+            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot);
+        if (bslot)
+            body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, wx, G.inv_mass);
     }
     return cudaGetLastError();
 }
@@ -1002,7 +1078,11 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     double *ext[2] = {nullptr, nullptr}, *tslots = nullptr, *acc = nullptr, *part = nullptr;
     double *tan_dy = nullptr, *tan_dvy = nullptr;
     double F0[3] = {0, 0, 0}, F1[3] = {0, 0, 0}, accv[3] = {0, 0, 0};
-    ForceWeights fw{{spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}};
+    // the swimmer free along x carries (X0, U0) as adjoint state
+    const bool free_body = ctx->has_body && ctx->G.free_motion != 0;
+    const BodyAdjoint badj0{0.0, 0.0, {spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}};
+    BodyAdjoint *badj = nullptr;
+    double *bslot = nullptr;
     DevBody hb{};
     int p = 0;
     const int save_bcur = ctx->bcur;
@@ -1014,7 +1094,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
         !B.get(&wf[1], N) || !B.get(&wrec, N) || !B.get(&ckbody, nseg) || !B.get(&segbody, K) || !B.get(&adjbody, 2) ||
         !B.get(&savebody, 2) || !B.get(&lam[0], state) || !B.get(&lam[1], state) ||
         !B.get(&ext[0], (size_t)cap * Q) || !B.get(&ext[1], (size_t)cap * Q) || !B.get(&tslots, (size_t)cap * 6) ||
-        !B.get(&acc, 3) || !B.get(&part, nparts) ||
+        !B.get(&acc, 3) || !B.get(&part, nparts) || !B.get(&badj, 1) ||
+        (free_body && !B.get(&bslot, (size_t)cap * BODY_SLOTS)) ||
         (body && ctx->G.kind == LBM_BODY_MESH &&
          (!B.get(&tan_dy, 3 * (size_t)ctx->G.n_vertices) || !B.get(&tan_dvy, 3 * (size_t)ctx->G.n_vertices))))
         return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the checkpoints failed");
@@ -1059,6 +1140,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     // ---- reverse sweep, one recomputed segment at a time
     ADJ_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s), "clear");
     ADJ_CUDA(cudaMemsetAsync(tslots, 0, (size_t)cap * 6 * sizeof(double), s), "clear");
+    ADJ_CUDA(cudaMemcpyAsync(badj, &badj0, sizeof(BodyAdjoint), cudaMemcpyHostToDevice, s), "body adjoint");
+    if (bslot) ADJ_CUDA(cudaMemsetAsync(bslot, 0, (size_t)cap * BODY_SLOTS * sizeof(double), s), "clear");
     {
         bool first = true;
         for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1095,7 +1178,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                     A = NextAdj<R>{lam[p ^ 1], body ? ext[p ^ 1] : nullptr, adjbody + (p ^ 1),
                                    body ? wf[p ^ 1] : nullptr, 0};
                 }
-                ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, fw),
+                ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, badj, bslot,
+                                         badj0.fw[0]),
                          "reverse step");
                 if (body)
                     ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),
@@ -1139,8 +1223,9 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
     if (ctx->L.gamma_mode == LBM_GAMMA_EXACT)
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: the exact stabilizer has no adjoint here");
-    if (ctx->has_body && ctx->G.free_motion)
-        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: needs a held or prescribed body (no free motion)");
+    if (ctx->has_body && ctx->G.free_motion && !(ctx->G.kind == LBM_BODY_MESH && ctx->G.free_motion == 1))
+        return afail(ctx, LBM_ERR_UNSUPPORTED,
+                     "lbm_adjoint_step: a free body must be the swimmer free along x alone (no free sphere, y or yaw)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
     if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");

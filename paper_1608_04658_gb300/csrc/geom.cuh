@@ -546,6 +546,78 @@ __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const
     }
 }
 
+// d y(s,t) / ds of the midline (Sec. 4.3): r(t) [a/1.03125 sin(ph) + A(s) cos(ph) 2 pi/lambda],
+// A(s) = a L (s/L + 0.03125)/1.03125, ph = 2 pi (s/lambda - t/T)
+__device__ __forceinline__ double swimmer_midline_ds(const GeomParams &G, double s, double t)
+{
+    double r = 1.0;
+    if (G.wave_ramp) {
+        if (t < 0.0) r = 0.0;
+        else if (t < G.wave_period) r = 0.5 * (1.0 - cos(MESH_PI * t / G.wave_period));
+    }
+    const double A = G.wave_amp * G.length * (s / G.length + 0.03125) / 1.03125;
+    const double ph = 2.0 * MESH_PI * (s / G.wave_length - t / G.wave_period);
+    return r * (G.wave_amp / 1.03125 * sin(ph) + A * cos(ph) * 2.0 * MESH_PI / G.wave_length);
+}
+
+// d/dX0 of the material velocity's y component at the node's arc position
+// s = x - X0 (the central difference of the midline): -d rate / ds, zero where
+// s is clamped to the ends
+__device__ __forceinline__ double swimmer_rate_dX(const GeomParams &G, double t, double s_raw)
+{
+    if (s_raw < 0.0 || s_raw > G.length) return 0.0;
+    return -0.5 * (swimmer_midline_ds(G, s_raw, t + 1.0) - swimmer_midline_ds(G, s_raw, t - 1.0));
+}
+
+// Derivatives of a mesh link's fraction q and wall velocity u_w with respect
+// to the head's position X0 along x (the swimmer free along x, head frame):
+// every vertex moves by e_x, so with the plane and barycentric relations of
+// mesh_link_tangent dq = -n_x/(n.c) and du e1 + dv e2 = -dq c - e_x; the
+// vertex velocities (U plus the midline's rate at the material position) do
+// not change.  d/dU0 is q: 0, u_w: e_x.
+__device__ __noinline__ static void mesh_link_body_tangent(const GeomParams &G, const DevBody *b, int x, int y, int z,
+                                                           int cx, int cy, int cz, double q, const MeshHit &h,
+                                                           double &dq, double duw[3])
+{
+    if (h.tri < 0) {
+        dq = 0.0;
+        duw[0] = 0.0;
+        duw[1] = swimmer_rate_dX(G, b->t, (double)x - 0.5 * cx - b->X[0]);
+        duw[2] = 0.0;
+        return;
+    }
+    const int tv[3] = {G.mesh_tris[3 * h.tri], G.mesh_tris[3 * h.tri + 1], G.mesh_tris[3 * h.tri + 2]};
+    double P[3][3], V[3][3];
+    for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a) {
+            P[m][a] = G.mesh_pos[3 * tv[m] + a];
+            V[m][a] = G.mesh_vel[3 * tv[m] + a];
+        }
+    const double c[3] = {(double)cx, (double)cy, (double)cz};
+    double e1[3], e2[3], n[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = P[1][a] - P[0][a];
+        e2[a] = P[2][a] - P[0][a];
+    }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double nc = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+    const double g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const double gdet = g11 * g22 - g12 * g12;
+    dq = nc != 0.0 ? -n[0] / nc : 0.0;
+    double rhs[3];
+    for (int a = 0; a < 3; ++a) rhs[a] = -dq * c[a];
+    rhs[0] -= 1.0;
+    const double b1 = e1[0] * rhs[0] + e1[1] * rhs[1] + e1[2] * rhs[2];
+    const double b2 = e2[0] * rhs[0] + e2[1] * rhs[1] + e2[2] * rhs[2];
+    const double du = gdet != 0.0 ? (b1 * g22 - b2 * g12) / gdet : 0.0;
+    const double dv = gdet != 0.0 ? (g11 * b2 - g12 * b1) / gdet : 0.0;
+    for (int a = 0; a < 3; ++a) duw[a] = du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]);
+}
+
 // ---------------------------------------------------------------- airfoil tangents
 // Derivatives with respect to theta = (h_amp, h_omega) of the plunge at body
 // time t (Sec. 4.2): X1 = y_base + A sin(w t), U1 = A w cos(w t).

@@ -53,11 +53,12 @@ def test_initial_state_gradient_matches_tape(faces, lbgk):
     assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
-def _swimmer_geom(L=24.0, X=(12.137, 12.371, 12.293), theta=(0.125, 24.0, 96.0), segments=48, ring=16):
+def _swimmer_geom(L=24.0, X=(12.137, 12.371, 12.293), theta=(0.125, 24.0, 96.0), segments=48, ring=16,
+                  free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0)):
     import paper_1608_04658_gb300 as lbm
     rest, tris = synth.swimmer_mesh(L, segments, ring)
     a, lam, T = theta
-    return lbm.swimmer(X, rest, tris, L, a, lam, T, mass=synth.swimmer_volume(L))
+    return lbm.swimmer(X, rest, tris, L, a, lam, T, mass=mass_scale * synth.swimmer_volume(L), free=free, U=U)
 
 
 def _dot_product_check(shape, geom_fn, storage="fp64", H=4, seed=41):
@@ -110,11 +111,22 @@ def test_dot_product_with_deforming_swimmer():
     assert ad == pytest.approx(fd, rel=1e-7)
 
 
-def _oracle_thrust(shape, theta, fields, H, w, L=24.0, X=(12.137, 12.371, 12.293), segments=48, ring=16):
+def test_dot_product_with_free_swimmer():
+    """The swimmer free along x (Sec. 4.3 Newton equation, explicit Euler):
+    the adjoint carries the head's position and velocity backwards, so the
+    initial-state gradient includes the force -> velocity -> pose -> flow
+    feedback."""
+    ad, fd = _dot_product_check((48, 24, 24), lambda: _swimmer_geom(free=True, mass_scale=0.25,
+                                                                    U=(-0.01, 0.0, 0.0)))
+    assert ad == pytest.approx(fd, rel=1e-7)
+
+
+def _oracle_thrust(shape, theta, fields, H, w, L=24.0, X=(12.137, 12.371, 12.293), segments=48, ring=16,
+                   free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0)):
     rest, tris = synth.swimmer_mesh(L, segments, ring)
     a, lam, T = theta
-    o = oracle.Oracle(shape, nu=0.02, body=oracle.mesh_body(X, rest, tris, L, a, lam, T,
-                                                           mass=synth.swimmer_volume(L)))
+    o = oracle.Oracle(shape, nu=0.02, body=oracle.mesh_body(X, rest, tris, L, a, lam, T, U=U, free=free,
+                                                           mass=mass_scale * synth.swimmer_volume(L)))
     rho, u, xi, amp = fields
     o.init_state(rho, u, xi, amp)
     J = 0.0
@@ -154,6 +166,46 @@ def test_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     g = out["dJ_dtheta"]
     assert np.all(np.abs(fd) > 0)
     assert np.abs(g - fd).max() <= tol * np.abs(fd).max()
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 2e-3)])
+def test_free_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
+    """As above with the swimmer free along x and a light body (mass a quarter
+    of the displaced fluid's), so the kinematics also change the head's path:
+    d(mean thrust)/d(theta) from the GPU adjoint, which carries (X0, U0) as
+    adjoint state, vs central differences of the FP64 oracle."""
+    shape, H = (48, 24, 24), 8
+    theta = np.array([0.125, 24.0, 96.0])
+    w = np.array([-1.0, 0.0, 0.0])
+    kw = dict(free=True, mass_scale=0.25, U=(-0.01, 0.0, 0.0))
+    rho, u, xi = synth.parity_fields(shape, 47)
+    fields = (rho, 0.2 * u, xi, 1e-3)
+    lat = _lat(shape, 0.02, storage=storage)
+    lat.set_geometry(_swimmer_geom(theta=tuple(theta), **kw))
+    lat.init_state(*fields)
+    out = lat.adjoint(H, w)
+    b = lat.body()
+    J0, _, _ = _oracle_thrust(shape, theta, fields, H, w, **kw)
+    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-3)
+    assert b["X"][0] != 12.137  # the head moved
+    fd = np.zeros(3)
+    for k in range(3):
+        h = 1e-6 * theta[k]
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        Jp, cp, sp = _oracle_thrust(shape, tp, fields, H, w, **kw)
+        Jm, cm, sm = _oracle_thrust(shape, tm, fields, H, w, **kw)
+        assert cp == cm and np.array_equal(sp, sm), "link set changed within the difference step"
+        fd[k] = (Jp - Jm) / (2 * h)
+    g = out["dJ_dtheta"]
+    assert np.all(np.abs(fd) > 0)
+    assert np.abs(g - fd).max() <= tol * np.abs(fd).max()
+    # the held swimmer's gradient differs: the feedback through the head's path counts
+    held = _lat(shape, 0.02, storage=storage)
+    held.set_geometry(_swimmer_geom(theta=tuple(theta), mass_scale=0.25, U=(-0.01, 0.0, 0.0)))
+    held.init_state(*fields)
+    assert np.abs(held.adjoint(H, w)["dJ_dtheta"] - g).max() > 10 * tol * np.abs(fd).max()
 
 
 def _airfoil_case(theta, t0=3.0):
@@ -263,13 +315,19 @@ def test_adjoint_near_rest_is_finite(storage):
     assert np.abs(out["dJ_dtheta"]).max() > 0
 
 
-def test_adjoint_rejects_free_bodies_and_16_bit_storage():
+def test_adjoint_rejects_unsupported_free_bodies_and_16_bit_storage():
     import paper_1608_04658_gb300 as lbm
     lat = _lat((12, 12, 12), 0.05)
     lat.set_geometry(lbm.sphere((5.6, 6.1, 5.9), 2.7, free=True, g=(0, 0, -1e-4)))
     lat.init_state(*synth.uniform_fields((12, 12, 12)))
     with pytest.raises(lbm.LbmError):
         lat.adjoint(2)
+    # the swimmer free in y or yaw (centre-of-mass frame) has no adjoint here
+    sw = _lat((48, 24, 24), 0.02)
+    sw.set_geometry(_swimmer_geom(X=(24.137, 12.371, 12.293), free=7))
+    sw.init_state(*synth.uniform_fields((48, 24, 24)))
+    with pytest.raises(lbm.LbmError):
+        sw.adjoint(2)
     lat16 = _lat((12, 12, 12), 0.05, storage="fp16")
     lat16.init_state(*synth.uniform_fields((12, 12, 12)))
     with pytest.raises(lbm.LbmError):
