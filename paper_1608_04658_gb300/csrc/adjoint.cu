@@ -445,6 +445,131 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) adjoint_bulk_kernel(c
     for (int i = 0; i < Q; ++i) lam_out[(size_t)i * N + n] = lam[i];
 }
 
+// ----------------------------------------------------------------- centre-of-mass frame
+// theta-derivatives of the mesh's volume sums (divergence theorem, as the
+// forward mass kernel): per triangle d = e1 x e2, V += d_x h1(x)/6,
+// S_x += d_x h2(x)/24, S_xx += d_x h3(x)/60, S_y += d_y h2(y)/24,
+// S_yy += d_y h3(y)/60; only the vertices' y moves with theta (by the
+// midline tangent), so d_x and the y polynomials carry the derivative.
+// Sums: at tau (V, Sx, Sy, Sxx, Syy and their 3 theta-derivatives, 20) and at
+// tau -+ 1 (V, Sx, Sy and derivatives, 12 each): 44 per triangle.
+constexpr int COM_SUMS = 44;
+
+__device__ __forceinline__ void com_triangle_sums(const GeomParams &G, int k, double t, bool second, double *acc)
+{
+    double P[3][3], ty[3][3];
+    for (int m = 0; m < 3; ++m) {
+        const int iv = G.mesh_tris[3 * k + m];
+        const double s = G.mesh_rest[3 * iv];
+        P[m][0] = s;
+        P[m][1] = swimmer_midline(G, s, t) + G.mesh_rest[3 * iv + 1];
+        P[m][2] = G.mesh_rest[3 * iv + 2];
+        swimmer_midline_tangent(G, s, t, ty[m]);
+    }
+    const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const double dx = e1[1] * e2[2] - e1[2] * e2[1], dy = e1[2] * e2[0] - e1[0] * e2[2];
+    const double x0 = P[0][0], x1 = P[1][0], x2 = P[2][0];
+    const double y0 = P[0][1], y1 = P[1][1], y2 = P[2][1];
+    const double hx1 = x0 + x1 + x2;
+    const double hx2 = x0 * x0 + x1 * x1 + x2 * x2 + x0 * x1 + x0 * x2 + x1 * x2;
+    const double hx3 = x0 * x0 * x0 + x1 * x1 * x1 + x2 * x2 * x2 + x0 * x0 * (x1 + x2) + x1 * x1 * (x0 + x2) +
+                       x2 * x2 * (x0 + x1) + x0 * x1 * x2;
+    const double hy2 = y0 * y0 + y1 * y1 + y2 * y2 + y0 * y1 + y0 * y2 + y1 * y2;
+    const double hy3 = y0 * y0 * y0 + y1 * y1 * y1 + y2 * y2 * y2 + y0 * y0 * (y1 + y2) + y1 * y1 * (y0 + y2) +
+                       y2 * y2 * (y0 + y1) + y0 * y1 * y2;
+    // d h2 / d y_m and d h3 / d y_m
+    const double g2[3] = {2 * y0 + y1 + y2, 2 * y1 + y0 + y2, 2 * y2 + y0 + y1};
+    const double g3[3] = {3 * y0 * y0 + 2 * y0 * (y1 + y2) + y1 * y1 + y2 * y2 + y1 * y2,
+                          3 * y1 * y1 + 2 * y1 * (y0 + y2) + y0 * y0 + y2 * y2 + y0 * y2,
+                          3 * y2 * y2 + 2 * y2 * (y0 + y1) + y0 * y0 + y1 * y1 + y0 * y1};
+    acc[0] += dx * hx1 / 6.0;
+    acc[1] += dx * hx2 / 24.0;
+    acc[2] += dy * hy2 / 24.0;
+    int o = 3;
+    if (second) {
+        acc[3] += dx * hx3 / 60.0;
+        acc[4] += dy * hy3 / 60.0;
+        o = 5;
+    }
+    for (int j = 0; j < 3; ++j) {
+        const double ddx = (ty[1][j] - ty[0][j]) * e2[2] - e1[2] * (ty[2][j] - ty[0][j]);
+        const double dh2 = g2[0] * ty[0][j] + g2[1] * ty[1][j] + g2[2] * ty[2][j];
+        acc[o + 0] += ddx * hx1 / 6.0;
+        acc[o + 1] += ddx * hx2 / 24.0;
+        acc[o + 2] += dy * dh2 / 24.0;
+        if (second) {
+            const double dh3 = g3[0] * ty[0][j] + g3[1] * ty[1][j] + g3[2] * ty[2][j];
+            acc[o + 3] += ddx * hx3 / 60.0;
+            acc[o + 4] += dy * dh3 / 60.0;
+            o += 5;
+        } else {
+            o += 3;
+        }
+    }
+}
+
+// ComTangents of the pose of body state b (time tau = b->t): block partials,
+// a fixed-order last-block sum, then dc = d(S/V), dc_dot, dI with
+// I = (m/V)(Sxx + Syy) - m (cx^2 + cy^2)
+__global__ void __launch_bounds__(256) com_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b,
+                                                          double *__restrict__ partials, unsigned *__restrict__ ticket,
+                                                          ComTangents *__restrict__ out)
+{
+    double acc[COM_SUMS];
+    for (int c = 0; c < COM_SUMS; ++c) acc[c] = 0.0;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < G.n_triangles) {
+        com_triangle_sums(G, k, b->t, true, acc);
+        com_triangle_sums(G, k, b->t + 1.0, false, acc + 20);
+        com_triangle_sums(G, k, b->t - 1.0, false, acc + 32);
+    }
+    __shared__ double sm[8][COM_SUMS];
+    __shared__ bool last;
+    for (int c = 0; c < COM_SUMS; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < COM_SUMS) {
+        double v = 0;
+        for (int w = 0; w < 8; ++w) v += sm[w][threadIdx.x];
+        partials[blockIdx.x * COM_SUMS + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double S[COM_SUMS];
+    if (threadIdx.x < COM_SUMS) {
+        double v = 0;
+        for (int p = 0; p < (int)gridDim.x; ++p) v += ((volatile double *)partials)[p * COM_SUMS + threadIdx.x];
+        S[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double m = G.mass;
+    const double V = S[0], cx = S[1] / V, cy = S[2] / V;
+    const double Vp = S[20], Vm = S[32];
+    for (int j = 0; j < 3; ++j) {
+        const double dV = S[5 + 5 * j], dSx = S[6 + 5 * j], dSy = S[7 + 5 * j];
+        const double dSxx = S[8 + 5 * j], dSyy = S[9 + 5 * j];
+        const double dcx = (dSx - cx * dV) / V, dcy = (dSy - cy * dV) / V;
+        out->dc[j][0] = dcx;
+        out->dc[j][1] = dcy;
+        out->dI[j] = -m * dV / (V * V) * (S[3] + S[4]) + m / V * (dSxx + dSyy) - 2.0 * m * (cx * dcx + cy * dcy);
+        const double dVp = S[23 + 3 * j], dVm = S[35 + 3 * j];
+        const double dcxp = (S[24 + 3 * j] - S[21] / Vp * dVp) / Vp, dcyp = (S[25 + 3 * j] - S[22] / Vp * dVp) / Vp;
+        const double dcxm = (S[36 + 3 * j] - S[33] / Vm * dVm) / Vm, dcym = (S[37 + 3 * j] - S[34] / Vm * dVm) / Vm;
+        out->dcdot[j][0] = (dcxp - dcxm) / 2.0;
+        out->dcdot[j][1] = (dcyp - dcym) / 2.0;
+    }
+    *ticket = 0u;
+}
+
 // adds (ub . (c_m - u_k)) / rho_k + rb to ext[node k][m] for every lane k with a
 // non-zero velocity or density adjoint; all lanes m < 27 write one entry each
 template <typename R>
@@ -536,13 +661,17 @@ __device__ __forceinline__ void grad_pressure_adj(R gb, int i, bool act, R rho, 
 // a_U/m (the force enters U0 of the state after it, U' = U + F/m).  For a held
 // or prescribed body only the weights are used (w/T, constant).
 struct BodyAdjoint {
-    double aX, aU;
-    double fw[3];
+    double aX[2], aU[2];  // dJ/dX, dJ/dU of the free axes (x, y)
+    double aPsi, aL;      // dJ/dpsi, dJ/d(I omega) (yaw free)
+    double fw[3];         // weights of the force of the step reversed next
+    double mw;            // weight of the torque M_z of the step reversed next (yaw free)
+    double dth[3];        // dJ/dtheta through omega = I omega / I(theta)
 };
 
-// one writer per band position and reversed step: d(terms)/dX0, d(terms)/dU0
-// from the boundary node there (0, 1) and from the refilled node there (2, 3)
-constexpr int BODY_SLOTS = 4;
+// one writer per band position and reversed step: derivatives with respect to
+// (X_x, X_y, psi, U_x, U_y, omega) from the boundary node there (0..5) and
+// from the refilled node there (6..11)
+constexpr int BODY_SLOTS = 12;
 
 // Boundary nodes of step t: forward recomputation of the Grad completion
 // (same operations as the boundary kernel), then its transpose.
@@ -551,7 +680,8 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ blist,
     const int *__restrict__ bpos, const S *__restrict__ st, const NextAdj<typename Codec<S>::R> A,
     const uint8_t *__restrict__ flags1, typename Codec<S>::R *__restrict__ lam_out, double *__restrict__ ext,
-    double *__restrict__ tslots, const BodyAdjoint *__restrict__ badj, double *__restrict__ bslot)
+    double *__restrict__ tslots, const BodyAdjoint *__restrict__ badj, double *__restrict__ bslot,
+    const ComTangents *__restrict__ ct)
 {
     using R = typename Codec<S>::R;
     __shared__ R s_f[BWARPS][Q][28];
@@ -565,6 +695,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
     const size_t N = (size_t)L.N;
     const R rho0 = (R)L.rho0, beta = (R)L.beta;
     const double fw[3] = {badj->fw[0], badj->fw[1], badj->fw[2]};
+    const double mw = badj->mw;
 
     for (int slot = blockIdx.x * BWARPS + w; slot < count; slot += gridDim.x * BWARPS) {
         const int n = blist[slot];
@@ -642,6 +773,9 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
         // momentum exchange in J: dF_a = (-c_a - uw_a) fout - (c_a - uw_a) fin
         double uwb[3] = {0, 0, 0};
         R fbbb = 0;
+        // the torque M_z about X of the free yaw enters J with weight mw:
+        // M_z = r_x dF_y - r_y dF_x, r = x_b - q c - X
+        double qb_m = 0.0, gXm[2] = {0.0, 0.0};
         if (miss) {
             const double Wr = weight<double>(i) * L.rho0;
             const double fout = (double)fbb + Wr, fin = (double)gi + Wr;
@@ -651,6 +785,18 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
                 sin_ -= (c[a] - uw[a]) * fw[a];
                 sout += (-c[a] - uw[a]) * fw[a];
                 uwb[a] += fw[a] * (fin - fout);
+            }
+            if (mw != 0.0) {
+                const double r0 = body_offset(L, G, b, 0, x) - q * c[0], r1 = body_offset(L, G, b, 1, y) - q * c[1];
+                const double dFx = (-c[0] - uw[0]) * fout - (c[0] - uw[0]) * fin;
+                const double dFy = (-c[1] - uw[1]) * fout - (c[1] - uw[1]) * fin;
+                sin_ += mw * (-r0 * (c[1] - uw[1]) + r1 * (c[0] - uw[0]));
+                sout += mw * (r0 * (-c[1] - uw[1]) - r1 * (-c[0] - uw[0]));
+                uwb[0] -= mw * r1 * (fin - fout);
+                uwb[1] += mw * r0 * (fin - fout);
+                qb_m = mw * (-c[0] * dFy + c[1] * dFx);
+                gXm[0] = -mw * dFy;
+                gXm[1] = mw * dFx;
             }
             Fb += (R)sin_;
             fbbb += (R)sout;
@@ -674,6 +820,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
                 }
             }
         }
+        qb += qb_m;
         // rho_t = rho0 + sum gstat + sum dyn
         R lam_row = 0;
         if (act && !miss) lam_row = Fb + rhob;
@@ -693,10 +840,28 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
         scatter_moment_adjoints<R>(L, G, b, lane, nk, has, unb, R(0), su, ext);
         // parameters: dJ/dtheta through q and u_w of each missing link
         double tb[3] = {0, 0, 0};
-        if (miss && G.kind == LBM_BODY_MESH) {
+        double gb[6] = {0, 0, 0, 0, 0, 0};  // (X_x, X_y, psi, U_x, U_y, omega)
+        if (miss && G.kind == LBM_BODY_MESH && G.com_frame) {
+            double dq[COM_DIRS], duw[COM_DIRS][3];
+            com_link_tangents(G, b, *ct, x, y, z, cx, cy, cz, q, hit, dq, duw);
+            for (int d = 0; d < COM_DIRS; ++d) {
+                const double v = qb * dq[d] + uwb[0] * duw[d][0] + uwb[1] * duw[d][1] + uwb[2] * duw[d][2];
+                if (d < 3) tb[d] = v;
+                else gb[d - 3] = v;
+            }
+            gb[0] += gXm[0];
+            gb[1] += gXm[1];
+        } else if (miss && G.kind == LBM_BODY_MESH) {
             double dq[3], duw[3][3];
             mesh_link_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
             for (int k = 0; k < 3; ++k) tb[k] = qb * dq[k] + uwb[0] * duw[k][0] + uwb[1] * duw[k][1] + uwb[2] * duw[k][2];
+            if (bslot) {
+                // the head frame: every vertex moves with X0, u_w with U0
+                double dqX, duwX[3];
+                mesh_link_body_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dqX, duwX);
+                gb[0] = qb * dqX + uwb[0] * duwX[0] + uwb[1] * duwX[1] + uwb[2] * duwX[2];
+                gb[3] = uwb[0];
+            }
         } else if (miss && G.kind == LBM_BODY_AIRFOIL) {
             double dq[2], dX1[2], dU1[2];
             airfoil_link_tangent(G, b, x, y, cx, cy, q, dq);
@@ -708,23 +873,12 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
             if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] += v;
         }
-        // the free swimmer's state: through q and u_w of each missing link
-        // (every vertex moves with X0; u_w moves with U0 along x)
+        // the free body's state through q and u_w of each missing link
         if (bslot) {
-            double gX = 0.0, gU = 0.0;
-            if (miss) {
-                double dq, duw[3];
-                mesh_link_body_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
-                gX = qb * dq + uwb[0] * duw[0] + uwb[1] * duw[1] + uwb[2] * duw[2];
-                gU = uwb[0];
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                gX += __shfl_down_sync(FULL, gX, o);
-                gU += __shfl_down_sync(FULL, gU, o);
-            }
-            if (lane == 0) {
-                bslot[(size_t)bpos[slot] * BODY_SLOTS + 0] = gX;
-                bslot[(size_t)bpos[slot] * BODY_SLOTS + 1] = gU;
+            for (int d = 0; d < 6; ++d) {
+                double v = gb[d];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+                if (lane == 0) bslot[(size_t)bpos[slot] * BODY_SLOTS + d] = v;
             }
         }
         __syncwarp();
@@ -739,7 +893,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
     const Lattice L, const GeomParams G, const DevBody *__restrict__ b, const int *__restrict__ ulist,
     const int *__restrict__ upos, const S *__restrict__ st, const typename Codec<S>::R *__restrict__ lam_t,
     const uint8_t *__restrict__ flags1, double *__restrict__ ext, double *__restrict__ tslots,
-    double *__restrict__ bslot)
+    double *__restrict__ bslot, const ComTangents *__restrict__ ct)
 {
     using R = typename Codec<S>::R;
     __shared__ R s_f[BWARPS][Q][28];
@@ -770,7 +924,7 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
             const double *v = (double)y < 0.5 * (G.y_lo + G.y_hi) ? G.U_lo : G.U_hi;
             ud[0] = v[0]; ud[1] = v[1]; ud[2] = v[2];
         } else if (G.kind == LBM_BODY_MESH) {
-            swimmer_velocity(G, b->U, b->t, clamp_arc(G, (double)x - b->X[0]), ud);
+            mesh_material_velocity(G, b, (double)x, (double)y, ud);
         }
         const R u[3] = {(R)ud[0], (R)ud[1], (R)ud[2]};
         R du[3][3];
@@ -793,10 +947,22 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
         scatter_moment_adjoints<R>(L, G, b, lane, nk, has, unb, rkb, su, ext);
         // parameters through the body velocity
         double tb[3] = {0, 0, 0};
-        if (lane == 0 && G.kind == LBM_BODY_MESH) {
+        double gb[6] = {0, 0, 0, 0, 0, 0};
+        if (lane == 0 && G.kind == LBM_BODY_MESH && G.com_frame) {
+            double du[COM_DIRS][3];
+            com_material_velocity_tangents(G, b, *ct, (double)x, (double)y, du);
+            for (int d = 0; d < COM_DIRS; ++d) {
+                const double v = (double)ub[0] * du[d][0] + (double)ub[1] * du[d][1] + (double)ub[2] * du[d][2];
+                if (d < 3) tb[d] = v;
+                else gb[d - 3] = v;
+            }
+        } else if (lane == 0 && G.kind == LBM_BODY_MESH) {
             double dv[3];
             swimmer_velocity_tangent(G, b->t, clamp_arc(G, (double)x - b->X[0]), dv);
             for (int k = 0; k < 3; ++k) tb[k] = (double)ub[1] * dv[k];
+            // the head frame: U0 e_x + rate(x - X0) e_y
+            gb[0] = (double)ub[1] * swimmer_rate_dX(G, b->t, (double)x - b->X[0]);
+            gb[3] = (double)ub[0];
         } else if (lane == 0 && G.kind == LBM_BODY_AIRFOIL) {
             double dX1[2], dU1[2];
             airfoil_plunge_tangent(G, b->t, dX1, dU1);
@@ -804,11 +970,9 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
         }
         if (lane == 0)
             for (int k = 0; k < 3; ++k) tslots[(size_t)upos[slot] * 6 + 3 + k] += tb[k];
-        // the free swimmer's state through the refill velocity U0 e_x + rate(x - X0) e_y
-        if (lane == 0 && bslot) {
-            bslot[(size_t)upos[slot] * BODY_SLOTS + 2] = (double)ub[1] * swimmer_rate_dX(G, b->t, (double)x - b->X[0]);
-            bslot[(size_t)upos[slot] * BODY_SLOTS + 3] = (double)ub[0];
-        }
+        // the free body's state through the refill velocity
+        if (lane == 0 && bslot)
+            for (int d = 0; d < 6; ++d) bslot[(size_t)upos[slot] * BODY_SLOTS + 6 + d] = gb[d];
         __syncwarp();
     }
 }
@@ -824,39 +988,65 @@ __global__ void __launch_bounds__(256) vertex_tangent_kernel(const GeomParams G,
     swimmer_velocity_tangent(G, b->t, s, G.mesh_dvy + 3 * (size_t)v);
 }
 
-// One reversed step of the free swimmer's state (explicit Euler, Sec. 4.3:
-// X' = X + U, U' = U + F/m with F the force of the step before): the step's
-// geometry gives g_X, g_U (sum of the band slots, fixed order; the slots are
-// cleared for the next step), then a_X = g_X + a_X', a_U = g_U + a_X' + a_U',
-// and the force of the step reversed next weighs w/T + a_U/m along x.
+// One reversed step of the free body's state (explicit Euler, Sec. 4.3, on
+// the free degrees: X' = X + U, U' = U + F/m; yaw: psi' = psi + omega,
+// L' = L + M_z, omega = L / I(tau)).  The step's geometry gives g over
+// (X_x, X_y, psi, U_x, U_y, omega) (sum of the band slots, fixed order; the
+// slots are cleared for the next step), then per free axis
+// a_X = g_X + a_X', a_U = g_U + a_X' + a_U' and the force of the step
+// reversed next weighs w/T + a_U/m; with yaw free a_omega = g_omega + a_psi',
+// a_psi = g_psi + a_psi', a_L = a_omega / I + a_L', the torque of the step
+// reversed next weighs a_L, and theta reaches omega through I(theta):
+// dJ/dtheta += a_omega (-omega / I) dI/dtheta.
 __global__ void __launch_bounds__(256) body_reduce_kernel(double *__restrict__ slots, int nslots,
-                                                          BodyAdjoint *__restrict__ badj, double wx, double inv_mass)
+                                                          BodyAdjoint *__restrict__ badj, const GeomParams G,
+                                                          const DevBody *__restrict__ b,
+                                                          const ComTangents *__restrict__ ct, double wx, double wy)
 {
-    __shared__ double sm[256][2];
-    double v[2] = {0, 0};
+    __shared__ double sm[256][6];
+    double v[6] = {0, 0, 0, 0, 0, 0};
     for (int s = threadIdx.x; s < nslots; s += 256) {
         double *p = slots + (size_t)s * BODY_SLOTS;
-        v[0] += p[0] + p[2];
-        v[1] += p[1] + p[3];
-        p[0] = p[1] = p[2] = p[3] = 0.0;
+        for (int d = 0; d < 6; ++d) {
+            v[d] += p[d] + p[6 + d];
+            p[d] = p[6 + d] = 0.0;
+        }
     }
-    sm[threadIdx.x][0] = v[0];
-    sm[threadIdx.x][1] = v[1];
+    for (int d = 0; d < 6; ++d) sm[threadIdx.x][d] = v[d];
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            sm[threadIdx.x][0] += sm[threadIdx.x + h][0];
-            sm[threadIdx.x][1] += sm[threadIdx.x + h][1];
-        }
+        if ((int)threadIdx.x < h)
+            for (int d = 0; d < 6; ++d) sm[threadIdx.x][d] += sm[threadIdx.x + h][d];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double aX = sm[0][0] + badj->aX;
-        const double aU = sm[0][1] + badj->aX + badj->aU;
-        badj->aX = aX;
-        badj->aU = aU;
-        badj->fw[0] = wx + aU * inv_mass;
+    if (threadIdx.x != 0) return;
+    const double *g = sm[0];
+    const double w[2] = {wx, wy};
+    for (int a = 0; a < 2; ++a) {
+        if (!(G.free_motion & (1 << a))) continue;
+        const double aX = g[a] + badj->aX[a];
+        const double aU = g[3 + a] + badj->aX[a] + badj->aU[a];
+        badj->aX[a] = aX;
+        badj->aU[a] = aU;
+        badj->fw[a] = w[a] + aU * G.inv_mass;
     }
+    if (G.com_frame && (G.free_motion & 4)) {
+        const double aw = g[5] + badj->aPsi;
+        badj->aPsi = g[2] + badj->aPsi;
+        badj->aL = aw / b->Izz + badj->aL;
+        badj->mw = badj->aL;
+        for (int k = 0; k < 3; ++k) badj->dth[k] += aw * (-b->omega / b->Izz) * ct->dI[k];
+    }
+}
+
+// The free yaw's initial angular momentum L^0 = I(t0; theta) omega_0 (set when
+// the geometry is given) also moves with theta: dJ/dtheta += a_L omega_0 dI/dtheta
+// with a_L the adjoint of L after the first step, dI at the initial pose.
+__global__ void initial_spin_kernel(BodyAdjoint *__restrict__ badj, const DevBody *__restrict__ b0,
+                                    const ComTangents *__restrict__ ct)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = 0; k < 3; ++k) badj->dth[k] += badj->aL * b0->omega * ct->dI[k];
 }
 
 // acc[k] = sum over band slots of slot[6 s + k] + slot[6 s + 3 + k], fixed
@@ -1023,7 +1213,7 @@ int list_blocks(int cap)
 template <typename S>
 cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
                          typename Codec<S>::R *lam_out, double *ext, double *tslots, BodyAdjoint *badj,
-                         double *bslot, double wx)
+                         double *bslot, double wx, double wy, ComTangents *ct, double *cpart, unsigned *cticket)
 {
     using R = typename Codec<S>::R;
     const Lattice &L = ctx->L;
@@ -1036,10 +1226,12 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     if (ctx->has_body) {
         if (G.kind == LBM_BODY_MESH)
             vertex_tangent_kernel<<<(G.n_vertices + 255) / 256, 256, 0, s>>>(G, b);
+        if (G.kind == LBM_BODY_MESH && G.com_frame)
+            com_tangent_kernel<<<(G.n_triangles + 255) / 256, 256, 0, s>>>(G, b, cpart, cticket, ct);
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
         adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, ctx->side>>>(
-            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot);
+            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot, ct);
         if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
     }
     const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
@@ -1048,9 +1240,9 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     if (ctx->has_body) {
         if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
-            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot);
+            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot, ct);
         if (bslot)
-            body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, wx, G.inv_mass);
+            body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, G, b, ct, wx, wy);
     }
     return cudaGetLastError();
 }
@@ -1080,9 +1272,15 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     double F0[3] = {0, 0, 0}, F1[3] = {0, 0, 0}, accv[3] = {0, 0, 0};
     // the swimmer free along x carries (X0, U0) as adjoint state
     const bool free_body = ctx->has_body && ctx->G.free_motion != 0;
-    const BodyAdjoint badj0{0.0, 0.0, {spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}};
+    const BodyAdjoint badj0{{0.0, 0.0}, {0.0, 0.0}, 0.0, 0.0,
+                            {spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}, 0.0, {0.0, 0.0, 0.0}};
     BodyAdjoint *badj = nullptr;
     double *bslot = nullptr;
+    const bool com = free_body && ctx->G.kind == LBM_BODY_MESH && ctx->G.com_frame;
+    ComTangents *ct = nullptr;
+    double *cpart = nullptr;
+    unsigned *cticket = nullptr;
+    BodyAdjoint hbadj{};
     DevBody hb{};
     int p = 0;
     const int save_bcur = ctx->bcur;
@@ -1096,6 +1294,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
         !B.get(&ext[0], (size_t)cap * Q) || !B.get(&ext[1], (size_t)cap * Q) || !B.get(&tslots, (size_t)cap * 6) ||
         !B.get(&acc, 3) || !B.get(&part, nparts) || !B.get(&badj, 1) ||
         (free_body && !B.get(&bslot, (size_t)cap * BODY_SLOTS)) ||
+        (com && (!B.get(&ct, 1) || !B.get(&cpart, (size_t)((ctx->G.n_triangles + 255) / 256) * COM_SUMS) ||
+                 !B.get(&cticket, 1))) ||
         (body && ctx->G.kind == LBM_BODY_MESH &&
          (!B.get(&tan_dy, 3 * (size_t)ctx->G.n_vertices) || !B.get(&tan_dvy, 3 * (size_t)ctx->G.n_vertices))))
         return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the checkpoints failed");
@@ -1142,6 +1342,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     ADJ_CUDA(cudaMemsetAsync(tslots, 0, (size_t)cap * 6 * sizeof(double), s), "clear");
     ADJ_CUDA(cudaMemcpyAsync(badj, &badj0, sizeof(BodyAdjoint), cudaMemcpyHostToDevice, s), "body adjoint");
     if (bslot) ADJ_CUDA(cudaMemsetAsync(bslot, 0, (size_t)cap * BODY_SLOTS * sizeof(double), s), "clear");
+    if (cticket) ADJ_CUDA(cudaMemsetAsync(cticket, 0, sizeof(unsigned), s), "clear");
     {
         bool first = true;
         for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1179,7 +1380,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                                    body ? wf[p ^ 1] : nullptr, 0};
                 }
                 ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, badj, bslot,
-                                         badj0.fw[0]),
+                                         badj0.fw[0], badj0.fw[1], ct, cpart, cticket),
                          "reverse step");
                 if (body)
                     ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),
@@ -1195,10 +1396,16 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
             ADJ_CUDA(cudaGetLastError(), "lambda0");
         }
     }
+    if (com && (ctx->G.free_motion & 4)) {
+        com_tangent_kernel<<<(ctx->G.n_triangles + 255) / 256, 256, 0, s>>>(ctx->G, ckbody, cpart, cticket, ct);
+        initial_spin_kernel<<<1, 32, 0, s>>>(badj, ckbody, ct);
+    }
     if (body) theta_reduce_kernel<<<1, 256, 0, s>>>(tslots, cap, acc);
     ADJ_CUDA(cudaMemcpyAsync(accv, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "theta");
+    ADJ_CUDA(cudaMemcpyAsync(&hbadj, badj, sizeof(BodyAdjoint), cudaMemcpyDeviceToHost, s), "body adjoint");
     ADJ_CUDA(cudaStreamSynchronize(s), "sync");
-    for (int k = 0; k < 3; ++k) dJ[k] = accv[k];
+    // plus what theta does through the free yaw's omega = L / I(theta)
+    for (int k = 0; k < 3; ++k) dJ[k] = accv[k] + hbadj.dth[k];
 
 done:
     ctx->G.mesh_dy = nullptr;
@@ -1223,9 +1430,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
     if (ctx->L.gamma_mode == LBM_GAMMA_EXACT)
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: the exact stabilizer has no adjoint here");
-    if (ctx->has_body && ctx->G.free_motion && !(ctx->G.kind == LBM_BODY_MESH && ctx->G.free_motion == 1))
-        return afail(ctx, LBM_ERR_UNSUPPORTED,
-                     "lbm_adjoint_step: a free body must be the swimmer free along x alone (no free sphere, y or yaw)");
+    if (ctx->has_body && ctx->G.free_motion && ctx->G.kind != LBM_BODY_MESH)
+        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: a free body must be the swimmer (no free sphere)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
     if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");

@@ -618,6 +618,158 @@ __device__ __noinline__ static void mesh_link_body_tangent(const GeomParams &G, 
     for (int a = 0; a < 3; ++a) duw[a] = du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]);
 }
 
+// ---------------------------------------------------------------- centre-of-mass frame tangents
+// The swimmer free in y or yaw (centre-of-mass frame): derivatives of the
+// pose at body time tau with respect to nine directions, the kinematic
+// parameters theta_0..2 and the body state X_x, X_y, psi, U_x, U_y, omega:
+//   vertex  p = X + R(psi) (b(tau) - c(tau)),
+//   velocity  v = U + omega e_z x (p - X) + R(psi) (b_dot - c_dot).
+// dc, dcdot and dI are the theta-derivatives of the centre of mass c(tau), of
+// its central-difference rate and of the moment of inertia I(tau).
+constexpr int COM_DIRS = 9;
+
+struct ComTangents {
+    double dc[3][2];
+    double dcdot[3][2];
+    double dI[3];
+};
+
+// per-vertex derivatives of position and velocity for the nine directions
+__device__ __forceinline__ void com_vertex_tangents(const GeomParams &G, const DevBody *b, const ComTangents &ct,
+                                                    int v, double dP[COM_DIRS][3], double dV[COM_DIRS][3])
+{
+    const double cs = cos(b->psi), sn = sin(b->psi), w = b->omega;
+    const double P[3] = {G.mesh_pos[3 * v], G.mesh_pos[3 * v + 1], G.mesh_pos[3 * v + 2]};
+    const double Vv[3] = {G.mesh_vel[3 * v], G.mesh_vel[3 * v + 1], G.mesh_vel[3 * v + 2]};
+    const double rx = P[0] - b->X[0], ry = P[1] - b->X[1];
+    for (int d = 0; d < COM_DIRS; ++d)
+        for (int a = 0; a < 3; ++a) dP[d][a] = dV[d][a] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        // body-frame displacement (-dc_x, dy_theta - dc_y), rotated
+        const double bx = -ct.dc[k][0], by = G.mesh_dy[3 * v + k] - ct.dc[k][1];
+        dP[k][0] = cs * bx - sn * by;
+        dP[k][1] = sn * bx + cs * by;
+        const double wx = -ct.dcdot[k][0], wy = G.mesh_dvy[3 * v + k] - ct.dcdot[k][1];
+        dV[k][0] = -w * dP[k][1] + (cs * wx - sn * wy);
+        dV[k][1] = w * dP[k][0] + (sn * wx + cs * wy);
+    }
+    dP[3][0] = 1.0;
+    dP[4][1] = 1.0;
+    // rotation about X: dp = e_z x r, dv = omega e_z x dp + e_z x (R w)
+    dP[5][0] = -ry;
+    dP[5][1] = rx;
+    const double Rw[2] = {Vv[0] - b->U[0] + w * ry, Vv[1] - b->U[1] - w * rx};
+    dV[5][0] = -w * dP[5][1] - Rw[1];
+    dV[5][1] = w * dP[5][0] + Rw[0];
+    dV[6][0] = 1.0;
+    dV[7][1] = 1.0;
+    dV[8][0] = -ry;
+    dV[8][1] = rx;
+}
+
+// derivatives of the material velocity at the fixed world point (px, py)
+// (mesh_material_velocity in the centre-of-mass frame): its arc position
+// s = [R^T (p - X)]_x + c_x moves with X, psi and c_x
+__device__ __forceinline__ void com_material_velocity_tangents(const GeomParams &G, const DevBody *b,
+                                                               const ComTangents &ct, double px, double py,
+                                                               double du[COM_DIRS][3])
+{
+    const double cs = cos(b->psi), sn = sin(b->psi), w = b->omega;
+    const double rx = px - b->X[0], ry = py - b->X[1];
+    const double s_raw = cs * rx + sn * ry + b->com[0];
+    const double s = clamp_arc(G, s_raw);
+    // d rate / ds (0 where the arc position is clamped)
+    const double rs = -swimmer_rate_dX(G, b->t, s_raw);
+    const double rate = (swimmer_midline(G, s, b->t + 1.0) - swimmer_midline(G, s, b->t - 1.0)) / 2.0;
+    const double Rw[2] = {cs * (-b->com_dot[0]) - sn * (rate - b->com_dot[1]),
+                          sn * (-b->com_dot[0]) + cs * (rate - b->com_dot[1])};
+    double dvt[3];
+    swimmer_velocity_tangent(G, b->t, s, dvt);
+    for (int d = 0; d < COM_DIRS; ++d) du[d][0] = du[d][1] = du[d][2] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double wx = -ct.dcdot[k][0], wy = dvt[k] + rs * ct.dc[k][0] - ct.dcdot[k][1];
+        du[k][0] = cs * wx - sn * wy;
+        du[k][1] = sn * wx + cs * wy;
+    }
+    // X: r moves by -e_a, s by -(cs, sn)_a
+    du[3][0] = -sn * (-cs * rs);
+    du[3][1] = -w + cs * (-cs * rs);
+    du[4][0] = w - sn * (-sn * rs);
+    du[4][1] = cs * (-sn * rs);
+    // psi: e_z x (R w) + R (0, rate' ds/dpsi)
+    const double dsp = -sn * rx + cs * ry;
+    du[5][0] = -Rw[1] - sn * rs * dsp;
+    du[5][1] = Rw[0] + cs * rs * dsp;
+    du[6][0] = 1.0;
+    du[7][1] = 1.0;
+    du[8][0] = -ry;
+    du[8][1] = rx;
+}
+
+// derivatives of a link's fraction q and wall velocity u_w for the nine
+// directions (plane and barycentric relations of mesh_link_tangent with
+// general vertex displacements and velocity changes)
+__device__ __noinline__ static void com_link_tangents(const GeomParams &G, const DevBody *b, const ComTangents &ct,
+                                                      int x, int y, int z, int cx, int cy, int cz, double q,
+                                                      const MeshHit &h, double dq[COM_DIRS],
+                                                      double duw[COM_DIRS][3])
+{
+    if (h.tri < 0) {
+        com_material_velocity_tangents(G, b, ct, (double)x - 0.5 * cx, (double)y - 0.5 * cy, duw);
+        for (int d = 0; d < COM_DIRS; ++d) dq[d] = 0.0;
+        return;
+    }
+    const int tv[3] = {G.mesh_tris[3 * h.tri], G.mesh_tris[3 * h.tri + 1], G.mesh_tris[3 * h.tri + 2]};
+    double P[3][3], V[3][3];
+    for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a) {
+            P[m][a] = G.mesh_pos[3 * tv[m] + a];
+            V[m][a] = G.mesh_vel[3 * tv[m] + a];
+        }
+    const double c[3] = {(double)cx, (double)cy, (double)cz};
+    double e1[3], e2[3], H[3], n[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = P[1][a] - P[0][a];
+        e2[a] = P[2][a] - P[0][a];
+    }
+    H[0] = (double)x - q * c[0] - P[0][0];
+    H[1] = (double)y - q * c[1] - P[0][1];
+    H[2] = (double)z - q * c[2] - P[0][2];
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double nc = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+    const double g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const double gdet = g11 * g22 - g12 * g12;
+    double dP[3][COM_DIRS][3], dV[3][COM_DIRS][3];
+    for (int m = 0; m < 3; ++m) com_vertex_tangents(G, b, ct, tv[m], dP[m], dV[m]);
+    for (int d = 0; d < COM_DIRS; ++d) {
+        double de1[3], de2[3], dn[3];
+        for (int a = 0; a < 3; ++a) {
+            de1[a] = dP[1][d][a] - dP[0][d][a];
+            de2[a] = dP[2][d][a] - dP[0][d][a];
+        }
+        dn[0] = de1[1] * e2[2] - de1[2] * e2[1] + e1[1] * de2[2] - e1[2] * de2[1];
+        dn[1] = de1[2] * e2[0] - de1[0] * e2[2] + e1[2] * de2[0] - e1[0] * de2[2];
+        dn[2] = de1[0] * e2[1] - de1[1] * e2[0] + e1[0] * de2[1] - e1[1] * de2[0];
+        const double ds = nc != 0.0 ? ((dn[0] * H[0] + dn[1] * H[1] + dn[2] * H[2]) -
+                                       (n[0] * dP[0][d][0] + n[1] * dP[0][d][1] + n[2] * dP[0][d][2])) / nc
+                                    : 0.0;
+        double rhs[3];
+        for (int a = 0; a < 3; ++a) rhs[a] = -ds * c[a] - dP[0][d][a] - h.u * de1[a] - h.v * de2[a];
+        const double b1 = e1[0] * rhs[0] + e1[1] * rhs[1] + e1[2] * rhs[2];
+        const double b2 = e2[0] * rhs[0] + e2[1] * rhs[1] + e2[2] * rhs[2];
+        const double du = gdet != 0.0 ? (b1 * g22 - b2 * g12) / gdet : 0.0;
+        const double dv = gdet != 0.0 ? (g11 * b2 - g12 * b1) / gdet : 0.0;
+        dq[d] = ds;
+        for (int a = 0; a < 3; ++a)
+            duw[d][a] = du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]) + (1.0 - h.u - h.v) * dV[0][d][a] +
+                        h.u * dV[1][d][a] + h.v * dV[2][d][a];
+    }
+}
+
 // ---------------------------------------------------------------- airfoil tangents
 // Derivatives with respect to theta = (h_amp, h_omega) of the plunge at body
 // time t (Sec. 4.2): X1 = y_base + A sin(w t), U1 = A w cos(w t).

@@ -54,11 +54,12 @@ def test_initial_state_gradient_matches_tape(faces, lbgk):
 
 
 def _swimmer_geom(L=24.0, X=(12.137, 12.371, 12.293), theta=(0.125, 24.0, 96.0), segments=48, ring=16,
-                  free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0)):
+                  free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0), psi=0.0, omega=0.0):
     import paper_1608_04658_gb300 as lbm
     rest, tris = synth.swimmer_mesh(L, segments, ring)
     a, lam, T = theta
-    return lbm.swimmer(X, rest, tris, L, a, lam, T, mass=mass_scale * synth.swimmer_volume(L), free=free, U=U)
+    return lbm.swimmer(X, rest, tris, L, a, lam, T, mass=mass_scale * synth.swimmer_volume(L), free=free, U=U,
+                       psi=psi, omega=omega)
 
 
 def _dot_product_check(shape, geom_fn, storage="fp64", H=4, seed=41):
@@ -122,11 +123,12 @@ def test_dot_product_with_free_swimmer():
 
 
 def _oracle_thrust(shape, theta, fields, H, w, L=24.0, X=(12.137, 12.371, 12.293), segments=48, ring=16,
-                   free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0)):
+                   free=False, mass_scale=1.0, U=(0.0, 0.0, 0.0), psi=0.0, omega=0.0):
     rest, tris = synth.swimmer_mesh(L, segments, ring)
     a, lam, T = theta
     o = oracle.Oracle(shape, nu=0.02, body=oracle.mesh_body(X, rest, tris, L, a, lam, T, U=U, free=free,
-                                                           mass=mass_scale * synth.swimmer_volume(L)))
+                                                           mass=mass_scale * synth.swimmer_volume(L),
+                                                           psi=psi, omega=omega))
     rho, u, xi, amp = fields
     o.init_state(rho, u, xi, amp)
     J = 0.0
@@ -206,6 +208,54 @@ def test_free_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     held.set_geometry(_swimmer_geom(theta=tuple(theta), mass_scale=0.25, U=(-0.01, 0.0, 0.0)))
     held.init_state(*fields)
     assert np.abs(held.adjoint(H, w)["dJ_dtheta"] - g).max() > 10 * tol * np.abs(fd).max()
+
+
+# the swimmer in the centre-of-mass frame: X is its centre of mass
+_COM = dict(X=(24.137, 12.371, 12.293), mass_scale=1.0, U=(-0.01, 0.004, 0.0), psi=0.1, omega=0.003)
+
+
+def test_dot_product_with_three_dof_swimmer():
+    """Swimmer free in x, y and yaw (centre-of-mass frame): the adjoint carries
+    the centre of mass, its velocity, the yaw angle and the angular momentum
+    backwards through the Euler update; initial-state gradient vs central
+    differences of the GPU forward."""
+    ad, fd = _dot_product_check((48, 24, 24), lambda: _swimmer_geom(free=7, **_COM))
+    assert ad == pytest.approx(fd, rel=1e-7)
+
+
+@pytest.mark.parametrize("free,storage,tol", [(3, "fp64", 1e-6), (4, "fp64", 1e-6), (7, "fp64", 1e-6),
+                                              (7, "fp32", 2e-3)])
+def test_com_frame_swimmer_thrust_gradient_matches_oracle_fd(free, storage, tol):
+    """Mean-thrust gradient of the swimmer free in x and y (3), in yaw (4) or
+    in x, y and yaw (7): the pose X + R(psi)(b - c(t)) moves with theta
+    through the midline and the centre of mass c and, with yaw free, through
+    omega = L / I(theta) (the initial L = I(t0) omega_0 included); GPU adjoint
+    vs central differences of the FP64 oracle."""
+    shape, H = (48, 24, 24), 8
+    theta = np.array([0.125, 24.0, 96.0])
+    w = np.array([-1.0, 0.0, 0.0])
+    kw = dict(free=free, **_COM)
+    rho, u, xi = synth.parity_fields(shape, 53)
+    fields = (rho, 0.2 * u, xi, 1e-3)
+    lat = _lat(shape, 0.02, storage=storage)
+    lat.set_geometry(_swimmer_geom(theta=tuple(theta), **kw))
+    lat.init_state(*fields)
+    out = lat.adjoint(H, w)
+    J0, _, _ = _oracle_thrust(shape, theta, fields, H, w, **kw)
+    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-3)
+    fd = np.zeros(3)
+    for k in range(3):
+        h = 1e-6 * theta[k]
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        Jp, cp, sp = _oracle_thrust(shape, tp, fields, H, w, **kw)
+        Jm, cm, sm = _oracle_thrust(shape, tm, fields, H, w, **kw)
+        assert cp == cm and np.array_equal(sp, sm), "link set changed within the difference step"
+        fd[k] = (Jp - Jm) / (2 * h)
+    g = out["dJ_dtheta"]
+    assert np.all(np.abs(fd) > 0)
+    assert np.abs(g - fd).max() <= tol * np.abs(fd).max()
 
 
 def _airfoil_case(theta, t0=3.0):
@@ -322,12 +372,6 @@ def test_adjoint_rejects_unsupported_free_bodies_and_16_bit_storage():
     lat.init_state(*synth.uniform_fields((12, 12, 12)))
     with pytest.raises(lbm.LbmError):
         lat.adjoint(2)
-    # the swimmer free in y or yaw (centre-of-mass frame) has no adjoint here
-    sw = _lat((48, 24, 24), 0.02)
-    sw.set_geometry(_swimmer_geom(X=(24.137, 12.371, 12.293), free=7))
-    sw.init_state(*synth.uniform_fields((48, 24, 24)))
-    with pytest.raises(lbm.LbmError):
-        sw.adjoint(2)
     lat16 = _lat((12, 12, 12), 0.05, storage="fp16")
     lat16.init_state(*synth.uniform_fields((12, 12, 12)))
     with pytest.raises(lbm.LbmError):
