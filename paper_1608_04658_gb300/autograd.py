@@ -25,9 +25,10 @@ class KinematicsObjective(torch.autograd.Function):
 
 def kinematics_objective(make_lattice, horizon: int, w_force, checkpoint_every: int = 0):
     """Returns f(theta) -> J as a differentiable torch function.
-    make_lattice(theta) must return a Lattice at its initial state with a held
-    swimmer whose (wave_amp, wave_length, wave_period) are theta; J is the mean
-    of w_force . F over ``horizon`` steps (w_force = e_swim for the thrust)."""
+    make_lattice(theta) must return a Lattice at its initial state with a
+    swimmer (held, or free in any of x, y and yaw) whose (wave_amp,
+    wave_length, wave_period) are theta; J is the mean of w_force . F over
+    ``horizon`` steps (w_force = e_swim for the thrust)."""
 
     def run(theta):
         lat = make_lattice(theta)
