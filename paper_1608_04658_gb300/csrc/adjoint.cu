@@ -21,6 +21,7 @@
 // lambda(St^t)(y).  The marks, boundary links and refilled nodes of each step
 // are those of the forward run (held fixed).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 
@@ -397,17 +398,38 @@ __device__ __noinline__ R next_adjoint_rare(const Lattice &L, const GeomParams &
 #define LBM_ADJ_MIN_BLOCKS 4
 #endif
 
+// Launch modes as those of the bulk kernel (BulkMode): ALL every node;
+// OUTSIDE the nodes outside box0 (the band of step t) and box1 (the band of
+// step t+1, whose ext and refill marks the gather reads), which are fluid and
+// no boundary node at t+1 and read neither; BAND the nodes of box0 that are
+// not in box1 (capacity-box grid).
 template <typename S>
 __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) adjoint_bulk_kernel(const Lattice L, const GeomParams G,
                                                            const S *__restrict__ st,
                                                            const NextAdj<typename Codec<S>::R> A,
                                                            const uint8_t *__restrict__ flags1,
-                                                           typename Codec<S>::R *__restrict__ lam_out)
+                                                           typename Codec<S>::R *__restrict__ lam_out,
+                                                           int mode, const int *__restrict__ box0,
+                                                           const int *__restrict__ box1)
 {
     using R = typename Codec<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= L.nx) return;
+    int x, y, z;
+    if (mode == BULK_BAND) {
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        const int lx = k % G.cap[0], ly = (k / G.cap[0]) % G.cap[1], lz = k / (G.cap[0] * G.cap[1]);
+        if (lz >= G.cap[2] || lx >= box0[3] || ly >= box0[4] || lz >= box0[5]) return;
+        x = sweep_coord(box0[0] + lx, L.nx);
+        y = sweep_coord(box0[1] + ly, L.ny);
+        z = sweep_coord(box0[2] + lz, L.nz);
+        if (box1 && in_sweep_box(L, box1, x, y, z)) return;
+    } else {
+        x = blockIdx.x * blockDim.x + threadIdx.x;
+        y = blockIdx.y;
+        z = blockIdx.z;
+        if (x >= L.nx) return;
+        if (mode == BULK_OUTSIDE && ((box0 && in_sweep_box(L, box0, x, y, z)) || (box1 && in_sweep_box(L, box1, x, y, z))))
+            return;
+    }
     const int n = x + L.nx * (y + L.ny * z);
     const size_t N = (size_t)L.N;
     const uint8_t f1 = flags1 ? flags1[n] : 0;
@@ -1208,20 +1230,55 @@ int list_blocks(int cap)
     return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
 }
 
-// the reverse of step t (body state of step t in S.body[bcur], marks of step t
-// in flags1 after the geometry re-run) for storage type S
+// the reverse of step t for storage type S.  Sequential order: the caller
+// has re-run the geometry (body state of step t+1 in S.body[1], marks in
+// flags1) and cleared ext.  Split order (split, a band known ahead): the body
+// state of step t is in S.body[0] and the geometry re-run, the boundary and
+// refill adjoints and the bulk adjoint over the two steps' bands run on the
+// side stream, beside the bulk adjoint of the nodes outside them.
 template <typename S>
 cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
                          typename Codec<S>::R *lam_out, double *ext, double *tslots, BodyAdjoint *badj,
-                         double *bslot, double wx, double wy, ComTangents *ct, double *cpart, unsigned *cticket)
+                         double *bslot, double wx, double wy, ComTangents *ct, double *cpart, unsigned *cticket,
+                         bool split)
 {
     using R = typename Codec<S>::R;
     const Lattice &L = ctx->L;
     const GeomParams &G = ctx->G;
     Scratch &Sc = ctx->S;
-    const DevBody *b = Sc.body + ctx->bcur;
     cudaStream_t s = ctx->stream;
+    cudaStream_t side = ctx->side;
     cudaError_t e;
+    const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
+    dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
+    if (split) {
+        // band of step t (stored with state t) and of step t+1 (A.band)
+        const int *box0 = (const int *)((const char *)(Sc.body + 0) + offsetof(DevBody, sweep));
+        const int *box1 = A.band ? (const int *)((const char *)A.band + offsetof(DevBody, band_lo)) : nullptr;
+        const DevBody *b = Sc.body + 1;
+        const int capv = G.cap[0] * G.cap[1] * G.cap[2];
+        const unsigned nbb = (unsigned)((capv + 127) / 128);
+        int nl = 0;
+        if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_geometry(L, G, Sc, 0, flags1, side, &nl)) != cudaSuccess) return e;
+        ctx->bcur = 1;
+        if ((e = cudaMemsetAsync(ext, 0, (size_t)capv * Q * sizeof(double), side)) != cudaSuccess) return e;
+        if (G.kind == LBM_BODY_MESH) vertex_tangent_kernel<<<(G.n_vertices + 255) / 256, 256, 0, side>>>(G, b);
+        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, side>>>(
+            L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot, ct);
+        adjoint_bulk_kernel<S><<<nbb, 128, 0, side>>>(L, G, st, A, flags1, lam_out, BULK_BAND, box0, nullptr);
+        if (box1)
+            adjoint_bulk_kernel<S><<<nbb, 128, 0, side>>>(L, G, st, A, flags1, lam_out, BULK_BAND, box1, box0);
+        adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, side>>>(
+            L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot, ct);
+        if (bslot) body_reduce_kernel<<<1, 256, 0, side>>>(bslot, capv, badj, G, b, ct, wx, wy);
+        if ((e = cudaEventRecord(ctx->ev_join, side)) != cudaSuccess) return e;
+        adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, nullptr, lam_out, BULK_OUTSIDE, box0, box1);
+        if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    const DevBody *b = Sc.body + ctx->bcur;
     // the boundary adjoint runs beside the bulk adjoint (disjoint rows of Lam^t)
     if (ctx->has_body) {
         if (G.kind == LBM_BODY_MESH)
@@ -1229,14 +1286,13 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
         if (G.kind == LBM_BODY_MESH && G.com_frame)
             com_tangent_kernel<<<(G.n_triangles + 255) / 256, 256, 0, s>>>(G, b, cpart, cticket, ct);
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
-        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, ctx->side>>>(
+        if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+        adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, side>>>(
             L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot, ct);
-        if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ctx->ev_join, side)) != cudaSuccess) return e;
     }
-    const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
-    dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
-    adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, ctx->has_body ? flags1 : nullptr, lam_out);
+    adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, ctx->has_body ? flags1 : nullptr, lam_out, BULK_ALL,
+                                               nullptr, nullptr);
     if (ctx->has_body) {
         if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
@@ -1277,6 +1333,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     BodyAdjoint *badj = nullptr;
     double *bslot = nullptr;
     const bool com = free_body && ctx->G.kind == LBM_BODY_MESH && ctx->G.com_frame;
+    // reverse steps in the split order when the band is known ahead
+    const bool split = body && sweep_ahead(ctx->G) && ctx->order != ORDER_SEQUENTIAL;
     ComTangents *ct = nullptr;
     double *cpart = nullptr;
     unsigned *cticket = nullptr;
@@ -1366,7 +1424,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                 ADJ_CUDA(cudaMemcpyAsync(wf[p], segflags + (size_t)j * N, N, cudaMemcpyDeviceToDevice, s), "flags");
                 ctx->bcur = 0;
                 ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, segbody + j, sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "body");
-                if (body) {
+                if (body && !split) {
                     int nl = 0;
                     ADJ_CUDA(launch_geometry(L, ctx->G, ctx->S, 0, wf[p], s, &nl), "geometry");
                     ctx->bcur = 1;
@@ -1380,7 +1438,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                                    body ? wf[p ^ 1] : nullptr, 0};
                 }
                 ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, badj, bslot,
-                                         badj0.fw[0], badj0.fw[1], ct, cpart, cticket),
+                                         badj0.fw[0], badj0.fw[1], ct, cpart, cticket, split),
                          "reverse step");
                 if (body)
                     ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),

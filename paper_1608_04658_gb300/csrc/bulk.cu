@@ -23,23 +23,6 @@ namespace lbm {
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
 
-// coordinate c on axis a (n nodes) inside the sweep box sw (wrapping on a
-// periodic axis, where lo lies in (-n, n))
-__device__ __forceinline__ bool in_sweep(const int *__restrict__ sw, int a, int c, int n, bool periodic)
-{
-    int d = c - sw[a];
-    if (periodic) {
-        if (d < 0) d += n;
-        else if (d >= n) d -= n;
-    }
-    return (unsigned)d < (unsigned)sw[3 + a];
-}
-
-__device__ __forceinline__ int sweep_coord(int v, int n)
-{
-    return v < 0 ? v + n : (v >= n ? v - n : v);
-}
-
 template <typename S, bool EXACT>
 __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const Lattice L, const S *__restrict__ fa,
                                                    S *__restrict__ fb,

@@ -36,6 +36,30 @@ __device__ __forceinline__ void axis_off(int a, int n, int stride, int face_lo, 
     }
 }
 
+// coordinate c on axis a (n nodes) inside the sweep box sw = {lo[3], n[3]}
+// (wrapping on a periodic axis, where lo lies in (-n, n))
+__device__ __forceinline__ bool in_sweep(const int *__restrict__ sw, int a, int c, int n, bool periodic)
+{
+    int d = c - sw[a];
+    if (periodic) {
+        if (d < 0) d += n;
+        else if (d >= n) d -= n;
+    }
+    return (unsigned)d < (unsigned)sw[3 + a];
+}
+
+__device__ __forceinline__ bool in_sweep_box(const Lattice &L, const int *__restrict__ sw, int x, int y, int z)
+{
+    return in_sweep(sw, 1, y, L.ny, L.face[2] == LBM_FACE_PERIODIC) &&
+           in_sweep(sw, 2, z, L.nz, L.face[4] == LBM_FACE_PERIODIC) &&
+           in_sweep(sw, 0, x, L.nx, L.face[0] == LBM_FACE_PERIODIC);
+}
+
+__device__ __forceinline__ int sweep_coord(int v, int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
 // pulls of node (x, y, z) from global memory under the box rules
 template <typename S>
 __device__ __forceinline__ void gather_global(const Lattice &L, const S *__restrict__ fa, int x, int y, int z,
