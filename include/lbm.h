@@ -335,16 +335,15 @@ LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *laun
  *   MESH: (wave_amp, wave_length, wave_period) of the midline (Sec. 4.3);
  *   AIRFOIL: (h_amp, h_omega) of the plunge (Sec. 4.2), third entry 0;
  *   other bodies: none (zeros).
- * The body is held or prescribed, or it is the swimmer free in any of x, y
- * and yaw: then the free degrees of its state are adjoint state too (the
- * head's X0 and U0 in the head frame; the centre of mass, its velocity, the
- * yaw angle and the angular momentum in the centre-of-mass frame), carried
- * back through the explicit Euler update, the links' fraction and wall
- * velocity, the refill velocity and the momentum-exchange force and torque;
- * theta also reaches the pose through the centre of mass c(t) and its rate,
- * and the yaw rate through the moment of inertia I(theta) (omega = L / I, the
- * initial L = I(t0) omega included).  A free sphere returns
- * LBM_ERR_UNSUPPORTED.
+ * The body is held, prescribed or free.  The free degrees of its state are
+ * adjoint state too (the sphere's centre and velocity; the swimmer's head X0
+ * and U0 in the head frame, or its centre of mass, velocity, yaw angle and
+ * angular momentum in the centre-of-mass frame), carried back through the
+ * explicit Euler update, the links' fraction and wall velocity, the refill
+ * velocity and the momentum-exchange force and torque; theta also reaches the
+ * swimmer's pose through the centre of mass c(t) and its rate, and the yaw
+ * rate through the moment of inertia I(theta) (omega = L / I, the initial
+ * L = I(t0) omega included).
  * Storage FP64 (arithmetic in double) or FP32 (arithmetic in float);
  * 16-bit storage returns LBM_ERR_UNSUPPORTED.
  *

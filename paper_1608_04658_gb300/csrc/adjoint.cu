@@ -683,7 +683,7 @@ __device__ __forceinline__ void grad_pressure_adj(R gb, int i, bool act, R rho, 
 // a_U/m (the force enters U0 of the state after it, U' = U + F/m).  For a held
 // or prescribed body only the weights are used (w/T, constant).
 struct BodyAdjoint {
-    double aX[2], aU[2];  // dJ/dX, dJ/dU of the free axes (x, y)
+    double aX[3], aU[3];  // dJ/dX, dJ/dU of the free axes
     double aPsi, aL;      // dJ/dpsi, dJ/d(I omega) (yaw free)
     double fw[3];         // weights of the force of the step reversed next
     double mw;            // weight of the torque M_z of the step reversed next (yaw free)
@@ -691,8 +691,9 @@ struct BodyAdjoint {
 };
 
 // one writer per band position and reversed step: derivatives with respect to
-// (X_x, X_y, psi, U_x, U_y, omega) from the boundary node there (0..5) and
-// from the refilled node there (6..11)
+// (X_x, X_y, psi, U_x, U_y, omega) for the swimmer, (X_x, X_y, X_z, U_x, U_y,
+// U_z) for the sphere, from the boundary node there (0..5) and from the
+// refilled node there (6..11)
 constexpr int BODY_SLOTS = 12;
 
 // Boundary nodes of step t: forward recomputation of the Grad completion
@@ -884,6 +885,20 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
                 gb[0] = qb * dqX + uwb[0] * duwX[0] + uwb[1] * duwX[1] + uwb[2] * duwX[2];
                 gb[3] = uwb[0];
             }
+        } else if (miss && G.kind == LBM_BODY_SPHERE && bslot) {
+            // the free sphere: q = (c.d - sqrt(disc))/|c|^2 with d = x_b - X,
+            // disc = (c.d)^2 - |c|^2 (|d|^2 - R^2); u_w = U
+            const double d[3] = {body_offset(L, G, b, 0, x), body_offset(L, G, b, 1, y), body_offset(L, G, b, 2, z)};
+            const double c[3] = {(double)cx, (double)cy, (double)cz};
+            const double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+            const double cd = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
+            const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const double sq = sqrt(fmax(cd * cd - cc * (dd - G.R * G.R), 0.0));
+            for (int a = 0; a < 3; ++a) {
+                const double dqdd = sq > 0.0 ? (c[a] - (cd * c[a] - cc * d[a]) / sq) / cc : 0.0;
+                gb[a] = -qb * dqdd;
+                gb[3 + a] = uwb[a];
+            }
         } else if (miss && G.kind == LBM_BODY_AIRFOIL) {
             double dq[2], dX1[2], dU1[2];
             airfoil_link_tangent(G, b, x, y, cx, cy, q, dq);
@@ -985,6 +1000,8 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
             // the head frame: U0 e_x + rate(x - X0) e_y
             gb[0] = (double)ub[1] * swimmer_rate_dX(G, b->t, (double)x - b->X[0]);
             gb[3] = (double)ub[0];
+        } else if (lane == 0 && G.kind == LBM_BODY_SPHERE) {
+            for (int a = 0; a < 3; ++a) gb[3 + a] = (double)ub[a];  // the refill velocity is U
         } else if (lane == 0 && G.kind == LBM_BODY_AIRFOIL) {
             double dX1[2], dU1[2];
             airfoil_plunge_tangent(G, b->t, dX1, dU1);
@@ -1023,7 +1040,8 @@ __global__ void __launch_bounds__(256) vertex_tangent_kernel(const GeomParams G,
 __global__ void __launch_bounds__(256) body_reduce_kernel(double *__restrict__ slots, int nslots,
                                                           BodyAdjoint *__restrict__ badj, const GeomParams G,
                                                           const DevBody *__restrict__ b,
-                                                          const ComTangents *__restrict__ ct, double wx, double wy)
+                                                          const ComTangents *__restrict__ ct, double wx, double wy,
+                                                          double wz)
 {
     __shared__ double sm[256][6];
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -1043,7 +1061,18 @@ __global__ void __launch_bounds__(256) body_reduce_kernel(double *__restrict__ s
     }
     if (threadIdx.x != 0) return;
     const double *g = sm[0];
-    const double w[2] = {wx, wy};
+    const double w[3] = {wx, wy, wz};
+    if (G.kind == LBM_BODY_SPHERE) {
+        // the free sphere (Sec. 4.1): X' = X + U, U' = U + F/m + (1 - rho_f/rho_s) g on all axes
+        for (int a = 0; a < 3; ++a) {
+            const double aX = g[a] + badj->aX[a];
+            const double aU = g[3 + a] + badj->aX[a] + badj->aU[a];
+            badj->aX[a] = aX;
+            badj->aU[a] = aU;
+            badj->fw[a] = w[a] + aU * G.inv_mass;
+        }
+        return;
+    }
     for (int a = 0; a < 2; ++a) {
         if (!(G.free_motion & (1 << a))) continue;
         const double aX = g[a] + badj->aX[a];
@@ -1239,8 +1268,8 @@ int list_blocks(int cap)
 template <typename S>
 cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec<S>::R> &A, uint8_t *flags1,
                          typename Codec<S>::R *lam_out, double *ext, double *tslots, BodyAdjoint *badj,
-                         double *bslot, double wx, double wy, ComTangents *ct, double *cpart, unsigned *cticket,
-                         bool split)
+                         double *bslot, double wx, double wy, double wz, ComTangents *ct, double *cpart,
+                         unsigned *cticket, bool split)
 {
     using R = typename Codec<S>::R;
     const Lattice &L = ctx->L;
@@ -1272,7 +1301,7 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
             adjoint_bulk_kernel<S><<<nbb, 128, 0, side>>>(L, G, st, A, flags1, lam_out, BULK_BAND, box1, box0);
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, side>>>(
             L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot, ct);
-        if (bslot) body_reduce_kernel<<<1, 256, 0, side>>>(bslot, capv, badj, G, b, ct, wx, wy);
+        if (bslot) body_reduce_kernel<<<1, 256, 0, side>>>(bslot, capv, badj, G, b, ct, wx, wy, wz);
         if ((e = cudaEventRecord(ctx->ev_join, side)) != cudaSuccess) return e;
         adjoint_bulk_kernel<S><<<grid, bx, 0, s>>>(L, G, st, A, nullptr, lam_out, BULK_OUTSIDE, box0, box1);
         if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
@@ -1298,7 +1327,7 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
         adjoint_refill_kernel<S><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(
             L, G, b, Sc.ulist, Sc.upos, st, lam_out, flags1, ext, tslots, bslot, ct);
         if (bslot)
-            body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, G, b, ct, wx, wy);
+            body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, G, b, ct, wx, wy, wz);
     }
     return cudaGetLastError();
 }
@@ -1328,7 +1357,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     double F0[3] = {0, 0, 0}, F1[3] = {0, 0, 0}, accv[3] = {0, 0, 0};
     // the swimmer free along x carries (X0, U0) as adjoint state
     const bool free_body = ctx->has_body && ctx->G.free_motion != 0;
-    const BodyAdjoint badj0{{0.0, 0.0}, {0.0, 0.0}, 0.0, 0.0,
+    const BodyAdjoint badj0{{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, 0.0, 0.0,
                             {spec->w_force[0] / T, spec->w_force[1] / T, spec->w_force[2] / T}, 0.0, {0.0, 0.0, 0.0}};
     BodyAdjoint *badj = nullptr;
     double *bslot = nullptr;
@@ -1438,7 +1467,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                                    body ? wf[p ^ 1] : nullptr, 0};
                 }
                 ADJ_CUDA(reverse_step<S>(ctx, seg + (size_t)j * state, A, wf[p], lam[p], ext[p], tslots, badj, bslot,
-                                         badj0.fw[0], badj0.fw[1], ct, cpart, cticket, split),
+                                         badj0.fw[0], badj0.fw[1], badj0.fw[2], ct, cpart, cticket, split),
                          "reverse step");
                 if (body)
                     ADJ_CUDA(cudaMemcpyAsync(adjbody + p, ctx->S.body + ctx->bcur, sizeof(DevBody),
@@ -1488,8 +1517,6 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
     if (ctx->L.gamma_mode == LBM_GAMMA_EXACT)
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: the exact stabilizer has no adjoint here");
-    if (ctx->has_body && ctx->G.free_motion && ctx->G.kind != LBM_BODY_MESH)
-        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: a free body must be the swimmer (no free sphere)");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
     if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");
