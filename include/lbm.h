@@ -344,8 +344,10 @@ LBM_API lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *laun
  * swimmer's pose through the centre of mass c(t) and its rate, and the yaw
  * rate through the moment of inertia I(theta) (omega = L / I, the initial
  * L = I(t0) omega included).
- * Storage FP64 (arithmetic in double) or FP32 (arithmetic in float);
- * 16-bit storage returns LBM_ERR_UNSUPPORTED.
+ * Storage FP64 (arithmetic in double), FP32 or 16-bit (arithmetic in float;
+ * 16-bit: the states and checkpoints in the storage type, each store's
+ * rounding passing the adjoint unchanged).  The exact stabilizer returns
+ * LBM_ERR_UNSUPPORTED.
  *
  * Memory: the forward states are kept by checkpoint-and-recompute: every
  * checkpoint_every steps (0: ceil(sqrt(horizon))) a state is kept, and each

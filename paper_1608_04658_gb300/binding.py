@@ -397,7 +397,7 @@ class Lattice:
         """Runs horizon steps and the adjoint sweep (lbm_adjoint_step).  J is
         the mean of w_force . F over the steps plus lambda_T . f at the end
         (lambda_T: device tensor (27, nz, ny, nx) of float64 for FP64 storage,
-        float32 for FP32).  Returns dict(J, dJ_dtheta, lambda_0)."""
+        float32 otherwise).  Returns dict(J, dJ_dtheta, lambda_0)."""
         torch = _torch()
         spec = AdjointSpec()
         spec.horizon = int(horizon)

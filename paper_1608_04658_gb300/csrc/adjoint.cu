@@ -1522,5 +1522,9 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");
     if (ctx->storage == LBM_FP64) return adjoint_run<double>(ctx, spec, J, dJ_dtheta);
     if (ctx->storage == LBM_FP32) return adjoint_run<float>(ctx, spec, J, dJ_dtheta);
-    return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: FP64 or FP32 storage only");
+    // 16-bit storage: states and checkpoints in the storage type, the adjoint
+    // in FP32 (the rounding of each store passes the adjoint unchanged)
+    if (ctx->storage == LBM_FP16) return adjoint_run<__half>(ctx, spec, J, dJ_dtheta);
+    if (ctx->storage == LBM_BF16) return adjoint_run<__nv_bfloat16>(ctx, spec, J, dJ_dtheta);
+    return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: unknown storage");
 }
