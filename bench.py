@@ -110,7 +110,10 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples go to LBM_CLOCKS_DIR (the system's temporary directory by default)
+        import tempfile
+        out = os.environ.get("LBM_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out, f"clocks_rank{device_index}.csv")
         self.proc = None
         self.windows = []
         self.dev = device_index
