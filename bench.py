@@ -55,7 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default=None,
-                    help="nx,ny,nz of a smaller box with the same sphere (profiling cases only)")
+                    help="nx,ny,nz of a smaller box with the same sphere (profiling cases only); "
+                         "n (or n,n,n) of the periodic Taylor-Green box (default 256)")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv"])
     ap.add_argument("--accuracy-steps", type=int, default=2000,
                     help="steps of the FP64/FP32/FP16/BF16 sphere comparison (0 to skip it)")
@@ -191,29 +192,35 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage: str):
+def ncu_traffic(storage: str, workload_name: str):
     """DRAM bytes per bulk launch from the committed ncu summary, or None when
-    the kernel sources changed since the capture."""
+    the kernel sources changed since the capture or the summary was taken on
+    another workload."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
-    sha, val = None, None
+    sha, val, name = None, None, None
     for line in open(PROFILE_SUMMARY):
         line = line.strip().strip("`")
         if line.startswith("source_sha:"):
             sha = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_workload:"):
+            name = line.split(":", 1)[1].strip()
         if line.startswith(f"traffic_bytes_per_launch[{storage}]:"):
             try:
                 val = float(line.split(":", 1)[1].strip())
             except ValueError:
                 val = None
-    return val if sha == kernel_sha() else None
+    return val if sha == kernel_sha() and name == workload_name else None
 
 
 # ----------------------------------------------------------------- workload
 def workload(shape=None, kind="sphere"):
     import synth
     if kind == "tgv":
-        wl = synth.tgv_periodic(256)
+        dims = {int(v) for v in shape.split(",")} if shape else {256}
+        if len(dims) != 1:
+            raise SystemExit("the Taylor-Green box is cubic: --shape n or n,n,n")
+        wl = synth.tgv_periodic(dims.pop())
     elif kind == "airfoil":
         wl = synth.plunging_airfoil()
     elif kind == "swimmer":
@@ -488,7 +495,7 @@ def run_ours(args):
     def roofline(st, r):
         bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
         achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
-        tr = ncu_traffic(st)
+        tr = ncu_traffic(st, wl["name"])
         return {"bound": "hbm", "kernel": "bulk_kernel", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch,

@@ -39,3 +39,17 @@ def test_dist_max_over_two_gloo_ranks():
         assert p.exitcode == 0
     got = sorted(q.get(timeout=5) for _ in range(2))
     assert got == [(0, 2.5), (1, 2.5)]
+
+
+def test_ncu_traffic_only_for_the_profiled_workload():
+    """The committed DRAM traffic per bulk launch belongs to one workload; any
+    other box (another size, the Taylor-Green box) reports none."""
+    import bench
+    sphere = bench.workload(None, "sphere")["name"]
+    for other in (bench.workload("384", "tgv")["name"], bench.workload("128,128,64", "sphere")["name"]):
+        assert bench.ncu_traffic("fp32", other) is None
+        assert bench.ncu_traffic("fp16", other) is None
+    for st in ("fp32", "fp16"):
+        v = bench.ncu_traffic(st, sphere)
+        # None once the kernel sources changed after the capture
+        assert v is None or v > 0.5 * bench.BYTES_PER_NODE[st] * 128 * 128 * 256
