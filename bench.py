@@ -10,12 +10,16 @@ reduction.  The value is GLUPS over box nodes, FP32 storage; FP16 and BF16
 storage forms are reported under "variants".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sphere|airfoil|swimmer]
+                    [--workload sphere|airfoil|swimmer|tgv] [--shape n]
 
 --workload selects another of the paper's configurations for the same
 measurement: the plunging airfoil (1024x512x64, chord 128, Sec. 4.2), the
 self-propelled anguilliform swimmer (768x256x256, L = 128, Sec. 4.3) or the
-bodiless periodic Taylor-Green box (256^3) that isolates the bulk kernel.
+bodiless periodic Taylor-Green box (256^3, or n^3 with --shape n) that
+isolates the bulk kernel.
+
+The CPU baseline is the FP64 oracle on the host: one thread on the full box,
+and under "all_cores" one independent replica per host core.
 
 With N > 1 (torchrun) every rank runs an independent replica (the path has
 no data-parallel split without a halo exchange); the value is all ranks'
@@ -453,6 +457,61 @@ def cpu_baseline(wl, nsteps=None):
             "seconds": round(t, 2)}
 
 
+def _oracle_replica(wl, nsteps, barrier, out):
+    """One independent FP64 oracle replica of the workload, in a spawned
+    process: set up, wait for the others, time its steps."""
+    import oracle
+    orc = oracle.Oracle(wl["shape"], nu=wl["nu"], faces=wl["faces"], u_face=wl.get("u_face", (0.0, 0.0, 0.0)),
+                        body=oracle_body(wl))
+    orc.init_state(*initial_flow(wl))
+    barrier.wait(timeout=900)
+    t0 = time.perf_counter()
+    orc.step(nsteps)
+    out.put((t0, time.perf_counter()))
+
+
+def cpu_baseline_all_cores(wl, nsteps=1, procs=None):
+    """The same oracle on every host core the process may use: one
+    independent single-threaded replica of the full box per core (the oracle
+    has no threads of its own), started together; the value is all replicas'
+    node updates over the span from the first start to the last finish.
+    Replicas are capped so that their buffers (about 650 bytes per node each)
+    fit in half of the free host memory."""
+    import multiprocessing as mp
+    nx, ny, nz = wl["shape"]
+    n = nx * ny * nz
+    cores = len(os.sched_getaffinity(0))
+    if procs is None:
+        free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        procs = max(1, min(cores, int(0.5 * free // (650 * n))))
+    ctx = mp.get_context("spawn")   # the parent may hold a CUDA context
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(wl, nsteps, barrier, out)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    import queue
+    spans, deadline = [], time.monotonic() + 1800
+    try:
+        while len(spans) < procs:
+            try:
+                spans.append(out.get(timeout=2))
+            except queue.Empty:
+                dead = [p.exitcode for p in ps if p.exitcode not in (None, 0)]
+                if dead or time.monotonic() > deadline:
+                    raise RuntimeError(f"oracle replicas failed (exit codes {dead})")
+    finally:
+        for p in ps:
+            p.join(timeout=60 if len(spans) == procs else 0)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=10)
+    t = max(b for _, b in spans) - min(a for a, _ in spans)
+    return {"value": procs * n * nsteps / t / 1e9, "unit": "GLUPS", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} independent replicas (one process each) of {nsteps} step(s) of the full "
+                      f"{nx}x{ny}x{nz} box, FP64, started together",
+            "seconds": round(t, 2)}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -488,6 +547,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+        cpu["all_cores"] = cpu_baseline_all_cores(wl)
     if rank != 0:
         return
     peak, peak_kind = measured_hbm_peak()

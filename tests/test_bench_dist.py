@@ -53,3 +53,14 @@ def test_ncu_traffic_only_for_the_profiled_workload():
         v = bench.ncu_traffic(st, sphere)
         # None once the kernel sources changed after the capture
         assert v is None or v > 0.5 * bench.BYTES_PER_NODE[st] * 128 * 128 * 256
+
+
+def test_all_cores_oracle_baseline_runs_replicas(orc):
+    """The all-cores CPU baseline starts independent oracle replicas in
+    spawned processes and reports their aggregate node updates."""
+    import bench
+    wl = bench.workload("16", "tgv")
+    r = bench.cpu_baseline_all_cores(wl, nsteps=2, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "GLUPS"
+    assert r["value"] > 0 and r["seconds"] > 0
+    assert "2 independent replicas" in r["sample"]
