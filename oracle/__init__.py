@@ -13,7 +13,7 @@ index i = 9(cx+1) + 3(cy+1) + (cz+1).
 
 Parity status per function (pins live in tests/test_oracle_*.py):
   feq, kbc_split, collide (all modes), gamma_exact, grad, stream/box faces,
-  refill moments, momentum exchange, Couette with Grad walls, shear-wave and
+  refill moments, momentum exchange force and torque, Couette with Grad walls, shear-wave and
   Taylor-Green viscosity: pinned.
   Sphere refill density average and the sphere's Euler update beyond one step:
   pinned only by invariants (moments of the refilled node, mass accounting).

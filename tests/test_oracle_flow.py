@@ -162,6 +162,49 @@ def test_momentum_exchange_balances_fluid_momentum(orc):
         assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
 
 
+def _angular_momentum(orc, f, fluid, X):
+    """Fluid angular momentum about X: sum over fluid nodes of r x j with r
+    the minimum-image offset of the node from X and j = sum_i c_i f_i."""
+    c, _ = orc.lattice()
+    nz, ny, nx = fluid.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.stack([x - X[0], y - X[1], z - X[2]], axis=-1)
+    n = np.array([nx, ny, nz], dtype=float)
+    r = (r + n / 2) % n - n / 2
+    j = np.einsum("ia,izyx->zyxa", c, f)
+    return np.cross(r[fluid], j[fluid]).sum(0)
+
+
+def test_momentum_exchange_torque_balances_fluid_angular_momentum(orc):
+    """Held sphere: the pull step carries each population along its own
+    velocity, so the moment r x c_i f_i of a population does not change when
+    it streams, and the collision keeps j at every node.  Away from the body
+    the fluid's angular momentum about the centre is therefore conserved, and
+    its change in one step is exactly minus the momentum-exchange torque
+    (with the wall at rest the arm x_w - X and x_b - X give the same moment,
+    as x_w - x_b is parallel to c_i).  The disturbance starts within 6 nodes
+    of the centre and grows by one node per step, so the seam of the periodic
+    box (10 nodes out) stays at rest equilibrium and adds nothing."""
+    shape = (20, 20, 20)
+    X = (10.3, 9.8, 10.1)
+    o = orc.Oracle(shape, nu=0.05, body=orc.sphere_body(X, 3.1))
+    rho, u, xi = synth.parity_fields(shape, 7, umax=0.08)
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape[::-1]], indexing="ij")
+    d = np.sqrt((x - X[0]) ** 2 + (y - X[1]) ** 2 + (z - X[2]) ** 2)
+    w = np.clip(6.0 - d, 0.0, 1.0)  # 1 within 5 nodes, exactly 0 beyond 6
+    o.init_state(1.0 + w * (rho - 1.0), w[..., None] * u, w[None] * xi, 1e-3)
+    fluid = o.solid() == 0
+    L0 = _angular_momentum(orc, o.get_f(), fluid, X)
+    for _ in range(3):
+        o.step(1)
+        L1 = _angular_momentum(orc, o.get_f(), fluid, X)
+        M = np.array(o.body.M)
+        assert np.linalg.norm(M) > 0.02
+        # rounding of the sums over ~10^4 nodes; a wrong arm or sign is O(|M|)
+        assert np.abs(L1 - L0 + M).max() < 1e-11 * np.linalg.norm(M) + 1e-12
+        L0 = L1
+
+
 def test_stationary_wall_force_is_zero_at_rest(orc):
     """Fluid at rest at uniform density around a fixed sphere: no force."""
     shape = (12, 12, 12)

@@ -181,6 +181,60 @@ def test_swimmer_momentum_exchange_balances_fluid_momentum(orc):
         assert o.counters()["error"] == 0
 
 
+def _moment_of_fluid(orc, f, fluid, X):
+    """sum over fluid nodes of (x - X) x j(x), j = sum_i c_i f_i, with the
+    node offsets taken as they are (no wrap): the disturbance never reaches
+    the box faces in the tests below."""
+    c, _ = orc.lattice()
+    nz, ny, nx = fluid.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.stack([x - X[0], y - X[1], z - X[2]], axis=-1)
+    j = np.einsum("ia,izyx->zyxa", c, f)
+    return np.cross(r[fluid], j[fluid]).sum(0)
+
+
+@pytest.mark.parametrize("free", [False, 4])
+def test_swimmer_torque_balances_fluid_angular_momentum(orc, free):
+    """Straight mesh at rest, held with the head as reference point, or free
+    in yaw about its centre of mass with a mass so large that it does not
+    turn: streaming keeps each population's moment about any point and the
+    collision keeps j, so the change of the fluid's angular momentum about the
+    reference point in one step is exactly minus the momentum-exchange torque.
+    The disturbance lies within 5 nodes of the body and spreads one node per
+    step, so the wrap at the box faces only moves rest-equilibrium
+    populations, whose moments cancel."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    shape = (48, 24, 24)
+    # the head (held) or the centre of mass (free in yaw)
+    X = np.array([24.137 if free else 12.137, 12.371, 12.293])
+    body = _body(orc, 24.0, 24, 12, X, free=free)
+    if free:
+        body.mass = 1e30
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    Xref = np.array(o.body.X)
+    assert np.array_equal(Xref, X)
+    fluid = o.solid() == 0
+    d = ndimage.distance_transform_edt(fluid)  # distance to the nearest solid node
+    w = np.clip(5.0 - d, 0.0, 1.0)
+    sol = np.argwhere(~fluid)
+    for a, n in enumerate(shape[::-1]):
+        # 5 nodes of disturbance, 2 steps of spread, and 1 node to spare
+        assert sol[:, a].min() >= 8 and sol[:, a].max() <= n - 9
+    rho, u, xi = synth.parity_fields(shape, 11, umax=0.08)
+    o.init_state(1.0 + w * (rho - 1.0), w[..., None] * u, w[None] * xi, 1e-3)
+    L0 = _moment_of_fluid(orc, o.get_f(), fluid, Xref)
+    for _ in range(2):
+        o.step(1)
+        assert np.array_equal(np.array(o.body.X), Xref)
+        L1 = _moment_of_fluid(orc, o.get_f(), fluid, Xref)
+        M = np.array(o.body.M)
+        assert np.linalg.norm(M) > 0.05
+        # rounding of the sums over ~10^4 nodes; a wrong arm or sign is O(|M|)
+        assert np.abs(L1 - L0 + M).max() < 1e-11 * np.linalg.norm(M) + 1e-12
+        assert o.counters()["error"] == 0
+        L0 = L1
+
+
 def test_swimmer_euler_update_along_the_swimming_axis(orc):
     """Newton's equation along x by explicit Euler (Sec. 4.3 with Sec. 4.1's
     scheme): X0 += U0, U0 += F0/m; the lateral and vertical position of the
