@@ -49,6 +49,15 @@ def test_struct_layout_matches_header(cls, cname):
         assert getattr(cls, f).offset == off, f
 
 
+def test_force_record_layout_matches_the_binding():
+    """The binding reads force records as rows of RECORD_DOUBLES doubles in a
+    ring of RECORD_DEPTH: F at 0..2, M at 3..5, the step time at 6."""
+    got = _c_layout("lbm_force_record", ["F", "M", "t", "status", "reserved"])
+    assert got == [8 * binding.RECORD_DOUBLES, 0, 24, 48, 56, 60]
+    text = open(binding.HEADER).read()
+    assert f"#define LBM_RECORD_DEPTH {binding.RECORD_DEPTH}" in text
+
+
 def test_invalid_arguments_are_rejected_without_a_gpu(L):
     ctx = C.c_void_p()
     dummy = C.c_void_p(16)
