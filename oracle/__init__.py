@@ -11,6 +11,9 @@ without fast-math or FMA contraction); this module is ctypes marshalling.
 Layout of a population array: numpy ``(27, nz, ny, nx)`` float64, direction
 index i = 9(cx+1) + 3(cy+1) + (cz+1).
 
+``slab.py`` runs the same oracle split into z slabs over CPU ranks (the
+decomposition of one box over several devices, tests/test_oracle_slab.py).
+
 Parity status per function (pins live in tests/test_oracle_*.py):
   feq, kbc_split, collide (all modes), gamma_exact, grad, stream/box faces,
   refill moments, momentum exchange force and torque, Couette with Grad walls, shear-wave and
@@ -109,6 +112,8 @@ def lib():
             L.orc_get_solid.argtypes = [C.c_void_p, C.c_void_p]
             L.orc_get_body.argtypes = [C.c_void_p, C.POINTER(Body)]
             L.orc_set_body.argtypes = [C.c_void_p, C.POINTER(Body)]
+            L.orc_set_owned_z.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_set_owned_z.restype = None
             L.orc_counter.argtypes = [C.c_void_p, C.c_int]
             L.orc_counter.restype = C.c_long
             L.orc_init_state.argtypes = [C.c_void_p, _D, _D, C.c_void_p, C.c_double]
@@ -259,6 +264,11 @@ class Oracle:
     @body.setter
     def body(self, b: Body):
         lib().orc_set_body(self._ctx, C.byref(b))
+
+    def set_owned_z(self, z_lo: int, z_hi: int):
+        """Later steps sum the force and torque over the boundary nodes of the
+        z layers [z_lo, z_hi) only (one slab of a decomposed box)."""
+        lib().orc_set_owned_z(self._ctx, int(z_lo), int(z_hi))
 
     def counters(self):
         L = lib()

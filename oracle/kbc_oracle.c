@@ -322,6 +322,7 @@ typedef struct {
     double *vpos, *vvel;  /* mesh vertex positions and velocities at the current pose */
     double box_lo[3], box_hi[3]; /* bounding box of the mesh vertices */
     int error;            /* 1: the mesh left the box */
+    int own_zlo, own_zhi; /* z layers whose boundary links enter F and M (the whole box by default) */
 } orc_ctx;
 
 static long nid(const orc_ctx *c, int x, int y, int z)
@@ -899,6 +900,8 @@ orc_ctx *orc_create(const orc_params *p, const orc_body *b)
     c->p = *p;
     c->b = *b;
     c->N = (long)p->nx * p->ny * p->nz;
+    c->own_zlo = 0;
+    c->own_zhi = p->nz;
     c->fa = (double *)calloc((size_t)Q * c->N, sizeof(double));
     c->solid0 = (uint8_t *)calloc((size_t)c->N, 1);
     c->solid1 = (uint8_t *)calloc((size_t)c->N, 1);
@@ -952,6 +955,15 @@ void orc_mesh_mass(const orc_ctx *c, double t, double *out)
 double orc_mesh_link(const orc_ctx *c, int x, int y, int z, int i, double *uw)
 {
     return mesh_link(c, x, y, z, C[i], uw);
+}
+
+/* Restricts the force and torque sums of later steps to the boundary nodes of
+ * the z layers [z_lo, z_hi) (one slab of a decomposed box); every node is
+ * still updated. */
+void orc_set_owned_z(orc_ctx *c, int z_lo, int z_hi)
+{
+    c->own_zlo = z_lo;
+    c->own_zhi = z_hi;
 }
 
 long orc_counter(const orc_ctx *c, int which)
@@ -1054,6 +1066,7 @@ int orc_step(orc_ctx *c, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         step_prepare(c);
         double F[3] = {0, 0, 0}, M[3] = {0, 0, 0}, out[Q];
+        double Fx[3] = {0, 0, 0}, Mx[3] = {0, 0, 0}; /* sums outside the owned layers, dropped */
         for (int z = 0; z < p->nz; ++z)
             for (int y = 0; y < p->ny; ++y)
                 for (int x = 0; x < p->nx; ++x) {
@@ -1062,7 +1075,8 @@ int orc_step(orc_ctx *c, int nsteps)
                         for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = c->fa[i * c->N + n];
                         continue;
                     }
-                    node_update(c, x, y, z, out, F, M);
+                    const int own = z >= c->own_zlo && z < c->own_zhi;
+                    node_update(c, x, y, z, out, own ? F : Fx, own ? M : Mx);
                     for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = out[i];
                 }
         double *t = c->fa; c->fa = c->fb; c->fb = t;
