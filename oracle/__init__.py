@@ -114,6 +114,8 @@ def lib():
             L.orc_set_body.argtypes = [C.c_void_p, C.POINTER(Body)]
             L.orc_set_owned_z.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_set_owned_z.restype = None
+            L.orc_set_z_frame.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_set_z_frame.restype = None
             L.orc_counter.argtypes = [C.c_void_p, C.c_int]
             L.orc_counter.restype = C.c_long
             L.orc_init_state.argtypes = [C.c_void_p, _D, _D, C.c_void_p, C.c_double]
@@ -269,6 +271,12 @@ class Oracle:
         """Later steps sum the force and torque over the boundary nodes of the
         z layers [z_lo, z_hi) only (one slab of a decomposed box)."""
         lib().orc_set_owned_z(self._ctx, int(z_lo), int(z_hi))
+
+    def set_z_frame(self, origin: int, period: int):
+        """Treats the box as a slab of a box periodic in z with `period`
+        layers, layer k at z = (k + origin) mod period, for the sphere's
+        geometry and centre wrap (recomputes the current solid marks)."""
+        lib().orc_set_z_frame(self._ctx, int(origin), int(period))
 
     def counters(self):
         L = lib()

@@ -323,6 +323,7 @@ typedef struct {
     double box_lo[3], box_hi[3]; /* bounding box of the mesh vertices */
     int error;            /* 1: the mesh left the box */
     int own_zlo, own_zhi; /* z layers whose boundary links enter F and M (the whole box by default) */
+    int zf_origin, zf_period; /* slab frame: layer k sits at z = (k + origin) mod period (period 0: off) */
 } orc_ctx;
 
 static long nid(const orc_ctx *c, int x, int y, int z)
@@ -339,9 +340,17 @@ static void sphere_offset(const orc_ctx *c, double x, double y, double z, double
     const orc_body *b = &c->b;
     double p[3] = {x, y, z};
     int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    int zper = c->p.face[4] == FACE_PERIODIC;
+    if (c->zf_period > 0) {
+        /* a slab of a larger box periodic in z: the layer's position there */
+        const long k = ((long)z + c->zf_origin) % c->zf_period;
+        p[2] = (double)(k < 0 ? k + c->zf_period : k);
+        n[2] = c->zf_period;
+        zper = 1;
+    }
     for (int a = 0; a < 3; ++a) {
         d[a] = p[a] - b->X[a];
-        if (c->p.face[2 * a] == FACE_PERIODIC) {
+        if (a == 2 ? zper : c->p.face[2 * a] == FACE_PERIODIC) {
             double h = 0.5 * n[a];
             if (d[a] > h) d[a] = d[a] - n[a];
             else if (d[a] < -h) d[a] = d[a] + n[a];
@@ -966,6 +975,21 @@ void orc_set_owned_z(orc_ctx *c, int z_lo, int z_hi)
     c->own_zhi = z_hi;
 }
 
+/* Places the box as a slab of a box periodic in z with `period` layers: layer
+ * k sits at z = (k + origin) mod period for the sphere's geometry, nearest
+ * image and centre wrap, so a slab sees the sphere exactly as the whole box
+ * does.  Recomputes the solid marks of the current pose. */
+void orc_set_z_frame(orc_ctx *c, int origin, int period)
+{
+    c->zf_origin = origin;
+    c->zf_period = period;
+    const orc_params *p = &c->p;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                c->solid0[nid(c, x, y, z)] = (uint8_t)inside_body(c, x, y, z);
+}
+
 long orc_counter(const orc_ctx *c, int which)
 {
     return which == 0 ? c->step : which == 1 ? c->n_boundary : which == 2 ? c->n_links
@@ -1025,11 +1049,16 @@ static void body_update(orc_ctx *c)
     const double inv_m = 1.0 / b->mass;
     const double buoy = 1.0 - 1.0 / b->rho_ratio;
     int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    int per[3] = {c->p.face[0] == FACE_PERIODIC, c->p.face[2] == FACE_PERIODIC, c->p.face[4] == FACE_PERIODIC};
+    if (c->zf_period > 0) {
+        n[2] = c->zf_period;
+        per[2] = 1;
+    }
     for (int a = 0; a < 3; ++a) {
         double acc = b->F[a] * inv_m + buoy * b->g[a];
         b->X[a] = b->X[a] + b->U[a];
         b->U[a] = b->U[a] + acc;
-        if (c->p.face[2 * a] == FACE_PERIODIC) {
+        if (per[a]) {
             if (b->X[a] >= n[a]) b->X[a] = b->X[a] - n[a];
             else if (b->X[a] < 0.0) b->X[a] = b->X[a] + n[a];
         }

@@ -8,23 +8,25 @@ TEST INFRASTRUCTURE ONLY: the tests are its only callers.
 
 Each rank owns the z layers [z0, z1) of a box periodic in z and keeps two
 halo layers on each side: a local oracle box of (z1 - z0) + 4 layers whose
-own z faces are walls, which no owned node reads.  Before every step the
-ranks swap edge layers, all 27 post-collision populations per node: the
-first two owned layers go to the rank below (its upper halo) and the last two
-to the rank above (its lower halo).  One layer feeds the pulls of the owned
-edge nodes, the Grad boundary's neighbour velocities and finite-difference
-gradient, and the refill's neighbour densities; the second makes the refill
-of a node in the first halo layer, which owned nodes then pull from, the one
-of the undivided box.  Owned nodes therefore end each step bitwise equal to
-the single-rank oracle.  The body is replicated on every rank; its force and
-torque are the owned-layer sums gathered from all ranks and added in rank
-order, the same on every rank.
-
-Supported body: a sphere moving with a fixed velocity in x and y (free with a
-mass large enough that the force leaves its velocity unchanged), whose centre
-z is a dyadic number: it is shifted by whole layers into each local frame,
-which is exact only then, and a free body's Euler update would need the
-gathered force inside the oracle's own step.
+own z faces are walls, which no owned node reads, placed as a slab of the
+whole box (`Oracle.set_z_frame`) so that the sphere's geometry, nearest
+image and centre wrap are computed from the same numbers as in the whole
+box.  Before every step the ranks swap edge layers, all 27 post-collision
+populations per node: the first two owned layers go to the rank below (its
+upper halo) and the last two to the rank above (its lower halo).  One layer
+feeds the pulls of the owned edge nodes, the Grad boundary's neighbour
+velocities and finite-difference gradient, and the refill's neighbour
+densities; the second makes the refill of a node in the first halo layer,
+which owned nodes then pull from, the one of the undivided box.  A boundary
+link belongs to the rank that owns its fluid node: each rank sums the force
+and torque over its own layers, and the ranks gather the six sums and add
+them in rank order, so every rank holds the same bits.  The body is
+replicated: each rank hands the gathered force to its own copy before the
+next step's Euler update, so all copies move alike.  Owned nodes end each
+step bitwise equal to the undivided oracle while the body's velocity does
+not depend on the force (a fixed velocity); a free body differs from the
+undivided run by the order in which the link forces are added.  The sphere
+is the supported body.
 """
 from __future__ import annotations
 
@@ -77,35 +79,31 @@ def _fixed_order_sum(v: np.ndarray, world: int) -> np.ndarray:
     return tot.numpy()
 
 
-def decomposed_run(shape, nu, faces, X, R, U, fields, amp, steps, world=None, rank=None, halo=HALO):
-    """Runs `steps` steps of the sphere problem on this rank's slab.
+def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, rank=None, halo=HALO):
+    """Runs `steps` steps of a sphere problem on this rank's slab.
 
-    shape (nx, ny, nz) with faces periodic in z; X, R, U the sphere (U[2] = 0,
-    X[2] dyadic); fields = (rho, u, xi) of the whole box as synth builds them.
-    Returns (z0, z1, f, forces): f (27, z1 - z0, ny, nx) the owned
-    post-collision populations, forces the per-step (F, M) summed over all
-    ranks, shape (steps, 6).  halo: layers kept on each side (two are needed; one, for
-    tests, leaves the refill of the first halo layer short of neighbours)."""
+    shape (nx, ny, nz) with faces periodic in z; sphere = keyword arguments of
+    `oracle.sphere_body`; fields = (rho, u, xi) of the whole box as synth
+    builds them.  Returns (z0, z1, f, forces, body): f (27, z1 - z0, ny, nx)
+    the owned post-collision populations, forces the per-step (F, M) summed
+    over all ranks, shape (steps, 6), body the final (X, U).  halo: layers
+    kept on each side (two are needed; one, for tests, leaves the refill of
+    the first halo layer short of neighbours)."""
     if world is None:
         import torch.distributed as dist
         world, rank = dist.get_world_size(), dist.get_rank()
     nx, ny, nz = shape
     if faces[4] != FACE_PERIODIC or faces[5] != FACE_PERIODIC:
         raise ValueError("the split axis z must be periodic")
-    if U[2] != 0.0 or float(X[2]) * 1024.0 != int(float(X[2]) * 1024.0):
-        raise ValueError("the sphere must move in x and y only and have a dyadic centre z")
     z0, z1 = slab_bounds(nz, world, rank)
     if z1 - z0 < halo:
         raise ValueError("slabs thinner than the halo")
     nloc = z1 - z0 + 2 * halo
     off = z0 - halo  # global z of local layer 0
     zidx = [(off + k) % nz for k in range(nloc)]
-    # the image of the centre nearest the slab, in the local frame
-    zc = 0.5 * (z0 + z1 - 1)
-    xz = float(X[2]) + nz * round((zc - float(X[2])) / nz) - off
-    body = sphere_body((X[0], X[1], xz), R, U=U, free=True, g=(0.0, 0.0, 0.0), mass=1e30)
     local_faces = (faces[0], faces[1], faces[2], faces[3], FACE_WALL, FACE_WALL)
-    o = Oracle((nx, ny, nloc), nu=nu, faces=local_faces, body=body)
+    o = Oracle((nx, ny, nloc), nu=nu, faces=local_faces, body=sphere_body(**sphere))
+    o.set_z_frame(off, nz)
     rho, u, xi = fields
     o.init_state(rho[zidx], u[zidx], xi[:, zidx] if xi is not None else None, amp)
     o.set_owned_z(halo, nloc - halo)
@@ -116,5 +114,10 @@ def decomposed_run(shape, nu, faces, X, R, U, fields, amp, steps, world=None, ra
         o.set_f(f)
         o.step(1)
         b = o.body
-        forces.append(_fixed_order_sum(np.array(list(b.F) + list(b.M)), world))
-    return z0, z1, o.get_f()[:, halo:nloc - halo].copy(), np.array(forces)
+        fm = _fixed_order_sum(np.array(list(b.F) + list(b.M)), world)
+        for a in range(3):
+            b.F[a], b.M[a] = fm[a], fm[3 + a]
+        o.body = b  # the gathered force drives the next Euler update
+        forces.append(fm)
+    b = o.body
+    return z0, z1, o.get_f()[:, halo:nloc - halo].copy(), np.array(forces), (list(b.X), list(b.U))

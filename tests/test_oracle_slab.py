@@ -14,9 +14,18 @@ import synth
 
 NU = 0.05
 FACES = (1, 1, 0, 0, 0, 0)  # walls in x, periodic y and z (the split axis)
-R = 3.2
-U = (0.35, -0.15, 0.0)
 AMP = 1e-3
+
+
+def _carried(X):
+    """Sphere carried at a fixed velocity (free, with a mass so large that
+    the force leaves its velocity unchanged), moving across z layers."""
+    return dict(X=X, R=3.2, U=(0.35, -0.15, 0.3), free=True, g=(0.0, 0.0, 0.0), mass=1e30)
+
+
+def _sedimenting(X):
+    """Free sphere, 1.5 times the fluid density, falling along -z."""
+    return dict(X=X, R=3.2, U=(0.02, 0.0, -0.25), free=True, rho_ratio=1.5, g=(0.0, 0.0, -0.01))
 
 
 def _free_port() -> int:
@@ -25,24 +34,24 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, shape, X, steps, halo, q):
+def _rank(rank, world, port, shape, sphere, steps, halo, q):
     os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
 
     from oracle.slab import decomposed_run
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        out = decomposed_run(shape, NU, FACES, X, R, U, synth.parity_fields(shape, 4), AMP, steps, halo=halo)
+        out = decomposed_run(shape, NU, FACES, sphere, synth.parity_fields(shape, 4), AMP, steps, halo=halo)
         q.put((rank, out))
     finally:
         dist.destroy_process_group()
 
 
-def _decomposed(world, shape, X, steps, halo=2):
+def _decomposed(world, shape, sphere, steps, halo=2):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, shape, X, steps, halo, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, shape, sphere, steps, halo, q)) for r in range(world)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=300) for _ in procs)
@@ -52,42 +61,75 @@ def _decomposed(world, shape, X, steps, halo=2):
     return [got[r] for r in range(world)]
 
 
-def _undivided(orc, shape, X, steps):
-    o = orc.Oracle(shape, nu=NU, faces=FACES, body=orc.sphere_body(X, R, U=U, free=True, g=(0, 0, 0), mass=1e30))
+def _undivided(orc, shape, sphere, steps):
+    o = orc.Oracle(shape, nu=NU, faces=FACES, body=orc.sphere_body(**sphere))
     o.init_state(*synth.parity_fields(shape, 4), AMP)
     fm = []
+    cut_solid = []
     for _ in range(steps):
         o.step(1)
         fm.append(list(o.body.F) + list(o.body.M))
-    return o, o.get_f(), np.array(fm)
+        cut_solid.append(o.solid())
+    return o, o.get_f(), np.array(fm), cut_solid
 
 
-@pytest.mark.parametrize("world,shape,X", [(2, (14, 12, 20), (6.3, 5.7, 10.375)),
-                                           (3, (14, 12, 21), (6.3, 5.7, 13.875))])
+def _straddles(solids, cuts):
+    """The body has solid nodes on both sides of some cut at some step, so
+    its links and refills reach both ranks there."""
+    return any(s[z - 1].any() and s[z].any() for s in solids for z in cuts)
+
+
+@pytest.mark.parametrize("world,shape,X", [(2, (14, 12, 20), (6.3, 5.7, 8.9)),
+                                           (3, (14, 12, 21), (6.3, 5.7, 12.6))])
 def test_slab_ranks_reproduce_the_undivided_oracle(orc, world, shape, X):
+    """Sphere carried across the cut at a fixed velocity: owned populations
+    bitwise equal, force and torque equal up to the order of addition."""
     pytest.importorskip("torch.distributed")
-    steps = 4
-    o, f, fm = _undivided(orc, shape, X, steps)
+    steps = 5
+    sphere = _carried(X)
+    o, f, fm, solids = _undivided(orc, shape, sphere, steps)
     c = o.counters()
     assert c["refill"] > 0 and c["boundary"] > 0
-    parts = _decomposed(world, shape, X, steps)
-    cuts = [z0 for z0, _, _, _ in parts[1:]]
-    solid = o.solid()
-    # the body's links and refills reach both sides of a cut
-    assert any(solid[z - 1].any() and solid[z].any() for z in cuts)
-    for z0, z1, fr, forces in parts:
+    parts = _decomposed(world, shape, sphere, steps)
+    assert _straddles(solids, [p[0] for p in parts[1:]])
+    for z0, z1, fr, forces, body in parts:
         assert np.array_equal(fr, f[:, z0:z1])
-        # the same gathered sums on every rank
+        # the same gathered sums and the same body on every rank
         assert np.array_equal(forces, parts[0][3])
-    scale = np.abs(fm).max()
-    assert np.abs(parts[0][3] - fm).max() <= 1e-13 * scale
+        assert body == parts[0][4]
+    assert np.abs(parts[0][3] - fm).max() <= 1e-13 * np.abs(fm).max()
+    assert parts[0][4] == (list(o.body.X), list(o.body.U))
+
+
+def test_slab_ranks_move_a_free_sphere_with_the_gathered_force(orc):
+    """Free sedimenting sphere crossing the cut: every rank's copy of the body
+    takes the Euler update of the gathered force, so all copies agree bit for
+    bit, and the run differs from the undivided oracle only through the order
+    in which the link forces are added."""
+    pytest.importorskip("torch.distributed")
+    shape, steps = (14, 12, 20), 6
+    sphere = _sedimenting((6.3, 5.7, 11.4))
+    o, f, fm, solids = _undivided(orc, shape, sphere, steps)
+    parts = _decomposed(2, shape, sphere, steps)
+    assert _straddles(solids, [parts[1][0]])
+    X, U = parts[0][4]
+    assert all(p[4] == parts[0][4] for p in parts)
+    assert np.abs(np.array(U) - np.array(o.body.U)).max() < 1e-15
+    assert np.abs(np.array(X) - np.array(o.body.X)).max() < 1e-13
+    # the body really moved with the force: U differs from its force-free value
+    U_free = np.array(sphere["U"]) + steps * (1 - 1 / 1.5) * np.array(sphere["g"])
+    assert np.abs(np.array(U) - U_free).max() > 1e-4
+    for z0, z1, fr, _, _ in parts:
+        assert np.abs(fr - f[:, z0:z1]).max() < 1e-13
+    assert np.abs(parts[0][3] - fm).max() <= 1e-12 * np.abs(fm).max()
 
 
 def test_one_halo_layer_is_not_enough_once_a_halo_node_is_refilled(orc):
     """With one halo layer a refilled node in it averages fewer neighbours
     than in the undivided box, and an owned node pulls the difference."""
     pytest.importorskip("torch.distributed")
-    shape, X, steps = (14, 12, 20), (6.3, 5.7, 10.375), 4
-    _, f, _ = _undivided(orc, shape, X, steps)
-    parts = _decomposed(2, shape, X, steps, halo=1)
-    assert any(not np.array_equal(fr, f[:, z0:z1]) for z0, z1, fr, _ in parts)
+    shape, steps = (14, 12, 20), 5
+    sphere = _carried((6.3, 5.7, 8.9))
+    _, f, _, _ = _undivided(orc, shape, sphere, steps)
+    parts = _decomposed(2, shape, sphere, steps, halo=1)
+    assert any(not np.array_equal(fr, f[:, z0:z1]) for z0, z1, fr, _, _ in parts)
