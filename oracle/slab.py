@@ -79,7 +79,8 @@ def _fixed_order_sum(v: np.ndarray, world: int) -> np.ndarray:
     return tot.numpy()
 
 
-def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, rank=None, halo=HALO):
+def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, rank=None, halo=HALO,
+                   after_step=None):
     """Runs `steps` steps of a sphere problem on this rank's slab.
 
     shape (nx, ny, nz) with faces periodic in z; sphere = keyword arguments of
@@ -88,7 +89,8 @@ def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, ran
     the owned post-collision populations, forces the per-step (F, M) summed
     over all ranks, shape (steps, 6), body the final (X, U).  halo: layers
     kept on each side (two are needed; one, for tests, leaves the refill of
-    the first halo layer short of neighbours)."""
+    the first halo layer short of neighbours).  after_step(k), if given, is
+    called after step k (tests use it to end a rank between steps)."""
     if world is None:
         import torch.distributed as dist
         world, rank = dist.get_world_size(), dist.get_rank()
@@ -108,7 +110,7 @@ def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, ran
     o.init_state(rho[zidx], u[zidx], xi[:, zidx] if xi is not None else None, amp)
     o.set_owned_z(halo, nloc - halo)
     forces = []
-    for _ in range(steps):
+    for k in range(steps):
         f = o.get_f()
         _exchange(f, world, rank, halo)
         o.set_f(f)
@@ -119,5 +121,7 @@ def decomposed_run(shape, nu, faces, sphere, fields, amp, steps, world=None, ran
             b.F[a], b.M[a] = fm[a], fm[3 + a]
         o.body = b  # the gathered force drives the next Euler update
         forces.append(fm)
+        if after_step is not None:
+            after_step(k)
     b = o.body
     return z0, z1, o.get_f()[:, halo:nloc - halo].copy(), np.array(forces), (list(b.X), list(b.U))

@@ -133,3 +133,45 @@ def test_one_halo_layer_is_not_enough_once_a_halo_node_is_refilled(orc):
     _, f, _, _ = _undivided(orc, shape, sphere, steps)
     parts = _decomposed(2, shape, sphere, steps, halo=1)
     assert any(not np.array_equal(fr, f[:, z0:z1]) for z0, z1, fr, _, _ in parts)
+
+
+def _rank_that_dies(rank, port, shape, q):
+    """Rank 1 ends its process after step 2, between steps; rank 0 reports
+    what its next exchange raises."""
+    import datetime
+
+    os.environ.update(RANK=str(rank), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+
+    from oracle.slab import decomposed_run
+    dist.init_process_group("gloo", rank=rank, world_size=2, timeout=datetime.timedelta(seconds=20))
+
+    def die(k):
+        if rank == 1 and k == 2:
+            os._exit(3)
+
+    try:
+        decomposed_run(shape, NU, FACES, _carried((6.3, 5.7, 8.9)), synth.parity_fields(shape, 4), AMP, 6,
+                       after_step=die)
+        q.put((rank, "finished"))
+    except RuntimeError as e:
+        q.put((rank, "error: " + str(e)[:200]))
+
+
+def test_a_rank_that_leaves_makes_its_peer_fail_not_hang(orc):
+    """A rank that exits between steps: its peer's next halo exchange ends
+    with an error (closed connection or the process group's timeout) instead
+    of waiting forever; the failure is made on the host, no device involved."""
+    pytest.importorskip("torch.distributed")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_that_dies, args=(r, port, (14, 12, 20), q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, msg = q.get(timeout=120)
+    assert rank == 0 and msg.startswith("error"), msg
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[1].exitcode == 3
+    assert procs[0].exitcode == 0
