@@ -120,6 +120,33 @@ def test_stationary_sphere(storage):
     assert b["n_links"] == orc.counters()["links"] // 10
 
 
+def test_monitor_records_carry_each_steps_force_and_sums(tmp_path):
+    """The run monitor's JSON lines, every 2 steps of a fixed sphere: each
+    record's force and torque are the oracle's for that step, its mass and
+    momentum the oracle's sums over fluid nodes."""
+    import json
+
+    from paper_1608_04658_gb300 import monitor
+    shape = (24, 20, 22)
+    rho, u, xi = synth.parity_fields(shape, 4)
+    fields = (rho, 0.3 * u + np.array([0.03, 0.01, -0.02]), xi, 1e-3)
+    import paper_1608_04658_gb300 as lbm
+    geom = lbm.sphere((11.37, 9.61, 10.83), 4.3)
+    lat, orc = run_pair(shape, 0.02, "fp32", fields, 0, geom=geom)
+    recs = monitor.run_logged(lat, 6, 2, tmp_path / "run.jsonl")
+    assert [json.loads(line) for line in (tmp_path / "run.jsonl").read_text().splitlines()] == recs
+    assert [r["step"] for r in recs] == [2, 4, 6]
+    for r in recs:
+        orc.step(2)
+        Fo, Mo = np.array(orc.body.F), np.array(orc.body.M)
+        assert np.abs(np.array(r["F"]) - Fo).max() <= 1e-5 * np.abs(Fo).max()
+        assert np.abs(np.array(r["M"]) - Mo).max() <= 1e-5 * np.abs(Mo).max() + 1e-12
+        T = orc.totals()
+        assert abs(r["mass"] - T[0]) <= 1e-6 * T[0]
+        assert np.abs(np.array(r["momentum"]) - T[1:4]).max() <= 1e-6 * T[0]
+        assert r["status"] == 0 and r["n_links"] > 0
+
+
 @pytest.mark.parametrize("storage", STORAGES)
 def test_moving_free_sphere_with_refill(storage):
     """Free sphere between no-slip x/y walls, periodic z, under gravity: body
