@@ -555,10 +555,11 @@ def run_ours(args):
         return
     peak, peak_kind = measured_hbm_peak()
 
-    def roofline(st, r):
+    def roofline(st, r, captured=True):
         bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
         achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
-        tr = ncu_traffic(st, wl["name"])
+        # the committed counters are those of the analytic-stabilizer kernel
+        tr = ncu_traffic(st, wl["name"]) if captured else None
         return {"bound": "hbm", "kernel": "bulk_kernel", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch,
@@ -591,7 +592,8 @@ def run_ours(args):
                           "ms_per_step": round(r["ms"] / args.steps, 5),
                           "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st.split("_")[0]]
                                                                 / world / peak, 2),
-                          "roofline": roofline(st.split("_")[0], r), "gpu_launches": r["launches"]}
+                          "roofline": roofline(st.split("_")[0], r, captured=st in BYTES_PER_NODE),
+                          "gpu_launches": r["launches"]}
                      for st, r in variants.items()},
     }
     print(json.dumps(line))
