@@ -77,6 +77,8 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
     assert not ctx.value
     p = lbm.make_params((2048, 2048, 1024), 0.1)  # N >= 2^31
     assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
+    p = lbm.make_params((400, 400, 500), 0.1)  # 27 N = 2.16e9: plane offsets beyond 32 bits
+    assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
     assert L.lbm_step(None, 1) == binding.LBM_ERR_ARG
     assert L.lbm_last_error(None) == b"null context"
 
