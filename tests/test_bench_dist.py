@@ -64,3 +64,33 @@ def test_all_cores_oracle_baseline_runs_replicas(orc):
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "GLUPS"
     assert r["value"] > 0 and r["seconds"] > 0
     assert "2 independent replicas" in r["sample"]
+
+
+def _bench(args, env_extra):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, "bench.py", *args], cwd=root, env=env, capture_output=True, text=True,
+                          timeout=600)
+
+
+def test_reference_arm_prints_one_line_on_rank_zero_only(orc):
+    """The reference arm (the FP64 oracle on host cores): rank 0 prints one
+    JSON line with the contract's keys; another rank prints nothing and exits
+    0 without work."""
+    import json
+    r1 = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r1.returncode == 0 and r1.stdout.strip() == ""
+    r0 = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "0", "WORLD_SIZE": "1"})
+    assert r0.returncode == 0, r0.stderr[-2000:]
+    lines = [s for s in r0.stdout.splitlines() if s.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GLUPS"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "sedimenting_sphere_128x128x256_D16"
