@@ -162,6 +162,36 @@ def test_momentum_exchange_balances_fluid_momentum(orc):
         assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
 
 
+def test_galilean_invariant_force_of_a_moving_sphere_closes_the_momentum_budget(orc):
+    """Sphere translating at U (Sec. 4.1, Galilean-invariant momentum exchange
+    with u_w = U on every link).  The links' exchange is the fluid's momentum
+    change minus U times its mass change, once the nodes the sphere covers
+    (they leave the fluid with j) and uncovers (the refill gives them exactly
+    rho U, so they drop out) are accounted for:
+        F = -(dP - U dM) - sum over covered nodes of (j - U rho)."""
+    c, _ = orc.lattice()
+    shape = (16, 14, 12)
+    U = np.array([0.6, 0.2, -0.1])  # several nodes covered and uncovered per step
+    body = orc.sphere_body((7.3, 6.6, 5.8), 3.1, U=U, free=True, g=(0, 0, 0), mass=1e30)
+    o = orc.Oracle(shape, nu=0.05, body=body)
+    rho, u, xi = synth.parity_fields(shape, 5)
+    o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
+    for _ in range(3):
+        T0, s0, f0 = o.totals(), o.solid(), o.get_f()
+        o.step(1)
+        T1, s1 = o.totals(), o.solid()
+        assert np.array_equal(np.array(o.body.U), U)
+        cov = (s0 == 0) & (s1 == 1)
+        assert cov.sum() >= 3 and ((s0 == 1) & (s1 == 0)).sum() >= 3
+        j = np.einsum("ia,izyx->zyxa", c, f0)[cov]
+        r = f0.sum(0)[cov]
+        F = np.array(o.body.F)
+        dP, dM = T1[1:4] - T0[1:4], T1[0] - T0[0]
+        budget = -(dP - U * dM) - (j - U * r[:, None]).sum(0)
+        assert np.linalg.norm(F) > 0.05
+        assert np.abs(F - budget).max() < 1e-12 * T0[0]
+
+
 def _angular_momentum(orc, f, fluid, X):
     """Fluid angular momentum about X: sum over fluid nodes of r x j with r
     the minimum-image offset of the node from X and j = sum_i c_i f_i."""
