@@ -162,17 +162,23 @@ def test_momentum_exchange_balances_fluid_momentum(orc):
         assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
 
 
-def test_galilean_invariant_force_of_a_moving_sphere_closes_the_momentum_budget(orc):
-    """Sphere translating at U (Sec. 4.1, Galilean-invariant momentum exchange
-    with u_w = U on every link).  The links' exchange is the fluid's momentum
-    change minus U times its mass change, once the nodes the sphere covers
-    (they leave the fluid with j) and uncovers (the refill gives them exactly
-    rho U, so they drop out) are accounted for:
+@pytest.mark.parametrize("kind", ["sphere", "airfoil"])
+def test_galilean_invariant_force_of_a_moving_body_closes_the_momentum_budget(orc, kind):
+    """Body translating at U: a sphere carried at a fixed velocity (Sec. 4.1)
+    or the plunging airfoil (Sec. 4.2), u_w = U on every link.  With the
+    Galilean-invariant momentum exchange the links' sum is the fluid's
+    momentum change minus U times its mass change, once the nodes the body
+    covers (they leave the fluid with j) and uncovers (the refill gives them
+    exactly rho U, so they drop out) are accounted for:
         F = -(dP - U dM) - sum over covered nodes of (j - U rho)."""
     c, _ = orc.lattice()
-    shape = (16, 14, 12)
-    U = np.array([0.6, 0.2, -0.1])  # several nodes covered and uncovered per step
-    body = orc.sphere_body((7.3, 6.6, 5.8), 3.1, U=U, free=True, g=(0, 0, 0), mass=1e30)
+    if kind == "sphere":
+        shape = (16, 14, 12)
+        # several nodes covered and uncovered per step
+        body = orc.sphere_body((7.3, 6.6, 5.8), 3.1, U=(0.6, 0.2, -0.1), free=True, g=(0, 0, 0), mass=1e30)
+    else:
+        shape = (40, 24, 3)
+        body = _airfoil(orc, 20.0, (10.3, 12.2), t0=3.0, h_amp=3.0, h_omega=0.1)
     o = orc.Oracle(shape, nu=0.05, body=body)
     rho, u, xi = synth.parity_fields(shape, 5)
     o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
@@ -180,7 +186,8 @@ def test_galilean_invariant_force_of_a_moving_sphere_closes_the_momentum_budget(
         T0, s0, f0 = o.totals(), o.solid(), o.get_f()
         o.step(1)
         T1, s1 = o.totals(), o.solid()
-        assert np.array_equal(np.array(o.body.U), U)
+        U = np.array(o.body.U)  # the velocity of the step's walls and refill
+        assert np.linalg.norm(U) > 0.2
         cov = (s0 == 0) & (s1 == 1)
         assert cov.sum() >= 3 and ((s0 == 1) & (s1 == 0)).sum() >= 3
         j = np.einsum("ia,izyx->zyxa", c, f0)[cov]
