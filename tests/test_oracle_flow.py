@@ -162,10 +162,11 @@ def test_momentum_exchange_balances_fluid_momentum(orc):
         assert np.abs(T1[1:4] - T0[1:4] + F).max() < 1e-12 * T0[0]
 
 
-@pytest.mark.parametrize("kind", ["sphere", "airfoil"])
+@pytest.mark.parametrize("kind", ["sphere", "airfoil", "swimmer"])
 def test_galilean_invariant_force_of_a_moving_body_closes_the_momentum_budget(orc, kind):
-    """Body translating at U: a sphere carried at a fixed velocity (Sec. 4.1)
-    or the plunging airfoil (Sec. 4.2), u_w = U on every link.  With the
+    """Body translating at U: a sphere carried at a fixed velocity (Sec. 4.1),
+    the plunging airfoil (Sec. 4.2) or an undeformed swimmer mesh carried
+    along x (Sec. 4.3), u_w = U on every link.  With the
     Galilean-invariant momentum exchange the links' sum is the fluid's
     momentum change minus U times its mass change, once the nodes the body
     covers (they leave the fluid with j) and uncovers (the refill gives them
@@ -176,12 +177,18 @@ def test_galilean_invariant_force_of_a_moving_body_closes_the_momentum_budget(or
         shape = (16, 14, 12)
         # several nodes covered and uncovered per step
         body = orc.sphere_body((7.3, 6.6, 5.8), 3.1, U=(0.6, 0.2, -0.1), free=True, g=(0, 0, 0), mass=1e30)
-    else:
+    elif kind == "airfoil":
         shape = (40, 24, 3)
         body = _airfoil(orc, 20.0, (10.3, 12.2), t0=3.0, h_amp=3.0, h_omega=0.1)
+    else:
+        shape = (48, 20, 20)
+        rest, tris = synth.swimmer_mesh(24.0, 24, 12)
+        body = orc.mesh_body((10.137, 10.371, 10.293), rest, tris, 24.0, 0.0, 24.0, 64.0, U=(0.4, 0, 0), free=True,
+                             mass=1e30)
     o = orc.Oracle(shape, nu=0.05, body=body)
     rho, u, xi = synth.parity_fields(shape, 5)
     o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
+    n_cov = n_unc = 0
     for _ in range(3):
         T0, s0, f0 = o.totals(), o.solid(), o.get_f()
         o.step(1)
@@ -189,7 +196,8 @@ def test_galilean_invariant_force_of_a_moving_body_closes_the_momentum_budget(or
         U = np.array(o.body.U)  # the velocity of the step's walls and refill
         assert np.linalg.norm(U) > 0.2
         cov = (s0 == 0) & (s1 == 1)
-        assert cov.sum() >= 3 and ((s0 == 1) & (s1 == 0)).sum() >= 3
+        n_cov += cov.sum()
+        n_unc += ((s0 == 1) & (s1 == 0)).sum()
         j = np.einsum("ia,izyx->zyxa", c, f0)[cov]
         r = f0.sum(0)[cov]
         F = np.array(o.body.F)
@@ -197,6 +205,9 @@ def test_galilean_invariant_force_of_a_moving_body_closes_the_momentum_budget(or
         budget = -(dP - U * dM) - (j - U * r[:, None]).sum(0)
         assert np.linalg.norm(F) > 0.05
         assert np.abs(F - budget).max() < 1e-12 * T0[0]
+    assert n_cov >= 3 and n_unc >= 3
+    if kind == "swimmer":
+        assert o.counters()["error"] == 0
 
 
 def _angular_momentum(orc, f, fluid, X):
