@@ -5,7 +5,9 @@ addition.  A moving sphere straddles a cut, so boundary nodes, links and
 refilled nodes lie on both sides of it."""
 import multiprocessing as mp
 import os
+import queue
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -54,10 +56,22 @@ def _decomposed(world, shape, sphere, steps, halo=2):
     procs = [ctx.Process(target=_rank, args=(r, world, port, shape, sphere, steps, halo, q)) for r in range(world)]
     for p in procs:
         p.start()
-    got = dict(q.get(timeout=300) for _ in procs)
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
+    got = {}
+    deadline = time.monotonic() + 300
+    try:
+        while len(got) < world:
+            try:
+                rank, out = q.get(timeout=2)
+                got[rank] = out
+            except queue.Empty:
+                dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+                assert not dead and time.monotonic() < deadline, f"ranks failed: exit codes {dead}"
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    assert all(p.exitcode == 0 for p in procs)
     return [got[r] for r in range(world)]
 
 
