@@ -1253,10 +1253,17 @@ cudaError_t forward_step(lbm_ctx *ctx, void *fa, void *fb, uint8_t *flags)
     return cudaSuccess;
 }
 
+// Grid of the boundary and refill adjoints: one warp per listed node, at most
+// LBM_ADJ_LIST_BLOCKS blocks (a build-time override, as the forward list
+// kernels' LBM_LIST_BLOCKS)
+#ifndef LBM_ADJ_LIST_BLOCKS
+#define LBM_ADJ_LIST_BLOCKS 1216
+#endif
+
 int list_blocks(int cap)
 {
     int nb = (cap + BWARPS - 1) / BWARPS;
-    return nb < 1 ? 1 : (nb > 1216 ? 1216 : nb);
+    return nb < 1 ? 1 : (nb > LBM_ADJ_LIST_BLOCKS ? LBM_ADJ_LIST_BLOCKS : nb);
 }
 
 // the reverse of step t for storage type S.  Sequential order: the caller
