@@ -112,6 +112,8 @@ def lib():
             L.orc_get_solid.argtypes = [C.c_void_p, C.c_void_p]
             L.orc_get_body.argtypes = [C.c_void_p, C.POINTER(Body)]
             L.orc_set_body.argtypes = [C.c_void_p, C.POINTER(Body)]
+            L.orc_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
+            L.orc_link.restype = C.c_double
             L.orc_set_owned_z.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_set_owned_z.restype = None
             L.orc_set_z_frame.argtypes = [C.c_void_p, C.c_int, C.c_int]
@@ -266,6 +268,13 @@ class Oracle:
     @body.setter
     def body(self, b: Body):
         lib().orc_set_body(self._ctx, C.byref(b))
+
+    def link(self, x: int, y: int, z: int, i: int):
+        """(q, u_w) of the link from fluid node (x, y, z) to the solid node
+        (x, y, z) - c_i at the current pose, as the boundary step takes them."""
+        uw = np.zeros(3)
+        q = lib().orc_link(self._ctx, int(x), int(y), int(z), int(i), _dp(uw))
+        return q, uw
 
     def set_owned_z(self, z_lo: int, z_hi: int):
         """Later steps sum the force and torque over the boundary nodes of the

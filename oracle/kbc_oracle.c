@@ -966,6 +966,17 @@ double orc_mesh_link(const orc_ctx *c, int x, int y, int z, int i, double *uw)
     return mesh_link(c, x, y, z, C[i], uw);
 }
 
+/* Link fraction q and wall velocity of the link from fluid node (x, y, z) to
+ * the solid node (x, y, z) - c_i at the current pose, for any body: the values
+ * the boundary step takes. */
+double orc_link(const orc_ctx *c, int x, int y, int z, int i, double *uw)
+{
+    const int *ci = C[i];
+    if (c->b.kind == BODY_MESH) return mesh_link(c, x, y, z, ci, uw);
+    wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), (double)(z - ci[2]), uw);
+    return link_q(c, x, y, z, ci);
+}
+
 /* Restricts the force and torque sums of later steps to the boundary nodes of
  * the z layers [z_lo, z_hi) (one slab of a decomposed box); every node is
  * still updated. */

@@ -403,6 +403,93 @@ def _airfoil(orc, chord, le, t0=0.0, h_amp=0.0, h_omega=0.0):
                             wl["thick"], t0)
 
 
+def _links(orc, o):
+    """(x, y, z, i) of every link from a fluid node to a solid neighbour
+    x - c_i (the missing directions of the boundary step)."""
+    c, _ = orc.lattice()
+    solid = o.solid()
+    nz, ny, nx = solid.shape
+    out = []
+    for z, y, x in np.argwhere(solid == 0):
+        for i in range(27):
+            if i == 13:
+                continue
+            sx, sy, sz = x - c[i][0], y - c[i][1], z - c[i][2]
+            if 0 <= sx < nx and 0 <= sy < ny and 0 <= sz < nz and solid[sz, sy, sx]:
+                out.append((int(x), int(y), int(z), i))
+    return out
+
+
+def test_sphere_link_fraction_is_the_first_surface_crossing(orc):
+    """Sec. 3 link fraction on the sphere: the wall point x_b - q c_i lies on
+    the sphere (|x_w - X| = R) and is the first crossing on the way from the
+    fluid node, q in (0, 1]; the wall velocity is the body's U."""
+    c, _ = orc.lattice()
+    X, R, U = np.array([8.3, 7.6, 8.9]), 3.4, (0.01, -0.02, 0.03)
+    o = orc.Oracle((17, 16, 18), nu=0.05, faces=(1, 1, 1, 1, 1, 1), body=orc.sphere_body(X, R, U=U))
+    links = _links(orc, o)
+    assert len(links) > 300
+    for x, y, z, i in links:
+        q, uw = o.link(x, y, z, i)
+        assert 0.0 < q <= 1.0
+        p = np.array([x, y, z], dtype=float)
+        assert abs(np.linalg.norm(p - q * c[i] - X) - R) < 1e-12
+        s = np.linspace(0.0, q, 9)[:-1]
+        assert (np.linalg.norm(p[None] - s[:, None] * c[i][None] - X, axis=1) > R).all()
+        assert np.array_equal(uw, U)
+
+
+def test_airfoil_link_fraction_is_a_surface_crossing(orc):
+    """Sec. 4.2 stand-in airfoil: the link fraction found by bisection places
+    the wall point on the profile, with the node's side outside and the solid
+    side inside within 1e-9 of it (the profile restated in the chord frame:
+    four-digit camber line m, p and the thickness law of the synth
+    coefficients); the wall velocity is the plunge velocity."""
+    c, _ = orc.lattice()
+    wl = synth.plunging_airfoil()
+    le, chord = (10.3, 12.2), 20.0
+    o = orc.Oracle((40, 24, 2), nu=0.05, body=_airfoil(orc, chord, le, t0=3.0, h_amp=2.0, h_omega=0.05))
+    X, U = np.array(o.body.X), np.array(o.body.U)
+    m, pp, a = wl["camber_m"], wl["camber_p"], wl["thick"]
+
+    def inside(px, py):
+        dx, dy = px - X[0], py - X[1]
+        xi = (dx * wl["ca"] - dy * wl["sa"]) / chord
+        eta = (dx * wl["sa"] + dy * wl["ca"]) / chord
+        if xi < 0.0 or xi > 1.0:
+            return False
+        yc = m / pp ** 2 * (2 * pp * xi - xi * xi) if xi < pp else \
+            m / (1 - pp) ** 2 * ((1 - 2 * pp) + 2 * pp * xi - xi * xi)
+        t = a[0] * np.sqrt(xi) + a[1] * xi + a[2] * xi ** 2 + a[3] * xi ** 3 + a[4] * xi ** 4
+        return abs(eta - yc) < t
+
+    links = _links(orc, o)
+    assert len(links) > 100
+    for x, y, z, i in links:
+        q, uw = o.link(x, y, z, i)
+        assert 0.0 < q < 1.0
+        lo, hi = q - 1e-9, q + 1e-9
+        assert not inside(x - lo * c[i][0], y - lo * c[i][1])
+        assert inside(x - hi * c[i][0], y - hi * c[i][1])
+        assert np.array_equal(uw, U)
+
+
+def test_plane_link_fraction_reaches_the_plane(orc):
+    """Planes y = y_lo and y = y_hi: the wall point's y is the plane's and its
+    velocity that plane's."""
+    c, _ = orc.lattice()
+    ny, y_lo, y_hi = 14, 1.7, 11.2
+    o = orc.Oracle((3, ny, 3), nu=0.05, body=orc.planes_body(y_lo, y_hi, U_hi=(0.05, 0, 0)))
+    links = _links(orc, o)
+    assert len(links) > 20
+    for x, y, z, i in links:
+        q, uw = o.link(x, y, z, i)
+        yw = y - q * c[i][1]
+        assert 0.0 < q <= 1.0
+        assert min(abs(yw - y_lo), abs(yw - y_hi)) < 1e-14
+        assert np.array_equal(uw, (0.05, 0, 0) if abs(yw - y_hi) < 1e-14 else (0, 0, 0))
+
+
 def test_airfoil_profile_synth_has_the_stated_thickness():
     """Analytic stand-in for the Sec. 4.2 airfoil: maximum half thickness
     0.0425 (8.5% of the chord) at 25% chord, closed trailing edge."""
