@@ -189,3 +189,22 @@ def test_a_rank_that_leaves_makes_its_peer_fail_not_hang(orc):
         p.join(timeout=60)
     assert procs[1].exitcode == 3
     assert procs[0].exitcode == 0
+
+
+def test_whole_box_frame_changes_nothing(orc):
+    """The slab frame of the whole box (origin 0, period nz) gives the same bits
+    as no frame, for a free sphere that crosses the periodic seam in z."""
+    shape = (16, 14, 18)
+
+    def run(frame):
+        o = orc.Oracle(shape, nu=0.02, faces=FACES, body=orc.sphere_body((7.3, 6.6, 17.1), 3.1, U=(0.05, -0.02, 0.3),
+                                                                          free=True, g=(0, 0, -1e-3)))
+        if frame:
+            o.set_z_frame(0, shape[2])
+        o.init_state(*synth.parity_fields(shape, 2), AMP)
+        o.step(6)
+        return o.get_f(), list(o.body.F), list(o.body.X)
+
+    a, b = run(False), run(True)
+    assert a[2][2] < 3.0  # the centre wrapped through z = 0
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
