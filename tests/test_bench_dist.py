@@ -94,3 +94,41 @@ def test_reference_arm_prints_one_line_on_rank_zero_only(orc):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "sedimenting_sphere_128x128x256_D16"
+
+
+def test_clock_sampler_reads_the_timed_window_and_its_throttle_reasons(tmp_path):
+    """The bench's clock record: samples inside the timed windows (with a
+    0.15 s margin) give the median SM clock, the maximum clock and every
+    throttle reason reported Active there; malformed lines are skipped."""
+    import datetime
+
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    t0 = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def row(dt, mhz, hw="Not Active", cap="Not Active"):
+        ts = (t0 + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.5, 0x0, {hw}, Not Active, Not Active, {cap}\n"
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(row(0.0, 1200, hw="Active") + "garbage line\n" + row(1.0, 2070) + row(1.1, 2040, cap="Active")
+                    + row(1.2, 2070) + row(3.0, 900, hw="Active"))
+    s = bench.ClockSampler(0)
+    s.path, s.proc, s.fh = str(path), _Proc(), open(os.devnull, "w")
+    base = t0.timestamp()
+    s.mark(base + 0.95, base + 1.25)
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
+                 "in_timed_region": True}
+    # no window marked: every sample counts, and the slowdowns outside show up
+    s = bench.ClockSampler(0)
+    s.path, s.proc, s.fh = str(path), _Proc(), open(os.devnull, "w")
+    c = s.stop()
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"] and c["samples"] == 5 and not c["in_timed_region"]
