@@ -132,3 +132,15 @@ def test_clock_sampler_reads_the_timed_window_and_its_throttle_reasons(tmp_path)
     s.path, s.proc, s.fh = str(path), _Proc(), open(os.devnull, "w")
     c = s.stop()
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap"] and c["samples"] == 5 and not c["in_timed_region"]
+
+
+def test_hbm_peak_comes_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    import json
+
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_peak() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6680.2, "bf16_tflops": 1930.3}))
+    assert bench.measured_hbm_peak() == (6680.2, "measured (hbm_gbs)")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
+    assert bench.measured_hbm_peak()[1] == "fallback"
