@@ -16,8 +16,9 @@ decomposition of one box over several devices, tests/test_oracle_slab.py).
 
 Parity status per function (pins live in tests/test_oracle_*.py):
   feq, kbc_split, collide (all modes), gamma_exact, grad, stream/box faces,
-  refill moments, momentum exchange force and torque, Couette with Grad walls, shear-wave and
-  Taylor-Green viscosity: pinned.
+  refill moments, momentum exchange force and torque, Couette with Grad walls, the Grad
+  wall targets (target velocity and static + dynamic target density in co-moving flow),
+  shear-wave and Taylor-Green viscosity: pinned.
   Sphere refill density average and the sphere's Euler update beyond one step:
   pinned only by invariants (moments of the refilled node, mass accounting).
 """
@@ -125,6 +126,8 @@ def lib():
             L.orc_step.restype = C.c_int
             L.orc_step_sampled.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_long), _D]
             L.orc_step_sampled.restype = C.c_int
+            L.orc_wall_targets_sampled.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_long), _D]
+            L.orc_wall_targets_sampled.restype = C.c_int
             L.orc_totals.argtypes = [C.c_void_p, _D]
             L.orc_mesh_pose.argtypes = [C.c_void_p, _D, _D]
             L.orc_mesh_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
@@ -303,6 +306,18 @@ class Oracle:
         out = np.empty((len(nodes), 27))
         lib().orc_step_sampled(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_long)),
                                _dp(out))
+        return out
+
+    def wall_targets_sampled(self, nodes) -> np.ndarray:
+        """Moves to t+1's marks (body update, marks, refill, as a step does)
+        and returns per listed node (number of missing directions, static
+        density, dynamic density, target density, target velocity x, y, z) of
+        the Grad wall boundary (Sec. 3); NaN densities where the node is no
+        boundary node.  The state is not advanced."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        out = np.empty((len(nodes), 7))
+        lib().orc_wall_targets_sampled(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_long)),
+                                       _dp(out))
         return out
 
     def mesh_pose(self):

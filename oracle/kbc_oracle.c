@@ -810,14 +810,15 @@ static void refill(orc_ctx *c, int x, int y, int z)
     c->n_refill++;
 }
 
-/* Post-collision state of fluid node (x,y,z) at t+1, written to out[27].
- * Adds the node's momentum-exchange force and torque to F, M. */
-static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F, double *M)
+/* Pull of fluid node (x,y,z) for the step to t+1 (Eq. kineticEq):
+ * F_i = f'_i(x - c_i, t) from the box rules; missing[i] = 1 where the source
+ * is solid at t+1 (then F_i = 0 until the wall boundary fills it).  Returns
+ * the number of missing directions. */
+static int gather_node(const orc_ctx *c, int x, int y, int z, double *Fi, int *missing)
 {
     const long N = c->N;
     const long n = nid(c, x, y, z);
-    double Fi[Q];
-    int missing[Q], nmiss = 0;
+    int nmiss = 0;
     for (int i = 0; i < Q; ++i) {
         int s[3];
         int kind = pull_source(c, x, y, z, i, s);
@@ -830,39 +831,69 @@ static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F,
             else Fi[i] = c->fa[i * N + m];
         }
     }
+    return nmiss;
+}
+
+/* Targets of the Grad boundary at x_b (Sec. 3), D = {i : x_b - c_i solid at
+ * t+1}.  For each missing i: the link fraction q_i and the wall velocity
+ * u_w,i; the static density sums the known pulls and the bounce-back
+ * populations, the dynamic density the wall motion, and the target velocity
+ * averages the interpolations between the wall point and the fluid node
+ * x_b + c_i. */
+static void wall_targets(const orc_ctx *c, int x, int y, int z, const double *Fi, const int *missing,
+                         int nmiss, double *q, double uw[][3], double *rho_stat_out, double *rho_dyn_out,
+                         double *utgt)
+{
+    const long N = c->N;
+    const long n = nid(c, x, y, z);
+    double rho_stat = 0, rho_dyn = 0;
+    for (int a = 0; a < 3; ++a) utgt[a] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        if (!missing[i]) { rho_stat += Fi[i]; continue; }
+        const int *ci = C[i];
+        if (c->b.kind == BODY_MESH) {
+            q[i] = mesh_link(c, x, y, z, ci, uw[i]);
+        } else {
+            q[i] = link_q(c, x, y, z, ci);
+            wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), (double)(z - ci[2]), uw[i]);
+        }
+        /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
+         * the wall and returns reflected (halfway bounce-back). */
+        rho_stat += c->fa[opp(i) * N + n];
+        /* Reading: rho_dyn uses the reference density rho0. */
+        rho_dyn += 6.0 * W[i] * c->p.rho0 * (ci[0] * uw[i][0] + ci[1] * uw[i][1] + ci[2] * uw[i][2]);
+        /* target velocity: linear interpolation between the wall point at
+         * -q and the fluid node x_f = x_b + c_i at +1, read at x_b.
+         * Reading: if x_f is not fluid the term is the wall velocity. */
+        long mf = neighbour(c, x, y, z, ci[0], ci[1], ci[2]);
+        if (mf >= 0 && !c->solid1[mf]) {
+            double rf, uf[3];
+            node_moments(c, c->fa, mf, &rf, uf);
+            for (int a = 0; a < 3; ++a) utgt[a] += (q[i] * uf[a] + uw[i][a]) / (1.0 + q[i]);
+        } else {
+            for (int a = 0; a < 3; ++a) utgt[a] += uw[i][a];
+        }
+    }
+    for (int a = 0; a < 3; ++a) utgt[a] /= nmiss;
+    *rho_stat_out = rho_stat;
+    *rho_dyn_out = rho_dyn;
+}
+
+/* Post-collision state of fluid node (x,y,z) at t+1, written to out[27].
+ * Adds the node's momentum-exchange force and torque to F, M. */
+static void node_update(orc_ctx *c, int x, int y, int z, double *out, double *F, double *M)
+{
+    const long N = c->N;
+    const long n = nid(c, x, y, z);
+    double Fi[Q];
+    int missing[Q];
+    const int nmiss = gather_node(c, x, y, z, Fi, missing);
     if (nmiss) {
-        /* Sec. 3 Grad boundary at x_b.  D = {i : x_b - c_i solid at t+1}. */
         double q[Q], uw[Q][3];
-        double rho_stat = 0, rho_dyn = 0, utgt[3] = {0, 0, 0};
+        double rho_stat, rho_dyn, utgt[3];
         double rb, ub[3];
         node_moments(c, c->fa, n, &rb, ub);
-        for (int i = 0; i < Q; ++i) {
-            if (!missing[i]) { rho_stat += Fi[i]; continue; }
-            const int *ci = C[i];
-            if (c->b.kind == BODY_MESH) {
-                q[i] = mesh_link(c, x, y, z, ci, uw[i]);
-            } else {
-                q[i] = link_q(c, x, y, z, ci);
-                wall_velocity(&c->b, (double)(x - ci[0]), (double)(y - ci[1]), (double)(z - ci[2]), uw[i]);
-            }
-            /* f^bb_i = f'_{opp i}(x_b, t): the population that left x_b towards
-             * the wall and returns reflected (halfway bounce-back). */
-            rho_stat += c->fa[opp(i) * N + n];
-            rho_dyn += 6.0 * W[i] * c->p.rho0 * (ci[0] * uw[i][0] + ci[1] * uw[i][1] + ci[2] * uw[i][2]);
-            /* target velocity: linear interpolation between the wall point at
-             * -q and the fluid node x_f = x_b + c_i at +1, read at x_b.
-             * Reading: if x_f is not fluid the term is the wall velocity. */
-            long mf = neighbour(c, x, y, z, ci[0], ci[1], ci[2]);
-            if (mf >= 0 && !c->solid1[mf]) {
-                double rf, uf[3];
-                node_moments(c, c->fa, mf, &rf, uf);
-                for (int a = 0; a < 3; ++a) utgt[a] += (q[i] * uf[a] + uw[i][a]) / (1.0 + q[i]);
-            } else {
-                for (int a = 0; a < 3; ++a) utgt[a] += uw[i][a];
-            }
-        }
-        for (int a = 0; a < 3; ++a) utgt[a] /= nmiss;
-        /* Reading: rho_dyn uses the reference density rho0. */
+        wall_targets(c, x, y, z, Fi, missing, nmiss, q, uw, &rho_stat, &rho_dyn, utgt);
         double rho = rho_stat + rho_dyn;
         double dudx[3][3], Pi[9], fs[Q];
         velocity_gradient(c, x, y, z, ub, c->solid1, dudx);
@@ -1021,9 +1052,8 @@ void orc_init_state(orc_ctx *c, const double *rho, const double *u, const double
 }
 
 /* Newton's equations of the sphere (Sec. 4.1) by explicit Euler:
- * X^{t+1} = X^t + U^t,  U^{t+1} = U^t + F^t (1/m_s) + (1 - rho_f/rho_s) g,
- * with 1/m_s and (1 - rho_f/rho_s) g formed once.  On periodic axes the
- * centre is wrapped back into [0, n). */
+ * X^{t+1} = X^t + U^t,  U^{t+1} = U^t + F^t / m_s + (1 - rho_f/rho_s) g.
+ * On periodic axes the centre is wrapped back into [0, n). */
 static void body_update(orc_ctx *c)
 {
     orc_body *b = &c->b;
@@ -1040,11 +1070,10 @@ static void body_update(orc_ctx *c)
          * psi += omega, (I omega) += M_z with I of the new pose (the yaw
          * equation d(I omega)/dt = M as printed); then the new pose */
         b->t = b->t + 1.0;
-        const double inv_m = 1.0 / b->mass;
         for (int a = 0; a < 2; ++a)
             if (b->free_motion & (1 << a)) {
                 b->X[a] = b->X[a] + b->U[a];
-                b->U[a] = b->U[a] + b->F[a] * inv_m;
+                b->U[a] = b->U[a] + b->F[a] / b->mass;
             }
         if (b->free_motion & 4) {
             double V, cx, cy, I;
@@ -1057,8 +1086,6 @@ static void body_update(orc_ctx *c)
         return;
     }
     if (!b->free_motion) return;
-    const double inv_m = 1.0 / b->mass;
-    const double buoy = 1.0 - 1.0 / b->rho_ratio;
     int n[3] = {c->p.nx, c->p.ny, c->p.nz};
     int per[3] = {c->p.face[0] == FACE_PERIODIC, c->p.face[2] == FACE_PERIODIC, c->p.face[4] == FACE_PERIODIC};
     if (c->zf_period > 0) {
@@ -1066,7 +1093,7 @@ static void body_update(orc_ctx *c)
         per[2] = 1;
     }
     for (int a = 0; a < 3; ++a) {
-        double acc = b->F[a] * inv_m + buoy * b->g[a];
+        double acc = b->F[a] / b->mass + (1.0 - 1.0 / b->rho_ratio) * b->g[a];
         b->X[a] = b->X[a] + b->U[a];
         b->U[a] = b->U[a] + acc;
         if (per[a]) {
@@ -1144,6 +1171,38 @@ int orc_step_sampled(orc_ctx *c, long nsample, const long *nodes, double *out)
             continue;
         }
         node_update(c, x, y, z, out + k * Q, F, M);
+    }
+    return 0;
+}
+
+/* The Grad boundary's targets for one step evaluated at the listed nodes:
+ * moves the body, updates the solid marks and refills as orc_step does, then
+ * writes per node out[k*7 + 0..6] = (number of missing directions, static
+ * density, dynamic density, target density, target velocity), with the
+ * densities and velocity NaN where the node is no boundary node at t+1.  The
+ * state is left as after the refill, not advanced. */
+int orc_wall_targets_sampled(orc_ctx *c, long nsample, const long *nodes, double *out)
+{
+    step_prepare(c);
+    const orc_params *p = &c->p;
+    for (long k = 0; k < nsample; ++k) {
+        long n = nodes[k];
+        int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx * p->ny));
+        double *o = out + k * 7;
+        for (int j = 0; j < 7; ++j) o[j] = NAN;
+        o[0] = 0.0;
+        if (c->solid1[n]) continue;
+        double Fi[Q];
+        int missing[Q];
+        const int nmiss = gather_node(c, x, y, z, Fi, missing);
+        if (!nmiss) continue;
+        double q[Q], uw[Q][3], rho_stat, rho_dyn, utgt[3];
+        wall_targets(c, x, y, z, Fi, missing, nmiss, q, uw, &rho_stat, &rho_dyn, utgt);
+        o[0] = nmiss;
+        o[1] = rho_stat;
+        o[2] = rho_dyn;
+        o[3] = rho_stat + rho_dyn;
+        for (int a = 0; a < 3; ++a) o[4 + a] = utgt[a];
     }
     return 0;
 }
