@@ -51,7 +51,8 @@ typedef enum {
     LBM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     LBM_ERR_OOM = 3,         /* device allocation failed */
     LBM_ERR_UNSTABLE = 4,    /* a node had non-finite or non-positive density */
-    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (status bit 4) */
+    LBM_ERR_TIMEOUT = 5,     /* reserved: no kernel of this library waits on a device
+                                flag or barrier, so no call returns it */
     LBM_ERR_STATE = 6,       /* call out of order (e.g. step before init) */
     LBM_ERR_UNSUPPORTED = 7  /* option not built */
 } lbm_status;
@@ -147,7 +148,8 @@ typedef struct {
     double R;
     double y_lo, y_hi;
     double U_lo[3], U_hi[3];
-    double mass;          /* m_s (rho_s * pi D^3 / 6 for the analytic volume) */
+    double mass;          /* body mass; a SPHERE given 0 takes m_s = rho_s pi D^3 / 6
+                             (rho_s = rho_ratio rho0, analytic volume, Sec. 4.1) */
     double rho_ratio;     /* rho_s / rho_f */
     double g[3];          /* gravity */
     double chord, ca, sa, h_amp, h_omega, camber_m, camber_p, thick[5], t0;  /* AIRFOIL; t0 also MESH */
@@ -172,7 +174,7 @@ typedef struct {
     int32_t n_boundary;   /* boundary nodes of the last step */
     int32_t n_uncovered;  /* nodes refilled in the last step */
     int32_t n_links;      /* missing populations of the last step */
-    int32_t status;       /* device status bits (1: unstable node, 2: band overflow, 4: timeout) */
+    int32_t status;       /* device status bits (1: unstable node, 2: band overflow) */
     int32_t n_band;       /* nodes of the last step's sweep box, updated by a launch of their own after the
                              body's marks (0 when the step used one flag-aware bulk launch) */
     double t;             /* time of the current pose (prescribed motion), steps */
@@ -260,7 +262,7 @@ LBM_API lbm_status lbm_body_forces_async(lbm_ctx *ctx, lbm_force_record *out, in
 
 /* Blocks until the record of ticket has landed in host memory, then returns
  * the error lbm_body_forces would return for that step's status bits
- * (LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE) or LBM_OK.  LBM_ERR_ARG
+ * (LBM_ERR_UNSTABLE, LBM_ERR_STATE) or LBM_OK.  LBM_ERR_ARG
  * for a ticket not yet issued. */
 LBM_API lbm_status lbm_body_forces_wait(lbm_ctx *ctx, int64_t ticket);
 
@@ -387,10 +389,16 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, doubl
  * asynchronously to out.  The work space is a fixed array inside the library
  * (160 KB on every GPU that loads it, held until the process exits), so
  * lattices of more than 67,108,864 nodes are rejected with LBM_ERR_ARG.  The
- * first call on a device looks up that array's device address; make it before
- * any stream capture.  All calls share the array: calls ordered on one stream
- * are safe, calls whose kernels overlap on the GPU race.  No error message is
- * kept (there is no context); the status says what failed. */
+ * kernels run on the current device: f, out and flags must be device memory
+ * of that device (LBM_ERR_ARG otherwise).  The first call on a device looks
+ * up that array's device address and keeps it for the life of the process
+ * (a cudaDeviceReset of the device invalidates it); make that first call
+ * before any stream capture.  All calls share the array: calls ordered on one
+ * stream are safe, calls whose kernels overlap on the GPU race.  If a CUDA
+ * error from earlier work is pending on the calling thread, nothing is
+ * enqueued, LBM_ERR_CUDA is returned and the error is left in place for its
+ * owner.  No error message is kept (there is no context); the status says
+ * what failed. */
 LBM_API lbm_status lbm_totals_noalloc(const lbm_params *p, const void *f, const uint8_t *flags,
                                       double *out, void *stream);
 

@@ -167,7 +167,8 @@ def make_params(shape, nu, storage="fp32", faces=(0,) * 6, rho0=1.0, u_face=(0.0
 
 
 def sphere(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0, 0.0), mass=None) -> Geometry:
-    """Sphere of radius R at X; mass defaults to rho_s pi D^3 / 6 with rho_f = 1."""
+    """Sphere of radius R at X; without a mass lbm_set_geometry takes
+    rho_s pi D^3 / 6 with rho_s = rho_ratio rho0."""
     G = Geometry()
     G.kind = BODY_SPHERE
     G.free_motion = 1 if free else 0
@@ -175,7 +176,7 @@ def sphere(X, R, U=(0.0, 0.0, 0.0), free=False, rho_ratio=1.5, g=(0.0, 0.0, 0.0)
         G.X[a], G.U[a], G.g[a] = float(X[a]), float(U[a]), float(g[a])
     G.R = float(R)
     G.rho_ratio = float(rho_ratio)
-    G.mass = float(mass) if mass is not None else float(rho_ratio) * np.pi * (2 * R) ** 3 / 6.0
+    G.mass = float(mass) if mass is not None else 0.0
     return G
 
 

@@ -216,7 +216,11 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
     LBM_CUDA(drain_records(ctx), "record copies");
     free_scratch(ctx->S, true);
-    ctx->has_body = g->kind != LBM_BODY_NONE;
+    // until the new body is in place the context has none and no node is
+    // marked, so a call that fails below leaves a consistent bodiless context
+    ctx->has_body = false;
+    LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
+    const bool body = g->kind != LBM_BODY_NONE;
     GeomParams &G = ctx->G;
     G = GeomParams{};
     ctx->order = ctx->order_request;
@@ -232,11 +236,18 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.g[a] = g->g[a];
         G.periodic[a] = L.face[2 * a] == LBM_FACE_PERIODIC;
     }
-    G.inv_mass = g->mass > 0.0 ? 1.0 / g->mass : 0.0;
+    // Sec. 4.1: a sphere given no mass takes m_s = rho_s pi D^3 / 6 with
+    // rho_s = rho_ratio rho0 (the analytic volume, not the voxel count)
+    double mass = g->mass;
+    if (g->kind == LBM_BODY_SPHERE && !(mass > 0.0) && g->R > 0.0 && g->rho_ratio > 0.0) {
+        const double D = 2.0 * g->R;
+        mass = g->rho_ratio * L.rho0 * M_PI * D * D * D / 6.0;
+    }
+    G.inv_mass = mass > 0.0 ? 1.0 / mass : 0.0;
     G.buoy = g->rho_ratio > 0.0 ? 1.0 - 1.0 / g->rho_ratio : 0.0;
     const int n[3] = {L.nx, L.ny, L.nz};
     if (g->kind == LBM_BODY_SPHERE) {
-        if (!(g->R > 0.0) || (g->free_motion && (!(g->mass > 0.0) || !(g->rho_ratio > 0.0))))
+        if (!(g->R > 0.0) || (g->free_motion && (!(mass > 0.0) || !(g->rho_ratio > 0.0))))
             return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: sphere needs R > 0 (and mass, rho_ratio > 0 when free)");
         for (int a = 0; a < 3; ++a) {
             const int c = (int)std::ceil(2.0 * g->R) + 9;
@@ -361,7 +372,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     Scratch &S = ctx->S;
     S.n_partials = 64;
     bool ok = true;
-    if (ctx->has_body) {
+    if (body) {
         ok = dalloc(&S.blist, vol) == cudaSuccess && dalloc(&S.bpos, vol) == cudaSuccess &&
              dalloc(&S.ulist, vol) == cudaSuccess && dalloc(&S.upos, vol) == cudaSuccess &&
              dalloc(&S.bforce, vol * 6) == cudaSuccess &&
@@ -401,7 +412,6 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     }
     if (!ok) {
         free_scratch(ctx->S, true);
-        ctx->has_body = false;
         return fail(ctx, LBM_ERR_OOM, "lbm_set_geometry: device allocation failed");
     }
     DevBody hb[2] = {};
@@ -420,7 +430,6 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     }
     ctx->bcur = 0;
     LBM_CUDA(cudaMemcpyAsync(S.body, hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream), "body upload");
-    LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
     if (g->kind == LBM_BODY_MESH) {
         LBM_CUDA(launch_mesh_mark_initial(L, G, S, 0, ctx->flags, ctx->stream), "initial marks");
         LBM_CUDA(launch_sweep_init(L, G, S, 0, ctx->stream), "sweep box");
@@ -429,17 +438,21 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
         if (mst) {
             free_scratch(ctx->S, true);
-            ctx->has_body = false;
+            // no body: no node stays marked
+            LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
+            LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
             return fail(ctx, LBM_ERR_ARG, (mst & 2) ? "lbm_set_geometry: mesh closer than two nodes to a box face"
                                                     : "lbm_set_geometry: mesh column or cell list overflow");
         }
+        ctx->has_body = true;
         return LBM_OK;
     }
-    if (ctx->has_body) {
+    if (body) {
         LBM_CUDA(launch_mark_initial(L, G, hb[0].X, ctx->flags, ctx->stream), "initial marks");
         LBM_CUDA(launch_sweep_init(L, G, S, 0, ctx->stream), "sweep box");
     }
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
+    ctx->has_body = body;
     return LBM_OK;
 }
 
@@ -674,7 +687,6 @@ lbm_status lbm_body_forces(lbm_ctx *ctx, double F[3], double M[3], int averaged)
         }
     }
     if (b.status & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
-    if (b.status & ST_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (b.status & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
     return LBM_OK;
 }
@@ -727,7 +739,6 @@ lbm_status lbm_body_forces_wait(lbm_ctx *ctx, int64_t ticket)
     if (ticket < ctx->next_ticket - LBM_RECORD_DEPTH) return LBM_OK;
     const int st = ctx->rec[k]->status;
     if (st & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "a node had non-finite or non-positive density");
-    if (st & ST_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (st & ST_BAND_OVERFLOW) return fail(ctx, LBM_ERR_STATE, "body band or boundary list overflowed its capacity");
     return LBM_OK;
 }

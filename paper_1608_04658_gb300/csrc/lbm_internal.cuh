@@ -23,7 +23,6 @@ constexpr uint8_t FL_UNCOVERED = 8;  // solid at the previous step, fluid now
 // device status bits
 constexpr int ST_UNSTABLE = 1;
 constexpr int ST_BAND_OVERFLOW = 2;
-constexpr int ST_TIMEOUT = 4;        // a bounded wait on an mbarrier gave up
 
 __host__ __device__ constexpr int cx_of(int i) { return i / 9 - 1; }
 __host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }

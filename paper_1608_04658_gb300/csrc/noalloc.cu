@@ -7,7 +7,10 @@
 // block sums a fixed chunk of NOALLOC_CHUNK consecutive nodes, so a lattice of
 // more than NOALLOC_MAX_PARTIALS * NOALLOC_CHUNK nodes is rejected.  The
 // partials are fully rewritten by every call (nothing has to start at zero);
-// two calls whose kernels overlap on the GPU would race on them.
+// two calls whose kernels overlap on the GPU would race on them.  The array's
+// device address is looked up on the first call on each device and kept for
+// the life of the process (a cudaDeviceReset of that device invalidates it,
+// as it does every other device pointer the caller holds).
 #include <mutex>
 
 #include "lbm_internal.cuh"
@@ -71,13 +74,24 @@ __global__ void noalloc_final_kernel(const double *__restrict__ partials, int np
     if (lane == 0) out[k] = v;
 }
 
-// device address of the scratch array, looked up once per device
-static double *scratch_on_current_device(lbm_status &st)
+// true when p is device (or managed) memory that device dev can address
+static bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();  // the query's own error, raised just now
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+// device address of the scratch array on device dev, looked up once per
+// device (the first call on a device does it)
+static double *scratch_on_device(int dev, lbm_status &st)
 {
     static std::mutex mu;
     static double *addr[NOALLOC_MAX_DEVICES] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
         st = LBM_ERR_CUDA;
         return nullptr;
     }
@@ -106,8 +120,16 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params *p, const void *f, con
     const long long N = (long long)p->nx * p->ny * p->nz;
     if (27 * N >= (1LL << 31)) return LBM_ERR_ARG;
     if (N > (long long)NOALLOC_MAX_PARTIALS * NOALLOC_CHUNK) return LBM_ERR_ARG;
+    if (p->storage < LBM_FP64 || p->storage > LBM_BF16) return LBM_ERR_ARG;
+    // an error left pending by earlier, unrelated work stays with its owner:
+    // enqueue nothing and leave it in place
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
+    // the kernels run on the current device, so the buffers must live there
+    if (!on_device(f, dev) || !on_device(out, dev) || (flags && !on_device(flags, dev))) return LBM_ERR_ARG;
     lbm_status st;
-    double *scratch = scratch_on_current_device(st);
+    double *scratch = scratch_on_device(dev, st);
     if (!scratch) return st;
     const int nparts = (int)((N + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
     cudaStream_t s = (cudaStream_t)stream;
@@ -127,6 +149,8 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params *p, const void *f, con
         break;
     default: return LBM_ERR_ARG;
     }
+    // nothing was pending before the launches, so an error now is their own
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     noalloc_final_kernel<<<1, 5 * 32, 0, s>>>(scratch, nparts, out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -24,7 +24,14 @@ def _entry():
     return lbm, fn
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def _call(fn, lat, out, flags=True):
+    import ctypes as C
+    return fn(C.byref(lat.params), C.c_void_p(lat.f.data_ptr()),
+              C.c_void_p(lat.flags.data_ptr()) if flags else None,
+              C.c_void_p(out.data_ptr()), C.c_void_p(lat.stream.cuda_stream))
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
 def test_noalloc_totals_match_the_context_totals(storage):
     """Two calls in a row (the shared work space keeps the previous call's
     partials) each equal lbm_totals on the same state, up to the addition
@@ -42,12 +49,57 @@ def test_noalloc_totals_match_the_context_totals(storage):
     for _ in range(2):
         lat.step(3)
         ref = lat.totals()
-        st = fn(C.byref(lat.params), C.c_void_p(lat.f.data_ptr()), C.c_void_p(lat.flags.data_ptr()),
-                C.c_void_p(out.data_ptr()), C.c_void_p(lat.stream.cuda_stream))
-        assert st == 0
+        assert _call(fn, lat, out) == 0
         lat.stream.synchronize()
         got = out.cpu().numpy()
         assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * ref[0])
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_noalloc_totals_on_a_large_bodiless_box(storage):
+    """128^3 nodes give 128 block partials, so each lane of the final sum adds
+    four of them; no body, so the call takes no flags (NULL) and the context
+    sums every node too.  Two calls in a row, a step between them."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm, fn = _entry()
+    shape = (128, 128, 128)
+    wl = synth.tgv_periodic(128)
+    rho, u = synth.taylor_green_fields(wl["shape"], wl["u0"])
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage)
+    lat.init_state(rho, u)
+    out = torch.zeros(5, dtype=torch.float64, device=lat.device)
+    for _ in range(2):
+        lat.step(1)
+        ref = lat.totals()
+        assert _call(fn, lat, out, flags=False) == 0
+        lat.stream.synchronize()
+        got = out.cpu().numpy()
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * ref[0])
+
+
+def test_noalloc_rejects_buffers_not_on_the_current_device():
+    """Host memory for the populations or the output is refused before
+    anything is enqueued."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm, fn = _entry()
+    shape = (8, 8, 8)
+    lat = lbm.Lattice(shape, 0.05, storage="fp32")
+    lat.init_state(*synth.uniform_fields(shape))
+    host_f = np.zeros(27 * 8 * 8 * 8, dtype=np.float32)
+    host_out = np.zeros(5)
+    dev_out = torch.zeros(5, dtype=torch.float64, device=lat.device)
+    assert fn(C.byref(lat.params), C.c_void_p(host_f.ctypes.data), None, C.c_void_p(dev_out.data_ptr()),
+              C.c_void_p(lat.stream.cuda_stream)) == 1  # LBM_ERR_ARG
+    assert fn(C.byref(lat.params), C.c_void_p(lat.f.data_ptr()), None, C.c_void_p(host_out.ctypes.data),
+              C.c_void_p(lat.stream.cuda_stream)) == 1
+    # a correct call afterwards still works
+    assert _call(fn, lat, dev_out, flags=False) == 0
+    lat.stream.synchronize()
+    assert np.allclose(dev_out.cpu().numpy(), lat.totals(), rtol=1e-12, atol=1e-12 * 512)
 
 
 def test_noalloc_rejects_lattices_beyond_its_work_space():
