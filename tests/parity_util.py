@@ -6,12 +6,13 @@ import oracle
 import synth
 
 # Parity bars on full populations, max over fluid nodes and directions of
-# |f_gpu - f_oracle| / |f_oracle| (10 steps for the storage forms).  The 2e-3
-# bar of 16-bit storage applies to FP16, the 16-bit form this library adopts;
-# BF16 keeps 8 significand bits (relative rounding 2^-9 = 2e-3 per store of
+# |f_gpu - f_oracle| / |f_oracle| (10 steps for the storage forms): 1e-12 in
+# FP64, 2e-6 in FP32 and 2e-3 in 16-bit storage.  FP16 meets the 16-bit bar;
+# BF16 keeps 8 significand bits (relative rounding up to 2^-9 per store of
 # g = f - W rho0, and |g|/f reaches 0.5 in the rough random fields of these
-# tests), so its bar is 8e-3.
-TOL = {"fp64": 1e-12, "fp32": 2e-6, "fp16": 2e-3, "bf16": 8e-3}
+# tests), so the BF16 cases that exceed it are marked as expected failures
+# with their measured errors.
+TOL = {"fp64": 1e-12, "fp32": 2e-6, "fp16": 2e-3, "bf16": 2e-3}
 
 
 def rel_err(a: np.ndarray, b: np.ndarray, mask: np.ndarray | None = None) -> float:
@@ -28,7 +29,8 @@ def oracle_body(geom):
     import paper_1608_04658_gb300 as lbm
     if geom.kind == lbm.BODY_SPHERE:
         return oracle.sphere_body(list(geom.X), geom.R, U=list(geom.U), free=bool(geom.free_motion),
-                                  rho_ratio=geom.rho_ratio, g=list(geom.g), mass=geom.mass)
+                                  rho_ratio=geom.rho_ratio, g=list(geom.g),
+                                  mass=geom.mass if geom.mass > 0 else None)
     if geom.kind == lbm.BODY_AIRFOIL:
         return oracle.airfoil_body((geom.X[0], geom.X[1]), geom.chord, geom.ca, geom.sa, geom.h_amp,
                                    geom.h_omega, geom.camber_m, geom.camber_p, list(geom.thick), geom.t0)

@@ -151,7 +151,7 @@ def _oracle_thrust(shape, theta, fields, H, w, L=24.0, X=(12.137, 12.371, 12.293
     return J / H, counts, o.solid()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 2e-3), ("fp16", 2e-5), ("bf16", 3e-4)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 1e-4), ("fp16", 2e-5), ("bf16", 3e-4)])
 def test_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     """Sec. 4.3 kinematics: d(mean thrust)/d(amplitude, wavelength, period)
     from the GPU adjoint vs central differences of the FP64 oracle, in every
@@ -167,7 +167,7 @@ def test_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     lat.init_state(*fields)
     out = lat.adjoint(H, w)
     J0, _, _ = _oracle_thrust(shape, theta, fields, H, w)
-    jrel = {"fp64": 1e-9, "fp32": 1e-3, "fp16": 1e-5, "bf16": 5e-4}[storage]
+    jrel = {"fp64": 1e-9, "fp32": 1e-6, "fp16": 1e-5, "bf16": 5e-4}[storage]
     print(f"{storage}: J rel err {abs(out['J'] - J0) / abs(J0):.2e}")
     assert out["J"] == pytest.approx(J0, rel=jrel)
     fd = np.zeros(3)
@@ -186,7 +186,7 @@ def test_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     assert np.abs(g - fd).max() <= tol * np.abs(fd).max()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_free_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     """As above with the swimmer free along x and a light body (mass a quarter
     of the displaced fluid's), so the kinematics also change the head's path:
@@ -204,7 +204,7 @@ def test_free_swimmer_thrust_gradient_matches_oracle_fd(storage, tol):
     out = lat.adjoint(H, w)
     b = lat.body()
     J0, _, _ = _oracle_thrust(shape, theta, fields, H, w, **kw)
-    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-3)
+    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-6)
     assert b["X"][0] != 12.137  # the head moved
     fd = np.zeros(3)
     for k in range(3):
@@ -240,7 +240,7 @@ def test_dot_product_with_three_dof_swimmer():
 
 
 @pytest.mark.parametrize("free,storage,tol", [(3, "fp64", 1e-6), (4, "fp64", 1e-6), (7, "fp64", 1e-6),
-                                              (7, "fp32", 2e-3)])
+                                              (7, "fp32", 1e-4)])
 def test_com_frame_swimmer_thrust_gradient_matches_oracle_fd(free, storage, tol):
     """Mean-thrust gradient of the swimmer free in x and y (3), in yaw (4) or
     in x, y and yaw (7): the pose X + R(psi)(b - c(t)) moves with theta
@@ -258,7 +258,7 @@ def test_com_frame_swimmer_thrust_gradient_matches_oracle_fd(free, storage, tol)
     lat.init_state(*fields)
     out = lat.adjoint(H, w)
     J0, _, _ = _oracle_thrust(shape, theta, fields, H, w, **kw)
-    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-3)
+    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-6)
     fd = np.zeros(3)
     for k in range(3):
         h = 1e-6 * theta[k]
@@ -294,7 +294,7 @@ def _oracle_airfoil(shape, theta, fields, H, w):
     return J / H, counts, o.solid()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_airfoil_lift_gradient_matches_oracle_fd(storage, tol):
     """Sec. 4.2 plunge: d(mean lift)/d(amplitude, angular frequency) from the
     GPU adjoint vs central differences of the FP64 oracle, with equilibrium
@@ -312,7 +312,7 @@ def test_airfoil_lift_gradient_matches_oracle_fd(storage, tol):
     out = lat.adjoint(H, w)
     J0, c0, _ = _oracle_airfoil(shape, theta, fields, H, w)
     assert sum(c[2] for c in c0) > 0  # nodes get refilled
-    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-3)
+    assert out["J"] == pytest.approx(J0, rel=1e-9 if storage == "fp64" else 1e-6)
     fd = np.zeros(2)
     for k in range(2):
         h = 1e-6 * theta[k]

@@ -178,19 +178,28 @@ def test_exact_stabilizer_solves_entropy_condition(orc):
 
 
 def test_analytic_stabilizer_converges_to_exact(orc):
-    """The analytic g is the first non-vanishing order of Eq. (gamma_min) in
-    ds/f^eq, dh/f^eq: along a fixed perturbation direction scaled by eps,
-    |g_analytic - g_exact| shrinks at least linearly with eps."""
+    """The analytic g is the root of Eq. (gamma_min) with the logarithm
+    expanded to first order in the deviations (ds, dh)/f^eq; the next order
+    of the expansion is smaller by one power of the deviation, so along a
+    fixed perturbation direction scaled by eps, g_analytic - g_exact = C eps
+    + O(eps^2): the fitted order over eps = 1e-3 ... 1e-5 is 1 and the error
+    over eps settles to a constant.  A wrong factor or sign in the analytic
+    formula leaves an O(1) error and fails both."""
     rng = np.random.default_rng(27)
     beta = 0.99
     fe0 = orc.feq(1.0, [0.04, 0.02, -0.03])
+    eps_l = np.array([1e-3, 3e-4, 1e-4, 3e-5, 1e-5])
     for _ in range(10):
         d = rng.standard_normal(27)
         errs = []
-        for eps in [1e-2, 1e-3, 1e-4]:
+        for eps in eps_l:
             f = fe0 * (1 + eps * d)
             fe, ds, dh = orc.kbc_split(f)
             _, ga = orc.collide(f, beta, 0)
             errs.append(abs(ga - orc.gamma_exact(ds, dh, fe, beta)))
-        assert errs[2] < 0.2 * errs[0] + 1e-9
-        assert errs[2] < 1e-3
+        errs = np.array(errs)
+        slope = np.polyfit(np.log(eps_l), np.log(errs), 1)[0]
+        assert abs(slope - 1.0) < 0.05
+        c = errs / eps_l
+        assert abs(c[-1] - c[-2]) < 0.02 * c[-1]
+        assert errs[-1] < 1e-4
