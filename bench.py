@@ -1,25 +1,30 @@
 #!/usr/bin/env python
-"""Throughput of the entropic (KBC) D3Q27 step on the two-way coupled
-sedimenting-sphere workload: 128x128x256 box, sphere D = 16, no-slip x/y
-walls, periodic z, solid/fluid density ratio 1.5, gravity set from the
-terminal-velocity force balance for u_t = 0.04 (arXiv 1608.04658, Sec. 4.1).
+"""Throughput of the entropic (KBC) D3Q27 step on the deforming, self-propelled
+anguilliform swimmer (arXiv 1608.04658, Sec. 4.3): 768x256x256 periodic box,
+body length L = 128 (19,200-triangle mesh of elliptic cross sections), midline
+wave with period T = 4000 steps, free along the swimming direction, refill of
+uncovered nodes every step.  This is the largest of the paper's single-GPU
+configurations (50,331,648 nodes).
 
-One step = the whole hot path: body update, node marks and boundary list,
-refill, bulk stream+collide, Grad boundary + collide, momentum-exchange
-reduction.  The value is GLUPS over box nodes, FP32 storage; FP16 and BF16
-storage forms are reported under "variants".
+One step = the whole hot path: body update and mesh pose, node marks and
+boundary list, refill, bulk stream+collide, Grad boundary + collide,
+momentum-exchange reduction.  The value is GLUPS over box nodes, FP32
+storage; FP16 and BF16 storage and the exact stabilizer are reported under
+"variants", and the two-way coupled sedimenting sphere (128x128x256, Sec. 4.1)
+under "workloads" with the same measurement.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sphere|airfoil|swimmer|tgv] [--shape n]
+                    [--workload swimmer|sphere|airfoil|tgv] [--shape n]
 
---workload selects another of the paper's configurations for the same
-measurement: the plunging airfoil (1024x512x64, chord 128, Sec. 4.2), the
-self-propelled anguilliform swimmer (768x256x256, L = 128, Sec. 4.3) or the
-bodiless periodic Taylor-Green box (256^3, or n^3 with --shape n) that
-isolates the bulk kernel.
+--workload selects another of the paper's configurations for the main line:
+the sedimenting sphere, the plunging airfoil (1024x512x64, chord 128,
+Sec. 4.2) or the bodiless periodic Taylor-Green box (256^3, or n^3 with
+--shape n) that isolates the bulk kernel.
 
-The CPU baseline is the FP64 oracle on the host: one thread on the full box,
-and under "all_cores" one independent replica per host core.
+The CPU baseline is the FP64 oracle on the host: one thread, and under
+"all_cores" one independent replica per host core, on a bounded sample of
+the workload (the swimmer: one step of a 176x64x32 periodic crop around the
+whole body; the sphere: two steps of the full box).
 
 With N > 1 (torchrun) every rank runs an independent replica (the path has
 no data-parallel split without a halo exchange); the value is all ranks'
@@ -44,11 +49,11 @@ METRIC = "GLUPS & % of HBM roofline, D3Q27 entropic step (FP32 vs 16-bit); adjoi
 BYTES_PER_NODE = {"fp64": 432, "fp32": 216, "fp16": 108, "bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32", "bf16": "f32"}
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "bulk_kernel_sedimenting_sphere.md")
+PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = ["bulk.cu", "pull.cuh", "kbc.cuh", "lbm_internal.cuh"]
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -61,7 +66,9 @@ def parse_args():
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only); "
                          "n (or n,n,n) of the periodic Taylor-Green box (default 256)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv"])
+    ap.add_argument("--workload", default="swimmer", choices=["sphere", "airfoil", "swimmer", "tgv"])
+    ap.add_argument("--second-workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv", "none"],
+                    help="workload measured beside the main line, reported under 'workloads'")
     ap.add_argument("--accuracy-steps", type=int, default=2000,
                     help="steps of the FP64/FP32/FP16/BF16 sphere comparison (0 to skip it)")
     ap.add_argument("--adjoint-horizon", type=int, default=8000,
@@ -70,7 +77,7 @@ def parse_args():
                     help="checkpoint spacing of the adjoint measurement (0: ceil(sqrt(horizon)))")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint measurement and print it (profiling runs)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ----------------------------------------------------------------- distributed
@@ -197,24 +204,30 @@ def kernel_sha() -> str:
 
 
 def ncu_traffic(storage: str, workload_name: str):
-    """DRAM bytes per bulk launch from the committed ncu summary, or None when
-    the kernel sources changed since the capture or the summary was taken on
-    another workload."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    """DRAM bytes per bulk launch from a committed ncu summary
+    (profiles/bulk_kernel_*.md) taken on this workload with the current
+    kernel sources, else None."""
+    if not os.path.isdir(PROFILES):
         return None
-    sha, val, name = None, None, None
-    for line in open(PROFILE_SUMMARY):
-        line = line.strip().strip("`")
-        if line.startswith("source_sha:"):
-            sha = line.split(":", 1)[1].strip()
-        if line.startswith("traffic_workload:"):
-            name = line.split(":", 1)[1].strip()
-        if line.startswith(f"traffic_bytes_per_launch[{storage}]:"):
-            try:
-                val = float(line.split(":", 1)[1].strip())
-            except ValueError:
-                val = None
-    return val if sha == kernel_sha() and name == workload_name else None
+    sha_now = kernel_sha()
+    for fn in sorted(os.listdir(PROFILES)):
+        if not (fn.startswith("bulk_kernel_") and fn.endswith(".md")):
+            continue
+        sha, val, name = None, None, None
+        for line in open(os.path.join(PROFILES, fn)):
+            line = line.strip().strip("`")
+            if line.startswith("source_sha:"):
+                sha = line.split(":", 1)[1].strip()
+            if line.startswith("traffic_workload:"):
+                name = line.split(":", 1)[1].strip()
+            if line.startswith(f"traffic_bytes_per_launch[{storage}]:"):
+                try:
+                    val = float(line.split(":", 1)[1].strip())
+                except ValueError:
+                    val = None
+        if sha == sha_now and name == workload_name and val is not None:
+            return val
+    return None
 
 
 # ----------------------------------------------------------------- workload
@@ -273,6 +286,13 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     lat, np = make_lattice(storage, wl, device, gamma_mode)
     K, W = args.steps, args.warmup
     lat.step(W)
+    # the library times both launch orders in its first steps after
+    # lbm_set_geometry; finish that trial before the timed region, so every
+    # timed step runs the chosen order
+    extra = 0
+    while lat.launch_order() == "auto" and extra < 32:
+        lat.step(1)
+        extra += 1
     torch.cuda.synchronize()
     dist_barrier(world)
     torch.cuda.synchronize()
@@ -298,7 +318,8 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     F, _ = lat.forces()  # raises on an unstable run
     N = lat.N
     res = dict(ms=ms, glups=N * K * world / (ms * 1e-3) / 1e9, launches=launches,
-               bulk_ms=bulk_ms / max(nbulk, 1), bulk_nodes=bulk_nodes, body=body, F=F)
+               bulk_ms=bulk_ms / max(nbulk, 1), bulk_nodes=bulk_nodes, body=body, F=F,
+               order=lat.launch_order(), trial_steps_after_warmup=extra)
     lat.close()
     del lat
     torch.cuda.empty_cache()
@@ -306,20 +327,27 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
 
 
 def e2e_storage(storage, wl, args, device):
-    """Same workload through the public API with host buffers: the pinned FP64
-    state goes in, K steps run with the body force read back every step, and
-    the state comes out, all inside the timed region."""
-    import numpy as np
+    """Same workload through the public API from host memory: the initial
+    density and velocity fields (pinned FP64, 4 doubles per node) are copied to
+    the device and lbm_init_state builds the state from them, then K steps run
+    with every step's force, torque, time and status record (60 bytes) copied
+    to pinned host memory and read by the host at most two steps later; all of
+    it inside the timed region.  The lattice and its body are set up, and the
+    launch order chosen, before it."""
     import torch
     lat, _ = make_lattice(storage, wl, device)
-    nx, ny, nz = wl["shape"]
-    host_in = torch.empty((27, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    host_out = torch.empty((27, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    lat.populations(out=host_in)
+    lat.step(max(args.warmup, 1))
+    extra = 0
+    while lat.launch_order() == "auto" and extra < 32:
+        lat.step(1)
+        extra += 1
+    rho, u = initial_flow(wl)
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_u = torch.from_numpy(u).pin_memory()
     K = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat.set_populations(host_in)
+    lat.init_state(h_rho, h_u)
     # each step's force record is copied to pinned host memory while the
     # next steps are enqueued; the host reads it at most two steps later
     pending = []
@@ -330,19 +358,19 @@ def e2e_storage(storage, wl, args, device):
             lat.forces_wait(pending.pop(0))
     for tk in pending:
         lat.forces_wait(tk)
-    lat.populations(out=host_out)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     N = lat.N
     lat.close()
     del lat
     torch.cuda.empty_cache()
-    state = 27 * N * 8
+    h2d = h_rho.numel() * 8 + h_u.numel() * 8
     return {"value": round(N * K / t / 1e9, 4), "unit": "GLUPS",
-            "h2d_bytes_per_step": int(round(state / K)), "d2h_bytes_per_step": int(round(state / K + 60)),
-            "note": "pinned FP64 state in and out once per run (amortised); every step's force, torque, "
-                    "time and status (60 bytes) copied to pinned host memory and read by the host at most "
-                    "two steps later (lbm_body_forces_async / lbm_body_forces_wait)"}
+            "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60,
+            "note": "initial density and velocity fields (pinned FP64, 32 bytes per node) copied to the device and "
+                    "turned into the state by lbm_init_state once per run (amortised over the steps); every "
+                    "step's force, torque, time and status (60 bytes) copied to pinned host memory and read by "
+                    "the host at most two steps later (lbm_body_forces_async / lbm_body_forces_wait)"}
 
 
 def oracle_body(wl):
@@ -438,58 +466,83 @@ def accuracy_bench(args, device):
     return out
 
 
-def cpu_baseline(wl, nsteps=None):
-    """The FP64 oracle, single-threaded, on the full box of the workload
-    (2 steps of the sphere box, 1 step of the larger boxes)."""
+def cpu_sample(wl):
+    """Bounded sample of a workload for the FP64 oracle on the host:
+    (workload of the sample, steps, description).  The swimmer's sample is one
+    step of a periodic crop around the whole body (same mesh, kinematics and
+    viscosity; the oracle's brute-force mesh geometry costs about as much as
+    the crop's bulk nodes); the sphere's two steps and the other boxes' one
+    step of the full box."""
+    if wl["kind"] == "swimmer":
+        import synth
+        L = wl["L"]
+        shape = (int(round(L)) + 48, 2 * int(math.ceil(0.165 * L)) + 20, 2 * int(math.ceil(0.08 * L)) + 10)
+        head = (16.137, shape[1] / 2 + 0.371, shape[2] / 2 + 0.293)
+        smp = synth.anguilliform_swimmer(shape=shape, L=L, period=wl["period"], amp=wl["amp"],
+                                         wavelength=wl["wavelength"], ramp=bool(wl["ramp"]), head=head)
+        smp["kind"] = "swimmer"
+        return smp, 1, (f"one step of a {shape[0]}x{shape[1]}x{shape[2]} periodic crop around the whole "
+                        f"swimmer (same mesh, kinematics and viscosity)")
+    n = 2 if wl["kind"] == "sphere" else 1
+    nx, ny, nz = wl["shape"]
+    return wl, n, f"{n} step(s) of the full {nx}x{ny}x{nz} box"
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle, single-threaded, on the bounded sample of the
+    workload (cpu_sample)."""
     import oracle
-    shape = wl["shape"]
-    if nsteps is None:
-        nsteps = 2 if wl["kind"] == "sphere" else 1
-    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"], u_face=wl.get("u_face", (0.0, 0.0, 0.0)),
-                        body=oracle_body(wl))
-    orc.init_state(*initial_flow(wl))
+    smp, nsteps, desc = cpu_sample(wl)
+    shape = smp["shape"]
+    orc = oracle.Oracle(shape, nu=smp["nu"], faces=smp["faces"], u_face=smp.get("u_face", (0.0, 0.0, 0.0)),
+                        body=oracle_body(smp))
+    orc.init_state(*initial_flow(smp))
     t0 = time.perf_counter()
     orc.step(nsteps)
     t = time.perf_counter() - t0
     n = shape[0] * shape[1] * shape[2]
     return {"value": n * nsteps / t / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} steps of the full {shape[0]}x{shape[1]}x{shape[2]} box, FP64, one thread",
-            "seconds": round(t, 2)}
+            "sample": desc + ", FP64, one thread", "seconds": round(t, 2)}
 
 
-def _oracle_replica(wl, nsteps, barrier, out):
+def _oracle_replica(wl, nsteps, barrier, out, warm=0):
     """One independent FP64 oracle replica of the workload, in a spawned
-    process: set up, wait for the others, time its steps."""
+    process: set up, run `warm` untimed steps, wait for the others, time its
+    steps."""
     import oracle
     orc = oracle.Oracle(wl["shape"], nu=wl["nu"], faces=wl["faces"], u_face=wl.get("u_face", (0.0, 0.0, 0.0)),
                         body=oracle_body(wl))
     orc.init_state(*initial_flow(wl))
+    if warm:
+        orc.step(warm)
     barrier.wait(timeout=900)
     t0 = time.perf_counter()
     orc.step(nsteps)
     out.put((t0, time.perf_counter()))
 
 
-def cpu_baseline_all_cores(wl, nsteps=1, procs=None):
-    """The same oracle on every host core the process may use: one
-    independent single-threaded replica of the full box per core (the oracle
-    has no threads of its own), started together; the value is all replicas'
-    node updates over the span from the first start to the last finish.
-    Replicas are capped so that their buffers (about 650 bytes per node each)
-    fit in half of the free host memory."""
-    import multiprocessing as mp
+def _replica_cap(wl, cores):
+    """Replicas whose buffers (about 650 bytes per node each) fit in half of
+    the free host memory, at most one per core."""
     nx, ny, nz = wl["shape"]
-    n = nx * ny * nz
-    cores = len(os.sched_getaffinity(0))
-    if procs is None:
-        free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
-        procs = max(1, min(cores, int(0.5 * free // (650 * n))))
+    free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    return max(1, min(cores, int(0.5 * free // (650 * nx * ny * nz))))
+
+
+def _run_replicas(wl, steps_each, warm_each=None):
+    """Starts one spawned oracle process per entry of steps_each, together
+    behind a barrier; returns the span from the first timed start to the last
+    finish."""
+    import multiprocessing as mp
+    import queue
+    procs = len(steps_each)
+    warm_each = warm_each or [0] * procs
     ctx = mp.get_context("spawn")   # the parent may hold a CUDA context
     barrier, out = ctx.Barrier(procs), ctx.Queue()
-    ps = [ctx.Process(target=_oracle_replica, args=(wl, nsteps, barrier, out)) for _ in range(procs)]
+    ps = [ctx.Process(target=_oracle_replica, args=(wl, steps_each[k], barrier, out, warm_each[k]))
+          for k in range(procs)]
     for p in ps:
         p.start()
-    import queue
     spans, deadline = [], time.monotonic() + 1800
     try:
         while len(spans) < procs:
@@ -505,10 +558,27 @@ def cpu_baseline_all_cores(wl, nsteps=1, procs=None):
             if p.is_alive():
                 p.terminate()
                 p.join(timeout=10)
-    t = max(b for _, b in spans) - min(a for a, _ in spans)
+    return max(b for _, b in spans) - min(a for a, _ in spans)
+
+
+def cpu_baseline_all_cores(wl, nsteps=None, procs=None):
+    """The same oracle on every host core the process may use: one
+    independent single-threaded replica of the workload's bounded sample per
+    core (the oracle has no threads of its own), started together; the value
+    is all replicas' node updates over the span from the first start to the
+    last finish.  Replicas are capped so that their buffers fit in half of the
+    free host memory."""
+    smp, n_default, desc = cpu_sample(wl)
+    nsteps = n_default if nsteps is None else nsteps
+    nx, ny, nz = smp["shape"]
+    n = nx * ny * nz
+    cores = len(os.sched_getaffinity(0))
+    if procs is None:
+        procs = _replica_cap(smp, cores)
+    t = _run_replicas(smp, [nsteps] * procs)
     return {"value": procs * n * nsteps / t / 1e9, "unit": "GLUPS", "cores": procs, "kind": "oracle",
-            "sample": f"{procs} independent replicas (one process each) of {nsteps} step(s) of the full "
-                      f"{nx}x{ny}x{nz} box, FP64, started together",
+            "sample": f"{procs} independent replicas (one process each) of {nsteps} step(s) of the "
+                      f"{nx}x{ny}x{nz} sample ({desc}), FP64, started together",
             "seconds": round(t, 2)}
 
 
@@ -540,6 +610,11 @@ def run_ours(args):
         # the exact stabilizer (root of Eq. gamma_min per node) instead of the analytic one
         variants[args.storage + "_exact_gamma"] = time_storage(args.storage, wl, args, world, device, clocks,
                                                                gamma_mode=1)
+    second = {}
+    if args.second_workload != "none" and args.second_workload != args.workload:
+        wl2 = workload(None, args.second_workload)
+        second[wl2["name"]] = (wl2, {st: time_storage(st, wl2, args, world, device, clocks)
+                                     for st in (["fp32", "fp16", "bf16"] if not args.no_variants else ["fp32"])})
     adj = adjoint_bench(args, world, device) if args.adjoint_horizon > 0 else None
     acc = accuracy_bench(args, device) if args.accuracy_steps > 0 and rank == 0 else None
     clk = clocks.stop()
@@ -555,11 +630,11 @@ def run_ours(args):
         return
     peak, peak_kind = measured_hbm_peak()
 
-    def roofline(st, r, captured=True):
+    def roofline(st, r, captured=True, name=wl["name"]):
         bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
         achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
         # the committed counters are those of the analytic-stabilizer kernel
-        tr = ncu_traffic(st, wl["name"]) if captured else None
+        tr = ncu_traffic(st, name) if captured else None
         return {"bound": "hbm", "kernel": "bulk_kernel", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch,
@@ -580,7 +655,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (population buffers %d MB each)"
                          % (27 * N * (BYTES_PER_NODE[args.storage] // 54) // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "boundary_nodes": main["body"]["n_boundary"], "links": main["body"]["n_links"]},
+                   "boundary_nodes": main["body"]["n_boundary"], "links": main["body"]["n_links"],
+                   "launch_order": main["order"],
+                   "trial_steps_after_warmup": main["trial_steps_after_warmup"]},
         "roofline": roofline(args.storage, main),
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -595,42 +672,46 @@ def run_ours(args):
                           "roofline": roofline(st.split("_")[0], r, captured=st in BYTES_PER_NODE),
                           "gpu_launches": r["launches"]}
                      for st, r in variants.items()},
+        "workloads": {name: {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],
+                                  "ms_per_step": round(r["ms"] / args.steps, 5),
+                                  "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st]
+                                                                        / world / peak, 2),
+                                  "roofline": roofline(st, r, name=name), "gpu_launches": r["launches"],
+                                  "launch_order": r["order"]}
+                             for st, r in res.items()}
+                      for name, (w2, res) in second.items()},
     }
     print(json.dumps(line))
 
 
 def run_reference(args):
-    """The FP64 oracle as the reference arm: each step is one oracle step of a
-    bounded sub-box of the workload (same physics, sphere D = 16), sized so the
-    whole run stays within a few minutes on one host core."""
+    """The FP64 oracle as the reference arm, on the host cores: the K timed
+    steps are oracle steps of the workload's bounded sample (cpu_sample),
+    shared out over one process per core (at most K, capped by host memory),
+    each of which first runs its share of the W warm-up steps; the value is
+    all timed node updates over the span from the first timed start to the
+    last finish."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    import synth
-    wl = workload()
-    total = args.steps + args.warmup
-    budget_nodes = 1.0e8  # node updates for the whole run
-    side = int(max(24, min(128, round((budget_nodes / max(total, 1)) ** (1 / 3)))))
-    shape = (side, side, side)
-    X = (side / 2 - 0.5 + 0.123, side / 2 - 0.5 + 0.0567, side / 2 + 0.311)
-    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
-                        body=oracle.sphere_body(X, wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
-    orc.init_state(*synth.uniform_fields(shape))
-    orc.step(args.warmup)
-    t0 = time.perf_counter()
-    orc.step(args.steps)
-    t = time.perf_counter() - t0
-    n = side ** 3
-    v = n * args.steps / t / 1e9
+    wl = workload(args.shape, args.workload)
+    smp, _, desc = cpu_sample(wl)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    P = min(_replica_cap(smp, len(os.sched_getaffinity(0))), K)
+    shares = [K // P + (1 if k < K % P else 0) for k in range(P)]
+    warm = [-(-W // P)] * P
+    t = _run_replicas(smp, shares, warm)
+    nx, ny, nz = smp["shape"]
+    v = nx * ny * nz * K / t / 1e9
+    sample = (f"{desc}; the {K} timed steps shared out over {P} single-threaded processes started together "
+              f"(each after {warm[0]} untimed warm-up step(s)), FP64")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["name"], "sample_box": list(shape)},
-        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{side}^3 sub-box of the workload (walls x/y, periodic z, sphere D=16) per step"},
+        "config": {"workload": wl["name"], "sample_box": list(smp["shape"]), "processes": P},
+        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": P, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }))

@@ -287,14 +287,19 @@ class Lattice:
     # -------------------------------------------------------------- state
     def init_state(self, rho, u, xi=None, amp: float = 0.0):
         """f = f^eq(rho, u) + amp W xi on the device.  rho (nz,ny,nx), u (nz,ny,nx,3),
-        xi (27,nz,ny,nx) or None; numpy or torch."""
+        xi (27,nz,ny,nx) or None; numpy arrays or torch tensors (host tensors in
+        pinned memory are copied asynchronously on the lattice's stream)."""
         torch = _torch()
         dev = self.device
-        t_rho = torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64)).to(dev).contiguous()
-        t_u = torch.as_tensor(np.ascontiguousarray(u, dtype=np.float64)).to(dev).contiguous()
-        t_xi = None
-        if xi is not None:
-            t_xi = torch.as_tensor(np.ascontiguousarray(xi, dtype=np.float64)).to(dev).contiguous()
+
+        def to_dev(a):
+            if torch.is_tensor(a):
+                return a.to(device=dev, dtype=torch.float64, non_blocking=True).contiguous()
+            return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev).contiguous()
+
+        with torch.cuda.stream(self.stream):
+            t_rho, t_u = to_dev(rho), to_dev(u)
+            t_xi = to_dev(xi) if xi is not None else None
         self.stream.synchronize()
         self._check(lib().lbm_init_state(self._ctx, t_rho.data_ptr(), t_u.data_ptr(),
                                          t_xi.data_ptr() if t_xi is not None else None, float(amp)))

@@ -127,6 +127,10 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     L.rho0 = p->rho0;
     for (int a = 0; a < 3; ++a) L.u_face[a] = p->u_face[a];
     face_equilibrium(p->rho0, p->u_face, L.g_face);
+    L.beta_f = (float)L.beta;
+    L.inv_beta_f = (float)L.inv_beta;
+    L.rho0_f = (float)L.rho0;
+    for (int i = 0; i < Q; ++i) L.g_face_f[i] = (float)L.g_face[i];
     ctx->storage = p->storage;
     ctx->elem = es;
     ctx->f[0] = f_a;

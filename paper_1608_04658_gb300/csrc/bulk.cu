@@ -23,7 +23,31 @@ namespace lbm {
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
 
-template <typename S, bool EXACT>
+// Resident blocks per SM asked of the register allocator for the two-node
+// kernel (64 threads, 128 nodes per block): 6 (166 registers, no spill) for
+// FP32 storage, 7 (128 registers, a 160-byte spill) for 16-bit storage,
+// each the faster on GB300 for its storage (swimmer box: FP32 0.88 vs 0.84,
+// FP16 0.57 vs 0.54 of the copy bandwidth).
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 6
+#endif
+#ifndef LBM_PAIR_MIN_BLOCKS_16
+#define LBM_PAIR_MIN_BLOCKS_16 7
+#endif
+template <typename S>
+struct PairBlocks {
+    static constexpr int value = sizeof(S) == 2 ? LBM_PAIR_MIN_BLOCKS_16 : LBM_PAIR_MIN_BLOCKS;
+};
+// FP32 storage takes the two-node kernel too (0: the one-node kernel with the
+// same arithmetic)
+#ifndef LBM_PAIR_FP32
+#define LBM_PAIR_FP32 1
+#endif
+
+// VMATH: the collision with explicit FP32 operations (kbc_collide_v), which
+// the two-node kernel shares bit for bit; otherwise kbc_collide (FP64
+// storage, exact stabilizer).
+template <typename S, bool EXACT, bool VMATH>
 __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const Lattice L, const S *__restrict__ fa,
                                                    S *__restrict__ fb,
                                                    const uint8_t *__restrict__ flags,
@@ -61,11 +85,60 @@ __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const La
     // the node itself and are replaced afterwards)
     R g[Q];
     gather_global<S>(L, fa, x, y, z, n, g);
-    const bool ok = kbc_collide<R, EXACT>(g, (R)L.beta, (R)L.inv_beta, (R)L.rho0, L.gamma_mode);
+    bool ok;
+    if constexpr (VMATH) ok = kbc_collide_v<F1>(g, L.beta_f, L.inv_beta_f, L.rho0_f, L.gamma_mode) & 1;
+    else ok = kbc_collide<R, EXACT>(g, (R)L.beta, (R)L.inv_beta, (R)L.rho0, L.gamma_mode);
     if (!ok) atomicOr(status, ST_UNSTABLE);
     S *q = fb + n;
 #pragma unroll
     for (int i = 0; i < Q; ++i) Codec<S>::store(q + L.plane[i], g[i]);
+}
+
+// Two nodes per thread, (x0, x0 + 1) with x0 even, for even nx: each pull
+// is an aligned word of the pair (two for c_x = +-1), the collision runs on
+// both nodes in packed FP32x2 arithmetic, each store writes the pair's word.
+// Node selection as in bulk_kernel (ALL or OUTSIDE; the sweep box takes the
+// one-node kernel), per node of the pair.
+template <typename S>
+__global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(const Lattice L,
+                                                                           const S *__restrict__ fa,
+                                                                           S *__restrict__ fb,
+                                                                           const uint8_t *__restrict__ flags,
+                                                                           int *__restrict__ status,
+                                                                           const int *__restrict__ sweep, int mode)
+{
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x0 >= L.nx) return;
+    int act = 3;  // bit 0: node x0 is updated here, bit 1: node x0 + 1
+    if (mode == BULK_OUTSIDE && in_sweep(sweep, 1, y, L.ny, L.face[2] == LBM_FACE_PERIODIC) &&
+        in_sweep(sweep, 2, z, L.nz, L.face[4] == LBM_FACE_PERIODIC)) {
+        const bool per = L.face[0] == LBM_FACE_PERIODIC;
+        act = (in_sweep(sweep, 0, x0, L.nx, per) ? 0 : 1) | (in_sweep(sweep, 0, x0 + 1, L.nx, per) ? 0 : 2);
+        if (!act) return;
+    }
+    const int n0 = x0 + L.nx * (y + L.ny * z);
+    if (flags != nullptr) {
+        const unsigned fw = *reinterpret_cast<const unsigned short *>(flags + n0);
+        if (fw & (FL_SOLID | FL_BOUNDARY)) act &= ~1;
+        if ((fw >> 8) & (FL_SOLID | FL_BOUNDARY)) act &= ~2;
+        if (!act) return;
+    }
+    float2 g[Q];
+    gather_pair<S>(L, fa, x0, y, z, n0, g);
+    const int ok = kbc_collide_v<F2>(g, L.beta_f, L.inv_beta_f, L.rho0_f, L.gamma_mode);
+    if (act & ~ok) atomicOr(status, ST_UNSTABLE);
+    S *q = fb + n0;
+    if (act == 3) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Pair<S>::store(q + L.plane[i], g[i]);
+    } else if (act == 1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Codec<S>::store(q + L.plane[i], g[i].x);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Codec<S>::store(q + 1 + L.plane[i], g[i].y);
+    }
 }
 
 template <typename S>
@@ -175,12 +248,26 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
             const long long vol = (long long)cap[0] * cap[1] * cap[2];
             grid = dim3((unsigned)((vol + bx - 1) / bx), 1, 1);
         }
-        // the exact stabilizer is a separate instance, so the analytic kernel
-        // keeps its registers and code size
-        if (L.gamma_mode == LBM_GAMMA_EXACT)
-            bulk_kernel<S, true><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode, capx, capy);
-        else
-            bulk_kernel<S, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode, capx, capy);
+        // the exact stabilizer and FP64 storage keep kbc_collide; FP32 and
+        // 16-bit storage with the analytic (or LBGK) stabilizer take the
+        // explicit-operation collision, in the two-node kernel where the row
+        // length allows (every node gets the same bits either way)
+        constexpr bool VM = !std::is_same<S, double>::value;
+        constexpr bool PAIR = VM && (LBM_PAIR_FP32 || !std::is_same<S, float>::value);
+        if (L.gamma_mode == LBM_GAMMA_EXACT) {
+            bulk_kernel<S, true, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode,
+                                                            capx, capy);
+            return cudaGetLastError();
+        }
+        if constexpr (PAIR) {
+            if (mode != BULK_BAND && (L.nx & 1) == 0) {
+                const dim3 g2((L.nx + 127) / 128, L.ny, L.nz);
+                bulk_pair_kernel<S><<<g2, 64, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode);
+                return cudaGetLastError();
+            }
+        }
+        bulk_kernel<S, false, VM><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode,
+                                                      capx, capy);
         return cudaGetLastError();
     });
 }

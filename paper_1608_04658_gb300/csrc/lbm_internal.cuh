@@ -84,6 +84,10 @@ struct Lattice {
     double rho0;
     double u_face[3];
     double g_face[27];  // f^eq(rho0, u_face) - W rho0 for EQ faces
+    // the same parameters rounded once to FP32 for the FP32 arithmetic of the
+    // bulk kernels (no FP64 conversion on the device)
+    float beta_f, inv_beta_f, rho0_f;
+    float g_face_f[27];
 };
 
 // Which nodes one bulk launch updates.  ALL: every node (those flagged SOLID

@@ -3,7 +3,7 @@
 // its adjoint.
 #pragma once
 
-#include "kbc.cuh"
+#include "kbcv.cuh"
 
 namespace lbm {
 
@@ -105,6 +105,104 @@ __device__ __forceinline__ void gather_global(const Lattice &L, const S *__restr
                         else g[i] = (R)L.g_face[i];
                     }
                 }
+    }
+}
+
+// The pulls of one node, as gather_global, written into lane H (0: x, 1: y)
+// of the float2 populations of a node pair (the pair's node at an x face).
+template <typename S, int H>
+__device__ __forceinline__ void gather_node_lane(const Lattice &L, const S *__restrict__ fa, int x, int y, int z,
+                                                 int n, float2 g[Q])
+{
+    int ox[3], oy[3], oz[3], kx[3], ky[3], kz[3];
+    axis_off(x, L.nx, 1, L.face[0], L.face[1], ox, kx);
+    axis_off(y, L.ny, L.nx, L.face[2], L.face[3], oy, ky);
+    axis_off(z, L.nz, L.nx * L.ny, L.face[4], L.face[5], oz, kz);
+    const S *p = fa + n;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int k = max(kx[cx_of(i) + 1], max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]));
+        const float v = k == 2 ? (float)Codec<S>::load(p + L.plane[26 - i])
+                      : k == 1 ? L.g_face_f[i]
+                               : (float)Codec<S>::load(p + (L.plane[i] + ox[cx_of(i) + 1] + oy[cy_of(i) + 1] +
+                                                            oz[cz_of(i) + 1]));
+        if (H) g[i].y = v;
+        else g[i].x = v;
+    }
+}
+
+// Storage word of two consecutive nodes along x: FP32 as float2 (8 bytes),
+// 16-bit as a 4-byte pair; cross(a, b) is the pair (second node of a, first
+// node of b).  The word address is even in nodes (n even, every plane and
+// row offset even when nx is even), so these are aligned vector accesses.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    using W = float2;
+    __device__ static W load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static W cross(W a, W b) { return make_float2(a.y, b.x); }
+    __device__ static float2 unpack(W w) { return w; }
+    __device__ static void store(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <> struct Pair<__half> {
+    using W = __half2;
+    __device__ static W load(const __half *p) { return *reinterpret_cast<const __half2 *>(p); }
+    __device__ static W cross(W a, W b) { return __halves2half2(__high2half(a), __low2half(b)); }
+    __device__ static float2 unpack(W w) { return __half22float2(w); }
+    __device__ static void store(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using W = __nv_bfloat162;
+    __device__ static W load(const __nv_bfloat16 *p) { return *reinterpret_cast<const __nv_bfloat162 *>(p); }
+    __device__ static W cross(W a, W b) { return __halves2bfloat162(__high2bfloat16(a), __low2bfloat16(b)); }
+    __device__ static float2 unpack(W w) { return __bfloat1622float2(w); }
+    __device__ static void store(__nv_bfloat16 *p, float2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
+
+// Pulls of the node pair (x0, x0 + 1), x0 even, nx even: per direction the
+// source word of the pair for c_x = 0, and for c_x = +-1 the pair assembled
+// from two aligned words of the source row (x0 - 2 | x0 and x0 | x0 + 2,
+// wrapped on a periodic x axis).  y and z faces are uniform over the pair
+// (and over the thread block); a node on a non-periodic x face is gathered
+// again on its own.
+template <typename S>
+__device__ __forceinline__ void gather_pair(const Lattice &L, const S *__restrict__ fa, int x0, int y, int z,
+                                            int n0, float2 g[Q])
+{
+    using P = Pair<S>;
+    int oy[3], oz[3], ky[3], kz[3];
+    axis_off(y, L.ny, L.nx, L.face[2], L.face[3], oy, ky);
+    axis_off(z, L.nz, L.nx * L.ny, L.face[4], L.face[5], oz, kz);
+    const bool xper = L.face[0] == LBM_FACE_PERIODIC;
+    // offsets of the words left and right of the pair; at a non-periodic x
+    // face any word of the row will do (that node is gathered again below)
+    int xl = -2, xr = 2;
+    if (x0 == 0) xl = xper ? L.nx - 2 : 0;
+    if (x0 + 2 >= L.nx) xr = xper ? 2 - L.nx : 0;
+    const S *p = fa + n0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i);
+        const S *q = p + (L.plane[i] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1]);
+        const typename P::W w = P::load(q);
+        if (cx == 0) g[i] = P::unpack(w);
+        else if (cx > 0) g[i] = P::unpack(P::cross(P::load(q + xl), w));   // sources x0 - 1, x0
+        else g[i] = P::unpack(P::cross(w, P::load(q + xr)));               // sources x0 + 1, x0 + 2
+    }
+    if (ky[0] | ky[2] | kz[0] | kz[2]) {
+        // a y or z face: walls win over equilibrium faces
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int k = max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]);
+            if (k == 2) g[i] = P::unpack(P::load(p + L.plane[26 - i]));
+            else if (k == 1) g[i] = make_float2(L.g_face_f[i], L.g_face_f[i]);
+        }
+    }
+    if (!xper) {
+        if (x0 == 0) gather_node_lane<S, 0>(L, fa, 0, y, z, n0, g);
+        if (x0 + 1 == L.nx - 1) gather_node_lane<S, 1>(L, fa, L.nx - 1, y, z, n0 + 1, g);
     }
 }
 

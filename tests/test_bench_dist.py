@@ -82,7 +82,9 @@ def test_reference_arm_prints_one_line_on_rank_zero_only(orc):
     import json
     r1 = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
     assert r1.returncode == 0 and r1.stdout.strip() == ""
-    r0 = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "0", "WORLD_SIZE": "1"})
+    # the sphere box keeps this CPU test short; the swimmer's sample is checked below
+    r0 = _bench(["--impl", "reference", "--workload", "sphere", "--steps", "2", "--warmup", "1"],
+                {"RANK": "0", "WORLD_SIZE": "1"})
     assert r0.returncode == 0, r0.stderr[-2000:]
     lines = [s for s in r0.stdout.splitlines() if s.strip()]
     assert len(lines) == 1
@@ -94,6 +96,30 @@ def test_reference_arm_prints_one_line_on_rank_zero_only(orc):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "sedimenting_sphere_128x128x256_D16"
+    assert d["steps"] == 2 and d["warmup"] == 1 and 1 <= d["config"]["processes"] <= 2
+
+
+def test_headline_workload_and_its_oracle_sample():
+    """The main line measures the largest configuration, the swimmer in
+    768x256x256; the oracle's sample of it is a periodic crop holding the whole
+    body with the same mesh, kinematics and viscosity."""
+    import bench
+    args = bench.parse_args([])
+    assert args.workload == "swimmer" and args.second_workload == "sphere"
+    wl = bench.workload(None, "swimmer")
+    assert wl["shape"] == (768, 256, 256)
+    smp, n, desc = bench.cpu_sample(wl)
+    assert smp["shape"] == (176, 64, 32) and n == 1 and "crop" in desc
+    for k in ("L", "period", "amp", "wavelength", "nu", "mass", "faces"):
+        assert smp[k] == wl[k], k
+    assert (smp["rest"] == wl["rest"]).all() and (smp["tris"] == wl["tris"]).all()
+    # the body (head at X, length L along +x, tail amplitude 0.125 L, half
+    # width 0.04 L, half height 0.08 L) stays two nodes clear of every face
+    X, L = smp["X"], smp["L"]
+    nx, ny, nz = smp["shape"]
+    assert X[0] - 2 > 0 and X[0] + L + 2 < nx
+    assert X[1] - 0.165 * L - 2 > 0 and X[1] + 0.165 * L + 2 < ny
+    assert X[2] - 0.08 * L - 2 > 0 and X[2] + 0.08 * L + 2 < nz
 
 
 def test_clock_sampler_reads_the_timed_window_and_its_throttle_reasons(tmp_path):
