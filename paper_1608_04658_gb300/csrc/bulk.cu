@@ -9,6 +9,7 @@
 // the boundary kernel.  With a body, one launch takes the nodes outside the
 // body's sweep box (no flag read) while the body's geometry runs beside it,
 // and a second the nodes of the box once their marks are known.
+#include <algorithm>
 #include <type_traits>
 
 #include "pull.cuh"
@@ -98,23 +99,17 @@ __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const La
 // is an aligned word of the pair (two for c_x = +-1), the collision runs on
 // both nodes in packed FP32x2 arithmetic, each store writes the pair's word.
 // Node selection as in bulk_kernel (ALL or OUTSIDE; the sweep box takes the
-// one-node kernel), per node of the pair.
-template <typename S>
-__global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(const Lattice L,
-                                                                           const S *__restrict__ fa,
-                                                                           S *__restrict__ fb,
-                                                                           const uint8_t *__restrict__ flags,
-                                                                           int *__restrict__ status,
-                                                                           const int *__restrict__ sweep, int mode)
+// one-node kernel), per node of the pair.  XPER: the x axis is periodic;
+// YZPER: the y and z axes are.
+template <typename S, bool XPER, bool YZPER>
+__device__ __forceinline__ void pair_update(const Lattice &L, const S *__restrict__ fa, S *__restrict__ fb,
+                                            const uint8_t *__restrict__ flags, int *__restrict__ status,
+                                            const int *__restrict__ sweep, int mode, int x0, int y, int z)
 {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x0 >= L.nx) return;
     int act = 3;  // bit 0: node x0 is updated here, bit 1: node x0 + 1
     if (mode == BULK_OUTSIDE && in_sweep(sweep, 1, y, L.ny, L.face[2] == LBM_FACE_PERIODIC) &&
         in_sweep(sweep, 2, z, L.nz, L.face[4] == LBM_FACE_PERIODIC)) {
-        const bool per = L.face[0] == LBM_FACE_PERIODIC;
-        act = (in_sweep(sweep, 0, x0, L.nx, per) ? 0 : 1) | (in_sweep(sweep, 0, x0 + 1, L.nx, per) ? 0 : 2);
+        act = (in_sweep(sweep, 0, x0, L.nx, XPER) ? 0 : 1) | (in_sweep(sweep, 0, x0 + 1, L.nx, XPER) ? 0 : 2);
         if (!act) return;
     }
     const int n0 = x0 + L.nx * (y + L.ny * z);
@@ -125,7 +120,7 @@ __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(con
         if (!act) return;
     }
     float2 g[Q];
-    gather_pair<S>(L, fa, x0, y, z, n0, g);
+    gather_pair<S, XPER, YZPER>(L, fa, x0, y, z, n0, g);
     const int ok = kbc_collide_v<F2>(g, L.beta_f, L.inv_beta_f, L.rho0_f, L.gamma_mode);
     if (act & ~ok) atomicOr(status, ST_UNSTABLE);
     S *q = fb + n0;
@@ -139,6 +134,20 @@ __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(con
 #pragma unroll
         for (int i = 0; i < Q; ++i) Codec<S>::store(q + 1 + L.plane[i], g[i].y);
     }
+}
+
+// One block per 128 nodes of a row.
+template <typename S, bool XPER, bool YZPER>
+__global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(const Lattice L,
+                                                                           const S *__restrict__ fa,
+                                                                           S *__restrict__ fb,
+                                                                           const uint8_t *__restrict__ flags,
+                                                                           int *__restrict__ status,
+                                                                           const int *__restrict__ sweep, int mode)
+{
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= L.nx) return;
+    pair_update<S, XPER, YZPER>(L, fa, fb, flags, status, sweep, mode, x0, blockIdx.y, blockIdx.z);
 }
 
 template <typename S>
@@ -261,8 +270,14 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
         }
         if constexpr (PAIR) {
             if (mode != BULK_BAND && (L.nx & 1) == 0) {
+                const int kind = (L.face[0] == LBM_FACE_PERIODIC ? 1 : 0) +
+                                 (L.face[2] == LBM_FACE_PERIODIC && L.face[4] == LBM_FACE_PERIODIC ? 2 : 0);
+                auto kernel = kind == 3 ? bulk_pair_kernel<S, true, true>
+                            : kind == 2 ? bulk_pair_kernel<S, false, true>
+                            : kind == 1 ? bulk_pair_kernel<S, true, false>
+                                        : bulk_pair_kernel<S, false, false>;
                 const dim3 g2((L.nx + 127) / 128, L.ny, L.nz);
-                bulk_pair_kernel<S><<<g2, 64, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode);
+                kernel<<<g2, 64, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode);
                 return cudaGetLastError();
             }
         }

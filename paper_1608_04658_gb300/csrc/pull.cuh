@@ -161,13 +161,21 @@ template <> struct Pair<__nv_bfloat16> {
     }
 };
 
-// Pulls of the node pair (x0, x0 + 1), x0 even, nx even: per direction the
-// source word of the pair for c_x = 0, and for c_x = +-1 the pair assembled
-// from two aligned words of the source row (x0 - 2 | x0 and x0 | x0 + 2,
-// wrapped on a periodic x axis).  y and z faces are uniform over the pair
-// (and over the thread block); a node on a non-periodic x face is gathered
-// again on its own.
-template <typename S>
+// Pulls of the node pair (x0, x0 + 1), x0 even, nx even.  Every load of the
+// pair is issued in one pass with addresses chosen by selects (a branch there
+// would hold back the later loads until the earlier ones return).
+//   XPER and YZPER (periodic box): per direction the source word of the pair
+//   for c_x = 0, and for c_x = +-1 the pair assembled from two aligned words
+//   of the source row (x0 - 2 | x0 and x0 | x0 + 2, wrapped around the row).
+//   Otherwise: the source word at x0 and, for c_x = +-1, the outer node as a
+//   single element: x0 - 1 or x0 + 2 inside the row, and at an x face the
+//   wrapped node (periodic), the node's own opposite population (wall) or the
+//   clamped source (outflow).  y and z faces, uniform over the pair's row,
+//   are applied after the loads: a wall takes the pair's own opposite word
+//   (loaded then), an equilibrium face its value.  A node on an equilibrium x
+//   face, or on an x wall of a row with an equilibrium y or z face, is
+//   gathered again on its own.
+template <typename S, bool XPER, bool YZPER>
 __device__ __forceinline__ void gather_pair(const Lattice &L, const S *__restrict__ fa, int x0, int y, int z,
                                             int n0, float2 g[Q])
 {
@@ -175,34 +183,63 @@ __device__ __forceinline__ void gather_pair(const Lattice &L, const S *__restric
     int oy[3], oz[3], ky[3], kz[3];
     axis_off(y, L.ny, L.nx, L.face[2], L.face[3], oy, ky);
     axis_off(z, L.nz, L.nx * L.ny, L.face[4], L.face[5], oz, kz);
-    const bool xper = L.face[0] == LBM_FACE_PERIODIC;
-    // offsets of the words left and right of the pair; at a non-periodic x
-    // face any word of the row will do (that node is gathered again below)
-    int xl = -2, xr = 2;
-    if (x0 == 0) xl = xper ? L.nx - 2 : 0;
-    if (x0 + 2 >= L.nx) xr = xper ? 2 - L.nx : 0;
     const S *p = fa + n0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i);
-        const S *q = p + (L.plane[i] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1]);
-        const typename P::W w = P::load(q);
-        if (cx == 0) g[i] = P::unpack(w);
-        else if (cx > 0) g[i] = P::unpack(P::cross(P::load(q + xl), w));   // sources x0 - 1, x0
-        else g[i] = P::unpack(P::cross(w, P::load(q + xr)));               // sources x0 + 1, x0 + 2
-    }
-    if (ky[0] | ky[2] | kz[0] | kz[2]) {
-        // a y or z face: walls win over equilibrium faces
+    if constexpr (XPER && YZPER) {
+        const int xl = x0 == 0 ? L.nx - 2 : -2, xr = x0 + 2 >= L.nx ? 2 - L.nx : 2;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int k = max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]);
-            if (k == 2) g[i] = P::unpack(P::load(p + L.plane[26 - i]));
-            else if (k == 1) g[i] = make_float2(L.g_face_f[i], L.g_face_f[i]);
+            const int cx = cx_of(i);
+            const S *q = p + (L.plane[i] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1]);
+            const typename P::W w = P::load(q);
+            if (cx == 0) g[i] = P::unpack(w);
+            else if (cx > 0) g[i] = P::unpack(P::cross(P::load(q + xl), w));   // sources x0 - 1, x0
+            else g[i] = P::unpack(P::cross(w, P::load(q + xr)));               // sources x0 + 1, x0 + 2
         }
-    }
-    if (!xper) {
-        if (x0 == 0) gather_node_lane<S, 0>(L, fa, 0, y, z, n0, g);
-        if (x0 + 1 == L.nx - 1) gather_node_lane<S, 1>(L, fa, L.nx - 1, y, z, n0 + 1, g);
+    } else {
+        // element offsets (from the pair's first node) of the outer node of the
+        // c_x = +1 directions (left) and c_x = -1 directions (right): dl / dr
+        // relative to the source word, or the own opposite population when
+        // own_l / own_r (a wall)
+        int dl = -1, dr = 2;
+        bool own_l = false, own_r = false, again_l = false, again_r = false;
+        const bool eq_yz = !YZPER && ((ky[0] | ky[2] | kz[0] | kz[2]) & 1);
+        if (x0 == 0) {
+            const int f = L.face[0];
+            dl = f == LBM_FACE_PERIODIC ? L.nx - 1 : 0;  // outflow: the clamped source x0
+            own_l = f == LBM_FACE_WALL;
+            again_l = f == LBM_FACE_EQ || (own_l && eq_yz);
+        }
+        if (x0 + 2 >= L.nx) {
+            const int f = L.face[1];
+            dr = f == LBM_FACE_PERIODIC ? 2 - L.nx : 1;  // outflow: the clamped source x0 + 1
+            own_r = f == LBM_FACE_WALL;
+            again_r = f == LBM_FACE_EQ || (own_r && eq_yz);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = cx_of(i);
+            const int src = L.plane[i] + oy[cy_of(i) + 1] + oz[cz_of(i) + 1];
+            const float2 m = P::unpack(P::load(p + src));
+            if (cx == 0) {
+                g[i] = m;
+            } else if (cx > 0) {
+                const int o = own_l ? L.plane[26 - i] : src + dl;            // source of node x0
+                g[i] = make_float2((float)Codec<S>::load(p + o), m.x);
+            } else {
+                const int o = own_r ? L.plane[26 - i] + 1 : src + dr;        // source of node x0 + 1
+                g[i] = make_float2(m.y, (float)Codec<S>::load(p + o));
+            }
+        }
+        if (!YZPER) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int k = max(ky[cy_of(i) + 1], kz[cz_of(i) + 1]);
+                if (k == 2) g[i] = P::unpack(P::load(p + L.plane[26 - i]));  // the pair's own bounce-back word
+                else if (k == 1) g[i] = make_float2(L.g_face_f[i], L.g_face_f[i]);
+            }
+        }
+        if (again_l) gather_node_lane<S, 0>(L, fa, 0, y, z, n0, g);
+        if (again_r) gather_node_lane<S, 1>(L, fa, L.nx - 1, y, z, n0 + 1, g);
     }
 }
 

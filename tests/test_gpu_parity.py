@@ -41,6 +41,24 @@ def test_periodic_random_state(storage, shape):
         assert err <= TOL[storage], (storage, steps, err)
 
 
+_PIPE_FACES = [(0,) * 6, (2, 3, 1, 1, 0, 0), (1, 1, 2, 2, 3, 3)]
+
+
+@pytest.mark.parametrize("storage,faces", [(st, f) for st in ("fp32", "fp16") for f in _PIPE_FACES]
+                         + [("bf16", _PIPE_FACES[0])])
+def test_persistent_bulk_walk(storage, faces):
+    """Rows of a multiple of 64 nodes take the persistent two-node kernel: a
+    grid of warps walks the lattice in units of 64 nodes, prefetching each
+    next unit's source words into L2.  128x64x64 gives each warp of the full
+    grid about four units, so the walk turns over several times with a
+    ragged last round.  Faces: periodic; equilibrium inflow x-, outflow x+,
+    walls y; walls x (folded into the outer words and byte selectors),
+    equilibrium y (the x-face nodes of those rows gathered again), outflow z."""
+    shape = (128, 64, 64)
+    lat, orc = run_pair(shape, 0.02, storage, random_fields(shape, 23), 10, faces=faces, u_face=(0.04, 0.0, 0.01))
+    assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage], faces
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_lbgk_mode(storage):
     shape = (40, 9, 7)
