@@ -29,11 +29,12 @@ def _built():
 
 
 @pytest.mark.parametrize("storage", STORAGES)
-@pytest.mark.parametrize("shape", [(150, 6, 5), (24, 20, 17), (1, 64, 1), (3, 3, 3)])
+@pytest.mark.parametrize("shape", [(150, 6, 5), (24, 20, 17), (1, 64, 1), (3, 3, 3), (64, 3, 2), (192, 5, 3)])
 def test_periodic_random_state(storage, shape):
     """Rough random fields on periodic boxes: 150 = 128 + 22 nodes per row (two
     x-blocks with a ragged tail), a non-power-of-two box, a one-node-wide
-    column (every pull wraps) and the smallest cube."""
+    column (every pull wraps), the smallest cube, and rows of 64 and 192 nodes
+    (the two-node kernel with one and two blocks per row, the second ragged)."""
     fields = random_fields(shape, 1)
     for steps in (1, 10):
         lat, orc = run_pair(shape, 0.01, storage, fields, steps)
@@ -46,14 +47,12 @@ _PIPE_FACES = [(0,) * 6, (2, 3, 1, 1, 0, 0), (1, 1, 2, 2, 3, 3)]
 
 @pytest.mark.parametrize("storage,faces", [(st, f) for st in ("fp32", "fp16") for f in _PIPE_FACES]
                          + [("bf16", _PIPE_FACES[0])])
-def test_persistent_bulk_walk(storage, faces):
-    """Rows of a multiple of 64 nodes take the persistent two-node kernel: a
-    grid of warps walks the lattice in units of 64 nodes, prefetching each
-    next unit's source words into L2.  128x64x64 gives each warp of the full
-    grid about four units, so the walk turns over several times with a
-    ragged last round.  Faces: periodic; equilibrium inflow x-, outflow x+,
-    walls y; walls x (folded into the outer words and byte selectors),
-    equilibrium y (the x-face nodes of those rows gathered again), outflow z."""
+def test_two_node_kernel_faces(storage, faces):
+    """The two-node bulk kernel on a 128x64x64 box (several blocks per row,
+    more blocks than fit on the GPU at once) with each kind of face: periodic;
+    equilibrium inflow x-, outflow x+, walls y; walls x (folded into the
+    outer nodes' addresses), equilibrium y (the x-face nodes of those rows
+    gathered again), outflow z."""
     shape = (128, 64, 64)
     lat, orc = run_pair(shape, 0.02, storage, random_fields(shape, 23), 10, faces=faces, u_face=(0.04, 0.0, 0.01))
     assert rel_err(lat.populations(), orc.get_f()) <= TOL[storage], faces
