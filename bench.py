@@ -50,7 +50,7 @@ BYTES_PER_NODE = {"fp64": 432, "fp32": 216, "fp16": 108, "bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32", "bf16": "f32"}
 FALLBACK_HBM_GBS = 6800.0
 PROFILES = os.path.join(ROOT, "profiles")
-KERNEL_SOURCES = ["bulk.cu", "pull.cuh", "kbc.cuh", "lbm_internal.cuh"]
+KERNEL_SOURCES = ["bulk.cu", "pull.cuh", "kbc.cuh", "kbcv.cuh", "lbm_internal.cuh"]
 
 
 def parse_args(argv=None):
@@ -291,6 +291,8 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     # timed step runs the chosen order
     extra = 0
     while lat.launch_order() == "auto" and extra < 32:
+        # the choice is made at the first step after the trial's last event
+        torch.cuda.synchronize()
         lat.step(1)
         extra += 1
     torch.cuda.synchronize()
@@ -339,6 +341,7 @@ def e2e_storage(storage, wl, args, device):
     lat.step(max(args.warmup, 1))
     extra = 0
     while lat.launch_order() == "auto" and extra < 32:
+        torch.cuda.synchronize()
         lat.step(1)
         extra += 1
     rho, u = initial_flow(wl)
