@@ -150,12 +150,17 @@ __device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int 
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
         const R ifeq = Rxy[cx + 1][cy + 1] * Rz[cz + 1];
-        const R ds = (nz == 1 || nz == 2) ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
-        const R dh = d[i] - ds;
-        const R t = dh * ifeq;
-        sh += ds * t;
-        hh += dh * t;
-        lh += lam[i] * dh;
+        if (nz == 1 || nz == 2) {
+            const R ds = shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz);
+            const R dh = d[i] - ds;
+            const R t = dh * ifeq;
+            sh += ds * t;
+            hh += dh * t;
+            lh += lam[i] * dh;
+        } else {
+            hh += d[i] * (d[i] * ifeq);
+            lh += lam[i] * d[i];
+        }
     }
     const bool analytic = gamma_mode == LBM_GAMMA_ANALYTIC && hh > gamma_floor<R>();
     const R ihh = analytic ? rcp_fast(hh) : R(0);
@@ -197,13 +202,23 @@ __device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int 
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i), nz = nonzero_of(i);
         const R ifeq = Rxy[cx + 1][cy + 1] * Rz[cz + 1];
         const R feq = Fxy[cx + 1][cy + 1] * Fz[cz + 1];
-        const R ds = (nz == 1 || nz == 2) ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
-        const R dh = d[i] - ds;
-        const R dhb = cl_h * lam[i] + (ab * ds + bb2 * dh) * ifeq;
-        const R dfb = dhb + nxzb * R(cx * cx) + nyzb * R(cy * cy) + pzzb * R(cz * cz) + pxyb * R(cx * cy) +
-                      pxzb * R(cx * cz) + pyzb * R(cy * cz);
+        // rest and corners carry no shear part (ds = 0, dh = d)
+        const bool sh_i = nz == 1 || nz == 2;
+        const R ds = sh_i ? shear_part<R>(i, sx, sy, sz, qxy, qxz, qyz) : R(0);
+        const R dh = sh_i ? d[i] - ds : d[i];
+        const R dhb = cl_h * lam[i] + (sh_i ? ab * ds + bb2 * dh : bb2 * dh) * ifeq;
+        // S^T of the shear sums: only the terms with nonzero c_a c_b (known
+        // per direction at compile time; a product with 0 would still cost an
+        // instruction)
+        R dfb = dhb;
+        if (cx) dfb += nxzb;
+        if (cy) dfb += nyzb;
+        if (cz) dfb += pzzb;
+        if (cx && cy) dfb = cx * cy > 0 ? dfb + pxyb : dfb - pxyb;
+        if (cx && cz) dfb = cx * cz > 0 ? dfb + pxzb : dfb - pxzb;
+        if (cy && cz) dfb = cy * cz > 0 ? dfb + pyzb : dfb - pyzb;
         // feq_bar * feq
-        const R t = -(ab * ds + bb * dh) * dh * ifeq - dfb * feq;
+        const R t = -(sh_i ? ab * ds + bb * dh : bb * dh) * dh * ifeq - dfb * feq;
         rhob += t;
         ub0 += t * dl[0][cx + 1];
         ub1 += t * dl[1][cy + 1];
@@ -214,8 +229,13 @@ __device__ void kbc_vjp(const R g[Q], R lam[Q], R beta, R inv_beta, R rho0, int 
     const R jb[3] = {ub0 * irho, ub1 * irho, ub2 * irho};
     rhob -= (ub0 * u[0] + ub1 * u[1] + ub2 * u[2]) * irho;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        lam[i] += rhob + R(cx_of(i)) * jb[0] + R(cy_of(i)) * jb[1] + R(cz_of(i)) * jb[2];
+    for (int i = 0; i < Q; ++i) {
+        R v = rhob;
+        if (cx_of(i)) v = cx_of(i) > 0 ? v + jb[0] : v - jb[0];
+        if (cy_of(i)) v = cy_of(i) > 0 ? v + jb[1] : v - jb[1];
+        if (cz_of(i)) v = cz_of(i) > 0 ? v + jb[2] : v - jb[2];
+        lam[i] += v;
+    }
 }
 
 // The same transpose with lane i < 27 holding g_i and lam_i (boundary nodes);
