@@ -439,6 +439,58 @@ def test_stationary_sphere_drag_and_wake_at_re100(D, u, steps, cd_tol):
     assert abs(ld - ld_paper) <= 0.06
 
 
+_LONG_RUN = {}
+
+
+def _long_run_oracle(wl):
+    """The FP64 oracle's mean force over steps 1001-2000 and its velocity at
+    step 2000 (about a minute and a half of one host core, run once)."""
+    if "r" not in _LONG_RUN:
+        shape = wl["shape"]
+        orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
+                            body=oracle.sphere_body(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"],
+                                                    g=wl["g"]))
+        orc.init_state(*synth.uniform_fields(shape))
+        orc.step(1000)
+        Fsum = np.zeros(3)
+        for _ in range(1000):
+            orc.step(1)
+            Fsum += np.array(orc.body.F)
+        _LONG_RUN["r"] = (Fsum / 1000, np.array(orc.body.U))
+    return _LONG_RUN["r"]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_long_run_drag_matches_the_oracle(storage):
+    """The sedimenting sphere of Sec. 4.1 on a reduced box (32x32x64, D = 8,
+    solid/fluid density ratio 1.5, x/y walls, periodic z, Re = u_t D / nu =
+    100 with gravity from the terminal-velocity balance), started at rest and
+    run 2000 steps on the GPU and in the FP64 oracle: the force averaged over
+    steps 1001-2000 and the settling velocity at step 2000 agree within 0.5%
+    (the long-run drag bar).  The sphere falls about 40 nodes, so its
+    boundary links, covered and refilled nodes change every few steps."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.sedimenting_sphere(shape=(32, 32, 64), D=8.0)
+    shape = wl["shape"]
+    geom = lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"])
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"])
+    lat.set_geometry(geom)
+    lat.init_state(*synth.uniform_fields(shape))
+    lat.step(1000)
+    lat.reset_average()
+    lat.step(1000)
+    F, _ = lat.forces(averaged=True)
+    U = np.array(lat.body()["U"])
+    Fo, Uo = _long_run_oracle(wl)
+    drag_err = abs(F[2] - Fo[2]) / abs(Fo[2])
+    u_err = abs(U[2] - Uo[2]) / abs(Uo[2])
+    print(f"{storage}: drag {F[2]:.6e} vs oracle {Fo[2]:.6e} (rel {drag_err:.2e}), "
+          f"U_z {U[2]:.6e} vs {Uo[2]:.6e} (rel {u_err:.2e})")
+    assert abs(Uo[2]) > 0.01 and Fo[2] > 0
+    assert drag_err <= 5e-3
+    assert u_err <= 5e-3
+
+
 def test_sedimenting_sphere_reaches_terminal_velocity():
     """The benchmark's sedimenting sphere (128x128x256, D = 16, rho_s/rho_f =
     1.5, walls in x and y, periodic z; Sec. 4.1 two-way coupling, Euler
