@@ -373,6 +373,42 @@ typedef struct {
 
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double dJ_dtheta[3]);
 
+/* ---- slab decomposition: one box split along z over several contexts ----
+ * The paper gives no parallel scheme; this places its step on slabs of the
+ * box, one exchange of edge layers per step (Sec. 2 streaming reads one layer
+ * across a cut; the Sec. 3 refill of a node in that layer reads one more).
+ *
+ * lbm_set_slab: the context's lattice is a slab of a box periodic in z with
+ * zper layers: its z layer k is the box's layer (zoff + k) mod zper.  Its
+ * layers [own_lo, own_hi) are its own; the others are halo layers that the
+ * caller refills before every step with the neighbouring slabs' own layers
+ * (two halo layers per side are needed).  The body's geometry (solid test,
+ * nearest image, the sphere's centre wrap, torque arm) uses the box's z; the
+ * force and torque of a step sum the links of own fluid nodes only; the
+ * caller adds the slabs' sums (in a fixed slab order, so every slab holds the
+ * same bits) and hands the total to every slab with lbm_set_body_force before
+ * the next step, so the body copies move alike.  The context's own z faces
+ * must be walls (no own node reads them).  Bodies: sphere, airfoil, planes
+ * (the mesh is LBM_ERR_UNSUPPORTED); no adjoint.  Call before
+ * lbm_set_geometry.  Errors: LBM_ERR_ARG (sizes, faces), LBM_ERR_STATE (a
+ * body is already set). */
+LBM_API lbm_status lbm_set_slab(lbm_ctx *ctx, int zoff, int zper, int own_lo, int own_hi);
+
+/* Copies the z layers [z0, z0 + nlayers) of the current state, all 27
+ * planes, to dst / from src: device buffers of 27 * nlayers * nx * ny
+ * elements of the storage type, plane-major (plane i first, then its
+ * layers, x fastest), in the stored shifted form.  Asynchronous on the
+ * context stream (one strided copy).  LBM_ERR_ARG for layers outside the box
+ * or a null buffer. */
+LBM_API lbm_status lbm_pack_layers(lbm_ctx *ctx, int z0, int nlayers, void *dst);
+LBM_API lbm_status lbm_unpack_layers(lbm_ctx *ctx, int z0, int nlayers, const void *src);
+
+/* Replaces the force F and torque M (host arrays of 3) of the body's current
+ * state: the next step's Euler update reads them, and the running sums of
+ * lbm_body_forces' average follow.  Asynchronous on the context stream.
+ * LBM_ERR_STATE without a body. */
+LBM_API lbm_status lbm_set_body_force(lbm_ctx *ctx, const double F[3], const double M[3]);
+
 /* Global sums without a context and without device allocation.  The paper
  * has no counterpart to this entry point; it exists for callers that cannot
  * call cudaMalloc: applications that hand all device memory to their own

@@ -138,6 +138,14 @@ def lib():
         L.lbm_profile_end.restype = C.c_int
         L.lbm_adjoint_step.argtypes = [vp, C.POINTER(AdjointSpec), _D, _D]
         L.lbm_adjoint_step.restype = C.c_int
+        L.lbm_set_slab.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.lbm_set_slab.restype = C.c_int
+        L.lbm_pack_layers.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.lbm_pack_layers.restype = C.c_int
+        L.lbm_unpack_layers.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.lbm_unpack_layers.restype = C.c_int
+        L.lbm_set_body_force.argtypes = [vp, _D, _D]
+        L.lbm_set_body_force.restype = C.c_int
         _lib = L
     return _lib
 
@@ -423,6 +431,35 @@ class Lattice:
         dJ = np.zeros(3)
         self._check(lib().lbm_adjoint_step(self._ctx, C.byref(spec), J.ctypes.data_as(_D), dJ.ctypes.data_as(_D)))
         return dict(J=float(J[0]), dJ_dtheta=dJ, lambda_0=lam0)
+
+    # -------------------------------------------------------------- slabs
+    def set_slab(self, zoff: int, zper: int, own_lo: int, own_hi: int):
+        """This lattice is a slab of a box periodic in z with zper layers, its
+        layer k the box's layer zoff + k, its own layers [own_lo, own_hi)
+        (lbm_set_slab; before set_geometry)."""
+        self._check(lib().lbm_set_slab(self._ctx, int(zoff), int(zper), int(own_lo), int(own_hi)))
+
+    def pack_layers(self, z0: int, n: int, out=None):
+        """The current state's layers [z0, z0 + n), all 27 planes, as a device
+        tensor (27, n, ny, nx) of the storage type (lbm_pack_layers)."""
+        torch = _torch()
+        nx, ny, _ = self.shape
+        if out is None:
+            out = torch.empty((27, n, ny, nx), dtype=self.f_a.dtype, device=self.device)
+        self._check(lib().lbm_pack_layers(self._ctx, int(z0), int(n), C.c_void_p(out.data_ptr())))
+        return out
+
+    def unpack_layers(self, z0: int, src):
+        """Writes a (27, n, ny, nx) device tensor of the storage type into the
+        current state's layers [z0, z0 + n) (lbm_unpack_layers)."""
+        src = src.contiguous()
+        self._check(lib().lbm_unpack_layers(self._ctx, int(z0), int(src.shape[1]), C.c_void_p(src.data_ptr())))
+
+    def set_body_force(self, F, M):
+        """Replaces the body's current force and torque (lbm_set_body_force)."""
+        Fa = np.ascontiguousarray(F, dtype=np.float64)
+        Ma = np.ascontiguousarray(M, dtype=np.float64)
+        self._check(lib().lbm_set_body_force(self._ctx, Fa.ctypes.data_as(_D), Ma.ctypes.data_as(_D)))
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

@@ -1544,6 +1544,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, do
     if (!ctx->initialised) return afail(ctx, LBM_ERR_STATE, "lbm_adjoint_step: state not initialised");
     if (ctx->L.gamma_mode == LBM_GAMMA_EXACT)
         return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: the exact stabilizer has no adjoint here");
+    if (ctx->slab_zper > 0)
+        return afail(ctx, LBM_ERR_UNSUPPORTED, "lbm_adjoint_step: a slab context has no adjoint here");
     for (int k = 0; k < 3; ++k) dJ_dtheta[k] = 0.0;
     *J = 0.0;
     if (drain_records(ctx) != cudaSuccess) return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: record copies");

@@ -231,6 +231,14 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     ctx->trial = 0;
     G.kind = g->kind;
     G.free_motion = g->free_motion;
+    G.zoff = ctx->slab_zoff;
+    G.zper = ctx->slab_zper;
+    G.own_lo = ctx->slab_zper > 0 ? ctx->slab_own_lo : 0;
+    G.own_hi = ctx->slab_zper > 0 ? ctx->slab_own_hi : L.nz;
+    if (ctx->slab_zper > 0 && g->kind == LBM_BODY_MESH)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "lbm_set_geometry: a slab takes the sphere, airfoil or planes, not the mesh");
+    if (ctx->slab_zper > 0 && g->kind == LBM_BODY_SPHERE && !(g->X[2] >= 0.0 && g->X[2] < (double)ctx->slab_zper))
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: sphere centre outside [0, zper) of the slab's whole box");
     G.R = g->R;
     G.y_lo = g->y_lo;
     G.y_hi = g->y_hi;
@@ -897,3 +905,58 @@ lbm_status lbm_profile_end(lbm_ctx *ctx, double *total_ms, int64_t *launches)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- slabs
+lbm_status lbm_set_slab(lbm_ctx *ctx, int zoff, int zper, int own_lo, int own_hi)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    const Lattice &L = ctx->L;
+    if (ctx->has_body) return fail(ctx, LBM_ERR_STATE, "lbm_set_slab: call it before lbm_set_geometry");
+    if (zper < L.nz - 2 || zper < 1 || own_lo < 0 || own_hi > L.nz || own_lo >= own_hi)
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_slab: need zper >= nz - 2 and 0 <= own_lo < own_hi <= nz");
+    if (L.face[4] != LBM_FACE_WALL || L.face[5] != LBM_FACE_WALL)
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_slab: the slab's own z faces must be walls");
+    ctx->slab_zoff = zoff;
+    ctx->slab_zper = zper;
+    ctx->slab_own_lo = own_lo;
+    ctx->slab_own_hi = own_hi;
+    return LBM_OK;
+}
+
+// layers [z0, z0 + nlayers) of all 27 planes of the current state <-> a
+// plane-major contiguous buffer: one strided copy (27 rows, pitch N)
+static lbm_status copy_layers(lbm_ctx *ctx, int z0, int nlayers, void *buf, bool pack)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    const Lattice &L = ctx->L;
+    if (!buf || nlayers < 1 || z0 < 0 || z0 + nlayers > L.nz)
+        return fail(ctx, LBM_ERR_ARG, "lbm_pack_layers / lbm_unpack_layers: layers outside the box or null buffer");
+    const size_t e = ctx->elem, layer = (size_t)L.nx * L.ny * e;
+    char *state = (char *)ctx->f[ctx->cur] + (size_t)z0 * layer;
+    const size_t width = (size_t)nlayers * layer, pitch = (size_t)L.N * e;
+    cudaError_t err = pack ? cudaMemcpy2DAsync(buf, width, state, pitch, width, Q, cudaMemcpyDeviceToDevice, ctx->stream)
+                           : cudaMemcpy2DAsync(state, pitch, buf, width, width, Q, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, pack ? "lbm_pack_layers" : "lbm_unpack_layers");
+    return LBM_OK;
+}
+
+lbm_status lbm_pack_layers(lbm_ctx *ctx, int z0, int nlayers, void *dst) { return copy_layers(ctx, z0, nlayers, dst, true); }
+
+lbm_status lbm_unpack_layers(lbm_ctx *ctx, int z0, int nlayers, const void *src)
+{
+    return copy_layers(ctx, z0, nlayers, const_cast<void *>(src), false);
+}
+
+lbm_status lbm_set_body_force(lbm_ctx *ctx, const double F[3], const double M[3])
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!F || !M) return fail(ctx, LBM_ERR_ARG, "lbm_set_body_force: null force or torque");
+    if (!ctx->has_body) return fail(ctx, LBM_ERR_STATE, "lbm_set_body_force: no body");
+    double fm[6];
+    for (int a = 0; a < 3; ++a) {
+        fm[a] = F[a];
+        fm[3 + a] = M[a];
+    }
+    LBM_CUDA(launch_set_force(ctx->S, ctx->bcur, fm, ctx->stream), "lbm_set_body_force");
+    return LBM_OK;
+}

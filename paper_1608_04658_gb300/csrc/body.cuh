@@ -50,6 +50,10 @@ struct GeomParams {
     double mass;              // body mass (density mass / mesh volume in the centre-of-mass frame)
     double mesh_ext[6];       // pose extent relative to the head: x, y, z min/max
     int periodic[3];
+    // slab of a box split along z (lbm_set_slab): local z layer k is layer
+    // zoff + k (mod zper) of the whole box; zper = 0: no slab.  The force and
+    // torque sum the links of the own layers [own_lo, own_hi) only.
+    int zoff, zper, own_lo, own_hi;
     int cap[3];          // band capacity per axis
     int cap_boundary;    // slots in the boundary list
     int cap_uncovered;   // slots in the uncovered list
@@ -107,6 +111,10 @@ cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, 
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s);
 cudaError_t launch_forces(const GeomParams &G, Scratch &S, int cur, cudaStream_t s, int *nlaunch);
 cudaError_t launch_sweep_init(const Lattice &L, const GeomParams &G, Scratch &S, int cur, cudaStream_t s);
+struct Force6 {
+    double v[6];
+};
+cudaError_t launch_set_force(Scratch &S, int cur, const double fm[6], cudaStream_t s);
 // true when the band is known before the step's geometry runs (all bodies but
 // the walls, whose band is the whole box, and the swimmer in the
 // centre-of-mass frame, whose band follows from the pose of the step)

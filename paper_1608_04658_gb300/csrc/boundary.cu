@@ -146,10 +146,12 @@ __global__ void __launch_bounds__(BWARPS * 32, LBM_LIST_MIN_BLOCKS) boundary_ker
             dF[5] = r[0] * dF[1] - r[1] * dF[0];
         }
         const int pos = bpos[slot];
+        // a slab's links count where it owns the fluid node
+        const bool own = z >= G.own_lo && z < G.own_hi;
         for (int k = 0; k < 6; ++k) {
             double v = dF[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) bforce[(size_t)pos * 6 + k] = v;
+            if (lane == 0) bforce[(size_t)pos * 6 + k] = own ? v : 0.0;
         }
 
         bool ok;

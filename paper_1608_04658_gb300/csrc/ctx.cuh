@@ -53,6 +53,8 @@ struct lbm_ctx {
     int prof_used = 0;
     bool prof_open = false;
     std::string err;
+    // slab of a box split along z (lbm_set_slab); zper = 0: none
+    int slab_zoff = 0, slab_zper = 0, slab_own_lo = 0, slab_own_hi = 0;
 };
 
 // waits on the host for the asynchronous force-record copies that may still

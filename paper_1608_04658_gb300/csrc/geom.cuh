@@ -34,6 +34,15 @@ __device__ __forceinline__ double axis_offset(int p, double X, int n, int period
     return d;
 }
 
+// Displacement of lattice coordinate p on axis a from the body coordinate X
+// in the whole box's frame: a slab's z layers sit at zoff of a box periodic
+// in z with zper layers (nearest image there), other axes as axis_offset.
+__device__ __forceinline__ double frame_offset(int a, int p, double X, int n, int periodic, int zoff, int zper)
+{
+    if (a == 2 && zper > 0) return axis_offset(p + zoff, X, zper, 1);
+    return axis_offset(p, X, n, periodic);
+}
+
 // Airfoil in its chord frame (see lbm_geometry): camber line and half thickness
 __device__ __forceinline__ double airfoil_camber(const GeomParams &G, double xi)
 {
@@ -67,7 +76,7 @@ __device__ __forceinline__ bool inside_body(const GeomParams &G, const Lattice &
     if (G.kind == LBM_BODY_SPHERE) {
         const double dx = axis_offset(x, X[0], L.nx, G.periodic[0]);
         const double dy = axis_offset(y, X[1], L.ny, G.periodic[1]);
-        const double dz = axis_offset(z, X[2], L.nz, G.periodic[2]);
+        const double dz = frame_offset(2, z, X[2], L.nz, G.periodic[2], G.zoff, G.zper);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         return d2 < __dmul_rn(G.R, G.R);
     }
@@ -403,7 +412,7 @@ __device__ __forceinline__ void link_data(const Lattice &L, const GeomParams &G,
     } else if (G.kind == LBM_BODY_SPHERE) {
         const double d0 = axis_offset(x, b->X[0], L.nx, G.periodic[0]);
         const double d1 = axis_offset(y, b->X[1], L.ny, G.periodic[1]);
-        const double d2 = axis_offset(z, b->X[2], L.nz, G.periodic[2]);
+        const double d2 = frame_offset(2, z, b->X[2], L.nz, G.periodic[2], G.zoff, G.zper);
         const double cc = (double)(cx * cx + cy * cy + cz * cz);
         const double cd = cx * d0 + cy * d1 + cz * d2;
         const double dd = d0 * d0 + d1 * d1 + d2 * d2;
@@ -812,10 +821,12 @@ __device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams
                                               int a, int p)
 {
     if (G.kind == LBM_BODY_MESH) return __dsub_rn((double)p, b->X[a]);
-    if (G.kind == LBM_BODY_AIRFOIL) return a < 2 ? __dsub_rn((double)p, b->X[a]) : (double)p;
-    if (G.kind != LBM_BODY_SPHERE) return (double)p;
+    // (a slab's z is that of the whole box)
+    const int pz = a == 2 && G.zper > 0 ? p + G.zoff : p;
+    if (G.kind == LBM_BODY_AIRFOIL) return a < 2 ? __dsub_rn((double)p, b->X[a]) : (double)pz;
+    if (G.kind != LBM_BODY_SPHERE) return (double)pz;
     const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
-    return axis_offset(p, b->X[a], n, G.periodic[a]);
+    return frame_offset(a, p, b->X[a], n, G.periodic[a], G.zoff, G.zper);
 }
 
 }  // namespace lbm

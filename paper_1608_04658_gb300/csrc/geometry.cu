@@ -105,9 +105,11 @@ __device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBod
             const double acc = __dadd_rn(__dmul_rn(prev->F[a], G.inv_mass), __dmul_rn(G.buoy, G.g[a]));
             X[a] = __dadd_rn(X[a], U[a]);
             U[a] = __dadd_rn(U[a], acc);
-            if (G.periodic[a]) {
-                if (X[a] >= (double)n[a]) X[a] = __dsub_rn(X[a], (double)n[a]);
-                else if (X[a] < 0.0) X[a] = __dadd_rn(X[a], (double)n[a]);
+            // the centre wraps on a periodic axis (a slab's z: the whole box's)
+            const int per = a == 2 && G.zper > 0 ? G.zper : (G.periodic[a] ? n[a] : 0);
+            if (per) {
+                if (X[a] >= (double)per) X[a] = __dsub_rn(X[a], (double)per);
+                else if (X[a] < 0.0) X[a] = __dadd_rn(X[a], (double)per);
             }
         }
         int l, c;
@@ -120,13 +122,24 @@ __device__ void advance_body(const Lattice &L, const GeomParams &G, const DevBod
         } else if (G.kind == LBM_BODY_SPHERE) {
             // box of the sphere at both positions; on a periodic axis the old
             // centre is taken at the image nearest the new one
-            double Xo = prev->X[a];
+            double Xo = prev->X[a], Xn = X[a];
             if (G.periodic[a]) {
                 const double h = 0.5 * (double)n[a];
-                if (Xo - X[a] > h) Xo -= (double)n[a];
-                else if (Xo - X[a] < -h) Xo += (double)n[a];
+                if (Xo - Xn > h) Xo -= (double)n[a];
+                else if (Xo - Xn < -h) Xo += (double)n[a];
             }
-            const double mn = fmin(Xo, X[a]) - G.R, mx = fmax(Xo, X[a]) + G.R;
+            if (a == 2 && G.zper > 0) {
+                // a slab: both centres in its own z frame, at the image of the
+                // whole box nearest its layers (the box is not periodic)
+                const double per = (double)G.zper, mid = 0.5 * (double)n[2];
+                Xn -= (double)G.zoff;
+                if (Xn - mid > 0.5 * per) Xn -= per;
+                else if (Xn - mid < -0.5 * per) Xn += per;
+                Xo -= (double)G.zoff;
+                if (Xo - Xn > 0.5 * per) Xo -= per;
+                else if (Xo - Xn < -0.5 * per) Xo += per;
+            }
+            const double mn = fmin(Xo, Xn) - G.R, mx = fmax(Xo, Xn) + G.R;
             l = (int)floor(mn) - BAND_MARGIN;
             c = (int)floor(mx) + BAND_MARGIN + 1 - l + 1;
         } else {
@@ -718,6 +731,26 @@ cudaError_t launch_mesh_body(const Lattice &L, const GeomParams &G, Scratch &S, 
                                                                    S.body + (advance ? prev ^ 1 : prev),
                                                                    advance ? 1 : 0);
     *nlaunch += 1;
+    return cudaGetLastError();
+}
+
+// replaces the force and torque of a body state, the running sums following
+__global__ void set_force_kernel(DevBody *__restrict__ b, Force6 fm)
+{
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        b->F_sum[a] = __dadd_rn(__dsub_rn(b->F_sum[a], b->F[a]), fm.v[a]);
+        b->M_sum[a] = __dadd_rn(__dsub_rn(b->M_sum[a], b->M[a]), fm.v[3 + a]);
+        b->F[a] = fm.v[a];
+        b->M[a] = fm.v[3 + a];
+    }
+}
+
+cudaError_t launch_set_force(Scratch &S, int cur, const double fm[6], cudaStream_t s)
+{
+    Force6 v;
+    for (int k = 0; k < 6; ++k) v.v[k] = fm[k];
+    set_force_kernel<<<1, 32, 0, s>>>(S.body + cur, v);
     return cudaGetLastError();
 }
 

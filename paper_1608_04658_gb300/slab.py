@@ -1,0 +1,177 @@
+"""Slab decomposition of one lattice along z: the box's z layers are split into
+consecutive slabs, each a lattice of its own (lbm_set_slab) with two halo
+layers on each side, and one exchange of edge layers per time step.
+
+The paper gives no parallel scheme; this places its step on slabs (Sec. 2:
+the pull reads one layer across a cut; Sec. 3: the refill of a node in that
+layer averages densities one layer further out, hence two halo layers).
+Before every step each slab's halo layers take the neighbouring slabs' own
+edge layers (all 27 post-collision populations); after it the slabs' forces
+and torques, each summed over the links of its own fluid nodes, are added in
+slab order and handed back to every slab's copy of the body, so all copies
+move alike.  Own nodes then end every step with the bits of the undivided
+lattice while the body's velocity does not depend on the force; a free body
+differs by the order in which the link forces are added.
+
+SlabSet keeps all slabs in this process (one device or several, the edge
+layers moved by device copies); DistSlab is one slab per rank of a
+torch.distributed process group (NCCL between GPUs), the edge layers sent
+and received as packed device tensors.  This module is host orchestration
+only: every step of the method runs in liblbm.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as _b
+
+HALO = 2
+
+
+def slab_bounds(nz: int, parts: int, k: int) -> tuple[int, int]:
+    """Own z layers [z0, z1) of slab k of parts: consecutive, sizes differing by one."""
+    return k * nz // parts, (k + 1) * nz // parts
+
+
+def slab_rows(nz: int, parts: int, k: int, halo: int = HALO) -> list[int]:
+    """The box's z layer of each local layer of slab k (halo layers wrapped)."""
+    z0, z1 = slab_bounds(nz, parts, k)
+    return [(z0 - halo + j) % nz for j in range(z1 - z0 + 2 * halo)]
+
+
+def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, **kw):
+    nx, ny, nz = shape
+    if faces[4] != _b.FACE_PERIODIC or faces[5] != _b.FACE_PERIODIC:
+        raise ValueError("the split axis z must be periodic")
+    z0, z1 = slab_bounds(nz, parts, k)
+    if z1 - z0 < halo:
+        raise ValueError("slabs thinner than the halo")
+    nloc = z1 - z0 + 2 * halo
+    local_faces = (faces[0], faces[1], faces[2], faces[3], _b.FACE_WALL, _b.FACE_WALL)
+    lat = _b.Lattice((nx, ny, nloc), nu, storage=storage, faces=local_faces, device=device, **kw)
+    lat.set_slab(z0 - halo, nz, halo, nloc - halo)
+    return lat
+
+
+def _fixed_order_sum(parts):
+    tot = np.array(parts[0], dtype=np.float64)
+    for p in parts[1:]:
+        tot = tot + np.asarray(p, dtype=np.float64)
+    return tot
+
+
+class SlabSet:
+    """All slabs of one box in this process.  devices: one device for every
+    slab, or a list (slab k on devices[k % len])."""
+
+    def __init__(self, shape, nu, parts, storage="fp32", faces=(0,) * 6, geometry=None, devices=None,
+                 halo=HALO, **kw):
+        self.shape = tuple(int(v) for v in shape)
+        self.parts, self.halo = int(parts), int(halo)
+        devs = devices if isinstance(devices, (list, tuple)) else [devices]
+        self.slabs = [_slab_lattice(self.shape, nu, storage, faces, self.parts, k, self.halo,
+                                    devs[k % len(devs)], **kw) for k in range(self.parts)]
+        self.body = geometry is not None
+        if self.body:
+            for lat in self.slabs:
+                lat.set_geometry(geometry)
+
+    def init_state(self, rho, u, xi=None, amp: float = 0.0):
+        """The whole box's fields (as Lattice.init_state takes them), each slab
+        its layers and halos."""
+        nz = self.shape[2]
+        for k, lat in enumerate(self.slabs):
+            rows = slab_rows(nz, self.parts, k, self.halo)
+            lat.init_state(rho[rows], u[rows], xi[:, rows] if xi is not None else None, amp)
+
+    def exchange(self):
+        """Every slab's halo layers from its neighbours' own edge layers."""
+        h = self.halo
+        lows = [lat.pack_layers(h, h) for lat in self.slabs]                       # first own layers
+        highs = [lat.pack_layers(lat.shape[2] - 2 * h, h) for lat in self.slabs]    # last own layers
+        for k, lat in enumerate(self.slabs):
+            lat.unpack_layers(0, highs[k - 1].to(lat.device))
+            lat.unpack_layers(lat.shape[2] - h, lows[(k + 1) % self.parts].to(lat.device))
+
+    def step(self, n: int = 1):
+        """n steps: exchange, step every slab, then the slabs' forces added in
+        slab order and handed to every body copy."""
+        for _ in range(n):
+            self.exchange()
+            for lat in self.slabs:
+                lat.step(1)
+            if self.body:
+                fm = _fixed_order_sum([np.concatenate([b["F"], b["M"]]) for b in (lat.body() for lat in self.slabs)])
+                for lat in self.slabs:
+                    lat.set_body_force(fm[:3], fm[3:])
+                self.last_force = fm
+
+    def populations(self) -> np.ndarray:
+        """The own layers of every slab assembled into the whole box, decoded
+        FP64 (27, nz, ny, nx)."""
+        nx, ny, nz = self.shape
+        out = np.empty((27, nz, ny, nx))
+        h = self.halo
+        for k, lat in enumerate(self.slabs):
+            z0, z1 = slab_bounds(nz, self.parts, k)
+            out[:, z0:z1] = lat.populations()[:, h:h + z1 - z0]
+        return out
+
+    def close(self):
+        for lat in self.slabs:
+            lat.close()
+
+
+class DistSlab:
+    """This rank's slab of one box split over the ranks of the default
+    torch.distributed process group (one slab per rank, ranks in z order):
+    edge layers by send/recv of packed device tensors, the force and torque
+    gathered and added in rank order."""
+
+    def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, geometry=None, device=None, halo=HALO, **kw):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world, self.rank = dist.get_world_size(), dist.get_rank()
+        self.shape = tuple(int(v) for v in shape)
+        self.halo = int(halo)
+        self.lat = _slab_lattice(self.shape, nu, storage, faces, self.world, self.rank, self.halo, device, **kw)
+        self.body = geometry is not None
+        if self.body:
+            self.lat.set_geometry(geometry)
+        self.z0, self.z1 = slab_bounds(self.shape[2], self.world, self.rank)
+
+    def init_state(self, rho, u, xi=None, amp: float = 0.0):
+        rows = slab_rows(self.shape[2], self.world, self.rank, self.halo)
+        self.lat.init_state(rho[rows], u[rows], xi[:, rows] if xi is not None else None, amp)
+
+    def exchange(self):
+        import torch
+        lat, h = self.lat, self.halo
+        nloc = lat.shape[2]
+        lo_out, hi_out = lat.pack_layers(h, h), lat.pack_layers(nloc - 2 * h, h)
+        if self.world == 1:
+            lo_in, hi_in = hi_out, lo_out
+        else:
+            lat.stream.synchronize()
+            lower, upper = (self.rank - 1) % self.world, (self.rank + 1) % self.world
+            lo_in, hi_in = torch.empty_like(lo_out), torch.empty_like(hi_out)
+            ops = [self.dist.P2POp(self.dist.isend, lo_out, lower), self.dist.P2POp(self.dist.isend, hi_out, upper),
+                   self.dist.P2POp(self.dist.irecv, hi_in, upper), self.dist.P2POp(self.dist.irecv, lo_in, lower)]
+            for r in self.dist.batch_isend_irecv(ops):
+                r.wait()
+        lat.unpack_layers(0, lo_in)
+        lat.unpack_layers(nloc - h, hi_in)
+
+    def step(self, n: int = 1):
+        import torch
+        for _ in range(n):
+            self.exchange()
+            self.lat.step(1)
+            if self.body:
+                b = self.lat.body()
+                mine = torch.tensor(np.concatenate([b["F"], b["M"]]), dtype=torch.float64, device=self.lat.device)
+                parts = [torch.empty_like(mine) for _ in range(self.world)]
+                self.dist.all_gather(parts, mine)
+                fm = _fixed_order_sum([p.cpu().numpy() for p in parts])
+                self.lat.set_body_force(fm[:3], fm[3:])
+                self.last_force = fm

@@ -1,0 +1,157 @@
+"""Slab decomposition on the GPU: one box split along z into slab lattices
+(lbm_set_slab) that exchange two edge layers per side before every step
+(lbm_pack_layers / lbm_unpack_layers, device copies in one process) and add
+their own links' forces in slab order (lbm_set_body_force).  Own nodes must
+end every step with the bits of the undivided lattice when the body's
+velocity does not depend on the force, and differ from it by the order of
+the force additions when it does.  A sphere straddles the cuts, so boundary
+nodes, links and refilled nodes lie on both sides of them."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+NU = 0.05
+FACES = (1, 1, 0, 0, 0, 0)  # walls in x, periodic y and z (the split axis)
+AMP = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1608_04658_gb300 as lbm
+    lbm.build()
+    lbm.lib()
+
+
+def _undivided(lbm, shape, storage, geom, steps, faces=FACES):
+    lat = lbm.Lattice(shape, NU, storage=storage, faces=faces)
+    if geom is not None:
+        lat.set_geometry(geom)
+    lat.init_state(*synth.parity_fields(shape, 4), AMP)
+    forces = []
+    for _ in range(steps):
+        lat.step(1)
+        if geom is not None:
+            b = lat.body()
+            forces.append(np.concatenate([b["F"], b["M"]]))
+    return lat, np.array(forces)
+
+
+def _split(lbm, shape, storage, geom, steps, parts, faces=FACES):
+    from paper_1608_04658_gb300.slab import SlabSet
+    ss = SlabSet(shape, NU, parts, storage=storage, faces=faces, geometry=geom)
+    rho, u, xi = synth.parity_fields(shape, 4)
+    ss.init_state(rho, u, xi, AMP)
+    forces = []
+    for _ in range(steps):
+        ss.step(1)
+        if geom is not None:
+            forces.append(ss.last_force.copy())
+    return ss, np.array(forces)
+
+
+def _straddles(lat, cuts):
+    """The body's solid nodes lie on both sides of a cut."""
+    solid = (lat.flags.cpu().numpy() & 1).astype(bool)
+    zs = np.nonzero(solid.any(axis=(1, 2)))[0]
+    return any(zs.min() < c <= zs.max() for c in cuts)
+
+
+def _fluid(lat, ss):
+    """Fluid nodes at the last step; the slabs' own layers carry the same
+    solid marks as the whole box.  (Solid nodes keep a stale state that no
+    fluid node reads, so only fluid nodes are compared.)"""
+    from paper_1608_04658_gb300.slab import slab_bounds
+    whole = (lat.flags.cpu().numpy() & 1).astype(bool)
+    nz = lat.shape[2]
+    for k, s in enumerate(ss.slabs):
+        z0, z1 = slab_bounds(nz, ss.parts, k)
+        own = (s.flags.cpu().numpy() & 1).astype(bool)[ss.halo:ss.halo + z1 - z0]
+        assert np.array_equal(own, whole[z0:z1])
+    return ~whole
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("parts,shape,X", [(2, (14, 12, 20), (6.3, 5.7, 9.1)),
+                                           (3, (14, 12, 21), (6.3, 5.7, 13.4))])
+def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, parts, shape, X):
+    """Sphere carried across a cut at a fixed velocity (free, with a mass so
+    large that the force leaves its velocity unchanged): the own layers of
+    every slab equal the undivided lattice bit for bit, the slab-ordered sum
+    of the forces equals the undivided force up to the order of addition."""
+    import paper_1608_04658_gb300 as lbm
+    from paper_1608_04658_gb300.slab import slab_bounds
+    geom = lbm.sphere(X, 3.2, U=(0.35, -0.15, 0.3), free=True, mass=1e30)
+    steps = 5
+    lat, fm = _undivided(lbm, shape, storage, geom, steps)
+    assert lat.body()["n_boundary"] > 0
+    ss, fs = _split(lbm, shape, storage, geom, steps, parts)
+    cuts = [slab_bounds(shape[2], parts, k)[0] for k in range(1, parts)]
+    assert _straddles(lat, cuts)
+    fluid = _fluid(lat, ss)
+    f = lat.populations()[:, fluid]
+    g = ss.populations()[:, fluid]
+    assert np.array_equal(g, f)
+    assert np.abs(fs - fm).max() <= 1e-12 * np.abs(fm).max()
+    bodies = [s.body() for s in ss.slabs]
+    for b in bodies:
+        assert np.array_equal(b["X"], bodies[0]["X"]) and np.array_equal(b["U"], bodies[0]["U"])
+    assert np.array_equal(bodies[0]["X"], lat.body()["X"])
+    ss.close()
+
+
+def test_slabs_move_a_free_sphere_with_the_summed_force():
+    """Free sedimenting sphere crossing the cut: every slab's copy of the body
+    takes the Euler update of the slab-ordered force sum, so the copies agree
+    bit for bit and differ from the undivided run only by rounding."""
+    import paper_1608_04658_gb300 as lbm
+    shape, steps = (14, 12, 20), 6
+    geom = lbm.sphere((6.3, 5.7, 11.4), 3.2, U=(0.02, 0.0, -0.25), free=True, rho_ratio=1.5, g=(0.0, 0.0, -0.01))
+    lat, fm = _undivided(lbm, shape, "fp32", geom, steps)
+    ss, fs = _split(lbm, shape, "fp32", geom, steps, 2)
+    bodies = [s.body() for s in ss.slabs]
+    assert np.array_equal(bodies[0]["U"], bodies[1]["U"]) and np.array_equal(bodies[0]["X"], bodies[1]["X"])
+    b0 = lat.body()
+    assert np.abs(np.array(bodies[0]["U"]) - np.array(b0["U"])).max() < 1e-14
+    assert np.abs(np.array(bodies[0]["X"]) - np.array(b0["X"])).max() < 1e-13
+    # the body moved with the force, not only with gravity
+    U_free = np.array([0.02, 0.0, -0.25]) + steps * (1 - 1 / 1.5) * np.array([0.0, 0.0, -0.01])
+    assert np.abs(np.array(b0["U"]) - U_free).max() > 1e-4
+    fluid = _fluid(lat, ss)
+    assert np.abs(ss.populations()[:, fluid] - lat.populations()[:, fluid]).max() < 1e-6
+    assert np.abs(fs - fm).max() <= 1e-9 * np.abs(fm).max()
+    ss.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_bodiless_periodic_box_over_slabs(storage):
+    """Periodic box without a body (rows of 64 nodes: the two-node kernel in
+    both the whole box and the slabs, whose own z faces are walls): 4 slabs,
+    bitwise equal to the undivided box."""
+    import paper_1608_04658_gb300 as lbm
+    shape = (64, 10, 24)
+    lat, _ = _undivided(lbm, shape, storage, None, 6, faces=(0,) * 6)
+    ss, _ = _split(lbm, shape, storage, None, 6, 4, faces=(0,) * 6)
+    assert np.array_equal(ss.populations(), lat.populations())
+    ss.close()
+
+
+def test_slab_arguments_are_checked():
+    import paper_1608_04658_gb300 as lbm
+    lat = lbm.Lattice((8, 8, 8), NU, faces=(0,) * 6)
+    with pytest.raises(lbm.LbmError):
+        lat.set_slab(-2, 12, 2, 6)  # z faces must be walls
+    lat = lbm.Lattice((8, 8, 8), NU, faces=(0, 0, 0, 0, 1, 1))
+    with pytest.raises(lbm.LbmError):
+        lat.set_slab(-2, 12, 6, 2)  # empty own range
+    lat.set_slab(-2, 12, 2, 6)
+    with pytest.raises(lbm.LbmError):
+        rest, tris = synth.swimmer_mesh(4.0, 8, 6)
+        lat.set_geometry(lbm.swimmer((2.1, 4.1, 4.1), rest, tris, 4.0, 0.1, 4.0, 40.0))
+    with pytest.raises(lbm.LbmError):
+        lat.pack_layers(7, 2)
