@@ -67,6 +67,11 @@ def parse_args(argv=None):
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only); "
                          "n (or n,n,n) of the periodic Taylor-Green box (default 256)")
     ap.add_argument("--workload", default="swimmer", choices=["sphere", "airfoil", "swimmer", "tgv"])
+    ap.add_argument("--parallel", default="auto", choices=["auto", "split", "replicas"],
+                    help="several GPUs: split the box along z into one slab per rank (auto, split) or run "
+                         "independent replicas; split on one GPU runs a single slab with halo exchange")
+    ap.add_argument("--slabs", type=int, default=2,
+                    help="--parallel split on one GPU: slab lattices in this process")
     ap.add_argument("--second-workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv", "none"],
                     help="workload measured beside the main line, reported under 'workloads'")
     ap.add_argument("--accuracy-steps", type=int, default=2000,
@@ -259,6 +264,20 @@ def initial_flow(wl):
     return synth.uniform_fields(wl["shape"], wl.get("u_face", (0.0, 0.0, 0.0)))
 
 
+def geometry_for(wl):
+    """The workload's body as the binding describes it (None without one)."""
+    import paper_1608_04658_gb300 as lbm
+    if wl["kind"] == "airfoil":
+        return lbm.airfoil(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
+                           wl["camber_m"], wl["camber_p"], wl["thick"])
+    if wl["kind"] == "swimmer":
+        return lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
+                           wl["period"], ramp=bool(wl["ramp"]), free=True, mass=wl["mass"])
+    if wl["kind"] == "tgv":
+        return None
+    return lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"])
+
+
 def make_lattice(storage, wl, device, gamma_mode=0):
     import numpy as np
 
@@ -266,16 +285,9 @@ def make_lattice(storage, wl, device, gamma_mode=0):
     shape = wl["shape"]
     lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device,
                       u_face=wl.get("u_face", (0.0, 0.0, 0.0)), gamma_mode=gamma_mode)
-    if wl["kind"] == "airfoil":
-        lat.set_geometry(lbm.airfoil(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
-                                     wl["camber_m"], wl["camber_p"], wl["thick"]))
-    elif wl["kind"] == "swimmer":
-        lat.set_geometry(lbm.swimmer(wl["X"], wl["rest"], wl["tris"], wl["L"], wl["amp"], wl["wavelength"],
-                                     wl["period"], ramp=bool(wl["ramp"]), free=True, mass=wl["mass"]))
-    elif wl["kind"] == "tgv":
-        pass
-    else:
-        lat.set_geometry(lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"]))
+    geom = geometry_for(wl)
+    if geom is not None:
+        lat.set_geometry(geom)
     rho, u = initial_flow(wl)
     lat.init_state(rho, u)
     return lat, np
@@ -326,6 +338,130 @@ def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     del lat
     torch.cuda.empty_cache()
     return res
+
+
+def _split_runner(storage, wl, args, world, device):
+    """One slab per rank (DistSlab, NCCL between the GPUs); on one GPU
+    (world 1), args.slabs slab lattices in this process (SlabSet, device
+    copies between them)."""
+    from paper_1608_04658_gb300.slab import DistSlab, SlabSet
+    kw = dict(storage=storage, faces=wl["faces"], geometry=geometry_for(wl),
+              u_face=wl.get("u_face", (0.0, 0.0, 0.0)))
+    if world > 1:
+        ds = DistSlab(wl["shape"], wl["nu"], device=device, **kw)
+        return ds, [ds.lat]
+    ds = SlabSet(wl["shape"], wl["nu"], args.slabs, devices=device, **kw)
+    return ds, ds.slabs
+
+
+def time_split(storage, wl, args, world, device, clocks):
+    """The workload's box split along z into slabs (paper_1608_04658_gb300.slab,
+    lbm_set_slab): before every step the slabs swap two edge layers per side
+    (NCCL send/recv of packed layers between ranks, device copies within one
+    process), after it their force records are added in slab order on the
+    device (lbm_sum_body_force).  The value is the whole box's node updates
+    over the slowest rank's time (strong scaling: the box is fixed, each rank
+    updates its share).  The roofline figures are those of the first slab's
+    bulk launch."""
+    import torch
+    ds, lats = _split_runner(storage, wl, args, world, device)
+    lat = lats[0]
+    ds.init_state(*initial_flow(wl))
+    K, W = args.steps, args.warmup
+    ds.step(W)
+    extra = 0
+    while ds.body and any(q.launch_order() == "auto" for q in lats) and extra < 32:
+        torch.cuda.synchronize()
+        ds.step(1)
+        extra += 1
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    lat.profile_begin(K)
+    t0 = time.time()
+    start.record(lat.stream)
+    ds.step(K)
+    end.record(lat.stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    dist_barrier(world)
+    clocks.mark(t0, t1)
+    launches = ds.launches
+    bulk_ms, nbulk = lat.profile_end()
+    ms = dist_max(start.elapsed_time(end), world)
+    body = lat.body()
+    bulk_nodes = lat.N - body["n_band"] if body["n_band"] > 0 else int(((lat.flags & 5) == 0).sum().item())
+    if ds.body:
+        lat.forces()  # raises on an unstable run
+    nx, ny, nz = wl["shape"]
+    res = dict(ms=ms, glups=nx * ny * nz * K / (ms * 1e-3) / 1e9, launches=launches,
+               bulk_ms=bulk_ms / max(nbulk, 1), bulk_nodes=bulk_nodes, body=body,
+               order=",".join(q.launch_order() for q in lats), trial_steps_after_warmup=extra,
+               slab_layers=lat.shape[2], slabs=len(lats) if world == 1 else world)
+    for q in lats:
+        q.close()
+    del ds, lat, lats
+    torch.cuda.empty_cache()
+    return res
+
+
+def e2e_split(storage, wl, args, world, device):
+    """e2e_storage for the z-slab split: each slab copies its rows of the
+    pinned initial fields (halo rows included) to the device and builds its
+    state from them, then K steps with the exchanges and force hand-overs,
+    each step's summed force record read by the host at most two steps later;
+    the value is the whole box's node updates over the slowest rank's time."""
+    import torch
+
+    from paper_1608_04658_gb300.slab import slab_rows
+    ds, lats = _split_runner(storage, wl, args, world, device)
+    rho, u = initial_flow(wl)
+    nz = wl["shape"][2]
+    parts = world if world > 1 else len(lats)
+    ks = [ds.rank] if world > 1 else list(range(parts))
+    rows = [slab_rows(nz, parts, k, 2) for k in ks]
+    ds.init_state(rho, u)
+    ds.step(max(args.warmup, 1))
+    extra = 0
+    while ds.body and any(q.launch_order() == "auto" for q in lats) and extra < 32:
+        torch.cuda.synchronize()
+        ds.step(1)
+        extra += 1
+    h_rho = [torch.from_numpy(rho[r]).pin_memory() for r in rows]
+    h_u = [torch.from_numpy(u[r]).pin_memory() for r in rows]
+    del rho, u
+    K = args.steps
+    lat = lats[0]
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    t0 = time.perf_counter()
+    for q, a, b in zip(lats, h_rho, h_u):
+        q.init_state(a, b)
+    pending = []
+    for _ in range(K):
+        ds.step(1)
+        if ds.body:
+            pending.append(lat.forces_async())
+            if len(pending) > 2:
+                lat.forces_wait(pending.pop(0))
+    for tk in pending:
+        lat.forces_wait(tk)
+    torch.cuda.synchronize()
+    t = dist_max(time.perf_counter() - t0, world)
+    for q in lats:
+        q.close()
+    del ds, lat, lats
+    torch.cuda.empty_cache()
+    nx, ny, _ = wl["shape"]
+    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in zip(h_rho, h_u))
+    return {"value": round(nx * ny * nz * K / t / 1e9, 4), "unit": "GLUPS",
+            "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60 if wl["kind"] != "tgv" else 0,
+            "note": "each slab: its rows of the initial density and velocity fields (pinned FP64, 32 bytes per "
+                    "node, halo rows included) copied to the device and turned into its state by lbm_init_state "
+                    "once per run; every step's summed force record (60 bytes) read by the host at most two "
+                    "steps later; h2d counted on this rank"}
 
 
 def e2e_storage(storage, wl, args, device):
@@ -600,8 +736,13 @@ def run_ours(args):
             print(json.dumps({"adjoint": adj}), flush=True)
         return
     wl = workload(args.shape, args.workload)
+    # several GPUs split the box along z (one slab per rank, halo exchange);
+    # --parallel replicas runs independent copies instead
+    split = args.parallel == "split" or (args.parallel == "auto" and world > 1)
     clocks = ClockSampler(local)
     clocks.start()
+    if split:
+        return run_split(args, wl, world, rank, device, clocks)
     main = time_storage(args.storage, wl, args, world, device, clocks)
     variants = {}
     if not args.no_variants:
@@ -683,6 +824,61 @@ def run_ours(args):
                                   "launch_order": r["order"]}
                              for st, r in res.items()}
                       for name, (w2, res) in second.items()},
+    }
+    print(json.dumps(line))
+
+
+def run_split(args, wl, world, rank, device, clocks):
+    """The JSON line of the z-slab split: the headline storage form on the
+    workload's box and, unless left out, the second workload's box in FP32;
+    the variants, the adjoint and the accuracy runs are single-GPU figures and
+    are not repeated here."""
+    main = time_split(args.storage, wl, args, world, device, clocks)
+    second = {}
+    if args.second_workload != "none" and args.second_workload != args.workload:
+        wl2 = workload(None, args.second_workload)
+        second[wl2["name"]] = {"fp32": time_split("fp32", wl2, args, world, device, clocks)}
+    clk = clocks.stop()
+    e2e = None if args.no_e2e else e2e_split(args.storage, wl, args, world, device)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_hbm_peak()
+    B = BYTES_PER_NODE[args.storage]
+
+    def roofline(st, r):
+        bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
+        achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "bulk_kernel (rank 0's slab)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": bytes_launch,
+                "bulk_ms_per_launch": round(r["bulk_ms"], 5)}
+
+    nx, ny, nz = wl["shape"]
+    N = nx * ny * nz
+    line = {
+        "metric": METRIC, "value": round(main["glups"], 4), "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(main["ms"] / args.steps, 5),
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": DTYPE[args.storage],
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "storage": args.storage, "nodes": N, "bytes_per_node_update": B,
+                   "hbm_roofline_glups": round(peak / B, 3),
+                   "percent_of_hbm_roofline_step": round(100 * main["glups"] * B / world / peak, 2),
+                   "l2": "inputs larger than L2 (population buffers %d MB per rank)"
+                         % (27 * N // world * (B // 54) // 2 ** 20),
+                   "parallelism": f"z slabs x{main['slabs']}" + (" (one GPU)" if world == 1 else ""),
+                   "slab_layers_rank0": main["slab_layers"],
+                   "halo_layers": 2, "launch_order": main["order"],
+                   "trial_steps_after_warmup": main["trial_steps_after_warmup"]},
+        "roofline": roofline(args.storage, main),
+        "cpu_baseline": None,
+        "e2e": e2e,
+        "gpu_launches": main["launches"],
+        "clocks": clk,
+        "workloads": {name: {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],
+                                  "ms_per_step": round(r["ms"] / args.steps, 5),
+                                  "roofline": roofline(st, r), "gpu_launches": r["launches"]}
+                             for st, r in res.items()}
+                      for name, res in second.items()},
     }
     print(json.dumps(line))
 

@@ -382,16 +382,24 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, doubl
  * zper layers: its z layer k is the box's layer (zoff + k) mod zper.  Its
  * layers [own_lo, own_hi) are its own; the others are halo layers that the
  * caller refills before every step with the neighbouring slabs' own layers
- * (two halo layers per side are needed).  The body's geometry (solid test,
- * nearest image, the sphere's centre wrap, torque arm) uses the box's z; the
- * force and torque of a step sum the links of own fluid nodes only; the
- * caller adds the slabs' sums (in a fixed slab order, so every slab holds the
- * same bits) and hands the total to every slab with lbm_set_body_force before
- * the next step, so the body copies move alike.  The context's own z faces
- * must be walls (no own node reads them).  Bodies: sphere, airfoil, planes
- * (the mesh is LBM_ERR_UNSUPPORTED); no adjoint.  Call before
- * lbm_set_geometry.  Errors: LBM_ERR_ARG (sizes, faces), LBM_ERR_STATE (a
- * body is already set). */
+ * (two halo layers per side are needed).  The body's pose stays in the box's
+ * z (lbm_body_state reports it there): the sphere, airfoil and planes test
+ * and wrap in the box's z; the mesh is placed in the slab's frame at the
+ * image of its z nearest the slab's middle layer (its band cut at the slab's
+ * layers).  The sphere's and the mesh's bands cover the image nearest the
+ * slab's middle layer mid = nz / 2, so every other image must miss the
+ * layers whose marks own nodes read, [own_lo - 1, own_hi]:
+ * lbm_set_geometry fails with LBM_ERR_ARG unless (zper - e) / 2 > m, e the
+ * body's z extent (sphere 2R, mesh that of its rest mesh) and m the largest
+ * distance of those layers from mid.  The force and
+ * torque of a step sum the links of own fluid nodes only; the caller adds the
+ * slabs' sums (in a fixed slab order, so every slab holds the same bits) and
+ * hands the total to every slab with lbm_set_body_force before the next step,
+ * so the body copies move alike.  The context's own z faces must be both
+ * walls or both periodic: no own node reads across them, and periodic faces
+ * let the bulk kernel take its all-periodic form when x and y are periodic
+ * too.  No adjoint on a slab.  Call before lbm_set_geometry.
+ * Errors: LBM_ERR_ARG (sizes, faces), LBM_ERR_STATE (a body is already set). */
 LBM_API lbm_status lbm_set_slab(lbm_ctx *ctx, int zoff, int zper, int own_lo, int own_hi);
 
 /* Copies the z layers [z0, z0 + nlayers) of the current state, all 27
@@ -408,6 +416,17 @@ LBM_API lbm_status lbm_unpack_layers(lbm_ctx *ctx, int z0, int nlayers, const vo
  * lbm_body_forces' average follow.  Asynchronous on the context stream.
  * LBM_ERR_STATE without a body. */
 LBM_API lbm_status lbm_set_body_force(lbm_ctx *ctx, const double F[3], const double M[3]);
+
+/* The same hand-over without the host: lbm_body_force_to_device copies the
+ * body's current force and torque (F x, y, z, then M x, y, z: 6 doubles) to
+ * the device buffer dst; lbm_sum_body_force replaces them by the sum of
+ * nparts such records at parts (device, 6 * nparts doubles, record k at
+ * 6k), added in record order from record 0 (the same bits as that order of
+ * additions on the host).  Both asynchronous on the context stream; dst and
+ * parts must stay valid until the stream reaches the call.  LBM_ERR_ARG for
+ * a null buffer or nparts < 1, LBM_ERR_STATE without a body. */
+LBM_API lbm_status lbm_body_force_to_device(lbm_ctx *ctx, double *dst);
+LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int nparts);
 
 /* Global sums without a context and without device allocation.  The paper
  * has no counterpart to this entry point; it exists for callers that cannot

@@ -146,6 +146,10 @@ def lib():
         L.lbm_unpack_layers.restype = C.c_int
         L.lbm_set_body_force.argtypes = [vp, _D, _D]
         L.lbm_set_body_force.restype = C.c_int
+        L.lbm_body_force_to_device.argtypes = [vp, vp]
+        L.lbm_body_force_to_device.restype = C.c_int
+        L.lbm_sum_body_force.argtypes = [vp, vp, C.c_int]
+        L.lbm_sum_body_force.restype = C.c_int
         _lib = L
     return _lib
 
@@ -257,6 +261,8 @@ class Lattice:
         self.storage = storage
         self.rho0 = float(rho0)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self.device.index is None:
+            self.device = torch.device(self.device.type, torch.cuda.current_device())
         dt = getattr(torch, _TORCH_DTYPES[storage])
         self.f_a = torch.empty((27, nz, ny, nx), dtype=dt, device=self.device)
         self.f_b = torch.empty((27, nz, ny, nx), dtype=dt, device=self.device)
@@ -460,6 +466,26 @@ class Lattice:
         Fa = np.ascontiguousarray(F, dtype=np.float64)
         Ma = np.ascontiguousarray(M, dtype=np.float64)
         self._check(lib().lbm_set_body_force(self._ctx, Fa.ctypes.data_as(_D), Ma.ctypes.data_as(_D)))
+
+    def body_force_to(self, out=None):
+        """The body's current force and torque (6 doubles) copied into a device
+        tensor, without a host synchronisation (lbm_body_force_to_device)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(6, dtype=torch.float64, device=self.device)
+        if out.dtype != torch.float64 or out.numel() < 6 or not out.is_contiguous() or out.device != self.device:
+            raise ValueError("body_force_to: a contiguous float64 tensor of 6 values on the lattice's device")
+        self._check(lib().lbm_body_force_to_device(self._ctx, C.c_void_p(out.data_ptr())))
+        return out
+
+    def sum_body_force(self, parts):
+        """Replaces the body's force and torque by the sum, in row order, of the
+        rows of a device tensor (nparts, 6) of float64 (lbm_sum_body_force)."""
+        torch = _torch()
+        if parts.dtype != torch.float64 or parts.dim() != 2 or parts.shape[1] != 6 or not parts.is_contiguous() \
+                or parts.device != self.device:
+            raise ValueError("sum_body_force: a contiguous float64 tensor (nparts, 6) on the lattice's device")
+        self._check(lib().lbm_sum_body_force(self._ctx, C.c_void_p(parts.data_ptr()), int(parts.shape[0])))
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

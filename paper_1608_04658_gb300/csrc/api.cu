@@ -2,6 +2,7 @@
 // management and the per-step launch sequence.  Host code only enqueues
 // kernels; the state, the body and its force never leave the device during
 // lbm_step.
+#include <cstddef>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -235,8 +236,6 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     G.zper = ctx->slab_zper;
     G.own_lo = ctx->slab_zper > 0 ? ctx->slab_own_lo : 0;
     G.own_hi = ctx->slab_zper > 0 ? ctx->slab_own_hi : L.nz;
-    if (ctx->slab_zper > 0 && g->kind == LBM_BODY_MESH)
-        return fail(ctx, LBM_ERR_UNSUPPORTED, "lbm_set_geometry: a slab takes the sphere, airfoil or planes, not the mesh");
     if (ctx->slab_zper > 0 && g->kind == LBM_BODY_SPHERE && !(g->X[2] >= 0.0 && g->X[2] < (double)ctx->slab_zper))
         return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: sphere centre outside [0, zper) of the slab's whole box");
     G.R = g->R;
@@ -246,7 +245,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.U_lo[a] = g->U_lo[a];
         G.U_hi[a] = g->U_hi[a];
         G.g[a] = g->g[a];
-        G.periodic[a] = L.face[2 * a] == LBM_FACE_PERIODIC;
+        // (a slab's z is cut at its layers whatever its faces)
+        G.periodic[a] = L.face[2 * a] == LBM_FACE_PERIODIC && !(a == 2 && ctx->slab_zper > 0);
     }
     // Sec. 4.1: a sphere given no mass takes m_s = rho_s pi D^3 / 6 with
     // rho_s = rho_ratio rho0 (the analytic volume, not the voxel count)
@@ -376,6 +376,19 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         }
     } else {
         for (int a = 0; a < 3; ++a) G.cap[a] = n[a];
+    }
+    if (ctx->slab_zper > 0 && (g->kind == LBM_BODY_SPHERE || g->kind == LBM_BODY_MESH)) {
+        // a slab marks and sweeps the image of the body nearest its middle
+        // layer; any other image (zper away) must miss the layers whose marks
+        // own nodes read, [own_lo - 1, own_hi], wherever the body is: half
+        // the period less half the body's z extent beyond the farthest of
+        // them from the middle
+        const double ext = g->kind == LBM_BODY_SPHERE ? 2.0 * G.R : G.mesh_ext[5] - G.mesh_ext[4];
+        const double mid = 0.5 * (double)L.nz;
+        const double m = std::max(mid - (double)(ctx->slab_own_lo - 1), (double)ctx->slab_own_hi - mid);
+        if (!(0.5 * ((double)ctx->slab_zper - ext) > m))
+            return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: body too long in z for the slab (its z extent "
+                                          "and the slab's layers reach the next image along z)");
     }
     const long long vol = (long long)G.cap[0] * G.cap[1] * G.cap[2];
     if (vol >= (1LL << 31) / 6) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: body band too large");
@@ -914,8 +927,8 @@ lbm_status lbm_set_slab(lbm_ctx *ctx, int zoff, int zper, int own_lo, int own_hi
     if (ctx->has_body) return fail(ctx, LBM_ERR_STATE, "lbm_set_slab: call it before lbm_set_geometry");
     if (zper < L.nz - 2 || zper < 1 || own_lo < 0 || own_hi > L.nz || own_lo >= own_hi)
         return fail(ctx, LBM_ERR_ARG, "lbm_set_slab: need zper >= nz - 2 and 0 <= own_lo < own_hi <= nz");
-    if (L.face[4] != LBM_FACE_WALL || L.face[5] != LBM_FACE_WALL)
-        return fail(ctx, LBM_ERR_ARG, "lbm_set_slab: the slab's own z faces must be walls");
+    if (L.face[4] != L.face[5] || (L.face[4] != LBM_FACE_WALL && L.face[4] != LBM_FACE_PERIODIC))
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_slab: the slab's own z faces must be both walls or both periodic");
     ctx->slab_zoff = zoff;
     ctx->slab_zper = zper;
     ctx->slab_own_lo = own_lo;
@@ -958,5 +971,26 @@ lbm_status lbm_set_body_force(lbm_ctx *ctx, const double F[3], const double M[3]
         fm[3 + a] = M[a];
     }
     LBM_CUDA(launch_set_force(ctx->S, ctx->bcur, fm, ctx->stream), "lbm_set_body_force");
+    return LBM_OK;
+}
+
+lbm_status lbm_body_force_to_device(lbm_ctx *ctx, double *dst)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!dst) return fail(ctx, LBM_ERR_ARG, "lbm_body_force_to_device: null buffer");
+    if (!ctx->has_body) return fail(ctx, LBM_ERR_STATE, "lbm_body_force_to_device: no body");
+    const DevBody *b = ctx->S.body + ctx->bcur;
+    static_assert(offsetof(DevBody, M) == offsetof(DevBody, F) + 3 * sizeof(double), "F and M adjacent");
+    LBM_CUDA(cudaMemcpyAsync(dst, b->F, 6 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+             "lbm_body_force_to_device");
+    return LBM_OK;
+}
+
+lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int nparts)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!parts || nparts < 1) return fail(ctx, LBM_ERR_ARG, "lbm_sum_body_force: null buffer or no parts");
+    if (!ctx->has_body) return fail(ctx, LBM_ERR_STATE, "lbm_sum_body_force: no body");
+    LBM_CUDA(launch_sum_force(ctx->S, ctx->bcur, parts, nparts, ctx->stream), "lbm_sum_body_force");
     return LBM_OK;
 }

@@ -115,6 +115,7 @@ struct Force6 {
     double v[6];
 };
 cudaError_t launch_set_force(Scratch &S, int cur, const double fm[6], cudaStream_t s);
+cudaError_t launch_sum_force(Scratch &S, int cur, const double *parts, int n, cudaStream_t s);
 // true when the band is known before the step's geometry runs (all bodies but
 // the walls, whose band is the whole box, and the swimmer in the
 // centre-of-mass frame, whose band follows from the pose of the step)

@@ -43,6 +43,18 @@ __device__ __forceinline__ double frame_offset(int a, int p, double X, int n, in
     return axis_offset(p, X, n, periodic);
 }
 
+// A z coordinate of the whole box in a slab's own frame, at the image
+// nearest the slab's middle layer (no slab: unchanged).
+__device__ __forceinline__ double slab_z(const GeomParams &G, double Zg, int nz)
+{
+    if (G.zper <= 0) return Zg;
+    double z = __dsub_rn(Zg, (double)G.zoff);
+    const double mid = 0.5 * (double)nz, per = (double)G.zper;
+    if (z - mid > 0.5 * per) z = __dsub_rn(z, per);
+    else if (z - mid < -0.5 * per) z = __dadd_rn(z, per);
+    return z;
+}
+
 // Airfoil in its chord frame (see lbm_geometry): camber line and half thickness
 __device__ __forceinline__ double airfoil_camber(const GeomParams &G, double xi)
 {
@@ -820,8 +832,9 @@ __device__ __forceinline__ void airfoil_link_tangent(const GeomParams &G, const 
 __device__ __forceinline__ double body_offset(const Lattice &L, const GeomParams &G, const DevBody *b,
                                               int a, int p)
 {
-    if (G.kind == LBM_BODY_MESH) return __dsub_rn((double)p, b->X[a]);
-    // (a slab's z is that of the whole box)
+    // (the mesh: a slab's z in the slab's frame, where its pose is placed;
+    // the other bodies: a slab's z is that of the whole box)
+    if (G.kind == LBM_BODY_MESH) return __dsub_rn((double)p, a == 2 ? slab_z(G, b->X[2], L.nz) : b->X[a]);
     const int pz = a == 2 && G.zper > 0 ? p + G.zoff : p;
     if (G.kind == LBM_BODY_AIRFOIL) return a < 2 ? __dsub_rn((double)p, b->X[a]) : (double)pz;
     if (G.kind != LBM_BODY_SPHERE) return (double)pz;

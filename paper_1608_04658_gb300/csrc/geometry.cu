@@ -41,11 +41,14 @@ __device__ void advance_mesh(const Lattice &L, const GeomParams &G, const DevBod
         h[0] = max(prev->ibox[1], next->ibox[1]) + BAND_MARGIN;
         l[1] = min(prev->ibox[2], next->ibox[2]) - BAND_MARGIN;
         h[1] = max(prev->ibox[3], next->ibox[3]) + BAND_MARGIN;
-        l[2] = (int)floor(X[2] + G.mesh_ext[4]) - BAND_MARGIN;
-        h[2] = (int)floor(X[2] + G.mesh_ext[5]) + BAND_MARGIN + 1;
+        const double Xz = slab_z(G, X[2], n[2]);
+        l[2] = (int)floor(Xz + G.mesh_ext[4]) - BAND_MARGIN;
+        h[2] = (int)floor(Xz + G.mesh_ext[5]) + BAND_MARGIN + 1;
         for (int a = 0; a < 3; ++a) {
-            if (l[a] < 0) { l[a] = 0; overflow = 1; }
-            if (h[a] > n[a] - 1) { h[a] = n[a] - 1; overflow = 1; }
+            // a slab's z: cut at its layers (not an overflow)
+            const bool cut = a == 2 && G.zper > 0;
+            if (l[a] < 0) { l[a] = 0; overflow |= !cut; }
+            if (h[a] > n[a] - 1) { h[a] = n[a] - 1; overflow |= !cut; }
             int c = h[a] >= l[a] ? h[a] - l[a] + 1 : 0;
             if (c > G.cap[a]) { c = G.cap[a]; overflow = 1; }
             lo[a] = l[a];
@@ -62,12 +65,16 @@ __device__ void advance_mesh(const Lattice &L, const GeomParams &G, const DevBod
         U[0] = __dadd_rn(prev->U[0], __dmul_rn(prev->F[0], G.inv_mass));
     }
     for (int a = 0; a < 3; ++a) {
-        const double mn = fmin(prev->X[a], X[a]) + G.mesh_ext[2 * a];
-        const double mx = fmax(prev->X[a], X[a]) + G.mesh_ext[2 * a + 1];
+        // a slab's z: the pose in its own frame, cut at its layers (not an overflow)
+        const bool cut = a == 2 && G.zper > 0;
+        const double Xp = cut ? slab_z(G, prev->X[2], n[2]) : prev->X[a];
+        const double Xn = cut ? slab_z(G, X[2], n[2]) : X[a];
+        const double mn = fmin(Xp, Xn) + G.mesh_ext[2 * a];
+        const double mx = fmax(Xp, Xn) + G.mesh_ext[2 * a + 1];
         int l = (int)floor(mn) - BAND_MARGIN;
         int hi = (int)floor(mx) + BAND_MARGIN + 1;
-        if (l < 0) { l = 0; overflow = 1; }
-        if (hi > n[a] - 1) { hi = n[a] - 1; overflow = 1; }
+        if (l < 0) { l = 0; overflow |= !cut; }
+        if (hi > n[a] - 1) { hi = n[a] - 1; overflow |= !cut; }
         int c = hi >= l ? hi - l + 1 : 0;
         if (c > G.cap[a]) { c = G.cap[a]; overflow = 1; }
         lo[a] = l;
@@ -404,7 +411,7 @@ __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L
         const double qx = s - next->com[0], qy = (swimmer_midline(G, s, t) + dy) - next->com[1];
         p[0] = sX[0] + (cs * qx - sn * qy);
         p[1] = sX[1] + (sn * qx + cs * qy);
-        p[2] = sX[2] + dz;
+        p[2] = slab_z(G, sX[2], L.nz) + dz;
         const double rate = 0.5 * (swimmer_midline(G, s, t + 1.0) - swimmer_midline(G, s, t - 1.0));
         const double wx = -next->com_dot[0], wy = rate - next->com_dot[1];
         double *q = G.mesh_vel + 3 * (size_t)gid;
@@ -424,7 +431,7 @@ __global__ void __launch_bounds__(MESH_THREADS) mesh_pose_kernel(const Lattice L
     }
     p[0] = __dadd_rn(sX[0], s);
     p[1] = __dadd_rn(__dadd_rn(sX[1], swimmer_midline(G, s, t)), dy);
-    p[2] = __dadd_rn(sX[2], dz);
+    p[2] = __dadd_rn(slab_z(G, sX[2], L.nz), dz);  // a slab's pose in its own z frame
     for (int a = 0; a < 3; ++a) {
         const double r = rint(p[a]);
         G.mesh_ipos[3 * (size_t)gid + a] = (int)r;
@@ -744,6 +751,29 @@ __global__ void set_force_kernel(DevBody *__restrict__ b, Force6 fm)
         b->F[a] = fm.v[a];
         b->M[a] = fm.v[3 + a];
     }
+}
+
+// the force and torque of a body state from n partial sums (6 doubles each,
+// device), added in part order starting from part 0; running sums follow
+__global__ void sum_force_kernel(DevBody *__restrict__ b, const double *__restrict__ parts, int n)
+{
+    if (threadIdx.x != 0) return;
+    double fm[6];
+    for (int k = 0; k < 6; ++k) fm[k] = parts[k];
+    for (int p = 1; p < n; ++p)
+        for (int k = 0; k < 6; ++k) fm[k] = __dadd_rn(fm[k], parts[6 * (size_t)p + k]);
+    for (int a = 0; a < 3; ++a) {
+        b->F_sum[a] = __dadd_rn(__dsub_rn(b->F_sum[a], b->F[a]), fm[a]);
+        b->M_sum[a] = __dadd_rn(__dsub_rn(b->M_sum[a], b->M[a]), fm[3 + a]);
+        b->F[a] = fm[a];
+        b->M[a] = fm[3 + a];
+    }
+}
+
+cudaError_t launch_sum_force(Scratch &S, int cur, const double *parts, int n, cudaStream_t s)
+{
+    sum_force_kernel<<<1, 32, 0, s>>>(S.body + cur, parts, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_set_force(Scratch &S, int cur, const double fm[6], cudaStream_t s)

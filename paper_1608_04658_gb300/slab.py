@@ -39,7 +39,7 @@ def slab_rows(nz: int, parts: int, k: int, halo: int = HALO) -> list[int]:
     return [(z0 - halo + j) % nz for j in range(z1 - z0 + 2 * halo)]
 
 
-def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, **kw):
+def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, local_z=_b.FACE_PERIODIC, **kw):
     nx, ny, nz = shape
     if faces[4] != _b.FACE_PERIODIC or faces[5] != _b.FACE_PERIODIC:
         raise ValueError("the split axis z must be periodic")
@@ -47,7 +47,10 @@ def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, **kw):
     if z1 - z0 < halo:
         raise ValueError("slabs thinner than the halo")
     nloc = z1 - z0 + 2 * halo
-    local_faces = (faces[0], faces[1], faces[2], faces[3], _b.FACE_WALL, _b.FACE_WALL)
+    # the slab's own z faces (no own node reads across them): periodic by
+    # default, so the bulk kernel keeps its all-periodic form where x and y
+    # are periodic; walls give the same own nodes
+    local_faces = (faces[0], faces[1], faces[2], faces[3], local_z, local_z)
     lat = _b.Lattice((nx, ny, nloc), nu, storage=storage, faces=local_faces, device=device, **kw)
     lat.set_slab(z0 - halo, nz, halo, nloc - halo)
     return lat
@@ -62,15 +65,17 @@ def _fixed_order_sum(parts):
 
 class SlabSet:
     """All slabs of one box in this process.  devices: one device for every
-    slab, or a list (slab k on devices[k % len])."""
+    slab, or a list (slab k on devices[k % len]); local_z: the slabs' own z
+    face kind (FACE_PERIODIC or FACE_WALL)."""
 
     def __init__(self, shape, nu, parts, storage="fp32", faces=(0,) * 6, geometry=None, devices=None,
-                 halo=HALO, **kw):
+                 halo=HALO, local_z=_b.FACE_PERIODIC, **kw):
         self.shape = tuple(int(v) for v in shape)
         self.parts, self.halo = int(parts), int(halo)
         devs = devices if isinstance(devices, (list, tuple)) else [devices]
         self.slabs = [_slab_lattice(self.shape, nu, storage, faces, self.parts, k, self.halo,
-                                    devs[k % len(devs)], **kw) for k in range(self.parts)]
+                                    devs[k % len(devs)], local_z=local_z, **kw) for k in range(self.parts)]
+        self.launches = 0
         self.body = geometry is not None
         if self.body:
             for lat in self.slabs:
@@ -95,16 +100,27 @@ class SlabSet:
 
     def step(self, n: int = 1):
         """n steps: exchange, step every slab, then the slabs' forces added in
-        slab order and handed to every body copy."""
+        slab order on the device and handed to every body copy
+        (lbm_body_force_to_device, lbm_sum_body_force: no host round trip)."""
+        import torch
+        self.launches = 0
         for _ in range(n):
             self.exchange()
             for lat in self.slabs:
                 lat.step(1)
+                self.launches += lat.launches()
             if self.body:
-                fm = _fixed_order_sum([np.concatenate([b["F"], b["M"]]) for b in (lat.body() for lat in self.slabs)])
+                dev0 = self.slabs[0].device
+                parts = torch.stack([lat.body_force_to().to(dev0) for lat in self.slabs])
                 for lat in self.slabs:
-                    lat.set_body_force(fm[:3], fm[3:])
-                self.last_force = fm
+                    lat.sum_body_force(parts.to(lat.device))
+                    self.launches += 1
+                self._parts = parts
+
+    @property
+    def last_force(self) -> np.ndarray:
+        """The summed force and torque of the last step (host copy, FP64 6)."""
+        return self.slabs[0].body_force_to().cpu().numpy()
 
     def populations(self) -> np.ndarray:
         """The own layers of every slab assembled into the whole box, decoded
@@ -126,52 +142,87 @@ class DistSlab:
     """This rank's slab of one box split over the ranks of the default
     torch.distributed process group (one slab per rank, ranks in z order):
     edge layers by send/recv of packed device tensors, the force and torque
-    gathered and added in rank order."""
+    records all-gathered and added in rank order on the device.  Every
+    operation is enqueued on the lattice's stream (the collectives wait on it
+    and it on them), so a step needs no host synchronisation.  lattice: an
+    object with the Lattice methods used here in place of a new slab lattice
+    (the exchange and the force hand-over run on it unchanged)."""
 
-    def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, geometry=None, device=None, halo=HALO, **kw):
+    def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, geometry=None, device=None, halo=HALO,
+                 lattice=None, **kw):
         import torch.distributed as dist
         self.dist = dist
-        self.world, self.rank = dist.get_world_size(), dist.get_rank()
+        if dist.is_available() and dist.is_initialized():
+            self.world, self.rank = dist.get_world_size(), dist.get_rank()
+        else:
+            self.world, self.rank = 1, 0
+        if self.world < 2:
+            raise ValueError("DistSlab needs a process group of two or more ranks (one GPU: SlabSet)")
         self.shape = tuple(int(v) for v in shape)
         self.halo = int(halo)
-        self.lat = _slab_lattice(self.shape, nu, storage, faces, self.world, self.rank, self.halo, device, **kw)
+        self.lat = lattice if lattice is not None else \
+            _slab_lattice(self.shape, nu, storage, faces, self.world, self.rank, self.halo, device, **kw)
         self.body = geometry is not None
-        if self.body:
+        if self.body and lattice is None:
             self.lat.set_geometry(geometry)
         self.z0, self.z1 = slab_bounds(self.shape[2], self.world, self.rank)
+        self.launches = 0
 
     def init_state(self, rho, u, xi=None, amp: float = 0.0):
         rows = slab_rows(self.shape[2], self.world, self.rank, self.halo)
         self.lat.init_state(rho[rows], u[rows], xi[:, rows] if xi is not None else None, amp)
 
-    def exchange(self):
+    def _on_stream(self):
+        import contextlib
+
         import torch
+        stream = getattr(self.lat, "stream", None)
+        return torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+
+    def exchange(self):
+        """Halo layers from the neighbouring ranks' own edge layers: rank r
+        sends its first own layers down to r - 1 and its last up to r + 1
+        (periodic in rank order)."""
         lat, h = self.lat, self.halo
         nloc = lat.shape[2]
         lo_out, hi_out = lat.pack_layers(h, h), lat.pack_layers(nloc - 2 * h, h)
-        if self.world == 1:
-            lo_in, hi_in = hi_out, lo_out
-        else:
-            lat.stream.synchronize()
-            lower, upper = (self.rank - 1) % self.world, (self.rank + 1) % self.world
-            lo_in, hi_in = torch.empty_like(lo_out), torch.empty_like(hi_out)
-            ops = [self.dist.P2POp(self.dist.isend, lo_out, lower), self.dist.P2POp(self.dist.isend, hi_out, upper),
-                   self.dist.P2POp(self.dist.irecv, hi_in, upper), self.dist.P2POp(self.dist.irecv, lo_in, lower)]
+        import torch
+        lower, upper = (self.rank - 1) % self.world, (self.rank + 1) % self.world
+        lo_in, hi_in = torch.empty_like(lo_out), torch.empty_like(hi_out)
+        with self._on_stream():
+            ops = [self.dist.P2POp(self.dist.isend, lo_out, lower),
+                   self.dist.P2POp(self.dist.isend, hi_out, upper),
+                   self.dist.P2POp(self.dist.irecv, hi_in, upper),
+                   self.dist.P2POp(self.dist.irecv, lo_in, lower)]
             for r in self.dist.batch_isend_irecv(ops):
                 r.wait()
         lat.unpack_layers(0, lo_in)
         lat.unpack_layers(nloc - h, hi_in)
 
-    def step(self, n: int = 1):
+    def hand_over_force(self):
+        """Every rank's force and torque record gathered and added in rank
+        order into this rank's body copy (all copies get the same bits)."""
         import torch
+        mine = self.lat.body_force_to()
+        parts = [torch.empty_like(mine) for _ in range(self.world)]
+        with self._on_stream():
+            self.dist.all_gather(parts, mine)
+        self.lat.sum_body_force(torch.stack(parts))
+
+    def step(self, n: int = 1):
+        """n steps: exchange, step, force hand-over."""
+        self.launches = 0
         for _ in range(n):
             self.exchange()
             self.lat.step(1)
+            self.launches += self.lat.launches()
             if self.body:
-                b = self.lat.body()
-                mine = torch.tensor(np.concatenate([b["F"], b["M"]]), dtype=torch.float64, device=self.lat.device)
-                parts = [torch.empty_like(mine) for _ in range(self.world)]
-                self.dist.all_gather(parts, mine)
-                fm = _fixed_order_sum([p.cpu().numpy() for p in parts])
-                self.lat.set_body_force(fm[:3], fm[3:])
-                self.last_force = fm
+                self.hand_over_force()
+                self.launches += 1
+
+    @property
+    def last_force(self) -> np.ndarray:
+        return self.lat.body_force_to().cpu().numpy()
+
+    def close(self):
+        self.lat.close()

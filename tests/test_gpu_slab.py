@@ -42,9 +42,10 @@ def _undivided(lbm, shape, storage, geom, steps, faces=FACES):
     return lat, np.array(forces)
 
 
-def _split(lbm, shape, storage, geom, steps, parts, faces=FACES):
+def _split(lbm, shape, storage, geom, steps, parts, faces=FACES, local_z=None):
     from paper_1608_04658_gb300.slab import SlabSet
-    ss = SlabSet(shape, NU, parts, storage=storage, faces=faces, geometry=geom)
+    ss = SlabSet(shape, NU, parts, storage=storage, faces=faces, geometry=geom,
+                 local_z=lbm.FACE_PERIODIC if local_z is None else local_z)
     rho, u, xi = synth.parity_fields(shape, 4)
     ss.init_state(rho, u, xi, AMP)
     forces = []
@@ -76,21 +77,23 @@ def _fluid(lat, ss):
     return ~whole
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage,local_z", [("fp32", "periodic"), ("fp16", "periodic"), ("fp32", "wall")])
 @pytest.mark.parametrize("parts,shape,X", [(2, (14, 12, 20), (6.3, 5.7, 9.1)),
                                            (3, (14, 12, 21), (6.3, 5.7, 13.4))])
-def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, parts, shape, X):
+def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, local_z, parts, shape, X):
     """Sphere carried across a cut at a fixed velocity (free, with a mass so
     large that the force leaves its velocity unchanged): the own layers of
     every slab equal the undivided lattice bit for bit, the slab-ordered sum
-    of the forces equals the undivided force up to the order of addition."""
+    of the forces equals the undivided force up to the order of addition.
+    The slabs' own z faces (periodic or walls) are never read by own nodes."""
     import paper_1608_04658_gb300 as lbm
     from paper_1608_04658_gb300.slab import slab_bounds
     geom = lbm.sphere(X, 3.2, U=(0.35, -0.15, 0.3), free=True, mass=1e30)
     steps = 5
     lat, fm = _undivided(lbm, shape, storage, geom, steps)
     assert lat.body()["n_boundary"] > 0
-    ss, fs = _split(lbm, shape, storage, geom, steps, parts)
+    ss, fs = _split(lbm, shape, storage, geom, steps, parts,
+                    local_z=lbm.FACE_WALL if local_z == "wall" else lbm.FACE_PERIODIC)
     cuts = [slab_bounds(shape[2], parts, k)[0] for k in range(1, parts)]
     assert _straddles(lat, cuts)
     fluid = _fluid(lat, ss)
@@ -128,11 +131,41 @@ def test_slabs_move_a_free_sphere_with_the_summed_force():
     ss.close()
 
 
+@pytest.mark.parametrize("storage,free", [("fp32", 1), ("fp16", 1), ("fp32", 7)])
+def test_deforming_swimmer_over_slabs(storage, free):
+    """The triangulated swimmer (Sec. 4.3, deforming, refilled nodes every
+    step; free along x in its head frame, or free in x, y and yaw in its
+    centre-of-mass frame) across the cut of two slabs: each slab places the
+    mesh in its own z frame.  The solid marks of the own layers equal the
+    whole box's, the body copies agree bit for bit, and the state differs from
+    the undivided run by rounding (the pose in the slab frame, the force
+    summed in another order)."""
+    import paper_1608_04658_gb300 as lbm
+    shape, steps = (64, 32, 20), 6
+    rest, tris = synth.swimmer_mesh(32.0, 40, 24)
+    geom = lbm.swimmer((20.137 if free == 1 else 36.137, 16.371, 10.293), rest, tris, 32.0, 0.125, 32.0, 160.0,
+                       free=free, mass=synth.swimmer_volume(32.0), U=(-0.004, 0.0, 0.0), t0=5.0)
+    faces = (0,) * 6
+    lat, fm = _undivided(lbm, shape, storage, geom, steps, faces=faces)
+    ss, fs = _split(lbm, shape, storage, geom, steps, 2, faces=faces)
+    assert _straddles(lat, [10])
+    assert lat.body()["n_uncovered"] > 0
+    fluid = _fluid(lat, ss)
+    tol = {"fp32": 2e-6, "fp16": 2e-3}[storage]
+    f, g = lat.populations()[:, fluid], ss.populations()[:, fluid]
+    assert (np.abs(g - f) / np.abs(f)).max() <= tol
+    bodies = [s.body() for s in ss.slabs]
+    assert np.array_equal(bodies[0]["X"], bodies[1]["X"]) and np.array_equal(bodies[0]["U"], bodies[1]["U"])
+    assert np.abs(np.array(bodies[0]["X"]) - np.array(lat.body()["X"])).max() < 1e-9
+    assert np.abs(fs - fm).max() <= 1e-3 * np.abs(fm).max()
+    ss.close()
+
+
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 def test_bodiless_periodic_box_over_slabs(storage):
-    """Periodic box without a body (rows of 64 nodes: the two-node kernel in
-    both the whole box and the slabs, whose own z faces are walls): 4 slabs,
-    bitwise equal to the undivided box."""
+    """Periodic box without a body (rows of 64 nodes: the two-node kernel's
+    all-periodic form in both the whole box and the slabs): 4 slabs, bitwise
+    equal to the undivided box."""
     import paper_1608_04658_gb300 as lbm
     shape = (64, 10, 24)
     lat, _ = _undivided(lbm, shape, storage, None, 6, faces=(0,) * 6)
@@ -143,15 +176,18 @@ def test_bodiless_periodic_box_over_slabs(storage):
 
 def test_slab_arguments_are_checked():
     import paper_1608_04658_gb300 as lbm
-    lat = lbm.Lattice((8, 8, 8), NU, faces=(0,) * 6)
-    with pytest.raises(lbm.LbmError):
-        lat.set_slab(-2, 12, 2, 6)  # z faces must be walls
+    for zf in ((0, 0, 0, 0, 3, 3), (0, 0, 0, 0, 2, 2), (0, 0, 0, 0, 1, 3)):
+        lat = lbm.Lattice((8, 8, 8), NU, faces=zf)
+        with pytest.raises(lbm.LbmError):
+            lat.set_slab(-2, 12, 2, 6)  # z faces: both walls or both periodic
     lat = lbm.Lattice((8, 8, 8), NU, faces=(0, 0, 0, 0, 1, 1))
     with pytest.raises(lbm.LbmError):
         lat.set_slab(-2, 12, 6, 2)  # empty own range
     lat.set_slab(-2, 12, 2, 6)
     with pytest.raises(lbm.LbmError):
-        rest, tris = synth.swimmer_mesh(4.0, 8, 6)
-        lat.set_geometry(lbm.swimmer((2.1, 4.1, 4.1), rest, tris, 4.0, 0.1, 4.0, 40.0))
+        # the next image of a sphere this large (12 layers away) reaches the
+        # layers that own nodes read, (12 - 2R) / 2 <= 3
+        lat.set_geometry(lbm.sphere((4.0, 4.0, 5.0), 3.0))
+    lat.set_geometry(lbm.sphere((4.0, 4.0, 5.0), 2.9))
     with pytest.raises(lbm.LbmError):
         lat.pack_layers(7, 2)
