@@ -136,7 +136,10 @@ __device__ __forceinline__ void pair_update(const Lattice &L, const S *__restric
     }
 }
 
-// One block per 128 nodes of a row.
+// One block per 128 nodes of a row.  A row that touches no y or z face
+// other than a periodic one pulls only from inside the box along y and z, so
+// it takes the y/z-periodic form of the gather whatever the box's y and z
+// faces are (the choice is uniform over the block).
 template <typename S, bool XPER, bool YZPER>
 __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(const Lattice L,
                                                                            const S *__restrict__ fa,
@@ -147,7 +150,16 @@ __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(con
 {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x0 >= L.nx) return;
-    pair_update<S, XPER, YZPER>(L, fa, fb, flags, status, sweep, mode, x0, blockIdx.y, blockIdx.z);
+    const int y = blockIdx.y, z = blockIdx.z;
+    if constexpr (!YZPER) {
+        const bool face_row = (L.face[2] != LBM_FACE_PERIODIC && (y == 0 || y == L.ny - 1)) ||
+                              (L.face[4] != LBM_FACE_PERIODIC && (z == 0 || z == L.nz - 1));
+        if (!face_row) {
+            pair_update<S, XPER, true>(L, fa, fb, flags, status, sweep, mode, x0, y, z);
+            return;
+        }
+    }
+    pair_update<S, XPER, YZPER>(L, fa, fb, flags, status, sweep, mode, x0, y, z);
 }
 
 template <typename S>
