@@ -20,6 +20,7 @@
 // outflow clamp.  lambda(S^t)(y) = 0 where y is refilled in step t, else
 // lambda(St^t)(y).  The marks, boundary links and refilled nodes of each step
 // are those of the forward run (held fixed).
+#include <vector>
 #include <algorithm>
 #include <cstddef>
 #include <cmath>
@@ -1037,8 +1038,12 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
 }
 
 // theta-tangents of every mesh vertex at the pose of body state b: dy/dtheta
-// (position) and the central difference of it (velocity), 3 + 3 per vertex
-__global__ void __launch_bounds__(256) vertex_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b)
+// (position) and the central difference of it (velocity), 3 + 3 per vertex.
+// One warp per block: the FP64 arithmetic of a few thousand vertices spread
+// over as many SMs as there are warps, not over the few schedulers of a
+// handful of large blocks.
+constexpr int TANGENT_THREADS = 32;
+__global__ void __launch_bounds__(TANGENT_THREADS) vertex_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= G.n_vertices) return;
@@ -1286,10 +1291,11 @@ int list_blocks(int cap)
     return nb < 1 ? 1 : (nb > LBM_ADJ_LIST_BLOCKS ? LBM_ADJ_LIST_BLOCKS : nb);
 }
 
-// the reverse of step t for storage type S.  Sequential order: the caller
-// has re-run the geometry (body state of step t+1 in S.body[1], marks in
-// flags1) and cleared ext.  Split order (split, a band known ahead): the body
-// state of step t is in S.body[0] and the geometry re-run, the boundary and
+// the reverse of step t for storage type S.  The caller has put step t's
+// geometry in place: the body state of step t in S.body[0], the one its
+// geometry gave in S.body[1], its marks in flags1 and its lists and mesh
+// arrays in the context's scratch.  Sequential order: the caller has also
+// cleared ext.  Split order (split, a band known ahead): the boundary and
 // refill adjoints and the bulk adjoint over the two steps' bands run on the
 // side stream, beside the bulk adjoint of the nodes outside them.
 template <typename S>
@@ -1314,13 +1320,12 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
         const DevBody *b = Sc.body + 1;
         const int capv = G.cap[0] * G.cap[1] * G.cap[2];
         const unsigned nbb = (unsigned)((capv + 127) / 128);
-        int nl = 0;
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
-        if ((e = launch_geometry(L, G, Sc, 0, flags1, side, &nl)) != cudaSuccess) return e;
         ctx->bcur = 1;
         if ((e = cudaMemsetAsync(ext, 0, (size_t)capv * Q * sizeof(double), side)) != cudaSuccess) return e;
-        if (G.kind == LBM_BODY_MESH) vertex_tangent_kernel<<<(G.n_vertices + 255) / 256, 256, 0, side>>>(G, b);
+        if (G.kind == LBM_BODY_MESH) vertex_tangent_kernel<<<(G.n_vertices + TANGENT_THREADS - 1) / TANGENT_THREADS, TANGENT_THREADS, 0, side>>>(
+            G, b);
         adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, side>>>(
             L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot, ct);
         adjoint_bulk_kernel<S><<<nbb, 128, 0, side>>>(L, G, st, A, flags1, lam_out, BULK_BAND, box0, nullptr);
@@ -1338,7 +1343,7 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     // the boundary adjoint runs beside the bulk adjoint (disjoint rows of Lam^t)
     if (ctx->has_body) {
         if (G.kind == LBM_BODY_MESH)
-            vertex_tangent_kernel<<<(G.n_vertices + 255) / 256, 256, 0, s>>>(G, b);
+            vertex_tangent_kernel<<<(G.n_vertices + TANGENT_THREADS - 1) / TANGENT_THREADS, TANGENT_THREADS, 0, s>>>(G, b);
         if (G.kind == LBM_BODY_MESH && G.com_frame)
             com_tangent_kernel<<<(G.n_triangles + 255) / 256, 256, 0, s>>>(G, b, cpart, cticket, ct);
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
@@ -1357,6 +1362,59 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
             body_reduce_kernel<<<1, 256, 0, s>>>(bslot, G.cap[0] * G.cap[1] * G.cap[2], badj, G, b, ct, wx, wy, wz);
     }
     return cudaGetLastError();
+}
+
+// The arrays a step's geometry writes and the later kernels of that step (and
+// of its reverse) read: the boundary and uncovered lists and, for the mesh,
+// the pose and the column and cell lists.  The recompute pass gives every
+// step of a segment a slot of its own, so the reversed step finds its
+// geometry there instead of running it again.
+struct GeoSlot {
+    int *blist = nullptr, *bpos = nullptr, *ulist = nullptr, *upos = nullptr;
+    double *mesh_pos = nullptr, *mesh_vel = nullptr, *col_x = nullptr;
+    int *mesh_ipos = nullptr, *col_count = nullptr, *cell_count = nullptr, *cell_tri = nullptr;
+    float *mesh_frac = nullptr, *tri_box = nullptr;
+};
+
+static GeoSlot live_slot(const lbm_ctx *ctx)
+{
+    GeoSlot g;
+    g.blist = ctx->S.blist;
+    g.bpos = ctx->S.bpos;
+    g.ulist = ctx->S.ulist;
+    g.upos = ctx->S.upos;
+    g.mesh_pos = ctx->S.mesh_pos;
+    g.mesh_vel = ctx->S.mesh_vel;
+    g.col_x = ctx->S.col_x;
+    g.mesh_ipos = ctx->S.mesh_ipos;
+    g.col_count = ctx->S.col_count;
+    g.cell_count = ctx->S.cell_count;
+    g.cell_tri = ctx->S.cell_tri;
+    g.mesh_frac = ctx->S.mesh_frac;
+    g.tri_box = ctx->S.tri_box;
+    return g;
+}
+
+// points the context's scratch (and the geometry parameters' copies of the
+// mesh arrays) at a slot
+static void use_slot(lbm_ctx *ctx, const GeoSlot &g)
+{
+    Scratch &S = ctx->S;
+    GeomParams &G = ctx->G;
+    S.blist = g.blist;
+    S.bpos = g.bpos;
+    S.ulist = g.ulist;
+    S.upos = g.upos;
+    if (G.kind != LBM_BODY_MESH) return;
+    S.mesh_pos = G.mesh_pos = g.mesh_pos;
+    S.mesh_vel = G.mesh_vel = g.mesh_vel;
+    S.col_x = G.col_x = g.col_x;
+    S.mesh_ipos = G.mesh_ipos = g.mesh_ipos;
+    S.col_count = G.col_count = g.col_count;
+    S.cell_count = G.cell_count = g.cell_count;
+    S.cell_tri = G.cell_tri = g.cell_tri;
+    S.mesh_frac = G.mesh_frac = g.mesh_frac;
+    S.tri_box = G.tri_box = g.tri_box;
 }
 
 template <typename S>
@@ -1402,8 +1460,9 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     double Jt = 0.0;
 
     if (!B.get(&ck, (size_t)nseg * state) || !B.get(&seg, (size_t)(K + 1) * state) ||
-        !B.get(&ckflags, (size_t)nseg * N) || !B.get(&segflags, (size_t)K * N) || !B.get(&wf[0], N) ||
-        !B.get(&wf[1], N) || !B.get(&wrec, N) || !B.get(&ckbody, nseg) || !B.get(&segbody, K) || !B.get(&adjbody, 2) ||
+        !B.get(&ckflags, (size_t)nseg * N) || !B.get(&segflags, (size_t)(K + 1) * N) || !B.get(&wf[0], N) ||
+        !B.get(&wf[1], N) || !B.get(&wrec, N) || !B.get(&ckbody, nseg) || !B.get(&segbody, K + 1) ||
+        !B.get(&adjbody, 2) ||
         !B.get(&savebody, 2) || !B.get(&lam[0], state) || !B.get(&lam[1], state) ||
         !B.get(&ext[0], (size_t)cap * Q) || !B.get(&ext[1], (size_t)cap * Q) || !B.get(&tslots, (size_t)cap * 6) ||
         !B.get(&acc, 3) || !B.get(&part, nparts) || !B.get(&badj, 1) ||
@@ -1413,6 +1472,25 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
         (body && ctx->G.kind == LBM_BODY_MESH &&
          (!B.get(&tan_dy, 3 * (size_t)ctx->G.n_vertices) || !B.get(&tan_dvy, 3 * (size_t)ctx->G.n_vertices))))
         return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the checkpoints failed");
+    // a geometry slot per step of a segment (see GeoSlot)
+    const GeoSlot live = live_slot(ctx);
+    std::vector<GeoSlot> slots(body ? K : 0);
+    if (body) {
+        const GeomParams &G = ctx->G;
+        const size_t nv = (size_t)G.n_vertices, nt = (size_t)G.n_triangles;
+        const size_t ncols = (size_t)G.cap[1] * G.cap[2], ncells = (size_t)G.cells[0] * G.cells[1] * G.cells[2];
+        for (GeoSlot &g : slots) {
+            bool ok = B.get(&g.blist, (size_t)G.cap_boundary) && B.get(&g.bpos, (size_t)G.cap_boundary) &&
+                      B.get(&g.ulist, (size_t)G.cap_uncovered) && B.get(&g.upos, (size_t)G.cap_uncovered);
+            if (ok && G.kind == LBM_BODY_MESH)
+                ok = B.get(&g.mesh_pos, 3 * nv) && B.get(&g.mesh_vel, 3 * nv) && B.get(&g.mesh_ipos, 3 * nv) &&
+                     B.get(&g.mesh_frac, 3 * nv) && B.get(&g.tri_box, 6 * nt) && B.get(&g.col_count, ncols) &&
+                     B.get(&g.col_x, ncols * MESH_COL_CAP) && B.get(&g.cell_count, ncells) &&
+                     B.get(&g.cell_tri, ncells * MESH_CELL_CAP);
+            if (!ok)
+                return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the geometry slots failed");
+        }
+    }
     ctx->G.mesh_dy = tan_dy;
     ctx->G.mesh_dvy = tan_dvy;
 
@@ -1467,22 +1545,30 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
             ADJ_CUDA(cudaMemcpyAsync(wrec, ckflags + (size_t)sg * N, N, cudaMemcpyDeviceToDevice, s), "restore");
             ctx->bcur = 0;
             ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, ckbody + sg, sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "restore");
-            for (int t = t0; t < t1; ++t) {
+            // segflags[j] / segbody[j]: marks and body state before step t0 + j,
+            // which are also those that step t0 + j - 1's geometry left
+            for (int t = t0; t <= t1; ++t) {
                 const int j = t - t0;
                 ADJ_CUDA(cudaMemcpyAsync(segflags + (size_t)j * N, wrec, N, cudaMemcpyDeviceToDevice, s), "seg flags");
                 ADJ_CUDA(cudaMemcpyAsync(segbody + j, ctx->S.body + ctx->bcur, sizeof(DevBody), cudaMemcpyDeviceToDevice,
                                          s), "seg body");
+                if (t == t1) break;
+                if (body) use_slot(ctx, slots[j]);
                 ADJ_CUDA(forward_step(ctx, seg + (size_t)j * state, seg + (size_t)(j + 1) * state, wrec), "recompute");
             }
             // reverse the segment's steps
             for (int t = t1 - 1; t >= t0; --t) {
                 const int j = t - t0;
-                ADJ_CUDA(cudaMemcpyAsync(wf[p], segflags + (size_t)j * N, N, cudaMemcpyDeviceToDevice, s), "flags");
+                // step t's geometry as the recompute left it: its marks, the
+                // body state after it (the adjoint reads none of the force
+                // fields the rest of the step wrote there) and its slot
+                ADJ_CUDA(cudaMemcpyAsync(wf[p], segflags + (size_t)(j + 1) * N, N, cudaMemcpyDeviceToDevice, s),
+                         "flags");
                 ctx->bcur = 0;
-                ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, segbody + j, sizeof(DevBody), cudaMemcpyDeviceToDevice, s), "body");
+                ADJ_CUDA(cudaMemcpyAsync(ctx->S.body, segbody + j, 2 * sizeof(DevBody), cudaMemcpyDeviceToDevice, s),
+                         "body");
+                if (body) use_slot(ctx, slots[j]);
                 if (body && !split) {
-                    int nl = 0;
-                    ADJ_CUDA(launch_geometry(L, ctx->G, ctx->S, 0, wf[p], s, &nl), "geometry");
                     ctx->bcur = 1;
                     ADJ_CUDA(cudaMemsetAsync(ext[p], 0, (size_t)cap * Q * sizeof(double), s), "clear");
                 }
@@ -1522,6 +1608,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     for (int k = 0; k < 3; ++k) dJ[k] = accv[k] + hbadj.dth[k];
 
 done:
+    use_slot(ctx, live);
     ctx->G.mesh_dy = nullptr;
     ctx->G.mesh_dvy = nullptr;
     // the context keeps the state after the horizon; restore its body copies

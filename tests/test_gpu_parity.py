@@ -215,26 +215,29 @@ def test_unstable_state_is_reported():
     assert e.value.status == 4
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16", "fp64"])
-def test_sedimenting_sphere_full_size_sampled(storage):
+@pytest.mark.parametrize("case", ["fp32", "fp16", "fp64", "bf16", "fp32_exact"])
+def test_sedimenting_sphere_full_size_sampled(case):
     """Full-size sedimenting-sphere box (128x128x256, D = 16, x/y walls,
     periodic z) in the launch configuration the benchmark times: one step from
     a seeded random state, compared at every boundary node and at 4000 random
-    nodes, which the oracle computes one by one."""
+    nodes, which the oracle computes one by one.  fp32_exact: the exact
+    stabilizer (root of Eq. gamma_min) on both sides."""
     import paper_1608_04658_gb300 as lbm
+    storage = case.split("_")[0]
+    gmode = lbm.GAMMA_EXACT if case.endswith("_exact") else lbm.GAMMA_ANALYTIC
     wl = synth.sedimenting_sphere()
     shape = wl["shape"]
     rho, u, xi = synth.parity_fields(shape, 7)
     geom = lbm.sphere(wl["X"], wl["D"] / 2, U=(0.0, 0.0, -0.04), free=True, rho_ratio=wl["rho_ratio"],
                       g=wl["g"])
-    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"])
+    lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], gamma_mode=gmode)
     lat.set_geometry(geom)
     lat.init_state(rho, u, xi, 1e-3)
     f0 = lat.populations()
     lat.step(1)
     f1 = lat.populations()
     flags = lat.flags.cpu().numpy().reshape(-1)
-    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"],
+    orc = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"], gamma_mode=gmode,
                         body=oracle.sphere_body(wl["X"], wl["D"] / 2, U=(0.0, 0.0, -0.04), free=True,
                                                 rho_ratio=wl["rho_ratio"], g=wl["g"]))
     orc.set_f(f0)  # the decoded stored state is the common input
@@ -247,8 +250,10 @@ def test_sedimenting_sphere_full_size_sampled(storage):
     got = f1.reshape(27, -1)[:, nodes].T
     ok = ~np.isnan(ref[:, 0])
     assert np.array_equal(ok, (flags[nodes] & 1) == 0)
-    # one step from the same stored input: FP32 arithmetic and one rounding to storage
-    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
+    # one step from the same stored input: FP32 arithmetic and one rounding
+    # to storage (BF16: the 2e-3 bar of 16-bit storage; the exact stabilizer:
+    # the GPU's FP32 Newton root against the oracle's FP64 bisection root)
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3, "bf16": 2e-3, "fp32_exact": 2e-6}[case]
     assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
 
 
@@ -289,7 +294,7 @@ def _full_size_sampled(lat, orc_body, wl, f_fields, storage, seed):
     ref = orc.step_sampled(nodes)
     ok = ~np.isnan(ref[:, 0])
     assert np.array_equal(ok, (flags[nodes] & 1) == 0)
-    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3}[storage]
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-3, "bf16": 2e-3}[storage]
     assert float((np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])).max()) <= tol
     return len(bnodes), len(unodes)
 
@@ -317,7 +322,7 @@ def test_plunging_airfoil_full_size_sampled(storage):
     assert nb > 10000
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 def test_anguilliform_swimmer_full_size_sampled(storage):
     """Full-size swimmer (768x256x256, L = 128, 19,200 triangles) in the
     benchmark's launch configuration, held so that its pose after the warm-up
