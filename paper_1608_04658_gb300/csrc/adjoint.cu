@@ -815,63 +815,68 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
         const R lam = act ? next_adjoint<R>(L, G, A, x, y, z, n, i) : R(0);
         R Fb = kbc_vjp_lanes<R>(gi, lam, i, beta, (R)L.inv_beta, rho0, L.gamma_mode);
         // momentum exchange in J: dF_a = (-c_a - uw_a) fout - (c_a - uw_a) fin
-        double uwb[3] = {0, 0, 0};
+        // (the link arithmetic in R, the collision's precision; fin - fout as
+        // the difference of the shifted values, where W rho0 cancels)
+        R uwb[3] = {0, 0, 0};
         R fbbb = 0;
         // the torque M_z about X of the free yaw enters J with weight mw:
         // M_z = r_x dF_y - r_y dF_x, r = x_b - q c - X
         double qb_m = 0.0, gXm[2] = {0.0, 0.0};
         if (miss) {
-            const double Wr = weight<double>(i) * L.rho0;
-            const double fout = (double)fbb + Wr, fin = (double)gi + Wr;
-            const double c[3] = {(double)cx, (double)cy, (double)cz};
-            double sin_ = 0, sout = 0;
+            const R Wr = weight<R>(i) * rho0;
+            const R fout = fbb + Wr, fin = gi + Wr, dio = gi - fbb;
+            const R c[3] = {R(cx), R(cy), R(cz)};
+            R sin_ = 0, sout = 0;
             for (int a = 0; a < 3; ++a) {
-                sin_ -= (c[a] - uw[a]) * fw[a];
-                sout += (-c[a] - uw[a]) * fw[a];
-                uwb[a] += fw[a] * (fin - fout);
+                const R u = (R)uw[a], f = (R)fw[a];
+                sin_ -= (c[a] - u) * f;
+                sout += (-c[a] - u) * f;
+                uwb[a] += f * dio;
             }
             if (mw != 0.0) {
-                const double r0 = body_offset(L, G, b, 0, x) - q * c[0], r1 = body_offset(L, G, b, 1, y) - q * c[1];
-                const double dFx = (-c[0] - uw[0]) * fout - (c[0] - uw[0]) * fin;
-                const double dFy = (-c[1] - uw[1]) * fout - (c[1] - uw[1]) * fin;
-                sin_ += mw * (-r0 * (c[1] - uw[1]) + r1 * (c[0] - uw[0]));
-                sout += mw * (r0 * (-c[1] - uw[1]) - r1 * (-c[0] - uw[0]));
-                uwb[0] -= mw * r1 * (fin - fout);
-                uwb[1] += mw * r0 * (fin - fout);
-                qb_m = mw * (-c[0] * dFy + c[1] * dFx);
+                const double cd[3] = {(double)cx, (double)cy, (double)cz};
+                const double fo = (double)fout, fi = (double)fin, dd = (double)dio;
+                const double r0 = body_offset(L, G, b, 0, x) - q * cd[0], r1 = body_offset(L, G, b, 1, y) - q * cd[1];
+                const double dFx = (-cd[0] - uw[0]) * fo - (cd[0] - uw[0]) * fi;
+                const double dFy = (-cd[1] - uw[1]) * fo - (cd[1] - uw[1]) * fi;
+                sin_ += (R)(mw * (-r0 * (cd[1] - uw[1]) + r1 * (cd[0] - uw[0])));
+                sout += (R)(mw * (r0 * (-cd[1] - uw[1]) - r1 * (-cd[0] - uw[0])));
+                uwb[0] -= (R)(mw * r1 * dd);
+                uwb[1] += (R)(mw * r0 * dd);
+                qb_m = mw * (-cd[0] * dFy + cd[1] * dFx);
                 gXm[0] = -mw * dFy;
                 gXm[1] = mw * dFx;
             }
-            Fb += (R)sin_;
-            fbbb += (R)sout;
+            Fb += sin_;
+            fbbb += sout;
         }
         // Grad completion (missing lanes) and pressure excess
         R rhob = 0, utb[3] = {0, 0, 0}, dub[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         grad_pressure_adj<R>(miss ? Fb : R(0), i, act, rho_t, u_t, du, beta, rhob, utb, dub);
         // u_t = mean over missing links of (q u_f + u_w)/(1 + q), or u_w
         R unb[3] = {0, 0, 0}, ucb[3] = {0, 0, 0};
-        double qb = 0;
+        R qb = 0;
         if (miss) {
             const R inv1q = R(1) / (R(1) + qq);
             for (int a = 0; a < 3; ++a) {
                 const R v = utb[a] / nmiss;
                 if (sok[i]) {
                     unb[a] += v * qq * inv1q;
-                    uwb[a] += (double)(v * inv1q);
-                    qb += (double)(v * (su[i][1 + a] - (R)uw[a]) * inv1q * inv1q);
+                    uwb[a] += v * inv1q;
+                    qb += v * (su[i][1 + a] - (R)uw[a]) * inv1q * inv1q;
                 } else {
-                    uwb[a] += (double)v;
+                    uwb[a] += v;
                 }
             }
         }
-        qb += qb_m;
+        qb += (R)qb_m;
         // rho_t = rho0 + sum gstat + sum dyn
         R lam_row = 0;
         if (act && !miss) lam_row = Fb + rhob;
         if (miss) {
             fbbb += rhob;
             for (int a = 0; a < 3; ++a)
-                uwb[a] += (double)(rhob * R(6) * weight<R>(i) * rho0 * R(a == 0 ? cx : a == 1 ? cy : cz));
+                uwb[a] += rhob * R(6) * weight<R>(i) * rho0 * R(a == 0 ? cx : a == 1 ? cy : cz);
         }
         fd_gradient_adj<R>(sok, dub, lane, unb, ucb);
         if (lane == 13)
@@ -897,8 +902,9 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             gb[1] += gXm[1];
         } else if (miss && G.kind == LBM_BODY_MESH) {
             double dq[3], duw[3][3];
-            mesh_link_tangent(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
-            for (int k = 0; k < 3; ++k) tb[k] = qb * dq[k] + uwb[0] * duw[k][0] + uwb[1] * duw[k][1] + uwb[2] * duw[k][2];
+            mesh_link_tangent<R>(G, b, x, y, z, cx, cy, cz, q, hit, dq, duw);
+            for (int k = 0; k < 3; ++k)
+                tb[k] = (double)(qb * (R)dq[k] + uwb[0] * (R)duw[k][0] + uwb[1] * (R)duw[k][1] + uwb[2] * (R)duw[k][2]);
             if (bslot) {
                 // the head frame: every vertex moves with X0, u_w with U0
                 double dqX, duwX[3];
@@ -926,10 +932,11 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_boundary_kernel(
             airfoil_plunge_tangent(G, b->t, dX1, dU1);
             for (int k = 0; k < 2; ++k) tb[k] = qb * dq[k] + uwb[1] * dU1[k];
         }
+        // per-node sums over the links in R; the slots sum the nodes in double
         for (int k = 0; k < 3; ++k) {
-            double v = tb[k];
+            R v = (R)tb[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] += v;
+            if (lane == 0) tslots[(size_t)bpos[slot] * 6 + k] += (double)v;
         }
         // the free body's state through q and u_w of each missing link
         if (bslot) {

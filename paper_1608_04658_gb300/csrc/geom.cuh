@@ -502,7 +502,10 @@ __device__ __forceinline__ void swimmer_velocity_tangent(const GeomParams &G, do
 // barycentric coordinates follow from dH - dA = du e1 + dv e2 + u de1 + v de2
 // (normal equations with e1, e2); u_w = (1-u-v) V_A + u V_B + v V_C.  Vertex
 // positions move only in y, by the midline tangent at the pose's time
-// (per-vertex tangents in G.mesh_dy / G.mesh_dvy).
+// (per-vertex tangents in G.mesh_dy / G.mesh_dvy).  R is the collision
+// arithmetic: the vertices are taken relative to the node in double, the
+// rest runs in R (the link search's own precision).
+template <typename R>
 __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const DevBody *b, int x, int y, int z, int cx, int cy, int cz,
                                   double q, const MeshHit &h, double dq[3], double duw[3][3])
 {
@@ -518,52 +521,53 @@ __device__ __noinline__ static void mesh_link_tangent(const GeomParams &G, const
         return;
     }
     const int tv[3] = {G.mesh_tris[3 * h.tri], G.mesh_tris[3 * h.tri + 1], G.mesh_tris[3 * h.tri + 2]};
-    double P[3][3], V[3][3], dy[3][3], dvy[3][3];
-    for (int m = 0; m < 3; ++m) {
+    const double xb[3] = {(double)x, (double)y, (double)z};
+    R P[3][3], V[3][3], dy[3], dvy[3][3];
+    for (int m = 0; m < 3; ++m)
         for (int a = 0; a < 3; ++a) {
-            P[m][a] = G.mesh_pos[3 * tv[m] + a];
-            V[m][a] = G.mesh_vel[3 * tv[m] + a];
-            dy[m][a] = G.mesh_dy[3 * tv[m] + a];
-            dvy[m][a] = G.mesh_dvy[3 * tv[m] + a];
+            P[m][a] = (R)(G.mesh_pos[3 * tv[m] + a] - xb[a]);
+            V[m][a] = (R)G.mesh_vel[3 * tv[m] + a];
         }
-    }
-    const double c[3] = {(double)cx, (double)cy, (double)cz};
-    double e1[3], e2[3], H[3], n[3];
+    const R c[3] = {R(cx), R(cy), R(cz)};
+    R e1[3], e2[3], H[3], n[3];
     for (int a = 0; a < 3; ++a) {
         e1[a] = P[1][a] - P[0][a];
         e2[a] = P[2][a] - P[0][a];
+        H[a] = -(R)q * c[a] - P[0][a];
     }
-    H[0] = (double)x - q * c[0] - P[0][0];
-    H[1] = (double)y - q * c[1] - P[0][1];
-    H[2] = (double)z - q * c[2] - P[0][2];
     n[0] = e1[1] * e2[2] - e1[2] * e2[1];
     n[1] = e1[2] * e2[0] - e1[0] * e2[2];
     n[2] = e1[0] * e2[1] - e1[1] * e2[0];
-    const double nc = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
-    const double g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
-    const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
-    const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
-    const double gdet = g11 * g22 - g12 * g12;
+    const R nc = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+    const R g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const R g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const R g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const R gdet = g11 * g22 - g12 * g12;
+    const R hu = (R)h.u, hv = (R)h.v, hw = R(1) - hu - hv;
     for (int k = 0; k < 3; ++k) {
-        // vertex displacements along y only
-        const double dA = dy[0][k], dB = dy[1][k], dC = dy[2][k];
-        const double de1[3] = {0.0, dB - dA, 0.0}, de2[3] = {0.0, dC - dA, 0.0};
-        double dn[3];
-        dn[0] = de1[1] * e2[2] - de1[2] * e2[1] + e1[1] * de2[2] - e1[2] * de2[1];
-        dn[1] = de1[2] * e2[0] - de1[0] * e2[2] + e1[2] * de2[0] - e1[0] * de2[2];
-        dn[2] = de1[0] * e2[1] - de1[1] * e2[0] + e1[0] * de2[1] - e1[1] * de2[0];
-        const double ds = nc != 0.0 ? ((dn[0] * H[0] + dn[1] * H[1] + dn[2] * H[2]) - n[1] * dA) / nc : 0.0;
-        double rhs[3];
-        for (int a = 0; a < 3; ++a) rhs[a] = -ds * c[a] - h.u * de1[a] - h.v * de2[a];
-        rhs[1] -= dA;
-        const double b1 = e1[0] * rhs[0] + e1[1] * rhs[1] + e1[2] * rhs[2];
-        const double b2 = e2[0] * rhs[0] + e2[1] * rhs[1] + e2[2] * rhs[2];
-        const double du = gdet != 0.0 ? (b1 * g22 - b2 * g12) / gdet : 0.0;
-        const double dv = gdet != 0.0 ? (g11 * b2 - g12 * b1) / gdet : 0.0;
-        dq[k] = ds;
-        for (int a = 0; a < 3; ++a)
-            duw[k][a] = du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]);
-        duw[k][1] += (1.0 - h.u - h.v) * dvy[0][k] + h.u * dvy[1][k] + h.v * dvy[2][k];
+        for (int m = 0; m < 3; ++m) {
+            dy[m] = (R)G.mesh_dy[3 * tv[m] + k];
+            dvy[m][k] = (R)G.mesh_dvy[3 * tv[m] + k];
+        }
+        // vertex displacements along y only: de1 = (0, dB - dA, 0), de2 = (0, dC - dA, 0)
+        const R dA = dy[0], d1 = dy[1] - dA, d2 = dy[2] - dA;
+        // dn = de1 x e2 + e1 x de2 (its y component vanishes)
+        R dn[3];
+        dn[0] = d1 * e2[2] - e1[2] * d2;
+        dn[1] = R(0);
+        dn[2] = e1[0] * d2 - d1 * e2[0];
+        const R ds = nc != R(0) ? ((dn[0] * H[0] + dn[1] * H[1] + dn[2] * H[2]) - n[1] * dA) / nc : R(0);
+        R rhs[3];
+        rhs[0] = -ds * c[0];
+        rhs[1] = -ds * c[1] - hu * d1 - hv * d2 - dA;
+        rhs[2] = -ds * c[2];
+        const R b1 = e1[0] * rhs[0] + e1[1] * rhs[1] + e1[2] * rhs[2];
+        const R b2 = e2[0] * rhs[0] + e2[1] * rhs[1] + e2[2] * rhs[2];
+        const R du = gdet != R(0) ? (b1 * g22 - b2 * g12) / gdet : R(0);
+        const R dv = gdet != R(0) ? (g11 * b2 - g12 * b1) / gdet : R(0);
+        dq[k] = (double)ds;
+        for (int a = 0; a < 3; ++a) duw[k][a] = (double)(du * (V[1][a] - V[0][a]) + dv * (V[2][a] - V[0][a]));
+        duw[k][1] += (double)(hw * dvy[0][k] + hu * dvy[1][k] + hv * dvy[2][k]);
     }
 }
 
