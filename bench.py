@@ -70,6 +70,9 @@ def parse_args(argv=None):
     ap.add_argument("--parallel", default="auto", choices=["auto", "split", "replicas"],
                     help="several GPUs: split the box along z into one slab per rank (auto, split) or run "
                          "independent replicas; split on one GPU runs a single slab with halo exchange")
+    ap.add_argument("--launch-order", default="auto", choices=["auto", "split", "sequential"],
+                    help="the step's launch order (lbm_set_launch_order); auto times both in the first steps "
+                         "and keeps the faster (the results do not depend on it)")
     ap.add_argument("--slabs", type=int, default=2,
                     help="--parallel split on one GPU: slab lattices in this process")
     ap.add_argument("--second-workload", default="sphere", choices=["sphere", "airfoil", "swimmer", "tgv", "none"],
@@ -278,13 +281,15 @@ def geometry_for(wl):
     return lbm.sphere(wl["X"], wl["D"] / 2, free=True, rho_ratio=wl["rho_ratio"], g=wl["g"])
 
 
-def make_lattice(storage, wl, device, gamma_mode=0):
+def make_lattice(storage, wl, device, gamma_mode=0, order="auto"):
     import numpy as np
 
     import paper_1608_04658_gb300 as lbm
     shape = wl["shape"]
     lat = lbm.Lattice(shape, wl["nu"], storage=storage, faces=wl["faces"], device=device,
                       u_face=wl.get("u_face", (0.0, 0.0, 0.0)), gamma_mode=gamma_mode)
+    if order != "auto":
+        lat.set_launch_order(order)
     geom = geometry_for(wl)
     if geom is not None:
         lat.set_geometry(geom)
@@ -295,7 +300,7 @@ def make_lattice(storage, wl, device, gamma_mode=0):
 
 def time_storage(storage, wl, args, world, device, clocks, gamma_mode=0):
     import torch
-    lat, np = make_lattice(storage, wl, device, gamma_mode)
+    lat, np = make_lattice(storage, wl, device, gamma_mode, args.launch_order)
     K, W = args.steps, args.warmup
     lat.step(W)
     # the library times both launch orders in its first steps after
