@@ -402,6 +402,22 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, doubl
  * Errors: LBM_ERR_ARG (sizes, faces), LBM_ERR_STATE (a body is already set). */
 LBM_API lbm_status lbm_set_slab(lbm_ctx *ctx, int zoff, int zper, int own_lo, int own_hi);
 
+/* A step of a slab in two calls, so that the halo exchange can run beside
+ * the bulk of the step: lbm_step_interior enqueues the bulk update of the own
+ * layers that pull from no halo layer, [own_lo + 1, own_hi - 1), for the
+ * nodes outside the body's sweep box; the caller then refills the halo layers
+ * (lbm_unpack_layers) and lbm_step_edges enqueues the rest of the step (the
+ * body's chain, the first and last own layers) and ends it.  The own layers
+ * get the bits of lbm_step; the halo layers of the new state are left as they
+ * were (the next exchange refills them).  It applies without a body, and
+ * with a body whose sweep box is known ahead once the split launch order is
+ * asked for (lbm_set_launch_order); otherwise lbm_step_interior enqueues
+ * nothing and lbm_step_edges runs the whole step.  lbm_step, and a second
+ * lbm_step_interior, while a step is open: LBM_ERR_STATE; both calls on a
+ * context that is not a slab: LBM_ERR_STATE. */
+LBM_API lbm_status lbm_step_interior(lbm_ctx *ctx);
+LBM_API lbm_status lbm_step_edges(lbm_ctx *ctx);
+
 /* Copies the z layers [z0, z0 + nlayers) of the current state, all 27
  * planes, to dst / from src: device buffers of 27 * nlayers * nx * ny
  * elements of the storage type, plane-major (plane i first, then its

@@ -146,6 +146,10 @@ def lib():
         L.lbm_unpack_layers.restype = C.c_int
         L.lbm_set_body_force.argtypes = [vp, _D, _D]
         L.lbm_set_body_force.restype = C.c_int
+        L.lbm_step_interior.argtypes = [vp]
+        L.lbm_step_interior.restype = C.c_int
+        L.lbm_step_edges.argtypes = [vp]
+        L.lbm_step_edges.restype = C.c_int
         L.lbm_body_force_to_device.argtypes = [vp, vp]
         L.lbm_body_force_to_device.restype = C.c_int
         L.lbm_sum_body_force.argtypes = [vp, vp, C.c_int]
@@ -466,6 +470,16 @@ class Lattice:
         Fa = np.ascontiguousarray(F, dtype=np.float64)
         Ma = np.ascontiguousarray(M, dtype=np.float64)
         self._check(lib().lbm_set_body_force(self._ctx, Fa.ctypes.data_as(_D), Ma.ctypes.data_as(_D)))
+
+    def step_interior(self):
+        """A slab step's own layers that pull from no halo layer
+        (lbm_step_interior); step_edges completes the step."""
+        self._check(lib().lbm_step_interior(self._ctx))
+
+    def step_edges(self):
+        """The rest of a slab step, after the halo layers were refilled
+        (lbm_step_edges)."""
+        self._check(lib().lbm_step_edges(self._ctx))
 
     def body_force_to(self, out=None):
         """The body's current force and torque (6 doubles) copied into a device

@@ -208,6 +208,7 @@ lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, cons
     if (!rho || !u) return fail(ctx, LBM_ERR_ARG, "lbm_init_state: rho and u are required");
     LBM_CUDA(launch_init(ctx->storage, ctx->L, ctx->f[ctx->cur], rho, u, xi, amp, ctx->stream), "init");
     ctx->initialised = true;
+    ctx->interior_pending = false;
     return LBM_OK;
 }
 
@@ -552,6 +553,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "lbm_step: nsteps < 0");
     if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step: state not initialised");
+    if (ctx->interior_pending) return fail(ctx, LBM_ERR_STATE, "lbm_step: a step begun by lbm_step_interior is open");
     int launches = 0;
     choose_order(ctx);
     for (int s = 0; s < nsteps; ++s) {
@@ -610,6 +612,92 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
 }
 
 
+// Two-phase step of a slab: the own layers that pull from no halo layer
+// first, the rest once the caller has refilled the halo layers.
+static void interior_range(const lbm_ctx *ctx, int &lo, int &hi)
+{
+    lo = ctx->slab_own_lo + 1;
+    hi = ctx->slab_own_hi - 1;
+    if (hi <= lo) lo = hi = ctx->slab_own_lo;  // too thin: all own layers are edges
+}
+
+lbm_status lbm_step_interior(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step_interior: state not initialised");
+    if (ctx->slab_zper <= 0) return fail(ctx, LBM_ERR_STATE, "lbm_step_interior: not a slab (lbm_set_slab)");
+    if (ctx->interior_pending)
+        return fail(ctx, LBM_ERR_STATE, "lbm_step_interior: the previous step's edges are still to run");
+    ctx->launches = 0;
+    // only where the band is known ahead and the split order is asked for;
+    // otherwise lbm_step_edges runs the whole step
+    if (ctx->has_body && (!sweep_ahead(ctx->G) || ctx->order != ORDER_SPLIT)) return LBM_OK;
+    void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
+    const int next = ctx->bcur ^ 1;
+    if (ctx->has_body && ctx->slot_pending[next]) {
+        LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_slot[next], 0), "record wait");
+        ctx->slot_pending[next] = false;
+    }
+    int *status = ctx->has_body ? &ctx->S.body[next].status : &ctx->S.body[ctx->bcur].status;
+    const int *sweep = ctx->has_body ? ctx->S.body[ctx->bcur].sweep : nullptr;
+    int lo, hi;
+    interior_range(ctx, lo, hi);
+    LBM_CUDA(prof_mark(ctx, 0), "profile event");
+    LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream,
+                         ctx->has_body ? BULK_OUTSIDE : BULK_ALL, sweep, nullptr, lo, hi - lo),
+             "bulk interior");
+    LBM_CUDA(prof_mark(ctx, 1), "profile event");
+    ctx->launches = hi > lo ? 1 : 0;
+    ctx->interior_pending = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step_edges(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!ctx->interior_pending) {
+        if (ctx->slab_zper <= 0) return fail(ctx, LBM_ERR_STATE, "lbm_step_edges: not a slab (lbm_set_slab)");
+        return lbm_step(ctx, 1);
+    }
+    ctx->interior_pending = false;
+    int launches = ctx->launches;
+    void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
+    int cur = ctx->bcur;
+    int *status = &ctx->S.body[cur].status;
+    const int *sweep = nullptr;
+    if (ctx->has_body) {
+        // the body's chain as in the split order of lbm_step
+        const int prev = ctx->bcur;
+        cur = prev ^ 1;
+        status = &ctx->S.body[cur].status;
+        sweep = ctx->S.body[prev].sweep;
+        LBM_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork");
+        LBM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
+        LBM_CUDA(launch_geometry(ctx->L, ctx->G, ctx->S, prev, ctx->flags, ctx->side, &launches), "geometry");
+        LBM_CUDA(launch_refill(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, ctx->flags, ctx->side), "refill");
+        LBM_CUDA(launch_boundary(ctx->storage, ctx->L, ctx->G, ctx->S, cur, fa, fb, ctx->flags, ctx->side), "boundary");
+        LBM_CUDA(launch_forces(ctx->G, ctx->S, cur, ctx->side, &launches), "forces");
+        LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, ctx->flags, status, ctx->side, BULK_BAND, sweep,
+                             ctx->G.cap), "bulk band");
+        LBM_CUDA(cudaEventRecord(ctx->ev_join, ctx->side), "join");
+        launches += 3;
+    }
+    int lo, hi;
+    interior_range(ctx, lo, hi);
+    const int mode = ctx->has_body ? BULK_OUTSIDE : BULK_ALL;
+    LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream, mode, sweep, nullptr,
+                         ctx->slab_own_lo, lo - ctx->slab_own_lo), "bulk edge");
+    LBM_CUDA(launch_bulk(ctx->storage, ctx->L, fa, fb, nullptr, status, ctx->stream, mode, sweep, nullptr,
+                         hi, ctx->slab_own_hi - hi), "bulk edge");
+    launches += (lo > ctx->slab_own_lo) + (ctx->slab_own_hi > hi);
+    if (ctx->has_body) LBM_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
+    ctx->last_split = ctx->has_body;
+    ctx->bcur = cur;
+    ctx->cur ^= 1;
+    ctx->launches = launches;
+    return LBM_OK;
+}
+
 int lbm_current_buffer(const lbm_ctx *ctx) { return ctx ? ctx->cur : -1; }
 
 lbm_status lbm_set_launch_order(lbm_ctx *ctx, int order)
@@ -665,6 +753,7 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *host_f)
         LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
     }
     ctx->initialised = true;
+    ctx->interior_pending = false;
     return LBM_OK;
 }
 
@@ -875,6 +964,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path)
     fclose(fp);
     if (!ok) return fail(ctx, LBM_ERR_ARG, std::string("lbm_load: read failed for ") + path);
     ctx->initialised = true;
+    ctx->interior_pending = false;
     return LBM_OK;
 }
 

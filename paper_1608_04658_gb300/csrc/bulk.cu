@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const La
                                                    const uint8_t *__restrict__ flags,
                                                    int *__restrict__ status,
                                                    const int *__restrict__ sweep, int mode, int capx,
-                                                   int capy)
+                                                   int capy, int z0)
 {
     using R = typename Codec<S>::R;
     int x, y, z;
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const La
     } else {
         x = blockIdx.x * blockDim.x + threadIdx.x;
         y = blockIdx.y;
-        z = blockIdx.z;
+        z = z0 + (int)blockIdx.z;
         if (x >= L.nx) return;
         // y and z are uniform over the block, so only rows crossing the box
         // test x
@@ -146,11 +146,12 @@ __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(con
                                                                            S *__restrict__ fb,
                                                                            const uint8_t *__restrict__ flags,
                                                                            int *__restrict__ status,
-                                                                           const int *__restrict__ sweep, int mode)
+                                                                           const int *__restrict__ sweep, int mode,
+                                                                           int z0)
 {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x0 >= L.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = z0 + (int)blockIdx.z;
     if constexpr (!YZPER) {
         const bool face_row = (L.face[2] != LBM_FACE_PERIODIC && (y == 0 || y == L.ny - 1)) ||
                               (L.face[4] != LBM_FACE_PERIODIC && (z == 0 || z == L.nz - 1));
@@ -254,13 +255,16 @@ static cudaError_t dispatch(int storage, F &&fn)
 
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s, int mode, const int *sweep,
-                        const int *cap)
+                        const int *cap, int z_lo, int z_n)
 {
     if (mode != BULK_ALL && (!sweep || (mode == BULK_BAND && !cap))) return cudaErrorInvalidValue;
+    if (z_n < 0) z_n = L.nz - z_lo;
+    if (z_lo < 0 || z_lo + z_n > L.nz) return cudaErrorInvalidValue;
+    if (z_n == 0 && mode != BULK_BAND) return cudaSuccess;
     return dispatch(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
-        dim3 grid((L.nx + bx - 1) / bx, L.ny, L.nz);
+        dim3 grid((L.nx + bx - 1) / bx, L.ny, z_n);
         int capx = 1, capy = 1;
         if (mode == BULK_BAND) {
             bx = 128;
@@ -277,7 +281,7 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
         constexpr bool PAIR = VM && (LBM_PAIR_FP32 || !std::is_same<S, float>::value);
         if (L.gamma_mode == LBM_GAMMA_EXACT) {
             bulk_kernel<S, true, false><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode,
-                                                            capx, capy);
+                                                            capx, capy, z_lo);
             return cudaGetLastError();
         }
         if constexpr (PAIR) {
@@ -288,13 +292,13 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                             : kind == 2 ? bulk_pair_kernel<S, false, true>
                             : kind == 1 ? bulk_pair_kernel<S, true, false>
                                         : bulk_pair_kernel<S, false, false>;
-                const dim3 g2((L.nx + 127) / 128, L.ny, L.nz);
-                kernel<<<g2, 64, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode);
+                const dim3 g2((L.nx + 127) / 128, L.ny, z_n);
+                kernel<<<g2, 64, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode, z_lo);
                 return cudaGetLastError();
             }
         }
         bulk_kernel<S, false, VM><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode,
-                                                      capx, capy);
+                                                      capx, capy, z_lo);
         return cudaGetLastError();
     });
 }

@@ -55,6 +55,9 @@ struct lbm_ctx {
     std::string err;
     // slab of a box split along z (lbm_set_slab); zper = 0: none
     int slab_zoff = 0, slab_zper = 0, slab_own_lo = 0, slab_own_hi = 0;
+    // lbm_step_interior has enqueued the interior layers of a step that
+    // lbm_step_edges completes
+    bool interior_pending = false;
 };
 
 // waits on the host for the asynchronous force-record copies that may still

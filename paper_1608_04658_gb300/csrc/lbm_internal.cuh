@@ -99,9 +99,11 @@ struct Lattice {
 enum BulkMode { BULK_ALL = 0, BULK_OUTSIDE = 1, BULK_BAND = 2 };
 
 // launchers ------------------------------------------------------------------
+// z_lo, z_n: the z layers [z_lo, z_lo + z_n) of ALL and OUTSIDE launches
+// (z_n < 0: to the last layer); BAND launches take the box's layers.
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s, int mode = BULK_ALL,
-                        const int *sweep = nullptr, const int *cap = nullptr);
+                        const int *sweep = nullptr, const int *cap = nullptr, int z_lo = 0, int z_n = -1);
 cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
                         const double *u, const double *xi, double amp, cudaStream_t s);
 cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,

@@ -39,7 +39,8 @@ def slab_rows(nz: int, parts: int, k: int, halo: int = HALO) -> list[int]:
     return [(z0 - halo + j) % nz for j in range(z1 - z0 + 2 * halo)]
 
 
-def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, local_z=_b.FACE_PERIODIC, **kw):
+def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, local_z=_b.FACE_PERIODIC, two_phase=False,
+                  **kw):
     nx, ny, nz = shape
     if faces[4] != _b.FACE_PERIODIC or faces[5] != _b.FACE_PERIODIC:
         raise ValueError("the split axis z must be periodic")
@@ -53,6 +54,8 @@ def _slab_lattice(shape, nu, storage, faces, parts, k, halo, device, local_z=_b.
     local_faces = (faces[0], faces[1], faces[2], faces[3], local_z, local_z)
     lat = _b.Lattice((nx, ny, nloc), nu, storage=storage, faces=local_faces, device=device, **kw)
     lat.set_slab(z0 - halo, nz, halo, nloc - halo)
+    if two_phase:  # the two-phase step takes the split launch order
+        lat.set_launch_order("split")
     return lat
 
 
@@ -66,15 +69,19 @@ def _fixed_order_sum(parts):
 class SlabSet:
     """All slabs of one box in this process.  devices: one device for every
     slab, or a list (slab k on devices[k % len]); local_z: the slabs' own z
-    face kind (FACE_PERIODIC or FACE_WALL)."""
+    face kind (FACE_PERIODIC or FACE_WALL); two_phase: each step as
+    lbm_step_interior, the exchange, lbm_step_edges (else the exchange, then
+    lbm_step)."""
 
     def __init__(self, shape, nu, parts, storage="fp32", faces=(0,) * 6, geometry=None, devices=None,
-                 halo=HALO, local_z=_b.FACE_PERIODIC, **kw):
+                 halo=HALO, local_z=_b.FACE_PERIODIC, two_phase=False, **kw):
         self.shape = tuple(int(v) for v in shape)
         self.parts, self.halo = int(parts), int(halo)
+        self.two_phase = bool(two_phase)
         devs = devices if isinstance(devices, (list, tuple)) else [devices]
         self.slabs = [_slab_lattice(self.shape, nu, storage, faces, self.parts, k, self.halo,
-                                    devs[k % len(devs)], local_z=local_z, **kw) for k in range(self.parts)]
+                                    devs[k % len(devs)], local_z=local_z, two_phase=self.two_phase, **kw)
+                      for k in range(self.parts)]
         self.launches = 0
         self.body = geometry is not None
         if self.body:
@@ -105,10 +112,19 @@ class SlabSet:
         import torch
         self.launches = 0
         for _ in range(n):
-            self.exchange()
-            for lat in self.slabs:
-                lat.step(1)
-                self.launches += lat.launches()
+            if self.two_phase:
+                for lat in self.slabs:
+                    lat.step_interior()
+                    self.launches += lat.launches()
+                self.exchange()
+                for lat in self.slabs:
+                    lat.step_edges()
+                    self.launches += lat.launches()
+            else:
+                self.exchange()
+                for lat in self.slabs:
+                    lat.step(1)
+                    self.launches += lat.launches()
             if self.body:
                 dev0 = self.slabs[0].device
                 parts = torch.stack([lat.body_force_to().to(dev0) for lat in self.slabs])
@@ -144,12 +160,15 @@ class DistSlab:
     edge layers by send/recv of packed device tensors, the force and torque
     records all-gathered and added in rank order on the device.  Every
     operation is enqueued on the lattice's stream (the collectives wait on it
-    and it on them), so a step needs no host synchronisation.  lattice: an
-    object with the Lattice methods used here in place of a new slab lattice
-    (the exchange and the force hand-over run on it unchanged)."""
+    and it on them), so a step needs no host synchronisation.  two_phase (the
+    default): the transfers are enqueued first and the bulk of the own layers
+    that read no halo layer runs beside them (lbm_step_interior), the rest of
+    the step after them (lbm_step_edges).  lattice: an object with the
+    Lattice methods used here in place of a new slab lattice (the exchange and
+    the force hand-over run on it unchanged)."""
 
     def __init__(self, shape, nu, storage="fp32", faces=(0,) * 6, geometry=None, device=None, halo=HALO,
-                 lattice=None, **kw):
+                 lattice=None, two_phase=True, **kw):
         import torch.distributed as dist
         self.dist = dist
         if dist.is_available() and dist.is_initialized():
@@ -160,8 +179,10 @@ class DistSlab:
             raise ValueError("DistSlab needs a process group of two or more ranks (one GPU: SlabSet)")
         self.shape = tuple(int(v) for v in shape)
         self.halo = int(halo)
+        self.two_phase = bool(two_phase)
         self.lat = lattice if lattice is not None else \
-            _slab_lattice(self.shape, nu, storage, faces, self.world, self.rank, self.halo, device, **kw)
+            _slab_lattice(self.shape, nu, storage, faces, self.world, self.rank, self.halo, device,
+                          two_phase=self.two_phase, **kw)
         self.body = geometry is not None
         if self.body and lattice is None:
             self.lat.set_geometry(geometry)
@@ -179,10 +200,11 @@ class DistSlab:
         stream = getattr(self.lat, "stream", None)
         return torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
 
-    def exchange(self):
+    def exchange(self, between=None):
         """Halo layers from the neighbouring ranks' own edge layers: rank r
         sends its first own layers down to r - 1 and its last up to r + 1
-        (periodic in rank order)."""
+        (periodic in rank order).  between: called once the transfers are
+        enqueued, before the lattice's stream waits for them."""
         lat, h = self.lat, self.halo
         nloc = lat.shape[2]
         lo_out, hi_out = lat.pack_layers(h, h), lat.pack_layers(nloc - 2 * h, h)
@@ -194,7 +216,10 @@ class DistSlab:
                    self.dist.P2POp(self.dist.isend, hi_out, upper),
                    self.dist.P2POp(self.dist.irecv, hi_in, upper),
                    self.dist.P2POp(self.dist.irecv, lo_in, lower)]
-            for r in self.dist.batch_isend_irecv(ops):
+            works = self.dist.batch_isend_irecv(ops)
+            if between is not None:
+                between()
+            for r in works:
                 r.wait()
         lat.unpack_layers(0, lo_in)
         lat.unpack_layers(nloc - h, hi_in)
@@ -210,11 +235,17 @@ class DistSlab:
         self.lat.sum_body_force(torch.stack(parts))
 
     def step(self, n: int = 1):
-        """n steps: exchange, step, force hand-over."""
+        """n steps: exchange and step (two-phase: the interior layers beside
+        the transfers), then the force hand-over."""
         self.launches = 0
         for _ in range(n):
-            self.exchange()
-            self.lat.step(1)
+            if self.two_phase:
+                self.exchange(between=self.lat.step_interior)
+                self.launches += self.lat.launches()
+                self.lat.step_edges()
+            else:
+                self.exchange()
+                self.lat.step(1)
             self.launches += self.lat.launches()
             if self.body:
                 self.hand_over_force()

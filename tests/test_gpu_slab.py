@@ -42,10 +42,10 @@ def _undivided(lbm, shape, storage, geom, steps, faces=FACES):
     return lat, np.array(forces)
 
 
-def _split(lbm, shape, storage, geom, steps, parts, faces=FACES, local_z=None):
+def _split(lbm, shape, storage, geom, steps, parts, faces=FACES, local_z=None, two_phase=False):
     from paper_1608_04658_gb300.slab import SlabSet
     ss = SlabSet(shape, NU, parts, storage=storage, faces=faces, geometry=geom,
-                 local_z=lbm.FACE_PERIODIC if local_z is None else local_z)
+                 local_z=lbm.FACE_PERIODIC if local_z is None else local_z, two_phase=two_phase)
     rho, u, xi = synth.parity_fields(shape, 4)
     ss.init_state(rho, u, xi, AMP)
     forces = []
@@ -77,15 +77,19 @@ def _fluid(lat, ss):
     return ~whole
 
 
-@pytest.mark.parametrize("storage,local_z", [("fp32", "periodic"), ("fp16", "periodic"), ("fp32", "wall")])
+@pytest.mark.parametrize("storage,local_z,two_phase", [("fp32", "periodic", False), ("fp16", "periodic", False),
+                                                       ("fp32", "wall", False), ("fp32", "periodic", True),
+                                                       ("fp16", "periodic", True)])
 @pytest.mark.parametrize("parts,shape,X", [(2, (14, 12, 20), (6.3, 5.7, 9.1)),
                                            (3, (14, 12, 21), (6.3, 5.7, 13.4))])
-def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, local_z, parts, shape, X):
+def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, local_z, two_phase, parts, shape, X):
     """Sphere carried across a cut at a fixed velocity (free, with a mass so
     large that the force leaves its velocity unchanged): the own layers of
     every slab equal the undivided lattice bit for bit, the slab-ordered sum
     of the forces equals the undivided force up to the order of addition.
-    The slabs' own z faces (periodic or walls) are never read by own nodes."""
+    The slabs' own z faces (periodic or walls) are never read by own nodes.
+    two_phase: each slab step as lbm_step_interior, the exchange,
+    lbm_step_edges."""
     import paper_1608_04658_gb300 as lbm
     from paper_1608_04658_gb300.slab import slab_bounds
     geom = lbm.sphere(X, 3.2, U=(0.35, -0.15, 0.3), free=True, mass=1e30)
@@ -93,7 +97,7 @@ def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, local_z, parts, 
     lat, fm = _undivided(lbm, shape, storage, geom, steps)
     assert lat.body()["n_boundary"] > 0
     ss, fs = _split(lbm, shape, storage, geom, steps, parts,
-                    local_z=lbm.FACE_WALL if local_z == "wall" else lbm.FACE_PERIODIC)
+                    local_z=lbm.FACE_WALL if local_z == "wall" else lbm.FACE_PERIODIC, two_phase=two_phase)
     cuts = [slab_bounds(shape[2], parts, k)[0] for k in range(1, parts)]
     assert _straddles(lat, cuts)
     fluid = _fluid(lat, ss)
@@ -108,7 +112,8 @@ def test_slabs_reproduce_the_undivided_lattice_bitwise(storage, local_z, parts, 
     ss.close()
 
 
-def test_slabs_move_a_free_sphere_with_the_summed_force():
+@pytest.mark.parametrize("two_phase", [False, True])
+def test_slabs_move_a_free_sphere_with_the_summed_force(two_phase):
     """Free sedimenting sphere crossing the cut: every slab's copy of the body
     takes the Euler update of the slab-ordered force sum, so the copies agree
     bit for bit and differ from the undivided run only by rounding."""
@@ -116,7 +121,7 @@ def test_slabs_move_a_free_sphere_with_the_summed_force():
     shape, steps = (14, 12, 20), 6
     geom = lbm.sphere((6.3, 5.7, 11.4), 3.2, U=(0.02, 0.0, -0.25), free=True, rho_ratio=1.5, g=(0.0, 0.0, -0.01))
     lat, fm = _undivided(lbm, shape, "fp32", geom, steps)
-    ss, fs = _split(lbm, shape, "fp32", geom, steps, 2)
+    ss, fs = _split(lbm, shape, "fp32", geom, steps, 2, two_phase=two_phase)
     bodies = [s.body() for s in ss.slabs]
     assert np.array_equal(bodies[0]["U"], bodies[1]["U"]) and np.array_equal(bodies[0]["X"], bodies[1]["X"])
     b0 = lat.body()
@@ -131,8 +136,9 @@ def test_slabs_move_a_free_sphere_with_the_summed_force():
     ss.close()
 
 
-@pytest.mark.parametrize("storage,free", [("fp32", 1), ("fp16", 1), ("fp32", 7)])
-def test_deforming_swimmer_over_slabs(storage, free):
+@pytest.mark.parametrize("storage,free,two_phase", [("fp32", 1, False), ("fp16", 1, False), ("fp32", 7, False),
+                                                    ("fp32", 1, True), ("fp32", 7, True)])
+def test_deforming_swimmer_over_slabs(storage, free, two_phase):
     """The triangulated swimmer (Sec. 4.3, deforming, refilled nodes every
     step; free along x in its head frame, or free in x, y and yaw in its
     centre-of-mass frame) across the cut of two slabs: each slab places the
@@ -147,7 +153,7 @@ def test_deforming_swimmer_over_slabs(storage, free):
                        free=free, mass=synth.swimmer_volume(32.0), U=(-0.004, 0.0, 0.0), t0=5.0)
     faces = (0,) * 6
     lat, fm = _undivided(lbm, shape, storage, geom, steps, faces=faces)
-    ss, fs = _split(lbm, shape, storage, geom, steps, 2, faces=faces)
+    ss, fs = _split(lbm, shape, storage, geom, steps, 2, faces=faces, two_phase=two_phase)
     assert _straddles(lat, [10])
     assert lat.body()["n_uncovered"] > 0
     fluid = _fluid(lat, ss)
@@ -161,15 +167,17 @@ def test_deforming_swimmer_over_slabs(storage, free):
     ss.close()
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
-def test_bodiless_periodic_box_over_slabs(storage):
+@pytest.mark.parametrize("storage,two_phase,nz", [("fp32", False, 24), ("fp16", False, 24), ("fp32", True, 24),
+                                                  ("fp16", True, 24), ("fp32", True, 8), ("fp32", True, 12)])
+def test_bodiless_periodic_box_over_slabs(storage, two_phase, nz):
     """Periodic box without a body (rows of 64 nodes: the two-node kernel's
     all-periodic form in both the whole box and the slabs): 4 slabs, bitwise
-    equal to the undivided box."""
+    equal to the undivided box; with the two-phase step also slabs of 2 and
+    3 own layers (no interior layer, one)."""
     import paper_1608_04658_gb300 as lbm
-    shape = (64, 10, 24)
+    shape = (64, 10, nz)
     lat, _ = _undivided(lbm, shape, storage, None, 6, faces=(0,) * 6)
-    ss, _ = _split(lbm, shape, storage, None, 6, 4, faces=(0,) * 6)
+    ss, _ = _split(lbm, shape, storage, None, 6, 4, faces=(0,) * 6, two_phase=two_phase)
     assert np.array_equal(ss.populations(), lat.populations())
     ss.close()
 
@@ -191,3 +199,17 @@ def test_slab_arguments_are_checked():
     lat.set_geometry(lbm.sphere((4.0, 4.0, 5.0), 2.9))
     with pytest.raises(lbm.LbmError):
         lat.pack_layers(7, 2)
+    # the two-phase step: only on a slab, and no plain step while one is open
+    whole = lbm.Lattice((8, 8, 8), NU, faces=(0,) * 6)
+    whole.init_state(*synth.uniform_fields((8, 8, 8)))
+    with pytest.raises(lbm.LbmError):
+        whole.step_interior()
+    lat.init_state(*synth.uniform_fields((8, 8, 8)))
+    lat.set_launch_order("split")
+    lat.step_interior()
+    with pytest.raises(lbm.LbmError):
+        lat.step(1)
+    with pytest.raises(lbm.LbmError):
+        lat.step_interior()
+    lat.step_edges()
+    lat.step(1)

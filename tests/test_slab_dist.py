@@ -41,15 +41,24 @@ class _Lattice:
         self.F = torch.from_numpy(_force(rank))
         self.summed = None
         self.device = torch.device("cpu")
+        self.calls = []
 
     def pack_layers(self, z0, n):
+        self.calls.append("pack")
         return self.state[:, z0:z0 + n].clone()
 
     def unpack_layers(self, z0, src):
+        self.calls.append("unpack")
         self.state[:, z0:z0 + src.shape[1]] = src
 
     def step(self, n=1):
-        pass
+        self.calls.append("step")
+
+    def step_interior(self):
+        self.calls.append("interior")
+
+    def step_edges(self):
+        self.calls.append("edges")
 
     def launches(self):
         return 0
@@ -72,7 +81,7 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, shape, q):
+def _rank(rank, world, port, shape, two_phase, q):
     os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
 
@@ -84,18 +93,19 @@ def _rank(rank, world, port, shape, q):
         layers = box[:, rows].copy()
         layers[:, :2] = np.nan
         layers[:, -2:] = np.nan
-        ds = DistSlab(shape, 0.05, faces=(0,) * 6, geometry=object(), lattice=_Lattice(shape, layers, rank))
+        ds = DistSlab(shape, 0.05, faces=(0,) * 6, geometry=object(), lattice=_Lattice(shape, layers, rank),
+                      two_phase=two_phase)
         ds.step(1)
-        q.put((rank, ds.lat.state.numpy(), rows, ds.last_force, ds.lat.summed, ds.launches))
+        q.put((rank, ds.lat.state.numpy(), rows, ds.last_force, ds.lat.summed, ds.launches, ds.lat.calls))
     finally:
         dist.destroy_process_group()
 
 
-def _run(world, shape):
+def _run(world, shape, two_phase):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, shape, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, shape, two_phase, q)) for r in range(world)]
     for p in procs:
         p.start()
     got = {}
@@ -117,10 +127,13 @@ def _run(world, shape):
     return [got[r] for r in range(world)]
 
 
+@pytest.mark.parametrize("two_phase", [True, False])
 @pytest.mark.parametrize("world,shape", [(2, (6, 4, 10)), (3, (6, 4, 13))])
-def test_dist_slab_exchange_and_force_hand_over(world, shape):
+def test_dist_slab_exchange_and_force_hand_over(world, shape, two_phase):
+    """Two-phase: the interior layers' launch is enqueued once the transfers
+    are (between the packs and the unpacks), the edges after the unpacks."""
     box = _box(shape)
-    out = _run(world, shape)
+    out = _run(world, shape, two_phase)
     expected = _force(0)
     for r in range(1, world):
         expected = expected + _force(r)
@@ -129,7 +142,10 @@ def test_dist_slab_exchange_and_force_hand_over(world, shape):
         for r in reversed(range(world - 1)):
             rev = rev + _force(r)
         assert not np.array_equal(expected, rev)
-    for state, rows, force, summed, launches in out:
+    calls = ["pack", "pack", "interior", "unpack", "unpack", "edges"] if two_phase else \
+        ["pack", "pack", "unpack", "unpack", "step"]
+    for state, rows, force, summed, launches, seen in out:
         assert np.array_equal(state, box[:, rows])   # halo layers refilled, own layers kept
         assert np.array_equal(force, expected)
         assert summed == world and launches == 1
+        assert seen == calls
