@@ -170,17 +170,21 @@ __global__ void init_kernel(const Lattice L, S *__restrict__ f, const double *__
     using R = typename Codec<S>::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= L.N) return;
-    // equilibrium evaluated in double, then rounded once to storage
-    double ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
-    axis_eq<double>(u[3 * n + 0], ex, rx);
-    axis_eq<double>(u[3 * n + 1], ey, ry);
-    axis_eq<double>(u[3 * n + 2], ez, rz);
-    const double r = rho[n], drho = r - L.rho0;
+    // equilibrium evaluated in the collision's arithmetic R (double for FP64
+    // storage, FP32 otherwise: GB300's FP64 rate made the double evaluation
+    // the slowest part of setting up a large lattice), the density excess
+    // taken in double; then rounded once to storage
+    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
+    axis_eq<R>((R)u[3 * n + 0], ex, rx);
+    axis_eq<R>((R)u[3 * n + 1], ey, ry);
+    axis_eq<R>((R)u[3 * n + 2], ez, rz);
+    const double r = rho[n];
+    const R drho = (R)(r - L.rho0), rr = (R)r;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        double g = shifted_feq<double>(i, drho, r, ex, ey, ez);
-        if (xi) g += amp * weight<double>(i) * xi[(size_t)i * L.N + n];
-        Codec<S>::store(f + (size_t)i * L.N + n, (R)g);
+        R g = shifted_feq<R>(i, drho, rr, ex, ey, ez);
+        if (xi) g += (R)(amp * weight<double>(i) * xi[(size_t)i * L.N + n]);
+        Codec<S>::store(f + (size_t)i * L.N + n, g);
     }
 }
 
