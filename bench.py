@@ -70,6 +70,9 @@ def parse_args(argv=None):
     ap.add_argument("--parallel", default="auto", choices=["auto", "split", "replicas"],
                     help="several GPUs: split the box along z into one slab per rank (auto, split) or run "
                          "independent replicas; split on one GPU runs a single slab with halo exchange")
+    ap.add_argument("--gamma", default="analytic", choices=["analytic", "exact"],
+                    help="the stabilizer of the headline line: the analytic formula or the exact root "
+                         "(the variants time the other storage forms and the exact root as well)")
     ap.add_argument("--launch-order", default="auto", choices=["auto", "split", "sequential"],
                     help="the step's launch order (lbm_set_launch_order); auto times both in the first steps "
                          "and keeps the faster (the results do not depend on it)")
@@ -753,7 +756,7 @@ def run_ours(args):
     clocks.start()
     if split:
         return run_split(args, wl, world, rank, device, clocks)
-    main = time_storage(args.storage, wl, args, world, device, clocks)
+    main = time_storage(args.storage, wl, args, world, device, clocks, gamma_mode=1 if args.gamma == "exact" else 0)
     variants = {}
     if not args.no_variants:
         for st in ("fp16", "bf16", "fp32"):
@@ -784,11 +787,12 @@ def run_ours(args):
         return
     peak, peak_kind = measured_hbm_peak()
 
-    def roofline(st, r, captured=True, name=wl["name"]):
+    def roofline(st, r, key=None, name=wl["name"]):
         bytes_launch = r["bulk_nodes"] * BYTES_PER_NODE[st]
         achieved = bytes_launch / (r["bulk_ms"] * 1e-3) / 1e9
-        # the committed counters are those of the analytic-stabilizer kernel
-        tr = ncu_traffic(st, name) if captured else None
+        # counters committed for this storage form (key: the variant, e.g.
+        # fp32_exact_gamma for the exact stabilizer's kernel)
+        tr = ncu_traffic(key or st, name)
         return {"bound": "hbm", "kernel": "bulk_kernel", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch,
@@ -801,7 +805,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(main["ms"] / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.storage],
         "data": "synthetic",
-        "config": {"workload": wl["name"], "storage": args.storage, "nodes": N,
+        "config": {"workload": wl["name"], "storage": args.storage, "stabilizer": args.gamma, "nodes": N,
                    "bytes_per_node_update": BYTES_PER_NODE[args.storage],
                    "hbm_roofline_glups": round(peak / BYTES_PER_NODE[args.storage], 3),
                    "percent_of_hbm_roofline_step": round(100 * main["glups"] * BYTES_PER_NODE[args.storage]
@@ -812,7 +816,7 @@ def run_ours(args):
                    "boundary_nodes": main["body"]["n_boundary"], "links": main["body"]["n_links"],
                    "launch_order": main["order"],
                    "trial_steps_after_warmup": main["trial_steps_after_warmup"]},
-        "roofline": roofline(args.storage, main),
+        "roofline": roofline(args.storage, main, key=args.storage + ("_exact_gamma" if args.gamma == "exact" else "")),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": main["launches"],
@@ -823,7 +827,7 @@ def run_ours(args):
                           "ms_per_step": round(r["ms"] / args.steps, 5),
                           "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st.split("_")[0]]
                                                                 / world / peak, 2),
-                          "roofline": roofline(st.split("_")[0], r, captured=st in BYTES_PER_NODE),
+                          "roofline": roofline(st.split("_")[0], r, key=st),
                           "gpu_launches": r["launches"]}
                      for st, r in variants.items()},
         "workloads": {name: {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st],

@@ -23,6 +23,17 @@ namespace lbm {
 #ifndef LBM_BULK_MIN_BLOCKS
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
+// The exact stabilizer's Newton iteration and FP64 storage's double
+// arithmetic spill heavily at 72 registers (280 and 1080 bytes of stack,
+// traffic that reaches DRAM); they get fewer, wider blocks.
+#ifndef LBM_BULK_MIN_BLOCKS_WIDE
+#define LBM_BULK_MIN_BLOCKS_WIDE 4
+#endif
+template <typename S, bool EXACT>
+struct BulkBlocks {
+    static constexpr int value =
+        (EXACT || std::is_same<S, double>::value) ? LBM_BULK_MIN_BLOCKS_WIDE : LBM_BULK_MIN_BLOCKS;
+};
 
 // Resident blocks per SM asked of the register allocator for the two-node
 // kernel (64 threads, 128 nodes per block): 6 (166 registers, no spill) for
@@ -49,7 +60,7 @@ struct PairBlocks {
 // the two-node kernel shares bit for bit; otherwise kbc_collide (FP64
 // storage, exact stabilizer).
 template <typename S, bool EXACT, bool VMATH>
-__global__ void __launch_bounds__(128, LBM_BULK_MIN_BLOCKS) bulk_kernel(const Lattice L, const S *__restrict__ fa,
+__global__ void __launch_bounds__(128, (BulkBlocks<S, EXACT>::value)) bulk_kernel(const Lattice L, const S *__restrict__ fa,
                                                    S *__restrict__ fb,
                                                    const uint8_t *__restrict__ flags,
                                                    int *__restrict__ status,
