@@ -479,8 +479,9 @@ def e2e_split(storage, wl, args, world, device):
 
 def e2e_storage(storage, wl, args, device):
     """Same workload through the public API from host memory: the initial
-    density and velocity fields (pinned FP64, 4 doubles per node) are copied to
-    the device and lbm_init_state builds the state from them, then K steps run
+    density and velocity fields (pinned FP64, 4 doubles per node) are read
+    across the host link by lbm_init_state, which builds the state from them
+    (the device reads the pinned pages in place), then K steps run
     with every step's force, torque, time and status record (60 bytes) copied
     to pinned host memory and read by the host at most two steps later; all of
     it inside the timed region.  The lattice and its body are set up, and the
@@ -519,8 +520,8 @@ def e2e_storage(storage, wl, args, device):
     h2d = h_rho.numel() * 8 + h_u.numel() * 8
     return {"value": round(N * K / t / 1e9, 4), "unit": "GLUPS",
             "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60,
-            "note": "initial density and velocity fields (pinned FP64, 32 bytes per node) copied to the device and "
-                    "turned into the state by lbm_init_state once per run (amortised over the steps); every "
+            "note": "initial density and velocity fields (pinned FP64, 32 bytes per node) read across the host link "
+                    "by lbm_init_state, which turns them into the state, once per run (amortised over the steps); every "
                     "step's force, torque, time and status (60 bytes) copied to pinned host memory and read by "
                     "the host at most two steps later (lbm_body_forces_async / lbm_body_forces_wait)"}
 

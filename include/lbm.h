@@ -203,8 +203,11 @@ LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
 /* Sets the state to f_i = f_i^eq(rho, u) + amp * W_i * xi_i (Eq. feq_min, exact
  * D3Q27 equilibrium), computed on the device in the collision's arithmetic
  * (double for FP64 storage, FP32 for the others) and rounded once to storage.
- *   rho  device, N doubles; u device, 3N doubles node-major (u[3n + a]);
- *   xi   device, 27N doubles direction-major, or NULL for none. */
+ *   rho  N doubles; u 3N doubles node-major (u[3n + a]);
+ *   xi   27N doubles direction-major, or NULL for none;
+ * each in device memory or in pinned host memory (cudaHostAlloc: the kernel
+ * reads it across the host link at its mapped device address); anything else
+ * (pageable host memory) is LBM_ERR_ARG. */
 LBM_API lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u,
                                   const double *xi, double amp);
 

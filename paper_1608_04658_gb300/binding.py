@@ -305,10 +305,24 @@ class Lattice:
     # -------------------------------------------------------------- state
     def init_state(self, rho, u, xi=None, amp: float = 0.0):
         """f = f^eq(rho, u) + amp W xi on the device.  rho (nz,ny,nx), u (nz,ny,nx,3),
-        xi (27,nz,ny,nx) or None; numpy arrays or torch tensors (host tensors in
-        pinned memory are copied asynchronously on the lattice's stream)."""
+        xi (27,nz,ny,nx) or None; numpy arrays or torch tensors.  Contiguous
+        float64 host tensors in pinned memory are read by the kernel itself
+        across the host link (no device copy); other host data is copied to the
+        device first."""
         torch = _torch()
         dev = self.device
+
+        def pinned(a):
+            return (torch.is_tensor(a) and a.device.type == "cpu" and a.is_pinned() and a.dtype == torch.float64
+                    and a.is_contiguous())
+
+        if pinned(rho) and pinned(u) and (xi is None or pinned(xi)):
+            st = lib().lbm_init_state(self._ctx, rho.data_ptr(), u.data_ptr(),
+                                      xi.data_ptr() if xi is not None else None, float(amp))
+            if st != LBM_ERR_ARG:  # (not addressable by the device: copied below)
+                self._check(st)
+                self.stream.synchronize()
+                return
 
         def to_dev(a):
             if torch.is_tensor(a):

@@ -202,11 +202,29 @@ void lbm_destroy(lbm_ctx *ctx)
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+// The device address of a buffer the kernels may read: device or managed
+// memory as it is, pinned host memory by its mapped device address; nullptr
+// for memory the device cannot address (pageable host memory).
+static const double *device_view(const double *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return (const double *)a.devicePointer;
+    return nullptr;
+}
+
 lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, const double *xi, double amp)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (!rho || !u) return fail(ctx, LBM_ERR_ARG, "lbm_init_state: rho and u are required");
-    LBM_CUDA(launch_init(ctx->storage, ctx->L, ctx->f[ctx->cur], rho, u, xi, amp, ctx->stream), "init");
+    const double *drho = device_view(rho), *du = device_view(u), *dxi = xi ? device_view(xi) : nullptr;
+    if (!drho || !du || (xi && !dxi))
+        return fail(ctx, LBM_ERR_ARG, "lbm_init_state: a field is neither device memory nor pinned host memory");
+    LBM_CUDA(launch_init(ctx->storage, ctx->L, ctx->f[ctx->cur], drho, du, dxi, amp, ctx->stream), "init");
     ctx->initialised = true;
     ctx->interior_pending = false;
     return LBM_OK;

@@ -344,6 +344,30 @@ def test_anguilliform_swimmer_full_size_sampled(storage):
     assert nb > 5000
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "fp64"])
+def test_init_from_pinned_host_fields(storage):
+    """lbm_init_state reading pinned host fields across the host link gives
+    the bits of the same fields in device memory; pageable host memory is
+    refused (LBM_ERR_ARG) before any kernel runs."""
+    import ctypes
+
+    import paper_1608_04658_gb300 as lbm
+    shape = (24, 10, 6)
+    rho, u, xi = synth.parity_fields(shape, 21)
+    a = lbm.Lattice(shape, 0.05, storage=storage)
+    a.init_state(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(xi).cuda(), 1e-3)
+    b = lbm.Lattice(shape, 0.05, storage=storage)
+    b.init_state(torch.from_numpy(rho).pin_memory(), torch.from_numpy(u).pin_memory(),
+                 torch.from_numpy(xi).pin_memory(), 1e-3)
+    assert torch.equal(a.f, b.f)
+    r = np.ascontiguousarray(rho)
+    v = np.ascontiguousarray(u)
+    st = lbm.lib().lbm_init_state(b._ctx, r.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                                  None, 0.0)
+    from paper_1608_04658_gb300.binding import LBM_ERR_ARG
+    assert st == LBM_ERR_ARG
+
+
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 def test_checkpoint_resume_is_bitwise(storage, tmp_path):
     """20 steps straight equal 10 steps + save + load into a fresh context +
