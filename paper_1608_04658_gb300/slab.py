@@ -209,6 +209,9 @@ class DistSlab:
         nloc = lat.shape[2]
         lo_out, hi_out = lat.pack_layers(h, h), lat.pack_layers(nloc - 2 * h, h)
         import torch
+        staged = self._host_staged()
+        if staged:  # a host-only backend: the layers travel through host memory
+            lo_out, hi_out = lo_out.cpu(), hi_out.cpu()
         lower, upper = (self.rank - 1) % self.world, (self.rank + 1) % self.world
         lo_in, hi_in = torch.empty_like(lo_out), torch.empty_like(hi_out)
         with self._on_stream():
@@ -221,18 +224,30 @@ class DistSlab:
                 between()
             for r in works:
                 r.wait()
+        if staged:
+            lo_in, hi_in = lo_in.to(lat.device), hi_in.to(lat.device)
         lat.unpack_layers(0, lo_in)
         lat.unpack_layers(nloc - h, hi_in)
+
+    def _host_staged(self) -> bool:
+        """A CUDA lattice in a group whose backend moves host memory only
+        (gloo): exchanges and gathers go through host copies."""
+        dev = getattr(self.lat, "device", None)
+        return dev is not None and dev.type == "cuda" and self.dist.get_backend() != "nccl"
 
     def hand_over_force(self):
         """Every rank's force and torque record gathered and added in rank
         order into this rank's body copy (all copies get the same bits)."""
         import torch
         mine = self.lat.body_force_to()
+        staged = self._host_staged()
+        if staged:
+            mine = mine.cpu()
         parts = [torch.empty_like(mine) for _ in range(self.world)]
         with self._on_stream():
             self.dist.all_gather(parts, mine)
-        self.lat.sum_body_force(torch.stack(parts))
+        all_parts = torch.stack(parts)
+        self.lat.sum_body_force(all_parts.to(self.lat.device) if staged else all_parts)
 
     def step(self, n: int = 1):
         """n steps: exchange and step (two-phase: the interior layers beside

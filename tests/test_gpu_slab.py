@@ -213,3 +213,77 @@ def test_slab_arguments_are_checked():
         lat.step_interior()
     lat.step_edges()
     lat.step(1)
+
+
+def _dist_rank(rank, world, port, shape, storage, steps, q):
+    """One rank of a gloo group on this GPU: its slab's own fluid layers and
+    the summed force after the steps (the group moves host memory only, so
+    the ranks' kernels never wait on one another)."""
+    import os
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+
+    import paper_1608_04658_gb300 as lbm
+    from paper_1608_04658_gb300.slab import DistSlab
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        geom = lbm.sphere((6.3, 5.7, 9.1), 3.2, U=(0.35, -0.15, 0.3), free=True, mass=1e30)
+        ds = DistSlab(shape, NU, storage=storage, faces=FACES, geometry=geom, device="cuda:0")
+        rho, u, xi = synth.parity_fields(shape, 4)
+        ds.init_state(rho, u, xi, AMP)
+        ds.step(steps)
+        f = ds.lat.populations()[:, ds.halo:ds.halo + ds.z1 - ds.z0]
+        solid = (ds.lat.flags.cpu().numpy() & 1).astype(bool)[ds.halo:ds.halo + ds.z1 - ds.z0]
+        q.put((rank, f, solid, ds.last_force, ds.z0, ds.z1))
+        ds.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_dist_slab_ranks_reproduce_the_undivided_lattice(storage):
+    """DistSlab end to end on the GPU: two ranks (processes) of a gloo group,
+    each with its slab on this GPU and the two-phase step, the edge layers and
+    force records staged through host memory.  Own fluid nodes equal the
+    undivided lattice bit for bit; the summed force equals its force up to
+    the order of addition."""
+    import multiprocessing as mp
+    import queue
+    import socket
+    import time
+
+    import paper_1608_04658_gb300 as lbm
+    shape, steps, world = (14, 12, 20), 5, 2
+    geom = lbm.sphere((6.3, 5.7, 9.1), 3.2, U=(0.35, -0.15, 0.3), free=True, mass=1e30)
+    lat, fm = _undivided(lbm, shape, storage, geom, steps)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_dist_rank, args=(r, world, port, shape, storage, steps, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got, deadline = {}, time.monotonic() + 240
+    try:
+        while len(got) < world:
+            try:
+                out = q.get(timeout=2)
+                got[out[0]] = out[1:]
+            except queue.Empty:
+                dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+                assert not dead and time.monotonic() < deadline, f"ranks failed: exit codes {dead}"
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    whole = lat.populations()
+    wsolid = (lat.flags.cpu().numpy() & 1).astype(bool)
+    for r in range(world):
+        f, solid, force, z0, z1 = got[r]
+        assert np.array_equal(solid, wsolid[z0:z1])
+        fluid = ~solid
+        assert np.array_equal(f[:, fluid], whole[:, z0:z1][:, fluid])
+        assert np.abs(force - fm[-1]).max() <= 1e-12 * np.abs(fm[-1]).max()
+    assert np.array_equal(got[0][2], got[1][2])
