@@ -99,9 +99,11 @@ def dist_setup():
     if world > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if backend == "nccl":
-            torch.cuda.set_device(local)
+        # LBM_DIST_BACKEND=gloo: a host-only group (the slab exchange is then
+        # staged through host memory), e.g. to run several ranks on one GPU
+        backend = os.environ.get("LBM_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local % torch.cuda.device_count())
         dist.init_process_group(backend=backend)
     return world, rank, local
 
@@ -472,9 +474,9 @@ def e2e_split(storage, wl, args, world, device):
     return {"value": round(nx * ny * nz * K / t / 1e9, 4), "unit": "GLUPS",
             "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60 if wl["kind"] != "tgv" else 0,
             "note": "each slab: its rows of the initial density and velocity fields (pinned FP64, 32 bytes per "
-                    "node, halo rows included) copied to the device and turned into its state by lbm_init_state "
-                    "once per run; every step's summed force record (60 bytes) read by the host at most two "
-                    "steps later; h2d counted on this rank"}
+                    "node, halo rows included) read across the host link by lbm_init_state, which turns them "
+                    "into its state, once per run; every step's summed force record (60 bytes) read by the host "
+                    "at most two steps later; h2d counted on this rank"}
 
 
 def e2e_storage(storage, wl, args, device):
@@ -742,6 +744,7 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU (the compute path is liblbm.so)")
     import paper_1608_04658_gb300 as lbm
     lbm.build()
+    local = local % torch.cuda.device_count()
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
     if args.adjoint_only:
