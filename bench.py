@@ -444,8 +444,10 @@ def e2e_split(storage, wl, args, world, device):
         torch.cuda.synchronize()
         ds.step(1)
         extra += 1
-    h_rho = [torch.from_numpy(rho[r]).pin_memory() for r in rows]
-    h_u = [torch.from_numpy(u[r]).pin_memory() for r in rows]
+    import numpy as np
+    fdt = np.float64 if storage == "fp64" else np.float32
+    h_rho = [torch.from_numpy(rho[r].astype(fdt)).pin_memory() for r in rows]
+    h_u = [torch.from_numpy(u[r].astype(fdt)).pin_memory() for r in rows]
     del rho, u
     K = args.steps
     lat = lats[0]
@@ -470,11 +472,11 @@ def e2e_split(storage, wl, args, world, device):
     del ds, lat, lats
     torch.cuda.empty_cache()
     nx, ny, _ = wl["shape"]
-    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in zip(h_rho, h_u))
+    h2d = sum(a.numel() * a.element_size() + b.numel() * b.element_size() for a, b in zip(h_rho, h_u))
     return {"value": round(nx * ny * nz * K / t / 1e9, 4), "unit": "GLUPS",
             "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60 if wl["kind"] != "tgv" else 0,
-            "note": "each slab: its rows of the initial density and velocity fields (pinned FP64, 32 bytes per "
-                    "node, halo rows included) read across the host link by lbm_init_state, which turns them "
+            "note": "each slab: its rows of the initial density and velocity fields (pinned, FP32 for FP32 and "
+                    "16-bit storage, halo rows included) read across the host link by lbm_init_state(_f32), which turns them "
                     "into its state, once per run; every step's summed force record (60 bytes) read by the host "
                     "at most two steps later; h2d counted on this rank"}
 
@@ -497,8 +499,12 @@ def e2e_storage(storage, wl, args, device):
         lat.step(1)
         extra += 1
     rho, u = initial_flow(wl)
-    h_rho = torch.from_numpy(rho).pin_memory()
-    h_u = torch.from_numpy(u).pin_memory()
+    # the fields in the collision's precision: FP32 for FP32 and 16-bit storage
+    import numpy as np
+    fdt = np.float64 if storage == "fp64" else np.float32
+    h_rho = torch.from_numpy(rho.astype(fdt)).pin_memory()
+    h_u = torch.from_numpy(u.astype(fdt)).pin_memory()
+    del rho, u
     K = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -519,11 +525,12 @@ def e2e_storage(storage, wl, args, device):
     lat.close()
     del lat
     torch.cuda.empty_cache()
-    h2d = h_rho.numel() * 8 + h_u.numel() * 8
+    h2d = h_rho.numel() * h_rho.element_size() + h_u.numel() * h_u.element_size()
     return {"value": round(N * K / t / 1e9, 4), "unit": "GLUPS",
             "h2d_bytes_per_step": int(round(h2d / K)), "d2h_bytes_per_step": 60,
-            "note": "initial density and velocity fields (pinned FP64, 32 bytes per node) read across the host link "
-                    "by lbm_init_state, which turns them into the state, once per run (amortised over the steps); every "
+            "note": "initial density and velocity fields (pinned, in the collision's precision: FP32 for FP32 and "
+                    "16-bit storage, 16 bytes per node) read across the host link by lbm_init_state(_f32), which "
+                    "turns them into the state, once per run (amortised over the steps); every "
                     "step's force, torque, time and status (60 bytes) copied to pinned host memory and read by "
                     "the host at most two steps later (lbm_body_forces_async / lbm_body_forces_wait)"}
 

@@ -210,6 +210,10 @@ LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
  * (pageable host memory) is LBM_ERR_ARG. */
 LBM_API lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u,
                                   const double *xi, double amp);
+/* The same from single-precision fields (half the bytes to move; each value
+ * is taken exactly as the double it converts to). */
+LBM_API lbm_status lbm_init_state_f32(lbm_ctx *ctx, const float *rho, const float *u,
+                                      const float *xi, double amp);
 
 /* Sets the immersed body (copied; may be called again to replace it) and
  * marks the nodes inside it as solid at the current step.  Allocates the

@@ -100,6 +100,8 @@ def lib():
         L.lbm_last_error.restype = C.c_char_p
         L.lbm_init_state.argtypes = [vp, vp, vp, vp, C.c_double]
         L.lbm_init_state.restype = C.c_int
+        L.lbm_init_state_f32.argtypes = [vp, vp, vp, vp, C.c_double]
+        L.lbm_init_state_f32.restype = C.c_int
         L.lbm_set_geometry.argtypes = [vp, C.POINTER(Geometry)]
         L.lbm_set_geometry.restype = C.c_int
         L.lbm_step.argtypes = [vp, C.c_int]
@@ -306,19 +308,21 @@ class Lattice:
     def init_state(self, rho, u, xi=None, amp: float = 0.0):
         """f = f^eq(rho, u) + amp W xi on the device.  rho (nz,ny,nx), u (nz,ny,nx,3),
         xi (27,nz,ny,nx) or None; numpy arrays or torch tensors.  Contiguous
-        float64 host tensors in pinned memory are read by the kernel itself
-        across the host link (no device copy); other host data is copied to the
-        device first."""
+        tensors on the lattice's device or in pinned host memory, all float64
+        or all float32, go to the kernel as they are (pinned pages read across
+        the host link; lbm_init_state / lbm_init_state_f32); other data is
+        copied to the device first (as float64)."""
         torch = _torch()
         dev = self.device
 
-        def pinned(a):
-            return (torch.is_tensor(a) and a.device.type == "cpu" and a.is_pinned() and a.dtype == torch.float64
-                    and a.is_contiguous())
+        def direct(a, dt):
+            return (torch.is_tensor(a) and a.dtype == dt and a.is_contiguous()
+                    and ((a.device.type == "cpu" and a.is_pinned()) or a.device == dev))
 
-        if pinned(rho) and pinned(u) and (xi is None or pinned(xi)):
-            st = lib().lbm_init_state(self._ctx, rho.data_ptr(), u.data_ptr(),
-                                      xi.data_ptr() if xi is not None else None, float(amp))
+        for dt, fn in ((torch.float64, lib().lbm_init_state), (torch.float32, lib().lbm_init_state_f32)):
+            if not (direct(rho, dt) and direct(u, dt) and (xi is None or direct(xi, dt))):
+                continue
+            st = fn(self._ctx, rho.data_ptr(), u.data_ptr(), xi.data_ptr() if xi is not None else None, float(amp))
             if st != LBM_ERR_ARG:  # (not addressable by the device: copied below)
                 self._check(st)
                 self.stream.synchronize()

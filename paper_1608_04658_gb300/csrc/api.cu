@@ -202,10 +202,13 @@ void lbm_destroy(lbm_ctx *ctx)
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+}  // extern "C"
+
 // The device address of a buffer the kernels may read: device or managed
 // memory as it is, pinned host memory by its mapped device address; nullptr
 // for memory the device cannot address (pageable host memory).
-static const double *device_view(const double *p)
+template <typename T>
+static const T *device_view(const T *p)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -213,21 +216,34 @@ static const double *device_view(const double *p)
         return nullptr;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return (const double *)a.devicePointer;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return (const T *)a.devicePointer;
     return nullptr;
 }
 
-lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, const double *xi, double amp)
+template <typename T>
+static lbm_status init_state(lbm_ctx *ctx, const T *rho, const T *u, const T *xi, double amp, const char *name)
 {
     if (!ctx) return LBM_ERR_ARG;
-    if (!rho || !u) return fail(ctx, LBM_ERR_ARG, "lbm_init_state: rho and u are required");
-    const double *drho = device_view(rho), *du = device_view(u), *dxi = xi ? device_view(xi) : nullptr;
+    if (!rho || !u) return fail(ctx, LBM_ERR_ARG, std::string(name) + ": rho and u are required");
+    const T *drho = device_view(rho), *du = device_view(u), *dxi = xi ? device_view(xi) : nullptr;
     if (!drho || !du || (xi && !dxi))
-        return fail(ctx, LBM_ERR_ARG, "lbm_init_state: a field is neither device memory nor pinned host memory");
-    LBM_CUDA(launch_init(ctx->storage, ctx->L, ctx->f[ctx->cur], drho, du, dxi, amp, ctx->stream), "init");
+        return fail(ctx, LBM_ERR_ARG, std::string(name) + ": a field is neither device memory nor pinned host memory");
+    LBM_CUDA(launch_init<T>(ctx->storage, ctx->L, ctx->f[ctx->cur], drho, du, dxi, amp, ctx->stream), name);
     ctx->initialised = true;
     ctx->interior_pending = false;
     return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, const double *xi, double amp)
+{
+    return init_state<double>(ctx, rho, u, xi, amp, "lbm_init_state");
+}
+
+lbm_status lbm_init_state_f32(lbm_ctx *ctx, const float *rho, const float *u, const float *xi, double amp)
+{
+    return init_state<float>(ctx, rho, u, xi, amp, "lbm_init_state_f32");
 }
 
 lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)

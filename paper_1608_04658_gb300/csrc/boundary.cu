@@ -212,17 +212,6 @@ __global__ void __launch_bounds__(BWARPS * 32, LBM_LIST_MIN_BLOCKS) refill_kerne
 }
 
 // ----------------------------------------------------------------- launchers
-template <typename F>
-static cudaError_t dispatch(int storage, F &&fn)
-{
-    switch (storage) {
-    case LBM_FP64: return fn((double *)nullptr);
-    case LBM_FP32: return fn((float *)nullptr);
-    case LBM_FP16: return fn((__half *)nullptr);
-    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 // Grid of the list kernels (grid-stride over the list).  The boundary kernel
 // runs beside the bulk kernel, and every resident block of it holds shared
@@ -249,7 +238,7 @@ static int list_blocks(int cap, int max_blocks = LBM_LIST_BLOCKS)
 cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur,
                             const void *fa, void *fb, const uint8_t *flags, cudaStream_t s)
 {
-    return dispatch(storage, [&](auto tag) {
+    return dispatch_storage(storage, [&](auto tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         const int nb = list_blocks(G.cap_boundary, G.kind == LBM_BODY_MESH ? LBM_MESH_LIST_BLOCKS : LBM_LIST_BLOCKS);
         boundary_kernel<T><<<nb, BWARPS * 32, 0, s>>>(L, G, S.body + cur, S.blist, S.bpos, S.bforce, (const T *)fa,
@@ -261,7 +250,7 @@ cudaError_t launch_boundary(int storage, const Lattice &L, const GeomParams &G, 
 cudaError_t launch_refill(int storage, const Lattice &L, const GeomParams &G, Scratch &S, int cur, void *fa,
                           const uint8_t *flags, cudaStream_t s)
 {
-    return dispatch(storage, [&](auto tag) {
+    return dispatch_storage(storage, [&](auto tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         refill_kernel<T><<<list_blocks(G.cap_uncovered), BWARPS * 32, 0, s>>>(L, G, S.body + cur, S.ulist,
                                                                                (T *)fa, flags);

@@ -1,5 +1,5 @@
 // Bulk fused pull-stream + KBC collide (arXiv 1608.04658, Sec. 2, Eq. kineticEq
-// with Eq. kbc_relax), plus state initialisation, plane codec and totals.
+// with Eq. kbc_relax).
 //
 // One thread per node, threads along x (the fastest axis of every population
 // plane) so each of the 27 plane loads and stores of a warp is one contiguous
@@ -174,100 +174,7 @@ __global__ void __launch_bounds__(64, PairBlocks<S>::value) bulk_pair_kernel(con
     pair_update<S, XPER, YZPER>(L, fa, fb, flags, status, sweep, mode, x0, y, z);
 }
 
-template <typename S>
-__global__ void init_kernel(const Lattice L, S *__restrict__ f, const double *__restrict__ rho,
-                            const double *__restrict__ u, const double *__restrict__ xi, double amp)
-{
-    using R = typename Codec<S>::R;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= L.N) return;
-    // equilibrium evaluated in the collision's arithmetic R (double for FP64
-    // storage, FP32 otherwise: GB300's FP64 rate made the double evaluation
-    // the slowest part of setting up a large lattice), the density excess
-    // taken in double; then rounded once to storage
-    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
-    axis_eq<R>((R)u[3 * n + 0], ex, rx);
-    axis_eq<R>((R)u[3 * n + 1], ey, ry);
-    axis_eq<R>((R)u[3 * n + 2], ez, rz);
-    const double r = rho[n];
-    const R drho = (R)(r - L.rho0), rr = (R)r;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        R g = shifted_feq<R>(i, drho, rr, ex, ey, ez);
-        if (xi) g += (R)(amp * weight<double>(i) * xi[(size_t)i * L.N + n]);
-        Codec<S>::store(f + (size_t)i * L.N + n, g);
-    }
-}
-
-template <typename S>
-__global__ void decode_kernel(const Lattice L, const S *__restrict__ f, int i, double *__restrict__ out)
-{
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= L.N) return;
-    out[n] = (double)Codec<S>::load(f + (size_t)i * L.N + n) + weight<double>(i) * L.rho0;
-}
-
-template <typename S>
-__global__ void encode_kernel(const Lattice L, S *__restrict__ f, int i, const double *__restrict__ in)
-{
-    using R = typename Codec<S>::R;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= L.N) return;
-    Codec<S>::store(f + (size_t)i * L.N + n, (R)(in[n] - weight<double>(i) * L.rho0));
-}
-
-// Per-block FP64 partial sums of mass, momentum and kinetic energy over
-// non-solid nodes; the host adds the block partials in block order.
-template <typename S>
-__global__ void __launch_bounds__(256) totals_kernel(const Lattice L, const S *__restrict__ f,
-                                                     const uint8_t *__restrict__ flags,
-                                                     double *__restrict__ partials)
-{
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < L.N;
-         n += (long long)gridDim.x * blockDim.x) {
-        if (flags && (flags[n] & FL_SOLID)) continue;
-        double r = 0, j[3] = {0, 0, 0};
-        for (int i = 0; i < Q; ++i) {
-            const double v = (double)Codec<S>::load(f + (size_t)i * L.N + n) + weight<double>(i) * L.rho0;
-            r += v;
-            j[0] += cx_of(i) * v;
-            j[1] += cy_of(i) * v;
-            j[2] += cz_of(i) * v;
-        }
-        acc[0] += r;
-        acc[1] += j[0];
-        acc[2] += j[1];
-        acc[3] += j[2];
-        acc[4] += 0.5 * (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) / r;
-    }
-    __shared__ double sm[8][5];
-    for (int k = 0; k < 5; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double v = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sm[w][threadIdx.x];
-        partials[blockIdx.x * 5 + threadIdx.x] = v;
-    }
-}
-
 // ----------------------------------------------------------------- launchers
-template <typename F>
-static cudaError_t dispatch(int storage, F &&fn)
-{
-    switch (storage) {
-    case LBM_FP64: return fn((double *)nullptr);
-    case LBM_FP32: return fn((float *)nullptr);
-    case LBM_FP16: return fn((__half *)nullptr);
-    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s, int mode, const int *sweep,
                         const int *cap, int z_lo, int z_n)
@@ -276,7 +183,7 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
     if (z_n < 0) z_n = L.nz - z_lo;
     if (z_lo < 0 || z_lo + z_n > L.nz) return cudaErrorInvalidValue;
     if (z_n == 0 && mode != BULK_BAND) return cudaSuccess;
-    return dispatch(storage, [&](auto tag) {
+    return dispatch_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
         dim3 grid((L.nx + bx - 1) / bx, L.ny, z_n);
@@ -314,50 +221,6 @@ cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
         }
         bulk_kernel<S, false, VM><<<grid, bx, 0, s>>>(L, (const S *)fa, (S *)fb, flags, status, sweep, mode,
                                                       capx, capy, z_lo);
-        return cudaGetLastError();
-    });
-}
-
-cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
-                        const double *u, const double *xi, double amp, cudaStream_t s)
-{
-    return dispatch(storage, [&](auto tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        const int nb = (int)((L.N + 255) / 256);
-        init_kernel<S><<<nb, 256, 0, s>>>(L, (S *)fa, rho, u, xi, amp);
-        return cudaGetLastError();
-    });
-}
-
-cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,
-                                double *out, cudaStream_t s)
-{
-    return dispatch(storage, [&](auto tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        const int nb = (int)((L.N + 255) / 256);
-        decode_kernel<S><<<nb, 256, 0, s>>>(L, (const S *)f, i, out);
-        return cudaGetLastError();
-    });
-}
-
-cudaError_t launch_encode_plane(int storage, const Lattice &L, void *f, int i,
-                                const double *in, cudaStream_t s)
-{
-    return dispatch(storage, [&](auto tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        const int nb = (int)((L.N + 255) / 256);
-        encode_kernel<S><<<nb, 256, 0, s>>>(L, (S *)f, i, in);
-        return cudaGetLastError();
-    });
-}
-
-cudaError_t launch_totals(int storage, const Lattice &L, const void *f, const uint8_t *flags,
-                          double *partials, int nblocks, double *out, cudaStream_t s)
-{
-    (void)out;
-    return dispatch(storage, [&](auto tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        totals_kernel<S><<<nblocks, 256, 0, s>>>(L, (const S *)f, flags, partials);
         return cudaGetLastError();
     });
 }

@@ -98,14 +98,31 @@ struct Lattice {
 // periodic axes); cap = capacity of the box per axis (the BAND grid).
 enum BulkMode { BULK_ALL = 0, BULK_OUTSIDE = 1, BULK_BAND = 2 };
 
+// Calls fn with a null pointer of the storage type (one instantiation per
+// storage form).
+template <typename F>
+static cudaError_t dispatch_storage(int storage, F &&fn)
+{
+    switch (storage) {
+    case LBM_FP64: return fn((double *)nullptr);
+    case LBM_FP32: return fn((float *)nullptr);
+    case LBM_FP16: return fn((__half *)nullptr);
+    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // launchers ------------------------------------------------------------------
 // z_lo, z_n: the z layers [z_lo, z_lo + z_n) of ALL and OUTSIDE launches
 // (z_n < 0: to the last layer); BAND launches take the box's layers.
 cudaError_t launch_bulk(int storage, const Lattice &L, const void *fa, void *fb,
                         const uint8_t *flags, int *status, cudaStream_t s, int mode = BULK_ALL,
                         const int *sweep = nullptr, const int *cap = nullptr, int z_lo = 0, int z_n = -1);
-cudaError_t launch_init(int storage, const Lattice &L, void *fa, const double *rho,
-                        const double *u, const double *xi, double amp, cudaStream_t s);
+// the initial state from density, velocity and noise fields in double (T =
+// double) or single precision (T = float)
+template <typename T>
+cudaError_t launch_init(int storage, const Lattice &L, void *fa, const T *rho, const T *u, const T *xi, double amp,
+                        cudaStream_t s);
 cudaError_t launch_decode_plane(int storage, const Lattice &L, const void *f, int i,
                                 double *out, cudaStream_t s);
 cudaError_t launch_encode_plane(int storage, const Lattice &L, void *f, int i,

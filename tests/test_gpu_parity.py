@@ -347,7 +347,8 @@ def test_anguilliform_swimmer_full_size_sampled(storage):
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "fp64"])
 def test_init_from_pinned_host_fields(storage):
     """lbm_init_state reading pinned host fields across the host link gives
-    the bits of the same fields in device memory; pageable host memory is
+    the bits of the same fields in device memory, and lbm_init_state_f32 those
+    of the same single-precision values in double; pageable host memory is
     refused (LBM_ERR_ARG) before any kernel runs."""
     import ctypes
 
@@ -360,6 +361,15 @@ def test_init_from_pinned_host_fields(storage):
     b.init_state(torch.from_numpy(rho).pin_memory(), torch.from_numpy(u).pin_memory(),
                  torch.from_numpy(xi).pin_memory(), 1e-3)
     assert torch.equal(a.f, b.f)
+    # single-precision fields (lbm_init_state_f32): the bits of the same values in double
+    r32, u32, x32 = (torch.from_numpy(v.astype(np.float32)) for v in (rho, u, xi))
+    c = lbm.Lattice(shape, 0.05, storage=storage)
+    c.init_state(r32.pin_memory(), u32.pin_memory(), x32.pin_memory(), 1e-3)
+    d = lbm.Lattice(shape, 0.05, storage=storage)
+    d.init_state(r32.double().cuda(), u32.double().cuda(), x32.double().cuda(), 1e-3)
+    e = lbm.Lattice(shape, 0.05, storage=storage)
+    e.init_state(r32.cuda(), u32.cuda(), x32.cuda(), 1e-3)
+    assert torch.equal(c.f, d.f) and torch.equal(e.f, d.f)
     r = np.ascontiguousarray(rho)
     v = np.ascontiguousarray(u)
     st = lbm.lib().lbm_init_state(b._ctx, r.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
