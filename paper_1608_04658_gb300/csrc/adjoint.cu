@@ -1044,19 +1044,23 @@ __global__ void __launch_bounds__(BWARPS * 32) adjoint_refill_kernel(
     }
 }
 
-// theta-tangents of every mesh vertex at the pose of body state b: dy/dtheta
-// (position) and the central difference of it (velocity), 3 + 3 per vertex.
-// One warp per block: the FP64 arithmetic of a few thousand vertices spread
-// over as many SMs as there are warps, not over the few schedulers of a
-// handful of large blocks.
+// theta-tangents of every mesh vertex at the pose of body state b[j]: dy/dtheta
+// (position) and the central difference of it (velocity), 3 + 3 per vertex,
+// into dy[j] / dvy[j], for the steps j = blockIdx.y of a recomputed segment
+// at once.  One warp per block: the FP64 arithmetic spread over as many SMs
+// as there are warps, not over the few schedulers of a handful of large
+// blocks.
 constexpr int TANGENT_THREADS = 32;
-__global__ void __launch_bounds__(TANGENT_THREADS) vertex_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b)
+__global__ void __launch_bounds__(TANGENT_THREADS) vertex_tangent_kernel(const GeomParams G, const DevBody *__restrict__ b,
+                                                                         double *const *__restrict__ dy,
+                                                                         double *const *__restrict__ dvy)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
     if (v >= G.n_vertices) return;
-    const double s = G.mesh_rest[3 * v];
-    swimmer_midline_tangent(G, s, b->t, G.mesh_dy + 3 * (size_t)v);
-    swimmer_velocity_tangent(G, b->t, s, G.mesh_dvy + 3 * (size_t)v);
+    const double s = G.mesh_rest[3 * v], t = b[j].t;
+    swimmer_midline_tangent(G, s, t, dy[j] + 3 * (size_t)v);
+    swimmer_velocity_tangent(G, t, s, dvy[j] + 3 * (size_t)v);
 }
 
 // One reversed step of the free body's state (explicit Euler, Sec. 4.3, on
@@ -1331,8 +1335,6 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
         if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
         ctx->bcur = 1;
         if ((e = cudaMemsetAsync(ext, 0, (size_t)capv * Q * sizeof(double), side)) != cudaSuccess) return e;
-        if (G.kind == LBM_BODY_MESH) vertex_tangent_kernel<<<(G.n_vertices + TANGENT_THREADS - 1) / TANGENT_THREADS, TANGENT_THREADS, 0, side>>>(
-            G, b);
         adjoint_boundary_kernel<S><<<list_blocks(G.cap_boundary), BWARPS * 32, 0, side>>>(
             L, G, b, Sc.blist, Sc.bpos, st, A, flags1, lam_out, ext, tslots, badj, bslot, ct);
         adjoint_bulk_kernel<S><<<nbb, 128, 0, side>>>(L, G, st, A, flags1, lam_out, BULK_BAND, box0, nullptr);
@@ -1349,8 +1351,6 @@ cudaError_t reverse_step(lbm_ctx *ctx, const S *st, const NextAdj<typename Codec
     const DevBody *b = Sc.body + ctx->bcur;
     // the boundary adjoint runs beside the bulk adjoint (disjoint rows of Lam^t)
     if (ctx->has_body) {
-        if (G.kind == LBM_BODY_MESH)
-            vertex_tangent_kernel<<<(G.n_vertices + TANGENT_THREADS - 1) / TANGENT_THREADS, TANGENT_THREADS, 0, s>>>(G, b);
         if (G.kind == LBM_BODY_MESH && G.com_frame)
             com_tangent_kernel<<<(G.n_triangles + 255) / 256, 256, 0, s>>>(G, b, cpart, cticket, ct);
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
@@ -1381,6 +1381,7 @@ struct GeoSlot {
     double *mesh_pos = nullptr, *mesh_vel = nullptr, *col_x = nullptr;
     int *mesh_ipos = nullptr, *col_count = nullptr, *cell_count = nullptr, *cell_tri = nullptr;
     float *mesh_frac = nullptr, *tri_box = nullptr;
+    double *tan_dy = nullptr, *tan_dvy = nullptr;  // the vertices' theta-tangents at the step's pose
 };
 
 static GeoSlot live_slot(const lbm_ctx *ctx)
@@ -1422,6 +1423,8 @@ static void use_slot(lbm_ctx *ctx, const GeoSlot &g)
     S.cell_tri = G.cell_tri = g.cell_tri;
     S.mesh_frac = G.mesh_frac = g.mesh_frac;
     S.tri_box = G.tri_box = g.tri_box;
+    G.mesh_dy = g.tan_dy;
+    G.mesh_dvy = g.tan_dvy;
 }
 
 template <typename S>
@@ -1493,10 +1496,24 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                 ok = B.get(&g.mesh_pos, 3 * nv) && B.get(&g.mesh_vel, 3 * nv) && B.get(&g.mesh_ipos, 3 * nv) &&
                      B.get(&g.mesh_frac, 3 * nv) && B.get(&g.tri_box, 6 * nt) && B.get(&g.col_count, ncols) &&
                      B.get(&g.col_x, ncols * MESH_COL_CAP) && B.get(&g.cell_count, ncells) &&
-                     B.get(&g.cell_tri, ncells * MESH_CELL_CAP);
+                     B.get(&g.cell_tri, ncells * MESH_CELL_CAP) && B.get(&g.tan_dy, 3 * nv) &&
+                     B.get(&g.tan_dvy, 3 * nv);
             if (!ok)
                 return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the geometry slots failed");
         }
+    }
+    // the slots' tangent arrays for the batched vertex tangents of a segment
+    double **tanp = nullptr;
+    if (body && ctx->G.kind == LBM_BODY_MESH) {
+        if (!B.get(&tanp, 2 * (size_t)K))
+            return afail(ctx, LBM_ERR_OOM, "lbm_adjoint_step: device allocation of the geometry slots failed");
+        std::vector<double *> hp(2 * (size_t)K);
+        for (int j = 0; j < K; ++j) {
+            hp[j] = slots[j].tan_dy;
+            hp[K + j] = slots[j].tan_dvy;
+        }
+        if (cudaMemcpy(tanp, hp.data(), hp.size() * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
+            return afail(ctx, LBM_ERR_CUDA, "lbm_adjoint_step: slot table upload failed");
     }
     ctx->G.mesh_dy = tan_dy;
     ctx->G.mesh_dvy = tan_dvy;
@@ -1562,6 +1579,13 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
                 if (t == t1) break;
                 if (body) use_slot(ctx, slots[j]);
                 ADJ_CUDA(forward_step(ctx, seg + (size_t)j * state, seg + (size_t)(j + 1) * state, wrec), "recompute");
+            }
+            // the vertex tangents of every step of the segment at once, at the
+            // pose each step's geometry left (segbody[j + 1])
+            if (tanp) {
+                const dim3 tg((ctx->G.n_vertices + TANGENT_THREADS - 1) / TANGENT_THREADS, t1 - t0);
+                vertex_tangent_kernel<<<tg, TANGENT_THREADS, 0, s>>>(ctx->G, segbody + 1, tanp, tanp + K);
+                ADJ_CUDA(cudaGetLastError(), "vertex tangents");
             }
             // reverse the segment's steps
             for (int t = t1 - 1; t >= t0; --t) {
