@@ -81,6 +81,14 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
     assert L.lbm_create(C.byref(p), dummy, dummy, dummy, None, C.byref(ctx)) == binding.LBM_ERR_ARG
     assert L.lbm_step(None, 1) == binding.LBM_ERR_ARG
     assert L.lbm_last_error(None) == b"null context"
+    # the slab, two-phase step and force hand-over entry points, null context
+    d6 = (C.c_double * 6)()
+    for rc in (L.lbm_step_interior(None), L.lbm_step_edges(None), L.lbm_set_slab(None, 0, 8, 0, 8),
+               L.lbm_pack_layers(None, 0, 1, dummy), L.lbm_unpack_layers(None, 0, 1, dummy),
+               L.lbm_body_force_to_device(None, dummy), L.lbm_sum_body_force(None, dummy, 1),
+               L.lbm_set_body_force(None, d6, d6), L.lbm_init_state(None, dummy, dummy, None, 0.0),
+               L.lbm_init_state_f32(None, dummy, dummy, None, 0.0)):
+        assert rc == binding.LBM_ERR_ARG
 
 
 def test_product_package_does_not_import_the_oracle():
