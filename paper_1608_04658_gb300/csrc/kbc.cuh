@@ -135,33 +135,47 @@ __device__ __forceinline__ double log1p_r(double x) { return log1p(x); }
 //   e_i = (dh_i - (2b - 1) ds_i)/f^eq_i,  B_i = b dh_i/f^eq_i,
 // on the interval where every f'_i(g) is positive; r falls monotonically
 // there (r' = -sum dh_i B_i/(1 + e_i - g B_i) <= 0).  Safeguarded Newton from
-// the analytic value g0 with the interval as bracket (bisection when a step
-// leaves it) until the step is below tol, at most 40 iterations.  e and B come from the caller through
+// the analytic value g0: the iterates bracket the root (each sets lo or hi by
+// the sign of r), a step that leaves the bracket bisects it, and an iterate
+// outside the positivity interval moves into it; until the step is below tol,
+// at most 40 iterations.  e and B come from the caller through
 // the per-direction values (dh, ds, 1/f^eq) the function below recomputes.
 template <typename R, typename Terms>
 __device__ R exact_gamma(const Terms &terms, R beta, R g0, R tol)
 {
+    // the positivity interval (lo, hi) is formed only once an iterate leaves
+    // it (27 divisions; Newton from the analytic value, the root of the
+    // linearised condition, seldom needs it)
     R lo = -R(1e30), hi = R(1e30);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        R dh, ds, ifeq;
-        terms(i, dh, ds, ifeq);
-        const R e = (dh - (R(2) * beta - R(1)) * ds) * ifeq, B = beta * dh * ifeq;
-        if (B > R(0)) hi = fmin(hi, (R(1) + e) / B);
-        else if (B < R(0)) lo = fmax(lo, (R(1) + e) / B);
-    }
+    bool bracket = false;
     R g = g0;
-    if (!(g > lo && g < hi)) g = (lo > -R(1e29) && hi < R(1e29)) ? R(0.5) * (lo + hi) : (g <= lo ? lo + R(1) : hi - R(1));
     for (int it = 0; it < 40; ++it) {
         R r = 0, dr = 0;
+        bool inside = true;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             R dh, ds, ifeq;
             terms(i, dh, ds, ifeq);
             const R e = (dh - (R(2) * beta - R(1)) * ds) * ifeq, B = beta * dh * ifeq;
             const R x = e - g * B;
+            inside = inside && R(1) + x > R(0);
             r += dh * log1p_r(x);
-            dr -= dh * B / (R(1) + x);
+            dr -= dh * B * rcp_fast(R(1) + x);  // (the slope only steers the step)
+        }
+        if (!inside) {
+            if (!bracket) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    R dh, ds, ifeq;
+                    terms(i, dh, ds, ifeq);
+                    const R e = (dh - (R(2) * beta - R(1)) * ds) * ifeq, B = beta * dh * ifeq;
+                    if (B > R(0)) hi = fmin(hi, (R(1) + e) / B);
+                    else if (B < R(0)) lo = fmax(lo, (R(1) + e) / B);
+                }
+                bracket = true;
+            }
+            g = (lo > -R(1e29) && hi < R(1e29)) ? R(0.5) * (lo + hi) : (g <= lo ? lo + R(1) : hi - R(1));
+            continue;
         }
         if (r > R(0)) lo = g;
         else hi = g;
