@@ -19,6 +19,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   refill moments, momentum exchange force and torque, Couette with Grad walls, the Grad
   wall targets (target velocity and static + dynamic target density in co-moving flow),
   shear-wave and Taylor-Green viscosity: pinned.
+  Two-level block refinement (RefinedOracle; Sec. 4.2's two-level grid, readings in
+  kbc_oracle.c): pinned by uniform flow, refined Couette flow and a sound wave against
+  the single-level run at the fine resolution (tests/test_oracle_refine.py).
   Sphere refill density average and the sphere's Euler update beyond one step:
   pinned only by invariants (moments of the refilled node, mass accounting).
 """
@@ -133,6 +136,16 @@ def lib():
             L.orc_mesh_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
             L.orc_mesh_link.restype = C.c_double
             L.orc_mesh_mass.argtypes = [C.c_void_p, C.c_double, _D]
+            L.orc_refine_create.argtypes = [C.c_void_p, _I, _I]
+            L.orc_refine_create.restype = C.c_void_p
+            L.orc_refine_fine.argtypes = [C.c_void_p]
+            L.orc_refine_fine.restype = C.c_void_p
+            L.orc_refine_destroy.argtypes = [C.c_void_p]
+            L.orc_refine_destroy.restype = None
+            L.orc_refine_init.argtypes = [C.c_void_p]
+            L.orc_refine_init.restype = None
+            L.orc_refine_step.argtypes = [C.c_void_p, C.c_int]
+            L.orc_refine_step.restype = C.c_int
             _lib = L
     return _lib
 
@@ -227,9 +240,9 @@ class Oracle:
         self.N = nx * ny * nz
 
     def __del__(self):
-        if getattr(self, "_ctx", None):
+        if getattr(self, "_ctx", None) and not getattr(self, "_borrowed", False):
             lib().orc_destroy(self._ctx)
-            self._ctx = None
+        self._ctx = None
 
     # state ------------------------------------------------------------
     def set_f(self, f: np.ndarray):
@@ -413,3 +426,67 @@ def mesh_body(X, rest, tris, length, wave_amp, wave_length, wave_period, ramp=Fa
     b.mass = float(mass)
     b.t = float(t0)
     return b
+
+
+def fine_beta(beta: float) -> float:
+    """b of the fine level of a ratio-2 block under acoustic scaling: the
+    viscosity in fine lattice units is twice the coarse one."""
+    return beta / (2.0 - beta)
+
+
+class RefinedOracle:
+    """Two-level block refinement over a coarse ``Oracle`` (Sec. 4.2's
+    two-level grid; the readings are stated in kbc_oracle.c).  ``lo``, ``hi``:
+    the block's corner coarse nodes, both included.  ``fine`` is an
+    ``Oracle``-like view of the fine level, (2m + 2) nodes per axis with m =
+    hi - lo: fine node j sits at coarse coordinate lo + j/2.
+
+    Use: initialise ``coarse`` and ``fine`` (``init_state`` / ``set_f``), call
+    ``init()``, then ``step(n)`` (n coarse steps, 2n fine steps)."""
+
+    def __init__(self, coarse: Oracle, lo, hi):
+        self.coarse = coarse
+        self.lo = tuple(int(v) for v in lo)
+        self.hi = tuple(int(v) for v in hi)
+        lo_a = (C.c_int * 3)(*self.lo)
+        hi_a = (C.c_int * 3)(*self.hi)
+        self._r = lib().orc_refine_create(coarse._ctx, lo_a, hi_a)
+        if not self._r:
+            raise ValueError("bad refinement block (needs 1 <= lo, hi <= n - 2, hi - lo >= 3 and "
+                             "fluid coarse nodes from lo - 1 to hi + 1)")
+        m = [h - l for l, h in zip(self.lo, self.hi)]
+        fine = Oracle.__new__(Oracle)
+        fine._ctx = lib().orc_refine_fine(self._r)
+        fine._borrowed = True
+        fine.shape = tuple(2 * v + 2 for v in m)
+        fine.N = fine.shape[0] * fine.shape[1] * fine.shape[2]
+        self.fine = fine
+
+    def __del__(self):
+        if getattr(self, "_r", None):
+            self.fine._ctx = None
+            lib().orc_refine_destroy(self._r)
+            self._r = None
+
+    def init(self):
+        lib().orc_refine_init(self._r)
+
+    def step(self, n: int = 1):
+        if lib().orc_refine_step(self._r, int(n)) != 0:
+            raise MemoryError("oracle step allocation failed")
+
+    def coarse_valid(self) -> np.ndarray:
+        """(nz, ny, nx) bool: coarse nodes the refined step defines (all but
+        those more than one layer inside the block's surface)."""
+        nx, ny, nz = self.coarse.shape
+        v = np.ones((nz, ny, nx), dtype=bool)
+        (x0, y0, z0), (x1, y1, z1) = self.lo, self.hi
+        v[z0 + 2:z1 - 1, y0 + 2:y1 - 1, x0 + 2:x1 - 1] = False
+        return v
+
+    def fine_valid(self) -> np.ndarray:
+        """(nz, ny, nx) bool of the fine level: every node but the pad."""
+        nx, ny, nz = self.fine.shape
+        v = np.zeros((nz, ny, nx), dtype=bool)
+        v[:nz - 1, :ny - 1, :nx - 1] = True
+        return v

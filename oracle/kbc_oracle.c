@@ -22,6 +22,8 @@
  *   Sec. 4.2  plunging airfoil (analytic cambered stand-in, prescribed plunge)
  *   Sec. 4.3  anguilliform swimmer: triangulated body of elliptic cross
  *             sections, prescribed midline deformation, free translation
+ *   Sec. 4.2  two-level grid (cited, not stated): one fine block of ratio 2
+ *             coupled through rebuilt states (readings at the end of the file)
  *
  * Readings of points the paper leaves open are listed at the top of each
  * routine that takes them.  All arithmetic is IEEE double.
@@ -1219,4 +1221,277 @@ void orc_totals(const orc_ctx *c, double *out)
         for (int a = 0; a < 3; ++a) out[1 + a] += r * u[a];
         out[4] += 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     }
+}
+
+/* ------------------------------------------------ two-level block refinement */
+/* Sec. 4.2 runs the airfoil on a grid with two levels of resolution and cites
+ * its refinement algorithm without stating it.  Readings (the paper is silent
+ * on every one of them):
+ *  - one fine block of ratio 2 inside the coarse lattice, vertex-coincident:
+ *    fine node j (per axis) sits at coarse coordinate lo + j/2, j = 0 .. 2m,
+ *    m = hi - lo; the fine lattice holds 2m + 2 nodes per axis, the last one
+ *    a pad that no update reads;
+ *  - acoustic scaling: the fine level takes two steps of half the coarse time
+ *    step; u and rho are the same numbers on both levels and the viscosity in
+ *    fine lattice units is twice the coarse one, b_f = b_c / (2 - b_c);
+ *  - the fine nodes on the block's surface (some j in {0, 2m}) are not
+ *    updated by the fine level: their post-collision state at fine time t' is
+ *    the fine collision of a state rebuilt from the coarse pre-collision
+ *    moments (rho, u, Pi^neq) at t', taken trilinearly in space from the
+ *    coarse nodes of the block's surface and linearly in time;
+ *  - the coarse nodes strictly inside the block are not updated by the coarse
+ *    level; those one layer inside its surface (the only ones a coarse update
+ *    pulls from) take, after the fine level reaches t+1, the coarse collision
+ *    of a state rebuilt from the pre-collision moments of the coincident fine
+ *    node (fine node 2(X - lo));
+ *  - a rebuilt state is the entropic equilibrium (Eq. feq_min) at (rho, u)
+ *    plus the second-order Hermite term of Grad's distribution (Eq. grad)
+ *    carrying the donor's non-equilibrium pressure tensor Pi^neq = Pi -
+ *    Pi(f^eq(rho, u)), rescaled by the ratio of the two levels' relaxation
+ *    times times time steps: b_c / (2 b_f) coarse to fine, 2 b_f / b_c fine
+ *    to coarse (tau = 1/(2b) in each level's units; Pi^neq ~ tau dt grad u);
+ *  - the coarse moments at t = 0 are those of the initial coarse state.
+ * The coarse level may carry a body outside the block (its nodes from lo - 1
+ * to hi + 1 must be fluid and no boundary node); the fine level carries none. */
+typedef struct {
+    orc_ctx *c, *f;
+    int lo[3], hi[3], m[3];
+    double *Mold, *Mnew;   /* 10 moments per coarse node of [lo, hi]^3 */
+    double s_cf, s_fc;     /* Pi^neq factors coarse -> fine, fine -> coarse */
+} orc_refine;
+
+enum { NMOM = 10 };  /* rho, u (3), Pi^neq xx yy zz xy xz yz */
+
+static long rbox(const orc_refine *r, int X, int Y, int Z)
+{
+    return (X - r->lo[0]) + (long)(r->m[0] + 1) * ((Y - r->lo[1]) + (long)(r->m[1] + 1) * (Z - r->lo[2]));
+}
+
+/* (rho, u, Pi^neq) of pre-collision populations F. */
+static void refine_moments(const double *F, double *M)
+{
+    double rho, u[3], feq[Q], P[6] = {0, 0, 0, 0, 0, 0};
+    moments(F, &rho, u);
+    orc_feq(rho, u, feq);
+    for (int i = 0; i < Q; ++i) {
+        const int *c = C[i];
+        double d = F[i] - feq[i];
+        P[0] += c[0] * c[0] * d; P[1] += c[1] * c[1] * d; P[2] += c[2] * c[2] * d;
+        P[3] += c[0] * c[1] * d; P[4] += c[0] * c[2] * d; P[5] += c[1] * c[2] * d;
+    }
+    M[0] = rho;
+    for (int a = 0; a < 3; ++a) M[1 + a] = u[a];
+    for (int k = 0; k < 6; ++k) M[4 + k] = P[k];
+}
+
+/* Post-collision state of a receiving node: f^eq(rho, u) + Hermite term of
+ * s * Pi^neq, collided with the receiver's b. */
+static void refine_rebuild(const double *M, double s, double beta, int mode, double *out)
+{
+    double u[3] = {M[1], M[2], M[3]}, z[3] = {0, 0, 0}, feq[Q], hn[Q], f[Q];
+    double Pn[9] = {s * M[4], s * M[7], s * M[8],
+                    s * M[7], s * M[5], s * M[9],
+                    s * M[8], s * M[9], s * M[6]};
+    orc_feq(M[0], u, feq);
+    orc_grad(0.0, z, Pn, hn);  /* W_i (9/2) Pn : (c_i c_i - I/3) */
+    for (int i = 0; i < Q; ++i) f[i] = feq[i] + hn[i];
+    orc_collide(f, beta, mode, out);
+}
+
+static int on_box_surface(const int *j, const int *n2)
+{
+    for (int a = 0; a < 3; ++a)
+        if (j[a] == 0 || j[a] == n2[a]) return 1;
+    return 0;
+}
+
+/* Fills the fine surface nodes of fine state fs from the coarse moments at
+ * (1 - w) Mold + w Mnew. */
+static void refine_fill_ghosts(orc_refine *r, double *fs, double w)
+{
+    orc_ctx *f = r->f;
+    int n2[3] = {2 * r->m[0], 2 * r->m[1], 2 * r->m[2]};
+    for (int jz = 0; jz <= n2[2]; ++jz)
+        for (int jy = 0; jy <= n2[1]; ++jy)
+            for (int jx = 0; jx <= n2[0]; ++jx) {
+                int j[3] = {jx, jy, jz};
+                if (!on_box_surface(j, n2)) continue;
+                /* per axis: one coarse node (even j) or the two around it */
+                int X0[3], nk[3];
+                for (int a = 0; a < 3; ++a) {
+                    X0[a] = r->lo[a] + j[a] / 2;
+                    nk[a] = (j[a] & 1) ? 2 : 1;
+                }
+                double M[NMOM] = {0};
+                for (int dz = 0; dz < nk[2]; ++dz)
+                    for (int dy = 0; dy < nk[1]; ++dy)
+                        for (int dx = 0; dx < nk[0]; ++dx) {
+                            double wt = 1.0 / (nk[0] * nk[1] * nk[2]);
+                            long b = rbox(r, X0[0] + dx, X0[1] + dy, X0[2] + dz);
+                            for (int k = 0; k < NMOM; ++k)
+                                M[k] += wt * ((1.0 - w) * r->Mold[b * NMOM + k] + w * r->Mnew[b * NMOM + k]);
+                        }
+                double out[Q];
+                refine_rebuild(M, r->s_cf, f->p.beta, f->p.gamma_mode, out);
+                long n = nid(f, jx, jy, jz);
+                for (int i = 0; i < Q; ++i) fs[i * f->N + n] = out[i];
+            }
+}
+
+/* Creates the fine level of the block [lo, hi] (coarse node coordinates,
+ * both ends included) over coarse level c.  Returns NULL on a bad block. */
+orc_refine *orc_refine_create(orc_ctx *c, const int *lo, const int *hi)
+{
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < 1 || hi[a] > n[a] - 2 || hi[a] - lo[a] < 3) return NULL;
+    for (int z = lo[2] - 1; z <= hi[2] + 1; ++z)
+        for (int y = lo[1] - 1; y <= hi[1] + 1; ++y)
+            for (int x = lo[0] - 1; x <= hi[0] + 1; ++x)
+                if (c->solid0[nid(c, x, y, z)]) return NULL;
+    orc_refine *r = (orc_refine *)calloc(1, sizeof(orc_refine));
+    if (!r) return NULL;
+    r->c = c;
+    orc_params pf = c->p;
+    for (int a = 0; a < 3; ++a) {
+        r->lo[a] = lo[a];
+        r->hi[a] = hi[a];
+        r->m[a] = hi[a] - lo[a];
+    }
+    pf.nx = 2 * r->m[0] + 2;
+    pf.ny = 2 * r->m[1] + 2;
+    pf.nz = 2 * r->m[2] + 2;
+    for (int k = 0; k < 6; ++k) pf.face[k] = FACE_PERIODIC;
+    pf.beta = c->p.beta / (2.0 - c->p.beta);
+    orc_body none;
+    memset(&none, 0, sizeof(none));
+    r->f = orc_create(&pf, &none);
+    if (!r->f) return NULL;
+    long nb = (long)(r->m[0] + 1) * (r->m[1] + 1) * (r->m[2] + 1);
+    r->Mold = (double *)calloc((size_t)nb * NMOM, sizeof(double));
+    r->Mnew = (double *)calloc((size_t)nb * NMOM, sizeof(double));
+    r->f->fb = (double *)calloc((size_t)Q * r->f->N, sizeof(double));
+    if (!r->Mold || !r->Mnew || !r->f->fb) return NULL;
+    r->s_cf = c->p.beta / (2.0 * pf.beta);
+    r->s_fc = 2.0 * pf.beta / c->p.beta;
+    return r;
+}
+
+orc_ctx *orc_refine_fine(orc_refine *r) { return r->f; }
+
+void orc_refine_destroy(orc_refine *r)
+{
+    if (!r) return;
+    orc_destroy(r->f);
+    free(r->Mold);
+    free(r->Mnew);
+    free(r);
+}
+
+/* After both levels hold their initial state: the coarse moments at t = 0
+ * (from the coarse populations themselves) and the fine surface from them. */
+void orc_refine_init(orc_refine *r)
+{
+    orc_ctx *c = r->c;
+    for (int Z = r->lo[2]; Z <= r->hi[2]; ++Z)
+        for (int Y = r->lo[1]; Y <= r->hi[1]; ++Y)
+            for (int X = r->lo[0]; X <= r->hi[0]; ++X) {
+                double g[Q];
+                long n = nid(c, X, Y, Z);
+                for (int i = 0; i < Q; ++i) g[i] = c->fa[i * c->N + n];
+                refine_moments(g, r->Mold + rbox(r, X, Y, Z) * NMOM);
+            }
+    refine_fill_ghosts(r, r->f->fa, 0.0);
+}
+
+/* One fine step over the nodes off the block's surface and pad (fa -> fb). */
+static void refine_fine_interior(orc_refine *r)
+{
+    orc_ctx *f = r->f;
+    double out[Q], F[3], M[3];
+    for (int jz = 0; jz < f->p.nz; ++jz)
+        for (int jy = 0; jy < f->p.ny; ++jy)
+            for (int jx = 0; jx < f->p.nx; ++jx) {
+                long n = nid(f, jx, jy, jz);
+                int inner = jx >= 1 && jx < 2 * r->m[0] && jy >= 1 && jy < 2 * r->m[1] &&
+                            jz >= 1 && jz < 2 * r->m[2];
+                if (!inner) {
+                    for (int i = 0; i < Q; ++i) f->fb[i * f->N + n] = f->fa[i * f->N + n];
+                    continue;
+                }
+                node_update(f, jx, jy, jz, out, F, M);
+                for (int i = 0; i < Q; ++i) f->fb[i * f->N + n] = out[i];
+            }
+}
+
+/* Coarse step t -> t+1 and two fine steps, as the readings above state. */
+int orc_refine_step(orc_refine *r, int nsteps)
+{
+    orc_ctx *c = r->c, *f = r->f;
+    if (!c->fb) {
+        c->fb = (double *)calloc((size_t)Q * c->N, sizeof(double));
+        if (!c->fb) return 1;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        step_prepare(c);
+        /* coarse pre-collision moments at t+1 on the block's surface */
+        for (int Z = r->lo[2]; Z <= r->hi[2]; ++Z)
+            for (int Y = r->lo[1]; Y <= r->hi[1]; ++Y)
+                for (int X = r->lo[0]; X <= r->hi[0]; ++X) {
+                    int inner = X > r->lo[0] && X < r->hi[0] && Y > r->lo[1] && Y < r->hi[1] &&
+                                Z > r->lo[2] && Z < r->hi[2];
+                    if (inner) continue;
+                    double Fi[Q];
+                    int missing[Q];
+                    gather_node(c, X, Y, Z, Fi, missing);
+                    refine_moments(Fi, r->Mnew + rbox(r, X, Y, Z) * NMOM);
+                }
+        /* coarse update off the block's inside */
+        double F[3] = {0, 0, 0}, M[3] = {0, 0, 0}, out[Q];
+        for (int z = 0; z < c->p.nz; ++z)
+            for (int y = 0; y < c->p.ny; ++y)
+                for (int x = 0; x < c->p.nx; ++x) {
+                    long n = nid(c, x, y, z);
+                    int inner = x > r->lo[0] && x < r->hi[0] && y > r->lo[1] && y < r->hi[1] &&
+                                z > r->lo[2] && z < r->hi[2];
+                    if (inner || c->solid1[n]) {
+                        for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = c->fa[i * c->N + n];
+                        continue;
+                    }
+                    node_update(c, x, y, z, out, F, M);
+                    for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = out[i];
+                }
+        /* fine step to t + 1/2, surface at t + 1/2 */
+        refine_fine_interior(r);
+        refine_fill_ghosts(r, f->fb, 0.5);
+        double *t = f->fa; f->fa = f->fb; f->fb = t;
+        /* fine step to t + 1, surface at t + 1 */
+        refine_fine_interior(r);
+        refine_fill_ghosts(r, f->fb, 1.0);
+        /* coarse nodes one layer inside the surface from the fine level: the
+         * pre-collision moments at t+1 of the coincident fine node are its
+         * pulls from the fine state at t + 1/2 (still in f->fa) */
+        for (int Z = r->lo[2] + 1; Z <= r->hi[2] - 1; ++Z)
+            for (int Y = r->lo[1] + 1; Y <= r->hi[1] - 1; ++Y)
+                for (int X = r->lo[0] + 1; X <= r->hi[0] - 1; ++X) {
+                    int shell = X == r->lo[0] + 1 || X == r->hi[0] - 1 || Y == r->lo[1] + 1 ||
+                                Y == r->hi[1] - 1 || Z == r->lo[2] + 1 || Z == r->hi[2] - 1;
+                    if (!shell) continue;
+                    double Fi[Q], Mf[NMOM];
+                    int missing[Q];
+                    gather_node(f, 2 * (X - r->lo[0]), 2 * (Y - r->lo[1]), 2 * (Z - r->lo[2]), Fi, missing);
+                    refine_moments(Fi, Mf);
+                    refine_rebuild(Mf, r->s_fc, c->p.beta, c->p.gamma_mode, out);
+                    long n = nid(c, X, Y, Z);
+                    for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = out[i];
+                }
+        t = f->fa; f->fa = f->fb; f->fb = t;
+        t = c->fa; c->fa = c->fb; c->fb = t;
+        uint8_t *u = c->solid0; c->solid0 = c->solid1; c->solid1 = u;
+        for (int a = 0; a < 3; ++a) { c->b.F[a] = F[a]; c->b.M[a] = M[a]; }
+        t = r->Mold; r->Mold = r->Mnew; r->Mnew = t;
+        c->step++;
+        f->step += 2;
+    }
+    return 0;
 }

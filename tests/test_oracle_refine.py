@@ -1,0 +1,141 @@
+"""Pins of the oracle's two-level block refinement (Sec. 4.2 runs the airfoil
+on a two-level grid and cites the algorithm without stating it; the readings
+are listed in oracle/kbc_oracle.c before orc_refine_create).
+
+What fixes the refined step independently of its own arithmetic:
+  - uniform flow is an exact steady state of the method on any lattice, so
+    both levels must keep it to round-off;
+  - plane Couette flow has a linear steady profile, which linear
+    interpolation carries exactly; the coupling only truncates Grad's
+    non-equilibrium to second order, an O(U) relative residual (about 5e-6
+    at U = 1e-3).  Rescaling the non-equilibrium pressure tensor by 1
+    instead of the ratio of the levels' relaxation times (either way), or
+    dropping it, or placing a surface node half a cell off, each leave
+    residuals of 1.7e-3 or more;
+  - a sound wave crossing the block must match the plain single-level
+    method run everywhere at the fine resolution (twice the nodes per axis,
+    half the time step, twice the viscosity in lattice units) as closely as
+    the plain coarse run does; the surface state of the half step taken at
+    t or at t+1 instead of their mean leaves 2.6e-2 or more of the wave's
+    amplitude instead of 3e-3.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+
+def _vel(orc, f):
+    c, _ = orc.lattice()
+    rho = f.sum(0)
+    return np.einsum("ia,izyx->zyxa", c, f) / rho[..., None], rho
+
+
+def test_fine_beta_doubles_the_viscosity(orc):
+    for beta in (0.3, 0.5, 0.8, 0.99):
+        nu_c = (1.0 / beta - 1.0) / 6.0
+        nu_f = (1.0 / orc.fine_beta(beta) - 1.0) / 6.0
+        assert nu_f == pytest.approx(2.0 * nu_c, rel=1e-14)
+
+
+def test_refined_block_keeps_uniform_flow(orc):
+    U = (0.05, -0.03, 0.02)
+    o = orc.Oracle((12, 12, 12), nu=0.01)
+    o.init_state(*synth.uniform_fields((12, 12, 12), U))
+    r = orc.RefinedOracle(o, (3, 3, 3), (8, 8, 8))
+    assert r.fine.shape == (12, 12, 12)
+    r.fine.init_state(*synth.uniform_fields(r.fine.shape, U))
+    r.init()
+    r.step(5)
+    fe = orc.feq(1.0, U)[:, None, None, None]
+    assert np.abs(o.get_f() - fe)[:, r.coarse_valid()].max() < 1e-14
+    assert np.abs(r.fine.get_f() - fe)[:, r.fine_valid()].max() < 1e-14
+
+
+def test_refined_block_rejects_blocks_it_cannot_hold(orc):
+    o = orc.Oracle((12, 12, 12), nu=0.01)
+    with pytest.raises(ValueError):
+        orc.RefinedOracle(o, (0, 3, 3), (8, 8, 8))   # touches the box face
+    with pytest.raises(ValueError):
+        orc.RefinedOracle(o, (3, 3, 3), (11, 8, 8))  # beyond n - 2
+    with pytest.raises(ValueError):
+        orc.RefinedOracle(o, (3, 3, 3), (5, 8, 8))   # fewer than 3 cells
+
+
+def test_refined_couette_keeps_the_linear_profile(orc):
+    """Couette flow between Grad walls (bottom at rest at y = 1.7, top moving
+    with U at y = 18.3), a fine block over y in [6, 13].  Both levels start
+    from the converged single-level states of their own resolution; after 501
+    coarse steps the velocity on both levels is the linear profile to 2e-5 U
+    and the cross-stream velocity stays below 1e-4 U."""
+    U, beta, ny = 1e-3, 0.8, 20
+    y_lo, y_hi = 1.7, ny - 2 + 0.3
+    oc = orc.Oracle((1, ny, 1), beta=beta, body=orc.planes_body(y_lo, y_hi, U_hi=(U, 0, 0)))
+    oc.init_state(*synth.uniform_fields((1, ny, 1)))
+    oc.step(20000)
+    of = orc.Oracle((1, 2 * ny, 1), beta=orc.fine_beta(beta),
+                    body=orc.planes_body(2 * y_lo, 2 * y_hi, U_hi=(U, 0, 0)))
+    of.init_state(*synth.uniform_fields((1, 2 * ny, 1)))
+    of.step(40000)
+    f1c, f1f = oc.get_f(), of.get_f()
+
+    nx = 6
+    o = orc.Oracle((nx, ny, nx), beta=beta, body=orc.planes_body(y_lo, y_hi, U_hi=(U, 0, 0)))
+    o.set_f(np.broadcast_to(f1c, (27, nx, ny, nx)).copy())
+    lo, hi = (1, 6, 1), (4, 13, 4)
+    r = orc.RefinedOracle(o, lo, hi)
+    fx, fy, fz = r.fine.shape
+    ff = np.empty((27, fz, fy, fx))
+    for j in range(fy):  # fine node j sits at coarse y = lo + j/2, fine-lattice row 2 lo + j
+        ff[:, :, j, :] = f1f[:, 0, min(2 * lo[1] + j, 2 * ny - 1), 0][:, None, None]
+    r.fine.set_f(ff)
+    r.init()
+    r.step(501)
+
+    uc, _ = _vel(orc, o.get_f())
+    uf, _ = _vel(orc, r.fine.get_f())
+    yc = np.arange(ny)[None, :, None]
+    yf = (lo[1] + np.arange(fy) / 2.0)[None, :, None]
+    fluid = r.coarse_valid() & (yc >= 2) & (yc <= ny - 2)
+    lin_c = U * (yc - y_lo) / (y_hi - y_lo)
+    lin_f = U * (yf - y_lo) / (y_hi - y_lo)
+    vf = r.fine_valid()
+    assert np.abs(uc[..., 0] - lin_c)[fluid].max() < 2e-5 * U
+    assert np.abs(uf[..., 0] - lin_f)[vf].max() < 2e-5 * U
+    assert np.abs(uc[..., 1:])[fluid].max() < 1e-4 * U
+    assert np.abs(uf[..., 1:])[vf].max() < 1e-4 * U
+
+
+def test_refined_sound_wave_matches_the_fine_single_level_run(orc):
+    """A standing sound wave rho = 1 + 1e-3 sin(2 pi x / 24) through a block
+    over x in [8, 15]: after 30 coarse steps the fine level's density matches
+    the single-level run at the fine resolution (48 x 16 x 16 nodes, 60
+    steps) to 6e-3 of the amplitude, and the coarse level matches it at the
+    coincident nodes to the same bar (the plain coarse run: 3.8e-3)."""
+    beta, T, d = 0.8, 30, 1e-3
+    nx, ny, nz = 24, 8, 8
+    lo, hi = (8, 2, 2), (15, 5, 5)
+
+    def fields(shape, scale, x0=0.0):
+        X, Y, Z = shape
+        x = x0 + np.arange(X) / scale
+        rho = np.ones((Z, Y, X)) + d * np.sin(2 * np.pi * x / nx)[None, None, :]
+        return rho, np.zeros((Z, Y, X, 3))
+
+    o = orc.Oracle((nx, ny, nz), beta=beta)
+    o.init_state(*fields((nx, ny, nz), 1))
+    r = orc.RefinedOracle(o, lo, hi)
+    r.fine.init_state(*fields(r.fine.shape, 2, lo[0]))
+    r.init()
+    r.step(T)
+    fine1 = orc.Oracle((2 * nx, 2 * ny, 2 * nz), beta=orc.fine_beta(beta))
+    fine1.init_state(*fields((2 * nx, 2 * ny, 2 * nz), 2))
+    fine1.step(2 * T)
+
+    ra = fine1.get_f().sum(0)
+    fx, fy, fz = r.fine.shape
+    sub = ra[2 * lo[2]:2 * lo[2] + fz, 2 * lo[1]:2 * lo[1] + fy, 2 * lo[0]:2 * lo[0] + fx]
+    rf = r.fine.get_f().sum(0)
+    rc = o.get_f().sum(0)
+    assert np.abs(rf - sub)[r.fine_valid()].max() < 6e-3 * d
+    assert np.abs(rc - ra[::2, ::2, ::2])[r.coarse_valid()].max() < 6e-3 * d
