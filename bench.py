@@ -63,6 +63,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-refinement", action="store_true",
+                    help="skip the two-level block refinement line (key refinement)")
+    ap.add_argument("--refinement-only", action="store_true",
+                    help="print only the two-level block refinement line")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller box with the same sphere (profiling cases only); "
                          "n (or n,n,n) of the periodic Taylor-Green box (default 256)")
@@ -628,6 +632,80 @@ def accuracy_bench(args, device):
     return out
 
 
+def refine_bench(args, world, device, clocks, storages=("fp32", "fp16")):
+    """The two-level block refinement (lbm_refine_step; Sec. 4.2's two-level
+    grid) on the refined block workload: per coarse step the coarse launch
+    off the block's inside, two fine launches over the block's interior and
+    the surface/restriction kernels.  GLUPS counts every node update (coarse
+    nodes updated + 2 x fine interior nodes per coarse step); the fine-grid
+    equivalent counts the updates a uniform fine grid over the whole coarse
+    box would make in the same simulated time (16 per coarse node and coarse
+    step).  The roofline is that of the fine bulk launch (CUDA events on the
+    shared stream around each of its launches)."""
+    import numpy as np
+    import torch
+
+    import paper_1608_04658_gb300 as lbm
+    import synth
+    wl = synth.refined_block()
+    (nx, ny, nz), lo, hi = wl["shape"], wl["lo"], wl["hi"]
+    m = [h - l for l, h in zip(lo, hi)]
+    coarse_updated = nx * ny * nz - (m[0] - 1) * (m[1] - 1) * (m[2] - 1)
+    fine_interior = (2 * m[0] - 1) * (2 * m[1] - 1) * (2 * m[2] - 1)
+    per_step = coarse_updated + 2 * fine_interior
+    K, W = args.steps, args.warmup
+    peak, peak_kind = measured_hbm_peak()
+    out = {"workload": wl["name"], "coarse_nodes_updated_per_step": coarse_updated,
+           "fine_interior_nodes": fine_interior, "node_updates_per_coarse_step": per_step,
+           "faces": list(wl["faces"]), "nu_coarse": wl["nu"], "steps": K, "warmup": W}
+    for st in storages:
+        lat = lbm.Lattice(wl["shape"], wl["nu"], storage=st, faces=wl["faces"], u_face=wl["u_face"], device=device)
+        ref = lbm.Refinement(lat, lo, hi)
+        lat.init_state(*synth.refined_fields(wl, "coarse"))
+        ref.fine.init_state(*synth.refined_fields(wl, "fine"))
+        ref.init()
+        ref.step(W)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        ref.fine.profile_begin(2 * K)
+        t0 = time.time()
+        start.record(lat.stream)
+        ref.step(K)
+        end.record(lat.stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        dist_barrier(world)
+        clocks.mark(t0, t1)
+        fine_ms, nfine = ref.fine.profile_end()
+        ms = dist_max(start.elapsed_time(end), world)
+        tot = lat.totals()  # finite sums: the run stayed stable
+        if not np.all(np.isfinite(tot)):
+            raise RuntimeError("refined run went unstable")
+        fine_ms /= max(nfine, 1)
+        bytes_launch = fine_interior * BYTES_PER_NODE[st]
+        achieved = bytes_launch / (fine_ms * 1e-3) / 1e9
+        out[st] = {"value": round(per_step * K * world / (ms * 1e-3) / 1e9, 4), "unit": "GLUPS",
+                   "dtype": DTYPE[st], "ms_per_step": round(ms / K, 5),
+                   "fine_grid_equivalent_glups": round(16 * nx * ny * nz * K * world / (ms * 1e-3) / 1e9, 4),
+                   "gpu_launches": lat.launches(),
+                   "roofline": {"bound": "hbm", "kernel": "bulk_pair_kernel (fine level)",
+                                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                                "traffic": ncu_traffic(st, wl["name"]),
+                                "algorithmic_bytes_per_launch": bytes_launch,
+                                "bulk_ms_per_launch": round(fine_ms, 5)},
+                   "fine_share_of_step": round(2 * fine_ms / (ms / K), 4)}
+        ref.close()
+        ref.fine.close()
+        lat.close()
+        del ref, lat
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_sample(wl):
     """Bounded sample of a workload for the FP64 oracle on the host:
     (workload of the sample, steps, description).  The swimmer's sample is one
@@ -759,6 +837,14 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"adjoint": adj}), flush=True)
         return
+    if args.refinement_only:
+        clocks = ClockSampler(local)
+        clocks.start()
+        ref = refine_bench(args, world, device, clocks)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"refinement": ref, "clocks": clk}), flush=True)
+        return
     wl = workload(args.shape, args.workload)
     # several GPUs split the box along z (one slab per rank, halo exchange);
     # --parallel replicas runs independent copies instead
@@ -783,6 +869,7 @@ def run_ours(args):
         wl2 = workload(None, args.second_workload)
         second[wl2["name"]] = (wl2, {st: time_storage(st, wl2, args, world, device, clocks)
                                      for st in (["fp32", "fp16", "bf16"] if not args.no_variants else ["fp32"])})
+    refined = refine_bench(args, world, device, clocks) if not args.no_refinement else None
     adj = adjoint_bench(args, world, device) if args.adjoint_horizon > 0 else None
     acc = accuracy_bench(args, device) if args.accuracy_steps > 0 and rank == 0 else None
     clk = clocks.stop()
@@ -834,6 +921,7 @@ def run_ours(args):
         "clocks": clk,
         "adjoint": adj,
         "accuracy": acc,
+        "refinement": refined,
         "variants": {st: {"value": round(r["glups"], 4), "unit": "GLUPS", "dtype": DTYPE[st.split("_")[0]],
                           "ms_per_step": round(r["ms"] / args.steps, 5),
                           "percent_of_hbm_roofline_step": round(100 * r["glups"] * BYTES_PER_NODE[st.split("_")[0]]

@@ -452,6 +452,60 @@ LBM_API lbm_status lbm_set_body_force(lbm_ctx *ctx, const double F[3], const dou
 LBM_API lbm_status lbm_body_force_to_device(lbm_ctx *ctx, double *dst);
 LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int nparts);
 
+/* ---------------------------------------------------- two-level block refinement
+ * Sec. 4.2 runs the airfoil on a grid with two levels of resolution and cites
+ * the refinement algorithm without stating it.  This is one fine block of
+ * ratio 2 inside a bodiless coarse lattice (both levels bodiless):
+ *   - fine node j (per axis) sits at coarse coordinate lo + j/2, j = 0 .. 2m,
+ *     m = hi - lo; the fine context's lattice has 2m + 2 nodes per axis and
+ *     periodic faces (no interior pull reaches them; the last layer is a pad
+ *     that nothing reads);
+ *   - acoustic scaling: the fine level takes two steps per coarse step with
+ *     the same rho and u and twice the coarse viscosity (its nu must be 2 nu
+ *     of the coarse context, so b_f = b_c / (2 - b_c), Sec. 2's b);
+ *   - the fine nodes on the block's surface are not updated by the fine
+ *     level: each fine time they take the fine KBC collision of the entropic
+ *     equilibrium (Eq. feq_min) at the coarse (rho, u) plus the second-order
+ *     Hermite term of Grad's distribution (Eq. grad) carrying the coarse
+ *     pre-collision Pi^neq times b_c / (2 b_f), the coarse moments taken
+ *     trilinearly from the coarse nodes of the block's surface and linearly
+ *     in time (the mean of t and t+1 at the half step);
+ *   - the coarse nodes strictly inside the block are not updated by the
+ *     coarse level; those one layer inside its surface take the coarse KBC
+ *     collision of the same rebuild from the pre-collision moments of the
+ *     coincident fine node, with the factor 2 b_f / b_c.
+ *
+ * lbm_refine_create couples coarse and fine (both from lbm_create, the same
+ * storage, stabilizer, rho0 and stream, no body, no slab) over the block of
+ * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2,
+ * hi - lo >= 3).  It writes the fine context's flags (the block's surface
+ * and the pad marked solid), allocates its own device scratch (two sets of
+ * 10 moments per node of the (m+1)^3 coarse box) with cudaMalloc and
+ * synchronises the stream.  Errors: LBM_ERR_ARG for a mismatch, with the
+ * reason in lbm_last_error(coarse); LBM_ERR_OOM.  *out is NULL on failure.
+ *
+ * lbm_refine_init, once both levels hold their initial state (lbm_init_state
+ * or lbm_set_populations): the coarse moments at t = 0 are taken from the
+ * coarse populations themselves and the fine surface is set from them.
+ * LBM_ERR_STATE if a level has no state.
+ *
+ * lbm_refine_step advances nsteps coarse steps (2 nsteps fine steps),
+ * asynchronously on the shared stream; afterwards read each level with
+ * lbm_get_populations as usual.  Do not call lbm_step on either context of a
+ * coupled pair.  Coarse nodes more than one layer inside the block's surface
+ * and the fine pad hold no defined state.  LBM_ERR_STATE before
+ * lbm_refine_init.  A fine profile (lbm_profile_begin on the fine context)
+ * times the fine bulk launches.
+ *
+ * lbm_refine_destroy synchronises the stream and frees the scratch; the two
+ * contexts stay valid. */
+typedef struct lbm_refine lbm_refine;
+LBM_API lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3], const int32_t hi[3],
+                                     lbm_refine **out);
+LBM_API lbm_status lbm_refine_init(lbm_refine *r);
+LBM_API lbm_status lbm_refine_step(lbm_refine *r, int nsteps);
+LBM_API void lbm_refine_destroy(lbm_refine *r);
+
 /* Global sums without a context and without device allocation.  The paper
  * has no counterpart to this entry point; it exists for callers that cannot
  * call cudaMalloc: applications that hand all device memory to their own

@@ -8,6 +8,6 @@ from .builder import build  # noqa: F401
 from .binding import (  # noqa: F401
     BODY_AIRFOIL, BODY_MESH, BODY_NONE, BODY_PLANES, BODY_SPHERE, FACE_EQ, FACE_OUTFLOW, FACE_PERIODIC, FACE_WALL,
     GAMMA_ANALYTIC, GAMMA_EXACT, GAMMA_LBGK, STORAGES, AdjointSpec, BodyState, Geometry, Lattice, LbmError, Params,
-    airfoil, declared_symbols, lib, make_params, planes, sphere, swimmer,
+    Refinement, airfoil, declared_symbols, fine_nu, lib, make_params, planes, sphere, swimmer,
 )
 from .autograd import KinematicsObjective, kinematics_objective  # noqa: F401,E402

@@ -155,6 +155,14 @@ def lib():
         L.lbm_body_force_to_device.argtypes = [vp, vp]
         L.lbm_body_force_to_device.restype = C.c_int
         L.lbm_sum_body_force.argtypes = [vp, vp, C.c_int]
+        L.lbm_refine_create.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(vp)]
+        L.lbm_refine_create.restype = C.c_int
+        L.lbm_refine_init.argtypes = [vp]
+        L.lbm_refine_init.restype = C.c_int
+        L.lbm_refine_step.argtypes = [vp, C.c_int]
+        L.lbm_refine_step.restype = C.c_int
+        L.lbm_refine_destroy.argtypes = [vp]
+        L.lbm_refine_destroy.restype = None
         L.lbm_sum_body_force.restype = C.c_int
         _lib = L
     return _lib
@@ -523,3 +531,53 @@ class Lattice:
         out = np.zeros(5)
         self._check(lib().lbm_totals(self._ctx, out.ctypes.data_as(_D)))
         return out
+
+
+def fine_nu(nu: float) -> float:
+    """Viscosity of the fine level of a ratio-2 block in its own lattice units
+    (acoustic scaling: twice the coarse value)."""
+    return 2.0 * float(nu)
+
+
+class Refinement:
+    """Two-level block refinement (lbm_refine_*; Sec. 4.2's two-level grid).
+
+    ``coarse`` is a bodiless Lattice; the block covers its nodes [lo, hi] per
+    axis (both ends included).  The fine Lattice (2 (hi - lo) + 2 nodes per
+    axis, periodic faces, twice the coarse viscosity, same storage, stabilizer
+    and stream) is created here as ``self.fine``: fine node j sits at coarse
+    coordinate lo + j/2.  Initialise both levels, call ``init()``, then
+    ``step(n)`` (n coarse steps, 2n fine steps)."""
+
+    def __init__(self, coarse: Lattice, lo, hi):
+        self.coarse = coarse
+        self.lo = tuple(int(v) for v in lo)
+        self.hi = tuple(int(v) for v in hi)
+        shape = tuple(2 * (h - l) + 2 for l, h in zip(self.lo, self.hi))
+        p = coarse.params
+        self.fine = Lattice(shape, fine_nu(p.nu), coarse.storage, rho0=coarse.rho0, gamma_mode=p.gamma_mode,
+                            device=coarse.device)
+        r = C.c_void_p()
+        lo_a = (C.c_int32 * 3)(*self.lo)
+        hi_a = (C.c_int32 * 3)(*self.hi)
+        st = lib().lbm_refine_create(coarse._ctx, self.fine._ctx, lo_a, hi_a, C.byref(r))
+        if st != LBM_OK:
+            raise LbmError(st, lib().lbm_last_error(coarse._ctx).decode())
+        self._r = r
+
+    def close(self):
+        if getattr(self, "_r", None):
+            lib().lbm_refine_destroy(self._r)
+            self._r = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self):
+        self.coarse._check(lib().lbm_refine_init(self._r))
+
+    def step(self, n: int = 1):
+        self.coarse._check(lib().lbm_refine_step(self._r, int(n)))

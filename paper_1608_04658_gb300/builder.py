@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["bulk.cu", "state.cu", "boundary.cu", "geometry.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["bulk.cu", "state.cu", "boundary.cu", "geometry.cu", "api.cu", "noalloc.cu", "adjoint.cu", "refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -516,8 +516,11 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     return LBM_OK;
 }
 
-// records the start (which = 0) or stop (1) event of a profiled bulk launch
-static cudaError_t prof_mark(lbm_ctx *ctx, int which)
+static cudaError_t prof_mark(lbm_ctx *ctx, int which) { return ctx_prof_mark(ctx, which); }
+
+}  // extern "C"
+
+cudaError_t ctx_prof_mark(lbm_ctx *ctx, int which)
 {
     if (!ctx->prof_open) return cudaSuccess;
     const int k = 2 * ctx->prof_used + which;
@@ -526,6 +529,8 @@ static cudaError_t prof_mark(lbm_ctx *ctx, int which)
     if (which == 1) ctx->prof_used++;
     return e;
 }
+
+extern "C" {
 
 // Geometry and refill first, then the boundary nodes and the force on the
 // side stream beside one bulk launch over all nodes (flags read when there is

@@ -60,6 +60,10 @@ struct lbm_ctx {
     bool interior_pending = false;
 };
 
+// records the start (which = 0) or stop (1) event of a profiled bulk launch
+// on the context stream while a profile (lbm_profile_begin) is open
+cudaError_t ctx_prof_mark(lbm_ctx *ctx, int which);
+
 // waits on the host for the asynchronous force-record copies that may still
 // read the body slots (before a call that rewrites the slots)
 inline cudaError_t drain_records(lbm_ctx *ctx)

@@ -1,0 +1,467 @@
+// Two-level block refinement (arXiv 1608.04658, Sec. 4.2: the airfoil runs on
+// a grid with two levels of resolution; the refinement algorithm is cited,
+// not stated).  One fine block of ratio 2 inside a bodiless coarse lattice:
+//
+//   - fine node j (per axis) sits at coarse coordinate lo + j/2, j = 0 .. 2m
+//     (m = hi - lo); the fine lattice has 2m + 2 nodes per axis, periodic
+//     faces that no interior pull reaches, and a last pad layer nothing reads;
+//   - acoustic scaling: two fine steps per coarse step, the same rho and u on
+//     both levels, twice the viscosity in fine lattice units;
+//   - the fine nodes on the block's surface are not updated by the fine
+//     level (flagged solid for its bulk launch): their post-collision state
+//     at fine time t' is the fine collision of a state rebuilt from the coarse
+//     pre-collision moments (rho, u, Pi^neq) at t', trilinear in space from
+//     the coarse nodes of the block's surface and linear in time;
+//   - the coarse nodes strictly inside the block are skipped by the coarse
+//     bulk launch; those one layer inside its surface (the only ones a
+//     coarse update pulls from) take the coarse collision of a state rebuilt
+//     from the pre-collision moments of the coincident fine node;
+//   - a rebuilt state is the entropic equilibrium (Eq. feq_min) at (rho, u)
+//     plus the second-order Hermite term of Grad's distribution (Eq. grad)
+//     carrying the donor's Pi^neq = Pi - Pi(f^eq(rho, u)), rescaled by the
+//     ratio of relaxation time x time step of the levels: b_c / (2 b_f)
+//     coarse to fine, 2 b_f / b_c fine to coarse.
+//
+// Per coarse step (one stream): coarse surface moments at t+1 (pulled from
+// the coarse state at t), the coarse bulk launch off the block's inside, two
+// fine bulk launches each followed by the surface fill (at t + 1/2 from the
+// mean of the moments at t and t+1, at t+1 from those at t+1), then the
+// coarse layer inside the surface from the fine state at t + 1/2's pulls.
+// Moments are kept in the collision's arithmetic (double for FP64 storage,
+// float otherwise) as rho - rho0, u, Pi^neq, one array per quantity.
+#include <cmath>
+#include <new>
+#include <string>
+#include <type_traits>
+
+#include "ctx.cuh"
+#include "kbc.cuh"
+
+using namespace lbm;
+
+namespace lbm {
+
+constexpr int NMOM = 10;  // rho - rho0, u (3), Pi^neq xx yy zz xy xz yz
+constexpr int REFINE_THREADS = 128;
+
+// nodes on the surface of a box of A x B x C nodes (each >= 2)
+__host__ __device__ inline long long surface_count(int A, int B, int C)
+{
+    return 2LL * A * B + 2LL * A * (C - 2) + 2LL * (B - 2) * (C - 2);
+}
+
+// k-th surface node of that box: the two z faces, then the two y faces
+// between them, then the two x faces between those
+__device__ inline void surface_node(long long k, int A, int B, int C, int &x, int &y, int &z)
+{
+    const long long ab = (long long)A * B;
+    if (k < 2 * ab) {
+        z = k < ab ? 0 : C - 1;
+        if (k >= ab) k -= ab;
+        x = (int)(k % A);
+        y = (int)(k / A);
+        return;
+    }
+    k -= 2 * ab;
+    const long long ac = (long long)A * (C - 2);
+    if (k < 2 * ac) {
+        y = k < ac ? 0 : B - 1;
+        if (k >= ac) k -= ac;
+        x = (int)(k % A);
+        z = 1 + (int)(k / A);
+        return;
+    }
+    k -= 2 * ac;
+    const long long bc = (long long)(B - 2) * (C - 2);
+    x = k < bc ? 0 : A - 1;
+    if (k >= bc) k -= bc;
+    y = 1 + (int)(k % (B - 2));
+    z = 1 + (int)(k / (B - 2));
+}
+
+// (rho - rho0, u, Pi^neq) of the shifted pre-collision populations g
+template <typename R>
+__device__ inline void node_moments(const R g[Q], R rho0, R M[NMOM])
+{
+    R drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += g[i];
+        j[0] += R(cx_of(i)) * g[i];
+        j[1] += R(cy_of(i)) * g[i];
+        j[2] += R(cz_of(i)) * g[i];
+    }
+    const R rho = rho0 + drho;
+    const R u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
+    axis_eq(u[0], ex, rx);
+    axis_eq(u[1], ey, ry);
+    axis_eq(u[2], ez, rz);
+    R P[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R d = g[i] - shifted_feq<R>(i, drho, rho, ex, ey, ez);
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        P[0] += R(cx * cx) * d;
+        P[1] += R(cy * cy) * d;
+        P[2] += R(cz * cz) * d;
+        P[3] += R(cx * cy) * d;
+        P[4] += R(cx * cz) * d;
+        P[5] += R(cy * cz) * d;
+    }
+    M[0] = drho;
+    M[1] = u[0];
+    M[2] = u[1];
+    M[3] = u[2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[4 + k] = P[k];
+}
+
+// shifted state f^eq(rho, u) + W_i (9/2) s Pi^neq : (c_i c_i - I/3) - W_i rho0
+template <typename R>
+__device__ inline void rebuild(const R M[NMOM], R s, R rho0, R g[Q])
+{
+    const R drho = M[0], rho = rho0 + drho;
+    R ex[3], ey[3], ez[3], rx[3], ry[3], rz[3];
+    axis_eq(M[1], ex, rx);
+    axis_eq(M[2], ey, ry);
+    axis_eq(M[3], ez, rz);
+    const R third = R(1) / R(3);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const R h = (R(cx * cx) - third) * M[4] + (R(cy * cy) - third) * M[5] + (R(cz * cz) - third) * M[6] +
+                    R(2 * cx * cy) * M[7] + R(2 * cx * cz) * M[8] + R(2 * cy * cz) * M[9];
+        g[i] = shifted_feq<R>(i, drho, rho, ex, ey, ez) + weight<R>(i) * (R(4.5) * s * h);
+    }
+}
+
+struct Box3 {
+    int lo[3];  // block corner in coarse nodes
+    int m[3];   // hi - lo per axis
+};
+
+// Coarse pre-collision moments on the block's surface: PULL, the pulls of the
+// next step from state f (the coarse state at t); otherwise f's own
+// populations (the initial state).  M[k * nbox + b], b the node's position in
+// the (m+1)^3 box.
+template <typename S, bool PULL>
+__global__ void __launch_bounds__(REFINE_THREADS) refine_moments_kernel(const Lattice L, const S *__restrict__ f,
+                                                                        const Box3 B,
+                                                                        typename Codec<S>::R *__restrict__ M)
+{
+    using R = typename Codec<S>::R;
+    const int A0 = B.m[0] + 1, A1 = B.m[1] + 1, A2 = B.m[2] + 1;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= surface_count(A0, A1, A2)) return;
+    int bx, by, bz;
+    surface_node(k, A0, A1, A2, bx, by, bz);
+    const int x = B.lo[0] + bx, y = B.lo[1] + by, z = B.lo[2] + bz;
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = PULL ? x - cx_of(i) : x, sy = PULL ? y - cy_of(i) : y, sz = PULL ? z - cz_of(i) : z;
+        g[i] = Codec<S>::load(f + L.plane[i] + (sx + L.nx * (sy + L.ny * sz)));
+    }
+    R Mn[NMOM];
+    node_moments<R>(g, (R)L.rho0, Mn);
+    const long long nbox = (long long)A0 * A1 * A2;
+    const long long b = bx + (long long)A0 * (by + (long long)A1 * bz);
+#pragma unroll
+    for (int q = 0; q < NMOM; ++q) M[q * nbox + b] = Mn[q];
+}
+
+// Fine surface nodes of fine state ff at the time (1 - w) t + w (t+1): the
+// moments trilinear from the coarse surface (each odd fine coordinate takes
+// the mean of the two coarse nodes around it), linear in time, rebuilt with
+// the coarse-to-fine factor and collided with the fine b.
+template <typename S, bool EXACT>
+__global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Lattice Lf, S *__restrict__ ff,
+                                                                     const Box3 B,
+                                                                     const typename Codec<S>::R *__restrict__ Mold,
+                                                                     const typename Codec<S>::R *__restrict__ Mnew,
+                                                                     typename Codec<S>::R w,
+                                                                     typename Codec<S>::R s_cf,
+                                                                     int *__restrict__ status)
+{
+    using R = typename Codec<S>::R;
+    const int F0 = 2 * B.m[0] + 1, F1 = 2 * B.m[1] + 1, F2 = 2 * B.m[2] + 1;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= surface_count(F0, F1, F2)) return;
+    int j[3];
+    surface_node(k, F0, F1, F2, j[0], j[1], j[2]);
+    const int A0 = B.m[0] + 1, A1 = B.m[1] + 1;
+    const long long nbox = (long long)A0 * A1 * (B.m[2] + 1);
+    int b0[3], nk[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b0[a] = j[a] >> 1;
+        nk[a] = (j[a] & 1) ? 2 : 1;
+    }
+    const R wt = R(1) / R(nk[0] * nk[1] * nk[2]);
+    R M[NMOM];
+#pragma unroll
+    for (int q = 0; q < NMOM; ++q) M[q] = R(0);
+    for (int dz = 0; dz < nk[2]; ++dz)
+        for (int dy = 0; dy < nk[1]; ++dy)
+            for (int dx = 0; dx < nk[0]; ++dx) {
+                const long long b = (b0[0] + dx) + (long long)A0 * ((b0[1] + dy) + (long long)A1 * (b0[2] + dz));
+#pragma unroll
+                for (int q = 0; q < NMOM; ++q)
+                    M[q] += wt * ((R(1) - w) * Mold[q * nbox + b] + w * Mnew[q * nbox + b]);
+            }
+    R g[Q];
+    rebuild<R>(M, s_cf, (R)Lf.rho0, g);
+    if (!kbc_collide<R, EXACT>(g, (R)Lf.beta, (R)Lf.inv_beta, (R)Lf.rho0, Lf.gamma_mode)) atomicOr(status, ST_UNSTABLE);
+    const int n = j[0] + Lf.nx * (j[1] + Lf.ny * j[2]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Codec<S>::store(ff + Lf.plane[i] + n, g[i]);
+}
+
+// Coarse nodes one layer inside the block's surface at t+1: the pulls of the
+// coincident fine node 2(X - lo) from the fine state at t + 1/2, their
+// moments rebuilt with the fine-to-coarse factor and collided with the
+// coarse b, written to the coarse state at t+1.
+template <typename S, bool EXACT>
+__global__ void __launch_bounds__(REFINE_THREADS) refine_restrict_kernel(const Lattice Lc, S *__restrict__ fc,
+                                                                         const Lattice Lf,
+                                                                         const S *__restrict__ ff, const Box3 B,
+                                                                         typename Codec<S>::R s_fc,
+                                                                         int *__restrict__ status)
+{
+    using R = typename Codec<S>::R;
+    const int A0 = B.m[0] - 1, A1 = B.m[1] - 1, A2 = B.m[2] - 1;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= surface_count(A0, A1, A2)) return;
+    int bx, by, bz;
+    surface_node(k, A0, A1, A2, bx, by, bz);
+    const int jx = 2 * (bx + 1), jy = 2 * (by + 1), jz = 2 * (bz + 1);
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        g[i] = Codec<S>::load(ff + Lf.plane[i] + ((jx - cx_of(i)) + Lf.nx * ((jy - cy_of(i)) + Lf.ny * (jz - cz_of(i)))));
+    R M[NMOM];
+    node_moments<R>(g, (R)Lf.rho0, M);
+    rebuild<R>(M, s_fc, (R)Lc.rho0, g);
+    if (!kbc_collide<R, EXACT>(g, (R)Lc.beta, (R)Lc.inv_beta, (R)Lc.rho0, Lc.gamma_mode)) atomicOr(status, ST_UNSTABLE);
+    const int n = (B.lo[0] + 1 + bx) + Lc.nx * ((B.lo[1] + 1 + by) + Lc.ny * (B.lo[2] + 1 + bz));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Codec<S>::store(fc + Lc.plane[i] + n, g[i]);
+}
+
+// fine-level marks: the block's surface and the pad are solid to the bulk
+// launch (it neither updates them nor reads their flags' neighbours' pulls)
+__global__ void refine_flags_kernel(uint8_t *flags, int nx, int ny, int nz, int e0, int e1, int e2)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (long long)nx * ny * nz) return;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const bool inner = x >= 1 && x < e0 && y >= 1 && y < e1 && z >= 1 && z < e2;
+    flags[n] = inner ? 0 : FL_SOLID;
+}
+
+static unsigned blocks_for(long long n) { return (unsigned)((n + REFINE_THREADS - 1) / REFINE_THREADS); }
+
+template <typename F>
+static cudaError_t dispatch_exact(int storage, bool exact, F &&fn)
+{
+    return dispatch_storage(storage, [&](auto tag) {
+        return exact ? fn(tag, std::true_type{}) : fn(tag, std::false_type{});
+    });
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------- host side
+struct lbm_refine {
+    lbm_ctx *c = nullptr, *f = nullptr;
+    Box3 B{};
+    void *M[2] = {nullptr, nullptr};  // moments at t (slot mcur) and t+1
+    int mcur = 0;
+    int *sweep = nullptr;             // device {lo + 1 (3), m - 1 (3)}: the coarse launch skips it
+    bool ready = false;
+    double s_cf = 0, s_fc = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+lbm_status rfail(lbm_ctx *c, lbm_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+#define RF_CUDA(call, where)                                                                            \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return rfail(r->c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void release(lbm_refine *r)
+{
+    cudaFree(r->M[0]);
+    cudaFree(r->M[1]);
+    cudaFree(r->sweep);
+    delete r;
+}
+
+cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pull)
+{
+    const long long n = surface_count(r->B.m[0] + 1, r->B.m[1] + 1, r->B.m[2] + 1);
+    const lbm_ctx *c = r->c;
+    return dispatch_storage(c->storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using R = typename Codec<S>::R;
+        if (pull)
+            refine_moments_kernel<S, true><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(c->L, (const S *)f, r->B, (R *)M);
+        else
+            refine_moments_kernel<S, false><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(c->L, (const S *)f, r->B, (R *)M);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const void *Mnew, double w)
+{
+    const long long n = surface_count(2 * r->B.m[0] + 1, 2 * r->B.m[1] + 1, 2 * r->B.m[2] + 1);
+    const lbm_ctx *f = r->f;
+    int *status = &f->S.body[f->bcur].status;
+    return dispatch_exact(f->storage, f->L.gamma_mode == LBM_GAMMA_EXACT, [&](auto tag, auto ex) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using R = typename Codec<S>::R;
+        refine_fill_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, f->stream>>>(
+            f->L, (S *)ff, r->B, (const R *)Mold, (const R *)Mnew, (R)w, (R)r->s_cf, status);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_restrict(const lbm_refine *r, void *fc, const void *ff)
+{
+    const long long n = surface_count(r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1);
+    const lbm_ctx *c = r->c;
+    int *status = &c->S.body[c->bcur].status;
+    return dispatch_exact(c->storage, c->L.gamma_mode == LBM_GAMMA_EXACT, [&](auto tag, auto ex) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using R = typename Codec<S>::R;
+        refine_restrict_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(
+            c->L, (S *)fc, r->f->L, (const S *)ff, r->B, (R)r->s_fc, status);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3], const int32_t hi[3],
+                             lbm_refine **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!coarse || !fine || !lo || !hi || coarse == fine) return LBM_ERR_ARG;
+    const Lattice &Lc = coarse->L, &Lf = fine->L;
+    const int n[3] = {Lc.nx, Lc.ny, Lc.nz}, nf[3] = {Lf.nx, Lf.ny, Lf.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (lo[a] < 1 || hi[a] > n[a] - 2 || hi[a] - lo[a] < 3)
+            return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the block needs 1 <= lo, hi <= n - 2, hi - lo >= 3");
+        if (nf[a] != 2 * (hi[a] - lo[a]) + 2)
+            return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine lattice needs 2 (hi - lo) + 2 nodes per axis");
+    }
+    for (int k = 0; k < 6; ++k)
+        if (Lf.face[k] != LBM_FACE_PERIODIC)
+            return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine lattice's faces must be periodic");
+    if (coarse->storage != fine->storage || Lc.gamma_mode != Lf.gamma_mode || Lc.rho0 != Lf.rho0)
+        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: storage, stabilizer and rho0 must match");
+    if (coarse->stream != fine->stream)
+        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: both levels must enqueue on the same stream");
+    // twice the coarse viscosity in fine lattice units: b_f = b_c / (2 - b_c)
+    const double bf = Lc.beta / (2.0 - Lc.beta);
+    if (!(std::fabs(Lf.beta - bf) <= 1e-12 * bf))
+        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine viscosity must be twice the coarse one");
+    if (coarse->has_body || fine->has_body || coarse->slab_zper || fine->slab_zper || !fine->flags)
+        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: both levels must be bodiless, unsplit contexts");
+
+    lbm_refine *r = new (std::nothrow) lbm_refine;
+    if (!r) return LBM_ERR_OOM;
+    r->c = coarse;
+    r->f = fine;
+    for (int a = 0; a < 3; ++a) {
+        r->B.lo[a] = lo[a];
+        r->B.m[a] = hi[a] - lo[a];
+    }
+    r->s_cf = Lc.beta / (2.0 * Lf.beta);
+    r->s_fc = 2.0 * Lf.beta / Lc.beta;
+    const size_t rsz = coarse->storage == LBM_FP64 ? sizeof(double) : sizeof(float);
+    const size_t nbox = (size_t)(r->B.m[0] + 1) * (r->B.m[1] + 1) * (r->B.m[2] + 1);
+    if (cudaMalloc(&r->M[0], NMOM * nbox * rsz) != cudaSuccess || cudaMalloc(&r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
+        cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        release(r);
+        return rfail(coarse, LBM_ERR_OOM, "lbm_refine_create: device allocation failed");
+    }
+    const int sw[6] = {lo[0] + 1, lo[1] + 1, lo[2] + 1, r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1};
+    cudaError_t e = cudaMemcpyAsync(r->sweep, sw, sizeof(sw), cudaMemcpyHostToDevice, coarse->stream);
+    if (e == cudaSuccess) {
+        const long long N = Lf.N;
+        refine_flags_kernel<<<blocks_for(N), REFINE_THREADS, 0, fine->stream>>>(
+            fine->flags, Lf.nx, Lf.ny, Lf.nz, 2 * r->B.m[0], 2 * r->B.m[1], 2 * r->B.m[2]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(coarse->stream);
+    if (e != cudaSuccess) {
+        release(r);
+        return rfail(coarse, LBM_ERR_CUDA, std::string("lbm_refine_create: ") + cudaGetErrorString(e));
+    }
+    *out = r;
+    return LBM_OK;
+}
+
+void lbm_refine_destroy(lbm_refine *r)
+{
+    if (!r) return;
+    if (r->c && r->c->stream) cudaStreamSynchronize(r->c->stream);
+    release(r);
+}
+
+lbm_status lbm_refine_init(lbm_refine *r)
+{
+    if (!r) return LBM_ERR_ARG;
+    if (!r->c->initialised || !r->f->initialised)
+        return rfail(r->c, LBM_ERR_STATE, "lbm_refine_init: both levels must hold their initial state");
+    RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], false), "refine moments");
+    RF_CUDA(launch_fill(r, r->f->f[r->f->cur], r->M[r->mcur], r->M[r->mcur], 0.0), "refine fill");
+    r->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_refine_step(lbm_refine *r, int nsteps)
+{
+    if (!r) return LBM_ERR_ARG;
+    if (nsteps < 0) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_step: nsteps < 0");
+    if (!r->ready) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_step: lbm_refine_init has not run");
+    lbm_ctx *c = r->c, *f = r->f;
+    for (int s = 0; s < nsteps; ++s) {
+        void *ca = c->f[c->cur], *cb = c->f[c->cur ^ 1];
+        void *fa = f->f[f->cur], *fb = f->f[f->cur ^ 1];
+        void *Mt = r->M[r->mcur], *Mn = r->M[r->mcur ^ 1];
+        int *cstat = &c->S.body[c->bcur].status, *fstat = &f->S.body[f->bcur].status;
+        RF_CUDA(launch_moments(r, ca, Mn, true), "refine moments");
+        RF_CUDA(launch_bulk(c->storage, c->L, ca, cb, nullptr, cstat, c->stream, BULK_OUTSIDE, r->sweep), "coarse bulk");
+        RF_CUDA(ctx_prof_mark(f, 0), "profile event");
+        RF_CUDA(launch_bulk(f->storage, f->L, fa, fb, f->flags, fstat, f->stream), "fine bulk");
+        RF_CUDA(ctx_prof_mark(f, 1), "profile event");
+        RF_CUDA(launch_fill(r, fb, Mt, Mn, 0.5), "refine fill");
+        RF_CUDA(ctx_prof_mark(f, 0), "profile event");
+        RF_CUDA(launch_bulk(f->storage, f->L, fb, fa, f->flags, fstat, f->stream), "fine bulk");
+        RF_CUDA(ctx_prof_mark(f, 1), "profile event");
+        RF_CUDA(launch_fill(r, fa, Mt, Mn, 1.0), "refine fill");
+        RF_CUDA(launch_restrict(r, cb, fb), "refine restrict");
+        c->cur ^= 1;
+        r->mcur ^= 1;
+    }
+    r->launches = 7LL * nsteps;
+    c->launches = 7LL * nsteps;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -139,6 +139,39 @@ def plunging_airfoil(shape=(1024, 512, 64), chord: float = 128.0, u_inf: float =
                 faces=(2, 3, 2, 2, 0, 0), u_face=(u_inf, 0.0, 0.0))
 
 
+def refined_block(shape=(512, 256, 64), lo=(128, 64, 8), hi=(383, 191, 55), u_inf: float = 0.05,
+                  nu: float = 1e-3, amp: float = 0.01):
+    """Two-level grid (Sec. 4.2 runs the airfoil on one): a bodiless coarse box
+    with the airfoil box's faces (equilibrium inflow x-, outflow x+,
+    equilibrium far field y, periodic z) and a ratio-2 block over the coarse
+    nodes [lo, hi]; the fine lattice holds 2 (hi - lo) + 2 nodes per axis.
+    The flow is the free stream plus a Taylor-Green perturbation of
+    amplitude amp (refined_fields)."""
+    nx, ny, nz = shape
+    fine = tuple(2 * (h - l) + 2 for l, h in zip(lo, hi))
+    return dict(name=f"refined_block_{nx}x{ny}x{nz}_fine_{fine[0]}x{fine[1]}x{fine[2]}", shape=shape,
+                lo=lo, hi=hi, fine_shape=fine, nu=nu, faces=(2, 3, 2, 2, 0, 0), u_face=(u_inf, 0.0, 0.0),
+                u_inf=u_inf, amp=amp)
+
+
+def refined_fields(wl, level: str):
+    """(rho, u) of the refined block workload on the coarse or the fine level:
+    u = (u_inf, 0, 0) + amp * (sin x^ cos y^ cos z^, -cos x^ sin y^ cos z^, 0)
+    with x^ = 2 pi x / n over the coarse box, evaluated at the level's node
+    positions (fine node j at coarse coordinate lo + j/2); rho = 1."""
+    nx, ny, nz = wl["shape"]
+    if level == "coarse":
+        dims, org, h = wl["shape"], (0, 0, 0), 1.0
+    else:
+        dims, org, h = wl["fine_shape"], wl["lo"], 0.5
+    ax = [2 * np.pi * (org[a] + h * np.arange(dims[a])) / wl["shape"][a] for a in range(3)]
+    z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    u = np.zeros((dims[2], dims[1], dims[0], 3))
+    u[..., 0] = wl["u_inf"] + wl["amp"] * np.sin(x) * np.cos(y) * np.cos(z)
+    u[..., 1] = -wl["amp"] * np.cos(x) * np.sin(y) * np.cos(z)
+    return np.ones((dims[2], dims[1], dims[0])), u
+
+
 # ------------------------------------------------------------------ swimmer
 def swimmer_half_width(s, L: float):
     """Half width w(s) of the anguilliform body (Sec. 4.3): sqrt(2 w_h s - s^2)

@@ -89,6 +89,15 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
                L.lbm_set_body_force(None, d6, d6), L.lbm_init_state(None, dummy, dummy, None, 0.0),
                L.lbm_init_state_f32(None, dummy, dummy, None, 0.0)):
         assert rc == binding.LBM_ERR_ARG
+    # the refinement entry points, null contexts and handles
+    r = C.c_void_p(7)
+    i3 = (C.c_int32 * 3)(1, 1, 1)
+    assert L.lbm_refine_create(None, None, i3, i3, C.byref(r)) == binding.LBM_ERR_ARG
+    assert not r.value
+    assert L.lbm_refine_create(dummy, dummy, i3, i3, None) == binding.LBM_ERR_ARG
+    assert L.lbm_refine_init(None) == binding.LBM_ERR_ARG
+    assert L.lbm_refine_step(None, 1) == binding.LBM_ERR_ARG
+    L.lbm_refine_destroy(None)
 
 
 def test_product_package_does_not_import_the_oracle():

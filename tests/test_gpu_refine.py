@@ -1,0 +1,142 @@
+"""GPU parity of the two-level block refinement (lbm_refine_*; Sec. 4.2's
+two-level grid, readings stated in include/lbm.h and oracle/kbc_oracle.c)
+against the oracle's RefinedOracle on the same seeded inputs, element by
+element on every node the refined step defines: all coarse nodes but those
+more than one layer inside the block's surface, all fine nodes but the pad.
+
+Bars as for the single-level step (tests/parity_util.py): 1e-12 FP64, 2e-6
+FP32, 2e-3 16-bit."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import TOL, random_fields, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1608_04658_gb300 as lbm
+    lbm.build()
+    lbm.lib()
+
+
+def run_refined(shape, nu, storage, lo, hi, steps, seed=1, faces=(0,) * 6, u_face=(0.0, 0.0, 0.0),
+                gamma_mode=0):
+    import paper_1608_04658_gb300 as lbm
+    rho, u, xi, amp = random_fields(shape, seed)
+    lat = lbm.Lattice(shape, nu, storage=storage, faces=faces, u_face=u_face, gamma_mode=gamma_mode)
+    ref = lbm.Refinement(lat, lo, hi)
+    frho, fu, fxi, famp = random_fields(ref.fine.shape, seed + 100)
+    lat.init_state(rho, u, xi, amp)
+    ref.fine.init_state(frho, fu, fxi, famp)
+    ref.init()
+    ref.step(steps)
+
+    orc = oracle.Oracle(shape, nu=nu, faces=faces, u_face=u_face, gamma_mode=gamma_mode)
+    orc.init_state(rho, u, xi, amp)
+    ro = oracle.RefinedOracle(orc, lo, hi)
+    assert ro.fine.shape == ref.fine.shape
+    ro.fine.init_state(frho, fu, fxi, famp)
+    ro.init()
+    ro.step(steps)
+    return lat, ref, orc, ro
+
+
+def errors(lat, ref, orc, ro):
+    ec = rel_err(lat.populations(), orc.get_f(), ro.coarse_valid())
+    ef = rel_err(ref.fine.populations(), ro.fine.get_f(), ro.fine_valid())
+    return ec, ef
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+def test_refined_step_matches_the_oracle(storage):
+    """A 24 x 20 x 18 periodic box with the block [5, 16] x [4, 13] x [3, 12]
+    (fine lattice 24 x 20 x 20), rough random states on both levels, 1 and 4
+    coarse steps."""
+    for steps in (1, 4):
+        lat, ref, orc, ro = run_refined((24, 20, 18), 0.02, storage, (5, 4, 3), (16, 13, 12), steps)
+        ec, ef = errors(lat, ref, orc, ro)
+        assert ec <= TOL[storage] and ef <= TOL[storage], (storage, steps, ec, ef)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_refined_step_with_box_faces_and_the_smallest_block(storage):
+    """Coarse faces of every kind (equilibrium inflow x-, outflow x+, walls y,
+    periodic z) around a block reaching to one node off them ([1, 14] x [1, 8]
+    on a 16 x 10 box), and the smallest block (three cells) in z."""
+    lat, ref, orc, ro = run_refined((16, 10, 9), 0.05, storage, (1, 1, 2), (14, 8, 5), 3, seed=5,
+                                    faces=(2, 3, 1, 1, 0, 0), u_face=(0.03, 0.0, 0.01))
+    ec, ef = errors(lat, ref, orc, ro)
+    assert ec <= TOL[storage] and ef <= TOL[storage], (storage, ec, ef)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_refined_step_exact_stabilizer(storage):
+    lat, ref, orc, ro = run_refined((20, 16, 14), 0.01, storage, (4, 3, 3), (13, 11, 9), 3, seed=9, gamma_mode=1)
+    ec, ef = errors(lat, ref, orc, ro)
+    assert ec <= TOL[storage] and ef <= TOL[storage], (storage, ec, ef)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_refined_step_several_tiles(storage):
+    """Fine rows of 160 nodes (two 128-node blocks of the bulk launch, the
+    second ragged) on a 100 x 36 x 30 coarse box, 3 coarse steps."""
+    lat, ref, orc, ro = run_refined((100, 36, 30), 0.01, storage, (10, 6, 5), (89, 21, 16), 3, seed=13)
+    assert ref.fine.shape == (160, 32, 24)
+    ec, ef = errors(lat, ref, orc, ro)
+    assert ec <= TOL[storage] and ef <= TOL[storage], (storage, ec, ef)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_refined_uniform_flow_stays_uniform(storage):
+    """Uniform flow is a steady state of both levels and of their coupling."""
+    import paper_1608_04658_gb300 as lbm
+    U = (0.04, -0.02, 0.03)
+    shape = (40, 24, 20)
+    lat = lbm.Lattice(shape, 0.01, storage=storage)
+    ref = lbm.Refinement(lat, (8, 5, 4), (31, 18, 15))
+    lat.init_state(*synth.uniform_fields(shape, U))
+    ref.fine.init_state(*synth.uniform_fields(ref.fine.shape, U))
+    ref.init()
+    ref.step(6)
+    fe = oracle.feq(1.0, U)[:, None, None, None]
+    vc = np.ones(shape[::-1], dtype=bool)
+    vc[6:14, 7:17, 10:30] = False
+    vf = np.zeros(ref.fine.shape[::-1], dtype=bool)
+    vf[:-1, :-1, :-1] = True
+    bar = 1e-14 if storage == "fp64" else 1e-6
+    assert rel_err(lat.populations(), np.broadcast_to(fe, (27,) + shape[::-1]), vc) < bar
+    assert rel_err(ref.fine.populations(), np.broadcast_to(fe, (27,) + ref.fine.shape[::-1]), vf) < bar
+
+
+def test_refinement_rejects_mismatched_levels():
+    import paper_1608_04658_gb300 as lbm
+    from paper_1608_04658_gb300 import binding
+    lat = lbm.Lattice((24, 20, 18), 0.02, storage="fp32")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Refinement(lat, (0, 4, 3), (16, 13, 12))  # touches the face
+    assert e.value.status == binding.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        lbm.Refinement(lat, (5, 4, 3), (7, 13, 12))   # two cells
+    # a fine lattice of the wrong viscosity or size, through the C ABI
+    import ctypes as C
+    L = lbm.lib()
+    r = C.c_void_p()
+    lo, hi = (C.c_int32 * 3)(5, 4, 3), (C.c_int32 * 3)(16, 13, 12)
+    wrong_nu = lbm.Lattice((24, 20, 20), 0.02, storage="fp32")
+    assert L.lbm_refine_create(lat._ctx, wrong_nu._ctx, lo, hi, C.byref(r)) == binding.LBM_ERR_ARG
+    wrong_shape = lbm.Lattice((24, 20, 22), 0.04, storage="fp32")
+    assert L.lbm_refine_create(lat._ctx, wrong_shape._ctx, lo, hi, C.byref(r)) == binding.LBM_ERR_ARG
+    wrong_storage = lbm.Lattice((24, 20, 20), 0.04, storage="fp16")
+    assert L.lbm_refine_create(lat._ctx, wrong_storage._ctx, lo, hi, C.byref(r)) == binding.LBM_ERR_ARG
+    assert not r.value
+    ref = lbm.Refinement(lat, (5, 4, 3), (16, 13, 12))
+    with pytest.raises(lbm.LbmError) as e:
+        ref.step(1)  # before init
+    assert e.value.status == binding.LBM_ERR_STATE
