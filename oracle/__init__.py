@@ -136,7 +136,7 @@ def lib():
             L.orc_mesh_link.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _D]
             L.orc_mesh_link.restype = C.c_double
             L.orc_mesh_mass.argtypes = [C.c_void_p, C.c_double, _D]
-            L.orc_refine_create.argtypes = [C.c_void_p, _I, _I]
+            L.orc_refine_create.argtypes = [C.c_void_p, _I, _I, C.c_void_p]
             L.orc_refine_create.restype = C.c_void_p
             L.orc_refine_fine.argtypes = [C.c_void_p]
             L.orc_refine_fine.restype = C.c_void_p
@@ -441,19 +441,25 @@ class RefinedOracle:
     ``Oracle``-like view of the fine level, (2m + 2) nodes per axis with m =
     hi - lo: fine node j sits at coarse coordinate lo + j/2.
 
+    ``fine_body``: a body of the fine level in fine lattice units (sphere,
+    airfoil or mesh; its solid nodes must stay four nodes inside the block's
+    surface, which ``step`` checks).
+
     Use: initialise ``coarse`` and ``fine`` (``init_state`` / ``set_f``), call
     ``init()``, then ``step(n)`` (n coarse steps, 2n fine steps)."""
 
-    def __init__(self, coarse: Oracle, lo, hi):
+    def __init__(self, coarse: Oracle, lo, hi, fine_body: Body | None = None):
         self.coarse = coarse
         self.lo = tuple(int(v) for v in lo)
         self.hi = tuple(int(v) for v in hi)
         lo_a = (C.c_int * 3)(*self.lo)
         hi_a = (C.c_int * 3)(*self.hi)
-        self._r = lib().orc_refine_create(coarse._ctx, lo_a, hi_a)
+        self._keep = getattr(fine_body, "_arrays", None)
+        bp = C.byref(fine_body) if fine_body is not None else None
+        self._r = lib().orc_refine_create(coarse._ctx, lo_a, hi_a, bp)
         if not self._r:
-            raise ValueError("bad refinement block (needs 1 <= lo, hi <= n - 2, hi - lo >= 3 and "
-                             "fluid coarse nodes from lo - 1 to hi + 1)")
+            raise ValueError("bad refinement block (needs 1 <= lo, hi <= n - 2, hi - lo >= 3, "
+                             "fluid coarse nodes from lo - 1 to hi + 1, no planes body on the fine level)")
         m = [h - l for l, h in zip(self.lo, self.hi)]
         fine = Oracle.__new__(Oracle)
         fine._ctx = lib().orc_refine_fine(self._r)
@@ -474,6 +480,8 @@ class RefinedOracle:
     def step(self, n: int = 1):
         if lib().orc_refine_step(self._r, int(n)) != 0:
             raise MemoryError("oracle step allocation failed")
+        if self.fine.counters()["error"] == 2:
+            raise ValueError("the fine body came within four nodes of the block's surface")
 
     def coarse_valid(self) -> np.ndarray:
         """(nz, ny, nx) bool: coarse nodes the refined step defines (all but

@@ -1252,7 +1252,11 @@ void orc_totals(const orc_ctx *c, double *out)
  *    to coarse (tau = 1/(2b) in each level's units; Pi^neq ~ tau dt grad u);
  *  - the coarse moments at t = 0 are those of the initial coarse state.
  * The coarse level may carry a body outside the block (its nodes from lo - 1
- * to hi + 1 must be fluid and no boundary node); the fine level carries none. */
+ * to hi + 1 must be fluid and no boundary node).  The fine level may carry a
+ * body of its own (sphere, airfoil or mesh, in fine lattice units: the fine
+ * level steps it like any lattice, two steps per coarse step); its solid
+ * nodes must stay at least four nodes inside the block's surface (j in
+ * [4, 2m - 4]), else the step sets the fine level's error counter. */
 typedef struct {
     orc_ctx *c, *f;
     int lo[3], hi[3], m[3];
@@ -1340,7 +1344,7 @@ static void refine_fill_ghosts(orc_refine *r, double *fs, double w)
 
 /* Creates the fine level of the block [lo, hi] (coarse node coordinates,
  * both ends included) over coarse level c.  Returns NULL on a bad block. */
-orc_refine *orc_refine_create(orc_ctx *c, const int *lo, const int *hi)
+orc_refine *orc_refine_create(orc_ctx *c, const int *lo, const int *hi, const orc_body *fine_body)
 {
     int n[3] = {c->p.nx, c->p.ny, c->p.nz};
     for (int a = 0; a < 3; ++a)
@@ -1365,7 +1369,8 @@ orc_refine *orc_refine_create(orc_ctx *c, const int *lo, const int *hi)
     pf.beta = c->p.beta / (2.0 - c->p.beta);
     orc_body none;
     memset(&none, 0, sizeof(none));
-    r->f = orc_create(&pf, &none);
+    if (fine_body && fine_body->kind == BODY_PLANES) { free(r); return NULL; }
+    r->f = orc_create(&pf, fine_body ? fine_body : &none);
     if (!r->f) return NULL;
     long nb = (long)(r->m[0] + 1) * (r->m[1] + 1) * (r->m[2] + 1);
     r->Mold = (double *)calloc((size_t)nb * NMOM, sizeof(double));
@@ -1404,24 +1409,32 @@ void orc_refine_init(orc_refine *r)
     refine_fill_ghosts(r, r->f->fa, 0.0);
 }
 
-/* One fine step over the nodes off the block's surface and pad (fa -> fb). */
+/* One fine step over the nodes off the block's surface and pad (fa -> fb),
+ * with the fine body's geometry, refill, Grad boundary and force as a step
+ * of the fine lattice alone takes them. */
 static void refine_fine_interior(orc_refine *r)
 {
     orc_ctx *f = r->f;
-    double out[Q], F[3], M[3];
+    double out[Q], F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
+    step_prepare(f);
     for (int jz = 0; jz < f->p.nz; ++jz)
         for (int jy = 0; jy < f->p.ny; ++jy)
             for (int jx = 0; jx < f->p.nx; ++jx) {
                 long n = nid(f, jx, jy, jz);
                 int inner = jx >= 1 && jx < 2 * r->m[0] && jy >= 1 && jy < 2 * r->m[1] &&
                             jz >= 1 && jz < 2 * r->m[2];
-                if (!inner) {
+                int clear = jx >= 4 && jx <= 2 * r->m[0] - 4 && jy >= 4 && jy <= 2 * r->m[1] - 4 &&
+                            jz >= 4 && jz <= 2 * r->m[2] - 4;
+                if (f->solid1[n] && !clear) f->error = 2;
+                if (!inner || f->solid1[n]) {
                     for (int i = 0; i < Q; ++i) f->fb[i * f->N + n] = f->fa[i * f->N + n];
                     continue;
                 }
                 node_update(f, jx, jy, jz, out, F, M);
                 for (int i = 0; i < Q; ++i) f->fb[i * f->N + n] = out[i];
             }
+    uint8_t *u = f->solid0; f->solid0 = f->solid1; f->solid1 = u;
+    for (int a = 0; a < 3; ++a) { f->b.F[a] = F[a]; f->b.M[a] = M[a]; }
 }
 
 /* Coarse step t -> t+1 and two fine steps, as the readings above state. */
