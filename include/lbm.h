@@ -455,7 +455,7 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
 /* ---------------------------------------------------- two-level block refinement
  * Sec. 4.2 runs the airfoil on a grid with two levels of resolution and cites
  * the refinement algorithm without stating it.  This is one fine block of
- * ratio 2 inside a bodiless coarse lattice (both levels bodiless):
+ * ratio 2 inside a bodiless coarse lattice; the fine level may carry a body:
  *   - fine node j (per axis) sits at coarse coordinate lo + j/2, j = 0 .. 2m,
  *     m = hi - lo; the fine context's lattice has 2m + 2 nodes per axis and
  *     periodic faces (no interior pull reaches them; the last layer is a pad
@@ -476,18 +476,32 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  *     coincident fine node, with the factor 2 b_f / b_c.
  *
  * lbm_refine_create couples coarse and fine (both from lbm_create, the same
- * storage, stabilizer, rho0 and stream, no body, no slab) over the block of
+ * storage, stabilizer, rho0 and stream, no slab) over the block of
  * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2,
  * hi - lo >= 3).  It writes the fine context's flags (the block's surface
  * and the pad marked solid), allocates its own device scratch (two sets of
  * 10 moments per node of the (m+1)^3 coarse box) with cudaMalloc and
- * synchronises the stream.  Errors: LBM_ERR_ARG for a mismatch, with the
+ * synchronises the stream.  The coarse context must carry no body; the fine
+ * one may (below).  Errors: LBM_ERR_ARG for a mismatch, with the
  * reason in lbm_last_error(coarse); LBM_ERR_OOM.  *out is NULL on failure.
  *
+ * A body on the fine level (lbm_set_geometry on the fine context, before
+ * lbm_refine_init): a sphere or a swimmer mesh in fine lattice units (fine
+ * node j at fine coordinate j), stepped by the fine level like a lattice of
+ * its own, two steps per coarse step (its geometry, refill, Grad boundary,
+ * force and Euler update each fine step; lbm_body_forces on the fine context
+ * reads it in fine units).  Its solid nodes must stay four nodes inside the
+ * block's surface (fine coordinates in [4, 2m - 4]) so that its band never
+ * reaches the surface; a band that does clears a surface mark, which the
+ * surface fill reports as LBM_ERR_STATE from lbm_body_forces on the fine
+ * context.  Walls and the airfoil (which spans the fine lattice's z extent)
+ * are LBM_ERR_UNSUPPORTED at lbm_refine_init.
+ *
  * lbm_refine_init, once both levels hold their initial state (lbm_init_state
- * or lbm_set_populations): the coarse moments at t = 0 are taken from the
- * coarse populations themselves and the fine surface is set from them.
- * LBM_ERR_STATE if a level has no state.
+ * or lbm_set_populations): re-marks the fine surface (lbm_set_geometry clears
+ * the marks), takes the coarse moments at t = 0 from the coarse populations
+ * themselves and sets the fine surface from them.  LBM_ERR_STATE if a level
+ * has no state.
  *
  * lbm_refine_step advances nsteps coarse steps (2 nsteps fine steps),
  * asynchronously on the shared stream; afterwards read each level with

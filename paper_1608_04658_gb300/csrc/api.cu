@@ -568,6 +568,27 @@ static cudaError_t sequential_step(lbm_ctx *ctx, void *fa, void *fb, int &cur, i
     return cudaSuccess;
 }
 
+}  // extern "C"
+
+cudaError_t ctx_step_flagged(lbm_ctx *ctx, int *launches)
+{
+    void *fa = ctx->f[ctx->cur], *fb = ctx->f[ctx->cur ^ 1];
+    int *status = &ctx->S.body[ctx->bcur].status;
+    int cur = ctx->bcur;
+    cudaError_t e;
+    if (ctx->has_body && ctx->slot_pending[ctx->bcur ^ 1]) {
+        if ((e = cudaStreamWaitEvent(ctx->stream, ctx->ev_slot[ctx->bcur ^ 1], 0)) != cudaSuccess) return e;
+        ctx->slot_pending[ctx->bcur ^ 1] = false;
+    }
+    ctx->last_split = false;
+    if ((e = sequential_step(ctx, fa, fb, cur, status, launches)) != cudaSuccess) return e;
+    ctx->bcur = cur;
+    ctx->cur ^= 1;
+    return cudaSuccess;
+}
+
+extern "C" {
+
 // Chooses the launch order once the trial steps have run: the order whose
 // two timed steps took less (the first pair of trial steps only warms up).
 static void choose_order(lbm_ctx *ctx)

@@ -64,6 +64,13 @@ struct lbm_ctx {
 // on the context stream while a profile (lbm_profile_begin) is open
 cudaError_t ctx_prof_mark(lbm_ctx *ctx, int which);
 
+// One step t -> t+1 of ctx in the sequential launch order (the body's
+// geometry and refill, then its boundary nodes and force beside one
+// flag-aware bulk launch), with the bookkeeping of lbm_step: the context's
+// current state buffer and body slot advance.  Adds its launches to
+// *launches.  Used by the refined step for a fine level that carries a body.
+cudaError_t ctx_step_flagged(lbm_ctx *ctx, int *launches);
+
 // waits on the host for the asynchronous force-record copies that may still
 // read the body slots (before a call that rewrites the slots)
 inline cudaError_t drain_records(lbm_ctx *ctx)

@@ -22,11 +22,12 @@
 //     ratio of relaxation time x time step of the levels: b_c / (2 b_f)
 //     coarse to fine, 2 b_f / b_c fine to coarse.
 //
-// Per coarse step (one stream): coarse surface moments at t+1 (pulled from
-// the coarse state at t), the coarse bulk launch off the block's inside, two
-// fine bulk launches each followed by the surface fill (at t + 1/2 from the
-// mean of the moments at t and t+1, at t+1 from those at t+1), then the
-// coarse layer inside the surface from the fine state at t + 1/2's pulls.
+// Per coarse step: coarse surface moments at t+1 (pulled from the coarse
+// state at t), the coarse bulk launch off the block's inside, two fine bulk
+// launches, the surface fills (at t + 1/2 from the mean of the moments at t
+// and t+1, at t+1 from those at t+1) and the coarse layer inside the surface
+// from the fine state at t + 1/2's pulls; the fine launches on the shared
+// stream, the rest beside them on a second stream.
 // Moments are kept in the collision's arithmetic (double for FP64 storage,
 // float otherwise) as rho - rho0, u, Pi^neq, one array per quantity.
 #include <cmath>
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Latti
                                                                      const typename Codec<S>::R *__restrict__ Mnew,
                                                                      typename Codec<S>::R w,
                                                                      typename Codec<S>::R s_cf,
-                                                                     int *__restrict__ status)
+                                                                     const uint8_t *__restrict__ flags,
+                                                                     int *__restrict__ st0, int *__restrict__ st1)
 {
     using R = typename Codec<S>::R;
     const int F0 = 2 * B.m[0] + 1, F1 = 2 * B.m[1] + 1, F2 = 2 * B.m[2] + 1;
@@ -212,8 +214,14 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Latti
             }
     R g[Q];
     rebuild<R>(M, s_cf, (R)Lf.rho0, g);
-    if (!kbc_collide<R, EXACT>(g, (R)Lf.beta, (R)Lf.inv_beta, (R)Lf.rho0, Lf.gamma_mode)) atomicOr(status, ST_UNSTABLE);
     const int n = j[0] + Lf.nx * (j[1] + Lf.ny * j[2]);
+    // a fine body whose band reached the surface has cleared its mark there
+    const int bad = (kbc_collide<R, EXACT>(g, (R)Lf.beta, (R)Lf.inv_beta, (R)Lf.rho0, Lf.gamma_mode) ? 0 : ST_UNSTABLE) |
+                    ((flags[n] & FL_SOLID) ? 0 : ST_BAND_OVERFLOW);
+    if (bad) {
+        atomicOr(st0, bad);
+        atomicOr(st1, bad);
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) Codec<S>::store(ff + Lf.plane[i] + n, g[i]);
 }
@@ -249,15 +257,16 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_restrict_kernel(const L
     for (int i = 0; i < Q; ++i) Codec<S>::store(fc + Lc.plane[i] + n, g[i]);
 }
 
-// fine-level marks: the block's surface and the pad are solid to the bulk
-// launch (it neither updates them nor reads their flags' neighbours' pulls)
+// fine-level marks: the block's surface and the pad are marked solid, so
+// the fine bulk launch does not update them (the marks of a fine body,
+// inside the block, are left as they are)
 __global__ void refine_flags_kernel(uint8_t *flags, int nx, int ny, int nz, int e0, int e1, int e2)
 {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (long long)nx * ny * nz) return;
     const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
     const bool inner = x >= 1 && x < e0 && y >= 1 && y < e1 && z >= 1 && z < e2;
-    flags[n] = inner ? 0 : FL_SOLID;
+    if (!inner) flags[n] |= FL_SOLID;
 }
 
 static unsigned blocks_for(long long n) { return (unsigned)((n + REFINE_THREADS - 1) / REFINE_THREADS); }
@@ -279,9 +288,13 @@ struct lbm_refine {
     void *M[2] = {nullptr, nullptr};  // moments at t (slot mcur) and t+1
     int mcur = 0;
     int *sweep = nullptr;             // device {lo + 1 (3), m - 1 (3)}: the coarse launch skips it
+    // fork of the side stream (the coarse context's, unused without a body),
+    // fine launch 1 done, first fill done, side work of the step done
+    cudaEvent_t ev_fork = nullptr, ev_fine1 = nullptr, ev_fill = nullptr, ev_side = nullptr;
     bool ready = false;
     double s_cf = 0, s_fc = 0;
     int64_t launches = 0;
+    int body_launches = 0;  // launches of a fine body's chain in the current lbm_refine_step
 };
 
 namespace {
@@ -300,13 +313,23 @@ lbm_status rfail(lbm_ctx *c, lbm_status st, const std::string &msg)
 
 void release(lbm_refine *r)
 {
+    for (cudaEvent_t e : {r->ev_fork, r->ev_fine1, r->ev_fill, r->ev_side})
+        if (e) cudaEventDestroy(e);
     cudaFree(r->M[0]);
     cudaFree(r->M[1]);
     cudaFree(r->sweep);
     delete r;
 }
 
-cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pull)
+cudaError_t launch_marks(const lbm_refine *r)
+{
+    const Lattice &Lf = r->f->L;
+    refine_flags_kernel<<<blocks_for(Lf.N), REFINE_THREADS, 0, r->f->stream>>>(
+        r->f->flags, Lf.nx, Lf.ny, Lf.nz, 2 * r->B.m[0], 2 * r->B.m[1], 2 * r->B.m[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pull, cudaStream_t st)
 {
     const long long n = surface_count(r->B.m[0] + 1, r->B.m[1] + 1, r->B.m[2] + 1);
     const lbm_ctx *c = r->c;
@@ -314,28 +337,29 @@ cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pul
         using S = std::remove_pointer_t<decltype(tag)>;
         using R = typename Codec<S>::R;
         if (pull)
-            refine_moments_kernel<S, true><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(c->L, (const S *)f, r->B, (R *)M);
+            refine_moments_kernel<S, true><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M);
         else
-            refine_moments_kernel<S, false><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(c->L, (const S *)f, r->B, (R *)M);
+            refine_moments_kernel<S, false><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const void *Mnew, double w)
+cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const void *Mnew, double w, cudaStream_t st)
 {
     const long long n = surface_count(2 * r->B.m[0] + 1, 2 * r->B.m[1] + 1, 2 * r->B.m[2] + 1);
     const lbm_ctx *f = r->f;
-    int *status = &f->S.body[f->bcur].status;
+    // both body slots: the step that reads the flag may be either
+    int *st0 = &f->S.body[0].status, *st1 = &f->S.body[1].status;
     return dispatch_exact(f->storage, f->L.gamma_mode == LBM_GAMMA_EXACT, [&](auto tag, auto ex) {
         using S = std::remove_pointer_t<decltype(tag)>;
         using R = typename Codec<S>::R;
-        refine_fill_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, f->stream>>>(
-            f->L, (S *)ff, r->B, (const R *)Mold, (const R *)Mnew, (R)w, (R)r->s_cf, status);
+        refine_fill_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, st>>>(
+            f->L, (S *)ff, r->B, (const R *)Mold, (const R *)Mnew, (R)w, (R)r->s_cf, f->flags, st0, st1);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_restrict(const lbm_refine *r, void *fc, const void *ff)
+cudaError_t launch_restrict(const lbm_refine *r, void *fc, const void *ff, cudaStream_t st)
 {
     const long long n = surface_count(r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1);
     const lbm_ctx *c = r->c;
@@ -343,10 +367,29 @@ cudaError_t launch_restrict(const lbm_refine *r, void *fc, const void *ff)
     return dispatch_exact(c->storage, c->L.gamma_mode == LBM_GAMMA_EXACT, [&](auto tag, auto ex) {
         using S = std::remove_pointer_t<decltype(tag)>;
         using R = typename Codec<S>::R;
-        refine_restrict_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, c->stream>>>(
+        refine_restrict_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, st>>>(
             c->L, (S *)fc, r->f->L, (const S *)ff, r->B, (R)r->s_fc, status);
         return cudaGetLastError();
     });
+}
+
+// One fine step from fa to fb over the block's interior on the shared
+// stream: one flag-aware bulk launch, or with a fine body the fine
+// context's own step in the sequential order (geometry, refill, boundary
+// and force beside the flag-aware bulk launch), whose buffers then advance.
+cudaError_t fine_step(lbm_refine *r, void *fa, void *fb, int *status, cudaStream_t main)
+{
+    lbm_ctx *f = r->f;
+    if (f->has_body) {
+        int n = 0;
+        const cudaError_t e = ctx_step_flagged(f, &n);
+        r->body_launches += n - 1;  // the bulk launch is one of the seven counted per step
+        return e;
+    }
+    cudaError_t e = ctx_prof_mark(f, 0);
+    if (e == cudaSuccess) e = launch_bulk(f->storage, f->L, fa, fb, f->flags, status, main);
+    if (e == cudaSuccess) e = ctx_prof_mark(f, 1);
+    return e;
 }
 
 }  // namespace
@@ -378,8 +421,8 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     const double bf = Lc.beta / (2.0 - Lc.beta);
     if (!(std::fabs(Lf.beta - bf) <= 1e-12 * bf))
         return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine viscosity must be twice the coarse one");
-    if (coarse->has_body || fine->has_body || coarse->slab_zper || fine->slab_zper || !fine->flags)
-        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: both levels must be bodiless, unsplit contexts");
+    if (coarse->has_body || coarse->slab_zper || fine->slab_zper || !fine->flags)
+        return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: a bodiless coarse level and unsplit contexts");
 
     lbm_refine *r = new (std::nothrow) lbm_refine;
     if (!r) return LBM_ERR_OOM;
@@ -394,19 +437,18 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     const size_t rsz = coarse->storage == LBM_FP64 ? sizeof(double) : sizeof(float);
     const size_t nbox = (size_t)(r->B.m[0] + 1) * (r->B.m[1] + 1) * (r->B.m[2] + 1);
     if (cudaMalloc(&r->M[0], NMOM * nbox * rsz) != cudaSuccess || cudaMalloc(&r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
-        cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_fine1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_fill, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_side, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         release(r);
         return rfail(coarse, LBM_ERR_OOM, "lbm_refine_create: device allocation failed");
     }
     const int sw[6] = {lo[0] + 1, lo[1] + 1, lo[2] + 1, r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1};
     cudaError_t e = cudaMemcpyAsync(r->sweep, sw, sizeof(sw), cudaMemcpyHostToDevice, coarse->stream);
-    if (e == cudaSuccess) {
-        const long long N = Lf.N;
-        refine_flags_kernel<<<blocks_for(N), REFINE_THREADS, 0, fine->stream>>>(
-            fine->flags, Lf.nx, Lf.ny, Lf.nz, 2 * r->B.m[0], 2 * r->B.m[1], 2 * r->B.m[2]);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = launch_marks(r);
     if (e == cudaSuccess) e = cudaStreamSynchronize(coarse->stream);
     if (e != cudaSuccess) {
         release(r);
@@ -419,7 +461,7 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
 void lbm_refine_destroy(lbm_refine *r)
 {
     if (!r) return;
-    if (r->c && r->c->stream) cudaStreamSynchronize(r->c->stream);
+    cudaStreamSynchronize(r->c->stream);  // the side stream's work is ordered before the step's end
     release(r);
 }
 
@@ -428,8 +470,15 @@ lbm_status lbm_refine_init(lbm_refine *r)
     if (!r) return LBM_ERR_ARG;
     if (!r->c->initialised || !r->f->initialised)
         return rfail(r->c, LBM_ERR_STATE, "lbm_refine_init: both levels must hold their initial state");
-    RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], false), "refine moments");
-    RF_CUDA(launch_fill(r, r->f->f[r->f->cur], r->M[r->mcur], r->M[r->mcur], 0.0), "refine fill");
+    if (r->c->has_body) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_init: the coarse level carries a body");
+    // walls mark the whole box and the airfoil spans the fine lattice's z
+    // extent: either would reach the block's surface
+    if (r->f->has_body && (r->f->G.kind == LBM_BODY_PLANES || r->f->G.kind == LBM_BODY_AIRFOIL))
+        return rfail(r->c, LBM_ERR_UNSUPPORTED, "lbm_refine_init: a fine body must be a sphere or a mesh");
+    // lbm_set_geometry on the fine level clears the surface marks
+    RF_CUDA(launch_marks(r), "refine marks");
+    RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], false, r->c->stream), "refine moments");
+    RF_CUDA(launch_fill(r, r->f->f[r->f->cur], r->M[r->mcur], r->M[r->mcur], 0.0, r->c->stream), "refine fill");
     r->ready = true;
     return LBM_OK;
 }
@@ -440,27 +489,42 @@ lbm_status lbm_refine_step(lbm_refine *r, int nsteps)
     if (nsteps < 0) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_step: nsteps < 0");
     if (!r->ready) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_step: lbm_refine_init has not run");
     lbm_ctx *c = r->c, *f = r->f;
+    // The fine launches run on the shared stream; the coupling kernels and
+    // the coarse launch on the side stream beside them.  They write disjoint
+    // nodes: the fine launches the block's interior, the fills its surface
+    // (flagged solid to the fine launch), the coarse launch the nodes off the
+    // block's inside, the restriction the layer inside the surface.  Orders
+    // kept by events: the first fill (fine state at t + 1/2) before the second
+    // fine launch reads it; the restriction (which pulls from the fine state
+    // at t + 1/2) and the second fill (fine state at t + 1, read by the first
+    // fine launch) after the first fine launch; the next step after all.
+    cudaStream_t main = c->stream, side = c->side;
     for (int s = 0; s < nsteps; ++s) {
         void *ca = c->f[c->cur], *cb = c->f[c->cur ^ 1];
         void *fa = f->f[f->cur], *fb = f->f[f->cur ^ 1];
         void *Mt = r->M[r->mcur], *Mn = r->M[r->mcur ^ 1];
-        int *cstat = &c->S.body[c->bcur].status, *fstat = &f->S.body[f->bcur].status;
-        RF_CUDA(launch_moments(r, ca, Mn, true), "refine moments");
-        RF_CUDA(launch_bulk(c->storage, c->L, ca, cb, nullptr, cstat, c->stream, BULK_OUTSIDE, r->sweep), "coarse bulk");
-        RF_CUDA(ctx_prof_mark(f, 0), "profile event");
-        RF_CUDA(launch_bulk(f->storage, f->L, fa, fb, f->flags, fstat, f->stream), "fine bulk");
-        RF_CUDA(ctx_prof_mark(f, 1), "profile event");
-        RF_CUDA(launch_fill(r, fb, Mt, Mn, 0.5), "refine fill");
-        RF_CUDA(ctx_prof_mark(f, 0), "profile event");
-        RF_CUDA(launch_bulk(f->storage, f->L, fb, fa, f->flags, fstat, f->stream), "fine bulk");
-        RF_CUDA(ctx_prof_mark(f, 1), "profile event");
-        RF_CUDA(launch_fill(r, fa, Mt, Mn, 1.0), "refine fill");
-        RF_CUDA(launch_restrict(r, cb, fb), "refine restrict");
+        int *cstat = &c->S.body[c->bcur].status, *fstat = &f->S.body[0].status;
+        RF_CUDA(cudaEventRecord(r->ev_fork, main), "fork");
+        RF_CUDA(cudaStreamWaitEvent(side, r->ev_fork, 0), "fork wait");
+        RF_CUDA(launch_moments(r, ca, Mn, true, side), "refine moments");
+        RF_CUDA(launch_fill(r, fb, Mt, Mn, 0.5, side), "refine fill");
+        RF_CUDA(cudaEventRecord(r->ev_fill, side), "fill event");
+        RF_CUDA(launch_bulk(c->storage, c->L, ca, cb, nullptr, cstat, side, BULK_OUTSIDE, r->sweep), "coarse bulk");
+        RF_CUDA(fine_step(r, fa, fb, fstat, main), "fine step");
+        RF_CUDA(cudaEventRecord(r->ev_fine1, main), "fine event");
+        RF_CUDA(cudaStreamWaitEvent(side, r->ev_fine1, 0), "fine wait");
+        RF_CUDA(launch_restrict(r, cb, fb, side), "refine restrict");
+        RF_CUDA(launch_fill(r, fa, Mt, Mn, 1.0, side), "refine fill");
+        RF_CUDA(cudaEventRecord(r->ev_side, side), "side event");
+        RF_CUDA(cudaStreamWaitEvent(main, r->ev_fill, 0), "fill wait");
+        RF_CUDA(fine_step(r, fb, fa, fstat, main), "fine step");
+        RF_CUDA(cudaStreamWaitEvent(main, r->ev_side, 0), "side wait");
         c->cur ^= 1;
         r->mcur ^= 1;
     }
-    r->launches = 7LL * nsteps;
-    c->launches = 7LL * nsteps;
+    r->launches = 7LL * nsteps + r->body_launches;
+    c->launches = r->launches;
+    r->body_launches = 0;
     return LBM_OK;
 }
 

@@ -140,3 +140,92 @@ def test_refinement_rejects_mismatched_levels():
     with pytest.raises(lbm.LbmError) as e:
         ref.step(1)  # before init
     assert e.value.status == binding.LBM_ERR_STATE
+
+
+def test_refined_block_bench_configuration_keeps_the_free_stream():
+    """The refined block workload the bench times (512 x 256 x 64 coarse box
+    with equilibrium inflow, outflow and far-field faces; fine block of
+    512 x 256 x 96), FP32, through lbm_refine_step: the uniform free stream
+    is a steady state, so every defined node of both levels keeps
+    f^eq(1, u_inf) to FP32 rounding over 4 coarse steps."""
+    import paper_1608_04658_gb300 as lbm
+    wl = synth.refined_block()
+    U = wl["u_face"]
+    lat = lbm.Lattice(wl["shape"], wl["nu"], storage="fp32", faces=wl["faces"], u_face=U)
+    ref = lbm.Refinement(lat, wl["lo"], wl["hi"])
+    assert ref.fine.shape == wl["fine_shape"]
+    lat.init_state(*synth.uniform_fields(wl["shape"], U))
+    ref.fine.init_state(*synth.uniform_fields(wl["fine_shape"], U))
+    ref.init()
+    ref.step(4)
+    fe = oracle.feq(1.0, U)
+    (x0, y0, z0), (x1, y1, z1) = wl["lo"], wl["hi"]
+    fc = lat.populations()
+    vc = np.ones(fc.shape[1:], dtype=bool)
+    vc[z0 + 2:z1 - 1, y0 + 2:y1 - 1, x0 + 2:x1 - 1] = False
+    for i in range(27):
+        assert np.abs(fc[i][vc] / fe[i] - 1.0).max() < 1e-6, i
+    del fc
+    ff = ref.fine.populations()
+    for i in range(27):
+        assert np.abs(ff[i, :-1, :-1, :-1] / fe[i] - 1.0).max() < 1e-6, i
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_refined_block_with_a_free_sphere(storage):
+    """A free sphere (fine units: centre (11.3, 9.4, 9.6), radius 2.6,
+    density ratio 2, launched at (0.02, 0.005, 0)) on the fine level of a
+    block over [6, 17] x [5, 14]^2 of a 24 x 20 x 20 periodic box, rough
+    random states, 6 coarse steps (12 steps of the sphere): populations on
+    both levels, the sphere's solid marks, force and velocity against the
+    oracle."""
+    import paper_1608_04658_gb300 as lbm
+    shape, lo, hi, nu = (24, 20, 20), (6, 5, 5), (17, 14, 14), 0.02
+    Xf, R, U = (11.3, 9.4, 9.6), 2.6, (0.02, 0.005, 0.0)
+    rho, u, xi, amp = random_fields(shape, 31)
+    lat = lbm.Lattice(shape, nu, storage=storage)
+    ref = lbm.Refinement(lat, lo, hi)
+    ref.fine.set_geometry(lbm.sphere(Xf, R, U=U, free=True, rho_ratio=2.0))
+    frho, fu, fxi, famp = random_fields(ref.fine.shape, 131)
+    lat.init_state(rho, 0.2 * u, xi, amp)
+    ref.fine.init_state(frho, 0.2 * fu, fxi, famp)
+    ref.init()
+    ref.step(6)
+    F, _ = ref.fine.forces()
+    body = ref.fine.body()
+
+    orc = oracle.Oracle(shape, nu=nu)
+    orc.init_state(rho, 0.2 * u, xi, amp)
+    ro = oracle.RefinedOracle(orc, lo, hi, fine_body=oracle.sphere_body(Xf, R, U=U, free=True, rho_ratio=2.0))
+    ro.fine.init_state(frho, 0.2 * fu, fxi, famp)
+    ro.init()
+    ro.step(6)
+    # the sphere's marks inside the block (the surface and pad carry the
+    # fine level's own solid marks)
+    inner = np.zeros(ro.fine_valid().shape, dtype=bool)
+    inner[1:-2, 1:-2, 1:-2] = True
+    solid = (ref.fine.flags.cpu().numpy() & 1).astype(bool) & inner
+    assert solid.sum() > 0
+    assert np.array_equal(solid, ro.fine.solid().astype(bool) & inner)
+    fluid = ro.fine_valid() & ~solid
+    assert rel_err(lat.populations(), orc.get_f(), ro.coarse_valid()) <= TOL[storage]
+    assert rel_err(ref.fine.populations(), ro.fine.get_f(), fluid) <= TOL[storage]
+    Fo, Uo = np.array(ro.fine.body.F), np.array(ro.fine.body.U)
+    fbar = {"fp64": 1e-10, "fp32": 1e-5, "fp16": 2e-2}[storage]
+    assert np.abs(np.array(F) - Fo).max() <= fbar * np.abs(Fo).max()
+    assert np.abs(np.array(body["U"]) - Uo).max() <= fbar * np.abs(Uo).max()
+
+
+def test_refinement_rejects_an_airfoil_on_the_fine_level():
+    import paper_1608_04658_gb300 as lbm
+    from paper_1608_04658_gb300 import binding
+    lat = lbm.Lattice((24, 20, 20), 0.02, storage="fp32")
+    ref = lbm.Refinement(lat, (6, 5, 5), (17, 14, 14))
+    wl = synth.plunging_airfoil()
+    ref.fine.set_geometry(lbm.airfoil((6.3, 9.1), 8.0, wl["ca"], wl["sa"], 0.0, 0.0, wl["camber_m"],
+                                      wl["camber_p"], wl["thick"]))
+    lat.init_state(*synth.uniform_fields((24, 20, 20)))
+    ref.fine.init_state(*synth.uniform_fields(ref.fine.shape))
+    with pytest.raises(lbm.LbmError) as e:
+        ref.init()
+    assert e.value.status == binding.LBM_ERR_UNSUPPORTED
