@@ -439,7 +439,9 @@ class RefinedOracle:
     two-level grid; the readings are stated in kbc_oracle.c).  ``lo``, ``hi``:
     the block's corner coarse nodes, both included.  ``fine`` is an
     ``Oracle``-like view of the fine level, (2m + 2) nodes per axis with m =
-    hi - lo: fine node j sits at coarse coordinate lo + j/2.
+    hi - lo: fine node j sits at coarse coordinate lo + j/2.  With lo = 0,
+    hi = n on a periodic axis the block spans that axis (2n fine nodes,
+    periodic, no surface along it).
 
     ``fine_body``: a body of the fine level in fine lattice units (sphere,
     airfoil or mesh; its solid nodes must stay four nodes inside the block's
@@ -460,11 +462,15 @@ class RefinedOracle:
         if not self._r:
             raise ValueError("bad refinement block (needs 1 <= lo, hi <= n - 2, hi - lo >= 3, "
                              "fluid coarse nodes from lo - 1 to hi + 1, no planes body on the fine level)")
-        m = [h - l for l, h in zip(self.lo, self.hi)]
+        n = coarse.shape
+        # a block with lo = 0, hi = n on a periodic axis spans that axis
+        self.full = tuple(l == 0 and h == nn and coarse.params.face[2 * a] == FACE_PERIODIC
+                          for a, (l, h, nn) in enumerate(zip(self.lo, self.hi, n)))
         fine = Oracle.__new__(Oracle)
         fine._ctx = lib().orc_refine_fine(self._r)
         fine._borrowed = True
-        fine.shape = tuple(2 * v + 2 for v in m)
+        fine.shape = tuple(2 * nn if f else 2 * (h - l) + 2
+                           for l, h, nn, f in zip(self.lo, self.hi, n, self.full))
         fine.N = fine.shape[0] * fine.shape[1] * fine.shape[2]
         self.fine = fine
 
@@ -488,13 +494,14 @@ class RefinedOracle:
         those more than one layer inside the block's surface)."""
         nx, ny, nz = self.coarse.shape
         v = np.ones((nz, ny, nx), dtype=bool)
-        (x0, y0, z0), (x1, y1, z1) = self.lo, self.hi
-        v[z0 + 2:z1 - 1, y0 + 2:y1 - 1, x0 + 2:x1 - 1] = False
+        sl = [slice(None) if f else slice(l + 2, h - 1) for l, h, f in zip(self.lo, self.hi, self.full)]
+        v[sl[2], sl[1], sl[0]] = False
         return v
 
     def fine_valid(self) -> np.ndarray:
         """(nz, ny, nx) bool of the fine level: every node but the pad."""
         nx, ny, nz = self.fine.shape
         v = np.zeros((nz, ny, nx), dtype=bool)
-        v[:nz - 1, :ny - 1, :nx - 1] = True
+        sl = [slice(None) if f else slice(0, nn - 1) for nn, f in zip(self.fine.shape, self.full)]
+        v[sl[2], sl[1], sl[0]] = True
         return v

@@ -1251,24 +1251,68 @@ void orc_totals(const orc_ctx *c, double *out)
  *    times times time steps: b_c / (2 b_f) coarse to fine, 2 b_f / b_c fine
  *    to coarse (tau = 1/(2b) in each level's units; Pi^neq ~ tau dt grad u);
  *  - the coarse moments at t = 0 are those of the initial coarse state.
+ * A block may also span a whole periodic axis of the coarse box (lo = 0,
+ * hi = n on that axis; the paper's airfoil is periodic along its span): along
+ * that axis it has no surface, the fine lattice holds 2n nodes with periodic
+ * wrap and no pad, and every coarse node along it belongs to the block.  At
+ * least one axis must be closed (1 <= lo, hi <= n - 2, hi - lo >= 3).
  * The coarse level may carry a body outside the block (its nodes from lo - 1
  * to hi + 1 must be fluid and no boundary node).  The fine level may carry a
  * body of its own (sphere, airfoil or mesh, in fine lattice units: the fine
- * level steps it like any lattice, two steps per coarse step); its solid
- * nodes must stay at least four nodes inside the block's surface (j in
- * [4, 2m - 4]), else the step sets the fine level's error counter. */
+ * level steps it like any lattice, two steps per coarse step); along closed
+ * axes its solid nodes must stay at least four nodes inside the block's
+ * surface (j in [4, 2m - 4]), else the step sets the fine level's error
+ * counter. */
 typedef struct {
     orc_ctx *c, *f;
     int lo[3], hi[3], m[3];
-    double *Mold, *Mnew;   /* 10 moments per coarse node of [lo, hi]^3 */
+    int full[3];           /* 1: the block spans this periodic axis */
+    int ext[3];            /* coarse box extent per axis: m + 1, or n if full */
+    double *Mold, *Mnew;   /* 10 moments per coarse node of the box */
     double s_cf, s_fc;     /* Pi^neq factors coarse -> fine, fine -> coarse */
 } orc_refine;
 
 enum { NMOM = 10 };  /* rho, u (3), Pi^neq xx yy zz xy xz yz */
 
-static long rbox(const orc_refine *r, int X, int Y, int Z)
+/* index of coarse node X in the block's box (X in the box) */
+static long rbox(const orc_refine *r, const int *X)
 {
-    return (X - r->lo[0]) + (long)(r->m[0] + 1) * ((Y - r->lo[1]) + (long)(r->m[1] + 1) * (Z - r->lo[2]));
+    int b[3];
+    for (int a = 0; a < 3; ++a) b[a] = X[a] - r->lo[a];
+    return b[0] + (long)r->ext[0] * (b[1] + (long)r->ext[1] * b[2]);
+}
+
+/* coarse node X lies in the block's box (both ends of closed axes included) */
+static int in_box(const orc_refine *r, const int *X)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!r->full[a] && (X[a] < r->lo[a] || X[a] > r->hi[a])) return 0;
+    return 1;
+}
+
+/* coarse node X lies strictly inside the block (closed axes strictly
+ * between lo and hi; any coordinate along a spanned axis) */
+static int in_inside(const orc_refine *r, const int *X)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!r->full[a] && (X[a] <= r->lo[a] || X[a] >= r->hi[a])) return 0;
+    return 1;
+}
+
+/* fine node j lies on the block's surface (some closed axis at 0 or 2m) */
+static int fine_on_surface(const orc_refine *r, const int *j)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!r->full[a] && (j[a] == 0 || j[a] == 2 * r->m[a])) return 1;
+    return 0;
+}
+
+/* fine node j is updated by the fine level (closed axes 1 <= j < 2m) */
+static int fine_inner(const orc_refine *r, const int *j)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!r->full[a] && (j[a] < 1 || j[a] >= 2 * r->m[a])) return 0;
+    return 1;
 }
 
 /* (rho, u, Pi^neq) of pre-collision populations F. */
@@ -1302,25 +1346,23 @@ static void refine_rebuild(const double *M, double s, double beta, int mode, dou
     orc_collide(f, beta, mode, out);
 }
 
-static int on_box_surface(const int *j, const int *n2)
-{
-    for (int a = 0; a < 3; ++a)
-        if (j[a] == 0 || j[a] == n2[a]) return 1;
-    return 0;
-}
-
 /* Fills the fine surface nodes of fine state fs from the coarse moments at
  * (1 - w) Mold + w Mnew. */
 static void refine_fill_ghosts(orc_refine *r, double *fs, double w)
 {
     orc_ctx *f = r->f;
-    int n2[3] = {2 * r->m[0], 2 * r->m[1], 2 * r->m[2]};
-    for (int jz = 0; jz <= n2[2]; ++jz)
-        for (int jy = 0; jy <= n2[1]; ++jy)
-            for (int jx = 0; jx <= n2[0]; ++jx) {
+    int n[3] = {r->c->p.nx, r->c->p.ny, r->c->p.nz};
+    for (int jz = 0; jz < f->p.nz; ++jz)
+        for (int jy = 0; jy < f->p.ny; ++jy)
+            for (int jx = 0; jx < f->p.nx; ++jx) {
                 int j[3] = {jx, jy, jz};
-                if (!on_box_surface(j, n2)) continue;
-                /* per axis: one coarse node (even j) or the two around it */
+                if (!fine_on_surface(r, j)) continue;
+                int pad = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (!r->full[a] && j[a] > 2 * r->m[a]) pad = 1;
+                if (pad) continue;
+                /* per axis: one coarse node (even j) or the two around it
+                 * (the second wrapping on a spanned axis) */
                 int X0[3], nk[3];
                 for (int a = 0; a < 3; ++a) {
                     X0[a] = r->lo[a] + j[a] / 2;
@@ -1331,48 +1373,66 @@ static void refine_fill_ghosts(orc_refine *r, double *fs, double w)
                     for (int dy = 0; dy < nk[1]; ++dy)
                         for (int dx = 0; dx < nk[0]; ++dx) {
                             double wt = 1.0 / (nk[0] * nk[1] * nk[2]);
-                            long b = rbox(r, X0[0] + dx, X0[1] + dy, X0[2] + dz);
+                            int X[3] = {X0[0] + dx, X0[1] + dy, X0[2] + dz};
+                            for (int a = 0; a < 3; ++a)
+                                if (r->full[a] && X[a] >= n[a]) X[a] -= n[a];
+                            long b = rbox(r, X);
                             for (int k = 0; k < NMOM; ++k)
                                 M[k] += wt * ((1.0 - w) * r->Mold[b * NMOM + k] + w * r->Mnew[b * NMOM + k]);
                         }
                 double out[Q];
                 refine_rebuild(M, r->s_cf, f->p.beta, f->p.gamma_mode, out);
-                long n = nid(f, jx, jy, jz);
-                for (int i = 0; i < Q; ++i) fs[i * f->N + n] = out[i];
+                long nn = nid(f, jx, jy, jz);
+                for (int i = 0; i < Q; ++i) fs[i * f->N + nn] = out[i];
             }
 }
 
 /* Creates the fine level of the block [lo, hi] (coarse node coordinates,
- * both ends included) over coarse level c.  Returns NULL on a bad block. */
+ * both ends included; lo = 0, hi = n on a periodic axis the block spans)
+ * over coarse level c.  Returns NULL on a bad block. */
 orc_refine *orc_refine_create(orc_ctx *c, const int *lo, const int *hi, const orc_body *fine_body)
 {
-    int n[3] = {c->p.nx, c->p.ny, c->p.nz};
-    for (int a = 0; a < 3; ++a)
+    int n[3] = {c->p.nx, c->p.ny, c->p.nz}, full[3], closed = 0;
+    for (int a = 0; a < 3; ++a) {
+        full[a] = lo[a] == 0 && hi[a] == n[a] && c->p.face[2 * a] == FACE_PERIODIC;
+        if (full[a]) continue;
+        closed++;
         if (lo[a] < 1 || hi[a] > n[a] - 2 || hi[a] - lo[a] < 3) return NULL;
-    for (int z = lo[2] - 1; z <= hi[2] + 1; ++z)
-        for (int y = lo[1] - 1; y <= hi[1] + 1; ++y)
-            for (int x = lo[0] - 1; x <= hi[0] + 1; ++x)
-                if (c->solid0[nid(c, x, y, z)]) return NULL;
+    }
+    if (!closed) return NULL;
+    if (fine_body && fine_body->kind == BODY_PLANES) return NULL;
     orc_refine *r = (orc_refine *)calloc(1, sizeof(orc_refine));
     if (!r) return NULL;
     r->c = c;
     orc_params pf = c->p;
+    int nf[3];
     for (int a = 0; a < 3; ++a) {
         r->lo[a] = lo[a];
         r->hi[a] = hi[a];
         r->m[a] = hi[a] - lo[a];
+        r->full[a] = full[a];
+        r->ext[a] = full[a] ? n[a] : r->m[a] + 1;
+        nf[a] = full[a] ? 2 * n[a] : 2 * r->m[a] + 2;
     }
-    pf.nx = 2 * r->m[0] + 2;
-    pf.ny = 2 * r->m[1] + 2;
-    pf.nz = 2 * r->m[2] + 2;
+    /* coarse nodes one layer around the block are fluid */
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x) {
+                int X[3] = {x, y, z}, near = 1;
+                for (int a = 0; a < 3; ++a)
+                    if (!full[a] && (X[a] < lo[a] - 1 || X[a] > hi[a] + 1)) near = 0;
+                if (near && c->solid0[nid(c, x, y, z)]) { free(r); return NULL; }
+            }
+    pf.nx = nf[0];
+    pf.ny = nf[1];
+    pf.nz = nf[2];
     for (int k = 0; k < 6; ++k) pf.face[k] = FACE_PERIODIC;
     pf.beta = c->p.beta / (2.0 - c->p.beta);
     orc_body none;
     memset(&none, 0, sizeof(none));
-    if (fine_body && fine_body->kind == BODY_PLANES) { free(r); return NULL; }
     r->f = orc_create(&pf, fine_body ? fine_body : &none);
     if (!r->f) return NULL;
-    long nb = (long)(r->m[0] + 1) * (r->m[1] + 1) * (r->m[2] + 1);
+    long nb = (long)r->ext[0] * r->ext[1] * r->ext[2];
     r->Mold = (double *)calloc((size_t)nb * NMOM, sizeof(double));
     r->Mnew = (double *)calloc((size_t)nb * NMOM, sizeof(double));
     r->f->fb = (double *)calloc((size_t)Q * r->f->N, sizeof(double));
@@ -1398,13 +1458,15 @@ void orc_refine_destroy(orc_refine *r)
 void orc_refine_init(orc_refine *r)
 {
     orc_ctx *c = r->c;
-    for (int Z = r->lo[2]; Z <= r->hi[2]; ++Z)
-        for (int Y = r->lo[1]; Y <= r->hi[1]; ++Y)
-            for (int X = r->lo[0]; X <= r->hi[0]; ++X) {
+    for (int z = 0; z < c->p.nz; ++z)
+        for (int y = 0; y < c->p.ny; ++y)
+            for (int x = 0; x < c->p.nx; ++x) {
+                int X[3] = {x, y, z};
+                if (!in_box(r, X) || in_inside(r, X)) continue;
                 double g[Q];
-                long n = nid(c, X, Y, Z);
+                long n = nid(c, x, y, z);
                 for (int i = 0; i < Q; ++i) g[i] = c->fa[i * c->N + n];
-                refine_moments(g, r->Mold + rbox(r, X, Y, Z) * NMOM);
+                refine_moments(g, r->Mold + rbox(r, X) * NMOM);
             }
     refine_fill_ghosts(r, r->f->fa, 0.0);
 }
@@ -1421,10 +1483,10 @@ static void refine_fine_interior(orc_refine *r)
         for (int jy = 0; jy < f->p.ny; ++jy)
             for (int jx = 0; jx < f->p.nx; ++jx) {
                 long n = nid(f, jx, jy, jz);
-                int inner = jx >= 1 && jx < 2 * r->m[0] && jy >= 1 && jy < 2 * r->m[1] &&
-                            jz >= 1 && jz < 2 * r->m[2];
-                int clear = jx >= 4 && jx <= 2 * r->m[0] - 4 && jy >= 4 && jy <= 2 * r->m[1] - 4 &&
-                            jz >= 4 && jz <= 2 * r->m[2] - 4;
+                int j[3] = {jx, jy, jz};
+                int inner = fine_inner(r, j), clear = 1;
+                for (int a = 0; a < 3; ++a)
+                    if (!r->full[a] && (j[a] < 4 || j[a] > 2 * r->m[a] - 4)) clear = 0;
                 if (f->solid1[n] && !clear) f->error = 2;
                 if (!inner || f->solid1[n]) {
                     for (int i = 0; i < Q; ++i) f->fb[i * f->N + n] = f->fa[i * f->N + n];
@@ -1448,16 +1510,15 @@ int orc_refine_step(orc_refine *r, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         step_prepare(c);
         /* coarse pre-collision moments at t+1 on the block's surface */
-        for (int Z = r->lo[2]; Z <= r->hi[2]; ++Z)
-            for (int Y = r->lo[1]; Y <= r->hi[1]; ++Y)
-                for (int X = r->lo[0]; X <= r->hi[0]; ++X) {
-                    int inner = X > r->lo[0] && X < r->hi[0] && Y > r->lo[1] && Y < r->hi[1] &&
-                                Z > r->lo[2] && Z < r->hi[2];
-                    if (inner) continue;
+        for (int z = 0; z < c->p.nz; ++z)
+            for (int y = 0; y < c->p.ny; ++y)
+                for (int x = 0; x < c->p.nx; ++x) {
+                    int X[3] = {x, y, z};
+                    if (!in_box(r, X) || in_inside(r, X)) continue;
                     double Fi[Q];
                     int missing[Q];
-                    gather_node(c, X, Y, Z, Fi, missing);
-                    refine_moments(Fi, r->Mnew + rbox(r, X, Y, Z) * NMOM);
+                    gather_node(c, x, y, z, Fi, missing);
+                    refine_moments(Fi, r->Mnew + rbox(r, X) * NMOM);
                 }
         /* coarse update off the block's inside */
         double F[3] = {0, 0, 0}, M[3] = {0, 0, 0}, out[Q];
@@ -1465,9 +1526,8 @@ int orc_refine_step(orc_refine *r, int nsteps)
             for (int y = 0; y < c->p.ny; ++y)
                 for (int x = 0; x < c->p.nx; ++x) {
                     long n = nid(c, x, y, z);
-                    int inner = x > r->lo[0] && x < r->hi[0] && y > r->lo[1] && y < r->hi[1] &&
-                                z > r->lo[2] && z < r->hi[2];
-                    if (inner || c->solid1[n]) {
+                    int X[3] = {x, y, z};
+                    if (in_inside(r, X) || c->solid1[n]) {
                         for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = c->fa[i * c->N + n];
                         continue;
                     }
@@ -1484,18 +1544,20 @@ int orc_refine_step(orc_refine *r, int nsteps)
         /* coarse nodes one layer inside the surface from the fine level: the
          * pre-collision moments at t+1 of the coincident fine node are its
          * pulls from the fine state at t + 1/2 (still in f->fa) */
-        for (int Z = r->lo[2] + 1; Z <= r->hi[2] - 1; ++Z)
-            for (int Y = r->lo[1] + 1; Y <= r->hi[1] - 1; ++Y)
-                for (int X = r->lo[0] + 1; X <= r->hi[0] - 1; ++X) {
-                    int shell = X == r->lo[0] + 1 || X == r->hi[0] - 1 || Y == r->lo[1] + 1 ||
-                                Y == r->hi[1] - 1 || Z == r->lo[2] + 1 || Z == r->hi[2] - 1;
+        for (int z = 0; z < c->p.nz; ++z)
+            for (int y = 0; y < c->p.ny; ++y)
+                for (int x = 0; x < c->p.nx; ++x) {
+                    int X[3] = {x, y, z}, shell = 0;
+                    if (!in_inside(r, X)) continue;
+                    for (int a = 0; a < 3; ++a)
+                        if (!r->full[a] && (X[a] == r->lo[a] + 1 || X[a] == r->hi[a] - 1)) shell = 1;
                     if (!shell) continue;
                     double Fi[Q], Mf[NMOM];
                     int missing[Q];
-                    gather_node(f, 2 * (X - r->lo[0]), 2 * (Y - r->lo[1]), 2 * (Z - r->lo[2]), Fi, missing);
+                    gather_node(f, 2 * (x - r->lo[0]), 2 * (y - r->lo[1]), 2 * (z - r->lo[2]), Fi, missing);
                     refine_moments(Fi, Mf);
                     refine_rebuild(Mf, r->s_fc, c->p.beta, c->p.gamma_mode, out);
-                    long n = nid(c, X, Y, Z);
+                    long n = nid(c, x, y, z);
                     for (int i = 0; i < Q; ++i) c->fb[i * c->N + n] = out[i];
                 }
         t = f->fa; f->fa = f->fb; f->fb = t;
