@@ -632,37 +632,57 @@ def accuracy_bench(args, device):
     return out
 
 
-def refine_bench(args, world, device, clocks, storages=("fp32", "fp16")):
+def refine_bench(args, world, device, clocks):
     """The two-level block refinement (lbm_refine_step; Sec. 4.2's two-level
-    grid) on the refined block workload: per coarse step the coarse launch
-    off the block's inside, two fine launches over the block's interior and
+    grid) on two workloads: the bodiless refined block (FP32 and FP16) and
+    the plunging airfoil on the fine level of a block spanning the periodic
+    span (FP32).  Per coarse step: the coarse launch off the block's inside,
+    two fine steps over the block's interior (with the airfoil's chain) and
     the surface/restriction kernels.  GLUPS counts every node update (coarse
     nodes updated + 2 x fine interior nodes per coarse step); the fine-grid
     equivalent counts the updates a uniform fine grid over the whole coarse
     box would make in the same simulated time (16 per coarse node and coarse
-    step).  The roofline is that of the fine bulk launch (CUDA events on the
-    shared stream around each of its launches)."""
+    step).  The roofline is that of the fine bulk launches (CUDA events on
+    the shared stream around each)."""
+    import synth
+    out = {}
+    for wl, storages in ((synth.refined_block(), ("fp32", "fp16")), (synth.refined_airfoil(), ("fp32",))):
+        out[wl["name"]] = refine_run(args, world, device, clocks, wl, storages)
+    return out
+
+
+def refine_run(args, world, device, clocks, wl, storages):
     import numpy as np
     import torch
 
     import paper_1608_04658_gb300 as lbm
     import synth
-    wl = synth.refined_block()
     (nx, ny, nz), lo, hi = wl["shape"], wl["lo"], wl["hi"]
-    m = [h - l for l, h in zip(lo, hi)]
-    coarse_updated = nx * ny * nz - (m[0] - 1) * (m[1] - 1) * (m[2] - 1)
-    fine_interior = (2 * m[0] - 1) * (2 * m[1] - 1) * (2 * m[2] - 1)
+    full = [l == 0 and h == n for l, h, n in zip(lo, hi, wl["shape"])]
+    inside = fine_interior = 1
+    for a in range(3):
+        m = hi[a] - lo[a]
+        inside *= wl["shape"][a] if full[a] else m - 1
+        fine_interior *= 2 * wl["shape"][a] if full[a] else 2 * m - 1
+    coarse_updated = nx * ny * nz - inside
     per_step = coarse_updated + 2 * fine_interior
     K, W = args.steps, args.warmup
     peak, peak_kind = measured_hbm_peak()
-    out = {"workload": wl["name"], "coarse_nodes_updated_per_step": coarse_updated,
-           "fine_interior_nodes": fine_interior, "node_updates_per_coarse_step": per_step,
-           "faces": list(wl["faces"]), "nu_coarse": wl["nu"], "steps": K, "warmup": W}
+    body = "airfoil" in wl["name"]
+    out = {"coarse_nodes_updated_per_step": coarse_updated, "fine_interior_nodes": fine_interior,
+           "node_updates_per_coarse_step": per_step, "faces": list(wl["faces"]), "nu_coarse": wl["nu"],
+           "spanned_axes": [a for a in range(3) if full[a]], "steps": K, "warmup": W}
     for st in storages:
         lat = lbm.Lattice(wl["shape"], wl["nu"], storage=st, faces=wl["faces"], u_face=wl["u_face"], device=device)
         ref = lbm.Refinement(lat, lo, hi)
-        lat.init_state(*synth.refined_fields(wl, "coarse"))
-        ref.fine.init_state(*synth.refined_fields(wl, "fine"))
+        if body:
+            ref.fine.set_geometry(lbm.airfoil(wl["le"], wl["chord"], wl["ca"], wl["sa"], wl["h_amp"], wl["h_omega"],
+                                              wl["camber_m"], wl["camber_p"], wl["thick"]))
+            lat.init_state(*synth.uniform_fields(wl["shape"], wl["u_face"]))
+            ref.fine.init_state(*synth.uniform_fields(wl["fine_shape"], wl["u_face"]))
+        else:
+            lat.init_state(*synth.refined_fields(wl, "coarse"))
+            ref.fine.init_state(*synth.refined_fields(wl, "fine"))
         ref.init()
         ref.step(W)
         torch.cuda.synchronize()
@@ -681,23 +701,30 @@ def refine_bench(args, world, device, clocks, storages=("fp32", "fp16")):
         clocks.mark(t0, t1)
         fine_ms, nfine = ref.fine.profile_end()
         ms = dist_max(start.elapsed_time(end), world)
-        tot = lat.totals()  # finite sums: the run stayed stable
+        tot = lat.totals()  # raises if a node went unstable
         if not np.all(np.isfinite(tot)):
             raise RuntimeError("refined run went unstable")
+        res = {}
+        if body:
+            F, _ = ref.fine.forces()  # raises if the band reached the block's surface
+            res["airfoil_force_fine_units"] = [float(v) for v in F]
         fine_ms /= max(nfine, 1)
         bytes_launch = fine_interior * BYTES_PER_NODE[st]
         achieved = bytes_launch / (fine_ms * 1e-3) / 1e9
-        out[st] = {"value": round(per_step * K * world / (ms * 1e-3) / 1e9, 4), "unit": "GLUPS",
-                   "dtype": DTYPE[st], "ms_per_step": round(ms / K, 5),
-                   "fine_grid_equivalent_glups": round(16 * nx * ny * nz * K * world / (ms * 1e-3) / 1e9, 4),
-                   "gpu_launches": lat.launches(),
-                   "roofline": {"bound": "hbm", "kernel": "bulk_pair_kernel (fine level)",
-                                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                                "traffic": ncu_traffic(st, wl["name"]),
-                                "algorithmic_bytes_per_launch": bytes_launch,
-                                "bulk_ms_per_launch": round(fine_ms, 5)},
-                   "fine_share_of_step": round(2 * fine_ms / (ms / K), 4)}
+        res.update({"value": round(per_step * K * world / (ms * 1e-3) / 1e9, 4), "unit": "GLUPS",
+                    "dtype": DTYPE[st], "ms_per_step": round(ms / K, 5),
+                    "fine_grid_equivalent_glups": round(16 * nx * ny * nz * K * world / (ms * 1e-3) / 1e9, 4),
+                    "gpu_launches": lat.launches(),
+                    "roofline": {"bound": "hbm", "kernel": "bulk_pair_kernel (fine level)",
+                                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                                 "traffic": ncu_traffic(st, wl["name"]),
+                                 "algorithmic_bytes_per_launch": bytes_launch,
+                                 "bulk_ms_per_launch": round(fine_ms, 5),
+                                 "note": "the coarse launch and the coupling kernels run beside the fine launches"},
+                    "step_algorithmic_gbs": round(per_step * BYTES_PER_NODE[st] / (ms / K) / 1e6, 1),
+                    "step_frac_of_peak": round(per_step * BYTES_PER_NODE[st] / (ms / K) / 1e6 / peak, 4)})
+        out[st] = res
         ref.close()
         ref.fine.close()
         lat.close()

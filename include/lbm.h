@@ -475,10 +475,16 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  *     collision of the same rebuild from the pre-collision moments of the
  *     coincident fine node, with the factor 2 b_f / b_c.
  *
+ * A block may span a whole periodic axis of the coarse box (lo = 0 and hi =
+ * n on that axis; the paper's airfoil is periodic along its span): it has no
+ * surface along that axis, the fine lattice holds 2n nodes there (periodic,
+ * no pad) and the surface interpolation wraps with the axis.  At least one
+ * axis must stay closed.
+ *
  * lbm_refine_create couples coarse and fine (both from lbm_create, the same
  * storage, stabilizer, rho0 and stream, no slab) over the block of
  * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2,
- * hi - lo >= 3).  It writes the fine context's flags (the block's surface
+ * hi - lo >= 3, unless spanned).  It writes the fine context's flags (the block's surface
  * and the pad marked solid), allocates its own device scratch (two sets of
  * 10 moments per node of the (m+1)^3 coarse box) with cudaMalloc and
  * synchronises the stream.  The coarse context must carry no body; the fine
@@ -490,12 +496,13 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * node j at fine coordinate j), stepped by the fine level like a lattice of
  * its own, two steps per coarse step (its geometry, refill, Grad boundary,
  * force and Euler update each fine step; lbm_body_forces on the fine context
- * reads it in fine units).  Its solid nodes must stay four nodes inside the
- * block's surface (fine coordinates in [4, 2m - 4]) so that its band never
- * reaches the surface; a band that does clears a surface mark, which the
- * surface fill reports as LBM_ERR_STATE from lbm_body_forces on the fine
- * context.  Walls and the airfoil (which spans the fine lattice's z extent)
- * are LBM_ERR_UNSUPPORTED at lbm_refine_init.
+ * reads it in fine units).  Along closed axes its solid nodes must stay four
+ * nodes inside the block's surface (fine coordinates in [4, 2m - 4]) so that
+ * its band never reaches the surface; a band that does clears a surface
+ * mark, which the surface fill reports as LBM_ERR_STATE from lbm_body_forces
+ * on the fine context.  Walls, and the airfoil (extruded over the fine
+ * lattice's z extent) in a block that does not span z, are
+ * LBM_ERR_UNSUPPORTED at lbm_refine_init.
  *
  * lbm_refine_init, once both levels hold their initial state (lbm_init_state
  * or lbm_set_populations): re-marks the fine surface (lbm_set_geometry clears

@@ -543,7 +543,7 @@ class Refinement:
     """Two-level block refinement (lbm_refine_*; Sec. 4.2's two-level grid).
 
     ``coarse`` is a bodiless Lattice; the block covers its nodes [lo, hi] per
-    axis (both ends included).  The fine Lattice (2 (hi - lo) + 2 nodes per
+    axis (both ends included; lo = 0, hi = n on a periodic axis spans it).  The fine Lattice (2 (hi - lo) + 2 nodes per
     axis, periodic faces, twice the coarse viscosity, same storage, stabilizer
     and stream) is created here as ``self.fine``: fine node j sits at coarse
     coordinate lo + j/2.  Initialise both levels, call ``init()``, then
@@ -553,8 +553,12 @@ class Refinement:
         self.coarse = coarse
         self.lo = tuple(int(v) for v in lo)
         self.hi = tuple(int(v) for v in hi)
-        shape = tuple(2 * (h - l) + 2 for l, h in zip(self.lo, self.hi))
         p = coarse.params
+        # lo = 0, hi = n on a periodic axis: the block spans it (2n fine nodes)
+        self.full = tuple(l == 0 and h == n and p.face[2 * a] == FACE_PERIODIC
+                          for a, (l, h, n) in enumerate(zip(self.lo, self.hi, coarse.shape)))
+        shape = tuple(2 * n if f else 2 * (h - l) + 2
+                      for l, h, n, f in zip(self.lo, self.hi, coarse.shape, self.full))
         self.fine = Lattice(shape, fine_nu(p.nu), coarse.storage, rho0=coarse.rho0, gamma_mode=p.gamma_mode,
                             device=coarse.device)
         r = C.c_void_p()

@@ -45,40 +45,55 @@ namespace lbm {
 constexpr int NMOM = 10;  // rho - rho0, u (3), Pi^neq xx yy zz xy xz yz
 constexpr int REFINE_THREADS = 128;
 
-// nodes on the surface of a box of A x B x C nodes (each >= 2)
-__host__ __device__ inline long long surface_count(int A, int B, int C)
+// A box of E[0] x E[1] x E[2] nodes whose surface lies along the closed
+// axes only (along an open axis the box wraps around and has no ends).
+struct SurfBox {
+    int E[3];
+    int closed[3];
+};
+
+// nodes of the box with some closed coordinate at 0 or E - 1
+__host__ __device__ inline long long surface_count(const SurfBox &S)
 {
-    return 2LL * A * B + 2LL * A * (C - 2) + 2LL * (B - 2) * (C - 2);
+    long long all = 1, in = 1;
+    for (int a = 0; a < 3; ++a) {
+        all *= S.E[a];
+        in *= S.closed[a] ? S.E[a] - 2 : S.E[a];
+    }
+    return all - in;
 }
 
-// k-th surface node of that box: the two z faces, then the two y faces
-// between them, then the two x faces between those
-__device__ inline void surface_node(long long k, int A, int B, int C, int &x, int &y, int &z)
+// k-th of those nodes: the two end slabs of the closed axes in the order z,
+// y, x, each slab without the nodes of the slabs before it (x fastest
+// within a slab)
+__device__ inline void surface_node(long long k, const SurfBox &S, int c[3])
 {
-    const long long ab = (long long)A * B;
-    if (k < 2 * ab) {
-        z = k < ab ? 0 : C - 1;
-        if (k >= ab) k -= ab;
-        x = (int)(k % A);
-        y = (int)(k / A);
-        return;
+    int done[3] = {0, 0, 0};
+    for (int t = 0; t < 3; ++t) {
+        const int a = 2 - t;
+        if (!S.closed[a]) continue;
+        long long r[3];
+        for (int b = 0; b < 3; ++b) r[b] = b == a ? 1 : (done[b] ? S.E[b] - 2 : S.E[b]);
+        const long long slab = r[0] * r[1] * r[2];
+        if (k < 2 * slab) {
+            const bool far = k >= slab;
+            if (far) k -= slab;
+            c[a] = far ? S.E[a] - 1 : 0;
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) continue;
+                c[b] = (int)(k % r[b]) + (done[b] ? 1 : 0);
+                k /= r[b];
+            }
+            return;
+        }
+        k -= 2 * slab;
+        done[a] = 1;
     }
-    k -= 2 * ab;
-    const long long ac = (long long)A * (C - 2);
-    if (k < 2 * ac) {
-        y = k < ac ? 0 : B - 1;
-        if (k >= ac) k -= ac;
-        x = (int)(k % A);
-        z = 1 + (int)(k / A);
-        return;
-    }
-    k -= 2 * ac;
-    const long long bc = (long long)(B - 2) * (C - 2);
-    x = k < bc ? 0 : A - 1;
-    if (k >= bc) k -= bc;
-    y = 1 + (int)(k % (B - 2));
-    z = 1 + (int)(k / (B - 2));
+    c[0] = c[1] = c[2] = 0;  // k beyond the count (not reached)
 }
+
+// v wrapped into [0, n) when it is at most one period off
+__device__ inline int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // (rho - rho0, u, Pi^neq) of the shifted pre-collision populations g
 template <typename R>
@@ -138,8 +153,39 @@ __device__ inline void rebuild(const R M[NMOM], R s, R rho0, R g[Q])
 }
 
 struct Box3 {
-    int lo[3];  // block corner in coarse nodes
-    int m[3];   // hi - lo per axis
+    int lo[3];    // block corner in coarse nodes (0 on a spanned axis)
+    int m[3];     // hi - lo per axis (n on a spanned axis)
+    int full[3];  // 1: the block spans this periodic axis of the coarse box
+    int n[3];     // coarse lattice size
+    // coarse box (moments), fine surface box and the coarse layer inside the
+    // surface, each with the spanned axes open
+    __host__ __device__ SurfBox coarse_box() const
+    {
+        SurfBox S;
+        for (int a = 0; a < 3; ++a) {
+            S.E[a] = full[a] ? n[a] : m[a] + 1;
+            S.closed[a] = !full[a];
+        }
+        return S;
+    }
+    __host__ __device__ SurfBox fine_box() const
+    {
+        SurfBox S;
+        for (int a = 0; a < 3; ++a) {
+            S.E[a] = full[a] ? 2 * n[a] : 2 * m[a] + 1;
+            S.closed[a] = !full[a];
+        }
+        return S;
+    }
+    __host__ __device__ SurfBox shell_box() const
+    {
+        SurfBox S;
+        for (int a = 0; a < 3; ++a) {
+            S.E[a] = full[a] ? n[a] : m[a] - 1;
+            S.closed[a] = !full[a];
+        }
+        return S;
+    }
 };
 
 // Coarse pre-collision moments on the block's surface: PULL, the pulls of the
@@ -152,22 +198,24 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_moments_kernel(const La
                                                                         typename Codec<S>::R *__restrict__ M)
 {
     using R = typename Codec<S>::R;
-    const int A0 = B.m[0] + 1, A1 = B.m[1] + 1, A2 = B.m[2] + 1;
+    const SurfBox SB = B.coarse_box();
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= surface_count(A0, A1, A2)) return;
-    int bx, by, bz;
-    surface_node(k, A0, A1, A2, bx, by, bz);
-    const int x = B.lo[0] + bx, y = B.lo[1] + by, z = B.lo[2] + bz;
+    if (k >= surface_count(SB)) return;
+    int bc[3];
+    surface_node(k, SB, bc);
+    const int x = B.lo[0] + bc[0], y = B.lo[1] + bc[1], z = B.lo[2] + bc[2];
     R g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int sx = PULL ? x - cx_of(i) : x, sy = PULL ? y - cy_of(i) : y, sz = PULL ? z - cz_of(i) : z;
+        // a closed axis keeps its sources inside the box; a spanned one wraps
+        const int sx = PULL ? wrap1(x - cx_of(i), L.nx) : x, sy = PULL ? wrap1(y - cy_of(i), L.ny) : y,
+                  sz = PULL ? wrap1(z - cz_of(i), L.nz) : z;
         g[i] = Codec<S>::load(f + L.plane[i] + (sx + L.nx * (sy + L.ny * sz)));
     }
     R Mn[NMOM];
     node_moments<R>(g, (R)L.rho0, Mn);
-    const long long nbox = (long long)A0 * A1 * A2;
-    const long long b = bx + (long long)A0 * (by + (long long)A1 * bz);
+    const long long nbox = (long long)SB.E[0] * SB.E[1] * SB.E[2];
+    const long long b = bc[0] + (long long)SB.E[0] * (bc[1] + (long long)SB.E[1] * bc[2]);
 #pragma unroll
     for (int q = 0; q < NMOM; ++q) M[q * nbox + b] = Mn[q];
 }
@@ -187,13 +235,13 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Latti
                                                                      int *__restrict__ st0, int *__restrict__ st1)
 {
     using R = typename Codec<S>::R;
-    const int F0 = 2 * B.m[0] + 1, F1 = 2 * B.m[1] + 1, F2 = 2 * B.m[2] + 1;
+    const SurfBox SF = B.fine_box(), SC = B.coarse_box();
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= surface_count(F0, F1, F2)) return;
+    if (k >= surface_count(SF)) return;
     int j[3];
-    surface_node(k, F0, F1, F2, j[0], j[1], j[2]);
-    const int A0 = B.m[0] + 1, A1 = B.m[1] + 1;
-    const long long nbox = (long long)A0 * A1 * (B.m[2] + 1);
+    surface_node(k, SF, j);
+    const int A0 = SC.E[0], A1 = SC.E[1];
+    const long long nbox = (long long)A0 * A1 * SC.E[2];
     int b0[3], nk[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -207,7 +255,11 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Latti
     for (int dz = 0; dz < nk[2]; ++dz)
         for (int dy = 0; dy < nk[1]; ++dy)
             for (int dx = 0; dx < nk[0]; ++dx) {
-                const long long b = (b0[0] + dx) + (long long)A0 * ((b0[1] + dy) + (long long)A1 * (b0[2] + dz));
+                // the node after the last of a spanned axis is its first
+                const int bx = B.full[0] ? wrap1(b0[0] + dx, B.n[0]) : b0[0] + dx;
+                const int by = B.full[1] ? wrap1(b0[1] + dy, B.n[1]) : b0[1] + dy;
+                const int bz = B.full[2] ? wrap1(b0[2] + dz, B.n[2]) : b0[2] + dz;
+                const long long b = bx + (long long)A0 * (by + (long long)A1 * bz);
 #pragma unroll
                 for (int q = 0; q < NMOM; ++q)
                     M[q] += wt * ((R(1) - w) * Mold[q * nbox + b] + w * Mnew[q * nbox + b]);
@@ -238,21 +290,27 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_restrict_kernel(const L
                                                                          int *__restrict__ status)
 {
     using R = typename Codec<S>::R;
-    const int A0 = B.m[0] - 1, A1 = B.m[1] - 1, A2 = B.m[2] - 1;
+    const SurfBox SS = B.shell_box();
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= surface_count(A0, A1, A2)) return;
-    int bx, by, bz;
-    surface_node(k, A0, A1, A2, bx, by, bz);
-    const int jx = 2 * (bx + 1), jy = 2 * (by + 1), jz = 2 * (bz + 1);
+    if (k >= surface_count(SS)) return;
+    int bs[3], X[3], j[3];
+    surface_node(k, SS, bs);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        X[a] = B.full[a] ? bs[a] : B.lo[a] + 1 + bs[a];
+        j[a] = 2 * (X[a] - B.lo[a]);
+    }
     R g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        g[i] = Codec<S>::load(ff + Lf.plane[i] + ((jx - cx_of(i)) + Lf.nx * ((jy - cy_of(i)) + Lf.ny * (jz - cz_of(i)))));
+        g[i] = Codec<S>::load(ff + Lf.plane[i] + (wrap1(j[0] - cx_of(i), Lf.nx) +
+                                                  Lf.nx * (wrap1(j[1] - cy_of(i), Lf.ny) +
+                                                           Lf.ny * wrap1(j[2] - cz_of(i), Lf.nz))));
     R M[NMOM];
     node_moments<R>(g, (R)Lf.rho0, M);
     rebuild<R>(M, s_fc, (R)Lc.rho0, g);
     if (!kbc_collide<R, EXACT>(g, (R)Lc.beta, (R)Lc.inv_beta, (R)Lc.rho0, Lc.gamma_mode)) atomicOr(status, ST_UNSTABLE);
-    const int n = (B.lo[0] + 1 + bx) + Lc.nx * ((B.lo[1] + 1 + by) + Lc.ny * (B.lo[2] + 1 + bz));
+    const int n = X[0] + Lc.nx * (X[1] + Lc.ny * X[2]);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Codec<S>::store(fc + Lc.plane[i] + n, g[i]);
 }
@@ -260,12 +318,14 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_restrict_kernel(const L
 // fine-level marks: the block's surface and the pad are marked solid, so
 // the fine bulk launch does not update them (the marks of a fine body,
 // inside the block, are left as they are)
-__global__ void refine_flags_kernel(uint8_t *flags, int nx, int ny, int nz, int e0, int e1, int e2)
+__global__ void refine_flags_kernel(uint8_t *flags, int nx, int ny, int nz, const Box3 B)
 {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (long long)nx * ny * nz) return;
-    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
-    const bool inner = x >= 1 && x < e0 && y >= 1 && y < e1 && z >= 1 && z < e2;
+    const int c[3] = {(int)(n % nx), (int)((n / nx) % ny), (int)(n / ((long long)nx * ny))};
+    bool inner = true;
+    for (int a = 0; a < 3; ++a)
+        if (!B.full[a] && (c[a] < 1 || c[a] >= 2 * B.m[a])) inner = false;
     if (!inner) flags[n] |= FL_SOLID;
 }
 
@@ -324,14 +384,13 @@ void release(lbm_refine *r)
 cudaError_t launch_marks(const lbm_refine *r)
 {
     const Lattice &Lf = r->f->L;
-    refine_flags_kernel<<<blocks_for(Lf.N), REFINE_THREADS, 0, r->f->stream>>>(
-        r->f->flags, Lf.nx, Lf.ny, Lf.nz, 2 * r->B.m[0], 2 * r->B.m[1], 2 * r->B.m[2]);
+    refine_flags_kernel<<<blocks_for(Lf.N), REFINE_THREADS, 0, r->f->stream>>>(r->f->flags, Lf.nx, Lf.ny, Lf.nz, r->B);
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pull, cudaStream_t st)
 {
-    const long long n = surface_count(r->B.m[0] + 1, r->B.m[1] + 1, r->B.m[2] + 1);
+    const long long n = surface_count(r->B.coarse_box());
     const lbm_ctx *c = r->c;
     return dispatch_storage(c->storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
@@ -346,7 +405,7 @@ cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pul
 
 cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const void *Mnew, double w, cudaStream_t st)
 {
-    const long long n = surface_count(2 * r->B.m[0] + 1, 2 * r->B.m[1] + 1, 2 * r->B.m[2] + 1);
+    const long long n = surface_count(r->B.fine_box());
     const lbm_ctx *f = r->f;
     // both body slots: the step that reads the flag may be either
     int *st0 = &f->S.body[0].status, *st1 = &f->S.body[1].status;
@@ -361,7 +420,7 @@ cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const v
 
 cudaError_t launch_restrict(const lbm_refine *r, void *fc, const void *ff, cudaStream_t st)
 {
-    const long long n = surface_count(r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1);
+    const long long n = surface_count(r->B.shell_box());
     const lbm_ctx *c = r->c;
     int *status = &c->S.body[c->bcur].status;
     return dispatch_exact(c->storage, c->L.gamma_mode == LBM_GAMMA_EXACT, [&](auto tag, auto ex) {
@@ -404,12 +463,22 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     if (!coarse || !fine || !lo || !hi || coarse == fine) return LBM_ERR_ARG;
     const Lattice &Lc = coarse->L, &Lf = fine->L;
     const int n[3] = {Lc.nx, Lc.ny, Lc.nz}, nf[3] = {Lf.nx, Lf.ny, Lf.nz};
+    int full[3], closed = 0;
     for (int a = 0; a < 3; ++a) {
+        // lo = 0, hi = n on a periodic axis: the block spans it
+        full[a] = lo[a] == 0 && hi[a] == n[a] && Lc.face[2 * a] == LBM_FACE_PERIODIC;
+        if (full[a]) {
+            if (nf[a] != 2 * n[a])
+                return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine lattice needs 2n nodes along a spanned axis");
+            continue;
+        }
+        closed++;
         if (lo[a] < 1 || hi[a] > n[a] - 2 || hi[a] - lo[a] < 3)
             return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the block needs 1 <= lo, hi <= n - 2, hi - lo >= 3");
         if (nf[a] != 2 * (hi[a] - lo[a]) + 2)
             return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine lattice needs 2 (hi - lo) + 2 nodes per axis");
     }
+    if (!closed) return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: a block spanning every axis has no surface");
     for (int k = 0; k < 6; ++k)
         if (Lf.face[k] != LBM_FACE_PERIODIC)
             return rfail(coarse, LBM_ERR_ARG, "lbm_refine_create: the fine lattice's faces must be periodic");
@@ -431,11 +500,14 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     for (int a = 0; a < 3; ++a) {
         r->B.lo[a] = lo[a];
         r->B.m[a] = hi[a] - lo[a];
+        r->B.full[a] = full[a];
+        r->B.n[a] = n[a];
     }
     r->s_cf = Lc.beta / (2.0 * Lf.beta);
     r->s_fc = 2.0 * Lf.beta / Lc.beta;
     const size_t rsz = coarse->storage == LBM_FP64 ? sizeof(double) : sizeof(float);
-    const size_t nbox = (size_t)(r->B.m[0] + 1) * (r->B.m[1] + 1) * (r->B.m[2] + 1);
+    const SurfBox SC = r->B.coarse_box();
+    const size_t nbox = (size_t)SC.E[0] * SC.E[1] * SC.E[2];
     if (cudaMalloc(&r->M[0], NMOM * nbox * rsz) != cudaSuccess || cudaMalloc(&r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
         cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -446,7 +518,12 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
         release(r);
         return rfail(coarse, LBM_ERR_OOM, "lbm_refine_create: device allocation failed");
     }
-    const int sw[6] = {lo[0] + 1, lo[1] + 1, lo[2] + 1, r->B.m[0] - 1, r->B.m[1] - 1, r->B.m[2] - 1};
+    // the coarse launch skips the block's inside: along a spanned axis all of it
+    int sw[6];
+    for (int a = 0; a < 3; ++a) {
+        sw[a] = full[a] ? 0 : lo[a] + 1;
+        sw[3 + a] = full[a] ? n[a] : r->B.m[a] - 1;
+    }
     cudaError_t e = cudaMemcpyAsync(r->sweep, sw, sizeof(sw), cudaMemcpyHostToDevice, coarse->stream);
     if (e == cudaSuccess) e = launch_marks(r);
     if (e == cudaSuccess) e = cudaStreamSynchronize(coarse->stream);
@@ -471,10 +548,11 @@ lbm_status lbm_refine_init(lbm_refine *r)
     if (!r->c->initialised || !r->f->initialised)
         return rfail(r->c, LBM_ERR_STATE, "lbm_refine_init: both levels must hold their initial state");
     if (r->c->has_body) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_init: the coarse level carries a body");
-    // walls mark the whole box and the airfoil spans the fine lattice's z
-    // extent: either would reach the block's surface
-    if (r->f->has_body && (r->f->G.kind == LBM_BODY_PLANES || r->f->G.kind == LBM_BODY_AIRFOIL))
-        return rfail(r->c, LBM_ERR_UNSUPPORTED, "lbm_refine_init: a fine body must be a sphere or a mesh");
+    // walls mark the whole box; the airfoil spans the fine lattice's z extent,
+    // which only a block spanning z leaves without a surface
+    if (r->f->has_body && (r->f->G.kind == LBM_BODY_PLANES || (r->f->G.kind == LBM_BODY_AIRFOIL && !r->B.full[2])))
+        return rfail(r->c, LBM_ERR_UNSUPPORTED,
+                     "lbm_refine_init: a fine body must be a sphere, a mesh, or an airfoil in a block spanning z");
     // lbm_set_geometry on the fine level clears the surface marks
     RF_CUDA(launch_marks(r), "refine marks");
     RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], false, r->c->stream), "refine moments");

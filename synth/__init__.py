@@ -154,6 +154,30 @@ def refined_block(shape=(512, 256, 64), lo=(128, 64, 8), hi=(383, 191, 55), u_in
                 u_inf=u_inf, amp=amp)
 
 
+def refined_airfoil(shape=(512, 256, 32), lo=(96, 64, 0), hi=(351, 191, 32), chord: float = 128.0,
+                    u_inf: float = 0.05, re: float = 40000.0, k: float = 3.93, h0: float = 0.05,
+                    alpha_deg: float = 4.0, le=(128.37, 128.29)):
+    """The plunging airfoil (Sec. 4.2) on a two-level grid: a coarse box with
+    the airfoil box's faces and a ratio-2 block over [lo, hi] in x and y that
+    spans the periodic span (z), the airfoil on the fine level in fine
+    lattice units (chord 128, leading edge at le of the fine lattice), so the
+    airfoil sees the resolution of the single-level 1024 x 512 x 64 box near
+    it.  Viscosity and plunge in fine units: nu_f = u_inf c / Re, the reduced
+    frequency k = pi f c / u_inf per fine step; the coarse level takes nu_f /
+    2 (acoustic scaling)."""
+    nx, ny, nz = shape
+    fine = tuple(2 * n if (l == 0 and h == n and a == 2) else 2 * (h - l) + 2
+                 for a, (l, h, n) in enumerate(zip(lo, hi, shape)))
+    f = k * u_inf / (math.pi * chord)
+    a = math.radians(alpha_deg)
+    nu_f = u_inf * chord / re
+    return dict(name=f"refined_airfoil_{nx}x{ny}x{nz}_fine_{fine[0]}x{fine[1]}x{fine[2]}_c{chord:g}",
+                shape=shape, lo=lo, hi=hi, fine_shape=fine, nu=nu_f / 2, faces=(2, 3, 2, 2, 0, 0),
+                u_face=(u_inf, 0.0, 0.0), u_inf=u_inf, chord=chord, ca=math.cos(a), sa=math.sin(a),
+                h_amp=h0 * chord, h_omega=2 * math.pi * f, camber_m=0.015, camber_p=0.35,
+                thick=airfoil_thickness(), le=le)
+
+
 def refined_fields(wl, level: str):
     """(rho, u) of the refined block workload on the coarse or the fine level:
     u = (u_inf, 0, 0) + amp * (sin x^ cos y^ cos z^, -cos x^ sin y^ cos z^, 0)

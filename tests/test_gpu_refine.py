@@ -229,3 +229,57 @@ def test_refinement_rejects_an_airfoil_on_the_fine_level():
     with pytest.raises(lbm.LbmError) as e:
         ref.init()
     assert e.value.status == binding.LBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_spanning_block_matches_the_oracle(storage):
+    """A block over [4, 11] x [3, 8] spanning the periodic z axis of a 16 x 12
+    x 10 box (fine lattice 16 x 12 x 20, periodic along z, the surface
+    interpolation wrapping there), rough random states, 4 coarse steps."""
+    lat, ref, orc, ro = run_refined((16, 12, 10), 0.02, storage, (4, 3, 0), (11, 8, 10), 4, seed=17)
+    assert ref.full == (False, False, True) and ref.fine.shape == (16, 12, 20)
+    ec, ef = errors(lat, ref, orc, ro)
+    assert ec <= TOL[storage] and ef <= TOL[storage], (storage, ec, ef)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_refined_plunging_airfoil(storage):
+    """The paper's two-level airfoil grid (Sec. 4.2) at small size: a
+    plunging cambered airfoil (chord 16 fine nodes) on the fine level of a
+    block over [12, 35] x [8, 23] spanning the periodic span of a 48 x 32 x 4
+    box with equilibrium inflow, outflow and far field, impulsive start, 6
+    coarse steps: both levels' populations, the airfoil's marks and its force
+    against the oracle."""
+    import math
+
+    import paper_1608_04658_gb300 as lbm
+    nu, U = 0.01, (0.05, 0.0, 0.0)
+    shape, lo, hi, faces = (48, 32, 4), (12, 8, 0), (35, 23, 4), (2, 3, 2, 2, 0, 0)
+    wl = synth.plunging_airfoil()
+    chord, le = 16.0, (14.3, 15.2)
+    args = (chord, wl["ca"], wl["sa"], 0.05 * chord, 2 * math.pi * 0.01, wl["camber_m"], wl["camber_p"], wl["thick"])
+    lat = lbm.Lattice(shape, nu, storage=storage, faces=faces, u_face=U)
+    ref = lbm.Refinement(lat, lo, hi)
+    ref.fine.set_geometry(lbm.airfoil(le, *args))
+    lat.init_state(*synth.uniform_fields(shape, U))
+    ref.fine.init_state(*synth.uniform_fields(ref.fine.shape, U))
+    ref.init()
+    ref.step(6)
+    F, _ = ref.fine.forces()
+
+    orc = oracle.Oracle(shape, nu=nu, faces=faces, u_face=U)
+    orc.init_state(*synth.uniform_fields(shape, U))
+    ro = oracle.RefinedOracle(orc, lo, hi, fine_body=oracle.airfoil_body(le, *args))
+    ro.fine.init_state(*synth.uniform_fields(ro.fine.shape, U))
+    ro.init()
+    ro.step(6)
+    inner = np.zeros(ro.fine_valid().shape, dtype=bool)
+    inner[:, 1:-2, 1:-2] = True
+    solid = (ref.fine.flags.cpu().numpy() & 1).astype(bool) & inner
+    assert solid.sum() > 0
+    assert np.array_equal(solid, ro.fine.solid().astype(bool) & inner)
+    assert rel_err(lat.populations(), orc.get_f(), ro.coarse_valid()) <= TOL[storage]
+    assert rel_err(ref.fine.populations(), ro.fine.get_f(), ro.fine_valid() & ~solid) <= TOL[storage]
+    Fo = np.array(ro.fine.body.F)
+    ftol = 1e-10 if storage == "fp64" else 1e-5
+    assert np.abs(np.array(F) - Fo).max() <= ftol * np.abs(Fo).max()
