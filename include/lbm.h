@@ -485,8 +485,9 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * storage, stabilizer, rho0 and stream, no slab) over the block of
  * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2,
  * hi - lo >= 3, unless spanned).  It writes the fine context's flags (the block's surface
- * and the pad marked solid), allocates its own device scratch (two sets of
- * 10 moments per node of the (m+1)^3 coarse box) with cudaMalloc and
+ * and the pad marked solid), allocates its own device scratch (three sets of
+ * 10 moments per node of the block's coarse box: t, t+1 and their mean)
+ * with cudaMalloc and
  * synchronises the stream.  The coarse context must carry no body; the fine
  * one may (below).  Errors: LBM_ERR_ARG for a mismatch, with the
  * reason in lbm_last_error(coarse); LBM_ERR_OOM.  *out is NULL on failure.

@@ -65,31 +65,34 @@ __host__ __device__ inline long long surface_count(const SurfBox &S)
 
 // k-th of those nodes: the two end slabs of the closed axes in the order z,
 // y, x, each slab without the nodes of the slabs before it (x fastest
-// within a slab)
-__device__ inline void surface_node(long long k, const SurfBox &S, int c[3])
+// within a slab); *axis = the closed axis whose end slab holds the node.
+// Surface counts stay far below 2^31, so the index arithmetic is 32-bit.
+__device__ inline void surface_node(int k, const SurfBox &S, int c[3], int *axis = nullptr)
 {
     int done[3] = {0, 0, 0};
     for (int t = 0; t < 3; ++t) {
         const int a = 2 - t;
         if (!S.closed[a]) continue;
-        long long r[3];
+        int r[3];
         for (int b = 0; b < 3; ++b) r[b] = b == a ? 1 : (done[b] ? S.E[b] - 2 : S.E[b]);
-        const long long slab = r[0] * r[1] * r[2];
+        const int slab = r[0] * r[1] * r[2];
         if (k < 2 * slab) {
             const bool far = k >= slab;
             if (far) k -= slab;
             c[a] = far ? S.E[a] - 1 : 0;
             for (int b = 0; b < 3; ++b) {
                 if (b == a) continue;
-                c[b] = (int)(k % r[b]) + (done[b] ? 1 : 0);
+                c[b] = k % r[b] + (done[b] ? 1 : 0);
                 k /= r[b];
             }
+            if (axis) *axis = a;
             return;
         }
         k -= 2 * slab;
         done[a] = 1;
     }
     c[0] = c[1] = c[2] = 0;  // k beyond the count (not reached)
+    if (axis) *axis = 0;
 }
 
 // v wrapped into [0, n) when it is at most one period off
@@ -189,17 +192,20 @@ struct Box3 {
 };
 
 // Coarse pre-collision moments on the block's surface: PULL, the pulls of the
-// next step from state f (the coarse state at t); otherwise f's own
-// populations (the initial state).  M[k * nbox + b], b the node's position in
-// the (m+1)^3 box.
+// next step from state f (the coarse state at t) into M, and the mean of the
+// moments at t (Mt) and those into Mh (the half step's); otherwise f's own
+// populations (the initial state) into M.  M[q * nbox + b], b the node's
+// position in the block's coarse box.
 template <typename S, bool PULL>
 __global__ void __launch_bounds__(REFINE_THREADS) refine_moments_kernel(const Lattice L, const S *__restrict__ f,
                                                                         const Box3 B,
-                                                                        typename Codec<S>::R *__restrict__ M)
+                                                                        typename Codec<S>::R *__restrict__ M,
+                                                                        const typename Codec<S>::R *__restrict__ Mt,
+                                                                        typename Codec<S>::R *__restrict__ Mh)
 {
     using R = typename Codec<S>::R;
     const SurfBox SB = B.coarse_box();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= surface_count(SB)) return;
     int bc[3];
     surface_node(k, SB, bc);
@@ -217,53 +223,55 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_moments_kernel(const La
     const long long nbox = (long long)SB.E[0] * SB.E[1] * SB.E[2];
     const long long b = bc[0] + (long long)SB.E[0] * (bc[1] + (long long)SB.E[1] * bc[2]);
 #pragma unroll
-    for (int q = 0; q < NMOM; ++q) M[q * nbox + b] = Mn[q];
+    for (int q = 0; q < NMOM; ++q) {
+        M[q * nbox + b] = Mn[q];
+        if (PULL) Mh[q * nbox + b] = R(0.5) * (Mt[q * nbox + b] + Mn[q]);
+    }
 }
 
-// Fine surface nodes of fine state ff at the time (1 - w) t + w (t+1): the
-// moments trilinear from the coarse surface (each odd fine coordinate takes
-// the mean of the two coarse nodes around it), linear in time, rebuilt with
-// the coarse-to-fine factor and collided with the fine b.
+// Fine surface nodes of fine state ff from the coarse moments Ms of that
+// time (the moments at t+1, or the half step's mean): trilinear from the
+// coarse surface (each odd fine coordinate takes the mean of the two coarse
+// nodes around it; a surface node's coordinate normal to its face is even,
+// so at most the two in-plane ones are odd: four corners, some repeated),
+// rebuilt with the coarse-to-fine factor and collided with the fine b.
 template <typename S, bool EXACT>
 __global__ void __launch_bounds__(REFINE_THREADS) refine_fill_kernel(const Lattice Lf, S *__restrict__ ff,
                                                                      const Box3 B,
-                                                                     const typename Codec<S>::R *__restrict__ Mold,
-                                                                     const typename Codec<S>::R *__restrict__ Mnew,
-                                                                     typename Codec<S>::R w,
+                                                                     const typename Codec<S>::R *__restrict__ Ms,
                                                                      typename Codec<S>::R s_cf,
                                                                      const uint8_t *__restrict__ flags,
                                                                      int *__restrict__ st0, int *__restrict__ st1)
 {
     using R = typename Codec<S>::R;
     const SurfBox SF = B.fine_box(), SC = B.coarse_box();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= surface_count(SF)) return;
-    int j[3];
-    surface_node(k, SF, j);
-    const int A0 = SC.E[0], A1 = SC.E[1];
-    const long long nbox = (long long)A0 * A1 * SC.E[2];
-    int b0[3], nk[3];
+    int j[3], a0;
+    surface_node(k, SF, j, &a0);
+    const int p = a0 == 0 ? 1 : 0, q = a0 == 2 ? 1 : 2;  // the in-plane axes
+    int lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        b0[a] = j[a] >> 1;
-        nk[a] = (j[a] & 1) ? 2 : 1;
+        lo[a] = j[a] >> 1;
+        hi[a] = lo[a] + (j[a] & 1);
+        if (B.full[a] && hi[a] == B.n[a]) hi[a] = 0;  // the node after the last of a spanned axis
     }
-    const R wt = R(1) / R(nk[0] * nk[1] * nk[2]);
+    const int A0 = SC.E[0], A1 = SC.E[1];
+    const int nbox = A0 * A1 * SC.E[2];
+    int cidx[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int b[3] = {lo[0], lo[1], lo[2]};
+        if (c & 1) b[p] = hi[p];
+        if (c & 2) b[q] = hi[q];
+        cidx[c] = b[0] + A0 * (b[1] + A1 * b[2]);
+    }
     R M[NMOM];
 #pragma unroll
-    for (int q = 0; q < NMOM; ++q) M[q] = R(0);
-    for (int dz = 0; dz < nk[2]; ++dz)
-        for (int dy = 0; dy < nk[1]; ++dy)
-            for (int dx = 0; dx < nk[0]; ++dx) {
-                // the node after the last of a spanned axis is its first
-                const int bx = B.full[0] ? wrap1(b0[0] + dx, B.n[0]) : b0[0] + dx;
-                const int by = B.full[1] ? wrap1(b0[1] + dy, B.n[1]) : b0[1] + dy;
-                const int bz = B.full[2] ? wrap1(b0[2] + dz, B.n[2]) : b0[2] + dz;
-                const long long b = bx + (long long)A0 * (by + (long long)A1 * bz);
-#pragma unroll
-                for (int q = 0; q < NMOM; ++q)
-                    M[q] += wt * ((R(1) - w) * Mold[q * nbox + b] + w * Mnew[q * nbox + b]);
-            }
+    for (int m = 0; m < NMOM; ++m)
+        M[m] = R(0.25) * ((Ms[m * nbox + cidx[0]] + Ms[m * nbox + cidx[1]]) +
+                          (Ms[m * nbox + cidx[2]] + Ms[m * nbox + cidx[3]]));
     R g[Q];
     rebuild<R>(M, s_cf, (R)Lf.rho0, g);
     const int n = j[0] + Lf.nx * (j[1] + Lf.ny * j[2]);
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_restrict_kernel(const L
 {
     using R = typename Codec<S>::R;
     const SurfBox SS = B.shell_box();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= surface_count(SS)) return;
     int bs[3], X[3], j[3];
     surface_node(k, SS, bs);
@@ -346,6 +354,7 @@ struct lbm_refine {
     lbm_ctx *c = nullptr, *f = nullptr;
     Box3 B{};
     void *M[2] = {nullptr, nullptr};  // moments at t (slot mcur) and t+1
+    void *Mh = nullptr;               // their mean, the half step's moments
     int mcur = 0;
     int *sweep = nullptr;             // device {lo + 1 (3), m - 1 (3)}: the coarse launch skips it
     // fork of the side stream (the coarse context's, unused without a body),
@@ -377,6 +386,7 @@ void release(lbm_refine *r)
         if (e) cudaEventDestroy(e);
     cudaFree(r->M[0]);
     cudaFree(r->M[1]);
+    cudaFree(r->Mh);
     cudaFree(r->sweep);
     delete r;
 }
@@ -388,7 +398,8 @@ cudaError_t launch_marks(const lbm_refine *r)
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pull, cudaStream_t st)
+cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, const void *Mt, void *Mh, bool pull,
+                           cudaStream_t st)
 {
     const long long n = surface_count(r->B.coarse_box());
     const lbm_ctx *c = r->c;
@@ -396,14 +407,16 @@ cudaError_t launch_moments(const lbm_refine *r, const void *f, void *M, bool pul
         using S = std::remove_pointer_t<decltype(tag)>;
         using R = typename Codec<S>::R;
         if (pull)
-            refine_moments_kernel<S, true><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M);
+            refine_moments_kernel<S, true><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M,
+                                                                                    (const R *)Mt, (R *)Mh);
         else
-            refine_moments_kernel<S, false><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M);
+            refine_moments_kernel<S, false><<<blocks_for(n), REFINE_THREADS, 0, st>>>(c->L, (const S *)f, r->B, (R *)M,
+                                                                                     nullptr, nullptr);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const void *Mnew, double w, cudaStream_t st)
+cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Ms, cudaStream_t st)
 {
     const long long n = surface_count(r->B.fine_box());
     const lbm_ctx *f = r->f;
@@ -413,7 +426,7 @@ cudaError_t launch_fill(const lbm_refine *r, void *ff, const void *Mold, const v
         using S = std::remove_pointer_t<decltype(tag)>;
         using R = typename Codec<S>::R;
         refine_fill_kernel<S, decltype(ex)::value><<<blocks_for(n), REFINE_THREADS, 0, st>>>(
-            f->L, (S *)ff, r->B, (const R *)Mold, (const R *)Mnew, (R)w, (R)r->s_cf, f->flags, st0, st1);
+            f->L, (S *)ff, r->B, (const R *)Ms, (R)r->s_cf, f->flags, st0, st1);
         return cudaGetLastError();
     });
 }
@@ -509,6 +522,7 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     const SurfBox SC = r->B.coarse_box();
     const size_t nbox = (size_t)SC.E[0] * SC.E[1] * SC.E[2];
     if (cudaMalloc(&r->M[0], NMOM * nbox * rsz) != cudaSuccess || cudaMalloc(&r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
+        cudaMalloc(&r->Mh, NMOM * nbox * rsz) != cudaSuccess ||
         cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fine1, cudaEventDisableTiming) != cudaSuccess ||
@@ -555,8 +569,9 @@ lbm_status lbm_refine_init(lbm_refine *r)
                      "lbm_refine_init: a fine body must be a sphere, a mesh, or an airfoil in a block spanning z");
     // lbm_set_geometry on the fine level clears the surface marks
     RF_CUDA(launch_marks(r), "refine marks");
-    RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], false, r->c->stream), "refine moments");
-    RF_CUDA(launch_fill(r, r->f->f[r->f->cur], r->M[r->mcur], r->M[r->mcur], 0.0, r->c->stream), "refine fill");
+    RF_CUDA(launch_moments(r, r->c->f[r->c->cur], r->M[r->mcur], nullptr, nullptr, false, r->c->stream),
+            "refine moments");
+    RF_CUDA(launch_fill(r, r->f->f[r->f->cur], r->M[r->mcur], r->c->stream), "refine fill");
     r->ready = true;
     return LBM_OK;
 }
@@ -584,15 +599,15 @@ lbm_status lbm_refine_step(lbm_refine *r, int nsteps)
         int *cstat = &c->S.body[c->bcur].status, *fstat = &f->S.body[0].status;
         RF_CUDA(cudaEventRecord(r->ev_fork, main), "fork");
         RF_CUDA(cudaStreamWaitEvent(side, r->ev_fork, 0), "fork wait");
-        RF_CUDA(launch_moments(r, ca, Mn, true, side), "refine moments");
-        RF_CUDA(launch_fill(r, fb, Mt, Mn, 0.5, side), "refine fill");
+        RF_CUDA(launch_moments(r, ca, Mn, Mt, r->Mh, true, side), "refine moments");
+        RF_CUDA(launch_fill(r, fb, r->Mh, side), "refine fill");
         RF_CUDA(cudaEventRecord(r->ev_fill, side), "fill event");
         RF_CUDA(launch_bulk(c->storage, c->L, ca, cb, nullptr, cstat, side, BULK_OUTSIDE, r->sweep), "coarse bulk");
         RF_CUDA(fine_step(r, fa, fb, fstat, main), "fine step");
         RF_CUDA(cudaEventRecord(r->ev_fine1, main), "fine event");
         RF_CUDA(cudaStreamWaitEvent(side, r->ev_fine1, 0), "fine wait");
         RF_CUDA(launch_restrict(r, cb, fb, side), "refine restrict");
-        RF_CUDA(launch_fill(r, fa, Mt, Mn, 1.0, side), "refine fill");
+        RF_CUDA(launch_fill(r, fa, Mn, side), "refine fill");
         RF_CUDA(cudaEventRecord(r->ev_side, side), "side event");
         RF_CUDA(cudaStreamWaitEvent(main, r->ev_fill, 0), "fill wait");
         RF_CUDA(fine_step(r, fb, fa, fstat, main), "fine step");
