@@ -520,7 +520,8 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * times the fine bulk launches.
  *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two
- * contexts stay valid. */
+ * contexts stay valid.  Destroy the coupling before either context: it keeps
+ * pointers to both. */
 typedef struct lbm_refine lbm_refine;
 LBM_API lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3], const int32_t hi[3],
                                      lbm_refine **out);

@@ -547,7 +547,8 @@ class Refinement:
     axis, periodic faces, twice the coarse viscosity, same storage, stabilizer
     and stream) is created here as ``self.fine``: fine node j sits at coarse
     coordinate lo + j/2.  Initialise both levels, call ``init()``, then
-    ``step(n)`` (n coarse steps, 2n fine steps)."""
+    ``step(n)`` (n coarse steps, 2n fine steps).  ``close()`` this object
+    before closing either Lattice."""
 
     def __init__(self, coarse: Lattice, lo, hi):
         self.coarse = coarse

@@ -352,6 +352,7 @@ static cudaError_t dispatch_exact(int storage, bool exact, F &&fn)
 // ---------------------------------------------------------------- host side
 struct lbm_refine {
     lbm_ctx *c = nullptr, *f = nullptr;
+    cudaStream_t stream = nullptr;    // the levels' shared stream (the caller's)
     Box3 B{};
     void *M[2] = {nullptr, nullptr};  // moments at t (slot mcur) and t+1
     void *Mh = nullptr;               // their mean, the half step's moments
@@ -510,6 +511,7 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     if (!r) return LBM_ERR_OOM;
     r->c = coarse;
     r->f = fine;
+    r->stream = coarse->stream;
     for (int a = 0; a < 3; ++a) {
         r->B.lo[a] = lo[a];
         r->B.m[a] = hi[a] - lo[a];
@@ -552,7 +554,8 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
 void lbm_refine_destroy(lbm_refine *r)
 {
     if (!r) return;
-    cudaStreamSynchronize(r->c->stream);  // the side stream's work is ordered before the step's end
+    // the side stream's work is ordered before each step's end on this stream
+    cudaStreamSynchronize(r->stream);
     release(r);
 }
 
