@@ -1,7 +1,8 @@
 """Writes tests/golden/oracle_regression.txt: outputs of short oracle runs of
-each body kind (force, torque, body state, and three sums of the populations'
-deviations from rest: plain, squared, and weighted by cos(0.37 n) over the
-flat index n, which a permutation would change), so a
+each body kind and of the two-level grid (force, torque, body state, and
+three sums of the populations' deviations from rest: plain, squared, and
+weighted by cos(0.37 n) over the flat index n, which a permutation would
+change), so a
 change to the oracle's arithmetic shows up as a failing comparison that its
 commit must then justify from the paper.  Calls only the oracle and the seeded
 input generators.
@@ -64,8 +65,45 @@ def run(name, shape, kw, make_body, steps):
     return vals
 
 
+def refined_cases():
+    """name -> (coarse shape, lo, hi, Oracle keyword arguments, fine body factory, coarse steps)."""
+    return {
+        "refined_block": ((20, 16, 14), (4, 3, 3), (13, 11, 9), dict(nu=0.02), lambda: None, 3),
+        "refined_span_free_sphere": ((24, 20, 8), (6, 5, 0), (17, 14, 8), dict(nu=0.02),
+                                     lambda: oracle.sphere_body((11.3, 9.4, 7.6), 2.6, U=(0.02, 0.005, 0.01),
+                                                                free=True, rho_ratio=2.0), 3),
+    }
+
+
+def run_refined(name, shape, lo, hi, kw, make_body, steps):
+    body = make_body()
+    o = oracle.Oracle(shape, **kw)
+    rho, u, xi = synth.parity_fields(shape, 22)
+    o.init_state(rho, u * 0.5, xi, 1e-3)
+    r = oracle.RefinedOracle(o, lo, hi, fine_body=body)
+    frho, fu, fxi = synth.parity_fields(r.fine.shape, 23)
+    r.fine.init_state(frho, fu * 0.5, fxi, 1e-3)
+    r.init()
+    r.step(steps)
+    _, W = oracle.lattice()
+    vals = {}
+    for lev, f, valid in (("c", o.get_f(), r.coarse_valid()), ("f", r.fine.get_f(), r.fine_valid())):
+        g = (f - W[:, None, None, None])[:, valid].reshape(-1)
+        vals[f"{lev}_g_sum"] = float(g.sum())
+        vals[f"{lev}_g_sq_sum"] = float((g * g).sum())
+        vals[f"{lev}_g_cos"] = float((g * np.cos(0.37 * np.arange(g.size))).sum())
+    if body is not None:
+        b = r.fine.body
+        for k in ("F", "M", "X", "U"):
+            for a in range(3):
+                vals[f"{k}{a}"] = float(getattr(b, k)[a])
+    return vals
+
+
 def compute():
-    return {name: run(name, *c) for name, c in cases().items()}
+    res = {name: run(name, *c) for name, c in cases().items()}
+    res.update({name: run_refined(name, *c) for name, c in refined_cases().items()})
+    return res
 
 
 def main():
