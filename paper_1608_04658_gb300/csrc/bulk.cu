@@ -17,9 +17,9 @@
 namespace lbm {
 
 // Minimum resident blocks per SM requested from the register allocator: 7
-// blocks of 128 threads cap the kernel at 72 registers (a 32-byte spill) and
-// give 28 warps per SM, which measured faster on GB300 than 80 registers with
-// 6 blocks or 64 registers with 8.
+// blocks of 128 threads cap the kernel at 72 registers (no spill) and give
+// 28 warps per SM, which measured faster on GB300 than 80 registers with 6
+// blocks or 64 registers with 8.
 #ifndef LBM_BULK_MIN_BLOCKS
 #define LBM_BULK_MIN_BLOCKS 7
 #endif
@@ -36,12 +36,14 @@ struct BulkBlocks {
 };
 
 // Resident blocks per SM asked of the register allocator for the two-node
-// kernel (64 threads, 128 nodes per block): 6 (166 registers, no spill) for
-// FP32 storage, 7 (128 registers, a 160-byte spill) for 16-bit storage,
-// each the faster on GB300 for its storage (swimmer box: FP32 0.88 vs 0.84,
-// FP16 0.57 vs 0.54 of the copy bandwidth).
+// kernel (64 threads, 128 nodes per block): 8 for FP32 storage, 7 for 16-bit
+// storage; both then fit in 128 registers without spilling (the collision
+// forms the equilibrium factors again after its scalar products instead of
+// keeping them live), 16 warps per SM.  Measured on GB300 (swimmer box,
+// fraction of the copy bandwidth): FP32 0.944 at 8 blocks against 0.896 at
+// 6 (166 registers, 12 warps); FP16 0.576 at 7 against 0.452 at 9.
 #ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 6
+#define LBM_PAIR_MIN_BLOCKS 8
 #endif
 #ifndef LBM_PAIR_MIN_BLOCKS_16
 #define LBM_PAIR_MIN_BLOCKS_16 7

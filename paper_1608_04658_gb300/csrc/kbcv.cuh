@@ -9,6 +9,10 @@
 
 #include "kbc.cuh"
 
+#ifndef LBM_RECOMPUTE_EQ
+#define LBM_RECOMPUTE_EQ 1
+#endif
+
 namespace lbm {
 
 // one node: V = float
@@ -65,6 +69,19 @@ __device__ __forceinline__ void axis_eq_v(typename O::V u, typename O::V e[3], t
     r[0] = O::fma(r1, bp, r1);
     r[1] = r1;
     r[2] = O::fma(r1, bm, r1);
+}
+
+// v, with a dependence on dep the compiler cannot see through: a value
+// computed from it again after dep is formed is recomputed there, not kept
+// live from its first evaluation
+template <typename O>
+__device__ __forceinline__ typename O::V after(typename O::V v, typename O::V dep)
+{
+    float out[2] = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(v) / sizeof(float)); ++k)
+        asm volatile("mov.b32 %0, %1;" : "=f"(out[k]) : "f"(O::lane(v, k)), "f"(O::lane(dep, k)));
+    return O::make(out[0], out[1]);
 }
 
 // Shear part ds_i for direction i (faces sx, sy, sz; edges the signed
@@ -204,6 +221,28 @@ __device__ __forceinline__ int kbc_collide_v(typename O::V g[Q], float beta, flo
     }
     const V c1 = O::make(c1v[0], c1v[NL - 1]);
     const V c2 = O::make(c2v[0], c2v[NL - 1]);
+#if LBM_RECOMPUTE_EQ
+    // the equilibrium again from the same velocity, bit for bit the same
+    // factors: keeping them across the scalar products needs some 46 more
+    // registers, which the 16-bit two-node kernel would spill
+    {
+        const V ir = after<O>(inv_rho, hh);
+        axis_eq_v<O>(O::mul(after<O>(jx, hh), ir), ex, px, rx);
+        axis_eq_v<O>(O::mul(after<O>(jy, hh), ir), ey, py, ry);
+        axis_eq_v<O>(O::mul(after<O>(jz, hh), ir), ez, pz, rz);
+        const V rho2 = after<O>(rho, hh), drho2 = after<O>(drho, hh);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float w = k == 0 ? 8.f / 27.f : k == 1 ? 2.f / 27.f : k == 2 ? 1.f / 54.f : 1.f / 216.f;
+            rw[k] = O::mul(rho2, O::c(w));
+            dw[k] = O::mul(drho2, O::c(w));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) exy[a][b] = O::fma(ey[b], px[a], ex[a]);
+    }
+#endif
     // g' = g^eq + c1 d + c2 ds
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
