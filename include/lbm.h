@@ -516,7 +516,7 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * lbm_get_populations as usual.  Do not call lbm_step on either context of a
  * coupled pair.  Coarse nodes more than one layer inside the block's surface
  * and the fine pad hold no defined state.  LBM_ERR_STATE before
- * lbm_refine_init.  A fine profile (lbm_profile_begin on the fine context)
+ * lbm_refine_init, or once the coarse context has been given a body.  A fine profile (lbm_profile_begin on the fine context)
  * times the fine bulk launches.
  *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two

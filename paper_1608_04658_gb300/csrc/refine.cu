@@ -584,6 +584,8 @@ lbm_status lbm_refine_step(lbm_refine *r, int nsteps)
     if (!r) return LBM_ERR_ARG;
     if (nsteps < 0) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_step: nsteps < 0");
     if (!r->ready) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_step: lbm_refine_init has not run");
+    // a body set on the coarse level after the coupling was made
+    if (r->c->has_body) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_step: the coarse level carries a body");
     lbm_ctx *c = r->c, *f = r->f;
     // The fine launches run on the shared stream; the coupling kernels and
     // the coarse launch on the side stream beside them.  They write disjoint

@@ -140,6 +140,14 @@ def test_refinement_rejects_mismatched_levels():
     with pytest.raises(lbm.LbmError) as e:
         ref.step(1)  # before init
     assert e.value.status == binding.LBM_ERR_STATE
+    lat.init_state(*synth.uniform_fields((24, 20, 18)))
+    ref.fine.init_state(*synth.uniform_fields(ref.fine.shape))
+    ref.init()
+    ref.step(1)
+    lat.set_geometry(lbm.sphere((3.3, 3.4, 3.6), 1.5))  # a coarse body after the coupling
+    with pytest.raises(lbm.LbmError) as e:
+        ref.step(1)
+    assert e.value.status == binding.LBM_ERR_STATE
 
 
 def test_refined_block_bench_configuration_keeps_the_free_stream():
