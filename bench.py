@@ -648,6 +648,8 @@ def refine_bench(args, world, device, clocks):
     out = {}
     for wl, storages in ((synth.refined_block(), ("fp32", "fp16")), (synth.refined_airfoil(), ("fp32",))):
         out[wl["name"]] = refine_run(args, world, device, clocks, wl, storages)
+        if world == 1 and not args.no_cpu_baseline:
+            out[wl["name"]]["cpu_baseline"] = refine_cpu_baseline(wl, "airfoil" in wl["name"])
     return out
 
 
@@ -769,6 +771,46 @@ def cpu_baseline(wl):
     t = time.perf_counter() - t0
     n = shape[0] * shape[1] * shape[2]
     return {"value": n * nsteps / t / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": desc + ", FP64, one thread", "seconds": round(t, 2)}
+
+
+def refine_cpu_baseline(wl, body: bool):
+    """The FP64 oracle's refined step (RefinedOracle), single-threaded, on a
+    bounded sample of a refined workload: the same faces, viscosity and flow
+    on a crop with a block of the same kind (closed, or spanning z with the
+    airfoil on the fine level, chord scaled to the crop), a few coarse steps;
+    the value counts node updates as the GPU line does."""
+    import math as _m
+
+    import oracle
+    import synth
+    if body:
+        shape, lo, hi, steps = (64, 48, 4), (8, 8, 0), (55, 39, 4), 24
+        chord, le = 32.0, (16.37, 32.29)
+        f = 3.93 * wl["u_inf"] / (_m.pi * chord)
+        fb = oracle.airfoil_body(le, chord, wl["ca"], wl["sa"], 0.05 * chord, 2 * _m.pi * f,
+                                 wl["camber_m"], wl["camber_p"], wl["thick"])
+        desc = (f"{steps} coarse steps of a {shape[0]}x{shape[1]}x{shape[2]} box, block [8, 55] x [8, 39] "
+                f"spanning z, the airfoil (chord {chord:g}) on the fine level")
+    else:
+        shape, lo, hi, steps, fb = (64, 32, 16), (16, 8, 2), (47, 23, 13), 24, None
+        desc = f"{steps} coarse steps of a {shape[0]}x{shape[1]}x{shape[2]} box, block [16, 47] x [8, 23] x [2, 13]"
+    o = oracle.Oracle(shape, nu=wl["nu"], faces=wl["faces"], u_face=wl["u_face"])
+    o.init_state(*synth.uniform_fields(shape, wl["u_face"]))
+    r = oracle.RefinedOracle(o, lo, hi, fine_body=fb)
+    r.fine.init_state(*synth.uniform_fields(r.fine.shape, wl["u_face"]))
+    r.init()
+    full = [l == 0 and h == n for l, h, n in zip(lo, hi, shape)]
+    inside = fine_interior = 1
+    for a in range(3):
+        m = hi[a] - lo[a]
+        inside *= shape[a] if full[a] else m - 1
+        fine_interior *= 2 * shape[a] if full[a] else 2 * m - 1
+    per_step = shape[0] * shape[1] * shape[2] - inside + 2 * fine_interior
+    t0 = time.perf_counter()
+    r.step(steps)
+    t = time.perf_counter() - t0
+    return {"value": per_step * steps / t / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
             "sample": desc + ", FP64, one thread", "seconds": round(t, 2)}
 
 
