@@ -194,6 +194,33 @@ typedef struct lbm_ctx lbm_ctx;
 LBM_API lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
                               void *stream, lbm_ctx **out);
 
+/* Device allocator for the library's own scratch (boundary lists and body
+ * arrays of lbm_set_geometry, the checkpoints and work arrays of
+ * lbm_adjoint_step, the plane buffer of lbm_get/set_populations, the
+ * moments of lbm_refine_create on a coarse context).  The paper has no such
+ * interface; it lets a caller that pools its device memory (PyTorch's caching
+ * allocator, an application arena) hand the library that memory instead of
+ * plain cudaMalloc / cudaFree.
+ *   alloc(bytes, stream, user)  returns device memory of the context's device,
+ *                               at least 256-byte aligned, or NULL (the
+ *                               calling entry point then fails with
+ *                               LBM_ERR_OOM); stream is the context's stream;
+ *   release(ptr, stream, user)  gives a block back; the library calls it only
+ *                               when no work of its own that uses the block
+ *                               is still in flight on any stream.
+ * Both NULL restores cudaMalloc / cudaFree.  The few small buffers of
+ * lbm_create itself stay cudaMalloc'd.  Call it before the first call that
+ * allocates scratch: LBM_ERR_STATE once the context holds scratch from the
+ * other allocator; LBM_ERR_ARG for a null context or only one of the two
+ * functions. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_release_fn)(void *ptr, void *stream, void *user);
+LBM_API lbm_status lbm_set_allocator(lbm_ctx *ctx, lbm_alloc_fn alloc, lbm_release_fn release, void *user);
+
+/* Sets the state to the entropic equilibrium f_i = f_i^eq(rho, u) (Eq.
+ * feq_min): lbm_init_state without the noise term; rho and u as there. */
+LBM_API lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u);
+
 /* Releases the context and the library's own device scratch. */
 LBM_API void lbm_destroy(lbm_ctx *ctx);
 

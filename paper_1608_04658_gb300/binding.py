@@ -77,6 +77,11 @@ _lib = None
 _D = C.POINTER(C.c_double)
 
 
+# caller-supplied device allocator of lbm_set_allocator
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 def declared_symbols() -> list[str]:
     """Entry points declared in include/lbm.h."""
     text = open(HEADER).read()
@@ -155,6 +160,10 @@ def lib():
         L.lbm_body_force_to_device.argtypes = [vp, vp]
         L.lbm_body_force_to_device.restype = C.c_int
         L.lbm_sum_body_force.argtypes = [vp, vp, C.c_int]
+        L.lbm_set_allocator.argtypes = [vp, _ALLOC_FN, _RELEASE_FN, vp]
+        L.lbm_set_allocator.restype = C.c_int
+        L.lbm_init_equilibrium.argtypes = [vp, vp, vp]
+        L.lbm_init_equilibrium.restype = C.c_int
         L.lbm_refine_create.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(vp)]
         L.lbm_refine_create.restype = C.c_int
         L.lbm_refine_init.argtypes = [vp]
@@ -348,6 +357,44 @@ class Lattice:
         self._check(lib().lbm_init_state(self._ctx, t_rho.data_ptr(), t_u.data_ptr(),
                                          t_xi.data_ptr() if t_xi is not None else None, float(amp)))
         self.stream.synchronize()
+
+    def init_equilibrium(self, rho, u):
+        """f = f^eq(rho, u) (lbm_init_equilibrium); rho (nz,ny,nx), u (nz,ny,nx,3)."""
+        torch = _torch()
+        with torch.cuda.stream(self.stream):
+            t_rho = torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64)).to(self.device)
+            t_u = torch.as_tensor(np.ascontiguousarray(u, dtype=np.float64)).to(self.device)
+        self.stream.synchronize()
+        self._check(lib().lbm_init_equilibrium(self._ctx, t_rho.data_ptr(), t_u.data_ptr()))
+        self.stream.synchronize()
+
+    def use_allocator(self, alloc, release):
+        """Route the library's device scratch of this lattice through Python
+        callables (lbm_set_allocator): alloc(nbytes, stream) -> device address
+        (int) or None, release(address, stream).  Call before set_geometry."""
+        def a(nbytes, stream, user):
+            try:
+                p = alloc(int(nbytes), stream)
+            except Exception:
+                return None
+            return int(p) if p else None
+
+        def r(ptr, stream, user):
+            try:
+                release(int(ptr), stream)
+            except Exception:
+                pass
+        cbs = (_ALLOC_FN(a), _RELEASE_FN(r))
+        self._check(lib().lbm_set_allocator(self._ctx, cbs[0], cbs[1], None))
+        self._alloc_cbs = cbs  # kept alive as long as the context
+
+    def use_torch_allocator(self):
+        """The library's scratch of this lattice from PyTorch's caching
+        allocator (on the lattice's device and stream)."""
+        torch = _torch()
+        dev = self.device.index
+        self.use_allocator(lambda n, stream: torch.cuda.caching_allocator_alloc(n, dev, stream),
+                           lambda p, stream: torch.cuda.caching_allocator_delete(p))
 
     def set_geometry(self, g: Geometry):
         self._check(lib().lbm_set_geometry(self._ctx, C.byref(g)))

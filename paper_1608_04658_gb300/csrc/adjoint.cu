@@ -1213,14 +1213,17 @@ lbm_status afail(lbm_ctx *c, lbm_status st, const std::string &msg)
         }                                                                                               \
     } while (0)
 
-// device buffers of one adjoint call, released together
+// device buffers of one adjoint call (through the context's allocator),
+// released together once the context's streams are idle
 struct AdjBuffers {
+    lbm_ctx *ctx;
     std::vector<void *> ptrs;
+    explicit AdjBuffers(lbm_ctx *c) : ctx(c) {}
     template <typename T>
     bool get(T **p, size_t count)
     {
         void *v = nullptr;
-        if (cudaMalloc(&v, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+        if (ctx_malloc(ctx, &v, count * sizeof(T)) != cudaSuccess) {
             *p = nullptr;
             return false;
         }
@@ -1230,7 +1233,11 @@ struct AdjBuffers {
     }
     ~AdjBuffers()
     {
-        for (void *p : ptrs) cudaFree(p);
+        if (!ptrs.empty()) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaStreamSynchronize(ctx->side);
+        }
+        for (void *p : ptrs) ctx_release(ctx, p);
     }
 };
 
@@ -1442,7 +1449,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     const int cap = body ? ctx->G.cap[0] * ctx->G.cap[1] * ctx->G.cap[2] : 1;
     cudaStream_t s = ctx->stream;
     lbm_status st = LBM_OK;
-    AdjBuffers B;
+    AdjBuffers B(ctx);
     S *ck = nullptr, *seg = nullptr;
     uint8_t *ckflags = nullptr, *segflags = nullptr, *wf[2] = {nullptr, nullptr}, *wrec = nullptr;
     DevBody *ckbody = nullptr, *segbody = nullptr, *adjbody = nullptr, *savebody = nullptr;

@@ -76,14 +76,22 @@ cudaError_t dalloc(T **p, size_t count)
     return cudaMalloc((void **)p, count * sizeof(T));
 }
 
-void free_scratch(Scratch &S, bool keep_body)
+// the body's scratch of lbm_set_geometry (through the context's allocator);
+// the body slots of lbm_create too unless keep_body
+void free_scratch(lbm_ctx *ctx, bool keep_body)
 {
-    cudaFree(S.blist); cudaFree(S.bpos); cudaFree(S.ulist); cudaFree(S.upos); cudaFree(S.bforce);
-    cudaFree(S.partials); cudaFree(S.ticket);
-    cudaFree(S.mesh_rest); cudaFree(S.mesh_pos); cudaFree(S.mesh_vel); cudaFree(S.col_x);
-    cudaFree(S.mesh_tris); cudaFree(S.col_count); cudaFree(S.cell_count); cudaFree(S.cell_tri);
-    cudaFree(S.mesh_status); cudaFree(S.tri_box); cudaFree(S.mesh_ipos); cudaFree(S.mesh_frac);
-    cudaFree(S.mesh_partials); cudaFree(S.mesh_ticket);
+    Scratch &S = ctx->S;
+    // a caller's allocator may hand the blocks out again at once
+    if (ctx->dev_release && ctx->live_blocks) {
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->side) cudaStreamSynchronize(ctx->side);
+    }
+    for (void *p : {(void *)S.blist, (void *)S.bpos, (void *)S.ulist, (void *)S.upos, (void *)S.bforce,
+                    (void *)S.partials, (void *)S.ticket, (void *)S.mesh_rest, (void *)S.mesh_pos,
+                    (void *)S.mesh_vel, (void *)S.col_x, (void *)S.mesh_tris, (void *)S.col_count,
+                    (void *)S.cell_count, (void *)S.cell_tri, (void *)S.mesh_status, (void *)S.tri_box,
+                    (void *)S.mesh_ipos, (void *)S.mesh_frac, (void *)S.mesh_partials, (void *)S.mesh_ticket})
+        ctx_release(ctx, p);
     DevBody *b = S.body;
     S = Scratch{};
     if (keep_body) S.body = b;
@@ -139,7 +147,7 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     ctx->flags = flags;
     ctx->stream = (cudaStream_t)stream;
     if (dalloc(&ctx->S.body, 2) != cudaSuccess || dalloc(&ctx->tot_partials, (size_t)ctx->tot_blocks * 5) != cudaSuccess) {
-        free_scratch(ctx->S, false);
+        free_scratch(ctx, false);
         cudaFree(ctx->tot_partials);
         delete ctx;
         return LBM_ERR_OOM;
@@ -154,7 +162,7 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     if (!trial_ok || cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        free_scratch(ctx->S, false);
+        free_scratch(ctx, false);
         cudaFree(ctx->tot_partials);
         if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -168,7 +176,7 @@ lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t *flags,
     if (cudaMemcpyAsync(ctx->S.body, zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(flags, 0, (size_t)N, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        free_scratch(ctx->S, false);
+        free_scratch(ctx, false);
         cudaFree(ctx->tot_partials);
         delete ctx;
         return LBM_ERR_CUDA;
@@ -182,6 +190,12 @@ void lbm_destroy(lbm_ctx *ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     cudaStreamSynchronize(ctx->side);
+    if (ctx->copy) cudaStreamSynchronize(ctx->copy);
+    // the scratch goes back while the streams still exist (a caller's
+    // allocator is given the context's stream with each block)
+    free_scratch(ctx, false);
+    ctx_release(ctx, ctx->plane);
+    ctx->plane = nullptr;
     for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
@@ -194,10 +208,21 @@ void lbm_destroy(lbm_ctx *ctx)
         for (cudaEvent_t e : ctx->ev_slot) cudaEventDestroy(e);
         cudaStreamDestroy(ctx->copy);
     }
-    free_scratch(ctx->S, false);
-    cudaFree(ctx->plane);
     cudaFree(ctx->tot_partials);
     delete ctx;
+}
+
+lbm_status lbm_set_allocator(lbm_ctx *ctx, lbm_alloc_fn alloc, lbm_release_fn release, void *user)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(ctx, LBM_ERR_ARG, "lbm_set_allocator: give both functions or neither");
+    if (ctx->live_blocks != 0)
+        return fail(ctx, LBM_ERR_STATE, "lbm_set_allocator: the context already holds scratch from another allocator");
+    ctx->dev_alloc = alloc;
+    ctx->dev_release = release;
+    ctx->alloc_user = user;
+    return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -241,6 +266,11 @@ lbm_status lbm_init_state(lbm_ctx *ctx, const double *rho, const double *u, cons
     return init_state<double>(ctx, rho, u, xi, amp, "lbm_init_state");
 }
 
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u)
+{
+    return init_state<double>(ctx, rho, u, nullptr, 0.0, "lbm_init_equilibrium");
+}
+
 lbm_status lbm_init_state_f32(lbm_ctx *ctx, const float *rho, const float *u, const float *xi, double amp)
 {
     return init_state<float>(ctx, rho, u, xi, amp, "lbm_init_state_f32");
@@ -255,7 +285,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     const Lattice &L = ctx->L;
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "sync");
     LBM_CUDA(drain_records(ctx), "record copies");
-    free_scratch(ctx->S, true);
+    free_scratch(ctx, true);
     // until the new body is in place the context has none and no node is
     // marked, so a call that fails below leaves a consistent bodiless context
     ctx->has_body = false;
@@ -433,24 +463,24 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
     S.n_partials = 64;
     bool ok = true;
     if (body) {
-        ok = dalloc(&S.blist, vol) == cudaSuccess && dalloc(&S.bpos, vol) == cudaSuccess &&
-             dalloc(&S.ulist, vol) == cudaSuccess && dalloc(&S.upos, vol) == cudaSuccess &&
-             dalloc(&S.bforce, vol * 6) == cudaSuccess &&
-             dalloc(&S.partials, (size_t)S.n_partials * 6) == cudaSuccess && dalloc(&S.ticket, 1) == cudaSuccess;
+        ok = ctx_alloc(ctx, &S.blist, vol) == cudaSuccess && ctx_alloc(ctx, &S.bpos, vol) == cudaSuccess &&
+             ctx_alloc(ctx, &S.ulist, vol) == cudaSuccess && ctx_alloc(ctx, &S.upos, vol) == cudaSuccess &&
+             ctx_alloc(ctx, &S.bforce, vol * 6) == cudaSuccess &&
+             ctx_alloc(ctx, &S.partials, (size_t)S.n_partials * 6) == cudaSuccess && ctx_alloc(ctx, &S.ticket, 1) == cudaSuccess;
         if (ok) ok = cudaMemsetAsync(S.ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
     }
     if (ok && g->kind == LBM_BODY_MESH) {
         const size_t nv = (size_t)G.n_vertices, nt = (size_t)G.n_triangles;
         const size_t ncols = (size_t)G.cap[1] * G.cap[2];
         const size_t ncells = (size_t)G.cells[0] * G.cells[1] * G.cells[2];
-        ok = dalloc(&S.mesh_rest, 3 * nv) == cudaSuccess && dalloc(&S.mesh_pos, 3 * nv) == cudaSuccess &&
-             dalloc(&S.mesh_vel, 3 * nv) == cudaSuccess && dalloc(&S.mesh_tris, 3 * nt) == cudaSuccess &&
-             dalloc(&S.tri_box, 6 * nt) == cudaSuccess && dalloc(&S.col_count, ncols) == cudaSuccess &&
-             dalloc(&S.col_x, ncols * MESH_COL_CAP) == cudaSuccess && dalloc(&S.cell_count, ncells) == cudaSuccess &&
-             dalloc(&S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && dalloc(&S.mesh_status, 1) == cudaSuccess &&
-             dalloc(&S.mesh_ipos, 3 * nv) == cudaSuccess && dalloc(&S.mesh_frac, 3 * nv) == cudaSuccess &&
-             dalloc(&S.mesh_partials, (nt + MESH_THREADS - 1) / MESH_THREADS * 11) == cudaSuccess &&
-             dalloc(&S.mesh_ticket, 1) == cudaSuccess;
+        ok = ctx_alloc(ctx, &S.mesh_rest, 3 * nv) == cudaSuccess && ctx_alloc(ctx, &S.mesh_pos, 3 * nv) == cudaSuccess &&
+             ctx_alloc(ctx, &S.mesh_vel, 3 * nv) == cudaSuccess && ctx_alloc(ctx, &S.mesh_tris, 3 * nt) == cudaSuccess &&
+             ctx_alloc(ctx, &S.tri_box, 6 * nt) == cudaSuccess && ctx_alloc(ctx, &S.col_count, ncols) == cudaSuccess &&
+             ctx_alloc(ctx, &S.col_x, ncols * MESH_COL_CAP) == cudaSuccess && ctx_alloc(ctx, &S.cell_count, ncells) == cudaSuccess &&
+             ctx_alloc(ctx, &S.cell_tri, ncells * MESH_CELL_CAP) == cudaSuccess && ctx_alloc(ctx, &S.mesh_status, 1) == cudaSuccess &&
+             ctx_alloc(ctx, &S.mesh_ipos, 3 * nv) == cudaSuccess && ctx_alloc(ctx, &S.mesh_frac, 3 * nv) == cudaSuccess &&
+             ctx_alloc(ctx, &S.mesh_partials, (nt + MESH_THREADS - 1) / MESH_THREADS * 11) == cudaSuccess &&
+             ctx_alloc(ctx, &S.mesh_ticket, 1) == cudaSuccess;
         if (ok) ok = cudaMemsetAsync(S.mesh_ticket, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
         if (ok)
             ok = cudaMemcpy(S.mesh_rest, g->mesh_rest, 3 * nv * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -471,7 +501,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         G.mesh_ticket = S.mesh_ticket;
     }
     if (!ok) {
-        free_scratch(ctx->S, true);
+        free_scratch(ctx, true);
         return fail(ctx, LBM_ERR_OOM, "lbm_set_geometry: device allocation failed");
     }
     DevBody hb[2] = {};
@@ -497,7 +527,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
         LBM_CUDA(cudaMemcpyAsync(&mst, S.mesh_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "mesh status");
         LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
         if (mst) {
-            free_scratch(ctx->S, true);
+            free_scratch(ctx, true);
             // no body: no node stays marked
             LBM_CUDA(cudaMemsetAsync(ctx->flags, 0, (size_t)L.N, ctx->stream), "flags clear");
             LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_geometry");
@@ -778,7 +808,7 @@ int64_t lbm_kernel_launches(const lbm_ctx *ctx) { return ctx ? ctx->launches : -
 static lbm_status ensure_plane(lbm_ctx *ctx)
 {
     if (ctx->plane) return LBM_OK;
-    if (dalloc(&ctx->plane, (size_t)ctx->L.N) != cudaSuccess)
+    if (ctx_alloc(ctx, &ctx->plane, (size_t)ctx->L.N) != cudaSuccess)
         return fail(ctx, LBM_ERR_OOM, "plane buffer allocation failed");
     return LBM_OK;
 }

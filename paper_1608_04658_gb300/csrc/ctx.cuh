@@ -58,7 +58,47 @@ struct lbm_ctx {
     // lbm_step_interior has enqueued the interior layers of a step that
     // lbm_step_edges completes
     bool interior_pending = false;
+    // caller's device allocator for the scratch (lbm_set_allocator; null:
+    // cudaMalloc / cudaFree) and the number of live blocks taken through
+    // ctx_malloc
+    lbm_alloc_fn dev_alloc = nullptr;
+    lbm_release_fn dev_release = nullptr;
+    void *alloc_user = nullptr;
+    long long live_blocks = 0;
 };
+
+// device scratch of a context, through the caller's allocator when one is set
+inline cudaError_t ctx_malloc(lbm_ctx *ctx, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 1;
+    if (ctx->dev_alloc) {
+        *p = ctx->dev_alloc(bytes, (void *)ctx->stream, ctx->alloc_user);
+        if (!*p) return cudaErrorMemoryAllocation;
+    } else {
+        const cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return e;
+        }
+    }
+    ctx->live_blocks++;
+    return cudaSuccess;
+}
+template <typename T>
+inline cudaError_t ctx_alloc(lbm_ctx *ctx, T **p, size_t count)
+{
+    void *v = nullptr;
+    const cudaError_t e = ctx_malloc(ctx, &v, count * sizeof(T));
+    *p = static_cast<T *>(v);
+    return e;
+}
+inline void ctx_release(lbm_ctx *ctx, void *p)
+{
+    if (!p) return;
+    if (ctx->dev_release) ctx->dev_release(p, (void *)ctx->stream, ctx->alloc_user);
+    else cudaFree(p);
+    ctx->live_blocks--;
+}
 
 // records the start (which = 0) or stop (1) event of a profiled bulk launch
 // on the context stream while a profile (lbm_profile_begin) is open

@@ -385,10 +385,8 @@ void release(lbm_refine *r)
 {
     for (cudaEvent_t e : {r->ev_fork, r->ev_fine1, r->ev_fill, r->ev_side})
         if (e) cudaEventDestroy(e);
-    cudaFree(r->M[0]);
-    cudaFree(r->M[1]);
-    cudaFree(r->Mh);
-    cudaFree(r->sweep);
+    // the scratch came from the coarse context's allocator
+    for (void *p : {r->M[0], r->M[1], r->Mh, (void *)r->sweep}) ctx_release(r->c, p);
     delete r;
 }
 
@@ -523,9 +521,10 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
     const size_t rsz = coarse->storage == LBM_FP64 ? sizeof(double) : sizeof(float);
     const SurfBox SC = r->B.coarse_box();
     const size_t nbox = (size_t)SC.E[0] * SC.E[1] * SC.E[2];
-    if (cudaMalloc(&r->M[0], NMOM * nbox * rsz) != cudaSuccess || cudaMalloc(&r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
-        cudaMalloc(&r->Mh, NMOM * nbox * rsz) != cudaSuccess ||
-        cudaMalloc((void **)&r->sweep, 6 * sizeof(int)) != cudaSuccess ||
+    if (ctx_malloc(coarse, &r->M[0], NMOM * nbox * rsz) != cudaSuccess ||
+        ctx_malloc(coarse, &r->M[1], NMOM * nbox * rsz) != cudaSuccess ||
+        ctx_malloc(coarse, &r->Mh, NMOM * nbox * rsz) != cudaSuccess ||
+        ctx_alloc(coarse, &r->sweep, 6) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fine1, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_fill, cudaEventDisableTiming) != cudaSuccess ||

@@ -89,6 +89,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
                L.lbm_set_body_force(None, d6, d6), L.lbm_init_state(None, dummy, dummy, None, 0.0),
                L.lbm_init_state_f32(None, dummy, dummy, None, 0.0)):
         assert rc == binding.LBM_ERR_ARG
+    # the allocator hook and the equilibrium initialisation, null context
+    assert L.lbm_set_allocator(None, binding._ALLOC_FN(), binding._RELEASE_FN(), None) == binding.LBM_ERR_ARG
+    assert L.lbm_init_equilibrium(None, dummy, dummy) == binding.LBM_ERR_ARG
     # the refinement entry points, null contexts and handles
     r = C.c_void_p(7)
     i3 = (C.c_int32 * 3)(1, 1, 1)
