@@ -1569,6 +1569,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double 
     {
         bool first = true;
         for (int sg = nseg - 1; sg >= 0; --sg) {
+            NvtxRange nvtx_seg("adjoint segment");  // its recompute and its reversed steps
             const int t0 = sg * K, t1 = std::min(T, t0 + K);
             // recompute the segment: seg[j] holds St^{t0+j} once step t0+j has run
             ADJ_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sg * state, state * sizeof(S), cudaMemcpyDeviceToDevice, s),
@@ -1660,6 +1661,7 @@ done:
 
 extern "C" lbm_status lbm_adjoint_step(lbm_ctx *ctx, const lbm_adjoint *spec, double *J, double dJ_dtheta[3])
 {
+    NvtxRange nvtx_("lbm_adjoint_step");
     if (!ctx) return LBM_ERR_ARG;
     if (!spec || !J || !dJ_dtheta) return afail(ctx, LBM_ERR_ARG, "lbm_adjoint_step: null argument");
     if (spec->horizon < 1 || spec->checkpoint_every < 0)

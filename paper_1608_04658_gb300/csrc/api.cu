@@ -248,6 +248,7 @@ static const T *device_view(const T *p)
 template <typename T>
 static lbm_status init_state(lbm_ctx *ctx, const T *rho, const T *u, const T *xi, double amp, const char *name)
 {
+    NvtxRange nvtx_(name);
     if (!ctx) return LBM_ERR_ARG;
     if (!rho || !u) return fail(ctx, LBM_ERR_ARG, std::string(name) + ": rho and u are required");
     const T *drho = device_view(rho), *du = device_view(u), *dxi = xi ? device_view(xi) : nullptr;
@@ -278,6 +279,7 @@ lbm_status lbm_init_state_f32(lbm_ctx *ctx, const float *rho, const float *u, co
 
 lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g)
 {
+    NvtxRange nvtx_("lbm_set_geometry");
     if (!ctx) return LBM_ERR_ARG;
     if (!g) return fail(ctx, LBM_ERR_ARG, "lbm_set_geometry: null geometry");
     if (g->kind < LBM_BODY_NONE || g->kind > LBM_BODY_MESH)
@@ -640,6 +642,7 @@ static void choose_order(lbm_ctx *ctx)
 
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
 {
+    NvtxRange nvtx_("lbm_step");
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "lbm_step: nsteps < 0");
     if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step: state not initialised");
@@ -713,6 +716,7 @@ static void interior_range(const lbm_ctx *ctx, int &lo, int &hi)
 
 lbm_status lbm_step_interior(lbm_ctx *ctx)
 {
+    NvtxRange nvtx_("lbm_step_interior");
     if (!ctx) return LBM_ERR_ARG;
     if (!ctx->initialised) return fail(ctx, LBM_ERR_STATE, "lbm_step_interior: state not initialised");
     if (ctx->slab_zper <= 0) return fail(ctx, LBM_ERR_STATE, "lbm_step_interior: not a slab (lbm_set_slab)");
@@ -744,6 +748,7 @@ lbm_status lbm_step_interior(lbm_ctx *ctx)
 
 lbm_status lbm_step_edges(lbm_ctx *ctx)
 {
+    NvtxRange nvtx_("lbm_step_edges");
     if (!ctx) return LBM_ERR_ARG;
     if (!ctx->interior_pending) {
         if (ctx->slab_zper <= 0) return fail(ctx, LBM_ERR_STATE, "lbm_step_edges: not a slab (lbm_set_slab)");
@@ -815,6 +820,7 @@ static lbm_status ensure_plane(lbm_ctx *ctx)
 
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *host_f)
 {
+    NvtxRange nvtx_("lbm_get_populations");
     if (!ctx) return LBM_ERR_ARG;
     if (!host_f) return fail(ctx, LBM_ERR_ARG, "lbm_get_populations: null output");
     lbm_status st = ensure_plane(ctx);
@@ -957,6 +963,7 @@ lbm_status lbm_reset_average(lbm_ctx *ctx)
 
 lbm_status lbm_totals(lbm_ctx *ctx, double out[5])
 {
+    NvtxRange nvtx_("lbm_totals");
     if (!ctx) return LBM_ERR_ARG;
     if (!out) return fail(ctx, LBM_ERR_ARG, "lbm_totals: null output");
     const uint8_t *fl = ctx->has_body ? ctx->flags : nullptr;

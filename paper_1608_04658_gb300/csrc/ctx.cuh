@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "body.cuh"
 
 // launch orders of a step whose band is known ahead (see lbm_step); the
@@ -99,6 +101,16 @@ inline void ctx_release(lbm_ctx *ctx, void *p)
     else cudaFree(p);
     ctx->live_blocks--;
 }
+
+// An NVTX range over one library call or phase, named after it: ncu and
+// nsys can select the kernels enqueued inside it (ncu --nvtx --nvtx-include
+// "lbm_refine_step/"); without a tool attached the push and pop do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // records the start (which = 0) or stop (1) event of a profiled bulk launch
 // on the context stream while a profile (lbm_profile_begin) is open

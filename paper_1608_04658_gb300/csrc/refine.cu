@@ -560,6 +560,7 @@ void lbm_refine_destroy(lbm_refine *r)
 
 lbm_status lbm_refine_init(lbm_refine *r)
 {
+    NvtxRange nvtx_("lbm_refine_init");
     if (!r) return LBM_ERR_ARG;
     if (!r->c->initialised || !r->f->initialised)
         return rfail(r->c, LBM_ERR_STATE, "lbm_refine_init: both levels must hold their initial state");
@@ -580,6 +581,7 @@ lbm_status lbm_refine_init(lbm_refine *r)
 
 lbm_status lbm_refine_step(lbm_refine *r, int nsteps)
 {
+    NvtxRange nvtx_("lbm_refine_step");
     if (!r) return LBM_ERR_ARG;
     if (nsteps < 0) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_step: nsteps < 0");
     if (!r->ready) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_step: lbm_refine_init has not run");
