@@ -632,6 +632,22 @@ def accuracy_bench(args, device):
     return out
 
 
+def refined_counts(shape, lo, hi):
+    """(coarse nodes updated, fine interior nodes, node updates per coarse
+    step) of a refined step: the coarse level skips the block's inside
+    (closed axes strictly between lo and hi, a spanned axis - lo = 0, hi = n
+    - whole), the fine level updates its interior twice (closed axes 1 .. 2m
+    - 1 of its 2m + 2 nodes, a spanned axis all 2n)."""
+    full = [l == 0 and h == n for l, h, n in zip(lo, hi, shape)]
+    inside = fine_interior = 1
+    for a in range(3):
+        m = hi[a] - lo[a]
+        inside *= shape[a] if full[a] else m - 1
+        fine_interior *= 2 * shape[a] if full[a] else 2 * m - 1
+    coarse_updated = shape[0] * shape[1] * shape[2] - inside
+    return coarse_updated, fine_interior, coarse_updated + 2 * fine_interior
+
+
 def refine_bench(args, world, device, clocks):
     """The two-level block refinement (lbm_refine_step; Sec. 4.2's two-level
     grid) on two workloads: the bodiless refined block (FP32 and FP16) and
@@ -661,13 +677,7 @@ def refine_run(args, world, device, clocks, wl, storages):
     import synth
     (nx, ny, nz), lo, hi = wl["shape"], wl["lo"], wl["hi"]
     full = [l == 0 and h == n for l, h, n in zip(lo, hi, wl["shape"])]
-    inside = fine_interior = 1
-    for a in range(3):
-        m = hi[a] - lo[a]
-        inside *= wl["shape"][a] if full[a] else m - 1
-        fine_interior *= 2 * wl["shape"][a] if full[a] else 2 * m - 1
-    coarse_updated = nx * ny * nz - inside
-    per_step = coarse_updated + 2 * fine_interior
+    coarse_updated, fine_interior, per_step = refined_counts(wl["shape"], lo, hi)
     K, W = args.steps, args.warmup
     peak, peak_kind = measured_hbm_peak()
     body = "airfoil" in wl["name"]
@@ -800,13 +810,7 @@ def refine_cpu_baseline(wl, body: bool):
     r = oracle.RefinedOracle(o, lo, hi, fine_body=fb)
     r.fine.init_state(*synth.uniform_fields(r.fine.shape, wl["u_face"]))
     r.init()
-    full = [l == 0 and h == n for l, h, n in zip(lo, hi, shape)]
-    inside = fine_interior = 1
-    for a in range(3):
-        m = hi[a] - lo[a]
-        inside *= shape[a] if full[a] else m - 1
-        fine_interior *= 2 * shape[a] if full[a] else 2 * m - 1
-    per_step = shape[0] * shape[1] * shape[2] - inside + 2 * fine_interior
+    per_step = refined_counts(shape, lo, hi)[2]
     t0 = time.perf_counter()
     r.step(steps)
     t = time.perf_counter() - t0

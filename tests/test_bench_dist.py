@@ -170,3 +170,26 @@ def test_hbm_peak_comes_from_the_measured_file_else_the_fallback(tmp_path, monke
     assert bench.measured_hbm_peak() == (6680.2, "measured (hbm_gbs)")
     (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
     assert bench.measured_hbm_peak()[1] == "fallback"
+
+
+def test_refined_node_counts_match_the_levels_masks():
+    """The node updates the refinement lines count per coarse step equal the
+    nodes the refined step updates, counted from the masks of what each level
+    computes (coarse: all but the block's inside; fine: the interior, twice),
+    for a closed block and for one spanning the periodic z axis."""
+    import numpy as np
+
+    import bench
+    for shape, lo, hi in (((64, 32, 16), (16, 8, 2), (47, 23, 13)), ((64, 48, 4), (8, 8, 0), (55, 39, 4))):
+        full = [l == 0 and h == n for l, h, n in zip(lo, hi, shape)]
+        inside = np.ones(shape[::-1], dtype=bool)
+        sl = [slice(None) if f else slice(l + 1, h) for l, h, f in zip(lo, hi, full)]
+        mask = np.zeros(shape[::-1], dtype=bool)
+        mask[sl[2], sl[1], sl[0]] = True
+        coarse = int((inside & ~mask).sum())
+        fshape = [2 * n if f else 2 * (h - l) + 2 for l, h, n, f in zip(lo, hi, shape, full)]
+        fmask = np.zeros(fshape[::-1], dtype=bool)
+        fsl = [slice(None) if f else slice(1, 2 * (h - l)) for l, h, f in zip(lo, hi, full)]
+        fmask[fsl[2], fsl[1], fsl[0]] = True
+        fine = int(fmask.sum())
+        assert bench.refined_counts(shape, lo, hi) == (coarse, fine, coarse + 2 * fine)
