@@ -580,6 +580,18 @@ class Lattice:
         return out
 
 
+def fine_shape(coarse_shape, faces, lo, hi):
+    """(spanned axes, fine lattice shape) of a ratio-2 block over the coarse
+    nodes [lo, hi]: an axis with lo = 0, hi = n and periodic faces is spanned
+    (2n fine nodes), any other holds 2 (hi - lo) + 2 (the block's 2m + 1
+    nodes and a pad)."""
+    full = tuple(int(l) == 0 and int(h) == int(n) and int(faces[2 * a]) == FACE_PERIODIC
+                 for a, (l, h, n) in enumerate(zip(lo, hi, coarse_shape)))
+    shape = tuple(2 * int(n) if f else 2 * (int(h) - int(l)) + 2
+                  for l, h, n, f in zip(lo, hi, coarse_shape, full))
+    return full, shape
+
+
 def fine_nu(nu: float) -> float:
     """Viscosity of the fine level of a ratio-2 block in its own lattice units
     (acoustic scaling: twice the coarse value)."""
@@ -602,11 +614,7 @@ class Refinement:
         self.lo = tuple(int(v) for v in lo)
         self.hi = tuple(int(v) for v in hi)
         p = coarse.params
-        # lo = 0, hi = n on a periodic axis: the block spans it (2n fine nodes)
-        self.full = tuple(l == 0 and h == n and p.face[2 * a] == FACE_PERIODIC
-                          for a, (l, h, n) in enumerate(zip(self.lo, self.hi, coarse.shape)))
-        shape = tuple(2 * n if f else 2 * (h - l) + 2
-                      for l, h, n, f in zip(self.lo, self.hi, coarse.shape, self.full))
+        self.full, shape = fine_shape(coarse.shape, list(p.face), self.lo, self.hi)
         self.fine = Lattice(shape, fine_nu(p.nu), coarse.storage, rho0=coarse.rho0, gamma_mode=p.gamma_mode,
                             device=coarse.device)
         r = C.c_void_p()

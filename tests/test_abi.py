@@ -116,3 +116,15 @@ def test_product_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "kbc_oracle" not in text, f
+
+
+def test_fine_shape_of_closed_and_spanning_blocks():
+    """The binding sizes the fine lattice as lbm_refine_create requires: 2 (hi -
+    lo) + 2 nodes along a closed axis, 2n along a spanned periodic one; a
+    block reaching both ends of a non-periodic axis is not spanning."""
+    from paper_1608_04658_gb300 import binding
+    assert binding.fine_shape((24, 20, 18), (0,) * 6, (5, 4, 3), (16, 13, 12)) == \
+        ((False, False, False), (24, 20, 20))
+    assert binding.fine_shape((48, 32, 4), (2, 3, 2, 2, 0, 0), (12, 8, 0), (35, 23, 4)) == \
+        ((False, False, True), (48, 32, 8))
+    assert binding.fine_shape((16, 12, 10), (0, 0, 0, 0, 1, 1), (4, 3, 0), (11, 8, 10))[0] == (False, False, False)
