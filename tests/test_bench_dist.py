@@ -193,3 +193,16 @@ def test_refined_node_counts_match_the_levels_masks():
         fmask[fsl[2], fsl[1], fsl[0]] = True
         fine = int(fmask.sum())
         assert bench.refined_counts(shape, lo, hi) == (coarse, fine, coarse + 2 * fine)
+
+
+def test_refined_cpu_baseline_line_is_well_formed():
+    """The refinement lines' oracle baseline runs the refined oracle on its
+    bounded crops (closed block; spanning block with the airfoil) and reports
+    node updates per second in the GPU line's unit."""
+    import bench
+    import synth
+    for wl, body in ((synth.refined_block(), False), (synth.refined_airfoil(), True)):
+        r = bench.refine_cpu_baseline(wl, body)
+        assert r["kind"] == "oracle" and r["unit"] == "GLUPS" and r["cores"] == 1
+        assert 0 < r["value"] < 1e-1 and r["seconds"] > 0
+        assert "FP64, one thread" in r["sample"]
