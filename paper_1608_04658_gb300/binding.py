@@ -299,6 +299,7 @@ class Lattice:
             raise LbmError(st, "lbm_create failed")
         self._ctx = ctx
         self._keep = []
+        self._dependents = []  # weak references to the refinements that use this lattice
 
     # -------------------------------------------------------------- helpers
     def _check(self, st: int):
@@ -306,6 +307,11 @@ class Lattice:
             raise LbmError(st, lib().lbm_last_error(self._ctx).decode())
 
     def close(self):
+        # a refinement keeps pointers to its levels: it goes first
+        for ref in getattr(self, "_dependents", ()):
+            dep = ref()
+            if dep is not None:
+                dep.close()
         if getattr(self, "_ctx", None):
             lib().lbm_destroy(self._ctx)
             self._ctx = None
@@ -624,6 +630,9 @@ class Refinement:
         if st != LBM_OK:
             raise LbmError(st, lib().lbm_last_error(coarse._ctx).decode())
         self._r = r
+        import weakref
+        coarse._dependents.append(weakref.ref(self))
+        self.fine._dependents.append(weakref.ref(self))
 
     def close(self):
         if getattr(self, "_r", None):

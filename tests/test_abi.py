@@ -128,3 +128,32 @@ def test_fine_shape_of_closed_and_spanning_blocks():
     assert binding.fine_shape((48, 32, 4), (2, 3, 2, 2, 0, 0), (12, 8, 0), (35, 23, 4)) == \
         ((False, False, True), (48, 32, 8))
     assert binding.fine_shape((16, 12, 10), (0, 0, 0, 0, 1, 1), (4, 3, 0), (11, 8, 10))[0] == (False, False, False)
+
+
+def test_closing_a_lattice_first_closes_its_refinements(monkeypatch):
+    """A refinement keeps pointers to both levels, so closing either Lattice
+    destroys the refinement before the context (library calls recorded, not
+    made)."""
+    import weakref
+    from paper_1608_04658_gb300 import binding
+    calls = []
+
+    class Rec:
+        def lbm_destroy(self, ctx):
+            calls.append(("destroy", ctx))
+
+        def lbm_refine_destroy(self, r):
+            calls.append(("refine_destroy", r))
+
+    monkeypatch.setattr(binding, "lib", lambda: Rec())
+    coarse = binding.Lattice.__new__(binding.Lattice)
+    fine = binding.Lattice.__new__(binding.Lattice)
+    coarse._ctx, fine._ctx, coarse._dependents, fine._dependents = "c", "f", [], []
+    ref = binding.Refinement.__new__(binding.Refinement)
+    ref._r, ref.coarse, ref.fine = "r", coarse, fine
+    coarse._dependents.append(weakref.ref(ref))
+    fine._dependents.append(weakref.ref(ref))
+    coarse.close()
+    fine.close()
+    ref.close()
+    assert calls == [("refine_destroy", "r"), ("destroy", "c"), ("destroy", "f")]
