@@ -204,7 +204,9 @@ LBM_API lbm_status lbm_create(const lbm_params *p, void *f_a, void *f_b, uint8_t
  *   alloc(bytes, stream, user)  returns device memory of the context's device,
  *                               at least 256-byte aligned, or NULL (the
  *                               calling entry point then fails with
- *                               LBM_ERR_OOM); stream is the context's stream;
+ *                               LBM_ERR_OOM; a block that is not 256-byte
+ *                               aligned is given back at once and counts as
+ *                               NULL); stream is the context's stream;
  *   release(ptr, stream, user)  gives a block back; the library calls it only
  *                               when no work of its own that uses the block
  *                               is still in flight on any stream.
@@ -543,7 +545,9 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * lbm_get_populations as usual.  Do not call lbm_step on either context of a
  * coupled pair.  Coarse nodes more than one layer inside the block's surface
  * and the fine pad hold no defined state.  LBM_ERR_STATE before
- * lbm_refine_init, or once the coarse context has been given a body.  A fine profile (lbm_profile_begin on the fine context)
+ * lbm_refine_init, or once the coarse context has been given a body.
+ * lbm_kernel_launches(coarse) then counts the kernels the call enqueued
+ * (seven per coarse step, plus a fine body's chain).  A fine profile (lbm_profile_begin on the fine context)
  * times the fine bulk launches.
  *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two

@@ -76,6 +76,12 @@ inline cudaError_t ctx_malloc(lbm_ctx *ctx, void **p, size_t bytes)
     if (ctx->dev_alloc) {
         *p = ctx->dev_alloc(bytes, (void *)ctx->stream, ctx->alloc_user);
         if (!*p) return cudaErrorMemoryAllocation;
+        // the kernels' vector accesses need the alignment cudaMalloc gives
+        if (reinterpret_cast<uintptr_t>(*p) & 255u) {
+            ctx->dev_release(*p, (void *)ctx->stream, ctx->alloc_user);
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
     } else {
         const cudaError_t e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {

@@ -90,6 +90,32 @@ def test_allocator_refusal_and_state_rules():
     lat.close()
 
 
+def test_misaligned_blocks_are_refused():
+    """A block that is not 256-byte aligned goes straight back to the caller
+    and the call fails with LBM_ERR_OOM, before any kernel could see it."""
+    import torch
+
+    import paper_1608_04658_gb300 as lbm
+    from paper_1608_04658_gb300 import binding
+    lat = lbm.Lattice((24, 20, 22), 0.02, storage="fp32", faces=(1, 1, 1, 1, 0, 0))
+    dev = lat.device.index
+    held, returned = [], []
+
+    def alloc(n, stream):
+        p = torch.cuda.caching_allocator_alloc(n + 256, dev, stream)
+        held.append(p)
+        return p + 16
+
+    lat.use_allocator(alloc, lambda p, stream: returned.append(p))
+    with pytest.raises(lbm.LbmError) as e:
+        lat.set_geometry(lbm.sphere((11.37, 9.61, 10.83), 4.3))
+    assert e.value.status == binding.LBM_ERR_OOM
+    assert returned == [held[0] + 16]
+    for p in held:
+        torch.cuda.caching_allocator_delete(p)
+    lat.close()
+
+
 def test_refinement_scratch_from_the_coarse_allocator():
     import paper_1608_04658_gb300 as lbm
     from parity_util import random_fields
