@@ -10,8 +10,9 @@ What fixes the refined step independently of its own arithmetic:
     non-equilibrium to second order, an O(U) relative residual (about 5e-6
     at U = 1e-3).  Rescaling the non-equilibrium pressure tensor by 1
     instead of the ratio of the levels' relaxation times (either way), or
-    dropping it, or placing a surface node half a cell off, each leave
-    residuals of 1.7e-3 or more;
+    dropping it, or placing a surface node half a cell off, or restricting
+    from the fine node next to the coincident one, each leave residuals of
+    1.7e-3 or more;
   - a sound wave crossing the block must match the plain single-level
     method run everywhere at the fine resolution (twice the nodes per axis,
     half the time step, twice the viscosity in lattice units) as closely as
