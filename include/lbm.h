@@ -512,18 +512,20 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  *
  * lbm_refine_create couples coarse and fine (both from lbm_create, the same
  * storage, stabilizer, rho0 and stream, no slab) over the block of
- * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2,
- * hi - lo >= 3, unless spanned).  It writes the fine context's flags (the block's surface
- * and the pad marked solid), allocates its own device scratch (three sets of
- * 10 moments per node of the block's coarse box: t, t+1 and their mean)
- * with cudaMalloc and
- * synchronises the stream.  The coarse context must carry no body; the fine
- * one may (below).  Errors: LBM_ERR_ARG for a mismatch, with the
- * reason in lbm_last_error(coarse); LBM_ERR_OOM.  *out is NULL on failure.
+ * coarse nodes [lo, hi] (both ends included, per axis 1 <= lo, hi <= n - 2
+ * and hi - lo >= 3, unless spanned).  It writes the fine context's flags
+ * (the block's surface and the pad marked solid), takes its device scratch
+ * (three sets of 10 moments per node of the block's coarse box: t, t+1 and
+ * their mean) from the coarse context's allocator (cudaMalloc unless
+ * lbm_set_allocator gave another) and synchronises the stream.  The coarse
+ * context must carry no body; the fine one may (below).  Errors:
+ * LBM_ERR_ARG for a mismatch, with the reason in lbm_last_error(coarse);
+ * LBM_ERR_OOM.  *out is NULL on failure.
  *
  * A body on the fine level (lbm_set_geometry on the fine context, before
- * lbm_refine_init): a sphere or a swimmer mesh in fine lattice units (fine
- * node j at fine coordinate j), stepped by the fine level like a lattice of
+ * lbm_refine_init): a sphere, a swimmer mesh, or (in a block spanning z) the
+ * airfoil, in fine lattice units (fine node j at fine coordinate j), stepped
+ * by the fine level like a lattice of
  * its own, two steps per coarse step (its geometry, refill, Grad boundary,
  * force and Euler update each fine step; lbm_body_forces on the fine context
  * reads it in fine units).  Along closed axes its solid nodes must stay four
@@ -547,8 +549,8 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * and the fine pad hold no defined state.  LBM_ERR_STATE before
  * lbm_refine_init, or once the coarse context has been given a body.
  * lbm_kernel_launches(coarse) then counts the kernels the call enqueued
- * (seven per coarse step, plus a fine body's chain).  A fine profile (lbm_profile_begin on the fine context)
- * times the fine bulk launches.
+ * (seven per coarse step, plus a fine body's chain).  A fine profile
+ * (lbm_profile_begin on the fine context) times the fine bulk launches.
  *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two
  * contexts stay valid.  Destroy the coupling before either context: it keeps
