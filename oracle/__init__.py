@@ -12,7 +12,10 @@ Layout of a population array: numpy ``(27, nz, ny, nx)`` float64, direction
 index i = 9(cx+1) + 3(cy+1) + (cz+1).
 
 ``slab.py`` runs the same oracle split into z slabs over CPU ranks (the
-decomposition of one box over several devices, tests/test_oracle_slab.py).
+decomposition of one box over several devices, tests/test_oracle_slab.py);
+``slab_adjoint.py`` runs the adjoint of that split, the halo exchange
+reversed, on the autograd restatement of the bodiless step
+(tests/test_oracle_slab_adjoint.py).
 
 Parity status per function (pins live in tests/test_oracle_*.py):
   feq, kbc_split, collide (all modes), gamma_exact, grad, stream/box faces,
