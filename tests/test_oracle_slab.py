@@ -208,3 +208,60 @@ def test_whole_box_frame_changes_nothing(orc):
     a, b = run(False), run(True)
     assert a[2][2] < 3.0  # the centre wrapped through z = 0
     assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
+
+
+def _crossing_rank(rank, world, port, shape, steps, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+
+    from oracle.slab import decomposed_run_crossing
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, decomposed_run_crossing(shape, NU, FACES, synth.parity_fields(shape, 5), AMP, steps)))
+    finally:
+        dist.destroy_process_group()
+
+
+def _crossing(world, shape, steps):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_crossing_rank, args=(r, world, port, shape, steps, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = {}
+    deadline = time.monotonic() + 300
+    try:
+        while len(got) < world:
+            try:
+                rank, out = q.get(timeout=2)
+                got[rank] = out
+            except queue.Empty:
+                dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+                assert not dead and time.monotonic() < deadline, f"ranks failed: exit codes {dead}"
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    assert all(p.exitcode == 0 for p in procs)
+    return [got[r] for r in range(world)]
+
+
+@pytest.mark.parametrize("world,shape", [(2, (14, 12, 20)), (3, (14, 12, 21))])
+def test_bodiless_slabs_need_only_the_crossing_populations(orc, world, shape):
+    """Without a body near a cut one halo layer of the nine populations that
+    cross it (c_z = +-1) is enough: every other halo value is NaN, and the
+    owned populations still equal the undivided oracle's bit for bit after 6
+    steps, for a sixth of the bytes of the two-layer exchange of all 27."""
+    steps = 6
+    o = orc.Oracle(shape, nu=NU, faces=FACES)
+    o.init_state(*synth.parity_fields(shape, 5), AMP)
+    o.step(steps)
+    ref = o.get_f()
+    parts = _crossing(world, shape, steps)
+    for z0, z1, f, sent in parts:
+        assert np.isfinite(f).all()
+        assert np.array_equal(f, ref[:, z0:z1])
+        nx, ny = shape[0], shape[1]
+        assert sent == 2 * 9 * nx * ny * 8 and 6 * sent == 2 * 2 * 27 * nx * ny * 8
