@@ -552,6 +552,12 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * (seven per coarse step, plus a fine body's chain).  A fine profile
  * (lbm_profile_begin on the fine context) times the fine bulk launches.
  *
+ * Checkpoints: lbm_save / lbm_load each level as usual; the coupling keeps the
+ * coarse surface moments of the last step, which no file holds, so a run
+ * resumed with lbm_refine_init takes them from the loaded coarse populations
+ * (the t = 0 reading) and departs from the uninterrupted run from its first
+ * step on.
+ *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two
  * contexts stay valid.  Destroy the coupling before either context: it keeps
  * pointers to both. */
