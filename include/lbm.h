@@ -552,11 +552,15 @@ LBM_API lbm_status lbm_sum_body_force(lbm_ctx *ctx, const double *parts, int npa
  * (seven per coarse step, plus a fine body's chain).  A fine profile
  * (lbm_profile_begin on the fine context) times the fine bulk launches.
  *
- * Checkpoints: lbm_save / lbm_load each level as usual; the coupling keeps the
- * coarse surface moments of the last step, which no file holds, so a run
- * resumed with lbm_refine_init takes them from the loaded coarse populations
- * (the t = 0 reading) and departs from the uninterrupted run from its first
- * step on.
+ * Checkpoints: lbm_save / lbm_load each level as usual, and lbm_refine_save /
+ * lbm_refine_load the coupling's own state, the coarse surface moments of
+ * the last step (a header naming the block and the storage, then the
+ * moments; synchronises; LBM_ERR_ARG for a file of another coupling,
+ * LBM_ERR_STATE for a save before lbm_refine_init).  Both levels loaded and
+ * lbm_refine_load (in place of lbm_refine_init) continue the run bit for bit.
+ * lbm_refine_init after a load instead takes the moments from the loaded
+ * coarse populations (the t = 0 reading) and departs from the uninterrupted
+ * run from its first step on.
  *
  * lbm_refine_destroy synchronises the stream and frees the scratch; the two
  * contexts stay valid.  Destroy the coupling before either context: it keeps
@@ -566,6 +570,8 @@ LBM_API lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32
                                      lbm_refine **out);
 LBM_API lbm_status lbm_refine_init(lbm_refine *r);
 LBM_API lbm_status lbm_refine_step(lbm_refine *r, int nsteps);
+LBM_API lbm_status lbm_refine_save(lbm_refine *r, const char *path);
+LBM_API lbm_status lbm_refine_load(lbm_refine *r, const char *path);
 LBM_API void lbm_refine_destroy(lbm_refine *r);
 
 /* Global sums without a context and without device allocation.  The paper

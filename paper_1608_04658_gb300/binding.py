@@ -170,6 +170,10 @@ def lib():
         L.lbm_refine_init.restype = C.c_int
         L.lbm_refine_step.argtypes = [vp, C.c_int]
         L.lbm_refine_step.restype = C.c_int
+        L.lbm_refine_save.argtypes = [vp, C.c_char_p]
+        L.lbm_refine_save.restype = C.c_int
+        L.lbm_refine_load.argtypes = [vp, C.c_char_p]
+        L.lbm_refine_load.restype = C.c_int
         L.lbm_refine_destroy.argtypes = [vp]
         L.lbm_refine_destroy.restype = None
         L.lbm_sum_body_force.restype = C.c_int
@@ -650,3 +654,12 @@ class Refinement:
 
     def step(self, n: int = 1):
         self.coarse._check(lib().lbm_refine_step(self._r, int(n)))
+
+    def save(self, path: str):
+        """The coupling's state (lbm_refine_save); save both levels beside it."""
+        self.coarse._check(lib().lbm_refine_save(self._r, str(path).encode()))
+
+    def load(self, path: str):
+        """Resume from lbm_refine_save's file (in place of init()), after both
+        levels have loaded theirs."""
+        self.coarse._check(lib().lbm_refine_load(self._r, str(path).encode()))

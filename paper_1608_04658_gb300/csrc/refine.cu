@@ -31,6 +31,8 @@
 // Moments are kept in the collision's arithmetic (double for FP64 storage,
 // float otherwise) as rho - rho0, u, Pi^neq, one array per quantity.
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -547,6 +549,84 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, const int32_t lo[3]
         return rfail(coarse, LBM_ERR_CUDA, std::string("lbm_refine_create: ") + cudaGetErrorString(e));
     }
     *out = r;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// file of the coupling's state: the coarse surface moments of the last step
+struct RefineFileHeader {
+    char magic[8];
+    int32_t version, storage;
+    int32_t lo[3], m[3], n[3], full[3];
+    int64_t bytes;
+};
+
+RefineFileHeader refine_header(const lbm_refine *r, int64_t bytes)
+{
+    RefineFileHeader h{};
+    memcpy(h.magic, "LBMREF01", 8);
+    h.version = 1;
+    h.storage = r->c->storage;
+    for (int a = 0; a < 3; ++a) {
+        h.lo[a] = r->B.lo[a];
+        h.m[a] = r->B.m[a];
+        h.n[a] = r->B.n[a];
+        h.full[a] = r->B.full[a];
+    }
+    h.bytes = bytes;
+    return h;
+}
+
+int64_t moment_bytes(const lbm_refine *r)
+{
+    const SurfBox SC = r->B.coarse_box();
+    const int64_t rsz = r->c->storage == LBM_FP64 ? 8 : 4;
+    return (int64_t)NMOM * SC.E[0] * SC.E[1] * SC.E[2] * rsz;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_refine_save(lbm_refine *r, const char *path)
+{
+    if (!r) return LBM_ERR_ARG;
+    if (!path) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_save: null path");
+    if (!r->ready) return rfail(r->c, LBM_ERR_STATE, "lbm_refine_save: lbm_refine_init has not run");
+    const int64_t bytes = moment_bytes(r);
+    std::string buf((size_t)bytes, '\0');
+    RF_CUDA(cudaStreamSynchronize(r->stream), "sync");
+    RF_CUDA(cudaMemcpy(&buf[0], r->M[r->mcur], (size_t)bytes, cudaMemcpyDeviceToHost), "moments");
+    const RefineFileHeader h = refine_header(r, bytes);
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return rfail(r->c, LBM_ERR_ARG, std::string("lbm_refine_save: cannot open ") + path);
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1 && fwrite(buf.data(), 1, (size_t)bytes, fp) == (size_t)bytes;
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : rfail(r->c, LBM_ERR_ARG, std::string("lbm_refine_save: write failed for ") + path);
+}
+
+lbm_status lbm_refine_load(lbm_refine *r, const char *path)
+{
+    if (!r) return LBM_ERR_ARG;
+    if (!path) return rfail(r->c, LBM_ERR_ARG, "lbm_refine_load: null path");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return rfail(r->c, LBM_ERR_ARG, std::string("lbm_refine_load: cannot open ") + path);
+    const int64_t bytes = moment_bytes(r);
+    const RefineFileHeader want = refine_header(r, bytes);
+    RefineFileHeader h{};
+    std::string buf((size_t)bytes, '\0');
+    const bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(&h, &want, sizeof(h)) == 0 &&
+                    fread(&buf[0], 1, (size_t)bytes, fp) == (size_t)bytes;
+    fclose(fp);
+    if (!ok) return rfail(r->c, LBM_ERR_ARG, std::string("lbm_refine_load: ") + path + " does not match this coupling");
+    RF_CUDA(cudaStreamSynchronize(r->stream), "sync");
+    RF_CUDA(cudaMemcpy(r->M[r->mcur], buf.data(), (size_t)bytes, cudaMemcpyHostToDevice), "moments");
+    RF_CUDA(launch_marks(r), "refine marks");
+    RF_CUDA(cudaStreamSynchronize(r->stream), "sync");
+    r->ready = true;
     return LBM_OK;
 }
 

@@ -100,6 +100,8 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
     assert L.lbm_refine_create(dummy, dummy, i3, i3, None) == binding.LBM_ERR_ARG
     assert L.lbm_refine_init(None) == binding.LBM_ERR_ARG
     assert L.lbm_refine_step(None, 1) == binding.LBM_ERR_ARG
+    assert L.lbm_refine_save(None, b"x") == binding.LBM_ERR_ARG
+    assert L.lbm_refine_load(None, b"x") == binding.LBM_ERR_ARG
     L.lbm_refine_destroy(None)
 
 

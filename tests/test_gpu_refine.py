@@ -291,3 +291,42 @@ def test_refined_plunging_airfoil(storage):
     Fo = np.array(ro.fine.body.F)
     ftol = 1e-10 if storage == "fp64" else 1e-5
     assert np.abs(np.array(F) - Fo).max() <= ftol * np.abs(Fo).max()
+
+
+def test_refined_run_resumes_bitwise(tmp_path):
+    """Both levels saved with lbm_save and the coupling with lbm_refine_save
+    after 3 coarse steps; fresh contexts loaded from the files continue the
+    next 3 steps to the same bits on every node the refined step defines."""
+    import paper_1608_04658_gb300 as lbm
+    shape, lo, hi = (24, 20, 18), (5, 4, 3), (16, 13, 12)
+    rho, u, xi, amp = random_fields(shape, 41)
+    lat = lbm.Lattice(shape, 0.02, storage="fp32")
+    ref = lbm.Refinement(lat, lo, hi)
+    frho, fu, fxi, famp = random_fields(ref.fine.shape, 141)
+    lat.init_state(rho, u, xi, amp)
+    ref.fine.init_state(frho, fu, fxi, famp)
+    ref.init()
+    ref.step(3)
+    pc, pf, pr = (str(tmp_path / n) for n in ("coarse.bin", "fine.bin", "coupling.bin"))
+    lat.save(pc)
+    ref.fine.save(pf)
+    ref.save(pr)
+    ref.step(3)
+    fc, ff = lat.populations(), ref.fine.populations()
+
+    lat2 = lbm.Lattice(shape, 0.02, storage="fp32")
+    ref2 = lbm.Refinement(lat2, lo, hi)
+    lat2.load(pc)
+    ref2.fine.load(pf)
+    ref2.load(pr)
+    ref2.step(3)
+    vc = np.ones(fc.shape[1:], dtype=bool)
+    vc[lo[2] + 2:hi[2] - 1, lo[1] + 2:hi[1] - 1, lo[0] + 2:hi[0] - 1] = False
+    assert np.array_equal(lat2.populations()[:, vc], fc[:, vc])
+    assert np.array_equal(ref2.fine.populations()[:, :-1, :-1, :-1], ff[:, :-1, :-1, :-1])
+    # a coupling of another block refuses the file
+    from paper_1608_04658_gb300 import binding
+    ref3 = lbm.Refinement(lbm.Lattice(shape, 0.02, storage="fp32"), lo, (15, 13, 12))
+    with pytest.raises(lbm.LbmError) as e:
+        ref3.load(pr)
+    assert e.value.status == binding.LBM_ERR_ARG
