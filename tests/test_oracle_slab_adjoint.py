@@ -84,7 +84,7 @@ def _undivided(shape, faces):
         f = box.step(f, BETA)
     J = (torch.tensor(lam) * f).sum()
     J.backward()
-    return float(J), x.grad.numpy()
+    return float(J.detach()), x.grad.numpy()
 
 
 @pytest.mark.parametrize("world,shape,faces", [(1, (8, 6, 7), (0,) * 6), (2, (8, 6, 10), (0,) * 6),
