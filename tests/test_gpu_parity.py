@@ -642,9 +642,9 @@ def test_async_force_records(storage):
 
 
 # BF16 exceeds the 2e-3 bar of 16-bit storage on this case (3.8e-3 measured
-# on GB300: the inflow at 0.05 with rough random fields makes |g|/f large, and
-# BF16 rounds each store of g by up to 2^-9 of it); every other BF16 case meets
-# the bar.
+# on GB300: the inflow at 0.05 with rough random fields makes |g|/f close to 1,
+# and BF16, with 8 significand bits, rounds each store of g by up to 2^-8 of it);
+# every other BF16 case meets the bar.
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", pytest.param(
     "bf16", marks=pytest.mark.xfail(strict=True, reason="BF16 storage: 3.8e-3 measured against the 2e-3 bar"))])
 def test_plunging_airfoil(storage):
