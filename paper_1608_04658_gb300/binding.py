@@ -616,8 +616,8 @@ class Refinement:
     axis, periodic faces, twice the coarse viscosity, same storage, stabilizer
     and stream) is created here as ``self.fine``: fine node j sits at coarse
     coordinate lo + j/2.  Initialise both levels, call ``init()``, then
-    ``step(n)`` (n coarse steps, 2n fine steps).  ``close()`` this object
-    before closing either Lattice."""
+    ``step(n)`` (n coarse steps, 2n fine steps).  Closing either Lattice
+    closes this object first (it holds pointers to both levels)."""
 
     def __init__(self, coarse: Lattice, lo, hi):
         self.coarse = coarse
@@ -632,7 +632,9 @@ class Refinement:
         hi_a = (C.c_int32 * 3)(*self.hi)
         st = lib().lbm_refine_create(coarse._ctx, self.fine._ctx, lo_a, hi_a, C.byref(r))
         if st != LBM_OK:
-            raise LbmError(st, lib().lbm_last_error(coarse._ctx).decode())
+            err = LbmError(st, lib().lbm_last_error(coarse._ctx).decode())
+            self.fine.close()  # nothing refers to it yet: give its memory back now
+            raise err
         self._r = r
         import weakref
         coarse._dependents.append(weakref.ref(self))

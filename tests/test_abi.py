@@ -159,3 +159,39 @@ def test_closing_a_lattice_first_closes_its_refinements(monkeypatch):
     fine.close()
     ref.close()
     assert calls == [("refine_destroy", "r"), ("destroy", "c"), ("destroy", "f")]
+
+
+def test_a_refused_refinement_closes_the_fine_lattice_it_made(monkeypatch):
+    """lbm_refine_create refusing the block raises LbmError with the coarse
+    context's message, and the fine Lattice made for it is closed at once
+    (library calls recorded, not made)."""
+    import types
+
+    from paper_1608_04658_gb300 import binding
+    made = []
+
+    class FakeLattice:
+        def __init__(self, shape, nu, storage, **kw):
+            self.shape, self.nu, self._ctx, self.closed = shape, nu, "f", False
+            made.append(self)
+
+        def close(self):
+            self.closed = True
+
+    class Rec:
+        def lbm_refine_create(self, c, f, lo, hi, out):
+            return binding.LBM_ERR_ARG
+
+        def lbm_last_error(self, ctx):
+            return b"block outside the coarse lattice"
+
+    monkeypatch.setattr(binding, "lib", lambda: Rec())
+    monkeypatch.setattr(binding, "Lattice", FakeLattice)
+    coarse = types.SimpleNamespace(_ctx="c", shape=(24, 20, 18), storage="fp32", rho0=1.0, device=None,
+                                   _dependents=[],
+                                   params=types.SimpleNamespace(face=[0] * 6, nu=0.02, gamma_mode=0))
+    with pytest.raises(binding.LbmError) as e:
+        binding.Refinement(coarse, (5, 4, 3), (16, 13, 12))
+    assert e.value.status == binding.LBM_ERR_ARG and "outside" in str(e.value)
+    assert len(made) == 1 and made[0].closed and made[0].shape == (24, 20, 20)
+    assert coarse._dependents == []
