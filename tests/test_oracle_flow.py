@@ -376,6 +376,39 @@ def test_target_density_cancels_the_wall_motion_in_comoving_flow(orc, kind):
         assert max(resid.values()) < 1e-14
 
 
+def test_wall_at_rest_targets_the_bounce_back_density(orc):
+    """Sec. 3 with u_w = 0 (a held sphere in a random periodic state): the
+    dynamic density vanishes, so the target density is the static one, and
+    that equals the sum a brute-force pass over the state gives: at each
+    boundary node, the pull f_i(x_b - c_i) wherever that source is fluid and
+    the bounce-back population f'_opp(i)(x_b) wherever it is solid (the
+    missing directions, whose number is reported too)."""
+    c, _ = orc.lattice()
+    opp = [int(np.nonzero((c == -c[i]).all(1))[0][0]) for i in range(27)]
+    shape = (16, 14, 12)
+    nx, ny, nz = shape
+    o = orc.Oracle(shape, nu=0.05, body=orc.sphere_body((7.3, 6.6, 5.8), 3.1))
+    rho, u, xi = synth.parity_fields(shape, 5)
+    o.init_state(rho, u * 0.5 + 0.02, xi, 1e-3)
+    f, solid = o.get_f(), o.solid()
+    t = o.wall_targets_sampled(np.arange(nx * ny * nz))
+    b = np.nonzero(t[:, 0] > 0)[0]
+    assert len(b) > 200
+    assert np.all(t[b, 2] == 0.0) and np.all(t[b, 3] == t[b, 1])
+    for n in b:
+        x, y, z = n % nx, (n // nx) % ny, n // (nx * ny)
+        total, missing = 0.0, 0
+        for i in range(27):
+            sx, sy, sz = (x - c[i, 0]) % nx, (y - c[i, 1]) % ny, (z - c[i, 2]) % nz
+            if solid[sz, sy, sx]:
+                total += f[opp[i], z, y, x]
+                missing += 1
+            else:
+                total += f[i, sz, sy, sx]
+        assert missing == t[n, 0]
+        assert abs(total - t[n, 1]) <= 1e-15 * total
+
+
 def _angular_momentum(orc, f, fluid, X):
     """Fluid angular momentum about X: sum over fluid nodes of r x j with r
     the minimum-image offset of the node from X and j = sum_i c_i f_i."""
